@@ -1,0 +1,320 @@
+"""Benchmark of the constant-weight PIR server answer path on GB300.
+
+Workload (the metric's configuration): index PIR over n = 65536 rows of
+8192 16-bit coefficients (1 GiB of payload, 16 GiB resident in NTT form),
+codewords of weight k = 4 and length m = 37, BFV with N = 8192, four 54-bit
+primes, t = 65537; one query of 37 ciphertexts per step.  Keys and queries
+are uniform residues (the distribution of RLWE keys and ciphertexts); the
+answer path does the same work on them as on real encryptions.
+
+A step is one full answer: selection vector (product tree with
+relinearisation), plain multiplication and accumulation over all rows.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank answers its own
+queries against its own copy of the database (queries are independent).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PIR answer DB MB/s per query (N=8192,k=4); batched vs plain; p50/p99 latency"
+WL = dict(N=8192, L=4, n=65536, k=4, m=37, plen=8192, t=65537, coef_bytes=2)
+WORKLOAD_NAME = ("index PIR n=65536 rows x 8192 16-bit coefficients, k=4, m=37, "
+                 "BFV N=8192 L=4 (54-bit primes) t=65537, one query per step")
+IMAD_PER_MODMUL = 10  # see the design doc: three 64x64-bit products on 32-bit pipes
+IMAD_PER_SM_CLK = 64
+SMS = 152
+
+
+def payload_mb(rows: int) -> float:
+    return rows * WL["plen"] * WL["coef_bytes"] / 1e6
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_inputs(seed: int = 12):
+    from paper_2202_07569_gb300 import binding as B
+    from paper_2202_07569_gb300 import synthetic as syn
+
+    N, L, n, k, m = WL["N"], WL["L"], WL["n"], WL["k"], WL["m"]
+    q = B.default_primes(N, L)
+    rlk = syn.uniform_residues(syn.Stream(seed, 3), q, (L, 2), N)
+    query = syn.uniform_ciphertexts(seed + 1, q, m, N)
+    items = syn.payload(syn.Stream(seed, 1), n, WL["plen"], 1 << 16)
+    cw = np.stack([B.map_perfect(i, m, k) for i in range(n)])
+    return q, rlk, query, items, cw
+
+
+def modmuls_per_job(kind: str) -> float:
+    """Algorithmic 54-bit modular multiplications per job of a kernel class."""
+    N, L = WL["N"], WL["L"]
+    K = L + 1
+    logN = N.bit_length() - 1
+    ntt = N // 2 * logN + N
+    if kind == "tensor_intt":
+        return 3 * (L + K) * ntt + 4 * (L + K) * N
+    if kind == "relin_pm":
+        return L * ((L + 2) * (N // 2 * logN) + 2 * L * N + 2 * N)
+    if kind == "scale":
+        return 3 * N * (2 * L * K + 3 * L + 3 * K)
+    if kind == "lift":
+        return 2 * N * (2 * L + L * K + K)
+    return 0.0
+
+
+def run_gpu(args, rank: int, world: int, dist):
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    q, rlk, query, items, cw = make_inputs(12 + rank)
+    ctx = B.Context(WL["N"], q, WL["t"], rlk)
+    db = ctx.load_db(items, cw, WL["m"])
+    del items
+    stream = torch.cuda.current_stream()
+    d_query = torch.from_numpy(query.view(np.int64)).to(f"cuda:{dev}")
+    d_resp = torch.empty((2, WL["L"], WL["N"]), dtype=torch.int64, device=f"cuda:{dev}")
+
+    def step():
+        ctx.answer_device(db, d_query.data_ptr(), d_resp.data_ptr(), 0, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = ctx.last_stats()
+
+    # device-timed region: per-step events on the launching stream
+    ctx.set_option(B.OPT_KERNEL_TIMING, 1)
+    ctx.kernel_times()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    lat = sorted(a.elapsed_time(b) for a, b in evs)
+    ktimes = ctx.kernel_times()
+    ctx.set_option(B.OPT_KERNEL_TIMING, 0)
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the host-buffer call (H2D of the query, D2H of the
+    # response inside the timed region)
+    resp = np.zeros((2, WL["L"], WL["N"]), np.uint64)
+    ctx.answer(db, query)
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        resp = ctx.answer(db, query)
+        e2e.append(time.perf_counter() - t)
+    e2e_s = statistics.median(e2e)
+    h2d = query.nbytes
+    d2h = resp.nbytes
+
+    rows = WL["n"]
+    mb = payload_mb(rows)
+    out = {
+        "value": world * mb / (ms_per_step / 1e3),
+        "ms_per_step": ms_per_step,
+        "p50_ms": lat[len(lat) // 2],
+        "p99_ms": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
+        "items_per_s": world * rows / (ms_per_step / 1e3),
+        "e2e": {"value": world * mb / e2e_s, "unit": "MB/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "stats": stats,
+        "kernels": {k: {"ms": v[0] / args.steps, "launches": v[1] // max(1, args.steps)}
+                    for k, v in ktimes.items() if v[1]},
+        "clocks": clk.summary(),
+    }
+    # roofline of the dominant kernel class
+    dom = max((k for k in ktimes if ktimes[k][1]), key=lambda k: ktimes[k][0])
+    ms, launches = ktimes[dom]
+    jobs_per_launch = {"tensor_intt": stats["mults"], "relin_pm": stats["mults"],
+                       "scale": stats["mults"], "lift": 0}.get(dom, 0)
+    launches_per_step = launches / args.steps
+    work_per_launch = modmuls_per_job(dom) * jobs_per_launch / max(1.0, launches_per_step)
+    avg_launch_s = ms / launches / 1e3
+    sm_max = out["clocks"].get("sm_max_mhz") or 2070.0
+    peak = SMS * IMAD_PER_SM_CLK * sm_max * 1e6 / IMAD_PER_MODMUL / 1e12
+    achieved = work_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else 0.0
+    out["roofline"] = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                       "unit": "Tmodmul/s", "frac": achieved / peak if peak else None,
+                       "traffic": None,
+                       "peak_basis": f"{SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
+                                     f"/ {IMAD_PER_MODMUL} IMAD per 54-bit modmul"}
+    ctx.free_db(db)
+    ctx.close()
+    return out
+
+
+def cpu_baseline(rows_per_step: int | None = None, reps: int = 1):
+    """The oracle as it stands, OpenMP over rows on all host cores, on a
+    bounded sample of the workload's rows; returns (MB/s, cores, sample)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    q, rlk, query, items, cw = make_inputs(12)
+    O = oracle.Oracle(WL["N"], q, WL["t"])
+    rows = rows_per_step or 2 * cores
+    times = []
+    for r in range(reps):
+        sel = np.arange(r * rows, (r + 1) * rows) % WL["n"]
+        t = time.perf_counter()
+        O.answer(items[sel], cw[sel], WL["m"], query, rlk, nthreads=cores)
+        times.append(time.perf_counter() - t)
+    mbps = [payload_mb(rows) / t for t in times]
+    return mbps, cores, f"{rows} of {WL['n']} rows per answer (3 multiplications each)"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl" if args.impl == "cuda" else "gloo")
+        dist = tdist
+
+    base = {"metric": METRIC, "unit": "MB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "rows": WL["n"], "k": WL["k"], "m": WL["m"],
+                       "N": WL["N"], "L": WL["L"],
+                       "payload_mb_per_query": payload_mb(WL["n"]),
+                       "l2": "inputs larger than L2 (16 GiB NTT-form database streamed per step)",
+                       "parallelism": "one query stream per GPU (replicas)"}}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cores = os.cpu_count() or 1
+        rows = 2 * cores
+        cpu_baseline(max(2, rows // 4), 1)  # warm the oracle (tables, page-in)
+        mbps, cores, sample = cpu_baseline(rows, args.warmup + args.steps)
+        timed = mbps[args.warmup:]
+        v = statistics.mean(timed)
+        line = dict(base, impl="reference", value=v,
+                    ms_per_step=payload_mb(rows) / v * 1e3,
+                    cpu_baseline={"value": v, "unit": "MB/s", "cores": cores, "kind": "oracle",
+                                  "sample": sample},
+                    e2e={"value": v, "unit": "MB/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 0})
+        print(json.dumps(line), flush=True)
+        return
+
+    from paper_2202_07569_gb300 import build as cuda_build
+
+    if rank == 0:
+        cuda_build.build()
+    if dist:
+        dist.barrier()
+    res = run_gpu(args, rank, world, dist)
+    if rank != 0:
+        return
+    line = dict(base)
+    line.update(res)
+    if world == 1 and not args.no_cpu_baseline:
+        mbps, cores, sample = cpu_baseline(None, 1)
+        line["cpu_baseline"] = {"value": mbps[0], "unit": "MB/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * cwpir.h -- C ABI of the GB300 (sm_103a) server answer path of
+ * constant-weight PIR (Mahdavi & Kerschbaum, arXiv 2202.07569).
+ *
+ * The calls follow the paper's protocol stages (Sec. 3.3, Table "Stages of
+ * PIR using constant-weight codewords"): Setup (parameters and evaluation
+ * keys, then the database in plaintext form) and Process (query expansion,
+ * selection vector, inner product).  Query construction and Extract are
+ * client-side and not part of this library.
+ *
+ * Conventions shared by every call
+ *  - Ring: R_Q = Z_Q[x]/(x^N + 1) with Q = q_0 * ... * q_{L-1}; plaintexts in
+ *    R_t (Sec. 2.1.1).  N is a power of two in [1024, 16384], 1 <= L <= 8,
+ *    every q_j is a prime with 2^53 < q_j < 2^54 and q_j = 1 (mod 2N), all
+ *    distinct; t is a prime in [3, 2^20).
+ *  - Polynomials cross the ABI in RNS coefficient form: u64 residues,
+ *    limb-major, [L][N], limb j holding the residues mod q_j, each < q_j.
+ *    A ciphertext is [2][L][N] (c0, c1), decrypting as c0 + c1*s.
+ *    The NTT form used inside the library is never observable.
+ *  - Switching keys are [L][2][L][N]: digit i, component (0: b_i, 1: a_i),
+ *    limb j, with b_i = -a_i*s + e_i + g_i*w (mod Q) where g_i is the CRT
+ *    idempotent of q_i (g_i = 1 mod q_i, 0 mod q_l for l != i) and w = s^2
+ *    (relinearisation) or s(x^g) (substitution by g).  Key switching of z
+ *    uses the digits D_i = [z]_{q_i} in [0, q_i): sum_i D_i * (b_i, a_i).
+ *  - Multiplication M (Sec. 2.1.1): lift both ciphertexts to centered
+ *    integers, multiply exactly, e_l = round(t * d_l / Q) for the three
+ *    products, then relinearise e_2.  Results are exact integer functions of
+ *    the inputs: identical bits for identical inputs, on any launch shape.
+ *  - Host pointers are caller-owned and only read (or written for outputs)
+ *    during the call; nothing is retained.  Device pointers (the *_device
+ *    calls) must stay valid until the work on the given stream completes.
+ *    The library owns all device memory it allocates until cwpir_free_db or
+ *    cwpir_destroy.
+ *  - Calls on one context are not thread-safe; use one context per thread
+ *    or serialise.  Every call returns CWPIR_OK (0) or a negative code; the
+ *    message of the last failure is available from cwpir_last_error.
+ */
+#ifndef CWPIR_H
+#define CWPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CWPIR_ABI_VERSION 1
+
+enum {
+  CWPIR_OK = 0,
+  CWPIR_EINVAL = -1,    /* an argument, shape or residue is out of range */
+  CWPIR_ENOMEM = -2,    /* device or host allocation failed */
+  CWPIR_ENODB = -3,     /* unknown database id */
+  CWPIR_ECUDA = -4,     /* a CUDA runtime call failed */
+  CWPIR_ETIMEDOUT = -5, /* a bounded device wait gave up */
+  CWPIR_EBUSY = -6,     /* serving: no admission slot or memory right now */
+  CWPIR_ENOKEY = -7,    /* a required Galois key was not supplied */
+  CWPIR_EINTERNAL = -8  /* a device-side consistency check failed */
+};
+
+typedef struct cwpir_ctx cwpir_ctx;
+
+/* Encryption parameters (Sec. 2.1.1; Sec. 4-5 use N in {4096, 8192, 16384}). */
+typedef struct {
+  uint32_t N;         /* ring degree */
+  uint32_t L;         /* number of ciphertext primes */
+  const uint64_t *q;  /* [L] primes, see conventions */
+  uint64_t t;         /* plaintext modulus */
+} cwpir_params;
+
+/* Evaluation keys.  relin: [L][2][L][N] for w = s^2.  galois: for query
+ * expansion with compression factor c the substitutions use the elements
+ * N/2^a + 1 for a < c (Alg. Query Expansion); n_galois keys are given with
+ * their elements in galois_elts, key g at galois + idx*L*2*L*N.  n_galois
+ * may be 0 when no query is compressed. */
+typedef struct {
+  const uint64_t *relin;
+  uint32_t n_galois;
+  const uint32_t *galois_elts;
+  const uint64_t *galois;
+} cwpir_keys;
+
+/* ---- library information and host helpers ---- */
+int cwpir_abi_version(void);
+const char *cwpir_strerror(int code);
+/* Message of the last failing call on ctx (or of the last failing setup in
+ * this thread when ctx is NULL).  Valid until the next call on ctx. */
+const char *cwpir_last_error(const cwpir_ctx *ctx);
+/* The L largest primes q < 2^54 with q = 1 (mod 2N), descending (all above
+ * 2^53 for N <= 16384 and L <= 8). */
+int cwpir_default_primes(uint32_t N, uint32_t L, uint64_t *q_out);
+/* Perfect mapping (Alg. Perfect Mapping, Sec. 3.2): x in [C(m,k)] -> the
+ * x-th codeword of CW(m,k); writes its k one-positions in ascending order.
+ * EINVAL if x >= C(m,k), k = 0, k > m or m > 65535. */
+int cwpir_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out);
+/* Smallest m with C(m,k) >= n (Sec. 3: "choose m such that C(m,k) >= n"). */
+int cwpir_code_length(uint64_t n, uint32_t k, uint32_t *m_out);
+
+/* ---- Setup (server, offline) ---- */
+/* Validates params and keys, builds the device tables and uploads the keys
+ * (converted to the internal NTT form).  *out receives a new context.
+ * EINVAL on invalid params or key residues >= q_j; ENOMEM; ECUDA. */
+int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys,
+                cwpir_ctx **out);
+void cwpir_destroy(cwpir_ctx *ctx);
+
+/* Database load (Setup, Sec. 3.3.1): n rows of payload_len <= N plaintext
+ * coefficients each < t (row-major [n][payload_len], zero-padded to N), and
+ * each row's codeword in CW(m,k) as k ascending one-positions < m
+ * ([n][k]).  For index PIR the codeword of row i is the perfect mapping of
+ * i; for keyword PIR (Sec. 3.3.6) the mapping of the row's keyword.  The
+ * rows are lifted to centered residues and kept in HBM in NTT form.
+ * 1 <= k <= 16, k <= m <= 16384, 1 <= n <= 2^24.  *db_id receives a handle.
+ * EINVAL (including a coefficient >= t or a bad codeword), ENOMEM, ECUDA. */
+int cwpir_load_db(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len, uint32_t k,
+                  uint32_t m, const uint32_t *items, const uint16_t *codewords,
+                  int32_t *db_id);
+int cwpir_free_db(cwpir_ctx *ctx, int32_t db_id);
+
+/* ---- Process (server, online) ---- */
+/* Answer one query against a database (Sec. 3.3.3): expansion when c > 0
+ * (Alg. Query Expansion), the selection vector by the plain constant-weight
+ * equality operator (Alg. Selection Vector Calculation, Eq. plain-cw-eq,
+ * balanced pairwise product tree over the ascending positions), and the
+ * inner product sum_i sel_i * DB_i (Eq. baseline-pir).
+ * query: [h][2][L][N] with h = m when c = 0, else h = ceil(m / 2^c) (Alg.
+ * Query); c <= log2 N and needs the Galois keys for N/2^a + 1, a < c.
+ * response: [2][L][N], written.  Host buffers; blocks until done.
+ * EINVAL, ENODB, ENOKEY, ECUDA, EINTERNAL. */
+int cwpir_answer(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
+                 const uint64_t *query, uint64_t *response);
+/* Same with device buffers, enqueued on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream).  Returns once the work is enqueued. */
+int cwpir_answer_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
+                        const uint64_t *d_query, uint64_t *d_response,
+                        void *stream);
+
+/* ---- the steps of Process, one at a time (host buffers) ---- */
+/* Homomorphic multiplication M of two ciphertexts with relinearisation. */
+int cwpir_mul(cwpir_ctx *ctx, const uint64_t *a, const uint64_t *b,
+              uint64_t *out);
+/* Substitution Sub_g (Sec. 2.1.1): automorphism x -> x^g plus key switch
+ * with the Galois key of g.  ENOKEY if no key for g was supplied. */
+int cwpir_substitute(cwpir_ctx *ctx, uint32_t g, const uint64_t *ct,
+                     uint64_t *out);
+/* Query expansion (Alg. Query Expansion): h = ceil(m / 2^c) ciphertexts ->
+ * the first m expanded ciphertexts, out: [m][2][L][N].  1 <= c. */
+int cwpir_expand(cwpir_ctx *ctx, uint32_t c, uint32_t m, const uint64_t *query,
+                 uint64_t *out);
+/* Selection-vector entries sel_i (Alg. Selection Vector Calculation) for
+ * `count` rows of a database: out: [count][2][L][N]. */
+int cwpir_selection(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
+                    const uint64_t *query, uint64_t count,
+                    const uint64_t *rows, uint64_t *out);
+/* Plain multiplication PM of a ciphertext by row `row` of a database. */
+int cwpir_plain_mul(cwpir_ctx *ctx, int32_t db_id, uint64_t row,
+                    const uint64_t *ct, uint64_t *out);
+
+/* ---- options ---- */
+enum {
+  /* 1 (default): compute each distinct first-level product of the tree once
+   * per query and share it between rows; 0: every row's tree in full.  The
+   * response bits are identical either way. */
+  CWPIR_OPT_SHARE_LEVEL1 = 1,
+  /* rows per device batch (0 = automatic) */
+  CWPIR_OPT_BATCH_ROWS = 2,
+  /* 1 (default): replay the answer as a captured CUDA graph */
+  CWPIR_OPT_USE_GRAPH = 3,
+  /* 1: bracket every kernel launch with CUDA events on its stream and add
+   * the durations per kernel class (read with cwpir_kernel_times); 0
+   * (default): no events */
+  CWPIR_OPT_KERNEL_TIMING = 4
+};
+int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
+
+/* Work counters of the last answer on ctx (for throughput accounting). */
+typedef struct {
+  uint64_t rows;            /* database rows processed */
+  uint64_t mults;           /* homomorphic multiplications executed */
+  uint64_t substitutions;   /* substitutions executed (expansion) */
+  uint64_t ntt_polys;       /* length-N NTTs/INTTs executed (per limb) */
+  uint64_t kernel_launches; /* kernels launched */
+  uint64_t db_bytes_read;   /* NTT-form database bytes streamed */
+} cwpir_stats;
+int cwpir_last_stats(const cwpir_ctx *ctx, cwpir_stats *out);
+
+/* Kernel classes of the answer path, for cwpir_kernel_times. */
+enum {
+  CWPIR_K_TENSOR = 0,  /* tensor product + inverse NTT */
+  CWPIR_K_SCALE = 1,   /* exact scale-down round(t d / Q) */
+  CWPIR_K_RELIN = 2,   /* key switching fused with plain multiplication */
+  CWPIR_K_LIFT = 3,    /* centered base conversion Q -> P */
+  CWPIR_K_NTT = 4,     /* stand-alone NTTs */
+  CWPIR_K_ACC = 5,     /* accumulation of partial products */
+  CWPIR_K_EXPAND = 6,  /* automorphisms, substitution key switches, combine */
+  CWPIR_K_CLASSES = 7
+};
+/* With CWPIR_OPT_KERNEL_TIMING on: waits for the recorded work, then writes
+ * per class the summed milliseconds (ms) and launch counts (launches),
+ * arrays of CWPIR_K_CLASSES entries, for all launches since the previous
+ * call, and resets the sums. */
+int cwpir_kernel_times(cwpir_ctx *ctx, double *ms, uint64_t *launches);
+const char *cwpir_kernel_class_name(int cls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -632,28 +632,31 @@ int orc_keyswitch(const orc_ctx *c, const uint64_t *z, const uint64_t *key,
                   uint64_t *out) {
   uint32_t N = c->N, L = c->L;
   size_t ln = LN(c);
-  uint64_t *d = malloc(N * sizeof(uint64_t)), *kp = malloc(N * sizeof(uint64_t));
-  uint64_t *acc0 = malloc(N * sizeof(uint64_t)), *acc1 = malloc(N * sizeof(uint64_t));
+  /* Output limb j: sum_i (D_i mod q_j) * key_ij in Z_{q_j}[x]/(x^N+1); the
+   * products are summed in the NTT domain and transformed back once. */
+#pragma omp parallel for schedule(static)
   for (uint32_t j = 0; j < L; ++j) {
     const ntab *T = &c->qt[j];
-    memset(acc0, 0, N * sizeof(uint64_t));
-    memset(acc1, 0, N * sizeof(uint64_t));
+    uint64_t *d = malloc(N * sizeof(uint64_t)), *kp = malloc(N * sizeof(uint64_t));
+    uint64_t *acc[2] = {calloc(N, sizeof(uint64_t)), calloc(N, sizeof(uint64_t))};
     for (uint32_t i = 0; i < L; ++i) {
       for (uint32_t x = 0; x < N; ++x) d[x] = z[(size_t)i * N + x] % c->q[j];
+      nega_fwd(T, d);
       for (int comp = 0; comp < 2; ++comp) {
-        const uint64_t *kk = key + ((size_t)i * 2 + comp) * ln + (size_t)j * N;
-        nega_mul(T, d, kk, kp);
-        uint64_t *acc = comp ? acc1 : acc0;
-        for (uint32_t x = 0; x < N; ++x) acc[x] = addmod(acc[x], kp[x], T->p);
+        memcpy(kp, key + ((size_t)i * 2 + comp) * ln + (size_t)j * N, N * sizeof(uint64_t));
+        nega_fwd(T, kp);
+        for (uint32_t x = 0; x < N; ++x)
+          acc[comp][x] = addmod(acc[comp][x], mulmod(d[x], kp[x], T->p), T->p);
       }
     }
-    memcpy(out + (size_t)j * N, acc0, N * sizeof(uint64_t));
-    memcpy(out + ln + (size_t)j * N, acc1, N * sizeof(uint64_t));
+    for (int comp = 0; comp < 2; ++comp) {
+      nega_inv(T, acc[comp]);
+      memcpy(out + comp * ln + (size_t)j * N, acc[comp], N * sizeof(uint64_t));
+      free(acc[comp]);
+    }
+    free(d);
+    free(kp);
   }
-  free(d);
-  free(kp);
-  free(acc0);
-  free(acc1);
   return 0;
 }
 
@@ -778,7 +781,6 @@ int orc_expand(const orc_ctx *c, uint32_t h, const uint64_t *query, uint32_t cf,
   if ((1u << cf) > N || m > (uint64_t)h << cf) return -1;
   uint32_t B = 1u << cf;
   uint64_t *cts = malloc((size_t)B * ctw * sizeof(uint64_t));
-  uint64_t *c0 = malloc(ctw * sizeof(uint64_t)), *c1 = malloc(ctw * sizeof(uint64_t));
   uint32_t written = 0;
   for (uint32_t j = 0; j < h && written < m; ++j) {
     memcpy(cts, query + (size_t)j * ctw, ctw * sizeof(uint64_t));
@@ -786,21 +788,24 @@ int orc_expand(const orc_ctx *c, uint32_t h, const uint64_t *query, uint32_t cf,
       uint32_t two_a = 1u << a;
       uint32_t g = N / two_a + 1;
       const uint64_t *gk = gkeys + (size_t)a * c->L * ctw;
+      /* the iterations over b touch disjoint entries: run them in parallel */
+#pragma omp parallel for schedule(dynamic, 1)
       for (uint32_t b = 0; b < two_a; ++b) {
+        uint64_t *c0 = malloc(ctw * sizeof(uint64_t)), *c1 = malloc(ctw * sizeof(uint64_t));
         uint64_t *cb = cts + (size_t)b * ctw, *cb2 = cts + (size_t)(b + two_a) * ctw;
         orc_substitute(c, g, cb, gk, c0);          /* c0 <- Sub(cts[b])        */
         ct_monomial(c, -(int64_t)two_a, c0, c1);  /* c1 <- x^-2^a * c0        */
         ct_monomial(c, -(int64_t)two_a, cb, cb2); /* cts[b+2^a] <- x^-2^a cts[b] */
         ct_add(c, cb, c0, cb);                    /* cts[b] += c0             */
         ct_sub(c, cb2, c1, cb2);                  /* cts[b+2^a] -= c1         */
+        free(c0);
+        free(c1);
       }
     }
     for (uint32_t b = 0; b < B && written < m; ++b, ++written)
       memcpy(out + (size_t)written * ctw, cts + (size_t)b * ctw, ctw * sizeof(uint64_t));
   }
   free(cts);
-  free(c0);
-  free(c1);
   return 0;
 }
 

@@ -1,0 +1,246 @@
+"""ctypes binding of the C ABI in ``include/cwpir.h`` (argument marshalling
+only: every step of the answer path runs in the CUDA library).
+
+The library is ``_build/libcwpir.so`` built by ``build.py``.  Loading fails
+loudly when it is missing; there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+u16p = np.ctypeslib.ndpointer(dtype=np.uint16, flags="C_CONTIGUOUS")
+
+OPT_SHARE_LEVEL1 = 1
+OPT_BATCH_ROWS = 2
+OPT_USE_GRAPH = 3
+OPT_KERNEL_TIMING = 4
+K_CLASSES = 7
+
+
+class CwpirError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"cwpir error {code}: {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("L", C.c_uint32), ("q", C.POINTER(C.c_uint64)),
+                ("t", C.c_uint64)]
+
+
+class _Keys(C.Structure):
+    _fields_ = [("relin", C.POINTER(C.c_uint64)), ("n_galois", C.c_uint32),
+                ("galois_elts", C.POINTER(C.c_uint32)), ("galois", C.POINTER(C.c_uint64))]
+
+
+class Stats(C.Structure):
+    _fields_ = [("rows", C.c_uint64), ("mults", C.c_uint64), ("substitutions", C.c_uint64),
+                ("ntt_polys", C.c_uint64), ("kernel_launches", C.c_uint64),
+                ("db_bytes_read", C.c_uint64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"CUDA library {path} is missing: run paper_2202_07569_gb300.build.build() "
+                "(or __graft_entry__.build()) first")
+        l = C.CDLL(path)
+        I, U32, U64, vp = C.c_int, C.c_uint32, C.c_uint64, C.c_void_p
+        sig = {
+            "cwpir_abi_version": (I, []),
+            "cwpir_strerror": (C.c_char_p, [I]),
+            "cwpir_last_error": (C.c_char_p, [vp]),
+            "cwpir_default_primes": (I, [U32, U32, u64p]),
+            "cwpir_map_perfect": (I, [U64, U32, U32, u16p]),
+            "cwpir_code_length": (I, [U64, U32, C.POINTER(U32)]),
+            "cwpir_setup": (I, [C.POINTER(_Params), C.POINTER(_Keys), C.POINTER(vp)]),
+            "cwpir_destroy": (None, [vp]),
+            "cwpir_load_db": (I, [vp, U64, U32, U32, U32, u32p, u16p, C.POINTER(C.c_int32)]),
+            "cwpir_free_db": (I, [vp, C.c_int32]),
+            "cwpir_answer": (I, [vp, C.c_int32, U32, u64p, u64p]),
+            "cwpir_answer_device": (I, [vp, C.c_int32, U32, vp, vp, vp]),
+            "cwpir_mul": (I, [vp, u64p, u64p, u64p]),
+            "cwpir_substitute": (I, [vp, U32, u64p, u64p]),
+            "cwpir_expand": (I, [vp, U32, U32, u64p, u64p]),
+            "cwpir_selection": (I, [vp, C.c_int32, U32, u64p, U64, u64p, u64p]),
+            "cwpir_plain_mul": (I, [vp, C.c_int32, U64, u64p, u64p]),
+            "cwpir_set_option": (I, [vp, I, C.c_int64]),
+            "cwpir_last_stats": (I, [vp, C.POINTER(Stats)]),
+            "cwpir_kernel_times": (I, [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+            "cwpir_kernel_class_name": (C.c_char_p, [I]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+        return l
+
+
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def abi_version() -> int:
+    return int(lib().cwpir_abi_version())
+
+
+def default_primes(N: int, L: int) -> np.ndarray:
+    out = np.zeros(L, np.uint64)
+    rc = lib().cwpir_default_primes(N, L, out)
+    if rc:
+        raise CwpirError(rc, "default primes")
+    return out
+
+
+def map_perfect(x: int, m: int, k: int) -> np.ndarray:
+    pos = np.zeros(k, np.uint16)
+    rc = lib().cwpir_map_perfect(int(x), m, k, pos)
+    if rc:
+        raise CwpirError(rc, f"perfect mapping of {x} into CW({m},{k})")
+    return pos
+
+
+def code_length(n: int, k: int) -> int:
+    m = C.c_uint32()
+    rc = lib().cwpir_code_length(int(n), k, C.byref(m))
+    if rc:
+        raise CwpirError(rc, "code length")
+    return int(m.value)
+
+
+class Context:
+    """A cwpir_ctx: parameters, evaluation keys and resident databases."""
+
+    def __init__(self, N: int, q, t: int, relin, galois: dict | None = None):
+        l = lib()
+        self._q = _u64(q)
+        self.N, self.L, self.t = int(N), int(self._q.size), int(t)
+        self._relin = _u64(relin)
+        galois = galois or {}
+        elts = np.array(sorted(galois), dtype=np.uint32)
+        gk = (np.stack([_u64(galois[g]) for g in elts]) if len(elts)
+              else np.zeros(1, np.uint64))
+        self._gk = np.ascontiguousarray(gk)
+        self._elts = elts if len(elts) else np.zeros(1, np.uint32)
+        p = _Params(self.N, self.L, self._q.ctypes.data_as(C.POINTER(C.c_uint64)), self.t)
+        k = _Keys(self._relin.ctypes.data_as(C.POINTER(C.c_uint64)), len(elts),
+                  self._elts.ctypes.data_as(C.POINTER(C.c_uint32)),
+                  self._gk.ctypes.data_as(C.POINTER(C.c_uint64)))
+        h = C.c_void_p()
+        rc = l.cwpir_setup(C.byref(p), C.byref(k), C.byref(h))
+        if rc:
+            raise CwpirError(rc, l.cwpir_last_error(None).decode())
+        self._h = h
+        # the library copied what it needs
+        del self._relin, self._gk
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cwpir_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise CwpirError(rc, lib().cwpir_last_error(self._h).decode())
+
+    @property
+    def ct_shape(self):
+        return (2, self.L, self.N)
+
+    def load_db(self, items, codewords, m: int) -> int:
+        items = np.ascontiguousarray(items, dtype=np.uint32)
+        cw = np.ascontiguousarray(codewords, dtype=np.uint16)
+        n = cw.shape[0]
+        plen = items.shape[1] if items.ndim == 2 else 0
+        if items.ndim == 2 and items.shape[0] != n:
+            raise ValueError("items and codewords disagree on n")
+        db = C.c_int32()
+        self._check(lib().cwpir_load_db(self._h, n, plen, cw.shape[1], m,
+                                        items.reshape(-1) if plen else np.zeros(1, np.uint32),
+                                        cw.reshape(-1), C.byref(db)))
+        return int(db.value)
+
+    def free_db(self, db: int):
+        self._check(lib().cwpir_free_db(self._h, db))
+
+    def answer(self, db: int, query, c: int = 0) -> np.ndarray:
+        out = np.zeros(self.ct_shape, np.uint64)
+        self._check(lib().cwpir_answer(self._h, db, c, _u64(query), out))
+        return out
+
+    def answer_device(self, db: int, query_ptr: int, resp_ptr: int, c: int = 0,
+                      stream: int = 0):
+        self._check(lib().cwpir_answer_device(self._h, db, c, query_ptr, resp_ptr, stream))
+
+    def mul(self, a, b) -> np.ndarray:
+        out = np.zeros(self.ct_shape, np.uint64)
+        self._check(lib().cwpir_mul(self._h, _u64(a), _u64(b), out))
+        return out
+
+    def substitute(self, g: int, ct) -> np.ndarray:
+        out = np.zeros(self.ct_shape, np.uint64)
+        self._check(lib().cwpir_substitute(self._h, g, _u64(ct), out))
+        return out
+
+    def expand(self, query, c: int, m: int) -> np.ndarray:
+        out = np.zeros((m,) + self.ct_shape, np.uint64)
+        self._check(lib().cwpir_expand(self._h, c, m, _u64(query), out))
+        return out
+
+    def selection(self, db: int, query, rows, c: int = 0) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        out = np.zeros((rows.size,) + self.ct_shape, np.uint64)
+        self._check(lib().cwpir_selection(self._h, db, c, _u64(query), rows.size, rows, out))
+        return out
+
+    def plain_mul(self, db: int, row: int, ct) -> np.ndarray:
+        out = np.zeros(self.ct_shape, np.uint64)
+        self._check(lib().cwpir_plain_mul(self._h, db, row, _u64(ct), out))
+        return out
+
+    def set_option(self, option: int, value: int):
+        self._check(lib().cwpir_set_option(self._h, option, value))
+
+    def last_stats(self) -> dict:
+        s = Stats()
+        self._check(lib().cwpir_last_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def kernel_times(self) -> dict:
+        """{class name: (milliseconds, launches)} since the previous call."""
+        ms = (C.c_double * K_CLASSES)()
+        n = (C.c_uint64 * K_CLASSES)()
+        self._check(lib().cwpir_kernel_times(self._h, ms, n))
+        return {lib().cwpir_kernel_class_name(i).decode(): (ms[i], int(n[i]))
+                for i in range(K_CLASSES)}

@@ -1,0 +1,223 @@
+// arith.cuh -- word-size modular arithmetic and per-coefficient RNS steps of
+// the BFV multiplication (FV scheme, arXiv 2202.07569 Sec. 2.1.1), written
+// for the 32-bit integer pipes of sm_103a.  Every function is exact.
+//
+// Residues are u64 values below primes q < 2^54.  The functions are
+// __host__ __device__ so that the same arithmetic can be exercised on the
+// CPU by the test suite.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define CW_HD __host__ __device__ __forceinline__
+#else
+#define CW_HD static inline
+#endif
+
+namespace cw {
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+constexpr int kMaxL = 8;       // ciphertext primes
+constexpr int kMaxK = 9;       // extension primes (L + 1)
+constexpr int kMaxP = kMaxL + kMaxK;
+
+CW_HD u64 mulhi(u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
+#else
+  return (u64)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+CW_HD u64 addq(u64 a, u64 b, u64 q) {
+  u64 s = a + b;
+  return s >= q ? s - q : s;
+}
+CW_HD u64 subq(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// Shoup multiplication by a constant w < q with ws = floor(w * 2^64 / q):
+// for any a < 2^64, a*w - mulhi(a, ws)*q lies in [0, 2q).  Result < q.
+CW_HD u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
+  u64 r = a * w - mulhi(a, ws) * q;
+  return r >= q ? r - q : r;
+}
+
+// Barrett multiplication of two variables a, b < 2q (product < 2^110) for a
+// prime 2^53 < q < 2^54 with mu = floor(2^116 / q) < 2^63.
+// With x = a*b, x1 = floor(x / 2^52), qh = floor(x1 * mu / 2^64):
+//   qh <= x/q  and  qh > x/q - x/2^116 - 2^52/q - 1 > x/q - 2,
+// so r = x - qh*q is in [0, 2q) and one subtraction finishes it.
+CW_HD u64 barrett(u64 a, u64 b, u64 q, u64 mu) {
+  u64 lo = a * b, hi = mulhi(a, b);
+  u64 x1 = (hi << 12) | (lo >> 52);
+  u64 qh = mulhi(x1, mu);
+  u64 r = lo - qh * q;
+  return r >= q ? r - q : r;
+}
+
+// ---------------------------------------------------------------------
+// NTT butterflies (negacyclic, psi = primitive 2N-th root of unity).
+// Forward: Cooley-Tukey with the powers of psi in bit-reversed order,
+// natural-order input, bit-reversed output.  Inverse: Gentleman-Sande with
+// the powers of psi^-1, bit-reversed input, natural output, then * N^-1.
+// Stage s of the forward transform has m = 2^s groups of half-length
+// len = N / 2^(s+1); butterfly b (< N/2) is in group b / len.
+// ---------------------------------------------------------------------
+CW_HD void fwd_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *psi,
+                    const u64 *psi_s, u64 q) {
+  u32 len = 1u << logh, g = b >> logh, pos = b & (len - 1);
+  u32 j = (g << (logh + 1)) + pos;
+  u64 U = a[j];
+  u64 V = shoup(a[j + len], psi[m + g], psi_s[m + g], q);
+  a[j] = addq(U, V, q);
+  a[j + len] = subq(U, V, q);
+}
+CW_HD void inv_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *ipsi,
+                    const u64 *ipsi_s, u64 q) {
+  u32 len = 1u << logh, g = b >> logh, pos = b & (len - 1);
+  u32 j = (g << (logh + 1)) + pos;
+  u64 U = a[j], V = a[j + len];
+  a[j] = addq(U, V, q);
+  a[j + len] = shoup(subq(U, V, q), ipsi[m + g], ipsi_s[m + g], q);
+}
+
+// Per-prime NTT data in device memory.
+struct NttPrime {
+  u64 q, mu;             // prime, Barrett constant floor(2^116/q)
+  u64 ninv, ninv_s;      // N^-1 mod q and Shoup companion
+  const u64 *psi, *psi_s;   // [N] psi^bitrev(i)
+  const u64 *ipsi, *ipsi_s; // [N] psi^-bitrev(i)
+};
+
+// ---------------------------------------------------------------------
+// Exact centered base conversion between RNS bases.
+//
+// x is given by residues x_j modulo the source primes s_j (product S).
+// With y_j = [x_j * (S/s_j)^-1]_{s_j}, sum_j y_j (S/s_j) = x + v S where
+// v = floor(sum_j y_j / s_j), and the centered representative of x is
+// x_c = sum_j y_j (S/s_j) - rho S with rho = round(sum_j y_j / s_j)
+// (S is odd, so sum_j y_j/s_j is never a half integer).
+//
+// rho is read from a 64.64 fixed-point sum of phi_j <= y_j 2^64 / s_j,
+// each low by less than 2 units, so the sum is low by less than 2*ns units:
+// rho = hi(2^63 + sum phi) unless the low word is within 2*ns of 2^64; in
+// that case x is within 2*ns*S/2^64 of S/2 and the exact comparison of x
+// with (S-1)/2 in mixed radix (Garner) decides.
+// ---------------------------------------------------------------------
+struct BaseConv {
+  u32 ns, nd;
+  u64 s[kMaxK];                 // source primes
+  u64 theta[kMaxK], theta_s[kMaxK]; // (S/s_j)^-1 mod s_j
+  u64 w_hi[kMaxK], w_lo[kMaxK];     // floor(2^128 / s_j)
+  u64 d[kMaxK];                 // target primes
+  u64 hat[kMaxK][kMaxK], hat_s[kMaxK][kMaxK]; // (S/s_j) mod d_k
+  u64 smod[kMaxK], smod_s[kMaxK];   // S mod d_k
+  u64 mrinv[kMaxK][kMaxK], mrinv_s[kMaxK][kMaxK]; // s_i^-1 mod s_j, i < j
+  u64 half_mr[kMaxK];           // mixed-radix digits of (S-1)/2
+};
+
+// 1 if x > (S-1)/2, by exact mixed-radix comparison.
+template <int NS>
+CW_HD u64 mr_greater_half(const u64 *x, const BaseConv &C) {
+  u64 a[NS];
+  for (int j = 0; j < NS; ++j) {
+    u64 sj = C.s[j], v = x[j];
+    for (int i = 0; i < j; ++i) {
+      u64 ai = a[i] >= sj ? a[i] - sj : a[i];
+      v = shoup(subq(v, ai, sj), C.mrinv[i][j], C.mrinv_s[i][j], sj);
+    }
+    a[j] = v;
+  }
+  for (int j = NS - 1; j >= 0; --j)
+    if (a[j] != C.half_mr[j]) return a[j] > C.half_mr[j] ? 1 : 0;
+  return 0;  // equal: x = (S-1)/2 is not greater
+}
+
+// hi(2^63 + sum_j phi_j) and whether the low word is in the ambiguous zone.
+template <int NS>
+CW_HD u64 round_sum(const u64 *y, const BaseConv &C, bool *ambiguous) {
+  u64 lo = 0x8000000000000000ull, hi = 0;
+  for (int j = 0; j < NS; ++j) {
+    u64 phi = y[j] * C.w_hi[j] + mulhi(y[j], C.w_lo[j]);
+    lo += phi;
+    hi += (lo < phi) ? 1 : 0;
+  }
+  *ambiguous = lo > ~0ull - 2ull * NS;
+  return hi;
+}
+
+// Centered conversion of one coefficient: x (NS source residues) -> out
+// (ND target residues of x_c).
+template <int NS, int ND>
+CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
+  u64 y[NS];
+  for (int j = 0; j < NS; ++j) y[j] = shoup(x[j], C.theta[j], C.theta_s[j], C.s[j]);
+  bool amb;
+  u64 rho = round_sum<NS>(y, C, &amb);
+  if (amb) rho += mr_greater_half<NS>(x, C);
+  for (int k = 0; k < ND; ++k) {
+    u64 dk = C.d[k], acc = 0;
+    for (int j = 0; j < NS; ++j)
+      acc = addq(acc, shoup(y[j], C.hat[j][k], C.hat_s[j][k], dk), dk);
+    out[k] = subq(acc, shoup(rho, C.smod[k], C.smod_s[k], dk), dk);
+  }
+}
+
+// ---------------------------------------------------------------------
+// Exact scale-down e = round(t d / Q) mod q_j of one tensor coefficient d,
+// known modulo Q (residues dq) and modulo P = prod p_k (residues dp), with
+// |d| < 2N(Q/2)^2 and P > t N Q + 1.
+//   eps = [t d]_Q centered: y_j = [d_j * t (Q/q_j)^-1]_{q_j}, rho as above,
+//   r = (t d - eps)/Q = round(t d / Q) exactly; modulo p_k:
+//   r_k = [t Q^-1]_{p_k} d_k - sum_j y_j [q_j^-1]_{p_k} + rho.
+//   |r| <= t N Q / 2 + 1 < P/2, so the centered conversion of r from the
+//   p-basis to the q-basis is exact (and never near the ambiguous zone).
+// ---------------------------------------------------------------------
+struct ScaleTab {
+  u64 t_theta[kMaxL], t_theta_s[kMaxL]; // t (Q/q_j)^-1 mod q_j
+  u64 t_mod[kMaxL], t_mod_s[kMaxL];     // t mod q_j (ambiguous path)
+  u64 tqinv[kMaxK], tqinv_s[kMaxK];     // t Q^-1 mod p_k
+  u64 qinv[kMaxL][kMaxK], qinv_s[kMaxL][kMaxK]; // q_j^-1 mod p_k
+  BaseConv q2b;  // Q -> P conversion data (fraction and Garner parts used)
+  BaseConv b2q;  // P -> Q conversion
+};
+
+// Returns false if the P-basis rounding ever lands in the ambiguous zone,
+// which the bound on |r| rules out; callers record it as an internal error.
+template <int L>
+CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S) {
+  constexpr int K = L + 1;
+  u64 y[L];
+  for (int j = 0; j < L; ++j)
+    y[j] = shoup(dq[j], S.t_theta[j], S.t_theta_s[j], S.q2b.s[j]);
+  bool amb;
+  u64 rho = round_sum<L>(y, S.q2b, &amb);
+  if (amb) {
+    u64 eps[L];
+    for (int j = 0; j < L; ++j)
+      eps[j] = shoup(dq[j], S.t_mod[j], S.t_mod_s[j], S.q2b.s[j]);
+    rho += mr_greater_half<L>(eps, S.q2b);
+  }
+  u64 yb[K];
+  for (int k = 0; k < K; ++k) {
+    u64 pk = S.b2q.s[k];
+    u64 r = shoup(dp[k], S.tqinv[k], S.tqinv_s[k], pk);
+    for (int j = 0; j < L; ++j)
+      r = subq(r, shoup(y[j], S.qinv[j][k], S.qinv_s[j][k], pk), pk);
+    r = addq(r, rho, pk);
+    yb[k] = shoup(r, S.b2q.theta[k], S.b2q.theta_s[k], pk);
+  }
+  bool amb2;
+  u64 rho2 = round_sum<K>(yb, S.b2q, &amb2);
+  for (int j = 0; j < L; ++j) {
+    u64 qj = S.b2q.d[j], acc = 0;
+    for (int k = 0; k < K; ++k)
+      acc = addq(acc, shoup(yb[k], S.b2q.hat[k][j], S.b2q.hat_s[k][j], qj), qj);
+    out[j] = subq(acc, shoup(rho2, S.b2q.smod[j], S.b2q.smod_s[j], qj), qj);
+  }
+  return !amb2;
+}
+
+}  // namespace cw

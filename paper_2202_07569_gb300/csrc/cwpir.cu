@@ -1,0 +1,1012 @@
+// cwpir.cu -- host side of the C ABI (include/cwpir.h): parameter tables,
+// contexts, database plans and the launch sequence of the answer path
+// (arXiv 2202.07569, Sec. 3.3).  All arithmetic of the path runs in the
+// kernels of kernels.cu; this file validates, plans and enqueues.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/cwpir.h"
+#include "host_tables.hpp"
+#include "kernels.cuh"
+
+using cw::u32;
+using cw::u64;
+using namespace cw::host;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+}  // namespace
+
+// ---------------------------------------------------------------------
+// Context and database state
+// ---------------------------------------------------------------------
+struct DevBuf {
+  u64 *p = nullptr;
+  size_t n = 0;  // u64 count
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t ensure(size_t count) {
+    if (count <= n) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(u64));
+    if (e == cudaSuccess) n = count;
+    return e;
+  }
+};
+
+struct Chunk {
+  u64 off;   // offset into the plan's job array
+  u32 count;
+  int mode;  // cw::RootMode
+};
+
+struct Plan {
+  u32 k = 0, top = 0;
+  bool memo = false;
+  u64 n_memo = 0;
+  std::vector<Chunk> memo_chunks;
+  std::vector<std::vector<Chunk>> batches;  // per batch, levels bottom-up
+  bool leaf_root = false;                   // k == 1
+  std::vector<cw::MulJob> host_jobs;
+  cw::MulJob *d_jobs = nullptr;
+  DevBuf memo_buf, level_buf;
+  u64 mults = 0;
+  ~Plan() {
+    if (d_jobs) cudaFree(d_jobs);
+  }
+};
+
+struct Db {
+  u64 n = 0;
+  u32 plen = 0, k = 0, m = 0;
+  DevBuf db;                   // [n][L][N] NTT form
+  std::vector<uint16_t> cw;    // [n][k]
+  DevBuf leaves;               // [m] QP-NTT cts
+  DevBuf leaves_coef;          // [m] coefficient cts (expansion output)
+  std::unique_ptr<Plan> plan;  // full answer plan (rows 0..n-1)
+  bool plan_memo = false;
+};
+
+struct cwpir_ctx {
+  int device = 0;
+  u32 N = 0, logN = 0, L = 0, K = 0;
+  u64 t = 0;
+  std::vector<u64> q, p;
+  cw::DevTables h;          // host copy (device pointers inside)
+  cw::DevTables *d_tab = nullptr;
+  DevBuf twiddles;
+  DevBuf rlk, rlk_s;        // [L][2][L][N] NTT form and Shoup companions
+  std::map<u32, std::pair<std::shared_ptr<DevBuf>, std::shared_ptr<DevBuf>>> gal;
+  std::map<int32_t, std::unique_ptr<Db>> dbs;
+  int32_t next_db = 1;
+  std::string err;
+  int opt_share = 1, opt_graph = 0;
+  u32 opt_batch_rows = 0;
+  cudaStream_t stream = nullptr;
+  // scratch
+  u32 jmax = 0;
+  DevBuf Tbuf, E, CP, acc, exp_a, exp_b, exp_tau, exp_S, tmp_ct, tmp_ct2, io_in, io_out;
+  int *d_err = nullptr;
+  cw::SubJob *d_subjobs = nullptr;
+  size_t n_subjobs = 0;
+  cwpir_stats stats{};
+  // kernel timing (CWPIR_OPT_KERNEL_TIMING)
+  int opt_timing = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;
+  size_t ev_used = 0;
+  double kt_ms[CWPIR_K_CLASSES] = {};
+  uint64_t kt_n[CWPIR_K_CLASSES] = {};
+  ~cwpir_ctx() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (d_tab) cudaFree(d_tab);
+    if (d_err) cudaFree(d_err);
+    if (d_subjobs) cudaFree(d_subjobs);
+    if (stream) cudaStreamDestroy(stream);
+  }
+  u64 qp_ct() const { return 2ull * (L + K) * N; }
+  u64 ct() const { return 2ull * L * N; }
+};
+
+namespace {
+
+int fail(cwpir_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_setup_error = buf;
+  return code;
+}
+
+// Runs `launch` (returning cudaError_t); with kernel timing on, brackets it
+// with two events on `st` and files the pair under `cls`.
+template <typename F>
+cudaError_t timed(cwpir_ctx *c, int cls, cudaStream_t st, F launch) {
+  if (!c->opt_timing) return launch();
+  while (c->ev_pool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->ev_pool.push_back(e);
+  }
+  size_t a = c->ev_used, b = c->ev_used + 1;
+  c->ev_used += 2;
+  cudaError_t r = cudaEventRecord(c->ev_pool[a], st);
+  if (r == cudaSuccess) r = launch();
+  if (r == cudaSuccess) r = cudaEventRecord(c->ev_pool[b], st);
+  c->ev_marks.push_back({cls, {a, b}});
+  return r;
+}
+
+#define CUDA_TRY(ctx, expr)                                                          \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? CWPIR_ENOMEM : CWPIR_ECUDA, \
+                  "%s: %s", #expr, cudaGetErrorString(e_));                        \
+  } while (0)
+
+int build_tables(cwpir_ctx *c) {
+  cw::DevTables &h = c->h;
+  memset(&h, 0, sizeof h);
+  h.N = c->N;
+  h.logN = c->logN;
+  h.L = c->L;
+  h.K = c->K;
+  h.t = c->t;
+  const u32 P = c->L + c->K, N = c->N;
+  std::vector<u64> all(c->q);
+  all.insert(all.end(), c->p.begin(), c->p.end());
+  std::vector<u64> host(4ull * P * N);
+  CUDA_TRY(c, c->twiddles.ensure(4ull * P * N));
+  for (u32 l = 0; l < P; ++l) {
+    u64 q = all[l];
+    u64 *tw = host.data() + 4ull * l * N;
+    if (!make_twiddles(q, N, c->logN, tw))
+      return fail(c, CWPIR_EINTERNAL, "no 2N-th root of unity mod %llu", (unsigned long long)q);
+    cw::NttPrime &pr = h.prime[l];
+    pr.q = q;
+    pr.mu = (u64)(((u128)1 << 116) / q);
+    pr.ninv = hinv(N % q, q);
+    pr.ninv_s = shoup_of(pr.ninv, q);
+    u64 *d = c->twiddles.p + 4ull * l * N;
+    pr.psi = d;
+    pr.psi_s = d + N;
+    pr.ipsi = d + 2 * N;
+    pr.ipsi_s = d + 3 * N;
+  }
+  CUDA_TRY(c, cudaMemcpy(c->twiddles.p, host.data(), host.size() * sizeof(u64),
+                         cudaMemcpyHostToDevice));
+  fill_conv(h.q2b, c->q, c->p);
+  fill_scale(h.scale, c->q, c->p, c->t);
+  CUDA_TRY(c, cudaMalloc(&c->d_tab, sizeof(cw::DevTables)));
+  CUDA_TRY(c, cudaMemcpy(c->d_tab, &h, sizeof h, cudaMemcpyHostToDevice));
+  return CWPIR_OK;
+}
+
+bool valid_residues(const u64 *v, u32 L, u32 N, const std::vector<u64> &q, u64 count) {
+  for (u64 u = 0; u < count; ++u)
+    for (u32 j = 0; j < L; ++j) {
+      const u64 *x = v + (u * L + j) * N;
+      for (u32 i = 0; i < N; ++i)
+        if (x[i] >= q[j]) return false;
+    }
+  return true;
+}
+
+int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
+  const u64 words = 2ull * c->L * c->L * c->N;
+  if (!valid_residues(key, c->L, c->N, c->q, 2ull * c->L))
+    return fail(c, CWPIR_EINVAL, "switching key residue out of range");
+  CUDA_TRY(c, kb.ensure(words));
+  CUDA_TRY(c, ks.ensure(words));
+  CUDA_TRY(c, cudaMemcpy(kb.p, key, words * sizeof(u64), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cw::launch_key_prep(c->d_tab, c->h, kb.p, ks.p, 1, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return CWPIR_OK;
+}
+
+// ---- scratch ----
+int ensure_scratch(cwpir_ctx *c) {
+  if (c->jmax) return CWPIR_OK;
+  const u64 N = c->N, L = c->L, K = c->K;
+  const u64 per_job = (3 * (L + K) + 3 * L + 2 * L) * N * sizeof(u64);
+  const u64 budget = 2ull << 30;
+  u64 j = budget / per_job;
+  j = std::max<u64>(32, std::min<u64>(1024, j));
+  c->jmax = (u32)j;
+  CUDA_TRY(c, c->Tbuf.ensure(j * 3 * (L + K) * N));
+  CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
+  CUDA_TRY(c, c->CP.ensure(j * 2 * L * N));
+  CUDA_TRY(c, c->acc.ensure(2 * L * N));
+  if (!c->d_err) {
+    CUDA_TRY(c, cudaMalloc(&c->d_err, sizeof(int)));
+    CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+  }
+  return CWPIR_OK;
+}
+
+// ---- plans: the product tree of every row (Alg. Selection Vector) ----
+// Node (l, r) of a row covers positions [r 2^l, min((r+1) 2^l, k)) of its
+// ascending codeword positions; a node with one position is a leaf and a
+// node whose right half is empty carries its left child up unchanged.
+struct PlanBuilder {
+  cwpir_ctx *c;
+  const uint16_t *cw;
+  u32 k;
+  const u64 *leaves;
+  u64 qp;
+  bool memo;
+  std::unordered_map<u32, u64> memo_id;
+  const u64 *memo_base = nullptr;
+  std::vector<u64> level_off;  // offset (cts) of level l inside level_buf
+  std::vector<u32> level_nodes;
+  u64 *level_base = nullptr;
+
+  const u64 *ptr(u64 row, u64 lr, u32 l, u32 r) {
+    const uint16_t *pos = cw + row * k;
+    u32 lo = r << l, hi = std::min<u32>(lo + (1u << l), k);
+    if (hi - lo == 1) return leaves + pos[lo] * qp;
+    u32 mid = lo + (1u << (l - 1));
+    if (mid >= hi) return ptr(row, lr, l - 1, 2 * r);
+    if (l == 1 && memo) return memo_base + memo_id.at(((u32)pos[lo] << 16) | pos[lo + 1]) * qp;
+    return level_base + (level_off[l] + lr * level_nodes[l] + r) * qp;
+  }
+};
+
+u32 ceil_log2(u32 k) {
+  u32 l = 0;
+  while ((1u << l) < k) ++l;
+  return l;
+}
+
+// rows: list of database rows; root_mode ROOT_PM (answer) or ROOT_SEL with
+// sel_out receiving [rows][2][L][N].
+int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, int root_mode, u64 *sel_out,
+               bool memo_opt, std::unique_ptr<Plan> &out) {
+  std::unique_ptr<Plan> P(new Plan());
+  const u32 k = db->k;
+  P->k = k;
+  P->top = ceil_log2(k);
+  P->memo = memo_opt && P->top >= 2;
+  const u64 qp = c->qp_ct();
+  PlanBuilder B;
+  B.c = c;
+  B.cw = db->cw.data();
+  B.k = k;
+  B.leaves = db->leaves.p;
+  B.qp = qp;
+  B.memo = P->memo;
+  auto &jobs = P->host_jobs;
+  const u32 J = c->jmax;
+
+  if (k == 1) {
+    P->leaf_root = true;
+    for (u64 x = 0; x < rows.size(); x += J) {
+      u32 cnt = (u32)std::min<u64>(J, rows.size() - x);
+      P->batches.push_back({Chunk{jobs.size(), cnt, cw::ROOT_PM}});
+      for (u32 i = 0; i < cnt; ++i) {
+        u64 row = rows[x + i];
+        cw::MulJob mj{B.leaves + db->cw[row] * qp, nullptr, nullptr, row};
+        jobs.push_back(mj);
+      }
+    }
+  } else {
+    // shared first level
+    if (P->memo) {
+      std::vector<std::pair<u32, u32>> pairs;
+      for (u64 row : rows) {
+        const uint16_t *pos = db->cw.data() + row * k;
+        for (u32 r = 0; 2 * r + 1 < k; ++r) {
+          u32 key = ((u32)pos[2 * r] << 16) | pos[2 * r + 1];
+          if (B.memo_id.emplace(key, pairs.size()).second) pairs.push_back({pos[2 * r], pos[2 * r + 1]});
+        }
+      }
+      P->n_memo = pairs.size();
+      CUDA_TRY(c, P->memo_buf.ensure(std::max<u64>(1, P->n_memo) * qp));
+      B.memo_base = P->memo_buf.p;
+      for (u64 x = 0; x < pairs.size(); x += J) {
+        u32 cnt = (u32)std::min<u64>(J, pairs.size() - x);
+        P->memo_chunks.push_back(Chunk{jobs.size(), cnt, cw::INTERNAL});
+        for (u32 i = 0; i < cnt; ++i) {
+          const auto &pr = pairs[x + i];
+          jobs.push_back(cw::MulJob{B.leaves + pr.first * qp, B.leaves + pr.second * qp,
+                                    P->memo_buf.p + (x + i) * qp, 0});
+        }
+      }
+      P->mults += pairs.size();
+    }
+    const u32 l0 = P->memo ? 2 : 1;
+    u32 max_nodes = 1;
+    B.level_off.assign(P->top + 1, 0);
+    B.level_nodes.assign(P->top + 1, 0);
+    for (u32 l = l0; l <= P->top; ++l) {
+      u32 nodes = (k + (1u << l) - 1) >> l;
+      B.level_nodes[l] = nodes;
+      max_nodes = std::max(max_nodes, nodes);
+    }
+    u64 rows_per_batch = std::max<u64>(1, J / max_nodes);
+    if (c->opt_batch_rows) rows_per_batch = std::min<u64>(rows_per_batch, c->opt_batch_rows);
+    u64 lvl_cts = 0;
+    for (u32 l = l0; l < P->top; ++l) {
+      B.level_off[l] = lvl_cts;
+      lvl_cts += rows_per_batch * B.level_nodes[l];
+    }
+    CUDA_TRY(c, P->level_buf.ensure(std::max<u64>(1, lvl_cts) * qp));
+    B.level_base = P->level_buf.p;
+    for (u64 x = 0; x < rows.size(); x += rows_per_batch) {
+      u64 cnt = std::min<u64>(rows_per_batch, rows.size() - x);
+      std::vector<Chunk> levels;
+      for (u32 l = l0; l <= P->top; ++l) {
+        Chunk ch{jobs.size(), 0, l == P->top ? root_mode : (int)cw::INTERNAL};
+        for (u64 lr = 0; lr < cnt; ++lr) {
+          u64 row = rows[x + lr];
+          for (u32 r = 0; r < B.level_nodes[l]; ++r) {
+            u32 lo = r << l, mid = lo + (1u << (l - 1));
+            if (mid >= std::min<u32>(lo + (1u << l), k)) continue;
+            cw::MulJob mj;
+            mj.a = B.ptr(row, lr, l - 1, 2 * r);
+            mj.b = B.ptr(row, lr, l - 1, 2 * r + 1);
+            mj.row = row;
+            if (l == P->top) mj.dst = sel_out ? sel_out + (x + lr) * c->ct() : nullptr;
+            else mj.dst = B.level_base + (B.level_off[l] + lr * B.level_nodes[l] + r) * qp;
+            jobs.push_back(mj);
+            ++ch.count;
+          }
+        }
+        P->mults += ch.count;
+        if (ch.count) levels.push_back(ch);
+      }
+      P->batches.push_back(levels);
+    }
+  }
+  CUDA_TRY(c, cudaMalloc(&P->d_jobs, std::max<size_t>(1, jobs.size()) * sizeof(cw::MulJob)));
+  CUDA_TRY(c, cudaMemcpy(P->d_jobs, jobs.data(), jobs.size() * sizeof(cw::MulJob),
+                         cudaMemcpyHostToDevice));
+  out = std::move(P);
+  return CWPIR_OK;
+}
+
+// One chunk of multiplications: tensor, scale-down, relinearisation and
+// the consumer of the result.
+int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream_t st) {
+  const cw::MulJob *jobs = P->d_jobs + ch.off;
+  if (P->leaf_root) {
+    CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] { return cw::launch_pm_leaf(c->d_tab, c->h, jobs, ch.count, dbp, c->CP.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.count, c->acc.p, st); }));
+    c->stats.kernel_launches += 2;
+    return CWPIR_OK;
+  }
+  CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, c->Tbuf.p, st); }));
+  CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
+  CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
+    return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, jobs, ch.mode, c->rlk.p, c->rlk_s.p,
+                            dbp, c->CP.p, st);
+  }));
+  c->stats.kernel_launches += 3;
+  c->stats.mults += ch.count;
+  c->stats.ntt_polys += (u64)ch.count * (3 * (c->L + c->K) + c->L * (c->L + 2));
+  if (ch.mode == cw::INTERNAL) {
+    CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, c->CP.p, jobs, ch.count, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_p(c->d_tab, c->h, jobs, ch.count, st); }));
+    c->stats.kernel_launches += 2;
+    c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
+  } else if (ch.mode == cw::ROOT_PM) {
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.count, c->acc.p, st); }));
+    c->stats.kernel_launches += 1;
+    c->stats.db_bytes_read += (u64)ch.count * c->L * c->N * sizeof(u64);
+  } else {
+    c->stats.ntt_polys += (u64)ch.count * 2 * c->L;
+  }
+  return CWPIR_OK;
+}
+
+int ensure_subjobs(cwpir_ctx *c, size_t n) {
+  if (n <= c->n_subjobs) return CWPIR_OK;
+  if (c->d_subjobs) cudaFree(c->d_subjobs);
+  c->d_subjobs = nullptr;
+  c->n_subjobs = 0;
+  CUDA_TRY(c, cudaMalloc(&c->d_subjobs, n * sizeof(cw::SubJob)));
+  c->n_subjobs = n;
+  return CWPIR_OK;
+}
+
+const std::pair<std::shared_ptr<DevBuf>, std::shared_ptr<DevBuf>> *find_gal(cwpir_ctx *c, u32 g) {
+  auto it = c->gal.find(g);
+  return it == c->gal.end() ? nullptr : &it->second;
+}
+
+// Alg. Query Expansion on device: h_in cts (coefficient form, d_query) ->
+// the first m expanded cts in `out` (coefficient form).
+int run_expand(cwpir_ctx *c, u32 cfac, u32 m, const u64 *d_query, u64 *out, cudaStream_t st) {
+  const u32 B = 1u << cfac;
+  const u32 h_in = (m + B - 1) / B;
+  const u64 ctw = c->ct();
+  for (u32 a = 0; a < cfac; ++a)
+    if (!find_gal(c, c->N / (1u << a) + 1))
+      return fail(c, CWPIR_ENOKEY, "no Galois key for element %u", c->N / (1u << a) + 1);
+  CUDA_TRY(c, c->exp_a.ensure((u64)h_in * B * ctw));
+  CUDA_TRY(c, c->exp_b.ensure((u64)h_in * B * ctw));
+  CUDA_TRY(c, c->exp_tau.ensure((u64)h_in * (B / 2) * ctw));
+  CUDA_TRY(c, c->exp_S.ensure((u64)h_in * (B / 2) * ctw));
+  int rc = ensure_subjobs(c, (size_t)h_in * (B / 2) * cfac);
+  if (rc) return rc;
+  for (u32 j = 0; j < h_in; ++j)
+    CUDA_TRY(c, cudaMemcpyAsync(c->exp_a.p + (u64)j * B * ctw, d_query + (u64)j * ctw,
+                                ctw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+  // job lists for every round, uploaded together
+  std::vector<cw::SubJob> sj;
+  std::vector<size_t> round_off;
+  u64 *cur = c->exp_a.p, *nxt = c->exp_b.p;
+  for (u32 a = 0; a < cfac; ++a) {
+    round_off.push_back(sj.size());
+    for (u32 j = 0; j < h_in; ++j)
+      for (u32 b = 0; b < (1u << a); ++b)
+        sj.push_back(cw::SubJob{cur + ((u64)j * B + b) * ctw,
+                                c->exp_S.p + ((u64)j * (1u << a) + b) * ctw});
+    std::swap(cur, nxt);
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_subjobs, sj.data(), sj.size() * sizeof(cw::SubJob),
+                              cudaMemcpyHostToDevice, st));
+  cur = c->exp_a.p;
+  nxt = c->exp_b.p;
+  for (u32 a = 0; a < cfac; ++a) {
+    const u32 g = c->N / (1u << a) + 1;
+    const u32 nj = h_in << a;
+    const auto *key = find_gal(c, g);
+    const cw::SubJob *jobs = c->d_subjobs + round_off[a];
+    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_automorph(c->d_tab, c->h, jobs, nj, g, c->exp_tau.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] {
+      return cw::launch_sub_keyswitch(c->d_tab, c->h, c->exp_tau.p, nj, jobs, key->first->p,
+                                      key->second->p, st);
+    }));
+    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_expand_combine(c->d_tab, c->h, cur, c->exp_S.p, nxt, h_in, cfac, a, st); }));
+    c->stats.kernel_launches += 3;
+    c->stats.substitutions += nj;
+    c->stats.ntt_polys += (u64)nj * c->L * (c->L + 3);
+    std::swap(cur, nxt);
+  }
+  // entry j * 2^c + b now encrypts query bit j * 2^c + b: natural order
+  CUDA_TRY(c, cudaMemcpyAsync(out, cur, (u64)m * ctw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+  return CWPIR_OK;
+}
+
+// Leaves: coefficient-form cts -> QP-NTT form.
+int prep_leaves(cwpir_ctx *c, const u64 *coef, u32 count, u64 *dst, cudaStream_t st) {
+  const u64 LK = c->L + c->K;
+  CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] {
+    return cw::launch_lift(c->d_tab, c->h, coef, (u64)c->L * c->N, dst, LK * c->N, 2 * count,
+                           true, st);
+  }));
+  CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] {
+    return cw::launch_ntt(c->d_tab, c->h, dst, 2 * count, LK * c->N, 0, (u32)LK, false, nullptr,
+                          0, st);
+  }));
+  c->stats.kernel_launches += 2;
+  c->stats.ntt_polys += 2ull * count * LK;
+  return CWPIR_OK;
+}
+
+int check_err_flag(cwpir_ctx *c) {
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    return fail(c, CWPIR_EINTERNAL, "device consistency check failed (scale-down rounding)");
+  }
+  return CWPIR_OK;
+}
+
+Db *get_db(cwpir_ctx *c, int32_t id) {
+  auto it = c->dbs.find(id);
+  return it == c->dbs.end() ? nullptr : it->second.get();
+}
+
+// Expansion (if c > 0) and leaf preparation for a database's code length.
+int prepare_query(cwpir_ctx *c, Db *db, u32 cfac, const u64 *d_query, cudaStream_t st) {
+  const u64 ctw = c->ct();
+  const u64 *coef = d_query;
+  if (cfac > 0) {
+    CUDA_TRY(c, db->leaves_coef.ensure((u64)db->m * ctw));
+    int rc = run_expand(c, cfac, db->m, d_query, db->leaves_coef.p, st);
+    if (rc) return rc;
+    coef = db->leaves_coef.p;
+  }
+  return prep_leaves(c, coef, db->m, db->leaves.p, st);
+}
+
+int answer_enqueue(cwpir_ctx *c, Db *db, u32 cfac, const u64 *d_query, u64 *d_resp,
+                   cudaStream_t st) {
+  c->stats = cwpir_stats{};
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  if (!db->plan || db->plan_memo != (c->opt_share != 0)) {
+    std::vector<u64> rows(db->n);
+    for (u64 i = 0; i < db->n; ++i) rows[i] = i;
+    rc = build_plan(c, db, rows, cw::ROOT_PM, nullptr, c->opt_share != 0, db->plan);
+    if (rc) return rc;
+    db->plan_memo = c->opt_share != 0;
+  }
+  rc = prepare_query(c, db, cfac, d_query, st);
+  if (rc) return rc;
+  Plan *P = db->plan.get();
+  CUDA_TRY(c, cudaMemsetAsync(c->acc.p, 0, 2ull * c->L * c->N * sizeof(u64), st));
+  for (const Chunk &ch : P->memo_chunks)
+    if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
+  for (const auto &batch : P->batches)
+    for (const Chunk &ch : batch)
+      if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
+  CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] {
+    return cw::launch_ntt(c->d_tab, c->h, d_resp, 2, (u64)c->L * c->N, 0, c->L, true, c->acc.p,
+                          (u64)c->L * c->N, st);
+  }));
+  c->stats.kernel_launches += 1;
+  c->stats.ntt_polys += 2 * c->L;
+  c->stats.rows = db->n;
+  return CWPIR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------
+extern "C" {
+
+int cwpir_abi_version(void) { return CWPIR_ABI_VERSION; }
+
+const char *cwpir_strerror(int code) {
+  switch (code) {
+    case CWPIR_OK: return "ok";
+    case CWPIR_EINVAL: return "invalid argument";
+    case CWPIR_ENOMEM: return "out of memory";
+    case CWPIR_ENODB: return "unknown database";
+    case CWPIR_ECUDA: return "CUDA error";
+    case CWPIR_ETIMEDOUT: return "device wait timed out";
+    case CWPIR_EBUSY: return "busy";
+    case CWPIR_ENOKEY: return "missing Galois key";
+    case CWPIR_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+const char *cwpir_last_error(const cwpir_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_error.c_str();
+}
+
+int cwpir_default_primes(uint32_t N, uint32_t L, uint64_t *q_out) {
+  if (N < 2 || (N & (N - 1)) || N > (1u << 20) || L == 0 || !q_out) return CWPIR_EINVAL;
+  std::vector<u64> p = ntt_primes(N, L, {});
+  if (p.size() != L) return CWPIR_EINVAL;
+  for (u32 i = 0; i < L; ++i) q_out[i] = p[i];
+  return CWPIR_OK;
+}
+
+static u128 binom_sat(u64 n, u64 r) {
+  if (r > n) return 0;
+  if (r > n - r) r = n - r;
+  const u128 lim = (u128)1 << 126;
+  u128 v = 1;
+  for (u64 i = 1; i <= r; ++i) {
+    u64 f = n - r + i;
+    if (v > lim / f) return lim;
+    v = v * f / i;
+  }
+  return v;
+}
+
+int cwpir_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out) {
+  if (!pos_out || k == 0 || k > m || m > 65535) return CWPIR_EINVAL;
+  if ((u128)x >= binom_sat(m, k)) return CWPIR_EINVAL;
+  // Alg. Perfect Mapping: scan m' = m-1 .. 0, take m' when the remainder is
+  // at least C(m', h); positions come out in descending order.
+  u128 rem = x;
+  u32 h = k;
+  for (int64_t mp = (int64_t)m - 1; mp >= 0 && h; --mp) {
+    u128 b = binom_sat((u64)mp, h);
+    if (rem >= b) {
+      pos_out[--h] = (uint16_t)mp;
+      rem -= b;
+    }
+  }
+  return h == 0 ? CWPIR_OK : CWPIR_EINVAL;
+}
+
+int cwpir_code_length(uint64_t n, uint32_t k, uint32_t *m_out) {
+  if (!m_out || k == 0 || k > 64) return CWPIR_EINVAL;
+  for (u64 m = k; m <= 65535; ++m)
+    if (binom_sat(m, k) >= (u128)n) {
+      *m_out = (uint32_t)m;
+      return CWPIR_OK;
+    }
+  return CWPIR_EINVAL;
+}
+
+int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys, cwpir_ctx **out) {
+  g_setup_error.clear();
+  if (!params || !keys || !out || !params->q || !keys->relin)
+    return fail(nullptr, CWPIR_EINVAL, "null argument");
+  const u32 N = params->N, L = params->L;
+  if (N < 1024 || N > 16384 || (N & (N - 1)))
+    return fail(nullptr, CWPIR_EINVAL, "N must be a power of two in [1024, 16384]");
+  if (L < 1 || L > (u32)cw::kMaxL) return fail(nullptr, CWPIR_EINVAL, "L must be in [1, 8]");
+  if (params->t < 3 || params->t >= (1ull << 20) || !miller_rabin(params->t))
+    return fail(nullptr, CWPIR_EINVAL, "t must be a prime in [3, 2^20)");
+  std::vector<u64> q(params->q, params->q + L);
+  for (u32 j = 0; j < L; ++j) {
+    if (q[j] <= (1ull << 53) || q[j] >= (1ull << 54) || !miller_rabin(q[j]) ||
+        (q[j] - 1) % (2ull * N))
+      return fail(nullptr, CWPIR_EINVAL, "q[%u] must be a prime in (2^53, 2^54), = 1 mod 2N", j);
+    for (u32 l = 0; l < j; ++l)
+      if (q[l] == q[j]) return fail(nullptr, CWPIR_EINVAL, "primes must be distinct");
+  }
+  std::unique_ptr<cwpir_ctx> c(new (std::nothrow) cwpir_ctx());
+  if (!c) return fail(nullptr, CWPIR_ENOMEM, "host allocation");
+  cudaGetDevice(&c->device);
+  c->N = N;
+  c->logN = 0;
+  while ((1u << c->logN) < N) ++c->logN;
+  c->L = L;
+  c->t = params->t;
+  c->q = q;
+  // Extension basis P: K = L + 1 primes, P > 2^16 t N Q (checked below).
+  c->K = L + 1;
+  c->p = ntt_primes(N, c->K, q);
+  if (c->p.size() != c->K) return fail(nullptr, CWPIR_EINVAL, "not enough extension primes");
+  long double lq = 0, lp = 0;
+  for (u64 v : q) lq += log2l((long double)v);
+  for (u64 v : c->p) lp += log2l((long double)v);
+  if (lp < lq + log2l((long double)N) + log2l((long double)params->t) + 17)
+    return fail(nullptr, CWPIR_EINVAL, "extension basis too small");
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(nullptr, CWPIR_ECUDA, "stream: %s", cudaGetErrorString(e));
+  int rc = build_tables(c.get());
+  if (rc) {
+    g_setup_error = c->err;
+    return rc;
+  }
+  rc = upload_key(c.get(), keys->relin, c->rlk, c->rlk_s);
+  if (rc) {
+    g_setup_error = c->err;
+    return rc;
+  }
+  for (u32 i = 0; i < keys->n_galois; ++i) {
+    u32 g = keys->galois_elts[i];
+    if (!(g & 1) || g >= 2 * N) return fail(nullptr, CWPIR_EINVAL, "bad Galois element %u", g);
+    auto kb = std::make_shared<DevBuf>(), ks = std::make_shared<DevBuf>();
+    rc = upload_key(c.get(), keys->galois + (u64)i * 2 * L * L * N, *kb, *ks);
+    if (rc) {
+      g_setup_error = c->err;
+      return rc;
+    }
+    c->gal[g] = {kb, ks};
+  }
+  *out = c.release();
+  return CWPIR_OK;
+}
+
+void cwpir_destroy(cwpir_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t m,
+                  const uint32_t *items, const uint16_t *codewords, int32_t *db_id) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!items || !codewords || !db_id) return fail(c, CWPIR_EINVAL, "null argument");
+  if (n < 1 || n > (1ull << 24)) return fail(c, CWPIR_EINVAL, "n must be in [1, 2^24]");
+  if (plen > c->N) return fail(c, CWPIR_EINVAL, "payload_len > N");
+  if (k < 1 || k > 16 || k > m || m > 16384)
+    return fail(c, CWPIR_EINVAL, "need 1 <= k <= 16, k <= m <= 16384");
+  for (u64 i = 0; i < n * plen; ++i)
+    if (items[i] >= c->t) return fail(c, CWPIR_EINVAL, "item coefficient >= t at %llu", (unsigned long long)i);
+  for (u64 i = 0; i < n; ++i)
+    for (u32 u = 0; u < k; ++u) {
+      uint16_t p = codewords[i * k + u];
+      if (p >= m || (u && p <= codewords[i * k + u - 1]))
+        return fail(c, CWPIR_EINVAL, "codeword of row %llu is not ascending positions < m",
+                    (unsigned long long)i);
+    }
+  std::unique_ptr<Db> db(new Db());
+  db->n = n;
+  db->plen = plen;
+  db->k = k;
+  db->m = m;
+  db->cw.assign(codewords, codewords + n * k);
+  CUDA_TRY(c, db->db.ensure(n * c->L * c->N));
+  CUDA_TRY(c, db->leaves.ensure((u64)m * c->qp_ct()));
+  // upload rows in chunks and transform
+  const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));
+  uint32_t *d_items = nullptr;
+  if (plen) {
+    CUDA_TRY(c, cudaMalloc(&d_items, std::min(chunk_rows, n) * plen * sizeof(uint32_t)));
+  }
+  for (u64 r0 = 0; r0 < n; r0 += chunk_rows) {
+    u64 nr = std::min(chunk_rows, n - r0);
+    if (plen) {
+      cudaError_t e = cudaMemcpyAsync(d_items, items + r0 * plen, nr * plen * sizeof(uint32_t),
+                                      cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cw::launch_db_load(c->d_tab, c->h, d_items, nr, plen,
+                                                   db->db.p + r0 * c->L * c->N, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) {
+        cudaFree(d_items);
+        return fail(c, CWPIR_ECUDA, "database upload: %s", cudaGetErrorString(e));
+      }
+    }
+  }
+  if (d_items) cudaFree(d_items);
+  if (!plen) CUDA_TRY(c, cudaMemset(db->db.p, 0, n * c->L * c->N * sizeof(u64)));
+  int32_t id = c->next_db++;
+  c->dbs[id] = std::move(db);
+  *db_id = id;
+  return CWPIR_OK;
+}
+
+int cwpir_free_db(cwpir_ctx *c, int32_t id) {
+  if (!c) return CWPIR_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (!c->dbs.erase(id)) return fail(c, CWPIR_ENODB, "unknown database %d", id);
+  return CWPIR_OK;
+}
+
+static int query_shape(cwpir_ctx *c, Db *db, u32 cfac, u64 *h) {
+  if (cfac > c->logN) return fail(c, CWPIR_EINVAL, "c > log2 N");
+  *h = cfac == 0 ? db->m : (db->m + (1u << cfac) - 1) >> cfac;
+  return CWPIR_OK;
+}
+
+int cwpir_answer_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *d_query,
+                        uint64_t *d_resp, void *stream) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  if (!d_query || !d_resp) return fail(c, CWPIR_EINVAL, "null buffer");
+  u64 h;
+  int rc = query_shape(c, db, cfac, &h);
+  if (rc) return rc;
+  return answer_enqueue(c, db, cfac, d_query, d_resp, (cudaStream_t)stream);
+}
+
+int cwpir_answer(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *query,
+                 uint64_t *response) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  if (!query || !response) return fail(c, CWPIR_EINVAL, "null buffer");
+  u64 h;
+  int rc = query_shape(c, db, cfac, &h);
+  if (rc) return rc;
+  if (!valid_residues(query, c->L, c->N, c->q, 2 * h))
+    return fail(c, CWPIR_EINVAL, "query residue out of range");
+  const u64 ctw = c->ct();
+  CUDA_TRY(c, c->io_in.ensure(h * ctw));
+  CUDA_TRY(c, c->io_out.ensure(ctw));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
+                              c->stream));
+  rc = answer_enqueue(c, db, cfac, c->io_in.p, c->io_out.p, c->stream);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(response, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_err_flag(c);
+}
+
+int cwpir_mul(cwpir_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!a || !b || !out) return fail(c, CWPIR_EINVAL, "null buffer");
+  if (!valid_residues(a, c->L, c->N, c->q, 2) || !valid_residues(b, c->L, c->N, c->q, 2))
+    return fail(c, CWPIR_EINVAL, "residue out of range");
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  const u64 ctw = c->ct(), qp = c->qp_ct();
+  CUDA_TRY(c, c->io_in.ensure(2 * ctw));
+  CUDA_TRY(c, c->io_out.ensure(ctw));
+  CUDA_TRY(c, c->tmp_ct.ensure(2 * qp));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, a, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p + ctw, b, ctw * sizeof(u64), cudaMemcpyHostToDevice,
+                              c->stream));
+  if ((rc = prep_leaves(c, c->io_in.p, 2, c->tmp_ct.p, c->stream))) return rc;
+  Plan P;
+  cw::MulJob job{c->tmp_ct.p, c->tmp_ct.p + qp, c->io_out.p, 0};
+  CUDA_TRY(c, cudaMalloc(&P.d_jobs, sizeof job));
+  CUDA_TRY(c, cudaMemcpy(P.d_jobs, &job, sizeof job, cudaMemcpyHostToDevice));
+  if ((rc = run_chunk(c, &P, Chunk{0, 1, cw::ROOT_SEL}, nullptr, c->stream))) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_err_flag(c);
+}
+
+int cwpir_substitute(cwpir_ctx *c, uint32_t g, const uint64_t *ct, uint64_t *out) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!ct || !out) return fail(c, CWPIR_EINVAL, "null buffer");
+  const auto *key = find_gal(c, g);
+  if (!key) return fail(c, CWPIR_ENOKEY, "no Galois key for element %u", g);
+  if (!valid_residues(ct, c->L, c->N, c->q, 2)) return fail(c, CWPIR_EINVAL, "residue out of range");
+  const u64 ctw = c->ct();
+  CUDA_TRY(c, c->io_in.ensure(ctw));
+  CUDA_TRY(c, c->io_out.ensure(ctw));
+  CUDA_TRY(c, c->exp_tau.ensure(ctw));
+  int rc = ensure_subjobs(c, 1);
+  if (rc) return rc;
+  cw::SubJob sj{c->io_in.p, c->io_out.p};
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, ct, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_subjobs, &sj, sizeof sj, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cw::launch_automorph(c->d_tab, c->h, c->d_subjobs, 1, g, c->exp_tau.p, c->stream));
+  CUDA_TRY(c, cw::launch_sub_keyswitch(c->d_tab, c->h, c->exp_tau.p, 1, c->d_subjobs,
+                                       key->first->p, key->second->p, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return CWPIR_OK;
+}
+
+int cwpir_expand(cwpir_ctx *c, uint32_t cfac, uint32_t m, const uint64_t *query, uint64_t *out) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!query || !out) return fail(c, CWPIR_EINVAL, "null buffer");
+  if (cfac < 1 || cfac > c->logN || m < 1 || m > 16384)
+    return fail(c, CWPIR_EINVAL, "need 1 <= c <= log2 N and 1 <= m <= 16384");
+  const u64 h = (m + (1u << cfac) - 1) >> cfac, ctw = c->ct();
+  if (!valid_residues(query, c->L, c->N, c->q, 2 * h)) return fail(c, CWPIR_EINVAL, "residue out of range");
+  CUDA_TRY(c, c->io_in.ensure(h * ctw));
+  CUDA_TRY(c, c->io_out.ensure((u64)m * ctw));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
+                              c->stream));
+  int rc = run_expand(c, cfac, m, c->io_in.p, c->io_out.p, c->stream);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, (u64)m * ctw * sizeof(u64), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return CWPIR_OK;
+}
+
+int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *query,
+                    uint64_t count, const uint64_t *rows, uint64_t *out) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  if (!query || !rows || !out || count == 0) return fail(c, CWPIR_EINVAL, "null buffer or empty");
+  for (u64 i = 0; i < count; ++i)
+    if (rows[i] >= db->n) return fail(c, CWPIR_EINVAL, "row out of range");
+  u64 h;
+  int rc = query_shape(c, db, cfac, &h);
+  if (rc) return rc;
+  if (!valid_residues(query, c->L, c->N, c->q, 2 * h)) return fail(c, CWPIR_EINVAL, "residue out of range");
+  if ((rc = ensure_scratch(c))) return rc;
+  const u64 ctw = c->ct();
+  CUDA_TRY(c, c->io_in.ensure(h * ctw));
+  CUDA_TRY(c, c->io_out.ensure(count * ctw));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
+                              c->stream));
+  if ((rc = prepare_query(c, db, cfac, c->io_in.p, c->stream))) return rc;
+  if (db->k == 1) {
+    // the selection entry is the expanded query ciphertext itself
+    const u64 *src = cfac ? db->leaves_coef.p : c->io_in.p;
+    for (u64 i = 0; i < count; ++i)
+      CUDA_TRY(c, cudaMemcpyAsync(out + i * ctw, src + db->cw[rows[i]] * ctw, ctw * sizeof(u64),
+                                  cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CWPIR_OK;
+  }
+  std::vector<u64> rv(rows, rows + count);
+  std::unique_ptr<Plan> P;
+  if ((rc = build_plan(c, db, rv, cw::ROOT_SEL, c->io_out.p, c->opt_share != 0, P))) return rc;
+  for (const Chunk &ch : P->memo_chunks)
+    if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
+  for (const auto &batch : P->batches)
+    for (const Chunk &ch : batch)
+      if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, count * ctw * sizeof(u64), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_err_flag(c);
+}
+
+int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *ct, uint64_t *out) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  if (!ct || !out || row >= db->n) return fail(c, CWPIR_EINVAL, "null buffer or row out of range");
+  if (!valid_residues(ct, c->L, c->N, c->q, 2)) return fail(c, CWPIR_EINVAL, "residue out of range");
+  const u64 ctw = c->ct(), LN = (u64)c->L * c->N;
+  CUDA_TRY(c, c->io_in.ensure(ctw));
+  CUDA_TRY(c, c->io_out.ensure(ctw));
+  CUDA_TRY(c, c->tmp_ct.ensure(ctw));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, ct, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, c->tmp_ct.p, 2, LN, 0, c->L, false, c->io_in.p, LN,
+                             c->stream));
+  CUDA_TRY(c, cw::launch_pm_ntt(c->d_tab, c->h, c->tmp_ct.p, db->db.p + row * LN, c->io_in.p,
+                                c->stream));
+  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, c->io_out.p, 2, LN, 0, c->L, true, c->io_in.p, LN,
+                             c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return CWPIR_OK;
+}
+
+int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
+  if (!c) return CWPIR_EINVAL;
+  switch (option) {
+    case CWPIR_OPT_SHARE_LEVEL1: c->opt_share = value ? 1 : 0; return CWPIR_OK;
+    case CWPIR_OPT_BATCH_ROWS:
+      if (value < 0) return fail(c, CWPIR_EINVAL, "batch rows must be >= 0");
+      c->opt_batch_rows = (u32)value;
+      for (auto &kv : c->dbs) kv.second->plan.reset();
+      return CWPIR_OK;
+    case CWPIR_OPT_USE_GRAPH: c->opt_graph = value ? 1 : 0; return CWPIR_OK;
+    case CWPIR_OPT_KERNEL_TIMING: c->opt_timing = value ? 1 : 0; return CWPIR_OK;
+    default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
+  }
+}
+
+int cwpir_kernel_times(cwpir_ctx *c, double *ms, uint64_t *launches) {
+  if (!c || !ms || !launches) return CWPIR_EINVAL;
+  cudaSetDevice(c->device);
+  for (const auto &mk : c->ev_marks) {
+    CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[mk.second.second]));
+    float t = 0;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev_pool[mk.second.first], c->ev_pool[mk.second.second]));
+    c->kt_ms[mk.first] += t;
+    c->kt_n[mk.first] += 1;
+  }
+  c->ev_marks.clear();
+  c->ev_used = 0;
+  for (int i = 0; i < CWPIR_K_CLASSES; ++i) {
+    ms[i] = c->kt_ms[i];
+    launches[i] = c->kt_n[i];
+    c->kt_ms[i] = 0;
+    c->kt_n[i] = 0;
+  }
+  return CWPIR_OK;
+}
+
+const char *cwpir_kernel_class_name(int cls) {
+  static const char *names[CWPIR_K_CLASSES] = {"tensor_intt", "scale", "relin_pm", "lift",
+                                                "ntt", "accumulate", "expand"};
+  return (cls >= 0 && cls < CWPIR_K_CLASSES) ? names[cls] : "unknown";
+}
+
+int cwpir_last_stats(const cwpir_ctx *c, cwpir_stats *out) {
+  if (!c || !out) return CWPIR_EINVAL;
+  *out = c->stats;
+  return CWPIR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// kernels.cuh -- device data structures and kernel entry points of the
+// constant-weight PIR answer path (arXiv 2202.07569, Sec. 3.3.3).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "arith.cuh"
+
+namespace cw {
+
+// All per-context constants the kernels read, in device memory.
+struct DevTables {
+  u32 N, logN, L, K;
+  u64 t;
+  NttPrime prime[kMaxP];  // q_0..q_{L-1}, then p_0..p_{K-1}
+  BaseConv q2b;           // centered Q -> P conversion (leaves, nodes)
+  ScaleTab scale;         // exact round(t d / Q)
+};
+
+// One homomorphic multiplication of two ciphertexts held in "QP-NTT" form:
+// [2][L+K][N] residues, NTT domain, Q limbs then P limbs.
+struct MulJob {
+  const u64 *a;
+  const u64 *b;
+  u64 *dst;   // internal node: QP-NTT destination; root: output slot (SEL)
+  u64 row;    // root: database row
+};
+
+// Substitution job: source ciphertext [2][L][N] coefficient form.
+struct SubJob {
+  const u64 *src;
+  u64 *dst;   // [2][L][N] coefficient form result
+};
+
+enum RootMode : int {
+  ROOT_PM = 0,    // sel * DB[row] -> partial products
+  ROOT_SEL = 1,   // sel in coefficient form -> dst ([2][L][N])
+  INTERNAL = 2    // sel -> QP-NTT form at dst (Q limbs here, P limbs later)
+};
+
+constexpr int kCoefPerThread = 16;  // N / blockDim for the NTT kernels
+
+// ---- launchers (kernels.cu); all enqueue on `st` and return the launch
+// error.  Buffers are described in kernels.cu next to each kernel. ----
+cudaError_t launch_db_load(const DevTables *T, const DevTables &h, const u32 *items,
+                           u64 rows, u32 plen, u64 *db, cudaStream_t st);
+cudaError_t launch_ntt(const DevTables *T, const DevTables &h, u64 *base, u32 units,
+                       u64 unit_stride, u32 limb_begin, u32 limb_end, bool inverse,
+                       const u64 *src, u64 src_unit_stride, cudaStream_t st);
+cudaError_t launch_lift(const DevTables *T, const DevTables &h, const u64 *src,
+                        u64 src_stride, u64 *dst, u64 dst_stride, u32 units,
+                        bool copy_q, cudaStream_t st);
+cudaError_t launch_lift_jobs(const DevTables *T, const DevTables &h, const u64 *C,
+                             const MulJob *jobs, u32 njobs, cudaStream_t st);
+cudaError_t launch_ntt_jobs_p(const DevTables *T, const DevTables &h, const MulJob *jobs,
+                              u32 njobs, cudaStream_t st);
+cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const MulJob *jobs,
+                               u32 njobs, u64 *Tbuf, cudaStream_t st);
+cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf, u32 njobs,
+                         u64 *E, int *err, cudaStream_t st);
+cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
+                         const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
+                         const u64 *db, u64 *out, cudaStream_t st);
+cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
+                           u32 njobs, const u64 *db, u64 *P, cudaStream_t st);
+cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P,
+                              u32 njobs, u64 *acc, cudaStream_t st);
+cudaError_t launch_automorph(const DevTables *T, const DevTables &h, const SubJob *jobs,
+                             u32 njobs, u32 g, u64 *tau, cudaStream_t st);
+cudaError_t launch_sub_keyswitch(const DevTables *T, const DevTables &h, const u64 *tau,
+                                 u32 njobs, const SubJob *jobs, const u64 *key,
+                                 const u64 *key_s, cudaStream_t st);
+cudaError_t launch_expand_combine(const DevTables *T, const DevTables &h, const u64 *cur,
+                                  const u64 *S, u64 *next, u32 h_in, u32 cfac, u32 a,
+                                  cudaStream_t st);
+cudaError_t launch_pm_ntt(const DevTables *T, const DevTables &h, const u64 *ct_ntt,
+                          const u64 *db_row, u64 *out, cudaStream_t st);
+cudaError_t launch_key_prep(const DevTables *T, const DevTables &h, u64 *key, u64 *key_s,
+                            u32 nkeys, cudaStream_t st);
+
+}  // namespace cw

@@ -82,8 +82,15 @@ def cbd(st: Stream, shape, eta: int = 21) -> np.ndarray:
 
 
 def payload(st: Stream, n: int, length: int, bound: int) -> np.ndarray:
-    """n items of `length` coefficients uniform in [0, bound) as u32."""
-    return st.below(bound, n * length).astype(np.uint32).reshape(n, length)
+    """n items of `length` coefficients uniform in [0, bound) as u32.
+
+    A bound of 2^16 (16-bit coefficients) takes four coefficients from each
+    64-bit word, low half-word first; other bounds use rejection sampling."""
+    count = n * length
+    if bound == 1 << 16:
+        w = st.words((count + 3) // 4).astype("<u8")
+        return w.view("<u2")[:count].astype(np.uint32).reshape(n, length)
+    return st.below(bound, count).astype(np.uint32).reshape(n, length)
 
 
 def distinct_u32(st: Stream, n: int, exclude=None) -> np.ndarray:

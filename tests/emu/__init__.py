@@ -1,0 +1,40 @@
+"""Test-only CPU emulation of the CUDA kernels' arithmetic (see emu.cpp)."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "emu.cpp")
+CSRC = os.path.join(os.path.dirname(os.path.dirname(HERE)), "paper_2202_07569_gb300", "csrc")
+SO = os.path.join(HERE, "_build", "libemu.so")
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    deps = [SRC] + [os.path.join(CSRC, f) for f in ("arith.cuh", "host_tables.hpp")]
+    if not os.path.exists(SO) or os.path.getmtime(SO) < max(map(os.path.getmtime, deps)):
+        os.makedirs(os.path.dirname(SO), exist_ok=True)
+        tmp = SO + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-x", "c++", SRC, "-o", tmp],
+                       check=True)
+        os.replace(tmp, SO)
+    l = C.CDLL(SO)
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    U32, U64 = C.c_uint32, C.c_uint64
+    l.emu_bfv_mul.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p, u64p]
+    l.emu_bfv_mul.restype = C.c_int
+    l.emu_lift.argtypes = [U32, U32, u64p, U64, u64p, u64p]
+    l.emu_lift.restype = None
+    l.emu_ext_primes.argtypes = [U32, U32, u64p, u64p]
+    l.emu_ext_primes.restype = None
+    l.emu_substitute.argtypes = [U32, U32, u64p, U64, U32, u64p, u64p, u64p]
+    l.emu_substitute.restype = None
+    l.emu_scale.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p]
+    l.emu_scale.restype = C.c_int
+    _lib = l
+    return l

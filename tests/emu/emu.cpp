@@ -1,0 +1,233 @@
+// emu.cpp -- TEST-ONLY host emulation of the kernels' arithmetic.
+//
+// Runs the per-coefficient and per-butterfly functions of csrc/arith.cuh
+// with the tables of csrc/host_tables.hpp, in the order the kernels apply
+// them (stage by stage for the NTTs), so that the arithmetic of the CUDA
+// path can be compared with the oracle on a machine without a GPU.  It is
+// not part of the library and nothing in the product calls it.
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../paper_2202_07569_gb300/csrc/host_tables.hpp"
+
+using namespace cw;
+using namespace cw::host;
+
+namespace {
+
+struct Emu {
+  u32 N, logN, L, K;
+  u64 t;
+  std::vector<u64> q, p, all;
+  std::vector<std::vector<u64>> tw;  // per prime: 4N
+  std::vector<u64> ninv, ninv_s, mu;
+  BaseConv q2b;
+  ScaleTab S;
+
+  Emu(u32 N_, u32 L_, const u64 *q_, u64 t_) : N(N_), L(L_), t(t_) {
+    logN = 0;
+    while ((1u << logN) < N) ++logN;
+    q.assign(q_, q_ + L);
+    K = L + 1;
+    p = ntt_primes(N, K, q);
+    all = q;
+    all.insert(all.end(), p.begin(), p.end());
+    for (u64 pr : all) {
+      std::vector<u64> w(4 * N);
+      make_twiddles(pr, N, logN, w.data());
+      tw.push_back(w);
+      ninv.push_back(hinv(N % pr, pr));
+      ninv_s.push_back(shoup_of(ninv.back(), pr));
+      mu.push_back((u64)(((u128)1 << 116) / pr));
+    }
+    fill_conv(q2b, q, p);
+    fill_scale(S, q, p, t);
+  }
+  void fwd(u64 *a, u32 l) {
+    const u64 *w = tw[l].data();
+    for (u32 st = 0; st < logN; ++st)
+      for (u32 b = 0; b < N / 2; ++b) fwd_bfly(a, b, logN - 1 - st, 1u << st, w, w + N, all[l]);
+  }
+  void inv(u64 *a, u32 l) {
+    const u64 *w = tw[l].data();
+    for (u32 st = 0; st < logN; ++st)
+      for (u32 b = 0; b < N / 2; ++b) inv_bfly(a, b, st, N >> (st + 1), w + 2 * N, w + 3 * N, all[l]);
+    for (u32 c = 0; c < N; ++c) a[c] = shoup(a[c], ninv[l], ninv_s[l], all[l]);
+  }
+  // coefficient ct [2][L][N] -> QP-NTT [2][L+K][N]
+  void to_qp(const u64 *ct, u64 *out) {
+    const u32 LK = L + K;
+    u64 x[kMaxL], y[kMaxK];
+    for (u32 poly = 0; poly < 2; ++poly) {
+      for (u32 c = 0; c < N; ++c) {
+        for (u32 j = 0; j < L; ++j) x[j] = ct[(poly * L + j) * N + c];
+        lift(x, y);
+        for (u32 j = 0; j < L; ++j) out[(poly * LK + j) * N + c] = x[j];
+        for (u32 k = 0; k < K; ++k) out[(poly * LK + L + k) * N + c] = y[k];
+      }
+      for (u32 l = 0; l < LK; ++l) fwd(out + (poly * LK + l) * N, l);
+    }
+  }
+  void lift(const u64 *x, u64 *y) {
+    switch (L) {
+      case 1: lift_centered<1, 2>(x, y, q2b); break;
+      case 2: lift_centered<2, 3>(x, y, q2b); break;
+      case 3: lift_centered<3, 4>(x, y, q2b); break;
+      case 4: lift_centered<4, 5>(x, y, q2b); break;
+      case 5: lift_centered<5, 6>(x, y, q2b); break;
+      case 6: lift_centered<6, 7>(x, y, q2b); break;
+      case 7: lift_centered<7, 8>(x, y, q2b); break;
+      default: lift_centered<8, 9>(x, y, q2b); break;
+    }
+  }
+  bool scale(const u64 *dq, const u64 *dp, u64 *e) {
+    switch (L) {
+      case 1: return scale_coeff<1>(dq, dp, e, S);
+      case 2: return scale_coeff<2>(dq, dp, e, S);
+      case 3: return scale_coeff<3>(dq, dp, e, S);
+      case 4: return scale_coeff<4>(dq, dp, e, S);
+      case 5: return scale_coeff<5>(dq, dp, e, S);
+      case 6: return scale_coeff<6>(dq, dp, e, S);
+      case 7: return scale_coeff<7>(dq, dp, e, S);
+      default: return scale_coeff<8>(dq, dp, e, S);
+    }
+  }
+  // key [L][2][L][N] coefficient -> NTT + Shoup companions
+  void prep_key(const u64 *key, std::vector<u64> &k, std::vector<u64> &ks) {
+    k.assign(key, key + 2ull * L * L * N);
+    ks.assign(k.size(), 0);
+    for (u32 unit = 0; unit < 2 * L; ++unit)
+      for (u32 j = 0; j < L; ++j) {
+        u64 *a = k.data() + ((u64)unit * L + j) * N;
+        fwd(a, j);
+        for (u32 c = 0; c < N; ++c) ks[((u64)unit * L + j) * N + c] = shoup_of(a[c], q[j]);
+      }
+  }
+  // key switch of z ([L][N] coefficient digits) plus optional addends,
+  // result in coefficient form [2][L][N]
+  void keyswitch(const u64 *z, const u64 *add0, const u64 *add1, const std::vector<u64> &k,
+                 const std::vector<u64> &ks, u64 *out) {
+    std::vector<u64> s(N), a0(N), a1(N);
+    for (u32 j = 0; j < L; ++j) {
+      u64 qj = q[j];
+      std::fill(a0.begin(), a0.end(), 0);
+      std::fill(a1.begin(), a1.end(), 0);
+      for (u32 i = 0; i < L; ++i) {
+        for (u32 c = 0; c < N; ++c) {
+          u64 d = z[(u64)i * N + c];
+          s[c] = d >= qj ? d - qj : d;
+        }
+        fwd(s.data(), j);
+        const u64 *kb = k.data() + ((u64)(i * 2) * L + j) * N, *ka = kb + (u64)L * N;
+        const u64 *kbs = ks.data() + ((u64)(i * 2) * L + j) * N, *kas = kbs + (u64)L * N;
+        for (u32 c = 0; c < N; ++c) {
+          a0[c] = addq(a0[c], shoup(s[c], kb[c], kbs[c], qj), qj);
+          a1[c] = addq(a1[c], shoup(s[c], ka[c], kas[c], qj), qj);
+        }
+      }
+      for (int comp = 0; comp < 2; ++comp) {
+        const u64 *ad = comp ? add1 : add0;
+        if (!ad) continue;
+        memcpy(s.data(), ad + (u64)j * N, N * 8);
+        fwd(s.data(), j);
+        std::vector<u64> &acc = comp ? a1 : a0;
+        for (u32 c = 0; c < N; ++c) acc[c] = addq(acc[c], s[c], qj);
+      }
+      inv(a0.data(), j);
+      inv(a1.data(), j);
+      memcpy(out + (u64)j * N, a0.data(), N * 8);
+      memcpy(out + ((u64)L + j) * N, a1.data(), N * 8);
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+// One homomorphic multiplication, returns 0 or 1 if the scale-down check
+// tripped.
+int emu_bfv_mul(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *rlk,
+                const uint64_t *a, const uint64_t *b, uint64_t *out) {
+  Emu E(N, L, q, t);
+  const u32 LK = L + E.K;
+  std::vector<u64> A(2ull * LK * N), B(2ull * LK * N);
+  E.to_qp(a, A.data());
+  E.to_qp(b, B.data());
+  std::vector<u64> Tb(3ull * LK * N), Eb(3ull * L * N);
+  for (u32 which = 0; which < 3; ++which)
+    for (u32 l = 0; l < LK; ++l) {
+      u64 pr = E.all[l], m = E.mu[l];
+      const u64 *a0 = A.data() + (u64)l * N, *a1 = a0 + (u64)LK * N;
+      const u64 *b0 = B.data() + (u64)l * N, *b1 = b0 + (u64)LK * N;
+      u64 *o = Tb.data() + ((u64)which * LK + l) * N;
+      for (u32 c = 0; c < N; ++c) {
+        if (which == 0) o[c] = barrett(a0[c], b0[c], pr, m);
+        else if (which == 2) o[c] = barrett(a1[c], b1[c], pr, m);
+        else o[c] = addq(barrett(a0[c], b1[c], pr, m), barrett(a1[c], b0[c], pr, m), pr);
+      }
+      E.inv(o, l);
+    }
+  int bad = 0;
+  u64 dq[kMaxL], dp[kMaxK], e[kMaxL];
+  for (u32 which = 0; which < 3; ++which)
+    for (u32 c = 0; c < N; ++c) {
+      const u64 *in = Tb.data() + (u64)which * LK * N;
+      for (u32 j = 0; j < L; ++j) dq[j] = in[(u64)j * N + c];
+      for (u32 k = 0; k < E.K; ++k) dp[k] = in[(u64)(L + k) * N + c];
+      if (!E.scale(dq, dp, e)) bad = 1;
+      for (u32 j = 0; j < L; ++j) Eb[((u64)which * L + j) * N + c] = e[j];
+    }
+  std::vector<u64> k, ks;
+  E.prep_key(rlk, k, ks);
+  E.keyswitch(Eb.data() + 2ull * L * N, Eb.data(), Eb.data() + (u64)L * N, k, ks, out);
+  return bad;
+}
+
+// Centered Q -> P conversion of one coefficient vector ([L] residues).
+void emu_lift(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *x,
+              uint64_t *y) {
+  Emu E(N, L, q, t);
+  E.lift(x, y);
+}
+
+// The extension primes the library chooses for these parameters.
+void emu_ext_primes(uint32_t N, uint32_t L, const uint64_t *q, uint64_t *p) {
+  std::vector<u64> v = ntt_primes(N, L + 1, std::vector<u64>(q, q + L));
+  for (u32 i = 0; i < L + 1; ++i) p[i] = v[i];
+}
+
+// Sub_g: automorphism then key switch with the Galois key (coefficient form).
+void emu_substitute(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint32_t g,
+                    const uint64_t *gkey, const uint64_t *ct, uint64_t *out) {
+  Emu E(N, L, q, t);
+  std::vector<u64> tau(2ull * L * N);
+  for (u32 pl = 0; pl < 2 * L; ++pl) {
+    u64 qj = q[pl % L];
+    for (u32 i = 0; i < N; ++i) {
+      u64 v = ct[(u64)pl * N + i];
+      u32 e = (u32)(((u64)i * g) & (2ull * N - 1));
+      if (e >= N) {
+        e -= N;
+        v = v ? qj - v : 0;
+      }
+      tau[(u64)pl * N + e] = v;
+    }
+  }
+  std::vector<u64> k, ks;
+  E.prep_key(gkey, k, ks);
+  E.keyswitch(tau.data() + (u64)L * N, tau.data(), nullptr, k, ks, out);
+}
+
+}  // extern "C"
+
+extern "C" {
+// round(t d / Q) mod q_j for one coefficient given by its residues mod the
+// q_j (dq) and the extension primes (dp); returns 0 if the check tripped.
+int emu_scale(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *dq,
+              const uint64_t *dp, uint64_t *out) {
+  Emu E(N, L, q, t);
+  return E.scale(dq, dp, out) ? 1 : 0;
+}
+}

@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (called through the C ABI) with the oracle.
+
+Every comparison is bit for bit: the path is exact integer arithmetic and
+the oracle computes the same exact function step by step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_07569_gb300 import synthetic as syn
+from tests.workloads import CONFIGS, T, Client, database
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2202_07569_gb300 import build
+
+    build.build()
+
+
+_clients = {}
+
+
+def client(N, L, seed=3, c_max=0):
+    key = (N, L, seed, c_max)
+    if key not in _clients:
+        cl = Client(N, L, seed, c_max)
+        cl.ctx = cl.context()
+        _clients[key] = cl
+    return _clients[key]
+
+
+# ------------------------------------------------------------ multiplication
+@pytest.mark.parametrize("N,L", [(1024, 1), (4096, 2), (8192, 4), (16384, 7)])
+def test_mul_matches_oracle(N, L):
+    cl = client(N, L)
+    st = syn.Stream(100, N + L)
+    for trial in range(2):
+        a = syn.uniform_residues(st, cl.q, (2,), N)
+        b = syn.uniform_residues(st, cl.q, (2,), N)
+        got = cl.ctx.mul(a, b)
+        assert np.array_equal(got, cl.O.bfv_mul(a, b, cl.rlk)), trial
+
+
+def test_mul_edge_coefficients():
+    """Coefficients at 0, 1, Q-1 and next to Q/2 (mixed-radix branch)."""
+    import math
+
+    N, L = 4096, 2
+    cl = client(N, L)
+    q = [int(v) for v in cl.q]
+    Q = math.prod(q)
+    st = syn.Stream(101)
+    a = syn.uniform_residues(st, q, (2,), N)
+    b = syn.uniform_residues(st, q, (2,), N)
+    specials = [0, 1, Q - 1, (Q - 1) // 2, (Q + 1) // 2, (Q - 3) // 2, (Q + 3) // 2]
+    for i, v in enumerate(specials):
+        for poly in range(2):
+            for j, qq in enumerate(q):
+                a[poly, j, 7 * i] = v % qq
+                b[poly, j, 11 * i + 1] = (Q - 1 - v) % qq
+    assert np.array_equal(cl.ctx.mul(a, b), cl.O.bfv_mul(a, b, cl.rlk))
+
+
+def test_mul_decrypts_to_product():
+    N, L = 8192, 4
+    cl = client(N, L)
+    mu = [np.zeros(N, np.uint32) for _ in range(2)]
+    mu[0][0], mu[0][5] = 1, 7
+    mu[1][0], mu[1][1] = 3, 1
+    a, e = cl.cd.encryption(2, 5)
+    ca = cl.O.encrypt(mu[0], cl.cd.s, a[0], e[0])
+    cb = cl.O.encrypt(mu[1], cl.cd.s, a[1], e[1])
+    got, budget = cl.decrypt(cl.ctx.mul(ca, cb))
+    want = np.zeros(N, np.uint32)
+    want[0], want[1], want[5], want[6] = 3, 1, 21, 7
+    assert np.array_equal(got, want) and budget > 0
+
+
+# ------------------------------------------------------------ substitution, expansion
+@pytest.mark.parametrize("N,L", [(4096, 2), (16384, 7)])
+def test_substitute_matches_oracle(N, L):
+    cl = client(N, L, c_max=3)
+    for g in cl.galois:
+        ct = syn.uniform_residues(syn.Stream(102, g), cl.q, (2,), N)
+        assert np.array_equal(cl.ctx.substitute(g, ct), cl.O.substitute(g, ct, cl.galois[g]))
+
+
+@pytest.mark.parametrize("N,L,m,c", [(4096, 2, 24, 3), (8192, 4, 37, 2), (16384, 7, 64, 6)])
+def test_expand_matches_oracle(N, L, m, c):
+    cl = client(N, L, c_max=c)
+    pos = oracle.map_perfect(12345 % oracle.binom(m, 4), m, 4)
+    query = cl.query(pos, m, c, stream=3)
+    got = cl.ctx.expand(query, c, m)
+    want = cl.O.expand(query, c, m, cl.gkeys)
+    assert np.array_equal(got, want)
+    bits = np.zeros(m, np.uint32)
+    bits[pos] = 1
+    for j in (int(pos[0]), (int(pos[0]) + 1) % m):
+        mu, budget = cl.decrypt(got[j])
+        assert mu[0] == bits[j] and not mu[1:].any() and budget > 0
+
+
+# ------------------------------------------------------------ plain multiplication
+def test_plain_mul_matches_oracle():
+    N, L = 8192, 4
+    cl = client(N, L)
+    items, cw, _ = database(5, 3000, T, 2, 5, seed=7)
+    db = cl.ctx.load_db(items, cw, 5)
+    ct = syn.uniform_residues(syn.Stream(103), cl.q, (2,), N)
+    for row in (0, 4):
+        assert np.array_equal(cl.ctx.plain_mul(db, row, ct), cl.O.plain_mul(ct, items[row]))
+    cl.ctx.free_db(db)
+
+
+# ------------------------------------------------------------ selection vector
+@pytest.mark.parametrize("k,m", [(2, 24), (3, 14), (4, 37), (5, 12)])
+def test_selection_matches_oracle(k, m):
+    N, L = 4096, 2
+    cl = client(N, L)
+    n = 60
+    items, cw, _ = database(n, 16, T, k, m, seed=8)
+    db = cl.ctx.load_db(items, cw, m)
+    query = cl.query(cw[17], m, 0, stream=4)
+    rows = np.array([0, 17, 59, 33], np.uint64)
+    for share in (1, 0):
+        cl.ctx.set_option(1, share)
+        got = cl.ctx.selection(db, query, rows)
+        for i, r in enumerate(rows.tolist()):
+            assert np.array_equal(got[i], cl.O.selection(query, cw[r], cl.rlk)), (share, r)
+    cl.ctx.set_option(1, 1)
+    cl.ctx.free_db(db)
+
+
+# ------------------------------------------------------------ full answers
+def test_c1_answer_bit_exact_and_decrypts():
+    """Configuration 1 at full size: n=256, k=2, m=24, N=4096, L=2."""
+    cfg = CONFIGS["c1"]
+    cl = Client(cfg["N"], cfg["L"], cfg["seed"])
+    ctx = cl.context()
+    items, cw, _ = database(cfg["n"], cfg["plen"], cfg["bound"], cfg["k"], cfg["m"], cfg["seed"] + 1)
+    db = ctx.load_db(items, cw, cfg["m"])
+    target = int(syn.Stream(cfg["seed"] + 2).below(cfg["n"], 1)[0])
+    query = cl.query(cw[target], cfg["m"], 0)
+    got = ctx.answer(db, query)
+    want = cl.O.answer(items, cw, cfg["m"], query, cl.rlk)
+    assert np.array_equal(got, want)
+    mu, budget = cl.decrypt(got)
+    assert np.array_equal(mu, items[target]) and budget > 0
+    stats = ctx.last_stats()
+    assert stats["rows"] == cfg["n"] and stats["mults"] == cfg["n"]
+
+
+@pytest.mark.parametrize("share,batch", [(1, 0), (0, 0), (1, 7), (0, 13)])
+def test_c2_params_answer_bit_exact(share, batch):
+    """N=8192, L=4, k=4, m=37 on 150 rows: shared first level on and off and
+    batch splits with ragged tails all give the oracle's response."""
+    cl = client(8192, 4, seed=11)
+    n, k, m = 150, 4, 37
+    items, cw, _ = database(n, 8192, 1 << 16, k, m, seed=12)
+    ctx = cl.ctx
+    ctx.set_option(1, share)
+    ctx.set_option(2, batch)
+    db = ctx.load_db(items, cw, m)
+    query = cl.query(cw[77], m, 0, stream=6)
+    got = ctx.answer(db, query)
+    if "c2small" not in _clients:
+        _clients["c2small"] = cl.O.answer(items, cw, m, query, cl.rlk)
+    assert np.array_equal(got, _clients["c2small"])
+    mu, budget = cl.decrypt(got)
+    assert np.array_equal(mu, items[77]) and budget > 0
+    ctx.set_option(1, 1)
+    ctx.set_option(2, 0)
+    ctx.free_db(db)
+
+
+def _sparse_rows(n, count, seed):
+    rows = syn.Stream(seed, 9).below(n, 4 * count)
+    return np.array(sorted(set(rows.tolist())))[:count]
+
+
+def test_c2_full_size_sparse_parity_and_random_decrypt():
+    """Configuration 2 at full size (n=65536, k=4, m=37, N=8192, L=4) in the
+    launch configuration of the benchmark.  The response is linear in the
+    rows: with all but a sample of rows zero the oracle computes the exact
+    response from the sampled rows alone while the GPU still runs the full
+    selection vector.  A second answer over uniform rows must decrypt to the
+    target row."""
+    cfg = CONFIGS["c2"]
+    cl = client(cfg["N"], cfg["L"], seed=cfg["seed"])
+    ctx = cl.ctx
+    n, k, m = cfg["n"], cfg["k"], cfg["m"]
+    items, cw, _ = database(n, cfg["plen"], cfg["bound"], k, m, cfg["seed"] + 1)
+    target = int(syn.Stream(cfg["seed"] + 2).below(n, 1)[0])
+    query = cl.query(cw[target], m, 0)
+    db = ctx.load_db(items, cw, m)
+    got = ctx.answer(db, query)
+    mu, budget = cl.decrypt(got)
+    assert np.array_equal(mu, items[target]) and budget > 0
+    ctx.free_db(db)
+    sample = np.union1d(_sparse_rows(n, 6, 13), [target])
+    sparse = np.zeros_like(items)
+    sparse[sample] = items[sample]
+    db = ctx.load_db(sparse, cw, m)
+    got = ctx.answer(db, query)
+    want = cl.O.answer(items[sample], cw[sample], m, query, cl.rlk)
+    assert np.array_equal(got, want)
+    ctx.free_db(db)
+
+
+def test_c3_keyword_full_size_sparse_parity_present_and_absent():
+    """Configuration 3 at full size: 16384 rows keyed by uniform 32-bit
+    keywords, k=8, m=64, N=16384, L=7, compressed query (c=6, one ct).
+    Present keyword decrypts to its row; absent keyword to zeros; sampled
+    rows give the oracle's exact response."""
+    cfg = CONFIGS["c3"]
+    cl = client(cfg["N"], cfg["L"], seed=cfg["seed"], c_max=cfg["c"])
+    ctx = cl.ctx
+    n, k, m, c = cfg["n"], cfg["k"], cfg["m"], cfg["c"]
+    items, cw, ids = database(n, cfg["plen"], cfg["bound"], k, m, cfg["seed"] + 1, keyword=True)
+    db = ctx.load_db(items, cw, m)
+    present = int(syn.Stream(cfg["seed"] + 2).below(n, 1)[0])
+    q1 = cl.query(cw[present], m, c, stream=1)
+    got = ctx.answer(db, q1, c)
+    mu, budget = cl.decrypt(got)
+    want = np.zeros(cfg["N"], np.uint32)
+    want[: cfg["plen"]] = items[present]
+    assert np.array_equal(mu, want) and budget > 0
+    absent = int(syn.distinct_u32(syn.Stream(cfg["seed"] + 3), 1, exclude=ids)[0])
+    q2 = cl.query(oracle.map_perfect(absent, m, k), m, c, stream=2)
+    got2 = ctx.answer(db, q2, c)
+    mu2, budget2 = cl.decrypt(got2)
+    assert not mu2.any() and budget2 > 0
+    ctx.free_db(db)
+    sample = np.union1d(_sparse_rows(n, 3, 23), [present])
+    sparse = np.zeros_like(items)
+    sparse[sample] = items[sample]
+    db = ctx.load_db(sparse, cw, m)
+    got = ctx.answer(db, q1, c)
+    want = cl.O.answer(items[sample], cw[sample], m, q1, cl.rlk, c=c, gkeys=cl.gkeys)
+    assert np.array_equal(got, want)
+    ctx.free_db(db)
+
+
+# ------------------------------------------------------------ edge cases and errors
+def test_single_row_and_unary_code():
+    cl = client(4096, 2)
+    items, cw, _ = database(1, 100, T, 2, 5, seed=31)
+    db = cl.ctx.load_db(items, cw, 5)
+    q = cl.query(cw[0], 5, 0, stream=8)
+    assert np.array_equal(cl.ctx.answer(db, q), cl.O.answer(items, cw, 5, q, cl.rlk))
+    cl.ctx.free_db(db)
+    items, cw, _ = database(9, 50, T, 1, 9, seed=32)  # k = 1: unary selection
+    db = cl.ctx.load_db(items, cw, 9)
+    q = cl.query(cw[4], 9, 0, stream=9)
+    got = cl.ctx.answer(db, q)
+    assert np.array_equal(got, cl.O.answer(items, cw, 9, q, cl.rlk))
+    cl.ctx.free_db(db)
+
+
+def test_errors_are_reported():
+    from paper_2202_07569_gb300 import binding as B
+
+    cl = client(4096, 2)
+    bad = syn.uniform_residues(syn.Stream(1), cl.q, (2,), 4096)
+    bad[0, 0, 0] = cl.q[0]
+    with pytest.raises(B.CwpirError) as ei:
+        cl.ctx.mul(bad, bad)
+    assert ei.value.code == -1
+    with pytest.raises(B.CwpirError) as ei:
+        cl.ctx.answer(12345, bad[None])
+    assert ei.value.code == -3
+    with pytest.raises(B.CwpirError) as ei:
+        cl.ctx.substitute(7, bad)
+    assert ei.value.code == -7
+    items, cw, _ = database(4, 10, T, 2, 4, seed=33)
+    cw[1] = cw[1][::-1]
+    with pytest.raises(B.CwpirError):
+        cl.ctx.load_db(items, cw, 4)

@@ -1,0 +1,114 @@
+"""The CUDA kernels' arithmetic, run on the CPU through the test-only
+emulator (tests/emu), against the oracle and exact integers.
+
+These need no GPU: they check the modular arithmetic, the exact base
+conversion (including the values next to Q/2 that take the mixed-radix
+path), the exact scale-down and the order of the multiplication steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2202_07569_gb300 import synthetic as syn
+from tests import emu
+
+T = 65537
+
+
+def centered(x, M):
+    return x - M if x > M // 2 else x
+
+
+def _setup(orc, N, L, seed=3):
+    q = orc.primes(N, L)
+    O = orc.Oracle(N, q)
+    cd = syn.ClientDraws(seed, q, N)
+    a, e = cd.relin()
+    rlk = O.keygen_relin(cd.s, a, e)
+    return q, O, cd, rlk
+
+
+@pytest.mark.parametrize("N,L", [(1024, 1), (1024, 3), (4096, 2), (8192, 4)])
+def test_emulated_multiplication_matches_oracle(orc, N, L):
+    q, O, cd, rlk = _setup(orc, N, L)
+    st = syn.Stream(5, N + L)
+    a = syn.uniform_residues(st, q, (2,), N)
+    b = syn.uniform_residues(st, q, (2,), N)
+    out = np.zeros((2, L, N), np.uint64)
+    bad = emu.lib().emu_bfv_mul(N, L, q, T, np.ascontiguousarray(rlk), a, b, out)
+    assert bad == 0
+    assert np.array_equal(out, O.bfv_mul(a, b, rlk))
+
+
+def test_emulated_multiplication_matches_oracle_n16384(orc):
+    q, O, cd, rlk = _setup(orc, 16384, 7)
+    st = syn.Stream(6)
+    a = syn.uniform_residues(st, q, (2,), 16384)
+    b = syn.uniform_residues(st, q, (2,), 16384)
+    out = np.zeros((2, 7, 16384), np.uint64)
+    assert emu.lib().emu_bfv_mul(16384, 7, q, T, np.ascontiguousarray(rlk), a, b, out) == 0
+    assert np.array_equal(out, O.bfv_mul(a, b, rlk))
+
+
+@pytest.mark.parametrize("N,L", [(1024, 2), (8192, 4), (16384, 7)])
+def test_centered_lift_near_half(orc, N, L):
+    """Values next to Q/2 and 0 take the exact mixed-radix branch."""
+    q = [int(v) for v in orc.primes(N, L)]
+    Q = math.prod(q)
+    p = np.zeros(L + 1, np.uint64)
+    emu.lib().emu_ext_primes(N, L, np.array(q, np.uint64), p)
+    p = [int(v) for v in p]
+    vals = [0, 1, Q - 1, (Q - 1) // 2, (Q + 1) // 2, (Q - 3) // 2, (Q + 3) // 2]
+    vals += [(Q >> 1) + d for d in (-(1 << 12), 1 << 12)]
+    st = syn.Stream(7)
+    vals += [int(w) * (Q >> 64) for w in st.words(5)]
+    for x in vals:
+        res = np.array([x % qq for qq in q], np.uint64)
+        y = np.zeros(L + 1, np.uint64)
+        emu.lib().emu_lift(N, L, np.array(q, np.uint64), T, res, y)
+        xc = centered(x, Q)
+        assert [int(v) for v in y] == [xc % pp for pp in p], x
+
+
+@pytest.mark.parametrize("N,L", [(1024, 2), (8192, 4), (16384, 7)])
+def test_exact_scale_down(orc, N, L):
+    """round(t d / Q) for extreme and near-tie d, including t d = (Q +- 1)/2
+    (mod Q), which takes the mixed-radix branch."""
+    q = [int(v) for v in orc.primes(N, L)]
+    Q = math.prod(q)
+    p = np.zeros(L + 1, np.uint64)
+    emu.lib().emu_ext_primes(N, L, np.array(q, np.uint64), p)
+    p = [int(v) for v in p]
+    dmax = 2 * N * (Q // 2) ** 2
+    inv_t = pow(T, -1, Q)
+    ds = [0, 1, -1, dmax, -dmax, dmax - 12345, -(dmax // 3)]
+    for r in ((Q - 1) // 2, (Q + 1) // 2, (Q - 5) // 2):
+        base = (r * inv_t) % Q
+        ds += [base, base - Q, base + 7 * Q, base - 11 * Q]
+    st = syn.Stream(8)
+    for w in st.words(10).tolist():
+        ds.append((int(w) * dmax) >> 64)
+        ds.append(-((int(w) * dmax) >> 65))
+    qa = np.array(q, np.uint64)
+    for d in ds:
+        assert abs(d) <= dmax
+        dq = np.array([d % v for v in q], np.uint64)
+        dp = np.array([d % v for v in p], np.uint64)
+        out = np.zeros(L, np.uint64)
+        assert emu.lib().emu_scale(N, L, qa, T, dq, dp, out) == 1
+        num = T * d
+        want = (num + Q // 2) // Q  # nearest integer: Q odd, no ties
+        assert [int(v) for v in out] == [want % v for v in q], d
+
+
+def test_emulated_substitution_matches_oracle(orc):
+    N, L = 1024, 3
+    q, O, cd, rlk = _setup(orc, N, L)
+    for gi, g in enumerate((N + 1, N // 4 + 1, 3)):
+        a, e = cd.galois(gi)
+        gk = O.keygen_galois(g, cd.s, a, e)
+        ct = syn.uniform_residues(syn.Stream(9, g), q, (2,), N)
+        out = np.zeros((2, L, N), np.uint64)
+        emu.lib().emu_substitute(N, L, q, T, g, np.ascontiguousarray(gk), ct, out)
+        assert np.array_equal(out, O.substitute(g, ct, gk))
