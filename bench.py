@@ -36,7 +36,7 @@ METRIC = "PIR answer DB MB/s per query (N=8192,k=4); batched vs plain; p50/p99 l
 WL = dict(N=8192, L=4, n=65536, k=4, m=37, plen=8192, t=65537, coef_bytes=2)
 WORKLOAD_NAME = ("index PIR n=65536 rows x 8192 16-bit coefficients, k=4, m=37, "
                  "BFV N=8192 L=4 (54-bit primes) t=65537, one query per step")
-IMAD_PER_MODMUL = 10  # see the design doc: three 64x64-bit products on 32-bit pipes
+IMAD_PER_MODMUL = 10  # one 64x64 high product (4 IMAD) + two low products (3 each)
 IMAD_PER_SM_CLK = 64
 SMS = 152
 
