@@ -97,11 +97,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def make_inputs(seed: int = 12):
+def make_inputs(seed: int = 12, rows: int | None = None):
     from paper_2202_07569_gb300 import binding as B
     from paper_2202_07569_gb300 import synthetic as syn
 
-    N, L, n, k, m = WL["N"], WL["L"], WL["n"], WL["k"], WL["m"]
+    N, L, n, k, m = WL["N"], WL["L"], rows or WL["n"], WL["k"], WL["m"]
     q = B.default_primes(N, L)
     rlk = syn.uniform_residues(syn.Stream(seed, 3), q, (L, 2), N)
     query = syn.uniform_ciphertexts(seed + 1, q, m, N)
@@ -134,8 +134,10 @@ def run_gpu(args, rank: int, world: int, dist):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    q, rlk, query, items, cw = make_inputs(12 + rank)
+    q, rlk, query, items, cw = make_inputs(12 + rank, args.rows)
     ctx = B.Context(WL["N"], q, WL["t"], rlk)
+    if args.max_jobs:
+        ctx.set_option(B.OPT_MAX_JOBS, args.max_jobs)
     db = ctx.load_db(items, cw, WL["m"])
     del items
     stream = torch.cuda.current_stream()
@@ -193,7 +195,7 @@ def run_gpu(args, rank: int, world: int, dist):
     h2d = query.nbytes
     d2h = resp.nbytes
 
-    rows = WL["n"]
+    rows = cw.shape[0]
     mb = payload_mb(rows)
     out = {
         "value": world * mb / (ms_per_step / 1e3),
@@ -256,6 +258,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="profiling only: answer over the first ROWS rows instead of 65536")
+    ap.add_argument("--max-jobs", type=int, default=0,
+                    help="multiplications per kernel launch (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -306,6 +312,11 @@ def main():
     if rank != 0:
         return
     line = dict(base)
+    if args.rows:
+        line["config"] = dict(base["config"], rows=args.rows,
+                              workload="PROFILING SIZE, not the metric workload: " + WORKLOAD_NAME)
+    if args.max_jobs:
+        line["config"]["max_jobs"] = args.max_jobs
     line.update(res)
     if world == 1 and not args.no_cpu_baseline:
         mbps, cores, sample = cpu_baseline(None, 1)

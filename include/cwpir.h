@@ -170,7 +170,11 @@ enum {
   /* 1: bracket every kernel launch with CUDA events on its stream and add
    * the durations per kernel class (read with cwpir_kernel_times); 0
    * (default): no events */
-  CWPIR_OPT_KERNEL_TIMING = 4
+  CWPIR_OPT_KERNEL_TIMING = 4,
+  /* multiplications per kernel launch (0 = automatic, at most 1024); sizes
+   * the context's scratch, so it takes effect only before the first call
+   * that needs scratch */
+  CWPIR_OPT_MAX_JOBS = 5
 };
 int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
 

@@ -25,6 +25,7 @@ OPT_SHARE_LEVEL1 = 1
 OPT_BATCH_ROWS = 2
 OPT_USE_GRAPH = 3
 OPT_KERNEL_TIMING = 4
+OPT_MAX_JOBS = 5
 K_CLASSES = 7
 
 

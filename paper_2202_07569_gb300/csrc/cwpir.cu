@@ -98,6 +98,7 @@ struct cwpir_ctx {
   std::string err;
   int opt_share = 1, opt_graph = 0;
   u32 opt_batch_rows = 0;
+  u32 opt_max_jobs = 0;
   cudaStream_t stream = nullptr;
   // scratch
   u32 jmax = 0;
@@ -233,6 +234,7 @@ int ensure_scratch(cwpir_ctx *c) {
   const u64 budget = 2ull << 30;
   u64 j = budget / per_job;
   j = std::max<u64>(32, std::min<u64>(1024, j));
+  if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
   c->jmax = (u32)j;
   CUDA_TRY(c, c->Tbuf.ensure(j * 3 * (L + K) * N));
   CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
@@ -972,6 +974,11 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
       return CWPIR_OK;
     case CWPIR_OPT_USE_GRAPH: c->opt_graph = value ? 1 : 0; return CWPIR_OK;
     case CWPIR_OPT_KERNEL_TIMING: c->opt_timing = value ? 1 : 0; return CWPIR_OK;
+    case CWPIR_OPT_MAX_JOBS:
+      if (value < 0 || value > 1024) return fail(c, CWPIR_EINVAL, "max jobs must be in [0, 1024]");
+      if (c->jmax) return fail(c, CWPIR_EINVAL, "max jobs must be set before the first answer");
+      c->opt_max_jobs = (u32)value;
+      return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
   }
 }
@@ -1010,3 +1017,4 @@ int cwpir_last_stats(const cwpir_ctx *c, cwpir_stats *out) {
 }
 
 }  // extern "C"
+
