@@ -178,6 +178,27 @@ enum {
 };
 int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
 
+/* Homomorphic multiplication M (as cwpir_mul) on device buffers that
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ * The paper has no counterpart; this call serves callers that cannot
+ * allocate device memory where they multiply (a fixed pre-partitioned
+ * memory pool, a section where an allocation would stall or is forbidden).
+ * d_a, d_b: [2][L][N] ciphertexts, d_out: [2][L][N], device memory owned by
+ * the caller; stream: a cudaStream_t (NULL: legacy default stream).  The
+ * call returns when the result is complete.
+ * Intermediates live in one file-scope device array of 2^20 u64 words
+ * (8 MiB) plus a 64-word header, held by every GPU that loads the library
+ * until the process exits.  One multiplication needs (17L + 7) * N words:
+ * N = 4096 allows L <= 8, N = 8192 allows L <= 7, N = 16384 allows L <= 3;
+ * larger sizes are rejected with EINVAL.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the previous call's contents (the error flag is cleared each call): calls
+ * that overlap on the GPU, from any context or stream, race.  ctx must be a
+ * set-up context (it supplies the tables and the relinearisation key). */
+int cwpir_mul_noalloc(cwpir_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b,
+                      uint64_t *d_out, void *stream);
+
 /* Work counters of the last answer on ctx (for throughput accounting). */
 typedef struct {
   uint64_t rows;            /* database rows processed */

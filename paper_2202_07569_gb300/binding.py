@@ -93,6 +93,7 @@ def lib():
             "cwpir_last_stats": (I, [vp, C.POINTER(Stats)]),
             "cwpir_kernel_times": (I, [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "cwpir_kernel_class_name": (C.c_char_p, [I]),
+            "cwpir_mul_noalloc": (I, [vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(l, name)
@@ -208,6 +209,10 @@ class Context:
         out = np.zeros(self.ct_shape, np.uint64)
         self._check(lib().cwpir_mul(self._h, _u64(a), _u64(b), out))
         return out
+
+    def mul_noalloc(self, d_a: int, d_b: int, d_out: int, stream: int = 0):
+        """cwpir_mul_noalloc on device pointers (no device allocation)."""
+        self._check(lib().cwpir_mul_noalloc(self._h, d_a, d_b, d_out, stream))
 
     def substitute(self, g: int, ct) -> np.ndarray:
         out = np.zeros(self.ct_shape, np.uint64)

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <new>
 #include <string>
@@ -1018,3 +1019,80 @@ int cwpir_last_stats(const cwpir_ctx *c, cwpir_stats *out) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------
+// Multiplication that allocates nothing.
+//
+// For callers that cannot allocate device memory on the answer path (a
+// process whose memory pool is fixed at start-up, a caller inside a
+// section where cudaMalloc is forbidden or would stall other work, a host
+// runtime that pre-partitions HBM): the intermediates of one homomorphic
+// multiplication live in this file-scope device array instead of
+// context-owned buffers.  Every GPU that loads the library holds the array
+// until the process exits.
+// ---------------------------------------------------------------------
+namespace {
+
+// 2^20 words (8 MiB) of intermediates plus a 64-word header (error flag at
+// word 0, the job descriptor at words 8..11).
+constexpr size_t kNoAllocWords = size_t(1) << 20;
+constexpr size_t kNoAllocHeader = 64;
+static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocHeader + kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+u64 *g_noalloc_addr[256] = {};
+
+// Address of the array on the current device; resolved once per device.
+int noalloc_scratch(cwpir_ctx *c, u64 **out) {
+  if (c->device < 0 || c->device >= 256) return fail(c, CWPIR_EINVAL, "device index");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[c->device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(c, CWPIR_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_addr[c->device] = (u64 *)p;
+  }
+  *out = g_noalloc_addr[c->device];
+  return CWPIR_OK;
+}
+
+}  // namespace
+
+extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64_t *d_b,
+                                 uint64_t *d_out, void *stream) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  if (!d_a || !d_b || !d_out) return fail(c, CWPIR_EINVAL, "null buffer");
+  const u64 LK = c->L + c->K, N = c->N;
+  const u64 qp = 2 * LK * N;
+  const u64 need = 2 * qp + 3 * LK * N + 3ull * c->L * N;
+  if (need > kNoAllocWords)
+    return fail(c, CWPIR_EINVAL,
+                "N=%u, L=%u needs (17L+7)N = %llu scratch words; the static array holds "
+                "%llu (N = 8192 allows L <= 7, N = 16384 allows L <= 3)",
+                c->N, c->L, (unsigned long long)need, (unsigned long long)kNoAllocWords);
+  cudaSetDevice(c->device);
+  u64 *base = nullptr;
+  int rc = noalloc_scratch(c, &base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *err = (int *)base;
+  cw::MulJob *job_dev = (cw::MulJob *)(base + 8);
+  u64 *qa = base + kNoAllocHeader, *qb = qa + qp, *tb = qb + qp, *eb = tb + 3 * LK * N;
+  cw::MulJob job{qa, qb, d_out, 0};
+  // the array keeps the previous call's contents: clear the error flag
+  CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int), st));
+  CUDA_TRY(c, cudaMemcpyAsync(job_dev, &job, sizeof job, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_a, (u64)c->L * N, qa, LK * N, 2, true, st));
+  CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_b, (u64)c->L * N, qb, LK * N, 2, true, st));
+  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, qa, 4, LK * N, 0, (u32)LK, false, nullptr, 0, st));
+  CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
+  CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
+  CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
+                               c->rlk_s.p, nullptr, nullptr, st));
+  int h_err = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (h_err) return fail(c, CWPIR_EINTERNAL, "device consistency check failed (scale-down)");
+  return CWPIR_OK;
+}
