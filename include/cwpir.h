@@ -172,8 +172,8 @@ enum {
    * (default): no events */
   CWPIR_OPT_KERNEL_TIMING = 4,
   /* multiplications per kernel launch (0 = automatic, at most 1024); sizes
-   * the context's scratch, so it takes effect only before the first call
-   * that needs scratch */
+   * the context's scratch: setting it waits for the device, frees the
+   * scratch and the answer plans, which the next call rebuilds */
   CWPIR_OPT_MAX_JOBS = 5
 };
 int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
@@ -188,9 +188,9 @@ int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
  * call returns when the result is complete.
  * Intermediates live in one file-scope device array of 2^20 u64 words
  * (8 MiB) plus a 64-word header, held by every GPU that loads the library
- * until the process exits.  One multiplication needs (17L + 7) * N words:
- * N = 4096 allows L <= 8, N = 8192 allows L <= 7, N = 16384 allows L <= 3;
- * larger sizes are rejected with EINVAL.  The first call on a device looks
+ * until the process exits.  One multiplication needs (L^2 + 21L + 7) * N
+ * words: N = 4096 allows L <= 8, N = 8192 allows L <= 4, N = 16384 allows
+ * L <= 2; larger sizes are rejected with EINVAL.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  All calls share the array and it keeps
  * the previous call's contents (the error flag is cleared each call): calls

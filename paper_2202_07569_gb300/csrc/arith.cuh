@@ -10,8 +10,10 @@
 
 #if defined(__CUDACC__)
 #define CW_HD __host__ __device__ __forceinline__
+#define CW_HDM __host__ __device__ __forceinline__
 #else
 #define CW_HD static inline
+#define CW_HDM inline
 #endif
 
 namespace cw {
@@ -57,38 +59,64 @@ CW_HD u64 barrett(u64 a, u64 b, u64 q, u64 mu) {
   return r >= q ? r - q : r;
 }
 
+// Reduction of X = hi 2^64 + lo < 2^112 modulo a prime 2^53 < q < 2^54
+// with mu = floor(2^116 / q): x1 = floor(X / 2^52) < 2^60 and
+// qh = floor(x1 mu / 2^64) > X/q - X/2^116 - 2^52/q - 1 > X/q - 1.57, so
+// X - qh q lies in [0, 2q).
+CW_HD u64 barrett_reduce(u64 hi, u64 lo, u64 q, u64 mu) {
+  u64 x1 = (hi << 12) | (lo >> 52);
+  u64 qh = mulhi(x1, mu);
+  u64 r = lo - qh * q;
+  return r >= q ? r - q : r;
+}
+
+// 128-bit accumulator of exact products of residues (< 2^108 each); at most
+// 16 terms keep the sum below 2^112.
+struct Acc128 {
+  u64 hi = 0, lo = 0;
+  CW_HDM void mac(u64 a, u64 b) {
+    u64 p = a * b;
+    u64 h = mulhi(a, b);
+    lo += p;
+    hi += h + (lo < p ? 1 : 0);
+  }
+  CW_HDM void add(u64 a) {
+    lo += a;
+    hi += lo < a ? 1 : 0;
+  }
+};
+
 // ---------------------------------------------------------------------
 // NTT butterflies (negacyclic, psi = primitive 2N-th root of unity).
+// Twiddles are stored as (value, Shoup companion) pairs.
 // Forward: Cooley-Tukey with the powers of psi in bit-reversed order,
 // natural-order input, bit-reversed output.  Inverse: Gentleman-Sande with
 // the powers of psi^-1, bit-reversed input, natural output, then * N^-1.
 // Stage s of the forward transform has m = 2^s groups of half-length
 // len = N / 2^(s+1); butterfly b (< N/2) is in group b / len.
 // ---------------------------------------------------------------------
-CW_HD void fwd_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *psi,
-                    const u64 *psi_s, u64 q) {
+CW_HD void fwd_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *psi2, u64 q) {
   u32 len = 1u << logh, g = b >> logh, pos = b & (len - 1);
   u32 j = (g << (logh + 1)) + pos;
   u64 U = a[j];
-  u64 V = shoup(a[j + len], psi[m + g], psi_s[m + g], q);
+  u64 V = shoup(a[j + len], psi2[2 * (m + g)], psi2[2 * (m + g) + 1], q);
   a[j] = addq(U, V, q);
   a[j + len] = subq(U, V, q);
 }
-CW_HD void inv_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *ipsi,
-                    const u64 *ipsi_s, u64 q) {
+CW_HD void inv_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *ipsi2, u64 q) {
   u32 len = 1u << logh, g = b >> logh, pos = b & (len - 1);
   u32 j = (g << (logh + 1)) + pos;
   u64 U = a[j], V = a[j + len];
   a[j] = addq(U, V, q);
-  a[j + len] = shoup(subq(U, V, q), ipsi[m + g], ipsi_s[m + g], q);
+  a[j + len] = shoup(subq(U, V, q), ipsi2[2 * (m + g)], ipsi2[2 * (m + g) + 1], q);
 }
 
 // Per-prime NTT data in device memory.
 struct NttPrime {
-  u64 q, mu;             // prime, Barrett constant floor(2^116/q)
-  u64 ninv, ninv_s;      // N^-1 mod q and Shoup companion
-  const u64 *psi, *psi_s;   // [N] psi^bitrev(i)
-  const u64 *ipsi, *ipsi_s; // [N] psi^-bitrev(i)
+  u64 q, mu;          // prime, Barrett constant floor(2^116/q)
+  u64 ninv, ninv_s;   // N^-1 mod q and Shoup companion
+  const u64 *psi2;    // [N][2]: psi^bitrev(i) and its Shoup companion
+  const u64 *ipsi2;   // [N][2]: psi^-bitrev(i) and its Shoup companion
 };
 
 // ---------------------------------------------------------------------
@@ -114,6 +142,8 @@ struct BaseConv {
   u64 d[kMaxK];                 // target primes
   u64 hat[kMaxK][kMaxK], hat_s[kMaxK][kMaxK]; // (S/s_j) mod d_k
   u64 smod[kMaxK], smod_s[kMaxK];   // S mod d_k
+  u64 negsmod[kMaxK];           // (-S) mod d_k
+  u64 d_mu[kMaxK];              // floor(2^116 / d_k)
   u64 mrinv[kMaxK][kMaxK], mrinv_s[kMaxK][kMaxK]; // s_i^-1 mod s_j, i < j
   u64 half_mr[kMaxK];           // mixed-radix digits of (S-1)/2
 };
@@ -149,7 +179,8 @@ CW_HD u64 round_sum(const u64 *y, const BaseConv &C, bool *ambiguous) {
 }
 
 // Centered conversion of one coefficient: x (NS source residues) -> out
-// (ND target residues of x_c).
+// (ND target residues of x_c): out_k = [sum_j y_j (S/s_j) - rho S]_{d_k},
+// accumulated exactly in 128 bits and reduced once.
 template <int NS, int ND>
 CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
   u64 y[NS];
@@ -158,10 +189,10 @@ CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
   u64 rho = round_sum<NS>(y, C, &amb);
   if (amb) rho += mr_greater_half<NS>(x, C);
   for (int k = 0; k < ND; ++k) {
-    u64 dk = C.d[k], acc = 0;
-    for (int j = 0; j < NS; ++j)
-      acc = addq(acc, shoup(y[j], C.hat[j][k], C.hat_s[j][k], dk), dk);
-    out[k] = subq(acc, shoup(rho, C.smod[k], C.smod_s[k], dk), dk);
+    Acc128 a;
+    for (int j = 0; j < NS; ++j) a.mac(y[j], C.hat[j][k]);
+    a.mac(rho, C.negsmod[k]);
+    out[k] = barrett_reduce(a.hi, a.lo, C.d[k], C.d_mu[k]);
   }
 }
 
@@ -171,15 +202,18 @@ CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
 // |d| < 2N(Q/2)^2 and P > t N Q + 1.
 //   eps = [t d]_Q centered: y_j = [d_j * t (Q/q_j)^-1]_{q_j}, rho as above,
 //   r = (t d - eps)/Q = round(t d / Q) exactly; modulo p_k:
-//   r_k = [t Q^-1]_{p_k} d_k - sum_j y_j [q_j^-1]_{p_k} + rho.
+//   r_k = [t Q^-1]_{p_k} d_k - sum_j y_j [q_j^-1]_{p_k} + rho, and its
+//   conversion digit yb_k = [r_k (P/p_k)^-1]_{p_k} is formed directly.
 //   |r| <= t N Q / 2 + 1 < P/2, so the centered conversion of r from the
 //   p-basis to the q-basis is exact (and never near the ambiguous zone).
 // ---------------------------------------------------------------------
 struct ScaleTab {
   u64 t_theta[kMaxL], t_theta_s[kMaxL]; // t (Q/q_j)^-1 mod q_j
   u64 t_mod[kMaxL], t_mod_s[kMaxL];     // t mod q_j (ambiguous path)
-  u64 tqinv[kMaxK], tqinv_s[kMaxK];     // t Q^-1 mod p_k
-  u64 qinv[kMaxL][kMaxK], qinv_s[kMaxL][kMaxK]; // q_j^-1 mod p_k
+  // yb_k = [r_k (P/p_k)^-1]_{p_k} = [A_k d_k + sum_j B_jk y_j + C_k rho]_{p_k}
+  u64 A[kMaxK];          // t Q^-1 (P/p_k)^-1 mod p_k
+  u64 B[kMaxL][kMaxK];   // -q_j^-1 (P/p_k)^-1 mod p_k
+  u64 Cr[kMaxK];         // (P/p_k)^-1 mod p_k
   BaseConv q2b;  // Q -> P conversion data (fraction and Garner parts used)
   BaseConv b2q;  // P -> Q conversion
 };
@@ -202,20 +236,19 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
   }
   u64 yb[K];
   for (int k = 0; k < K; ++k) {
-    u64 pk = S.b2q.s[k];
-    u64 r = shoup(dp[k], S.tqinv[k], S.tqinv_s[k], pk);
-    for (int j = 0; j < L; ++j)
-      r = subq(r, shoup(y[j], S.qinv[j][k], S.qinv_s[j][k], pk), pk);
-    r = addq(r, rho, pk);
-    yb[k] = shoup(r, S.b2q.theta[k], S.b2q.theta_s[k], pk);
+    Acc128 a;
+    a.mac(dp[k], S.A[k]);
+    for (int j = 0; j < L; ++j) a.mac(y[j], S.B[j][k]);
+    a.mac(rho, S.Cr[k]);
+    yb[k] = barrett_reduce(a.hi, a.lo, S.b2q.s[k], S.q2b.d_mu[k]);
   }
   bool amb2;
   u64 rho2 = round_sum<K>(yb, S.b2q, &amb2);
   for (int j = 0; j < L; ++j) {
-    u64 qj = S.b2q.d[j], acc = 0;
-    for (int k = 0; k < K; ++k)
-      acc = addq(acc, shoup(yb[k], S.b2q.hat[k][j], S.b2q.hat_s[k][j], qj), qj);
-    out[j] = subq(acc, shoup(rho2, S.b2q.smod[j], S.b2q.smod_s[j], qj), qj);
+    Acc128 a;
+    for (int k = 0; k < K; ++k) a.mac(yb[k], S.b2q.hat[k][j]);
+    a.mac(rho2, S.b2q.negsmod[j]);
+    out[j] = barrett_reduce(a.hi, a.lo, S.b2q.d[j], S.b2q.d_mu[j]);
   }
   return !amb2;
 }

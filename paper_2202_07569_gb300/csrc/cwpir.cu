@@ -40,6 +40,11 @@ struct DevBuf {
   ~DevBuf() {
     if (p) cudaFree(p);
   }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
   cudaError_t ensure(size_t count) {
     if (count <= n) return cudaSuccess;
     if (p) cudaFree(p);
@@ -103,7 +108,8 @@ struct cwpir_ctx {
   cudaStream_t stream = nullptr;
   // scratch
   u32 jmax = 0;
-  DevBuf Tbuf, E, CP, acc, exp_a, exp_b, exp_tau, exp_S, tmp_ct, tmp_ct2, io_in, io_out;
+  DevBuf Tbuf, E, CP, DN, acc, exp_a, exp_b, exp_tau, exp_S, exp_DN, exp_O, tmp_ct, tmp_ct2,
+      io_in, io_out;
   int *d_err = nullptr;
   cw::SubJob *d_subjobs = nullptr;
   size_t n_subjobs = 0;
@@ -191,10 +197,8 @@ int build_tables(cwpir_ctx *c) {
     pr.ninv = hinv(N % q, q);
     pr.ninv_s = shoup_of(pr.ninv, q);
     u64 *d = c->twiddles.p + 4ull * l * N;
-    pr.psi = d;
-    pr.psi_s = d + N;
-    pr.ipsi = d + 2 * N;
-    pr.ipsi_s = d + 3 * N;
+    pr.psi2 = d;
+    pr.ipsi2 = d + 2 * N;
   }
   CUDA_TRY(c, cudaMemcpy(c->twiddles.p, host.data(), host.size() * sizeof(u64),
                          cudaMemcpyHostToDevice));
@@ -231,8 +235,8 @@ int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
 int ensure_scratch(cwpir_ctx *c) {
   if (c->jmax) return CWPIR_OK;
   const u64 N = c->N, L = c->L, K = c->K;
-  const u64 per_job = (3 * (L + K) + 3 * L + 2 * L) * N * sizeof(u64);
-  const u64 budget = 2ull << 30;
+  const u64 per_job = (3 * (L + K) + 3 * L + 2 * L + (L + 2) * L) * N * sizeof(u64);
+  const u64 budget = 4ull << 30;
   u64 j = budget / per_job;
   j = std::max<u64>(32, std::min<u64>(1024, j));
   if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
@@ -240,6 +244,7 @@ int ensure_scratch(cwpir_ctx *c) {
   CUDA_TRY(c, c->Tbuf.ensure(j * 3 * (L + K) * N));
   CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
   CUDA_TRY(c, c->CP.ensure(j * 2 * L * N));
+  CUDA_TRY(c, c->DN.ensure(j * (L + 2) * L * N));
   CUDA_TRY(c, c->acc.ensure(2 * L * N));
   if (!c->d_err) {
     CUDA_TRY(c, cudaMalloc(&c->d_err, sizeof(int)));
@@ -403,21 +408,23 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
     return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, jobs, ch.mode, c->rlk.p, c->rlk_s.p,
-                            dbp, c->CP.p, st);
+                            dbp, c->DN.p, c->CP.p, st);
   }));
-  c->stats.kernel_launches += 3;
+  c->stats.kernel_launches += 4;  // tensor, scale, digit NTTs, key multiply-accumulate
   c->stats.mults += ch.count;
   c->stats.ntt_polys += (u64)ch.count * (3 * (c->L + c->K) + c->L * (c->L + 2));
   if (ch.mode == cw::INTERNAL) {
     CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, c->CP.p, jobs, ch.count, st); }));
     CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_p(c->d_tab, c->h, jobs, ch.count, st); }));
-    c->stats.kernel_launches += 2;
+    c->stats.kernel_launches += 3;  // inverse NTT, lift, P-limb NTT
     c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
   } else if (ch.mode == cw::ROOT_PM) {
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.count, c->acc.p, st); }));
+    const u32 groups = cw::relin_pm_groups(c->h, ch.count);
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, groups, c->acc.p, st); }));
     c->stats.kernel_launches += 1;
     c->stats.db_bytes_read += (u64)ch.count * c->L * c->N * sizeof(u64);
   } else {
+    c->stats.kernel_launches += 1;  // inverse NTT
     c->stats.ntt_polys += (u64)ch.count * 2 * c->L;
   }
   return CWPIR_OK;
@@ -451,6 +458,8 @@ int run_expand(cwpir_ctx *c, u32 cfac, u32 m, const u64 *d_query, u64 *out, cuda
   CUDA_TRY(c, c->exp_b.ensure((u64)h_in * B * ctw));
   CUDA_TRY(c, c->exp_tau.ensure((u64)h_in * (B / 2) * ctw));
   CUDA_TRY(c, c->exp_S.ensure((u64)h_in * (B / 2) * ctw));
+  CUDA_TRY(c, c->exp_DN.ensure((u64)h_in * (B / 2) * (c->L + 1) * c->L * c->N));
+  CUDA_TRY(c, c->exp_O.ensure((u64)h_in * (B / 2) * ctw));
   int rc = ensure_subjobs(c, (size_t)h_in * (B / 2) * cfac);
   if (rc) return rc;
   for (u32 j = 0; j < h_in; ++j)
@@ -480,10 +489,10 @@ int run_expand(cwpir_ctx *c, u32 cfac, u32 m, const u64 *d_query, u64 *out, cuda
     CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_automorph(c->d_tab, c->h, jobs, nj, g, c->exp_tau.p, st); }));
     CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] {
       return cw::launch_sub_keyswitch(c->d_tab, c->h, c->exp_tau.p, nj, jobs, key->first->p,
-                                      key->second->p, st);
+                                      key->second->p, c->exp_DN.p, c->exp_O.p, st);
     }));
     CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_expand_combine(c->d_tab, c->h, cur, c->exp_S.p, nxt, h_in, cfac, a, st); }));
-    c->stats.kernel_launches += 3;
+    c->stats.kernel_launches += 5;
     c->stats.substitutions += nj;
     c->stats.ntt_polys += (u64)nj * c->L * (c->L + 3);
     std::swap(cur, nxt);
@@ -862,6 +871,8 @@ int cwpir_substitute(cwpir_ctx *c, uint32_t g, const uint64_t *ct, uint64_t *out
   CUDA_TRY(c, c->io_in.ensure(ctw));
   CUDA_TRY(c, c->io_out.ensure(ctw));
   CUDA_TRY(c, c->exp_tau.ensure(ctw));
+  CUDA_TRY(c, c->exp_DN.ensure((u64)(c->L + 1) * c->L * c->N));
+  CUDA_TRY(c, c->exp_O.ensure(ctw));
   int rc = ensure_subjobs(c, 1);
   if (rc) return rc;
   cw::SubJob sj{c->io_in.p, c->io_out.p};
@@ -869,7 +880,8 @@ int cwpir_substitute(cwpir_ctx *c, uint32_t g, const uint64_t *ct, uint64_t *out
   CUDA_TRY(c, cudaMemcpyAsync(c->d_subjobs, &sj, sizeof sj, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cw::launch_automorph(c->d_tab, c->h, c->d_subjobs, 1, g, c->exp_tau.p, c->stream));
   CUDA_TRY(c, cw::launch_sub_keyswitch(c->d_tab, c->h, c->exp_tau.p, 1, c->d_subjobs,
-                                       key->first->p, key->second->p, c->stream));
+                                       key->first->p, key->second->p, c->exp_DN.p, c->exp_O.p,
+                                       c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return CWPIR_OK;
@@ -977,8 +989,16 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
     case CWPIR_OPT_KERNEL_TIMING: c->opt_timing = value ? 1 : 0; return CWPIR_OK;
     case CWPIR_OPT_MAX_JOBS:
       if (value < 0 || value > 1024) return fail(c, CWPIR_EINVAL, "max jobs must be in [0, 1024]");
-      if (c->jmax) return fail(c, CWPIR_EINVAL, "max jobs must be set before the first answer");
+      cudaSetDevice(c->device);
+      cudaStreamSynchronize(c->stream);
+      cudaDeviceSynchronize();
       c->opt_max_jobs = (u32)value;
+      c->jmax = 0;  // scratch is re-sized on the next call that needs it
+      c->Tbuf.release();
+      c->E.release();
+      c->CP.release();
+      c->DN.release();
+      for (auto &kv : c->dbs) kv.second->plan.reset();
       return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
   }
@@ -1063,13 +1083,13 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   if (!c) return CWPIR_EINVAL;
   c->err.clear();
   if (!d_a || !d_b || !d_out) return fail(c, CWPIR_EINVAL, "null buffer");
-  const u64 LK = c->L + c->K, N = c->N;
+  const u64 LK = c->L + c->K, N = c->N, L = c->L;
   const u64 qp = 2 * LK * N;
-  const u64 need = 2 * qp + 3 * LK * N + 3ull * c->L * N;
+  const u64 need = 2 * qp + 3 * LK * N + 3 * L * N + (L + 2) * L * N + 2 * L * N;
   if (need > kNoAllocWords)
     return fail(c, CWPIR_EINVAL,
-                "N=%u, L=%u needs (17L+7)N = %llu scratch words; the static array holds "
-                "%llu (N = 8192 allows L <= 7, N = 16384 allows L <= 3)",
+                "N=%u, L=%u needs (L^2+21L+7)N = %llu scratch words; the static array holds "
+                "%llu (N = 8192 allows L <= 4, N = 16384 allows L <= 2)",
                 c->N, c->L, (unsigned long long)need, (unsigned long long)kNoAllocWords);
   cudaSetDevice(c->device);
   u64 *base = nullptr;
@@ -1079,6 +1099,7 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   int *err = (int *)base;
   cw::MulJob *job_dev = (cw::MulJob *)(base + 8);
   u64 *qa = base + kNoAllocHeader, *qb = qa + qp, *tb = qb + qp, *eb = tb + 3 * LK * N;
+  u64 *dn = eb + 3 * L * N, *ob = dn + (L + 2) * L * N;
   cw::MulJob job{qa, qb, d_out, 0};
   // the array keeps the previous call's contents: clear the error flag
   CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -1089,7 +1110,7 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
   CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
   CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
-                               c->rlk_s.p, nullptr, nullptr, st));
+                               c->rlk_s.p, nullptr, dn, ob, st));
   int h_err = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));

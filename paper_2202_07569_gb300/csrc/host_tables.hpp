@@ -101,6 +101,8 @@ inline void fill_conv(cw::BaseConv &C, const std::vector<u64> &src, const std::v
     for (u32 j = 0; j < C.ns; ++j) smod = hmul(smod, src[j] % d, d);
     C.smod[k] = smod;
     C.smod_s[k] = shoup_of(smod, d);
+    C.negsmod[k] = smod ? d - smod : 0;
+    C.d_mu[k] = (u64)(((u128)1 << 116) / d);
     for (u32 j = 0; j < C.ns; ++j) {
       u64 hat = 1;
       for (u32 l = 0; l < C.ns; ++l)
@@ -126,18 +128,20 @@ inline void fill_conv(cw::BaseConv &C, const std::vector<u64> &src, const std::v
 }
 
 
-// Forward tables (psi^bitrev(i), Shoup) then inverse (psi^-bitrev(i), Shoup):
-// tw[0..4N).  Returns false if q has no primitive 2N-th root of unity.
+// Forward pairs (psi^bitrev(i), Shoup) at tw[0..2N), inverse pairs
+// (psi^-bitrev(i), Shoup) at tw[2N..4N).  Returns false if q has no
+// primitive 2N-th root of unity.
 inline bool make_twiddles(u64 q, u32 N, u32 logN, u64 *tw) {
   u64 psi = primitive_2n_root(q, N);
   if (!psi) return false;
   u64 ipsi = hinv(psi, q);
   for (u32 i = 0; i < N; ++i) {
     u32 e = bitrev(i, logN);
-    tw[i] = hpow(psi, e, q);
-    tw[N + i] = shoup_of(tw[i], q);
-    tw[2 * N + i] = hpow(ipsi, e, q);
-    tw[3 * N + i] = shoup_of(tw[2 * N + i], q);
+    u64 f = hpow(psi, e, q), b = hpow(ipsi, e, q);
+    tw[2 * i] = f;
+    tw[2 * i + 1] = shoup_of(f, q);
+    tw[2 * N + 2 * i] = b;
+    tw[2 * N + 2 * i + 1] = shoup_of(b, q);
   }
   return true;
 }
@@ -159,11 +163,12 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
     u64 pk = p[k];
     u64 Qm = 1;
     for (u32 j = 0; j < L; ++j) Qm = hmul(Qm, q[j] % pk, pk);
-    S.tqinv[k] = hmul(t % pk, hinv(Qm, pk), pk);
-    S.tqinv_s[k] = shoup_of(S.tqinv[k], pk);
+    const u64 th = S.b2q.theta[k];  // (P/p_k)^-1 mod p_k
+    S.A[k] = hmul(hmul(t % pk, hinv(Qm, pk), pk), th, pk);
+    S.Cr[k] = th;
     for (u32 j = 0; j < L; ++j) {
-      S.qinv[j][k] = hinv(q[j] % pk, pk);
-      S.qinv_s[j][k] = shoup_of(S.qinv[j][k], pk);
+      u64 v = hmul(hinv(q[j] % pk, pk), th, pk);
+      S.B[j][k] = v ? pk - v : 0;
     }
   }
 }

@@ -7,64 +7,120 @@
 //   tensor buffer  Tbuf      [jobs][3][L+K][N] coefficient form of d0, d1, d2
 //   scaled buffer  E         [jobs][3][L][N]   round(t d / Q) mod q_j
 //   partials       P         [jobs][2][L][N]   NTT-form sel * DB rows
-// NTT kernels run one length-N transform per CTA in shared memory with
-// blockDim = N / 16 threads.
+//
+// NTT kernels run one length-N transform per CTA of N/16 threads; each
+// thread holds 16 coefficients in registers (ntt_pass.cuh).  A forward
+// transform takes coefficient t + r N/16 in register r of thread t and
+// leaves NTT-domain value 16t + r there; the inverse goes the other way.
+// NTT-domain arrays are stored permuted (ntt_pos) so that both ends of a
+// transform move through global memory coalesced.
 #include "kernels.cuh"
+#include "ntt_pass.cuh"
 
 namespace cw {
 
 namespace {
 
-__device__ __forceinline__ void smem_ntt_fwd(u64 *s, const NttPrime &P, u32 logN) {
-  const u32 half = 1u << (logN - 1);
-  for (u32 st = 0; st < logN; ++st) {
-    const u32 m = 1u << st, logh = logN - 1 - st;
-    for (u32 b = threadIdx.x; b < half; b += blockDim.x)
-      fwd_bfly(s, b, logh, m, P.psi, P.psi_s, P.q);
-    __syncthreads();
-  }
+template <int LOGN>
+__device__ __forceinline__ u32 strided_idx(u32 t, u32 r) {
+  return t | (r << (LOGN - 4));
+}
+// Storage position of NTT-domain coefficient 16t + r (the value thread t
+// holds in register r after a forward transform): t + r N/16, so that
+// stores after a forward transform and loads before an inverse transform
+// are coalesced.  Every NTT-domain array (database, keys, QP-NTT
+// ciphertexts, digit transforms, accumulators) uses this order; element-wise
+// kernels are indifferent to it and the ABI never exposes it.
+template <int LOGN>
+__device__ __forceinline__ u32 ntt_pos(u32 t, u32 r) {
+  return t | (r << (LOGN - 4));
 }
 
-__device__ __forceinline__ void smem_ntt_inv(u64 *s, const NttPrime &P, u32 logN) {
-  const u32 N = 1u << logN, half = N >> 1;
-  for (u32 st = 0; st < logN; ++st) {
-    const u32 logh = st, m = N >> (st + 1);
-    for (u32 b = threadIdx.x; b < half; b += blockDim.x)
-      inv_bfly(s, b, logh, m, P.ipsi, P.ipsi_s, P.q);
-    __syncthreads();
+// Forward transform: x[r] = coefficient t + r N/16 (< 4q) -> x[r] = NTT
+// value 16t + r, canonical.  Uses s (smem_words(N) words) and all
+// threads of the block; s may be reused after return.
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd(u64 (&x)[16], u64 *s, const NttPrime &P) {
+  constexpr int NP = Passes<LOGN>::count;
+  const u32 t = threadIdx.x;
+  u32 wprev = 0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    u32 lo, c, w;
+    Passes<LOGN>::fwd(p, lo, c, w);
+    if (p > 0) {
+#pragma unroll
+      for (u32 r = 0; r < 16; ++r) s[sidx(pass_idx(t, r, wprev))] = x[r];
+      __syncthreads();
+#pragma unroll
+      for (u32 r = 0; r < 16; ++r) x[r] = s[sidx(pass_idx(t, r, w))];
+      __syncthreads();
+    }
+    fwd_pass<LOGN>(x, t, lo, c, w, P.psi2, P.q);
+    wprev = w;
   }
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) s[c] = shoup(s[c], P.ninv, P.ninv_s, P.q);
-  __syncthreads();
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) x[r] = reduce4(x[r], P.q);
 }
 
-inline dim3 ntt_block(const DevTables &h) { return dim3(h.N / kCoefPerThread); }
-inline size_t ntt_smem(const DevTables &h) { return (size_t)h.N * sizeof(u64); }
+// Inverse transform including the factor N^-1: x[r] = NTT value 16t + r
+// (< 2q) -> x[r] = coefficient t + r N/16, canonical.
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv(u64 (&x)[16], u64 *s, const NttPrime &P) {
+  constexpr int NP = Passes<LOGN>::count;
+  const u32 t = threadIdx.x;
+  u32 wprev = 0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    u32 lo, c, w;
+    Passes<LOGN>::inv(p, lo, c, w);
+    if (p > 0) {
+#pragma unroll
+      for (u32 r = 0; r < 16; ++r) s[sidx(pass_idx(t, r, wprev))] = x[r];
+      __syncthreads();
+#pragma unroll
+      for (u32 r = 0; r < 16; ++r) x[r] = s[sidx(pass_idx(t, r, w))];
+      __syncthreads();
+    }
+    inv_pass<LOGN>(x, t, lo, c, w, P.ipsi2, P.q);
+    wprev = w;
+  }
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) x[r] = shoup(x[r], P.ninv, P.ninv_s, P.q);
+}
+
+inline size_t ntt_smem(const DevTables &h) { return (size_t)smem_words(h.N) * sizeof(u64); }
 
 template <typename F>
 cudaError_t allow_smem(F *kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // ---------------------------------------------------------------------
 // Database load: row r, limb j: centered lift of the payload (v > t/2 ->
 // v - t), zero-padded to N, forward NTT.  grid (L, rows).
 // ---------------------------------------------------------------------
-__global__ void k_db_load(const DevTables *T, const u32 *items, u32 plen, u64 *db) {
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+    k_db_load(const DevTables *T, const u32 *items, u32 plen, u64 *db) {
   extern __shared__ u64 s[];
-  const u32 N = T->N, L = T->L, j = blockIdx.x;
+  constexpr u32 N = 1u << LOGN;
+  const u32 L = T->L, j = blockIdx.x, t = threadIdx.x;
   const u64 row = blockIdx.y;
   const NttPrime P = T->prime[j];
-  const u64 t = T->t;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) {
-    u64 v = c < plen ? (u64)items[row * plen + c] : 0;
-    s[c] = v > t / 2 ? P.q - (t - v) : v;
+  const u64 tt = T->t;
+  u64 x[16];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) {
+    const u32 c = strided_idx<LOGN>(t, r);
+    const u64 v = c < plen ? (u64)items[row * plen + c] : 0;
+    x[r] = v > tt / 2 ? P.q - (tt - v) : v;
   }
-  __syncthreads();
-  smem_ntt_fwd(s, P, T->logN);
+  ntt_fwd<LOGN>(x, s, P);
   u64 *out = db + (row * L + j) * N;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) out[c] = s[c];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -72,33 +128,50 @@ __global__ void k_db_load(const DevTables *T, const u32 *items, u32 plen, u64 *d
 // from src (same limb offset, src_unit_stride) when src != nullptr.
 // grid (limb_end - limb_begin, units).
 // ---------------------------------------------------------------------
-__global__ void k_ntt(const DevTables *T, u64 *base, u64 unit_stride, u32 limb_begin,
-                      int inverse, const u64 *src, u64 src_unit_stride) {
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+    k_ntt(const DevTables *T, u64 *base, u64 unit_stride, u32 limb_begin, int inverse,
+          const u64 *src, u64 src_unit_stride) {
   extern __shared__ u64 s[];
-  const u32 N = T->N, l = limb_begin + blockIdx.x;
+  constexpr u32 N = 1u << LOGN;
+  const u32 l = limb_begin + blockIdx.x, t = threadIdx.x;
   const u64 u = blockIdx.y;
   const NttPrime P = T->prime[l];
   const u64 *in = src ? src + u * src_unit_stride + (u64)l * N : base + u * unit_stride + (u64)l * N;
   u64 *out = base + u * unit_stride + (u64)l * N;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) s[c] = in[c];
-  __syncthreads();
-  if (inverse) smem_ntt_inv(s, P, T->logN);
-  else smem_ntt_fwd(s, P, T->logN);
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) out[c] = s[c];
+  u64 x[16];
+  if (inverse) {
+#pragma unroll
+    for (u32 r = 0; r < 16; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
+    ntt_inv<LOGN>(x, s, P);
+#pragma unroll
+    for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
+  } else {
+#pragma unroll
+    for (u32 r = 0; r < 16; ++r) x[r] = in[strided_idx<LOGN>(t, r)];
+    ntt_fwd<LOGN>(x, s, P);
+#pragma unroll
+    for (u32 r = 0; r < 16; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+  }
 }
 
-// Forward NTT of the P limbs of every job's destination (both polys).
-// grid (K, 2 * njobs).
-__global__ void k_ntt_jobs_p(const DevTables *T, const MulJob *jobs) {
+// Forward NTT of the P limbs of every job's destination (both polys),
+// in place.  grid (K, 2 * njobs).
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+    k_ntt_jobs_p(const DevTables *T, const MulJob *jobs) {
   extern __shared__ u64 s[];
-  const u32 N = T->N, L = T->L, K = T->K, l = L + blockIdx.x;
+  constexpr u32 N = 1u << LOGN;
+  const u32 L = T->L, K = T->K, l = L + blockIdx.x, t = threadIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const NttPrime P = T->prime[l];
   u64 *p = jobs[job].dst + ((u64)poly * (L + K) + l) * N;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) s[c] = p[c];
-  __syncthreads();
-  smem_ntt_fwd(s, P, T->logN);
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) p[c] = s[c];
+  u64 x[16];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
+  ntt_fwd<LOGN>(x, s, P);  // contains barriers: all loads precede all stores
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) p[ntt_pos<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -150,26 +223,32 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // CTA, followed by the inverse NTT: d0 = a0 b0, d1 = a0 b1 + a1 b0,
 // d2 = a1 b1.  grid (L+K, njobs, 3).
 // ---------------------------------------------------------------------
-__global__ void k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+    k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
   extern __shared__ u64 s[];
-  const u32 N = T->N, LK = T->L + T->K, l = blockIdx.x, which = blockIdx.z;
+  constexpr u32 N = 1u << LOGN;
+  const u32 LK = T->L + T->K, l = blockIdx.x, which = blockIdx.z, t = threadIdx.x;
   const u64 job = blockIdx.y;
   const NttPrime P = T->prime[l];
   const MulJob J = jobs[job];
   const u64 ps = (u64)LK * N;
   const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
   const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) {
+  u64 x[16];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) {
+    const u32 c = ntt_pos<LOGN>(t, r);
     u64 v;
     if (which == 0) v = barrett(a0[c], b0[c], P.q, P.mu);
     else if (which == 2) v = barrett(a1[c], b1[c], P.q, P.mu);
     else v = addq(barrett(a0[c], b1[c], P.q, P.mu), barrett(a1[c], b0[c], P.q, P.mu), P.q);
-    s[c] = v;
+    x[r] = v;
   }
-  __syncthreads();
-  smem_ntt_inv(s, P, T->logN);
+  ntt_inv<LOGN>(x, s, P);
   u64 *out = Tbuf + ((job * 3 + which) * LK + l) * N;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) out[c] = s[c];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -194,10 +273,16 @@ __global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err) {
 }
 
 // ---------------------------------------------------------------------
-// Key switching with RNS digits, fused with its consumers.  For job `job`
-// and output limb j: acc0 = NTT(add0_j) + sum_i NTT([z_i]_{q_j}) * b_ij,
-// acc1 = NTT(add1_j) + sum_i NTT([z_i]_{q_j}) * a_ij (digits z_i in
-// [0, q_i) < 2 q_j, so one subtraction reduces them).  grid (L, njobs).
+// Key switching with RNS digits in two kernels.
+//
+// (A) k_ks_ntt: for job `job`, output limb j and unit d: d < L is digit
+//     [z_d]_{q_j} (z_d in [0, q_d) < 2 q_j, one subtraction reduces it),
+//     d = L is add0 (limb j), d = L+1 is add1; forward NTT mod q_j into
+//     DN[job][d][j][N].  grid (L + n_add, L, njobs).
+// (B) element-wise over the NTT domain:
+//     acc0 = DN[L] + sum_i DN[i] * b_ij, acc1 = DN[L+1] + sum_i DN[i] * a_ij,
+//     followed by the consumer (plain multiplication summed over rows, or
+//     the NTT-form result).
 // ---------------------------------------------------------------------
 struct KsArgs {
   const u64 *z;
@@ -206,106 +291,142 @@ struct KsArgs {
   u64 add0_stride;
   const u64 *add1;
   u64 add1_stride;
-  const u64 *key;
-  const u64 *key_s;
-  int mode;  // RootMode, or 3 = substitution output
-  const MulJob *jobs;
-  const SubJob *sjobs;
-  const u64 *db;
-  u64 *out;
+  u32 n_add;
 };
 
-template <int BD>
-__global__ void __launch_bounds__(BD) k_keyswitch(const DevTables *T, KsArgs A) {
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1)) k_ks_ntt(const DevTables *T, KsArgs A,
+                                                             u64 *DN) {
   extern __shared__ u64 s[];
-  const u32 N = T->N, L = T->L, logN = T->logN, bd = blockDim.x, tid = threadIdx.x;
-  const u32 j = blockIdx.x;
-  const u64 job = blockIdx.y;
+  constexpr u32 N = 1u << LOGN;
+  const u32 L = T->L, t = threadIdx.x, d = blockIdx.x, j = blockIdx.y;
+  const u64 job = blockIdx.z;
   const NttPrime P = T->prime[j];
   const u64 q = P.q;
-  u64 acc0[kCoefPerThread], acc1[kCoefPerThread];
+  u64 x[16];
+  if (d < L) {
+    const u64 *zi = A.z + job * A.z_stride + (u64)d * N;
 #pragma unroll
-  for (int r = 0; r < kCoefPerThread; ++r) acc0[r] = acc1[r] = 0;
+    for (u32 r = 0; r < 16; ++r) {
+      const u64 v = zi[strided_idx<LOGN>(t, r)];
+      x[r] = v >= q ? v - q : v;
+    }
+  } else {
+    const u64 *ad = (d == L ? A.add0 + job * A.add0_stride : A.add1 + job * A.add1_stride) +
+                    (u64)j * N;
+#pragma unroll
+    for (u32 r = 0; r < 16; ++r) x[r] = ad[strided_idx<LOGN>(t, r)];
+  }
+  ntt_fwd<LOGN>(x, s, P);
+  u64 *o = DN + ((job * (L + A.n_add) + d) * L + j) * N;
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) o[ntt_pos<LOGN>(t, r)] = x[r];
+}
 
-  const u64 *z = A.z + job * A.z_stride;
-  for (u32 i = 0; i < L; ++i) {
-    const u64 *zi = z + (u64)i * N;
+// acc0/acc1 of one coefficient c of limb j for one job (see (B) above).
+template <int L>
+__device__ __forceinline__ void ks_mac(const u64 *DN, u64 job, u32 n_add, u32 j, u32 c, u32 N,
+                                       const u64 *kb, const u64 *kbs, const u64 *ka,
+                                       const u64 *kas, u64 q, u64 &a0, u64 &a1) {
+  const u64 unit = (u64)L * N;
+  const u64 *base = DN + job * (L + n_add) * unit + (u64)j * N + c;
+  a0 = n_add >= 1 ? base[L * unit] : 0;
+  a1 = n_add >= 2 ? base[(L + 1) * unit] : 0;
 #pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) {
-      u32 c = tid + r * bd;
-      u64 d = zi[c];
-      s[c] = d >= q ? d - q : d;
-    }
-    __syncthreads();
-    smem_ntt_fwd(s, P, logN);
-    const u64 *kb = A.key + ((u64)(i * 2 + 0) * L + j) * N;
-    const u64 *ka = A.key + ((u64)(i * 2 + 1) * L + j) * N;
-    const u64 *kbs = A.key_s + ((u64)(i * 2 + 0) * L + j) * N;
-    const u64 *kas = A.key_s + ((u64)(i * 2 + 1) * L + j) * N;
-#pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) {
-      u32 c = tid + r * bd;
-      u64 v = s[c];
-      acc0[r] = addq(acc0[r], shoup(v, kb[c], kbs[c], q), q);
-      acc1[r] = addq(acc1[r], shoup(v, ka[c], kas[c], q), q);
-    }
-    __syncthreads();
+  for (int i = 0; i < L; ++i) {
+    const u64 v = base[i * unit];
+    a0 = addq(a0, shoup(v, kb[i], kbs[i], q), q);
+    a1 = addq(a1, shoup(v, ka[i], kas[i], q), q);
   }
-  for (int comp = 0; comp < 2; ++comp) {
-    const u64 *add = comp ? A.add1 : A.add0;
-    if (!add) continue;
-    const u64 *ad = add + job * (comp ? A.add1_stride : A.add0_stride) + (u64)j * N;
-#pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) s[tid + r * bd] = ad[tid + r * bd];
-    __syncthreads();
-    smem_ntt_fwd(s, P, logN);
-#pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) {
-      u32 c = tid + r * bd;
-      if (comp) acc1[r] = addq(acc1[r], s[c], q);
-      else acc0[r] = addq(acc0[r], s[c], q);
-    }
-    __syncthreads();
-  }
+}
 
-  if (A.mode == ROOT_PM) {
-    const u64 *dbr = A.db + ((u64)A.jobs[job].row * L + j) * N;
-    u64 *o0 = A.out + (job * 2 + 0) * L * N + (u64)j * N;
-    u64 *o1 = A.out + (job * 2 + 1) * L * N + (u64)j * N;
+// (B) for the answer's last level: sum over the jobs of group g (jobs
+// g, g+G, ...) of (acc0, acc1) * DB[row] -> P[g][2][L][N].
+// grid (N/256, L, G).
+template <int L>
+__global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 njobs,
+                            const MulJob *jobs, const u64 *key, const u64 *key_s,
+                            const u64 *db, u64 *P) {
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  const u32 g = blockIdx.z, G = gridDim.z;
+  const NttPrime Pr = T->prime[j];
+  const u64 q = Pr.q;
+  u64 kb[L], kbs[L], ka[L], kas[L];
 #pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) {
-      u32 c = tid + r * bd;
-      u64 m = dbr[c];
-      o0[c] = barrett(acc0[r], m, q, P.mu);
-      o1[c] = barrett(acc1[r], m, q, P.mu);
-    }
-    return;
+  for (int i = 0; i < L; ++i) {
+    const u64 ob = ((u64)(i * 2 + 0) * L + j) * N + c, oa = ((u64)(i * 2 + 1) * L + j) * N + c;
+    kb[i] = key[ob];
+    kbs[i] = key_s[ob];
+    ka[i] = key[oa];
+    kas[i] = key_s[oa];
   }
-  if (A.mode == INTERNAL) {
-    u64 *d = A.jobs[job].dst;
-    const u64 ps = (u64)(L + T->K) * N;
-#pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) {
-      u32 c = tid + r * bd;
-      d[(u64)j * N + c] = acc0[r];
-      d[ps + (u64)j * N + c] = acc1[r];
-    }
+  u64 sum0 = 0, sum1 = 0;
+  for (u32 job = g; job < njobs; job += G) {
+    u64 a0, a1;
+    ks_mac<L>(DN, job, n_add, j, c, N, kb, kbs, ka, kas, q, a0, a1);
+    const u64 m = db[((u64)jobs[job].row * L + j) * N + c];
+    sum0 = addq(sum0, barrett(a0, m, q, Pr.mu), q);
+    sum1 = addq(sum1, barrett(a1, m, q, Pr.mu), q);
   }
-  // coefficient-form output of both polys
-  u64 *dst;
-  if (A.mode == INTERNAL) dst = A.out + job * 2 * L * N;
-  else if (A.mode == ROOT_SEL) dst = A.jobs[job].dst;
-  else dst = A.sjobs[job].dst;
-  for (int comp = 0; comp < 2; ++comp) {
+  P[((u64)g * 2 * L + j) * N + c] = sum0;
+  P[((u64)(g * 2 + 1) * L + j) * N + c] = sum1;
+}
+
+// (B) producing the NTT-form result: INTERNAL mode writes it to the Q
+// limbs of jobs[job].dst (QP layout), other modes to O[job][2][L][N].
+// grid (N/256, L, njobs).
+template <int L>
+__global__ void k_ks_mac_out(const DevTables *T, const u64 *DN, u32 n_add, const MulJob *jobs,
+                             int internal, const u64 *key, const u64 *key_s, u64 *O) {
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  const u64 job = blockIdx.z;
+  const u64 q = T->prime[j].q;
+  u64 kb[L], kbs[L], ka[L], kas[L];
 #pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) s[tid + r * bd] = comp ? acc1[r] : acc0[r];
-    __syncthreads();
-    smem_ntt_inv(s, P, logN);
-    u64 *o = dst + ((u64)comp * L + j) * N;
-#pragma unroll
-    for (int r = 0; r < kCoefPerThread; ++r) o[tid + r * bd] = s[tid + r * bd];
-    __syncthreads();
+  for (int i = 0; i < L; ++i) {
+    const u64 ob = ((u64)(i * 2 + 0) * L + j) * N + c, oa = ((u64)(i * 2 + 1) * L + j) * N + c;
+    kb[i] = key[ob];
+    kbs[i] = key_s[ob];
+    ka[i] = key[oa];
+    kas[i] = key_s[oa];
   }
+  u64 a0, a1;
+  ks_mac<L>(DN, job, n_add, j, c, N, kb, kbs, ka, kas, q, a0, a1);
+  if (internal) {
+    u64 *d = jobs[job].dst;
+    d[(u64)j * N + c] = a0;
+    d[((u64)(L + T->K) + j) * N + c] = a1;
+  } else {
+    O[(job * 2 + 0) * L * N + (u64)j * N + c] = a0;
+    O[(job * 2 + 1) * L * N + (u64)j * N + c] = a1;
+  }
+}
+
+// Inverse NTT of NTT-form results into coefficient form.  Source: the Q
+// limbs of jobs[job].dst (src_from_jobs, QP layout) or O[job][2][L][N];
+// destination: C[job][2][L][N] (dst_to_jobs = 0), jobs[job].dst (1) or
+// sjobs[job].dst (2), both [2][L][N].  grid (L, 2 * njobs).
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+    k_intt_jobs(const DevTables *T, const MulJob *jobs, const SubJob *sjobs, int src_from_jobs,
+                const u64 *O, int dst_to_jobs, u64 *C) {
+  extern __shared__ u64 s[];
+  constexpr u32 N = 1u << LOGN;
+  const u32 L = T->L, t = threadIdx.x, j = blockIdx.x;
+  const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
+  const NttPrime P = T->prime[j];
+  const u64 *in = src_from_jobs ? jobs[job].dst + ((u64)poly * (L + T->K) + j) * N
+                                : O + (((u64)job * 2 + poly) * L + j) * N;
+  u64 *out;
+  if (dst_to_jobs == 1) out = jobs[job].dst + ((u64)poly * L + j) * N;
+  else if (dst_to_jobs == 2) out = sjobs[job].dst + ((u64)poly * L + j) * N;
+  else out = C + (((u64)job * 2 + poly) * L + j) * N;
+  u64 x[16];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
+  ntt_inv<LOGN>(x, s, P);
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
 
 // k = 1: the selection entry is the leaf itself (Q limbs in NTT form).
@@ -391,44 +512,46 @@ __global__ void k_pm_ntt(const DevTables *T, const u64 *ct, const u64 *dbr, u64 
 // Switching keys [nkeys][L][2][L][N]: forward NTT of every limb (prime =
 // limb index) and the Shoup companion floor(w 2^64 / q) by long division.
 // grid (L, nkeys*2*L).
-__global__ void k_key_prep(const DevTables *T, u64 *key, u64 *key_s) {
+template <int LOGN>
+__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+    k_key_prep(const DevTables *T, u64 *key, u64 *key_s) {
   extern __shared__ u64 s[];
-  const u32 N = T->N, j = blockIdx.x;
+  constexpr u32 N = 1u << LOGN;
+  const u32 j = blockIdx.x, t = threadIdx.x;
   const u64 unit = blockIdx.y;
   const NttPrime P = T->prime[j];
   u64 *p = key + (unit * T->L + j) * N;
   u64 *ps = key_s + (unit * T->L + j) * N;
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) s[c] = p[c];
-  __syncthreads();
-  smem_ntt_fwd(s, P, T->logN);
-  for (u32 c = threadIdx.x; c < N; c += blockDim.x) {
-    u64 w = s[c], rem = w, quo = 0;
+  u64 x[16];
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
+  ntt_fwd<LOGN>(x, s, P);
+#pragma unroll
+  for (u32 r = 0; r < 16; ++r) {
+    u64 w = x[r], rem = w, quo = 0;
     for (int b = 0; b < 64; ++b) {
       rem <<= 1;
-      u64 bit = rem >= P.q ? 1 : 0;
+      const u64 bit = rem >= P.q ? 1 : 0;
       if (bit) rem -= P.q;
       quo = (quo << 1) | bit;
     }
-    p[c] = w;
-    ps[c] = quo;
+    p[ntt_pos<LOGN>(t, r)] = w;
+    ps[ntt_pos<LOGN>(t, r)] = quo;
   }
 }
 
-// blockDim = N / 16: 1024 threads at N = 16384, at most 512 below.
-cudaError_t launch_ks(const DevTables *T, const DevTables &h, const KsArgs &A, u32 njobs,
-                      cudaStream_t st) {
-  cudaError_t e;
-  if (h.N / kCoefPerThread > 512) {
-    e = allow_smem(k_keyswitch<1024>, ntt_smem(h));
-    if (e != cudaSuccess) return e;
-    k_keyswitch<1024><<<dim3(h.L, njobs), ntt_block(h), ntt_smem(h), st>>>(T, A);
-  } else {
-    e = allow_smem(k_keyswitch<512>, ntt_smem(h));
-    if (e != cudaSuccess) return e;
-    k_keyswitch<512><<<dim3(h.L, njobs), ntt_block(h), ntt_smem(h), st>>>(T, A);
+// blockDim = N / 16 for the transform kernels.
+inline dim3 ntt_block(const DevTables &h) { return dim3(h.N / 16); }
+
+#define CW_DISPATCH_LOGN(LOGN_, ...)                       \
+  switch (LOGN_) {                                         \
+    case 10: { constexpr int LG = 10; __VA_ARGS__; } break; \
+    case 11: { constexpr int LG = 11; __VA_ARGS__; } break; \
+    case 12: { constexpr int LG = 12; __VA_ARGS__; } break; \
+    case 13: { constexpr int LG = 13; __VA_ARGS__; } break; \
+    case 14: { constexpr int LG = 14; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;                 \
   }
-  return cudaGetLastError();
-}
 
 }  // namespace
 
@@ -450,13 +573,15 @@ cudaError_t launch_ks(const DevTables *T, const DevTables &h, const KsArgs &A, u
 
 cudaError_t launch_db_load(const DevTables *T, const DevTables &h, const u32 *items, u64 rows,
                            u32 plen, u64 *db, cudaStream_t st) {
-  cudaError_t e = allow_smem(k_db_load, ntt_smem(h));
-  if (e != cudaSuccess) return e;
   const u64 chunk = 32768;
   for (u64 r0 = 0; r0 < rows; r0 += chunk) {
     u64 nr = rows - r0 < chunk ? rows - r0 : chunk;
-    k_db_load<<<dim3(h.L, (u32)nr), ntt_block(h), ntt_smem(h), st>>>(
-        T, items + r0 * plen, plen, db + r0 * h.L * h.N);
+    CW_DISPATCH_LOGN(h.logN, {
+      cudaError_t e = allow_smem(k_db_load<LG>, ntt_smem(h));
+      if (e != cudaSuccess) return e;
+      k_db_load<LG><<<dim3(h.L, (u32)nr), ntt_block(h), ntt_smem(h), st>>>(
+          T, items + r0 * plen, plen, db + r0 * h.L * h.N);
+    });
   }
   return cudaGetLastError();
 }
@@ -465,14 +590,16 @@ cudaError_t launch_ntt(const DevTables *T, const DevTables &h, u64 *base, u32 un
                        u64 unit_stride, u32 limb_begin, u32 limb_end, bool inverse,
                        const u64 *src, u64 src_unit_stride, cudaStream_t st) {
   if (!units || limb_end <= limb_begin) return cudaSuccess;
-  cudaError_t e = allow_smem(k_ntt, ntt_smem(h));
-  if (e != cudaSuccess) return e;
   const u32 chunk = 32768;
   for (u32 u0 = 0; u0 < units; u0 += chunk) {
     u32 nu = units - u0 < chunk ? units - u0 : chunk;
-    k_ntt<<<dim3(limb_end - limb_begin, nu), ntt_block(h), ntt_smem(h), st>>>(
-        T, base + (u64)u0 * unit_stride, unit_stride, limb_begin, inverse ? 1 : 0,
-        src ? src + (u64)u0 * src_unit_stride : nullptr, src_unit_stride);
+    CW_DISPATCH_LOGN(h.logN, {
+      cudaError_t e = allow_smem(k_ntt<LG>, ntt_smem(h));
+      if (e != cudaSuccess) return e;
+      k_ntt<LG><<<dim3(limb_end - limb_begin, nu), ntt_block(h), ntt_smem(h), st>>>(
+          T, base + (u64)u0 * unit_stride, unit_stride, limb_begin, inverse ? 1 : 0,
+          src ? src + (u64)u0 * src_unit_stride : nullptr, src_unit_stride);
+    });
   }
   return cudaGetLastError();
 }
@@ -501,18 +628,23 @@ cudaError_t launch_lift_jobs(const DevTables *T, const DevTables &h, const u64 *
 cudaError_t launch_ntt_jobs_p(const DevTables *T, const DevTables &h, const MulJob *jobs,
                               u32 njobs, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
-  cudaError_t e = allow_smem(k_ntt_jobs_p, ntt_smem(h));
-  if (e != cudaSuccess) return e;
-  k_ntt_jobs_p<<<dim3(h.K, 2 * njobs), ntt_block(h), ntt_smem(h), st>>>(T, jobs);
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_ntt_jobs_p<LG>, ntt_smem(h));
+    if (e != cudaSuccess) return e;
+    k_ntt_jobs_p<LG><<<dim3(h.K, 2 * njobs), ntt_block(h), ntt_smem(h), st>>>(T, jobs);
+  });
   return cudaGetLastError();
 }
 
 cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const MulJob *jobs,
                                u32 njobs, u64 *Tbuf, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
-  cudaError_t e = allow_smem(k_tensor_intt, ntt_smem(h));
-  if (e != cudaSuccess) return e;
-  k_tensor_intt<<<dim3(h.L + h.K, njobs, 3), ntt_block(h), ntt_smem(h), st>>>(T, jobs, Tbuf);
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_tensor_intt<LG>, ntt_smem(h));
+    if (e != cudaSuccess) return e;
+    k_tensor_intt<LG><<<dim3(h.L + h.K, njobs, 3), ntt_block(h), ntt_smem(h), st>>>(T, jobs,
+                                                                                    Tbuf);
+  });
   return cudaGetLastError();
 }
 
@@ -524,9 +656,39 @@ cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf
   return cudaGetLastError();
 }
 
+static cudaError_t launch_ks_ntt(const DevTables *T, const DevTables &h, const KsArgs &A,
+                                 u32 njobs, u64 *DN, cudaStream_t st) {
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_ks_ntt<LG>, ntt_smem(h));
+    if (e != cudaSuccess) return e;
+    k_ks_ntt<LG><<<dim3(h.L + A.n_add, h.L, njobs), ntt_block(h), ntt_smem(h), st>>>(T, A, DN);
+  });
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_intt_jobs(const DevTables *T, const DevTables &h, const MulJob *jobs,
+                                    const SubJob *sjobs, u32 njobs, int src_from_jobs,
+                                    const u64 *O, int dst_to_jobs, u64 *C, cudaStream_t st) {
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_intt_jobs<LG>, ntt_smem(h));
+    if (e != cudaSuccess) return e;
+    k_intt_jobs<LG><<<dim3(h.L, 2 * njobs), ntt_block(h), ntt_smem(h), st>>>(
+        T, jobs, sjobs, src_from_jobs, O, dst_to_jobs, C);
+  });
+  return cudaGetLastError();
+}
+
+u32 pm_groups(const DevTables &h, u32 njobs) {
+  // row groups: about four waves of 2048 threads per SM over the L*N lanes
+  u64 lanes = (u64)h.L * h.N;
+  u64 g = (4 * 152ull * 2048 + lanes - 1) / lanes;
+  g = g < 1 ? 1 : g;
+  return (u32)(g < njobs ? g : njobs);
+}
+
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                          const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
-                         const u64 *db, u64 *out, cudaStream_t st) {
+                         const u64 *db, u64 *DN, u64 *out, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   const u64 LN = (u64)h.L * h.N;
   KsArgs A;
@@ -536,15 +698,25 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
   A.add0_stride = 3 * LN;
   A.add1 = E + LN;
   A.add1_stride = 3 * LN;
-  A.key = rlk;
-  A.key_s = rlk_s;
-  A.mode = mode;
-  A.jobs = jobs;
-  A.sjobs = nullptr;
-  A.db = db;
-  A.out = out;
-  return launch_ks(T, h, A, njobs, st);
+  A.n_add = 2;
+  cudaError_t e = launch_ks_ntt(T, h, A, njobs, DN, st);
+  if (e != cudaSuccess) return e;
+  if (mode == ROOT_PM) {
+    dim3 grid(h.N / 256, h.L, pm_groups(h, njobs));
+    CW_DISPATCH_L(h.L, k_ks_mac_pm, grid, 256, 0, st, T, DN, 2u, njobs, jobs, rlk, rlk_s, db,
+                  out);
+    return cudaGetLastError();
+  }
+  dim3 grid(h.N / 256, h.L, njobs);
+  const int internal = mode == INTERNAL ? 1 : 0;
+  CW_DISPATCH_L(h.L, k_ks_mac_out, grid, 256, 0, st, T, DN, 2u, jobs, internal, rlk, rlk_s, out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (internal) return launch_intt_jobs(T, h, jobs, nullptr, njobs, 1, nullptr, 0, out, st);
+  return launch_intt_jobs(T, h, jobs, nullptr, njobs, 0, out, 1, nullptr, st);
 }
+
+u32 relin_pm_groups(const DevTables &h, u32 njobs) { return pm_groups(h, njobs); }
 
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
                            u32 njobs, const u64 *db, u64 *P, cudaStream_t st) {
@@ -569,7 +741,7 @@ cudaError_t launch_automorph(const DevTables *T, const DevTables &h, const SubJo
 
 cudaError_t launch_sub_keyswitch(const DevTables *T, const DevTables &h, const u64 *tau,
                                  u32 njobs, const SubJob *jobs, const u64 *key,
-                                 const u64 *key_s, cudaStream_t st) {
+                                 const u64 *key_s, u64 *DN, u64 *O, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   const u64 LN = (u64)h.L * h.N;
   KsArgs A;
@@ -579,14 +751,14 @@ cudaError_t launch_sub_keyswitch(const DevTables *T, const DevTables &h, const u
   A.add0_stride = 2 * LN;
   A.add1 = nullptr;
   A.add1_stride = 0;
-  A.key = key;
-  A.key_s = key_s;
-  A.mode = 3;
-  A.jobs = nullptr;
-  A.sjobs = jobs;
-  A.db = nullptr;
-  A.out = nullptr;
-  return launch_ks(T, h, A, njobs, st);
+  A.n_add = 1;
+  cudaError_t e = launch_ks_ntt(T, h, A, njobs, DN, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid(h.N / 256, h.L, njobs);
+  CW_DISPATCH_L(h.L, k_ks_mac_out, grid, 256, 0, st, T, DN, 1u, nullptr, 0, key, key_s, O);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_intt_jobs(T, h, nullptr, jobs, njobs, 0, O, 2, nullptr, st);
 }
 
 cudaError_t launch_expand_combine(const DevTables *T, const DevTables &h, const u64 *cur,
@@ -607,9 +779,12 @@ cudaError_t launch_pm_ntt(const DevTables *T, const DevTables &h, const u64 *ct_
 cudaError_t launch_key_prep(const DevTables *T, const DevTables &h, u64 *key, u64 *key_s,
                             u32 nkeys, cudaStream_t st) {
   if (!nkeys) return cudaSuccess;
-  cudaError_t e = allow_smem(k_key_prep, ntt_smem(h));
-  if (e != cudaSuccess) return e;
-  k_key_prep<<<dim3(h.L, nkeys * 2 * h.L), ntt_block(h), ntt_smem(h), st>>>(T, key, key_s);
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_key_prep<LG>, ntt_smem(h));
+    if (e != cudaSuccess) return e;
+    k_key_prep<LG><<<dim3(h.L, nkeys * 2 * h.L), ntt_block(h), ntt_smem(h), st>>>(T, key,
+                                                                                  key_s);
+  });
   return cudaGetLastError();
 }
 

@@ -37,7 +37,6 @@ enum RootMode : int {
   INTERNAL = 2    // sel -> QP-NTT form at dst (Q limbs here, P limbs later)
 };
 
-constexpr int kCoefPerThread = 16;  // N / blockDim for the NTT kernels
 
 // ---- launchers (kernels.cu); all enqueue on `st` and return the launch
 // error.  Buffers are described in kernels.cu next to each kernel. ----
@@ -57,18 +56,27 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
                                u32 njobs, u64 *Tbuf, cudaStream_t st);
 cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf, u32 njobs,
                          u64 *E, int *err, cudaStream_t st);
+// Relinearisation of the scaled tensor E with its consumer.  DN: scratch
+// [njobs][L+2][L][N].  mode ROOT_PM: out = partials [relin_pm_groups][2][L][N]
+// (sum over row groups of sel * DB); INTERNAL: NTT-form Q limbs to
+// jobs[].dst and coefficient form to out ([njobs][2][L][N]); ROOT_SEL:
+// coefficient form to jobs[].dst, out is scratch [njobs][2][L][N].
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                          const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
-                         const u64 *db, u64 *out, cudaStream_t st);
+                         const u64 *db, u64 *DN, u64 *out, cudaStream_t st);
+u32 relin_pm_groups(const DevTables &h, u32 njobs);
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
                            u32 njobs, const u64 *db, u64 *P, cudaStream_t st);
 cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P,
                               u32 njobs, u64 *acc, cudaStream_t st);
 cudaError_t launch_automorph(const DevTables *T, const DevTables &h, const SubJob *jobs,
                              u32 njobs, u32 g, u64 *tau, cudaStream_t st);
+// Sub_g key switch: tau [njobs][2][L][N] (automorphism images) ->
+// sjobs[].dst = (tau0 + u0, u1) in coefficient form.  DN: scratch
+// [njobs][L+1][L][N]; O: scratch [njobs][2][L][N].
 cudaError_t launch_sub_keyswitch(const DevTables *T, const DevTables &h, const u64 *tau,
                                  u32 njobs, const SubJob *jobs, const u64 *key,
-                                 const u64 *key_s, cudaStream_t st);
+                                 const u64 *key_s, u64 *DN, u64 *O, cudaStream_t st);
 cudaError_t launch_expand_combine(const DevTables *T, const DevTables &h, const u64 *cur,
                                   const u64 *S, u64 *next, u32 h_in, u32 cfac, u32 a,
                                   cudaStream_t st);

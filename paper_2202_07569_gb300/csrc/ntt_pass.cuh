@@ -27,43 +27,73 @@ CW_HD u32 pass_idx(u32 t, u32 r, u32 w) {
   return (t & ((1u << w) - 1)) | (r << w) | ((t >> w) << (w + 4));
 }
 
-// Forward butterflies for bits lo+c-1 .. lo of one thread's 16 values.
+// Shoup product without the final correction: a*w mod q in [0, 2q) for any
+// a < 2^64.
+CW_HD u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) { return a * w - mulhi(a, ws) * q; }
+
+// Forward butterflies (Harvey's lazy Cooley-Tukey) for bits lo+c-1 .. lo of
+// one thread's 16 values: values stay in [0, 4q) (q < 2^54 keeps 4q far
+// below 2^64); U is brought into [0, 2q), V = W x in [0, 2q), outputs
+// U + V and U - V + 2q.
 template <int LOGN>
-CW_HD void fwd_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *psi, const u64 *psi_s,
-                    u64 q) {
+CW_HD void fwd_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *psi2, u64 q) {
+  const u64 q2 = 2 * q;
 #pragma unroll
   for (int bi = 3; bi >= 0; --bi) {
     if ((u32)bi >= c) continue;
     const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
+    // registers r and r | 2^rb pair up; the twiddle depends only on the
+    // bits of r above rb, so each distinct twiddle is loaded once
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) {
-      if (r & (1u << rb)) continue;
-      const u32 g = pass_idx(t, r, w) >> (b + 1);
-      const u64 W = psi[m + g], Ws = psi_s[m + g];
-      const u64 U = x[r], V = shoup(x[r | (1u << rb)], W, Ws, q);
-      x[r] = addq(U, V, q);
-      x[r | (1u << rb)] = subq(U, V, q);
+    for (u32 hv = 0; hv < (16u >> (rb + 1)); ++hv) {
+      const u32 r0 = hv << (rb + 1);
+      const u32 g = pass_idx(t, r0, w) >> (b + 1);
+      const u64 W = psi2[2 * (m + g)], Ws = psi2[2 * (m + g) + 1];
+#pragma unroll
+      for (u32 lv = 0; lv < (1u << rb); ++lv) {
+        const u32 r = r0 | lv;
+        u64 U = x[r];
+        U = U >= q2 ? U - q2 : U;
+        const u64 V = shoup_lazy(x[r | (1u << rb)], W, Ws, q);
+        x[r] = U + V;
+        x[r | (1u << rb)] = U - V + q2;
+      }
     }
   }
 }
 
-// Inverse (Gentleman-Sande) butterflies for bits lo .. lo+c-1.
+// Inverse butterflies (lazy Gentleman-Sande) for bits lo .. lo+c-1: inputs
+// and outputs in [0, 2q); U + V is brought back into [0, 2q), the difference
+// U - V + 2q < 4q goes through a lazy Shoup product.
 template <int LOGN>
-CW_HD void inv_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi, const u64 *ipsi_s,
-                    u64 q) {
+CW_HD void inv_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi2, u64 q) {
+  const u64 q2 = 2 * q;
 #pragma unroll
   for (int bi = 0; bi < 4; ++bi) {
     if ((u32)bi >= c) continue;
     const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) {
-      if (r & (1u << rb)) continue;
-      const u32 g = pass_idx(t, r, w) >> (b + 1);
-      const u64 U = x[r], V = x[r | (1u << rb)];
-      x[r] = addq(U, V, q);
-      x[r | (1u << rb)] = shoup(subq(U, V, q), ipsi[m + g], ipsi_s[m + g], q);
+    for (u32 hv = 0; hv < (16u >> (rb + 1)); ++hv) {
+      const u32 r0 = hv << (rb + 1);
+      const u32 g = pass_idx(t, r0, w) >> (b + 1);
+      const u64 W = ipsi2[2 * (m + g)], Ws = ipsi2[2 * (m + g) + 1];
+#pragma unroll
+      for (u32 lv = 0; lv < (1u << rb); ++lv) {
+        const u32 r = r0 | lv;
+        const u64 U = x[r], V = x[r | (1u << rb)];
+        const u64 S = U + V;
+        x[r] = S >= q2 ? S - q2 : S;
+        x[r | (1u << rb)] = shoup_lazy(U - V + q2, W, Ws, q);
+      }
     }
   }
+}
+
+// [0, 4q) -> [0, q)
+CW_HD u64 reduce4(u64 v, u64 q) {
+  const u64 q2 = 2 * q;
+  v = v >= q2 ? v - q2 : v;
+  return v >= q ? v - q : v;
 }
 
 // Pass schedule: forward passes take bits from the top in chunks of four,
@@ -72,13 +102,13 @@ CW_HD void inv_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi, const 
 template <int LOGN>
 struct Passes {
   static constexpr int count = (LOGN + 3) / 4;
-  CW_HD static void fwd(int p, u32 &lo, u32 &c, u32 &w) {
+  CW_HDM static void fwd(int p, u32 &lo, u32 &c, u32 &w) {
     int hi = LOGN - 4 * p;
     c = hi >= 4 ? 4 : hi;
     lo = hi - c;
     w = lo < LOGN - 4 ? lo : LOGN - 4;
   }
-  CW_HD static void inv(int p, u32 &lo, u32 &c, u32 &w) {
+  CW_HDM static void inv(int p, u32 &lo, u32 &c, u32 &w) {
     lo = 4 * p;
     c = LOGN - (int)lo >= 4 ? 4 : LOGN - lo;
     w = lo < LOGN - 4 ? lo : LOGN - 4;

@@ -16,7 +16,7 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    deps = [SRC] + [os.path.join(CSRC, f) for f in ("arith.cuh", "host_tables.hpp")]
+    deps = [SRC] + [os.path.join(CSRC, f) for f in ("arith.cuh", "host_tables.hpp", "ntt_pass.cuh")]
     if not os.path.exists(SO) or os.path.getmtime(SO) < max(map(os.path.getmtime, deps)):
         os.makedirs(os.path.dirname(SO), exist_ok=True)
         tmp = SO + f".tmp{os.getpid()}"
@@ -36,5 +36,7 @@ def lib():
     l.emu_substitute.restype = None
     l.emu_scale.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p]
     l.emu_scale.restype = C.c_int
+    l.emu_ntt_compare.argtypes = [U32, U32, u64p, U64, u64p]
+    l.emu_ntt_compare.restype = C.c_uint64
     _lib = l
     return l

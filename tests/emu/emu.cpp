@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../paper_2202_07569_gb300/csrc/host_tables.hpp"
+#include "../../paper_2202_07569_gb300/csrc/ntt_pass.cuh"
 
 using namespace cw;
 using namespace cw::host;
@@ -47,12 +48,12 @@ struct Emu {
   void fwd(u64 *a, u32 l) {
     const u64 *w = tw[l].data();
     for (u32 st = 0; st < logN; ++st)
-      for (u32 b = 0; b < N / 2; ++b) fwd_bfly(a, b, logN - 1 - st, 1u << st, w, w + N, all[l]);
+      for (u32 b = 0; b < N / 2; ++b) fwd_bfly(a, b, logN - 1 - st, 1u << st, w, all[l]);
   }
   void inv(u64 *a, u32 l) {
     const u64 *w = tw[l].data();
     for (u32 st = 0; st < logN; ++st)
-      for (u32 b = 0; b < N / 2; ++b) inv_bfly(a, b, st, N >> (st + 1), w + 2 * N, w + 3 * N, all[l]);
+      for (u32 b = 0; b < N / 2; ++b) inv_bfly(a, b, st, N >> (st + 1), w + 2 * N, all[l]);
     for (u32 c = 0; c < N; ++c) a[c] = shoup(a[c], ninv[l], ninv_s[l], all[l]);
   }
   // coefficient ct [2][L][N] -> QP-NTT [2][L+K][N]
@@ -229,5 +230,66 @@ int emu_scale(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint6
               const uint64_t *dp, uint64_t *out) {
   Emu E(N, L, q, t);
   return E.scale(dq, dp, out) ? 1 : 0;
+}
+}
+
+namespace {
+// The register-blocked schedule of the kernels, thread by thread: every
+// pass reads the thread's 16 slots, runs its butterflies, writes them back.
+template <int LOGN>
+void pass_ntt(u64 *a, const u64 *tw, u64 q, bool inverse, u64 ninv, u64 ninv_s) {
+  const u32 N = 1u << LOGN, T = N / 16;
+  std::vector<u64> s(smem_words(N));
+  for (u32 i = 0; i < N; ++i) s[sidx(i)] = a[i];
+  for (int p = 0; p < Passes<LOGN>::count; ++p) {
+    u32 lo, c, w;
+    if (inverse) Passes<LOGN>::inv(p, lo, c, w);
+    else Passes<LOGN>::fwd(p, lo, c, w);
+    for (u32 t = 0; t < T; ++t) {
+      u64 x[16];
+      for (u32 r = 0; r < 16; ++r) x[r] = s[sidx(pass_idx(t, r, w))];
+      if (inverse) inv_pass<LOGN>(x, t, lo, c, w, tw + 2 * N, q);
+      else fwd_pass<LOGN>(x, t, lo, c, w, tw, q);
+      if (p == Passes<LOGN>::count - 1)
+        for (u32 r = 0; r < 16; ++r)
+          x[r] = inverse ? shoup(x[r], ninv, ninv_s, q) : reduce4(x[r], q);
+      for (u32 r = 0; r < 16; ++r) s[sidx(pass_idx(t, r, w))] = x[r];
+    }
+  }
+  for (u32 i = 0; i < N; ++i) a[i] = s[sidx(i)];
+}
+}  // namespace
+
+extern "C" {
+// Runs the pass schedule and the stage-by-stage transform on the same data
+// for every prime of the parameter set; returns the number of mismatches.
+uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
+                         const uint64_t *data) {
+  Emu E(N, L, q, t);
+  uint64_t bad = 0;
+  for (u32 l = 0; l < E.all.size(); ++l) {
+    u64 pr = E.all[l];
+    std::vector<u64> a(N), b(N);
+    for (u32 i = 0; i < N; ++i) a[i] = b[i] = data[i] % pr;
+    E.fwd(a.data(), l);
+    switch (E.logN) {
+      case 10: pass_ntt<10>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
+      case 11: pass_ntt<11>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
+      case 12: pass_ntt<12>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
+      case 13: pass_ntt<13>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
+      default: pass_ntt<14>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
+    }
+    for (u32 i = 0; i < N; ++i) bad += a[i] != b[i];
+    E.inv(a.data(), l);
+    switch (E.logN) {
+      case 10: pass_ntt<10>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
+      case 11: pass_ntt<11>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
+      case 12: pass_ntt<12>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
+      case 13: pass_ntt<13>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
+      default: pass_ntt<14>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
+    }
+    for (u32 i = 0; i < N; ++i) bad += a[i] != b[i] || b[i] != data[i] % pr;
+  }
+  return bad;
 }
 }
