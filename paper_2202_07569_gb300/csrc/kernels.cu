@@ -221,15 +221,16 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // ---------------------------------------------------------------------
 // Tensor of two QP-NTT ciphertexts, one output polynomial and limb per
 // CTA, followed by the inverse NTT: d0 = a0 b0, d1 = a0 b1 + a1 b0,
-// d2 = a1 b1.  grid (L+K, njobs, 3).
+// d2 = a1 b1.  grid (njobs, 3, L+K): the limb varies slowest so that the
+// blocks resident on one SM share one prime's twiddles in L1.
 // ---------------------------------------------------------------------
 template <int LOGN>
 __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
     k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 LK = T->L + T->K, l = blockIdx.x, which = blockIdx.z, t = threadIdx.x;
-  const u64 job = blockIdx.y;
+  const u32 LK = T->L + T->K, l = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
+  const u64 job = blockIdx.x;
   const NttPrime P = T->prime[l];
   const MulJob J = jobs[job];
   const u64 ps = (u64)LK * N;
@@ -299,8 +300,8 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1)) k_ks_nt
                                                              u64 *DN) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 L = T->L, t = threadIdx.x, d = blockIdx.x, j = blockIdx.y;
-  const u64 job = blockIdx.z;
+  const u32 L = T->L, t = threadIdx.x, d = blockIdx.x, j = blockIdx.z;
+  const u64 job = blockIdx.y;
   const NttPrime P = T->prime[j];
   const u64 q = P.q;
   u64 x[16];
@@ -642,7 +643,7 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_tensor_intt<LG>, ntt_smem(h));
     if (e != cudaSuccess) return e;
-    k_tensor_intt<LG><<<dim3(h.L + h.K, njobs, 3), ntt_block(h), ntt_smem(h), st>>>(T, jobs,
+    k_tensor_intt<LG><<<dim3(njobs, 3, h.L + h.K), ntt_block(h), ntt_smem(h), st>>>(T, jobs,
                                                                                     Tbuf);
   });
   return cudaGetLastError();
@@ -661,7 +662,7 @@ static cudaError_t launch_ks_ntt(const DevTables *T, const DevTables &h, const K
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_ks_ntt<LG>, ntt_smem(h));
     if (e != cudaSuccess) return e;
-    k_ks_ntt<LG><<<dim3(h.L + A.n_add, h.L, njobs), ntt_block(h), ntt_smem(h), st>>>(T, A, DN);
+    k_ks_ntt<LG><<<dim3(h.L + A.n_add, njobs, h.L), ntt_block(h), ntt_smem(h), st>>>(T, A, DN);
   });
   return cudaGetLastError();
 }

@@ -27,6 +27,19 @@ CW_HD u32 pass_idx(u32 t, u32 r, u32 w) {
   return (t & ((1u << w) - 1)) | (r << w) | ((t >> w) << (w + 4));
 }
 
+// One (twiddle, Shoup companion) pair: a 16-byte read-only load on the
+// device.
+CW_HD void ld_pair(const u64 *p, u64 &a, u64 &b) {
+#if defined(__CUDA_ARCH__)
+  const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+  a = v.x;
+  b = v.y;
+#else
+  a = p[0];
+  b = p[1];
+#endif
+}
+
 // Shoup product without the final correction: a*w mod q in [0, 2q) for any
 // a < 2^64.
 CW_HD u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) { return a * w - mulhi(a, ws) * q; }
@@ -48,7 +61,8 @@ CW_HD void fwd_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *psi2, u64 q)
     for (u32 hv = 0; hv < (16u >> (rb + 1)); ++hv) {
       const u32 r0 = hv << (rb + 1);
       const u32 g = pass_idx(t, r0, w) >> (b + 1);
-      const u64 W = psi2[2 * (m + g)], Ws = psi2[2 * (m + g) + 1];
+      u64 W, Ws;
+      ld_pair(psi2 + 2 * (m + g), W, Ws);
 #pragma unroll
       for (u32 lv = 0; lv < (1u << rb); ++lv) {
         const u32 r = r0 | lv;
@@ -76,7 +90,8 @@ CW_HD void inv_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi2, u64 q
     for (u32 hv = 0; hv < (16u >> (rb + 1)); ++hv) {
       const u32 r0 = hv << (rb + 1);
       const u32 g = pass_idx(t, r0, w) >> (b + 1);
-      const u64 W = ipsi2[2 * (m + g)], Ws = ipsi2[2 * (m + g) + 1];
+      u64 W, Ws;
+      ld_pair(ipsi2 + 2 * (m + g), W, Ws);
 #pragma unroll
       for (u32 lv = 0; lv < (1u << rb); ++lv) {
         const u32 r = r0 | lv;
