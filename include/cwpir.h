@@ -136,6 +136,31 @@ int cwpir_answer_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                         const uint64_t *d_query, uint64_t *d_response,
                         void *stream);
 
+/* Answer nq queries against one database together (configuration 4 of
+ * the benchmark: batched answering).  Every query is answered exactly as
+ * by cwpir_answer (identical response bits); the queries share each kernel
+ * launch: expansion rounds, first-level products and tree levels of all nq
+ * queries run in the same grids.  queries: [nq][h][2][L][N] (h as for
+ * cwpir_answer, same c for all), responses: [nq][2][L][N].  With
+ * CWPIR_OPT_USE_GRAPH the launch sequence for (database, nq, c) is captured
+ * once into a CUDA graph on the first call and replayed afterwards.
+ * EINVAL also when nq times the tree's widest level exceeds the
+ * multiplications per launch (CWPIR_OPT_MAX_JOBS). */
+int cwpir_answer_batch(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
+                       const uint64_t *queries, uint64_t *responses);
+int cwpir_answer_batch_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
+                              uint32_t nq, const uint64_t *d_queries,
+                              uint64_t *d_responses, void *stream);
+/* Autotuner: times answers of the nq device queries (as for
+ * cwpir_answer_batch_device) for each candidate number of multiplications
+ * per launch in `candidates` (count entries, 0 = automatic), keeps the
+ * fastest on ctx (CWPIR_OPT_MAX_JOBS) and writes it and its time per call
+ * in milliseconds.  d_responses is scratch of [nq][2][L][N]. */
+int cwpir_autotune(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
+                   const uint64_t *d_queries, uint64_t *d_responses,
+                   const int64_t *candidates, uint32_t count, int64_t *best,
+                   double *best_ms);
+
 /* ---- the steps of Process, one at a time (host buffers) ---- */
 /* Homomorphic multiplication M of two ciphertexts with relinearisation. */
 int cwpir_mul(cwpir_ctx *ctx, const uint64_t *a, const uint64_t *b,

@@ -94,6 +94,10 @@ def lib():
             "cwpir_kernel_times": (I, [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "cwpir_kernel_class_name": (C.c_char_p, [I]),
             "cwpir_mul_noalloc": (I, [vp, vp, vp, vp, vp]),
+            "cwpir_answer_batch": (I, [vp, C.c_int32, U32, U32, u64p, u64p]),
+            "cwpir_answer_batch_device": (I, [vp, C.c_int32, U32, U32, vp, vp, vp]),
+            "cwpir_autotune": (I, [vp, C.c_int32, U32, U32, vp, vp, C.POINTER(C.c_int64), U32,
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(l, name)
@@ -204,6 +208,26 @@ class Context:
     def answer_device(self, db: int, query_ptr: int, resp_ptr: int, c: int = 0,
                       stream: int = 0):
         self._check(lib().cwpir_answer_device(self._h, db, c, query_ptr, resp_ptr, stream))
+
+    def answer_batch(self, db: int, queries, c: int = 0) -> np.ndarray:
+        q = _u64(queries)
+        nq = q.shape[0]
+        out = np.zeros((nq,) + self.ct_shape, np.uint64)
+        self._check(lib().cwpir_answer_batch(self._h, db, c, nq, q.reshape(-1), out))
+        return out
+
+    def answer_batch_device(self, db: int, nq: int, queries_ptr: int, resp_ptr: int,
+                            c: int = 0, stream: int = 0):
+        self._check(lib().cwpir_answer_batch_device(self._h, db, c, nq, queries_ptr, resp_ptr,
+                                                    stream))
+
+    def autotune(self, db: int, nq: int, queries_ptr: int, resp_ptr: int, candidates,
+                 c: int = 0):
+        cand = (C.c_int64 * len(candidates))(*candidates)
+        best, ms = C.c_int64(), C.c_double()
+        self._check(lib().cwpir_autotune(self._h, db, c, nq, queries_ptr, resp_ptr, cand,
+                                         len(candidates), C.byref(best), C.byref(ms)))
+        return int(best.value), float(ms.value)
 
     def mul(self, a, b) -> np.ndarray:
         out = np.zeros(self.ct_shape, np.uint64)

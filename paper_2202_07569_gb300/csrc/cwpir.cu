@@ -57,36 +57,56 @@ struct DevBuf {
 };
 
 struct Chunk {
-  u64 off;   // offset into the plan's job array
-  u32 count;
-  int mode;  // cw::RootMode
+  u64 off;    // offset into the plan's job array
+  u32 count;  // jobs in the launch
+  int mode;   // cw::RootMode
+  u32 segs;   // ROOT_PM: queries in the launch, count / segs jobs each
 };
 
+// One expansion round: `count` substitution jobs (all queries) at `off`.
+struct ExpRound {
+  u64 off;
+  u32 count;
+};
+
+// The launch sequence of an answer for nq queries (slots) against one
+// database: leaves, shared first-level products, the batches of tree
+// levels, accumulators, and for compressed queries the expansion rounds.
+// All device job lists are uploaded when the plan is built, so the
+// sequence itself contains only kernel launches and device copies and can
+// be captured into a CUDA graph.
 struct Plan {
-  u32 k = 0, top = 0;
-  bool memo = false;
-  u64 n_memo = 0;
+  u32 nq = 1, cfac = 0, k = 0, top = 0, m = 0, h_in = 0;
+  bool memo = false, leaf_root = false;
+  u64 n_memo = 0, mults = 0;
   std::vector<Chunk> memo_chunks;
-  std::vector<std::vector<Chunk>> batches;  // per batch, levels bottom-up
-  bool leaf_root = false;                   // k == 1
+  std::vector<std::vector<Chunk>> batches;  // per row batch, levels bottom-up
   std::vector<cw::MulJob> host_jobs;
   cw::MulJob *d_jobs = nullptr;
   DevBuf memo_buf, level_buf;
-  u64 mults = 0;
+  DevBuf leaves;     // [nq][m] QP-NTT cts
+  DevBuf acc;        // [nq][2][L][N] NTT-form accumulators
+  DevBuf q_in, resp; // graph staging: [nq][h_in] cts and [nq][2][L][N]
+  DevBuf exp_a, exp_b, exp_tau, exp_S, exp_DN, exp_O, leaves_coef;
+  std::vector<ExpRound> exp_rounds;
+  cw::SubJob *d_subjobs = nullptr;
+  u64 *exp_final = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cwpir_stats graph_stats{};
   ~Plan() {
+    if (graph) cudaGraphExecDestroy(graph);
     if (d_jobs) cudaFree(d_jobs);
+    if (d_subjobs) cudaFree(d_subjobs);
   }
 };
 
 struct Db {
   u64 n = 0;
   u32 plen = 0, k = 0, m = 0;
-  DevBuf db;                   // [n][L][N] NTT form
-  std::vector<uint16_t> cw;    // [n][k]
-  DevBuf leaves;               // [m] QP-NTT cts
-  DevBuf leaves_coef;          // [m] coefficient cts (expansion output)
-  std::unique_ptr<Plan> plan;  // full answer plan (rows 0..n-1)
-  bool plan_memo = false;
+  DevBuf db;                  // [n][L][N] NTT form
+  std::vector<uint16_t> cw;   // [n][k]
+  // answer plans over all rows, by (queries per call, compression factor)
+  std::map<std::pair<u32, u32>, std::unique_ptr<Plan>> plans;
 };
 
 struct cwpir_ctx {
@@ -108,8 +128,8 @@ struct cwpir_ctx {
   cudaStream_t stream = nullptr;
   // scratch
   u32 jmax = 0;
-  DevBuf Tbuf, E, CP, DN, acc, exp_a, exp_b, exp_tau, exp_S, exp_DN, exp_O, tmp_ct, tmp_ct2,
-      io_in, io_out;
+  DevBuf Tbuf, E, CP, DN, exp_tau, exp_DN, exp_O, tmp_ct, io_in, io_out;
+  bool capturing = false;
   int *d_err = nullptr;
   cw::SubJob *d_subjobs = nullptr;
   size_t n_subjobs = 0;
@@ -149,7 +169,7 @@ int fail(cwpir_ctx *ctx, int code, const char *fmt, ...) {
 // with two events on `st` and files the pair under `cls`.
 template <typename F>
 cudaError_t timed(cwpir_ctx *c, int cls, cudaStream_t st, F launch) {
-  if (!c->opt_timing) return launch();
+  if (!c->opt_timing || c->capturing) return launch();
   while (c->ev_pool.size() < c->ev_used + 2) {
     cudaEvent_t e;
     cudaError_t r = cudaEventCreate(&e);
@@ -245,7 +265,6 @@ int ensure_scratch(cwpir_ctx *c) {
   CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
   CUDA_TRY(c, c->CP.ensure(j * 2 * L * N));
   CUDA_TRY(c, c->DN.ensure(j * (L + 2) * L * N));
-  CUDA_TRY(c, c->acc.ensure(2 * L * N));
   if (!c->d_err) {
     CUDA_TRY(c, cudaMalloc(&c->d_err, sizeof(int)));
     CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
@@ -257,27 +276,33 @@ int ensure_scratch(cwpir_ctx *c) {
 // Node (l, r) of a row covers positions [r 2^l, min((r+1) 2^l, k)) of its
 // ascending codeword positions; a node with one position is a leaf and a
 // node whose right half is empty carries its left child up unchanged.
+// Every query slot s has its own leaves, shared pair products and tree
+// levels; the jobs of all slots share launches.
 struct PlanBuilder {
-  cwpir_ctx *c;
   const uint16_t *cw;
-  u32 k;
+  u32 k, m, nq;
+  u64 qp, rows_per_batch = 0;
   const u64 *leaves;
-  u64 qp;
   bool memo;
   std::unordered_map<u32, u64> memo_id;
+  u64 n_memo = 0;
   const u64 *memo_base = nullptr;
   std::vector<u64> level_off;  // offset (cts) of level l inside level_buf
   std::vector<u32> level_nodes;
   u64 *level_base = nullptr;
 
-  const u64 *ptr(u64 row, u64 lr, u32 l, u32 r) {
+  u64 *level_slot(u32 s, u64 lr, u32 l, u32 r) const {
+    return level_base + (level_off[l] + (s * rows_per_batch + lr) * level_nodes[l] + r) * qp;
+  }
+  const u64 *ptr(u32 s, u64 row, u64 lr, u32 l, u32 r) const {
     const uint16_t *pos = cw + row * k;
     u32 lo = r << l, hi = std::min<u32>(lo + (1u << l), k);
-    if (hi - lo == 1) return leaves + pos[lo] * qp;
+    if (hi - lo == 1) return leaves + ((u64)s * m + pos[lo]) * qp;
     u32 mid = lo + (1u << (l - 1));
-    if (mid >= hi) return ptr(row, lr, l - 1, 2 * r);
-    if (l == 1 && memo) return memo_base + memo_id.at(((u32)pos[lo] << 16) | pos[lo + 1]) * qp;
-    return level_base + (level_off[l] + lr * level_nodes[l] + r) * qp;
+    if (mid >= hi) return ptr(s, row, lr, l - 1, 2 * r);
+    if (l == 1 && memo)
+      return memo_base + ((u64)s * n_memo + memo_id.at(((u32)pos[lo] << 16) | pos[lo + 1])) * qp;
+    return level_slot(s, lr, l, r);
   }
 };
 
@@ -287,100 +312,152 @@ u32 ceil_log2(u32 k) {
   return l;
 }
 
-// rows: list of database rows; root_mode ROOT_PM (answer) or ROOT_SEL with
-// sel_out receiving [rows][2][L][N].
-int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, int root_mode, u64 *sel_out,
-               bool memo_opt, std::unique_ptr<Plan> &out) {
+// Buffers and substitution job lists of Alg. Query Expansion for the
+// plan's nq * h_in inputs of 2^c entries each (uploaded once).
+int setup_expand(cwpir_ctx *c, Plan *P) {
+  const u64 ctw = c->ct();
+  const u64 B = 1ull << P->cfac, inputs = (u64)P->nq * P->h_in;
+  CUDA_TRY(c, P->exp_a.ensure(inputs * B * ctw));
+  CUDA_TRY(c, P->exp_b.ensure(inputs * B * ctw));
+  CUDA_TRY(c, P->exp_tau.ensure(inputs * (B / 2) * ctw));
+  CUDA_TRY(c, P->exp_S.ensure(inputs * (B / 2) * ctw));
+  CUDA_TRY(c, P->exp_O.ensure(inputs * (B / 2) * ctw));
+  CUDA_TRY(c, P->exp_DN.ensure(inputs * (B / 2) * (c->L + 1) * c->L * c->N));
+  CUDA_TRY(c, P->leaves_coef.ensure((u64)P->nq * P->m * ctw));
+  std::vector<cw::SubJob> sj;
+  u64 *cur = P->exp_a.p, *nxt = P->exp_b.p;
+  for (u32 a = 0; a < P->cfac; ++a) {
+    P->exp_rounds.push_back(ExpRound{sj.size(), (u32)(inputs << a)});
+    for (u64 ja = 0; ja < inputs; ++ja)
+      for (u64 b = 0; b < (1ull << a); ++b)
+        sj.push_back(cw::SubJob{cur + (ja * B + b) * ctw, P->exp_S.p + ((ja << a) + b) * ctw});
+    std::swap(cur, nxt);
+  }
+  P->exp_final = cur;
+  CUDA_TRY(c, cudaMalloc(&P->d_subjobs, sj.size() * sizeof(cw::SubJob)));
+  CUDA_TRY(c, cudaMemcpy(P->d_subjobs, sj.data(), sj.size() * sizeof(cw::SubJob),
+                         cudaMemcpyHostToDevice));
+  return CWPIR_OK;
+}
+
+// Plan over `rows` for nq query slots with compression factor cfac.
+// root_mode ROOT_PM (answers into the plan's accumulators) or ROOT_SEL
+// (nq = 1; selection entries in coefficient form to sel_out, [rows][2][L][N]).
+int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 cfac,
+               int root_mode, u64 *sel_out, bool memo_opt, std::unique_ptr<Plan> &out) {
   std::unique_ptr<Plan> P(new Plan());
-  const u32 k = db->k;
+  const u32 k = db->k, m = db->m;
+  const u64 qp = c->qp_ct(), ctw = c->ct();
+  P->nq = nq;
+  P->cfac = cfac;
   P->k = k;
+  P->m = m;
   P->top = ceil_log2(k);
   P->memo = memo_opt && P->top >= 2;
-  const u64 qp = c->qp_ct();
-  PlanBuilder B;
-  B.c = c;
-  B.cw = db->cw.data();
-  B.k = k;
-  B.leaves = db->leaves.p;
-  B.qp = qp;
-  B.memo = P->memo;
-  auto &jobs = P->host_jobs;
+  P->h_in = cfac ? (m + (1u << cfac) - 1) >> cfac : m;
   const u32 J = c->jmax;
+  CUDA_TRY(c, P->leaves.ensure((u64)nq * m * qp));
+  CUDA_TRY(c, P->acc.ensure((u64)nq * ctw));
+  CUDA_TRY(c, P->q_in.ensure((u64)nq * P->h_in * ctw));
+  CUDA_TRY(c, P->resp.ensure((u64)nq * ctw));
+
+  if (cfac) {
+    int rc = setup_expand(c, P.get());
+    if (rc) return rc;
+  }
+
+  PlanBuilder Bd;
+  Bd.cw = db->cw.data();
+  Bd.k = k;
+  Bd.m = m;
+  Bd.nq = nq;
+  Bd.qp = qp;
+  Bd.leaves = P->leaves.p;
+  Bd.memo = P->memo;
+  auto &jobs = P->host_jobs;
 
   if (k == 1) {
     P->leaf_root = true;
-    for (u64 x = 0; x < rows.size(); x += J) {
-      u32 cnt = (u32)std::min<u64>(J, rows.size() - x);
-      P->batches.push_back({Chunk{jobs.size(), cnt, cw::ROOT_PM}});
-      for (u32 i = 0; i < cnt; ++i) {
-        u64 row = rows[x + i];
-        cw::MulJob mj{B.leaves + db->cw[row] * qp, nullptr, nullptr, row};
-        jobs.push_back(mj);
-      }
+    const u64 per = std::max<u64>(1, J / nq);
+    for (u64 x = 0; x < rows.size(); x += per) {
+      u32 cnt = (u32)std::min<u64>(per, rows.size() - x);
+      P->batches.push_back({Chunk{jobs.size(), cnt * nq, cw::ROOT_PM, nq}});
+      for (u32 s = 0; s < nq; ++s)
+        for (u32 i = 0; i < cnt; ++i) {
+          u64 row = rows[x + i];
+          jobs.push_back(cw::MulJob{Bd.leaves + ((u64)s * m + db->cw[row]) * qp, nullptr, nullptr, row});
+        }
     }
   } else {
-    // shared first level
     if (P->memo) {
       std::vector<std::pair<u32, u32>> pairs;
       for (u64 row : rows) {
         const uint16_t *pos = db->cw.data() + row * k;
         for (u32 r = 0; 2 * r + 1 < k; ++r) {
           u32 key = ((u32)pos[2 * r] << 16) | pos[2 * r + 1];
-          if (B.memo_id.emplace(key, pairs.size()).second) pairs.push_back({pos[2 * r], pos[2 * r + 1]});
+          if (Bd.memo_id.emplace(key, pairs.size()).second) pairs.push_back({pos[2 * r], pos[2 * r + 1]});
         }
       }
-      P->n_memo = pairs.size();
-      CUDA_TRY(c, P->memo_buf.ensure(std::max<u64>(1, P->n_memo) * qp));
-      B.memo_base = P->memo_buf.p;
-      for (u64 x = 0; x < pairs.size(); x += J) {
-        u32 cnt = (u32)std::min<u64>(J, pairs.size() - x);
-        P->memo_chunks.push_back(Chunk{jobs.size(), cnt, cw::INTERNAL});
-        for (u32 i = 0; i < cnt; ++i) {
-          const auto &pr = pairs[x + i];
-          jobs.push_back(cw::MulJob{B.leaves + pr.first * qp, B.leaves + pr.second * qp,
-                                    P->memo_buf.p + (x + i) * qp, 0});
-        }
+      P->n_memo = Bd.n_memo = pairs.size();
+      CUDA_TRY(c, P->memo_buf.ensure(std::max<u64>(1, (u64)nq * P->n_memo) * qp));
+      Bd.memo_base = P->memo_buf.p;
+      std::vector<cw::MulJob> mj;
+      for (u32 s = 0; s < nq; ++s)
+        for (u64 i = 0; i < pairs.size(); ++i)
+          mj.push_back(cw::MulJob{Bd.leaves + ((u64)s * m + pairs[i].first) * qp,
+                                  Bd.leaves + ((u64)s * m + pairs[i].second) * qp,
+                                  P->memo_buf.p + ((u64)s * P->n_memo + i) * qp, 0});
+      for (u64 x = 0; x < mj.size(); x += J) {
+        u32 cnt = (u32)std::min<u64>(J, mj.size() - x);
+        P->memo_chunks.push_back(Chunk{jobs.size(), cnt, cw::INTERNAL, 1});
+        jobs.insert(jobs.end(), mj.begin() + x, mj.begin() + x + cnt);
       }
-      P->mults += pairs.size();
+      P->mults += mj.size();
     }
     const u32 l0 = P->memo ? 2 : 1;
     u32 max_nodes = 1;
-    B.level_off.assign(P->top + 1, 0);
-    B.level_nodes.assign(P->top + 1, 0);
+    Bd.level_off.assign(P->top + 1, 0);
+    Bd.level_nodes.assign(P->top + 1, 0);
     for (u32 l = l0; l <= P->top; ++l) {
       u32 nodes = (k + (1u << l) - 1) >> l;
-      B.level_nodes[l] = nodes;
+      Bd.level_nodes[l] = nodes;
       max_nodes = std::max(max_nodes, nodes);
     }
-    u64 rows_per_batch = std::max<u64>(1, J / max_nodes);
-    if (c->opt_batch_rows) rows_per_batch = std::min<u64>(rows_per_batch, c->opt_batch_rows);
+    if ((u64)nq * max_nodes > J)
+      return fail(c, CWPIR_EINVAL, "%u queries per call need more than %u multiplications per "
+                  "launch (raise CWPIR_OPT_MAX_JOBS)", nq, J);
+    u64 rpb = std::max<u64>(1, J / ((u64)nq * max_nodes));
+    if (c->opt_batch_rows) rpb = std::min<u64>(rpb, c->opt_batch_rows);
+    Bd.rows_per_batch = rpb;
     u64 lvl_cts = 0;
     for (u32 l = l0; l < P->top; ++l) {
-      B.level_off[l] = lvl_cts;
-      lvl_cts += rows_per_batch * B.level_nodes[l];
+      Bd.level_off[l] = lvl_cts;
+      lvl_cts += (u64)nq * rpb * Bd.level_nodes[l];
     }
     CUDA_TRY(c, P->level_buf.ensure(std::max<u64>(1, lvl_cts) * qp));
-    B.level_base = P->level_buf.p;
-    for (u64 x = 0; x < rows.size(); x += rows_per_batch) {
-      u64 cnt = std::min<u64>(rows_per_batch, rows.size() - x);
+    Bd.level_base = P->level_buf.p;
+    for (u64 x = 0; x < rows.size(); x += rpb) {
+      u64 cnt = std::min<u64>(rpb, rows.size() - x);
       std::vector<Chunk> levels;
       for (u32 l = l0; l <= P->top; ++l) {
-        Chunk ch{jobs.size(), 0, l == P->top ? root_mode : (int)cw::INTERNAL};
-        for (u64 lr = 0; lr < cnt; ++lr) {
-          u64 row = rows[x + lr];
-          for (u32 r = 0; r < B.level_nodes[l]; ++r) {
-            u32 lo = r << l, mid = lo + (1u << (l - 1));
-            if (mid >= std::min<u32>(lo + (1u << l), k)) continue;
-            cw::MulJob mj;
-            mj.a = B.ptr(row, lr, l - 1, 2 * r);
-            mj.b = B.ptr(row, lr, l - 1, 2 * r + 1);
-            mj.row = row;
-            if (l == P->top) mj.dst = sel_out ? sel_out + (x + lr) * c->ct() : nullptr;
-            else mj.dst = B.level_base + (B.level_off[l] + lr * B.level_nodes[l] + r) * qp;
-            jobs.push_back(mj);
-            ++ch.count;
+        const bool root = l == P->top;
+        Chunk ch{jobs.size(), 0, root ? root_mode : (int)cw::INTERNAL, root ? nq : 1};
+        for (u32 s = 0; s < nq; ++s)
+          for (u64 lr = 0; lr < cnt; ++lr) {
+            u64 row = rows[x + lr];
+            for (u32 r = 0; r < Bd.level_nodes[l]; ++r) {
+              u32 lo = r << l, mid = lo + (1u << (l - 1));
+              if (mid >= std::min<u32>(lo + (1u << l), k)) continue;
+              cw::MulJob mj;
+              mj.a = Bd.ptr(s, row, lr, l - 1, 2 * r);
+              mj.b = Bd.ptr(s, row, lr, l - 1, 2 * r + 1);
+              mj.row = row;
+              if (root) mj.dst = sel_out ? sel_out + (x + lr) * ctw : nullptr;
+              else mj.dst = Bd.level_slot(s, lr, l, r);
+              jobs.push_back(mj);
+              ++ch.count;
+            }
           }
-        }
         P->mults += ch.count;
         if (ch.count) levels.push_back(ch);
       }
@@ -400,15 +477,16 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
   const cw::MulJob *jobs = P->d_jobs + ch.off;
   if (P->leaf_root) {
     CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] { return cw::launch_pm_leaf(c->d_tab, c->h, jobs, ch.count, dbp, c->CP.p, st); }));
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.count, c->acc.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, ch.count / ch.segs, P->acc.p, st); }));
     c->stats.kernel_launches += 2;
+    c->stats.db_bytes_read += (u64)ch.count * c->L * c->N * sizeof(u64);
     return CWPIR_OK;
   }
   CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, c->Tbuf.p, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
-    return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, jobs, ch.mode, c->rlk.p, c->rlk_s.p,
-                            dbp, c->DN.p, c->CP.p, st);
+    return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
+                            c->rlk_s.p, dbp, c->DN.p, c->CP.p, st);
   }));
   c->stats.kernel_launches += 4;  // tensor, scale, digit NTTs, key multiply-accumulate
   c->stats.mults += ch.count;
@@ -419,8 +497,9 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
     c->stats.kernel_launches += 3;  // inverse NTT, lift, P-limb NTT
     c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
   } else if (ch.mode == cw::ROOT_PM) {
-    const u32 groups = cw::relin_pm_groups(c->h, ch.count);
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, groups, c->acc.p, st); }));
+    const u32 seg_len = ch.count / ch.segs;
+    const u32 groups = cw::relin_pm_groups(c->h, ch.segs, seg_len);
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, groups, P->acc.p, st); }));
     c->stats.kernel_launches += 1;
     c->stats.db_bytes_read += (u64)ch.count * c->L * c->N * sizeof(u64);
   } else {
@@ -445,60 +524,42 @@ const std::pair<std::shared_ptr<DevBuf>, std::shared_ptr<DevBuf>> *find_gal(cwpi
   return it == c->gal.end() ? nullptr : &it->second;
 }
 
-// Alg. Query Expansion on device: h_in cts (coefficient form, d_query) ->
-// the first m expanded cts in `out` (coefficient form).
-int run_expand(cwpir_ctx *c, u32 cfac, u32 m, const u64 *d_query, u64 *out, cudaStream_t st) {
-  const u32 B = 1u << cfac;
-  const u32 h_in = (m + B - 1) / B;
-  const u64 ctw = c->ct();
+int check_keys(cwpir_ctx *c, u32 cfac) {
   for (u32 a = 0; a < cfac; ++a)
     if (!find_gal(c, c->N / (1u << a) + 1))
       return fail(c, CWPIR_ENOKEY, "no Galois key for element %u", c->N / (1u << a) + 1);
-  CUDA_TRY(c, c->exp_a.ensure((u64)h_in * B * ctw));
-  CUDA_TRY(c, c->exp_b.ensure((u64)h_in * B * ctw));
-  CUDA_TRY(c, c->exp_tau.ensure((u64)h_in * (B / 2) * ctw));
-  CUDA_TRY(c, c->exp_S.ensure((u64)h_in * (B / 2) * ctw));
-  CUDA_TRY(c, c->exp_DN.ensure((u64)h_in * (B / 2) * (c->L + 1) * c->L * c->N));
-  CUDA_TRY(c, c->exp_O.ensure((u64)h_in * (B / 2) * ctw));
-  int rc = ensure_subjobs(c, (size_t)h_in * (B / 2) * cfac);
-  if (rc) return rc;
-  for (u32 j = 0; j < h_in; ++j)
-    CUDA_TRY(c, cudaMemcpyAsync(c->exp_a.p + (u64)j * B * ctw, d_query + (u64)j * ctw,
-                                ctw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
-  // job lists for every round, uploaded together
-  std::vector<cw::SubJob> sj;
-  std::vector<size_t> round_off;
-  u64 *cur = c->exp_a.p, *nxt = c->exp_b.p;
-  for (u32 a = 0; a < cfac; ++a) {
-    round_off.push_back(sj.size());
-    for (u32 j = 0; j < h_in; ++j)
-      for (u32 b = 0; b < (1u << a); ++b)
-        sj.push_back(cw::SubJob{cur + ((u64)j * B + b) * ctw,
-                                c->exp_S.p + ((u64)j * (1u << a) + b) * ctw});
-    std::swap(cur, nxt);
-  }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_subjobs, sj.data(), sj.size() * sizeof(cw::SubJob),
-                              cudaMemcpyHostToDevice, st));
-  cur = c->exp_a.p;
-  nxt = c->exp_b.p;
-  for (u32 a = 0; a < cfac; ++a) {
+  return CWPIR_OK;
+}
+
+// Alg. Query Expansion for the plan's nq * h_in inputs (d_query, [nq][h_in]
+// cts): rounds of substitutions shared by all queries; the first m entries
+// of every query end up in P->leaves_coef ([nq][m] cts).  Capturable.
+int enqueue_expand(cwpir_ctx *c, Plan *P, const u64 *d_query, cudaStream_t st) {
+  const u64 B = 1ull << P->cfac, ctw = c->ct(), inputs = (u64)P->nq * P->h_in;
+  CUDA_TRY(c, cudaMemcpy2DAsync(P->exp_a.p, B * ctw * sizeof(u64), d_query, ctw * sizeof(u64),
+                                ctw * sizeof(u64), inputs, cudaMemcpyDeviceToDevice, st));
+  u64 *cur = P->exp_a.p, *nxt = P->exp_b.p;
+  for (u32 a = 0; a < P->cfac; ++a) {
     const u32 g = c->N / (1u << a) + 1;
-    const u32 nj = h_in << a;
+    const u32 nj = P->exp_rounds[a].count;
     const auto *key = find_gal(c, g);
-    const cw::SubJob *jobs = c->d_subjobs + round_off[a];
-    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_automorph(c->d_tab, c->h, jobs, nj, g, c->exp_tau.p, st); }));
+    const cw::SubJob *jobs = P->d_subjobs + P->exp_rounds[a].off;
+    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_automorph(c->d_tab, c->h, jobs, nj, g, P->exp_tau.p, st); }));
     CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] {
-      return cw::launch_sub_keyswitch(c->d_tab, c->h, c->exp_tau.p, nj, jobs, key->first->p,
-                                      key->second->p, c->exp_DN.p, c->exp_O.p, st);
+      return cw::launch_sub_keyswitch(c->d_tab, c->h, P->exp_tau.p, nj, jobs, key->first->p,
+                                      key->second->p, P->exp_DN.p, P->exp_O.p, st);
     }));
-    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_expand_combine(c->d_tab, c->h, cur, c->exp_S.p, nxt, h_in, cfac, a, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_EXPAND, st, [&] { return cw::launch_expand_combine(c->d_tab, c->h, cur, P->exp_S.p, nxt, (u32)inputs, P->cfac, a, st); }));
     c->stats.kernel_launches += 5;
     c->stats.substitutions += nj;
     c->stats.ntt_polys += (u64)nj * c->L * (c->L + 3);
     std::swap(cur, nxt);
   }
-  // entry j * 2^c + b now encrypts query bit j * 2^c + b: natural order
-  CUDA_TRY(c, cudaMemcpyAsync(out, cur, (u64)m * ctw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+  // entry j * 2^c + b of input j encrypts query bit j * 2^c + b: the first
+  // m entries of each query's h_in * 2^c are its expanded ciphertexts
+  CUDA_TRY(c, cudaMemcpy2DAsync(P->leaves_coef.p, (u64)P->m * ctw * sizeof(u64), P->exp_final,
+                                (u64)P->h_in * B * ctw * sizeof(u64), (u64)P->m * ctw * sizeof(u64),
+                                P->nq, cudaMemcpyDeviceToDevice, st));
   return CWPIR_OK;
 }
 
@@ -533,47 +594,89 @@ Db *get_db(cwpir_ctx *c, int32_t id) {
   return it == c->dbs.end() ? nullptr : it->second.get();
 }
 
-// Expansion (if c > 0) and leaf preparation for a database's code length.
-int prepare_query(cwpir_ctx *c, Db *db, u32 cfac, const u64 *d_query, cudaStream_t st) {
-  const u64 ctw = c->ct();
-  const u64 *coef = d_query;
-  if (cfac > 0) {
-    CUDA_TRY(c, db->leaves_coef.ensure((u64)db->m * ctw));
-    int rc = run_expand(c, cfac, db->m, d_query, db->leaves_coef.p, st);
-    if (rc) return rc;
-    coef = db->leaves_coef.p;
-  }
-  return prep_leaves(c, coef, db->m, db->leaves.p, st);
-}
-
-int answer_enqueue(cwpir_ctx *c, Db *db, u32 cfac, const u64 *d_query, u64 *d_resp,
+// The whole answer of a plan: expansion, leaves, tree, accumulation and the
+// final inverse transform into d_resp ([nq][2][L][N]).  Capturable.
+int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_resp,
                    cudaStream_t st) {
-  c->stats = cwpir_stats{};
-  int rc = ensure_scratch(c);
-  if (rc) return rc;
-  if (!db->plan || db->plan_memo != (c->opt_share != 0)) {
-    std::vector<u64> rows(db->n);
-    for (u64 i = 0; i < db->n; ++i) rows[i] = i;
-    rc = build_plan(c, db, rows, cw::ROOT_PM, nullptr, c->opt_share != 0, db->plan);
-    if (rc) return rc;
-    db->plan_memo = c->opt_share != 0;
+  int rc;
+  const u64 *coef = d_query;
+  if (P->cfac) {
+    if ((rc = enqueue_expand(c, P, d_query, st))) return rc;
+    coef = P->leaves_coef.p;
   }
-  rc = prepare_query(c, db, cfac, d_query, st);
-  if (rc) return rc;
-  Plan *P = db->plan.get();
-  CUDA_TRY(c, cudaMemsetAsync(c->acc.p, 0, 2ull * c->L * c->N * sizeof(u64), st));
+  if ((rc = prep_leaves(c, coef, P->nq * P->m, P->leaves.p, st))) return rc;
+  CUDA_TRY(c, cudaMemsetAsync(P->acc.p, 0, (u64)P->nq * c->ct() * sizeof(u64), st));
   for (const Chunk &ch : P->memo_chunks)
     if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
   for (const auto &batch : P->batches)
     for (const Chunk &ch : batch)
       if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
   CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] {
-    return cw::launch_ntt(c->d_tab, c->h, d_resp, 2, (u64)c->L * c->N, 0, c->L, true, c->acc.p,
-                          (u64)c->L * c->N, st);
+    return cw::launch_ntt(c->d_tab, c->h, d_resp, 2 * P->nq, (u64)c->L * c->N, 0, c->L, true,
+                          P->acc.p, (u64)c->L * c->N, st);
   }));
   c->stats.kernel_launches += 1;
-  c->stats.ntt_polys += 2 * c->L;
-  c->stats.rows = db->n;
+  c->stats.ntt_polys += 2ull * P->nq * c->L;
+  c->stats.rows = db->n * P->nq;
+  return CWPIR_OK;
+}
+
+// The cached all-rows plan of a database for (nq, cfac).
+int get_plan(cwpir_ctx *c, Db *db, u32 nq, u32 cfac, Plan **out) {
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  auto key = std::make_pair(nq, cfac);
+  auto it = db->plans.find(key);
+  if (it == db->plans.end()) {
+    std::vector<u64> rows(db->n);
+    for (u64 i = 0; i < db->n; ++i) rows[i] = i;
+    std::unique_ptr<Plan> P;
+    if ((rc = build_plan(c, db, rows, nq, cfac, cw::ROOT_PM, nullptr, c->opt_share != 0, P)))
+      return rc;
+    it = db->plans.emplace(key, std::move(P)).first;
+  }
+  *out = it->second.get();
+  return CWPIR_OK;
+}
+
+// Answers nq queries (d_query: [nq][h_in] cts) into d_resp ([nq][2][L][N]).
+// With CWPIR_OPT_USE_GRAPH the plan's sequence is captured once into a
+// CUDA graph (on the context's stream) and replayed on `st`, staging the
+// queries and responses through the plan's fixed buffers.
+int answer_batch_enqueue(cwpir_ctx *c, Db *db, u32 cfac, u32 nq, const u64 *d_query,
+                         u64 *d_resp, cudaStream_t st) {
+  Plan *P;
+  int rc = get_plan(c, db, nq, cfac, &P);
+  if (rc) return rc;
+  c->stats = cwpir_stats{};
+  if (!c->opt_graph) return enqueue_answer(c, db, P, d_query, d_resp, st);
+  const u64 ctw = c->ct();
+  if (!P->graph) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaGraph_t g = nullptr;
+    c->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue_answer(c, db, P, P->q_in.p, P->resp.p, c->stream);
+      e = cudaStreamEndCapture(c->stream, &g);
+    }
+    c->capturing = false;
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+      return fail(c, CWPIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    P->graph_stats = c->stats;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(P->q_in.p, d_query, (u64)nq * P->h_in * ctw * sizeof(u64),
+                              cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(c, cudaGraphLaunch(P->graph, st));
+  CUDA_TRY(c, cudaMemcpyAsync(d_resp, P->resp.p, (u64)nq * ctw * sizeof(u64),
+                              cudaMemcpyDeviceToDevice, st));
+  c->stats = P->graph_stats;
   return CWPIR_OK;
 }
 
@@ -749,7 +852,6 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
   db->m = m;
   db->cw.assign(codewords, codewords + n * k);
   CUDA_TRY(c, db->db.ensure(n * c->L * c->N));
-  CUDA_TRY(c, db->leaves.ensure((u64)m * c->qp_ct()));
   // upload rows in chunks and transform
   const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));
   uint32_t *d_items = nullptr;
@@ -792,44 +894,102 @@ static int query_shape(cwpir_ctx *c, Db *db, u32 cfac, u64 *h) {
   return CWPIR_OK;
 }
 
-int cwpir_answer_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *d_query,
-                        uint64_t *d_resp, void *stream) {
+int cwpir_answer_batch_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
+                              const uint64_t *d_queries, uint64_t *d_responses, void *stream) {
   if (!c) return CWPIR_EINVAL;
   c->err.clear();
   cudaSetDevice(c->device);
   Db *db = get_db(c, db_id);
   if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
-  if (!d_query || !d_resp) return fail(c, CWPIR_EINVAL, "null buffer");
+  if (!d_queries || !d_responses || nq == 0) return fail(c, CWPIR_EINVAL, "null buffer or nq = 0");
   u64 h;
   int rc = query_shape(c, db, cfac, &h);
+  if (rc || (rc = check_keys(c, cfac))) return rc;
+  return answer_batch_enqueue(c, db, cfac, nq, d_queries, d_responses, (cudaStream_t)stream);
+}
+
+int cwpir_answer_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *d_query,
+                        uint64_t *d_resp, void *stream) {
+  return cwpir_answer_batch_device(c, db_id, cfac, 1, d_query, d_resp, stream);
+}
+
+int cwpir_answer_batch(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
+                       const uint64_t *queries, uint64_t *responses) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  if (!queries || !responses || nq == 0) return fail(c, CWPIR_EINVAL, "null buffer or nq = 0");
+  u64 h;
+  int rc = query_shape(c, db, cfac, &h);
+  if (rc || (rc = check_keys(c, cfac))) return rc;
+  if (!valid_residues(queries, c->L, c->N, c->q, 2 * h * nq))
+    return fail(c, CWPIR_EINVAL, "query residue out of range");
+  const u64 ctw = c->ct();
+  CUDA_TRY(c, c->io_in.ensure(h * nq * ctw));
+  CUDA_TRY(c, c->io_out.ensure((u64)nq * ctw));
+  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, queries, h * nq * ctw * sizeof(u64),
+                              cudaMemcpyHostToDevice, c->stream));
+  rc = answer_batch_enqueue(c, db, cfac, nq, c->io_in.p, c->io_out.p, c->stream);
   if (rc) return rc;
-  return answer_enqueue(c, db, cfac, d_query, d_resp, (cudaStream_t)stream);
+  CUDA_TRY(c, cudaMemcpyAsync(responses, c->io_out.p, (u64)nq * ctw * sizeof(u64),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_err_flag(c);
 }
 
 int cwpir_answer(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *query,
                  uint64_t *response) {
+  return cwpir_answer_batch(c, db_id, cfac, 1, query, response);
+}
+
+int cwpir_autotune(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
+                   const uint64_t *d_queries, uint64_t *d_responses, const int64_t *cand,
+                   uint32_t count, int64_t *best, double *best_ms) {
   if (!c) return CWPIR_EINVAL;
-  c->err.clear();
+  if (!cand || !count || !best || !best_ms) return fail(c, CWPIR_EINVAL, "null argument");
   cudaSetDevice(c->device);
-  Db *db = get_db(c, db_id);
-  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
-  if (!query || !response) return fail(c, CWPIR_EINVAL, "null buffer");
-  u64 h;
-  int rc = query_shape(c, db, cfac, &h);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  double best_t = 1e300;
+  int64_t best_v = -1;
+  int rc = CWPIR_OK;
+  for (uint32_t i = 0; i < count && rc == CWPIR_OK; ++i) {
+    if ((rc = cwpir_set_option(c, CWPIR_OPT_MAX_JOBS, cand[i]))) break;
+    // first call builds the plan (and the graph when enabled)
+    rc = cwpir_answer_batch_device(c, db_id, cfac, nq, d_queries, d_responses, c->stream);
+    if (rc == CWPIR_EINVAL) {  // this size cannot hold nq queries: skip it
+      rc = CWPIR_OK;
+      continue;
+    }
+    if (rc) break;
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2 && rc == CWPIR_OK; ++r)
+      rc = cwpir_answer_batch_device(c, db_id, cfac, nq, d_queries, d_responses, c->stream);
+    cudaEventRecord(e1, c->stream);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fail(c, CWPIR_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (ms / 2 < best_t) {
+      best_t = ms / 2;
+      best_v = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   if (rc) return rc;
-  if (!valid_residues(query, c->L, c->N, c->q, 2 * h))
-    return fail(c, CWPIR_EINVAL, "query residue out of range");
-  const u64 ctw = c->ct();
-  CUDA_TRY(c, c->io_in.ensure(h * ctw));
-  CUDA_TRY(c, c->io_out.ensure(ctw));
-  CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
-                              c->stream));
-  rc = answer_enqueue(c, db, cfac, c->io_in.p, c->io_out.p, c->stream);
-  if (rc) return rc;
-  CUDA_TRY(c, cudaMemcpyAsync(response, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost,
-                              c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return check_err_flag(c);
+  if (best_v < 0) return fail(c, CWPIR_EINVAL, "no candidate could hold %u queries", nq);
+  if ((rc = cwpir_set_option(c, CWPIR_OPT_MAX_JOBS, best_v))) return rc;
+  *best = best_v;
+  *best_ms = best_t;
+  return CWPIR_OK;
 }
 
 int cwpir_mul(cwpir_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out) {
@@ -853,7 +1013,7 @@ int cwpir_mul(cwpir_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out)
   cw::MulJob job{c->tmp_ct.p, c->tmp_ct.p + qp, c->io_out.p, 0};
   CUDA_TRY(c, cudaMalloc(&P.d_jobs, sizeof job));
   CUDA_TRY(c, cudaMemcpy(P.d_jobs, &job, sizeof job, cudaMemcpyHostToDevice));
-  if ((rc = run_chunk(c, &P, Chunk{0, 1, cw::ROOT_SEL}, nullptr, c->stream))) return rc;
+  if ((rc = run_chunk(c, &P, Chunk{0, 1, cw::ROOT_SEL, 1}, nullptr, c->stream))) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return check_err_flag(c);
@@ -900,10 +1060,17 @@ int cwpir_expand(cwpir_ctx *c, uint32_t cfac, uint32_t m, const uint64_t *query,
   CUDA_TRY(c, c->io_out.ensure((u64)m * ctw));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
                               c->stream));
-  int rc = run_expand(c, cfac, m, c->io_in.p, c->io_out.p, c->stream);
+  int rc = check_keys(c, cfac);
   if (rc) return rc;
-  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, (u64)m * ctw * sizeof(u64), cudaMemcpyDeviceToHost,
-                              c->stream));
+  Plan P;
+  P.nq = 1;
+  P.cfac = cfac;
+  P.m = m;
+  P.h_in = (u32)h;
+  if ((rc = setup_expand(c, &P))) return rc;
+  if ((rc = enqueue_expand(c, &P, c->io_in.p, c->stream))) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(out, P.leaves_coef.p, (u64)m * ctw * sizeof(u64),
+                              cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return CWPIR_OK;
 }
@@ -928,19 +1095,25 @@ int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *
   CUDA_TRY(c, c->io_out.ensure(count * ctw));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
                               c->stream));
-  if ((rc = prepare_query(c, db, cfac, c->io_in.p, c->stream))) return rc;
+  if ((rc = check_keys(c, cfac))) return rc;
+  std::vector<u64> rv(rows, rows + count);
+  std::unique_ptr<Plan> P;
+  if ((rc = build_plan(c, db, rv, 1, cfac, cw::ROOT_SEL, c->io_out.p, c->opt_share != 0, P)))
+    return rc;
+  const u64 *coef = c->io_in.p;
+  if (cfac) {
+    if ((rc = enqueue_expand(c, P.get(), c->io_in.p, c->stream))) return rc;
+    coef = P->leaves_coef.p;
+  }
   if (db->k == 1) {
-    // the selection entry is the expanded query ciphertext itself
-    const u64 *src = cfac ? db->leaves_coef.p : c->io_in.p;
+    // the selection entry is the (expanded) query ciphertext itself
     for (u64 i = 0; i < count; ++i)
-      CUDA_TRY(c, cudaMemcpyAsync(out + i * ctw, src + db->cw[rows[i]] * ctw, ctw * sizeof(u64),
+      CUDA_TRY(c, cudaMemcpyAsync(out + i * ctw, coef + db->cw[rows[i]] * ctw, ctw * sizeof(u64),
                                   cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return CWPIR_OK;
   }
-  std::vector<u64> rv(rows, rows + count);
-  std::unique_ptr<Plan> P;
-  if ((rc = build_plan(c, db, rv, cw::ROOT_SEL, c->io_out.p, c->opt_share != 0, P))) return rc;
+  if ((rc = prep_leaves(c, coef, db->m, P->leaves.p, c->stream))) return rc;
   for (const Chunk &ch : P->memo_chunks)
     if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
   for (const auto &batch : P->batches)
@@ -979,13 +1152,22 @@ int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *c
 int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
   if (!c) return CWPIR_EINVAL;
   switch (option) {
-    case CWPIR_OPT_SHARE_LEVEL1: c->opt_share = value ? 1 : 0; return CWPIR_OK;
+    case CWPIR_OPT_SHARE_LEVEL1:
+      cudaSetDevice(c->device);
+      cudaDeviceSynchronize();
+      c->opt_share = value ? 1 : 0;
+      for (auto &kv : c->dbs) kv.second->plans.clear();
+      return CWPIR_OK;
     case CWPIR_OPT_BATCH_ROWS:
       if (value < 0) return fail(c, CWPIR_EINVAL, "batch rows must be >= 0");
+      cudaSetDevice(c->device);
+      cudaDeviceSynchronize();
       c->opt_batch_rows = (u32)value;
-      for (auto &kv : c->dbs) kv.second->plan.reset();
+      for (auto &kv : c->dbs) kv.second->plans.clear();
       return CWPIR_OK;
-    case CWPIR_OPT_USE_GRAPH: c->opt_graph = value ? 1 : 0; return CWPIR_OK;
+    case CWPIR_OPT_USE_GRAPH:
+      c->opt_graph = value ? 1 : 0;
+      return CWPIR_OK;
     case CWPIR_OPT_KERNEL_TIMING: c->opt_timing = value ? 1 : 0; return CWPIR_OK;
     case CWPIR_OPT_MAX_JOBS:
       if (value < 0 || value > 1024) return fail(c, CWPIR_EINVAL, "max jobs must be in [0, 1024]");
@@ -998,7 +1180,7 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
       c->E.release();
       c->CP.release();
       c->DN.release();
-      for (auto &kv : c->dbs) kv.second->plan.reset();
+      for (auto &kv : c->dbs) kv.second->plans.clear();
       return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
   }
@@ -1109,7 +1291,7 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, qa, 4, LK * N, 0, (u32)LK, false, nullptr, 0, st));
   CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
   CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
-  CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
+  CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
                                c->rlk_s.p, nullptr, dn, ob, st));
   int h_err = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));

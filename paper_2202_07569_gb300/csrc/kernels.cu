@@ -341,15 +341,16 @@ __device__ __forceinline__ void ks_mac(const u64 *DN, u64 job, u32 n_add, u32 j,
   }
 }
 
-// (B) for the answer's last level: sum over the jobs of group g (jobs
-// g, g+G, ...) of (acc0, acc1) * DB[row] -> P[g][2][L][N].
-// grid (N/256, L, G).
+// (B) for the answer's last level.  The launch's jobs form `segs` segments
+// of seg_len consecutive jobs (one segment per query); block z = s*G + g
+// sums (acc0, acc1) * DB[row] over jobs g, g+G, ... of segment s into
+// P[s*G + g][2][L][N].  grid (N/256, L, segs*G).
 template <int L>
-__global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 njobs,
+__global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 seg_len, u32 G,
                             const MulJob *jobs, const u64 *key, const u64 *key_s,
                             const u64 *db, u64 *P) {
   const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  const u32 g = blockIdx.z, G = gridDim.z;
+  const u32 sg = blockIdx.z, seg = sg / G, g = sg % G;
   const NttPrime Pr = T->prime[j];
   const u64 q = Pr.q;
   u64 kb[L], kbs[L], ka[L], kas[L];
@@ -362,15 +363,16 @@ __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 nj
     kas[i] = key_s[oa];
   }
   u64 sum0 = 0, sum1 = 0;
-  for (u32 job = g; job < njobs; job += G) {
+  for (u32 x = g; x < seg_len; x += G) {
+    const u64 job = (u64)seg * seg_len + x;
     u64 a0, a1;
     ks_mac<L>(DN, job, n_add, j, c, N, kb, kbs, ka, kas, q, a0, a1);
     const u64 m = db[((u64)jobs[job].row * L + j) * N + c];
     sum0 = addq(sum0, barrett(a0, m, q, Pr.mu), q);
     sum1 = addq(sum1, barrett(a1, m, q, Pr.mu), q);
   }
-  P[((u64)g * 2 * L + j) * N + c] = sum0;
-  P[((u64)(g * 2 + 1) * L + j) * N + c] = sum1;
+  P[((u64)sg * 2 * L + j) * N + c] = sum0;
+  P[((u64)(sg * 2 + 1) * L + j) * N + c] = sum1;
 }
 
 // (B) producing the NTT-form result: INTERNAL mode writes it to the Q
@@ -444,17 +446,19 @@ __global__ void k_pm_leaf(const DevTables *T, const MulJob *jobs, const u64 *db,
   P[(job * 2 + 1) * L * N + (u64)j * N + c] = barrett(J.a[ps + (u64)j * N + c], m, Pr.q, Pr.mu);
 }
 
-// acc[2][L][N] += sum over jobs of P[job][2][L][N] (mod q_j).
-// grid (N/256, 2L).
-__global__ void k_accumulate(const DevTables *T, const u64 *P, u32 njobs, u64 *acc) {
+// acc[s][2][L][N] += sum over x < per_seg of P[s*per_seg + x][2][L][N]
+// (mod q_j) for every segment s.  grid (N/256, 2L, segs).
+__global__ void k_accumulate(const DevTables *T, const u64 *P, u32 per_seg, u64 *acc) {
   const u32 N = T->N, L = T->L;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
-  const u32 pl = blockIdx.y, j = pl % L;
+  const u32 pl = blockIdx.y, j = pl % L, seg = blockIdx.z;
   const u64 q = T->prime[j].q;
-  const u64 off = (u64)pl * N + c, stride = 2ull * L * N;
-  u64 a = acc[off];
-  for (u32 x = 0; x < njobs; ++x) a = addq(a, P[x * stride + off], q);
-  acc[off] = a;
+  const u64 stride = 2ull * L * N, off = (u64)pl * N + c;
+  const u64 *ps = P + (u64)seg * per_seg * stride;
+  u64 *as = acc + (u64)seg * stride;
+  u64 a = as[off];
+  for (u32 x = 0; x < per_seg; ++x) a = addq(a, ps[x * stride + off], q);
+  as[off] = a;
 }
 
 // tau[job] = (tau_g(c0), tau_g(c1)) of sjobs[job].src, x^i -> x^(i g mod 2N)
@@ -679,16 +683,17 @@ static cudaError_t launch_intt_jobs(const DevTables *T, const DevTables &h, cons
   return cudaGetLastError();
 }
 
-u32 pm_groups(const DevTables &h, u32 njobs) {
-  // row groups: about four waves of 2048 threads per SM over the L*N lanes
-  u64 lanes = (u64)h.L * h.N;
+u32 pm_groups(const DevTables &h, u32 segs, u32 seg_len) {
+  // row groups per segment: about four waves of 2048 threads per SM over
+  // the segs * L * N lanes, at most seg_len
+  u64 lanes = (u64)segs * h.L * h.N;
   u64 g = (4 * 152ull * 2048 + lanes - 1) / lanes;
   g = g < 1 ? 1 : g;
-  return (u32)(g < njobs ? g : njobs);
+  return (u32)(g < seg_len ? g : seg_len);
 }
 
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
-                         const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
+                         u32 segs, const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
                          const u64 *db, u64 *DN, u64 *out, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   const u64 LN = (u64)h.L * h.N;
@@ -703,8 +708,9 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
   cudaError_t e = launch_ks_ntt(T, h, A, njobs, DN, st);
   if (e != cudaSuccess) return e;
   if (mode == ROOT_PM) {
-    dim3 grid(h.N / 256, h.L, pm_groups(h, njobs));
-    CW_DISPATCH_L(h.L, k_ks_mac_pm, grid, 256, 0, st, T, DN, 2u, njobs, jobs, rlk, rlk_s, db,
+    const u32 seg_len = njobs / segs, G = pm_groups(h, segs, seg_len);
+    dim3 grid(h.N / 256, h.L, segs * G);
+    CW_DISPATCH_L(h.L, k_ks_mac_pm, grid, 256, 0, st, T, DN, 2u, seg_len, G, jobs, rlk, rlk_s, db,
                   out);
     return cudaGetLastError();
   }
@@ -717,7 +723,9 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
   return launch_intt_jobs(T, h, jobs, nullptr, njobs, 0, out, 1, nullptr, st);
 }
 
-u32 relin_pm_groups(const DevTables &h, u32 njobs) { return pm_groups(h, njobs); }
+u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len) {
+  return pm_groups(h, segs, seg_len);
+}
 
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
                            u32 njobs, const u64 *db, u64 *P, cudaStream_t st) {
@@ -726,10 +734,10 @@ cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob 
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P, u32 njobs,
-                              u64 *acc, cudaStream_t st) {
-  if (!njobs) return cudaSuccess;
-  k_accumulate<<<dim3(h.N / 256, 2 * h.L), 256, 0, st>>>(T, P, njobs, acc);
+cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P, u32 segs,
+                              u32 per_seg, u64 *acc, cudaStream_t st) {
+  if (!segs || !per_seg) return cudaSuccess;
+  k_accumulate<<<dim3(h.N / 256, 2 * h.L, segs), 256, 0, st>>>(T, P, per_seg, acc);
   return cudaGetLastError();
 }
 

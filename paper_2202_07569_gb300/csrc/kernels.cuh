@@ -57,18 +57,21 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
 cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf, u32 njobs,
                          u64 *E, int *err, cudaStream_t st);
 // Relinearisation of the scaled tensor E with its consumer.  DN: scratch
-// [njobs][L+2][L][N].  mode ROOT_PM: out = partials [relin_pm_groups][2][L][N]
-// (sum over row groups of sel * DB); INTERNAL: NTT-form Q limbs to
-// jobs[].dst and coefficient form to out ([njobs][2][L][N]); ROOT_SEL:
-// coefficient form to jobs[].dst, out is scratch [njobs][2][L][N].
+// [njobs][L+2][L][N].  mode ROOT_PM: the jobs form `segs` equal segments
+// (one per query); out = partials [segs * G][2][L][N] with
+// G = relin_pm_groups(h, segs, njobs / segs) (sums of sel * DB over row
+// groups); INTERNAL: NTT-form Q limbs to jobs[].dst and coefficient form to
+// out ([njobs][2][L][N]); ROOT_SEL: coefficient form to jobs[].dst, out is
+// scratch [njobs][2][L][N].
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
-                         const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
-                         const u64 *db, u64 *DN, u64 *out, cudaStream_t st);
-u32 relin_pm_groups(const DevTables &h, u32 njobs);
+                         u32 segs, const MulJob *jobs, int mode, const u64 *rlk,
+                         const u64 *rlk_s, const u64 *db, u64 *DN, u64 *out, cudaStream_t st);
+u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len);
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
                            u32 njobs, const u64 *db, u64 *P, cudaStream_t st);
-cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P,
-                              u32 njobs, u64 *acc, cudaStream_t st);
+// acc[s] += sum of P[s * per_seg .. (s+1) * per_seg) for s < segs.
+cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P, u32 segs,
+                              u32 per_seg, u64 *acc, cudaStream_t st);
 cudaError_t launch_automorph(const DevTables *T, const DevTables &h, const SubJob *jobs,
                              u32 njobs, u32 g, u64 *tau, cudaStream_t st);
 // Sub_g key switch: tau [njobs][2][L][N] (automorphism images) ->
