@@ -227,9 +227,202 @@ def run_gpu(args, rank: int, world: int, dist):
                        "traffic": None,
                        "peak_basis": f"{SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
                                      f"/ {IMAD_PER_MODMUL} IMAD per 54-bit modmul"}
+    # batched vs plain: 16 queries in one batched call replayed from a CUDA
+    # graph, against the plain one-query calls timed above
+    if args.batch:
+        nq = args.batch
+        qs = np.concatenate([query] * nq)
+        d_qs = torch.from_numpy(qs.view(np.int64)).to(f"cuda:{dev}")
+        d_rs = torch.empty((nq, 2, WL["L"], WL["N"]), dtype=torch.int64, device=f"cuda:{dev}")
+        ctx.set_option(B.OPT_USE_GRAPH, 1)
+        ctx.answer_batch_device(db, nq, d_qs.data_ptr(), d_rs.data_ptr(), 0, stream.cuda_stream)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(2):
+            ctx.answer_batch_device(db, nq, d_qs.data_ptr(), d_rs.data_ptr(), 0, stream.cuda_stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / 2
+        bstats = ctx.last_stats()
+        ctx.set_option(B.OPT_USE_GRAPH, 0)
+        out["batched"] = {
+            "queries_per_call": nq, "ms_per_call": bms, "ms_per_query": bms / nq,
+            "value": world * mb * nq / (bms / 1e3), "unit": "MB/s",
+            "plain_ms_per_query": ms_per_step, "speedup_vs_plain": ms_per_step * nq / bms,
+            "graph": True, "gpu_launches_per_call": int(bstats["kernel_launches"])}
+        del d_qs, d_rs
     ctx.free_db(db)
     ctx.close()
     return out
+
+
+def run_c4(args):
+    """Configuration 4: 64 queries over four resident databases, batched
+    (queries of one database share launches, replayed from CUDA graphs,
+    multiplications per launch picked by the autotuner) against 64
+    sequential one-query answers."""
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+    from paper_2202_07569_gb300 import synthetic as syn
+
+    specs = [  # name, n, k, m, N, L, c, keyword
+        ("n1024_k2", 1024, 2, 46, 8192, 4, 0, False),
+        ("n4096_k2", 4096, 2, 92, 8192, 4, 0, False),
+        ("n16384_k8_keyword", 16384, 8, 64, 16384, 7, 6, True),
+        ("n65536_k4", 65536, 4, 37, 8192, 4, 0, False),
+    ]
+    ctxs = {}
+    for N, L in ((8192, 4), (16384, 7)):
+        q = B.default_primes(N, L)
+        rlk = syn.uniform_residues(syn.Stream(31, N), q, (L, 2), N)
+        gal = {}
+        if N == 16384:
+            for a in range(6):
+                g = N // (1 << a) + 1
+                gal[g] = syn.uniform_residues(syn.Stream(32, g), q, (L, 2), N)
+        ctxs[N] = (B.Context(N, q, 65537, rlk, gal), q)
+    dbs = []
+    for i, (name, n, k, m, N, L, c, kw) in enumerate(specs):
+        ctx, q = ctxs[N]
+        items = syn.payload(syn.Stream(33, i), n, 8192, 1 << 16)
+        ids = (syn.distinct_u32(syn.Stream(34, i), n) if kw else np.arange(n, dtype=np.uint64))
+        cw = np.stack([B.map_perfect(int(x), m, k) for x in ids])
+        db = ctx.load_db(items, cw, m)
+        del items
+        h = m if c == 0 else -(-m // (1 << c))
+        qs = syn.uniform_ciphertexts(35 + i, q, 16 * h, N).reshape(16, h, 2, L, N)
+        d_qs = torch.from_numpy(qs.view(np.int64)).cuda()
+        d_rs = torch.empty((16, 2, L, N), dtype=torch.int64, device="cuda")
+        nq = 4 if N == 16384 else 16  # bounds the per-query first-level products in HBM
+        dbs.append(dict(name=name, ctx=ctx, db=db, c=c, h=h, L=L, N=N, d_qs=d_qs, d_rs=d_rs,
+                        nq=nq, mb=payload_mb(n)))
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    # plain: 64 one-query calls, no graph
+    for d in dbs:
+        d["ctx"].set_option(B.OPT_USE_GRAPH, 0)
+        d["ctx"].answer_device(d["db"], d["d_qs"][0].data_ptr(), d["d_rs"][0].data_ptr(), d["c"],
+                               st.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for d in dbs:
+        for i in range(16):
+            d["ctx"].answer_device(d["db"], d["d_qs"][i].data_ptr(), d["d_rs"][i].data_ptr(),
+                                   d["c"], st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    plain = [t.clone() for t in (d["d_rs"] for d in dbs)]
+    # batched: autotune per database, graphs on
+    tuned = {}
+    for d in dbs:
+        d["ctx"].set_option(B.OPT_USE_GRAPH, 1)
+        best, ms = d["ctx"].autotune(d["db"], d["nq"], d["d_qs"].data_ptr(), d["d_rs"].data_ptr(),
+                                     [256, 512, 0], d["c"])
+        tuned[d["name"]] = {"max_jobs": best, "ms_per_call": ms}
+        for j in range(16 // d["nq"]):  # build and capture
+            d["ctx"].answer_batch_device(d["db"], d["nq"], d["d_qs"][j * d["nq"]].data_ptr(),
+                                         d["d_rs"][j * d["nq"]].data_ptr(), d["c"], st.cuda_stream)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for d in dbs:
+        for j in range(16 // d["nq"]):
+            d["ctx"].answer_batch_device(d["db"], d["nq"], d["d_qs"][j * d["nq"]].data_ptr(),
+                                         d["d_rs"][j * d["nq"]].data_ptr(), d["c"], st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    same = all(bool(torch.equal(a, d["d_rs"])) for a, d in zip(plain, dbs))
+    total_mb = sum(16 * d["mb"] for d in dbs)
+    return {"metric": "batched PIR answer DB MB/s, 64 queries over 4 resident databases",
+            "value": total_mb / (batched_ms / 1e3), "unit": "MB/s",
+            "ms_per_64_queries": batched_ms, "plain_ms_per_64_queries": plain_ms,
+            "plain_value": total_mb / (plain_ms / 1e3), "speedup_vs_plain": plain_ms / batched_ms,
+            "responses_identical_to_plain": same, "autotuned": tuned,
+            "databases": [{k: d[k] for k in ("name", "N", "L", "c", "nq", "mb")} for d in dbs]}
+
+
+def run_c5(args, per_rate: int = 24, rates=(10, 30, 100, 300, 1000, 2000)):
+    """Configuration 5: Poisson arrivals of index and keyword queries (2:1)
+    over three resident databases, served with continuous batching; per
+    offered rate the p50/p99 latency (submission to completion) and the
+    sustained DB MB/s.  Every response is compared with the same query
+    answered alone."""
+    import threading
+
+    from paper_2202_07569_gb300 import binding as B
+    from paper_2202_07569_gb300 import synthetic as syn
+
+    specs = [  # name, n, k, m, N, L, c, keyword
+        ("n65536_k4", 65536, 4, 37, 8192, 4, 0, False),
+        ("n4096_k2", 4096, 2, 92, 8192, 4, 0, False),
+        ("n16384_k8_keyword", 16384, 8, 64, 16384, 7, 6, True),
+    ]
+    ctxs = {}
+    for N, L in ((8192, 4), (16384, 7)):
+        q = B.default_primes(N, L)
+        rlk = syn.uniform_residues(syn.Stream(41, N), q, (L, 2), N)
+        gal = {}
+        if N == 16384:
+            for a in range(6):
+                g = N // (1 << a) + 1
+                gal[g] = syn.uniform_residues(syn.Stream(42, g), q, (L, 2), N)
+        ctxs[N] = (B.Context(N, q, 65537, rlk, gal), q)
+    targets, pools, mbs = [], [], []
+    for i, (name, n, k, m, N, L, c, kw) in enumerate(specs):
+        ctx, q = ctxs[N]
+        items = syn.payload(syn.Stream(43, i), n, 8192, 1 << 16)
+        ids = syn.distinct_u32(syn.Stream(44, i), n) if kw else np.arange(n, dtype=np.uint64)
+        cw = np.stack([B.map_perfect(int(x), m, k) for x in ids])
+        db = ctx.load_db(items, cw, m)
+        del items
+        h = m if c == 0 else -(-m // (1 << c))
+        qs = syn.uniform_ciphertexts(45 + i, q, 4 * h, N).reshape(4, h, 2, L, N)
+        alone = [ctx.answer(db, qs[j], c) for j in range(4)]
+        targets.append((ctx, db, c))
+        pools.append((qs, alone))
+        mbs.append(payload_mb(n))
+    srv = B.Server(targets, max_batch=8, hbm_reserve=8 << 30)
+    mix = [0, 2, 1]  # index : keyword = 2 : 1
+    results = []
+    all_same = True
+    st = syn.Stream(46)
+    for rate in rates:
+        gaps = -np.log((st.below(1 << 53, per_rate).astype(np.float64) + 0.5) / 2.0 ** 53) / rate
+        sent = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(per_rate):
+            t_next += gaps[i]
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tg = mix[i % 3]
+            j = i % 4
+            sent.append((srv.submit(tg, pools[tg][0][j]), tg, j))
+        lat, mb = [], 0.0
+        for tk, tg, j in sent:
+            status, resp, l = srv.wait(tk, tg, timeout=3600)
+            all_same &= status == 1 and bool(np.array_equal(resp, pools[tg][1][j]))
+            lat.append(l)
+            mb += mbs[tg]
+        wall = time.perf_counter() - t0
+        lat.sort()
+        results.append({"offered_qps": rate, "queries": per_rate, "wall_s": wall,
+                        "achieved_qps": per_rate / wall, "db_mb_per_s": mb / wall,
+                        "p50_ms": 1e3 * lat[len(lat) // 2],
+                        "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))]})
+    stats = srv.stats()
+    srv.close()
+    return {"metric": "served PIR: p50/p99 latency and sustained DB MB/s vs offered rate",
+            "value": max(r["db_mb_per_s"] for r in results), "unit": "MB/s",
+            "rates": results, "responses_identical_to_alone": all_same,
+            "server": stats, "max_batch": 8,
+            "databases": [s[0] for s in specs], "mix": "index:keyword = 2:1"}
 
 
 def cpu_baseline(rows_per_step: int | None = None, reps: int = 1):
@@ -262,6 +455,11 @@ def main():
                     help="profiling only: answer over the first ROWS rows instead of 65536")
     ap.add_argument("--max-jobs", type=int, default=0,
                     help="multiplications per kernel launch (0 = library default)")
+    ap.add_argument("--batch", type=int, default=16,
+                    help="queries per batched call in the batched-vs-plain comparison (0: skip)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+                    help="c2: the metric's workload (default); c4: batched answering over "
+                         "four databases")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -308,6 +506,11 @@ def main():
         cuda_build.build()
     if dist:
         dist.barrier()
+    if args.workload in ("c4", "c5"):
+        if rank == 0:
+            fn = run_c4 if args.workload == "c4" else run_c5
+            print(json.dumps(dict(fn(args), data="synthetic", n_gpus=1)), flush=True)
+        return
     res = run_gpu(args, rank, world, dist)
     if rank != 0:
         return

@@ -161,6 +161,16 @@ int cwpir_autotune(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
                    const int64_t *candidates, uint32_t count, int64_t *best,
                    double *best_ms);
 
+/* Device memory (bytes, an upper estimate) that the first
+ * cwpir_answer_batch(_device) call for (db_id, nq, c) would allocate for
+ * its plan and, if not yet allocated, the context's scratch; 0 when the
+ * plan is cached.  Used for admission by free device memory. */
+int cwpir_plan_bytes(cwpir_ctx *ctx, int32_t db_id, uint32_t nq, uint32_t c,
+                     uint64_t *bytes);
+/* Frees the cached plans (and graphs) of one database, or of all databases
+ * of ctx when db_id < 0; waits for the device first. */
+int cwpir_release_plans(cwpir_ctx *ctx, int32_t db_id);
+
 /* ---- the steps of Process, one at a time (host buffers) ---- */
 /* Homomorphic multiplication M of two ciphertexts with relinearisation. */
 int cwpir_mul(cwpir_ctx *ctx, const uint64_t *a, const uint64_t *b,
@@ -223,6 +233,55 @@ int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
  * set-up context (it supplies the tables and the relinearisation key). */
 int cwpir_mul_noalloc(cwpir_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b,
                       uint64_t *d_out, void *stream);
+
+/* Shape of a loaded database: ring degree, number of primes, code length. */
+int cwpir_db_shape(const cwpir_ctx *ctx, int32_t db_id, uint32_t *N, uint32_t *L,
+                   uint32_t *m);
+/* CUDA device of the context. */
+int cwpir_ctx_device(const cwpir_ctx *ctx, int *device);
+
+/* ---- online serving (configuration 5 of the benchmark) ---- */
+/* A server answers queries for registered targets (a context, one of its
+ * databases, and the compression factor c of that target's queries).  One
+ * worker thread per distinct context ("lane") takes, whenever it is free,
+ * the waiting requests of its target with the oldest request, up to the
+ * largest power of two <= max_batch whose answer plan fits in free device
+ * memory minus hbm_reserve_bytes (cached plans of the context are released
+ * when nothing fits), and answers them with one cwpir_answer_batch_device
+ * call replayed from a CUDA graph; requests arriving meanwhile wait for the
+ * next batch (continuous batching).  Lanes of different contexts run
+ * concurrently on their own streams.  Each response is bit-identical to
+ * cwpir_answer for the same query.  While a server runs, its contexts must
+ * not be used by other threads.  Requests beyond max_pending waiting or
+ * running are refused with EBUSY. */
+typedef struct cwpir_server cwpir_server;
+typedef struct {
+  cwpir_ctx *ctx;
+  int32_t db_id;
+  uint32_t c;
+} cwpir_target;
+typedef struct {
+  uint64_t submitted, completed, batches, max_batch_seen, rejected_busy;
+  double busy_s; /* summed wall time of the lanes' batches */
+} cwpir_server_stats;
+int cwpir_server_create(const cwpir_target *targets, uint32_t n_targets,
+                        uint32_t max_batch, uint64_t hbm_reserve_bytes,
+                        uint32_t max_pending, cwpir_server **out);
+/* Queues one query ([h][2][L][N] host memory, copied) for a target;
+ * *ticket identifies it.  Non-blocking; EBUSY when max_pending is reached. */
+int cwpir_submit(cwpir_server *srv, uint32_t target, const uint64_t *query,
+                 uint64_t *ticket);
+/* Non-blocking: *status = 0 while waiting or running; when done, 1 (the
+ * response [2][L][N] is written, latency_s = completion - submission) or
+ * a negative error code; a finished ticket is forgotten after it is read. */
+int cwpir_poll(cwpir_server *srv, uint64_t ticket, uint64_t *response,
+               int32_t *status, double *latency_s);
+/* Blocking variant of cwpir_poll; ETIMEDOUT after timeout_s seconds. */
+int cwpir_wait(cwpir_server *srv, uint64_t ticket, uint64_t *response,
+               int32_t *status, double *latency_s, double timeout_s);
+int cwpir_server_get_stats(cwpir_server *srv, cwpir_server_stats *out);
+/* Finishes the waiting requests, stops the lanes and frees the server. */
+void cwpir_server_destroy(cwpir_server *srv);
 
 /* Work counters of the last answer on ctx (for throughput accounting). */
 typedef struct {

@@ -45,6 +45,20 @@ class _Keys(C.Structure):
                 ("galois_elts", C.POINTER(C.c_uint32)), ("galois", C.POINTER(C.c_uint64))]
 
 
+class _Target(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("db_id", C.c_int32), ("c", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
+                ("max_batch_seen", C.c_uint64), ("rejected_busy", C.c_uint64),
+                ("busy_s", C.c_double)]
+
+    def as_dict(self):
+        return {f: (float(getattr(self, f)) if f == "busy_s" else int(getattr(self, f)))
+                for f, _ in self._fields_}
+
+
 class Stats(C.Structure):
     _fields_ = [("rows", C.c_uint64), ("mults", C.c_uint64), ("substitutions", C.c_uint64),
                 ("ntt_polys", C.c_uint64), ("kernel_launches", C.c_uint64),
@@ -94,6 +108,19 @@ def lib():
             "cwpir_kernel_times": (I, [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "cwpir_kernel_class_name": (C.c_char_p, [I]),
             "cwpir_mul_noalloc": (I, [vp, vp, vp, vp, vp]),
+            "cwpir_plan_bytes": (I, [vp, C.c_int32, U32, U32, C.POINTER(U64)]),
+            "cwpir_release_plans": (I, [vp, C.c_int32]),
+            "cwpir_db_shape": (I, [vp, C.c_int32, C.POINTER(U32), C.POINTER(U32),
+                                   C.POINTER(U32)]),
+            "cwpir_ctx_device": (I, [vp, C.POINTER(C.c_int)]),
+            "cwpir_server_create": (I, [C.POINTER(_Target), U32, U32, U64, U32,
+                                        C.POINTER(vp)]),
+            "cwpir_submit": (I, [vp, U32, u64p, C.POINTER(U64)]),
+            "cwpir_poll": (I, [vp, U64, u64p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+            "cwpir_wait": (I, [vp, U64, u64p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                               C.c_double]),
+            "cwpir_server_get_stats": (I, [vp, C.POINTER(ServerStats)]),
+            "cwpir_server_destroy": (None, [vp]),
             "cwpir_answer_batch": (I, [vp, C.c_int32, U32, U32, u64p, u64p]),
             "cwpir_answer_batch_device": (I, [vp, C.c_int32, U32, U32, vp, vp, vp]),
             "cwpir_autotune": (I, [vp, C.c_int32, U32, U32, vp, vp, C.POINTER(C.c_int64), U32,
@@ -274,3 +301,66 @@ class Context:
         self._check(lib().cwpir_kernel_times(self._h, ms, n))
         return {lib().cwpir_kernel_class_name(i).decode(): (ms[i], int(n[i]))
                 for i in range(K_CLASSES)}
+
+
+class Server:
+    """cwpir_server: continuous batching over registered (context, database,
+    c) targets."""
+
+    def __init__(self, targets, max_batch: int = 16, hbm_reserve: int = 1 << 30,
+                 max_pending: int = 4096):
+        arr = (_Target * len(targets))()
+        self._shapes = []
+        for i, (ctx, db, c) in enumerate(targets):
+            arr[i] = _Target(ctx._h, db, c)
+            self._shapes.append((ctx.L, ctx.N))
+        h = C.c_void_p()
+        rc = lib().cwpir_server_create(arr, len(targets), max_batch, hbm_reserve, max_pending,
+                                       C.byref(h))
+        if rc:
+            raise CwpirError(rc, "server create")
+        self._h = h
+        self._ctxs = [t[0] for t in targets]  # keep contexts alive
+
+    def submit(self, target: int, query) -> int:
+        t = C.c_uint64()
+        rc = lib().cwpir_submit(self._h, target, _u64(query).reshape(-1), C.byref(t))
+        if rc:
+            raise CwpirError(rc, "submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, target: int):
+        """(status, response or None, latency seconds)."""
+        L, N = self._shapes[target]
+        out = np.zeros((2, L, N), np.uint64)
+        st, lat = C.c_int32(), C.c_double()
+        rc = lib().cwpir_poll(self._h, ticket, out.reshape(-1), C.byref(st), C.byref(lat))
+        if rc:
+            raise CwpirError(rc, "poll")
+        return int(st.value), (out if st.value == 1 else None), float(lat.value)
+
+    def wait(self, ticket: int, target: int, timeout: float = 600.0):
+        L, N = self._shapes[target]
+        out = np.zeros((2, L, N), np.uint64)
+        st, lat = C.c_int32(), C.c_double()
+        rc = lib().cwpir_wait(self._h, ticket, out.reshape(-1), C.byref(st), C.byref(lat),
+                              timeout)
+        if rc:
+            raise CwpirError(rc, "wait")
+        return int(st.value), (out if st.value == 1 else None), float(lat.value)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        lib().cwpir_server_get_stats(self._h, C.byref(s))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cwpir_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

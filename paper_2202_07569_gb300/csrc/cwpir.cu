@@ -101,7 +101,7 @@ struct Plan {
 };
 
 struct Db {
-  u64 n = 0;
+  u64 n = 0, n_pairs = 0;  // rows, distinct first-level position pairs
   u32 plen = 0, k = 0, m = 0;
   DevBuf db;                  // [n][L][N] NTT form
   std::vector<uint16_t> cw;   // [n][k]
@@ -851,6 +851,13 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
   db->k = k;
   db->m = m;
   db->cw.assign(codewords, codewords + n * k);
+  {
+    std::unordered_map<u32, char> seen;
+    for (u64 i = 0; i < n; ++i)
+      for (u32 r = 0; 2 * r + 1 < k; ++r)
+        seen.emplace(((u32)codewords[i * k + 2 * r] << 16) | codewords[i * k + 2 * r + 1], 0);
+    db->n_pairs = seen.size();
+  }
   CUDA_TRY(c, db->db.ensure(n * c->L * c->N));
   // upload rows in chunks and transform
   const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));
@@ -1146,6 +1153,77 @@ int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *c
                              c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return CWPIR_OK;
+}
+
+int cwpir_db_shape(const cwpir_ctx *c, int32_t db_id, uint32_t *N, uint32_t *L, uint32_t *m) {
+  if (!c || !N || !L || !m) return CWPIR_EINVAL;
+  auto it = c->dbs.find(db_id);
+  if (it == c->dbs.end()) return CWPIR_ENODB;
+  *N = c->N;
+  *L = c->L;
+  *m = it->second->m;
+  return CWPIR_OK;
+}
+
+int cwpir_ctx_device(const cwpir_ctx *c, int *device) {
+  if (!c || !device) return CWPIR_EINVAL;
+  *device = c->device;
+  return CWPIR_OK;
+}
+
+int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
+                     uint64_t *bytes) {
+  if (!c || !bytes || !nq) return CWPIR_EINVAL;
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  if (db->plans.count(std::make_pair(nq, cfac))) {
+    *bytes = 0;
+    return CWPIR_OK;
+  }
+  const u64 N = c->N, L = c->L, K = c->K, qp = c->qp_ct(), ctw = c->ct();
+  u64 w = 0;
+  if (!c->jmax) {  // the context's scratch comes first
+    const u64 per_job = (3 * (L + K) + 3 * L + 2 * L + (L + 2) * L) * N;
+    u64 j = std::max<u64>(32, std::min<u64>(1024, (4ull << 30) / (per_job * 8)));
+    if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
+    w += j * per_job;
+  }
+  const u64 J = c->jmax ? c->jmax : 1024;
+  const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();
+  const bool memo = c->opt_share && top >= 2;
+  const u64 h = cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
+  w += (u64)nq * db->m * qp + 2ull * nq * ctw + (u64)nq * h * ctw;
+  if (memo) w += (u64)nq * db->n_pairs * qp;
+  u64 widest = 1, internal_nodes = 0;
+  for (u32 l = memo ? 2 : 1; l <= top; ++l) {
+    u64 nodes = (db->k + (1u << l) - 1) >> l;
+    widest = std::max(widest, nodes);
+    if (l < top) internal_nodes += nodes;
+  }
+  const u64 rpb = std::max<u64>(1, J / (nq * widest));
+  w += (u64)nq * rpb * internal_nodes * qp;
+  if (cfac) {
+    const u64 B = 1ull << cfac, in = (u64)nq * h;
+    w += 2 * in * B * ctw + 3 * in * (B / 2) * ctw + in * (B / 2) * (L + 1) * L * N +
+         (u64)nq * db->m * ctw;
+  }
+  *bytes = w * sizeof(u64) + (u64)nq * (db->n + db->n_pairs) * db->k * sizeof(cw::MulJob);
+  return CWPIR_OK;
+}
+
+int cwpir_release_plans(cwpir_ctx *c, int32_t db_id) {
+  if (!c) return CWPIR_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
+  if (db_id < 0) {
+    for (auto &kv : c->dbs) kv.second->plans.clear();
+    return CWPIR_OK;
+  }
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  db->plans.clear();
   return CWPIR_OK;
 }
 
