@@ -207,17 +207,21 @@ CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
 //   |r| <= t N Q / 2 + 1 < P/2, so the centered conversion of r from the
 //   p-basis to the q-basis is exact (and never near the ambiguous zone).
 // ---------------------------------------------------------------------
+// The residues handed to scale_coeff are those of f*d for a fixed factor f
+// (f = N: the inverse transforms that produce d skip their N^-1); every
+// constant that multiplies d carries f^-1.
 struct ScaleTab {
-  u64 t_theta[kMaxL], t_theta_s[kMaxL]; // t (Q/q_j)^-1 mod q_j
-  u64 t_mod[kMaxL], t_mod_s[kMaxL];     // t mod q_j (ambiguous path)
-  // yb_k = [r_k (P/p_k)^-1]_{p_k} = [A_k d_k + sum_j B_jk y_j + C_k rho]_{p_k}
-  u64 A[kMaxK];          // t Q^-1 (P/p_k)^-1 mod p_k
+  u64 t_theta[kMaxL], t_theta_s[kMaxL]; // t f^-1 (Q/q_j)^-1 mod q_j
+  u64 t_mod[kMaxL], t_mod_s[kMaxL];     // t f^-1 mod q_j (ambiguous path)
+  // yb_k = [r_k (P/p_k)^-1]_{p_k} = [A_k (f d)_k + sum_j B_jk y_j + C_k rho]_{p_k}
+  u64 A[kMaxK];          // t f^-1 Q^-1 (P/p_k)^-1 mod p_k
   u64 B[kMaxL][kMaxK];   // -q_j^-1 (P/p_k)^-1 mod p_k
   u64 Cr[kMaxK];         // (P/p_k)^-1 mod p_k
   BaseConv q2b;  // Q -> P conversion data (fraction and Garner parts used)
   BaseConv b2q;  // P -> Q conversion
 };
 
+// dq, dp: residues of f*d below 2^55 (lazy [0, 2q) values are fine).
 // Returns false if the P-basis rounding ever lands in the ambiguous zone,
 // which the bound on |r| rules out; callers record it as an internal error.
 template <int L>

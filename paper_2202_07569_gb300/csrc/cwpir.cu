@@ -223,7 +223,7 @@ int build_tables(cwpir_ctx *c) {
   CUDA_TRY(c, cudaMemcpy(c->twiddles.p, host.data(), host.size() * sizeof(u64),
                          cudaMemcpyHostToDevice));
   fill_conv(h.q2b, c->q, c->p);
-  fill_scale(h.scale, c->q, c->p, c->t);
+  fill_scale(h.scale, c->q, c->p, c->t, N);
   CUDA_TRY(c, cudaMalloc(&c->d_tab, sizeof(cw::DevTables)));
   CUDA_TRY(c, cudaMemcpy(c->d_tab, &h, sizeof h, cudaMemcpyHostToDevice));
   return CWPIR_OK;

@@ -146,15 +146,17 @@ inline bool make_twiddles(u64 q, u32 N, u32 logN, u64 *tw) {
   return true;
 }
 
-// Scale-down constants for round(t d / Q) (see ScaleTab in arith.cuh).
+// Scale-down constants for round(t d / Q) (see ScaleTab in arith.cuh),
+// for residues given as f*d: the constants that multiply d carry f^-1 (the
+// tensor kernel leaves the factor N of its inverse transforms in place).
 inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::vector<u64> &p,
-                       u64 t) {
+                       u64 t, u64 f) {
   const u32 L = (u32)q.size(), K = (u32)p.size();
   fill_conv(S.q2b, q, p);
   fill_conv(S.b2q, p, q);
   for (u32 j = 0; j < L; ++j) {
     u64 qj = q[j];
-    S.t_mod[j] = t % qj;
+    S.t_mod[j] = hmul(t % qj, hinv(f % qj, qj), qj);
     S.t_mod_s[j] = shoup_of(S.t_mod[j], qj);
     S.t_theta[j] = hmul(S.t_mod[j], S.q2b.theta[j], qj);
     S.t_theta_s[j] = shoup_of(S.t_theta[j], qj);
@@ -164,7 +166,7 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
     u64 Qm = 1;
     for (u32 j = 0; j < L; ++j) Qm = hmul(Qm, q[j] % pk, pk);
     const u64 th = S.b2q.theta[k];  // (P/p_k)^-1 mod p_k
-    S.A[k] = hmul(hmul(t % pk, hinv(Qm, pk), pk), th, pk);
+    S.A[k] = hmul(hmul(hmul(t % pk, hinv(Qm, pk), pk), th, pk), hinv(f % pk, pk), pk);
     S.Cr[k] = th;
     for (u32 j = 0; j < L; ++j) {
       u64 v = hmul(hinv(q[j] % pk, pk), th, pk);

@@ -4,7 +4,7 @@
 //   coefficient ciphertext   [2][L][N]
 //   QP-NTT ciphertext        [2][L+K][N]  NTT form over q_0..q_{L-1}, p_0..p_{K-1}
 //   database                 [rows][L][N] NTT form (centered plaintext lift)
-//   tensor buffer  Tbuf      [jobs][3][L+K][N] coefficient form of d0, d1, d2
+//   tensor buffer  Tbuf      [jobs][3][L+K][N] N d0, N d1, N d2 (lazy residues)
 //   scaled buffer  E         [jobs][3][L][N]   round(t d / Q) mod q_j
 //   partials       P         [jobs][2][L][N]   NTT-form sel * DB rows
 //
@@ -63,9 +63,10 @@ __device__ __forceinline__ void ntt_fwd(u64 (&x)[16], u64 *s, const NttPrime &P)
   for (u32 r = 0; r < 16; ++r) x[r] = reduce4(x[r], P.q);
 }
 
-// Inverse transform including the factor N^-1: x[r] = NTT value 16t + r
-// (< 2q) -> x[r] = coefficient t + r N/16, canonical.
-template <int LOGN>
+// Inverse transform: x[r] = NTT value 16t + r (< 2q) -> x[r] = coefficient
+// t + r N/16.  With SCALE the factor N^-1 is applied and the output is
+// canonical; without it the output is N times the coefficient, in [0, 2q).
+template <int LOGN, bool SCALE = true>
 __device__ __forceinline__ void ntt_inv(u64 (&x)[16], u64 *s, const NttPrime &P) {
   constexpr int NP = Passes<LOGN>::count;
   const u32 t = threadIdx.x;
@@ -85,8 +86,10 @@ __device__ __forceinline__ void ntt_inv(u64 (&x)[16], u64 *s, const NttPrime &P)
     inv_pass<LOGN>(x, t, lo, c, w, P.ipsi2, P.q);
     wprev = w;
   }
+  if (SCALE) {
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) x[r] = shoup(x[r], P.ninv, P.ninv_s, P.q);
+    for (u32 r = 0; r < 16; ++r) x[r] = shoup(x[r], P.ninv, P.ninv_s, P.q);
+  }
 }
 
 inline size_t ntt_smem(const DevTables &h) { return (size_t)smem_words(h.N) * sizeof(u64); }
@@ -179,9 +182,11 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
 // unit u: src + u*src_stride ([L][N]) -> dst + u*dst_stride ([L+K][N], P
 // limbs written; Q limbs copied when copy_q).  grid (N/256, units).
 // ---------------------------------------------------------------------
+// The conversion tables are passed by value (__grid_constant__): they sit
+// in the constant bank and the integer multiplies read them as operands.
 template <int L>
 __global__ void k_lift(const DevTables *T, const u64 *src, u64 src_stride, u64 *dst,
-                       u64 dst_stride, int copy_q) {
+                       u64 dst_stride, int copy_q, const __grid_constant__ BaseConv C) {
   constexpr int K = L + 1;
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,7 +196,7 @@ __global__ void k_lift(const DevTables *T, const u64 *src, u64 src_stride, u64 *
   u64 x[L], y[K];
 #pragma unroll
   for (int j = 0; j < L; ++j) x[j] = in[(u64)j * N + c];
-  lift_centered<L, K>(x, y, T->q2b);
+  lift_centered<L, K>(x, y, C);
   if (copy_q) {
 #pragma unroll
     for (int j = 0; j < L; ++j) out[(u64)j * N + c] = x[j];
@@ -203,7 +208,8 @@ __global__ void k_lift(const DevTables *T, const u64 *src, u64 src_stride, u64 *
 // Internal tree nodes: C ([jobs][2][L][N] coefficient form) -> the P limbs
 // of jobs[j].dst.  grid (N/256, 2 * njobs).
 template <int L>
-__global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs) {
+__global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs,
+                            const __grid_constant__ BaseConv Cv) {
   constexpr int K = L + 1;
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,7 +219,7 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
   u64 x[L], y[K];
 #pragma unroll
   for (int j = 0; j < L; ++j) x[j] = in[(u64)j * N + c];
-  lift_centered<L, K>(x, y, T->q2b);
+  lift_centered<L, K>(x, y, Cv);
 #pragma unroll
   for (int k = 0; k < K; ++k) out[(u64)(L + k) * N + c] = y[k];
 }
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
     else v = addq(barrett(a0[c], b1[c], P.q, P.mu), barrett(a1[c], b0[c], P.q, P.mu), P.q);
     x[r] = v;
   }
-  ntt_inv<LOGN>(x, s, P);
+  ntt_inv<LOGN, false>(x, s, P);  // N d in [0, 2q): the scale-down absorbs N^-1
   u64 *out = Tbuf + ((job * 3 + which) * LK + l) * N;
 #pragma unroll
   for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
@@ -256,7 +262,8 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
 // Exact scale-down of every tensor coefficient.  grid (N/256, 3*njobs).
 // ---------------------------------------------------------------------
 template <int L>
-__global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err) {
+__global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err,
+                        const __grid_constant__ ScaleTab S) {
   constexpr int K = L + 1;
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -267,7 +274,7 @@ __global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err) {
   for (int j = 0; j < L; ++j) dq[j] = in[(u64)j * N + c];
 #pragma unroll
   for (int k = 0; k < K; ++k) dp[k] = in[(u64)(L + k) * N + c];
-  if (!scale_coeff<L>(dq, dp, e, T->scale)) atomicOr(err, 1);
+  if (!scale_coeff<L>(dq, dp, e, S)) atomicOr(err, 1);
   u64 *out = E + jw * L * N;
 #pragma unroll
   for (int j = 0; j < L; ++j) out[(u64)j * N + c] = e[j];
@@ -617,7 +624,7 @@ cudaError_t launch_lift(const DevTables *T, const DevTables &h, const u64 *src,
     u32 nu = units - u0 < chunk ? units - u0 : chunk;
     dim3 grid(h.N / 256, nu);
     CW_DISPATCH_L(h.L, k_lift, grid, 256, 0, st, T, src + (u64)u0 * src_stride, src_stride,
-                  dst + (u64)u0 * dst_stride, dst_stride, copy_q ? 1 : 0);
+                  dst + (u64)u0 * dst_stride, dst_stride, copy_q ? 1 : 0, h.q2b);
   }
   return cudaGetLastError();
 }
@@ -626,7 +633,7 @@ cudaError_t launch_lift_jobs(const DevTables *T, const DevTables &h, const u64 *
                              const MulJob *jobs, u32 njobs, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   dim3 grid(h.N / 256, 2 * njobs);
-  CW_DISPATCH_L(h.L, k_lift_jobs, grid, 256, 0, st, T, C, jobs);
+  CW_DISPATCH_L(h.L, k_lift_jobs, grid, 256, 0, st, T, C, jobs, h.q2b);
   return cudaGetLastError();
 }
 
@@ -657,7 +664,7 @@ cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf
                          u64 *E, int *err, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   dim3 grid(h.N / 256, 3 * njobs);
-  CW_DISPATCH_L(h.L, k_scale, grid, 256, 0, st, T, Tbuf, E, err);
+  CW_DISPATCH_L(h.L, k_scale, grid, 256, 0, st, T, Tbuf, E, err, h.scale);
   return cudaGetLastError();
 }
 

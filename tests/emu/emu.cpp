@@ -43,7 +43,7 @@ struct Emu {
       mu.push_back((u64)(((u128)1 << 116) / pr));
     }
     fill_conv(q2b, q, p);
-    fill_scale(S, q, p, t);
+    fill_scale(S, q, p, t, N);
   }
   void fwd(u64 *a, u32 l) {
     const u64 *w = tw[l].data();
@@ -168,7 +168,8 @@ int emu_bfv_mul(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uin
         else if (which == 2) o[c] = barrett(a1[c], b1[c], pr, m);
         else o[c] = addq(barrett(a0[c], b1[c], pr, m), barrett(a1[c], b0[c], pr, m), pr);
       }
-      E.inv(o, l);
+      E.inv(o, l);  // canonical d; the scale-down takes N d as the kernels hand it over
+      for (u32 c = 0; c < N; ++c) o[c] = hmul(o[c], N % pr, pr) + ((c & 1) ? pr : 0);
     }
   int bad = 0;
   u64 dq[kMaxL], dp[kMaxK], e[kMaxL];

@@ -91,10 +91,11 @@ def test_exact_scale_down(orc, N, L):
         ds.append((int(w) * dmax) >> 64)
         ds.append(-((int(w) * dmax) >> 65))
     qa = np.array(q, np.uint64)
-    for d in ds:
+    for i, d in enumerate(ds):
         assert abs(d) <= dmax
-        dq = np.array([d % v for v in q], np.uint64)
-        dp = np.array([d % v for v in p], np.uint64)
+        # the kernels hand over N d in lazy form: residues in [0, 2q)
+        dq = np.array([(N * d) % v + (v if i % 2 else 0) for v in q], np.uint64)
+        dp = np.array([(N * d) % v + (v if i % 3 == 1 else 0) for v in p], np.uint64)
         out = np.zeros(L, np.uint64)
         assert emu.lib().emu_scale(N, L, qa, T, dq, dp, out) == 1
         num = T * d
