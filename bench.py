@@ -127,6 +127,18 @@ def modmuls_per_job(kind: str) -> float:
     return 0.0
 
 
+# DRAM bytes (read + write) per job of each kernel class, from one ncu
+# capture of the current kernels on the profiling size (4096 rows, 128
+# multiplications per launch; profiles/ncu_full_c2_4096rows.md).  DRAM
+# traffic grows in proportion to the jobs of a launch, so a full launch's
+# traffic is this figure times its jobs.
+DRAM_BYTES_PER_JOB = {
+    "tensor_intt": (74429952 + 179669504) / 128,
+    "scale": (226552320 + 73764096) / 128,
+    "relin_pm": (187928832 + 153922304 + 239259392 + 14970880) / 128,
+}
+
+
 def run_gpu(args, rank: int, world: int, dist):
     import torch
 
@@ -224,7 +236,10 @@ def run_gpu(args, rank: int, world: int, dist):
     achieved = work_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else 0.0
     out["roofline"] = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                        "unit": "Tmodmul/s", "frac": achieved / peak if peak else None,
-                       "traffic": None,
+                       "traffic": (DRAM_BYTES_PER_JOB[dom] * jobs_per_launch
+                                   / max(1.0, launches_per_step)
+                                   if dom in DRAM_BYTES_PER_JOB else None),
+                       "traffic_unit": "bytes per launch",
                        "peak_basis": f"{SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
                                      f"/ {IMAD_PER_MODMUL} IMAD per 54-bit modmul"}
     # batched vs plain: 16 queries in one batched call replayed from a CUDA
