@@ -277,7 +277,8 @@ class Oracle:
         cw = _c(codewords, np.uint16)
         n, plen = items.shape
         k = cw.shape[1]
-        out = np.zeros(self.ct_shape, np.uint64)
+        s = max(1, -(-plen // self.N))  # plaintexts per row (Sec. 3.3.1)
+        out = np.zeros(((s,) if s > 1 else ()) + self.ct_shape, np.uint64)
         gk = None
         if gkeys is not None:
             gkeys = _c(gkeys, np.uint64)

@@ -912,7 +912,10 @@ int orc_answer(const orc_ctx *c, uint64_t n, uint32_t payload_len,
                const uint64_t *rlk, const uint64_t *gkeys, int nthreads,
                uint64_t *resp) {
   size_t ctw = 2 * LN(c);
-  if (k == 0 || k > m || payload_len > c->N) return -1;
+  /* Sec. 3.3.1: a row holds s >= 1 plaintexts; plaintext p carries payload
+   * coefficients p*N .. p*N + N - 1 (the last one zero-padded). */
+  const uint32_t s = payload_len == 0 ? 1 : (payload_len + c->N - 1) / c->N;
+  if (k == 0 || k > m || s > ORC_MAX_PLAINTEXTS) return -1;
   for (uint64_t i = 0; i < n; ++i)
     for (uint32_t u = 0; u < k; ++u) {
       uint16_t p = codewords[i * k + u];
@@ -928,7 +931,7 @@ int orc_answer(const orc_ctx *c, uint64_t n, uint32_t payload_len,
     orc_expand(c, h, query, cf, m, gkeys, expanded);
     ctxts = expanded;
   }
-  memset(resp, 0, ctw * sizeof(uint64_t));
+  memset(resp, 0, (size_t)s * ctw * sizeof(uint64_t));
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -936,16 +939,21 @@ int orc_answer(const orc_ctx *c, uint64_t n, uint32_t payload_len,
 #endif
 #pragma omp parallel
   {
-    uint64_t *local = calloc(ctw, sizeof(uint64_t));
+    uint64_t *local = calloc((size_t)s * ctw, sizeof(uint64_t));
     uint64_t *sel = malloc(ctw * sizeof(uint64_t)), *pm = malloc(ctw * sizeof(uint64_t));
 #pragma omp for schedule(dynamic, 1)
     for (int64_t i = 0; i < (int64_t)n; ++i) {
+      /* one selection entry per row, then s inner products (Sec. 3.3.3) */
       orc_selection(c, ctxts, codewords + (size_t)i * k, k, rlk, sel);
-      orc_plain_mul(c, sel, items + (size_t)i * payload_len, payload_len, pm);
-      ct_add(c, local, pm, local);
+      for (uint32_t p = 0; p < s; ++p) {
+        uint32_t lo = p * c->N, len = payload_len - lo < c->N ? payload_len - lo : c->N;
+        orc_plain_mul(c, sel, items + (size_t)i * payload_len + lo, len, pm);
+        ct_add(c, local + (size_t)p * ctw, pm, local + (size_t)p * ctw);
+      }
     }
 #pragma omp critical
-    ct_add(c, resp, local, resp);
+    for (uint32_t p = 0; p < s; ++p)
+      ct_add(c, resp + (size_t)p * ctw, local + (size_t)p * ctw, resp + (size_t)p * ctw);
     free(local);
     free(sel);
     free(pm);

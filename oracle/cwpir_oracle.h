@@ -95,8 +95,12 @@ int orc_selection(const orc_ctx *ctx, const uint64_t *ctxts,
                   uint64_t *out);
 /* Full server answer: expansion (c > 0), selection vector, inner product.
  * query: [h][2][L][N] with h = m when c = 0, else ceil(m / 2^c).
- * items: [n][payload_len]; codewords: [n][k] ascending positions < m.
+ * items: [n][payload_len]; a row is s = ceil(payload_len / N) plaintexts
+ * (Sec. 3.3.1), plaintext p holding coefficients p*N .. p*N + N - 1, and the
+ * answer is s inner products with the same selection vector (Sec. 3.3.3):
+ * resp [s][2][L][N].  codewords: [n][k] ascending positions < m.
  * gkeys may be NULL when c = 0.  nthreads <= 0 uses the OpenMP default. */
+#define ORC_MAX_PLAINTEXTS 256
 int orc_answer(const orc_ctx *ctx, uint64_t n, uint32_t payload_len,
                const uint32_t *items, const uint16_t *codewords, uint32_t k,
                uint32_t m, uint32_t c, const uint64_t *query,

@@ -390,6 +390,30 @@ def test_keyword_pir_present_and_absent(orc):
     assert not got.any() and budget > 0
 
 
+def test_multi_plaintext_rows_return_every_plaintext(orc):
+    """Sec. 3.3.1 / 3.3.3: a row of s plaintexts is answered by s inner
+    products with one selection vector; response p decrypts to plaintext p
+    of the selected row (the last one zero-padded), for a present index and
+    for rows the query does not select."""
+    N, L = 64, 2
+    O, q, cd, rlk = small_setup(orc, N, L)
+    n, k = 30, 2
+    m = orc.code_length(5, k)
+    plen = 2 * N + 21  # three plaintexts, the third ragged
+    items = syn.payload(syn.Stream(53), n, plen, T)
+    cw = np.stack([orc.map_perfect(i, m, k) for i in range(n)])
+    for target in (0, 13, n - 1):
+        a, e = cd.encryption(m, 80 + target)
+        query = O.make_query(orc.map_perfect(target, m, k), m, 0, cd.s, a, e)
+        resp = O.answer(items, cw, m, query, rlk)
+        assert resp.shape == (3, 2, L, N)
+        want = np.zeros(3 * N, np.uint32)
+        want[:plen] = items[target]
+        for p in range(3):
+            got, budget = O.decrypt(resp[p], cd.s)
+            assert np.array_equal(got, want[p * N:(p + 1) * N]) and budget > 0, (target, p)
+
+
 def test_c1_full_answer_decrypts_with_positive_budget(orc):
     """Workload of the first configuration: n=256, k=2, m=24, N=4096, two
     54-bit primes, t=65537."""
