@@ -45,7 +45,9 @@
 extern "C" {
 #endif
 
-#define CWPIR_ABI_VERSION 1
+#define CWPIR_ABI_VERSION 2
+/* Largest number of plaintexts per database row (payload_len <= this * N). */
+#define CWPIR_MAX_PLAINTEXTS 256
 
 enum {
   CWPIR_OK = 0,
@@ -105,10 +107,14 @@ int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys,
                 cwpir_ctx **out);
 void cwpir_destroy(cwpir_ctx *ctx);
 
-/* Database load (Setup, Sec. 3.3.1): n rows of payload_len <= N plaintext
- * coefficients each < t (row-major [n][payload_len], zero-padded to N), and
- * each row's codeword in CW(m,k) as k ascending one-positions < m
- * ([n][k]).  For index PIR the codeword of row i is the perfect mapping of
+/* Database load (Setup, Sec. 3.3.1): n rows of payload_len plaintext
+ * coefficients each < t (row-major [n][payload_len]), and each row's
+ * codeword in CW(m,k) as k ascending one-positions < m ([n][k]).  A row is
+ * s = ceil(payload_len / N) plaintexts (s = 1 for payload_len <= N;
+ * payload_len <= CWPIR_MAX_PLAINTEXTS * N): plaintext p holds payload
+ * coefficients p*N .. p*N + N - 1, the last one zero-padded; every answer
+ * against the database returns s ciphertexts, the inner products of the one
+ * selection vector with each plaintext column (Sec. 3.3.3).  For index PIR the codeword of row i is the perfect mapping of
  * i; for keyword PIR (Sec. 3.3.6) the mapping of the row's keyword.  The
  * rows are lifted to centered residues and kept in HBM in NTT form.
  * 1 <= k <= 16, k <= m <= 16384, 1 <= n <= 2^24.  *db_id receives a handle.
@@ -126,7 +132,8 @@ int cwpir_free_db(cwpir_ctx *ctx, int32_t db_id);
  * inner product sum_i sel_i * DB_i (Eq. baseline-pir).
  * query: [h][2][L][N] with h = m when c = 0, else h = ceil(m / 2^c) (Alg.
  * Query); c <= log2 N and needs the Galois keys for N/2^a + 1, a < c.
- * response: [2][L][N], written.  Host buffers; blocks until done.
+ * response: [s][2][L][N] (s = cwpir_db_plaintexts), written.  Host buffers;
+ * blocks until done.
  * EINVAL, ENODB, ENOKEY, ECUDA, EINTERNAL. */
 int cwpir_answer(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                  const uint64_t *query, uint64_t *response);
@@ -141,11 +148,11 @@ int cwpir_answer_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
  * by cwpir_answer (identical response bits); the queries share each kernel
  * launch: expansion rounds, first-level products and tree levels of all nq
  * queries run in the same grids.  queries: [nq][h][2][L][N] (h as for
- * cwpir_answer, same c for all), responses: [nq][2][L][N].  With
+ * cwpir_answer, same c for all), responses: [nq][s][2][L][N].  With
  * CWPIR_OPT_USE_GRAPH the launch sequence for (database, nq, c) is captured
  * once into a CUDA graph on the first call and replayed afterwards.
  * EINVAL also when nq times the tree's widest level exceeds the
- * multiplications per launch (CWPIR_OPT_MAX_JOBS). */
+ * multiplications per launch (CWPIR_OPT_MAX_JOBS), or nq * s exceeds it. */
 int cwpir_answer_batch(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
                        const uint64_t *queries, uint64_t *responses);
 int cwpir_answer_batch_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
@@ -155,7 +162,7 @@ int cwpir_answer_batch_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
  * cwpir_answer_batch_device) for each candidate number of multiplications
  * per launch in `candidates` (count entries, 0 = automatic), keeps the
  * fastest on ctx (CWPIR_OPT_MAX_JOBS) and writes it and its time per call
- * in milliseconds.  d_responses is scratch of [nq][2][L][N]. */
+ * in milliseconds.  d_responses is scratch of [nq][s][2][L][N]. */
 int cwpir_autotune(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
                    const uint64_t *d_queries, uint64_t *d_responses,
                    const int64_t *candidates, uint32_t count, int64_t *best,
@@ -188,7 +195,8 @@ int cwpir_expand(cwpir_ctx *ctx, uint32_t c, uint32_t m, const uint64_t *query,
 int cwpir_selection(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                     const uint64_t *query, uint64_t count,
                     const uint64_t *rows, uint64_t *out);
-/* Plain multiplication PM of a ciphertext by row `row` of a database. */
+/* Plain multiplication PM of a ciphertext by row `row` of a database: by
+ * each of the row's s plaintexts, out: [s][2][L][N]. */
 int cwpir_plain_mul(cwpir_ctx *ctx, int32_t db_id, uint64_t row,
                     const uint64_t *ct, uint64_t *out);
 
@@ -237,6 +245,8 @@ int cwpir_mul_noalloc(cwpir_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b,
 /* Shape of a loaded database: ring degree, number of primes, code length. */
 int cwpir_db_shape(const cwpir_ctx *ctx, int32_t db_id, uint32_t *N, uint32_t *L,
                    uint32_t *m);
+/* Plaintexts per row s of a loaded database (responses are [s][2][L][N]). */
+int cwpir_db_plaintexts(const cwpir_ctx *ctx, int32_t db_id, uint32_t *s);
 /* CUDA device of the context. */
 int cwpir_ctx_device(const cwpir_ctx *ctx, int *device);
 
@@ -272,7 +282,7 @@ int cwpir_server_create(const cwpir_target *targets, uint32_t n_targets,
 int cwpir_submit(cwpir_server *srv, uint32_t target, const uint64_t *query,
                  uint64_t *ticket);
 /* Non-blocking: *status = 0 while waiting or running; when done, 1 (the
- * response [2][L][N] is written, latency_s = completion - submission) or
+ * response [s][2][L][N] is written, latency_s = completion - submission) or
  * a negative error code; a finished ticket is forgotten after it is read. */
 int cwpir_poll(cwpir_server *srv, uint64_t ticket, uint64_t *response,
                int32_t *status, double *latency_s);

@@ -112,6 +112,7 @@ def lib():
             "cwpir_release_plans": (I, [vp, C.c_int32]),
             "cwpir_db_shape": (I, [vp, C.c_int32, C.POINTER(U32), C.POINTER(U32),
                                    C.POINTER(U32)]),
+            "cwpir_db_plaintexts": (I, [vp, C.c_int32, C.POINTER(U32)]),
             "cwpir_ctx_device": (I, [vp, C.POINTER(C.c_int)]),
             "cwpir_server_create": (I, [C.POINTER(_Target), U32, U32, U64, U32,
                                         C.POINTER(vp)]),
@@ -224,11 +225,23 @@ class Context:
                                         cw.reshape(-1), C.byref(db)))
         return int(db.value)
 
+    def plaintexts(self, db: int) -> int:
+        """Plaintexts per row s of a database (Sec. 3.3.1)."""
+        s = C.c_uint32()
+        self._check(lib().cwpir_db_plaintexts(self._h, db, C.byref(s)))
+        return int(s.value)
+
+    def resp_shape(self, db: int):
+        """Shape of one query's response: [2][L][N], or [s][2][L][N] for rows
+        of s > 1 plaintexts."""
+        s = self.plaintexts(db)
+        return ((s,) if s > 1 else ()) + self.ct_shape
+
     def free_db(self, db: int):
         self._check(lib().cwpir_free_db(self._h, db))
 
     def answer(self, db: int, query, c: int = 0) -> np.ndarray:
-        out = np.zeros(self.ct_shape, np.uint64)
+        out = np.zeros(self.resp_shape(db), np.uint64)
         self._check(lib().cwpir_answer(self._h, db, c, _u64(query), out))
         return out
 
@@ -239,7 +252,7 @@ class Context:
     def answer_batch(self, db: int, queries, c: int = 0) -> np.ndarray:
         q = _u64(queries)
         nq = q.shape[0]
-        out = np.zeros((nq,) + self.ct_shape, np.uint64)
+        out = np.zeros((nq,) + self.resp_shape(db), np.uint64)
         self._check(lib().cwpir_answer_batch(self._h, db, c, nq, q.reshape(-1), out))
         return out
 
@@ -282,7 +295,7 @@ class Context:
         return out
 
     def plain_mul(self, db: int, row: int, ct) -> np.ndarray:
-        out = np.zeros(self.ct_shape, np.uint64)
+        out = np.zeros(self.resp_shape(db), np.uint64)
         self._check(lib().cwpir_plain_mul(self._h, db, row, _u64(ct), out))
         return out
 
@@ -313,7 +326,7 @@ class Server:
         self._shapes = []
         for i, (ctx, db, c) in enumerate(targets):
             arr[i] = _Target(ctx._h, db, c)
-            self._shapes.append((ctx.L, ctx.N))
+            self._shapes.append(ctx.resp_shape(db))
         h = C.c_void_p()
         rc = lib().cwpir_server_create(arr, len(targets), max_batch, hbm_reserve, max_pending,
                                        C.byref(h))
@@ -331,8 +344,7 @@ class Server:
 
     def poll(self, ticket: int, target: int):
         """(status, response or None, latency seconds)."""
-        L, N = self._shapes[target]
-        out = np.zeros((2, L, N), np.uint64)
+        out = np.zeros(self._shapes[target], np.uint64)
         st, lat = C.c_int32(), C.c_double()
         rc = lib().cwpir_poll(self._h, ticket, out.reshape(-1), C.byref(st), C.byref(lat))
         if rc:
@@ -340,8 +352,7 @@ class Server:
         return int(st.value), (out if st.value == 1 else None), float(lat.value)
 
     def wait(self, ticket: int, target: int, timeout: float = 600.0):
-        L, N = self._shapes[target]
-        out = np.zeros((2, L, N), np.uint64)
+        out = np.zeros(self._shapes[target], np.uint64)
         st, lat = C.c_int32(), C.c_double()
         rc = lib().cwpir_wait(self._h, ticket, out.reshape(-1), C.byref(st), C.byref(lat),
                               timeout)

@@ -76,7 +76,7 @@ struct ExpRound {
 // sequence itself contains only kernel launches and device copies and can
 // be captured into a CUDA graph.
 struct Plan {
-  u32 nq = 1, cfac = 0, k = 0, top = 0, m = 0, h_in = 0;
+  u32 nq = 1, cfac = 0, k = 0, top = 0, m = 0, h_in = 0, sp = 1;
   bool memo = false, leaf_root = false;
   u64 n_memo = 0, mults = 0;
   std::vector<Chunk> memo_chunks;
@@ -85,8 +85,8 @@ struct Plan {
   cw::MulJob *d_jobs = nullptr;
   DevBuf memo_buf, level_buf;
   DevBuf leaves;     // [nq][m] QP-NTT cts
-  DevBuf acc;        // [nq][2][L][N] NTT-form accumulators
-  DevBuf q_in, resp; // graph staging: [nq][h_in] cts and [nq][2][L][N]
+  DevBuf acc;        // [nq][sp][2][L][N] NTT-form accumulators
+  DevBuf q_in, resp; // graph staging: [nq][h_in] cts and [nq][sp][2][L][N]
   DevBuf exp_a, exp_b, exp_tau, exp_S, exp_DN, exp_O, leaves_coef;
   std::vector<ExpRound> exp_rounds;
   cw::SubJob *d_subjobs = nullptr;
@@ -103,7 +103,8 @@ struct Plan {
 struct Db {
   u64 n = 0, n_pairs = 0;  // rows, distinct first-level position pairs
   u32 plen = 0, k = 0, m = 0;
-  DevBuf db;                  // [n][L][N] NTT form
+  u32 sp = 1;                 // plaintexts per row (Sec. 3.3.1): ceil(plen / N)
+  DevBuf db;                  // [n][sp][L][N] NTT form
   std::vector<uint16_t> cw;   // [n][k]
   // answer plans over all rows, by (queries per call, compression factor)
   std::map<std::pair<u32, u32>, std::unique_ptr<Plan>> plans;
@@ -355,11 +356,15 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
   P->top = ceil_log2(k);
   P->memo = memo_opt && P->top >= 2;
   P->h_in = cfac ? (m + (1u << cfac) - 1) >> cfac : m;
+  P->sp = db->sp;
   const u32 J = c->jmax;
+  if (root_mode == cw::ROOT_PM && (u64)nq * db->sp > J)
+    return fail(c, CWPIR_EINVAL, "%u queries x %u plaintexts per row need more than %u partial "
+                "sums per launch (raise CWPIR_OPT_MAX_JOBS)", nq, db->sp, J);
   CUDA_TRY(c, P->leaves.ensure((u64)nq * m * qp));
-  CUDA_TRY(c, P->acc.ensure((u64)nq * ctw));
+  CUDA_TRY(c, P->acc.ensure((u64)nq * db->sp * ctw));
   CUDA_TRY(c, P->q_in.ensure((u64)nq * P->h_in * ctw));
-  CUDA_TRY(c, P->resp.ensure((u64)nq * ctw));
+  CUDA_TRY(c, P->resp.ensure((u64)nq * db->sp * ctw));
 
   if (cfac) {
     int rc = setup_expand(c, P.get());
@@ -378,7 +383,7 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
 
   if (k == 1) {
     P->leaf_root = true;
-    const u64 per = std::max<u64>(1, J / nq);
+    const u64 per = std::max<u64>(1, J / ((u64)nq * db->sp));  // partials [job][sp] fit J
     for (u64 x = 0; x < rows.size(); x += per) {
       u32 cnt = (u32)std::min<u64>(per, rows.size() - x);
       P->batches.push_back({Chunk{jobs.size(), cnt * nq, cw::ROOT_PM, nq}});
@@ -476,17 +481,17 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
 int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream_t st) {
   const cw::MulJob *jobs = P->d_jobs + ch.off;
   if (P->leaf_root) {
-    CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] { return cw::launch_pm_leaf(c->d_tab, c->h, jobs, ch.count, dbp, c->CP.p, st); }));
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, ch.count / ch.segs, P->acc.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] { return cw::launch_pm_leaf(c->d_tab, c->h, jobs, ch.count, P->sp, dbp, c->CP.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, ch.count / ch.segs, P->sp, P->acc.p, st); }));
     c->stats.kernel_launches += 2;
-    c->stats.db_bytes_read += (u64)ch.count * c->L * c->N * sizeof(u64);
+    c->stats.db_bytes_read += (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
     return CWPIR_OK;
   }
   CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, c->Tbuf.p, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
     return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
-                            c->rlk_s.p, dbp, c->DN.p, c->CP.p, st);
+                            c->rlk_s.p, dbp, P->sp, c->jmax, c->DN.p, c->CP.p, st);
   }));
   c->stats.kernel_launches += 4;  // tensor, scale, digit NTTs, key multiply-accumulate
   c->stats.mults += ch.count;
@@ -498,10 +503,10 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
     c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
   } else if (ch.mode == cw::ROOT_PM) {
     const u32 seg_len = ch.count / ch.segs;
-    const u32 groups = cw::relin_pm_groups(c->h, ch.segs, seg_len);
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, groups, P->acc.p, st); }));
+    const u32 groups = cw::relin_pm_groups(c->h, ch.segs, seg_len, P->sp, c->jmax);
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, groups, P->sp, P->acc.p, st); }));
     c->stats.kernel_launches += 1;
-    c->stats.db_bytes_read += (u64)ch.count * c->L * c->N * sizeof(u64);
+    c->stats.db_bytes_read += (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
   } else {
     c->stats.kernel_launches += 1;  // inverse NTT
     c->stats.ntt_polys += (u64)ch.count * 2 * c->L;
@@ -595,7 +600,7 @@ Db *get_db(cwpir_ctx *c, int32_t id) {
 }
 
 // The whole answer of a plan: expansion, leaves, tree, accumulation and the
-// final inverse transform into d_resp ([nq][2][L][N]).  Capturable.
+// final inverse transform into d_resp ([nq][sp][2][L][N]).  Capturable.
 int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_resp,
                    cudaStream_t st) {
   int rc;
@@ -605,18 +610,18 @@ int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_res
     coef = P->leaves_coef.p;
   }
   if ((rc = prep_leaves(c, coef, P->nq * P->m, P->leaves.p, st))) return rc;
-  CUDA_TRY(c, cudaMemsetAsync(P->acc.p, 0, (u64)P->nq * c->ct() * sizeof(u64), st));
+  CUDA_TRY(c, cudaMemsetAsync(P->acc.p, 0, (u64)P->nq * P->sp * c->ct() * sizeof(u64), st));
   for (const Chunk &ch : P->memo_chunks)
     if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
   for (const auto &batch : P->batches)
     for (const Chunk &ch : batch)
       if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
   CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] {
-    return cw::launch_ntt(c->d_tab, c->h, d_resp, 2 * P->nq, (u64)c->L * c->N, 0, c->L, true,
-                          P->acc.p, (u64)c->L * c->N, st);
+    return cw::launch_ntt(c->d_tab, c->h, d_resp, 2 * P->nq * P->sp, (u64)c->L * c->N, 0, c->L,
+                          true, P->acc.p, (u64)c->L * c->N, st);
   }));
   c->stats.kernel_launches += 1;
-  c->stats.ntt_polys += 2ull * P->nq * c->L;
+  c->stats.ntt_polys += 2ull * P->nq * P->sp * c->L;
   c->stats.rows = db->n * P->nq;
   return CWPIR_OK;
 }
@@ -639,7 +644,7 @@ int get_plan(cwpir_ctx *c, Db *db, u32 nq, u32 cfac, Plan **out) {
   return CWPIR_OK;
 }
 
-// Answers nq queries (d_query: [nq][h_in] cts) into d_resp ([nq][2][L][N]).
+// Answers nq queries (d_query: [nq][h_in] cts) into d_resp ([nq][sp][2][L][N]).
 // With CWPIR_OPT_USE_GRAPH the plan's sequence is captured once into a
 // CUDA graph (on the context's stream) and replayed on `st`, staging the
 // queries and responses through the plan's fixed buffers.
@@ -674,7 +679,7 @@ int answer_batch_enqueue(cwpir_ctx *c, Db *db, u32 cfac, u32 nq, const u64 *d_qu
   CUDA_TRY(c, cudaMemcpyAsync(P->q_in.p, d_query, (u64)nq * P->h_in * ctw * sizeof(u64),
                               cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(c, cudaGraphLaunch(P->graph, st));
-  CUDA_TRY(c, cudaMemcpyAsync(d_resp, P->resp.p, (u64)nq * ctw * sizeof(u64),
+  CUDA_TRY(c, cudaMemcpyAsync(d_resp, P->resp.p, (u64)nq * P->sp * ctw * sizeof(u64),
                               cudaMemcpyDeviceToDevice, st));
   c->stats = P->graph_stats;
   return CWPIR_OK;
@@ -833,7 +838,8 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
   cudaSetDevice(c->device);
   if (!items || !codewords || !db_id) return fail(c, CWPIR_EINVAL, "null argument");
   if (n < 1 || n > (1ull << 24)) return fail(c, CWPIR_EINVAL, "n must be in [1, 2^24]");
-  if (plen > c->N) return fail(c, CWPIR_EINVAL, "payload_len > N");
+  if (plen > (u64)CWPIR_MAX_PLAINTEXTS * c->N)
+    return fail(c, CWPIR_EINVAL, "payload_len > %u N", CWPIR_MAX_PLAINTEXTS);
   if (k < 1 || k > 16 || k > m || m > 16384)
     return fail(c, CWPIR_EINVAL, "need 1 <= k <= 16, k <= m <= 16384");
   for (u64 i = 0; i < n * plen; ++i)
@@ -850,6 +856,7 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
   db->plen = plen;
   db->k = k;
   db->m = m;
+  db->sp = plen ? (plen + c->N - 1) / c->N : 1;
   db->cw.assign(codewords, codewords + n * k);
   {
     std::unordered_map<u32, char> seen;
@@ -858,7 +865,8 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
         seen.emplace(((u32)codewords[i * k + 2 * r] << 16) | codewords[i * k + 2 * r + 1], 0);
     db->n_pairs = seen.size();
   }
-  CUDA_TRY(c, db->db.ensure(n * c->L * c->N));
+  const u64 row_words = (u64)db->sp * c->L * c->N;
+  CUDA_TRY(c, db->db.ensure(n * row_words));
   // upload rows in chunks and transform
   const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));
   uint32_t *d_items = nullptr;
@@ -870,8 +878,8 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
     if (plen) {
       cudaError_t e = cudaMemcpyAsync(d_items, items + r0 * plen, nr * plen * sizeof(uint32_t),
                                       cudaMemcpyHostToDevice, c->stream);
-      if (e == cudaSuccess) e = cw::launch_db_load(c->d_tab, c->h, d_items, nr, plen,
-                                                   db->db.p + r0 * c->L * c->N, c->stream);
+      if (e == cudaSuccess) e = cw::launch_db_load(c->d_tab, c->h, d_items, nr, plen, db->sp,
+                                                   db->db.p + r0 * row_words, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) {
         cudaFree(d_items);
@@ -880,7 +888,7 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
     }
   }
   if (d_items) cudaFree(d_items);
-  if (!plen) CUDA_TRY(c, cudaMemset(db->db.p, 0, n * c->L * c->N * sizeof(u64)));
+  if (!plen) CUDA_TRY(c, cudaMemset(db->db.p, 0, n * row_words * sizeof(u64)));
   int32_t id = c->next_db++;
   c->dbs[id] = std::move(db);
   *db_id = id;
@@ -935,12 +943,12 @@ int cwpir_answer_batch(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
     return fail(c, CWPIR_EINVAL, "query residue out of range");
   const u64 ctw = c->ct();
   CUDA_TRY(c, c->io_in.ensure(h * nq * ctw));
-  CUDA_TRY(c, c->io_out.ensure((u64)nq * ctw));
+  CUDA_TRY(c, c->io_out.ensure((u64)nq * db->sp * ctw));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, queries, h * nq * ctw * sizeof(u64),
                               cudaMemcpyHostToDevice, c->stream));
   rc = answer_batch_enqueue(c, db, cfac, nq, c->io_in.p, c->io_out.p, c->stream);
   if (rc) return rc;
-  CUDA_TRY(c, cudaMemcpyAsync(responses, c->io_out.p, (u64)nq * ctw * sizeof(u64),
+  CUDA_TRY(c, cudaMemcpyAsync(responses, c->io_out.p, (u64)nq * db->sp * ctw * sizeof(u64),
                               cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return check_err_flag(c);
@@ -1140,18 +1148,20 @@ int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *c
   if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
   if (!ct || !out || row >= db->n) return fail(c, CWPIR_EINVAL, "null buffer or row out of range");
   if (!valid_residues(ct, c->L, c->N, c->q, 2)) return fail(c, CWPIR_EINVAL, "residue out of range");
-  const u64 ctw = c->ct(), LN = (u64)c->L * c->N;
-  CUDA_TRY(c, c->io_in.ensure(ctw));
-  CUDA_TRY(c, c->io_out.ensure(ctw));
+  const u64 ctw = c->ct(), LN = (u64)c->L * c->N, sp = db->sp;
+  CUDA_TRY(c, c->io_in.ensure(sp * ctw));
+  CUDA_TRY(c, c->io_out.ensure(sp * ctw));
   CUDA_TRY(c, c->tmp_ct.ensure(ctw));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, ct, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, c->tmp_ct.p, 2, LN, 0, c->L, false, c->io_in.p, LN,
                              c->stream));
-  CUDA_TRY(c, cw::launch_pm_ntt(c->d_tab, c->h, c->tmp_ct.p, db->db.p + row * LN, c->io_in.p,
-                                c->stream));
-  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, c->io_out.p, 2, LN, 0, c->L, true, c->io_in.p, LN,
-                             c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  for (u64 p = 0; p < sp; ++p)
+    CUDA_TRY(c, cw::launch_pm_ntt(c->d_tab, c->h, c->tmp_ct.p, db->db.p + (row * sp + p) * LN,
+                                  c->io_in.p + p * ctw, c->stream));
+  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, c->io_out.p, 2 * (u32)sp, LN, 0, c->L, true,
+                             c->io_in.p, LN, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, sp * ctw * sizeof(u64), cudaMemcpyDeviceToHost,
+                              c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return CWPIR_OK;
 }
@@ -1163,6 +1173,14 @@ int cwpir_db_shape(const cwpir_ctx *c, int32_t db_id, uint32_t *N, uint32_t *L, 
   *N = c->N;
   *L = c->L;
   *m = it->second->m;
+  return CWPIR_OK;
+}
+
+int cwpir_db_plaintexts(const cwpir_ctx *c, int32_t db_id, uint32_t *sp) {
+  if (!c || !sp) return CWPIR_EINVAL;
+  auto it = c->dbs.find(db_id);
+  if (it == c->dbs.end()) return CWPIR_ENODB;
+  *sp = it->second->sp;
   return CWPIR_OK;
 }
 
@@ -1193,7 +1211,7 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
   const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();
   const bool memo = c->opt_share && top >= 2;
   const u64 h = cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
-  w += (u64)nq * db->m * qp + 2ull * nq * ctw + (u64)nq * h * ctw;
+  w += (u64)nq * db->m * qp + 2ull * nq * db->sp * ctw + (u64)nq * h * ctw;
   if (memo) w += (u64)nq * db->n_pairs * qp;
   u64 widest = 1, internal_nodes = 0;
   for (u32 l = memo ? 2 : 1; l <= top; ++l) {
@@ -1370,7 +1388,7 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
   CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
   CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
-                               c->rlk_s.p, nullptr, dn, ob, st));
+                               c->rlk_s.p, nullptr, 1, 1, dn, ob, st));
   int h_err = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));

@@ -101,27 +101,28 @@ cudaError_t allow_smem(F *kernel, size_t bytes) {
 }
 
 // ---------------------------------------------------------------------
-// Database load: row r, limb j: centered lift of the payload (v > t/2 ->
-// v - t), zero-padded to N, forward NTT.  grid (L, rows).
+// Database load: row r, plaintext p (payload coefficients p N .. p N + N-1,
+// zero-padded), limb j: centered lift (v > t/2 -> v - t), forward NTT into
+// db[r][p][j].  grid (sp L, rows).
 // ---------------------------------------------------------------------
 template <int LOGN>
 __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
-    k_db_load(const DevTables *T, const u32 *items, u32 plen, u64 *db) {
+    k_db_load(const DevTables *T, const u32 *items, u32 plen, u32 sp, u64 *db) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 L = T->L, j = blockIdx.x, t = threadIdx.x;
+  const u32 L = T->L, p = blockIdx.x / L, j = blockIdx.x % L, t = threadIdx.x;
   const u64 row = blockIdx.y;
   const NttPrime P = T->prime[j];
   const u64 tt = T->t;
   u64 x[16];
 #pragma unroll
   for (u32 r = 0; r < 16; ++r) {
-    const u32 c = strided_idx<LOGN>(t, r);
+    const u32 c = p * N + strided_idx<LOGN>(t, r);
     const u64 v = c < plen ? (u64)items[row * plen + c] : 0;
     x[r] = v > tt / 2 ? P.q - (tt - v) : v;
   }
   ntt_fwd<LOGN>(x, s, P);
-  u64 *out = db + (row * L + j) * N;
+  u64 *out = db + ((row * sp + p) * L + j) * N;
 #pragma unroll
   for (u32 r = 0; r < 16; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
 }
@@ -349,17 +350,22 @@ __device__ __forceinline__ void ks_mac(const u64 *DN, u64 job, u32 n_add, u32 j,
 }
 
 // (B) for the answer's last level.  The launch's jobs form `segs` segments
-// of seg_len consecutive jobs (one segment per query); block z = s*G + g
-// sums (acc0, acc1) * DB[row] over jobs g, g+G, ... of segment s into
-// P[s*G + g][2][L][N].  grid (N/256, L, segs*G).
-template <int L>
+// of seg_len consecutive jobs (one segment per query); a database row holds
+// sp plaintexts ([row][sp][L][N]).  Block z = (s*G + g) * pcn + pc sums
+// (acc0, acc1) * DB[row][p] over jobs g, g+G, ... of segment s for the
+// plaintexts p of chunk pc (SP per chunk) into P[s*G + g][p][2][L][N]; the
+// key products are formed once per job and chunk.
+// grid (N/256, L, segs*G*pcn).
+template <int L, int SP>
 __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 seg_len, u32 G,
-                            const MulJob *jobs, const u64 *key, const u64 *key_s,
-                            const u64 *db, u64 *P) {
+                            u32 sp, u32 pcn, const MulJob *jobs, const u64 *key,
+                            const u64 *key_s, const u64 *db, u64 *P) {
   const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  const u32 sg = blockIdx.z, seg = sg / G, g = sg % G;
+  const u32 pc = blockIdx.z % pcn, sg = blockIdx.z / pcn, seg = sg / G, g = sg % G;
+  const u32 p0 = pc * SP;
   const NttPrime Pr = T->prime[j];
   const u64 q = Pr.q;
+  const u64 LN = (u64)L * N;
   u64 kb[L], kbs[L], ka[L], kas[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) {
@@ -369,17 +375,31 @@ __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 se
     ka[i] = key[oa];
     kas[i] = key_s[oa];
   }
-  u64 sum0 = 0, sum1 = 0;
+  u64 sum0[SP], sum1[SP];
+#pragma unroll
+  for (int p = 0; p < SP; ++p) sum0[p] = sum1[p] = 0;
   for (u32 x = g; x < seg_len; x += G) {
     const u64 job = (u64)seg * seg_len + x;
     u64 a0, a1;
     ks_mac<L>(DN, job, n_add, j, c, N, kb, kbs, ka, kas, q, a0, a1);
-    const u64 m = db[((u64)jobs[job].row * L + j) * N + c];
-    sum0 = addq(sum0, barrett(a0, m, q, Pr.mu), q);
-    sum1 = addq(sum1, barrett(a1, m, q, Pr.mu), q);
+    const u64 *dr = db + ((u64)jobs[job].row * sp + p0) * LN + (u64)j * N + c;
+#pragma unroll
+    for (int p = 0; p < SP; ++p) {
+      if (p0 + p < sp) {
+        const u64 m = dr[(u64)p * LN];
+        sum0[p] = addq(sum0[p], barrett(a0, m, q, Pr.mu), q);
+        sum1[p] = addq(sum1[p], barrett(a1, m, q, Pr.mu), q);
+      }
+    }
   }
-  P[((u64)sg * 2 * L + j) * N + c] = sum0;
-  P[((u64)(sg * 2 + 1) * L + j) * N + c] = sum1;
+#pragma unroll
+  for (int p = 0; p < SP; ++p) {
+    if (p0 + p < sp) {
+      u64 *o = P + ((u64)sg * sp + p0 + p) * 2 * LN + (u64)j * N + c;
+      o[0] = sum0[p];
+      o[LN] = sum1[p];
+    }
+  }
 }
 
 // (B) producing the NTT-form result: INTERNAL mode writes it to the Q
@@ -439,28 +459,31 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
 
-// k = 1: the selection entry is the leaf itself (Q limbs in NTT form).
-// grid (N/256, L, njobs).
-__global__ void k_pm_leaf(const DevTables *T, const MulJob *jobs, const u64 *db, u64 *P) {
-  const u32 N = T->N, L = T->L, K = T->K, j = blockIdx.y;
+// k = 1: the selection entry is the leaf itself (Q limbs in NTT form);
+// P[job][p][2][L][N] = leaf * DB[row][p].  grid (N/256, sp L, njobs).
+__global__ void k_pm_leaf(const DevTables *T, const MulJob *jobs, u32 sp, const u64 *db,
+                          u64 *P) {
+  const u32 N = T->N, L = T->L, K = T->K, p = blockIdx.y / L, j = blockIdx.y % L;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 job = blockIdx.z;
   const NttPrime Pr = T->prime[j];
   const MulJob J = jobs[job];
-  const u64 m = db[((u64)J.row * L + j) * N + c];
+  const u64 LN = (u64)L * N;
+  const u64 m = db[((u64)J.row * sp + p) * LN + (u64)j * N + c];
   const u64 ps = (u64)(L + K) * N;
-  P[(job * 2 + 0) * L * N + (u64)j * N + c] = barrett(J.a[(u64)j * N + c], m, Pr.q, Pr.mu);
-  P[(job * 2 + 1) * L * N + (u64)j * N + c] = barrett(J.a[ps + (u64)j * N + c], m, Pr.q, Pr.mu);
+  u64 *o = P + (job * sp + p) * 2 * LN + (u64)j * N + c;
+  o[0] = barrett(J.a[(u64)j * N + c], m, Pr.q, Pr.mu);
+  o[LN] = barrett(J.a[ps + (u64)j * N + c], m, Pr.q, Pr.mu);
 }
 
-// acc[s][2][L][N] += sum over x < per_seg of P[s*per_seg + x][2][L][N]
-// (mod q_j) for every segment s.  grid (N/256, 2L, segs).
-__global__ void k_accumulate(const DevTables *T, const u64 *P, u32 per_seg, u64 *acc) {
+// acc[s][sp][2][L][N] += sum over x < per_seg of P[s*per_seg + x][sp][2][L][N]
+// (mod q_j) for every segment s.  grid (N/256, 2 L sp, segs).
+__global__ void k_accumulate(const DevTables *T, const u64 *P, u32 per_seg, u32 sp, u64 *acc) {
   const u32 N = T->N, L = T->L;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u32 pl = blockIdx.y, j = pl % L, seg = blockIdx.z;
   const u64 q = T->prime[j].q;
-  const u64 stride = 2ull * L * N, off = (u64)pl * N + c;
+  const u64 stride = 2ull * sp * L * N, off = (u64)pl * N + c;
   const u64 *ps = P + (u64)seg * per_seg * stride;
   u64 *as = acc + (u64)seg * stride;
   u64 a = as[off];
@@ -584,15 +607,15 @@ inline dim3 ntt_block(const DevTables &h) { return dim3(h.N / 16); }
   }
 
 cudaError_t launch_db_load(const DevTables *T, const DevTables &h, const u32 *items, u64 rows,
-                           u32 plen, u64 *db, cudaStream_t st) {
+                           u32 plen, u32 sp, u64 *db, cudaStream_t st) {
   const u64 chunk = 32768;
   for (u64 r0 = 0; r0 < rows; r0 += chunk) {
     u64 nr = rows - r0 < chunk ? rows - r0 : chunk;
     CW_DISPATCH_LOGN(h.logN, {
       cudaError_t e = allow_smem(k_db_load<LG>, ntt_smem(h));
       if (e != cudaSuccess) return e;
-      k_db_load<LG><<<dim3(h.L, (u32)nr), ntt_block(h), ntt_smem(h), st>>>(
-          T, items + r0 * plen, plen, db + r0 * h.L * h.N);
+      k_db_load<LG><<<dim3(sp * h.L, (u32)nr), ntt_block(h), ntt_smem(h), st>>>(
+          T, items + r0 * plen, plen, sp, db + r0 * sp * h.L * h.N);
     });
   }
   return cudaGetLastError();
@@ -690,18 +713,38 @@ static cudaError_t launch_intt_jobs(const DevTables *T, const DevTables &h, cons
   return cudaGetLastError();
 }
 
-u32 pm_groups(const DevTables &h, u32 segs, u32 seg_len) {
+// plaintexts per k_ks_mac_pm block
+u32 pm_chunk(u32 sp) { return sp <= 1 ? 1 : sp == 2 ? 2 : sp <= 4 ? 4 : 8; }
+
+u32 pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) {
   // row groups per segment: about four waves of 2048 threads per SM over
-  // the segs * L * N lanes, at most seg_len
-  u64 lanes = (u64)segs * h.L * h.N;
+  // the segs * L * N * (plaintext chunks) lanes, at most seg_len, and at
+  // most cap partial slots of [sp][2][L][N] in all
+  const u32 pcn = (sp + pm_chunk(sp) - 1) / pm_chunk(sp);
+  u64 lanes = (u64)segs * h.L * h.N * pcn;
   u64 g = (4 * 152ull * 2048 + lanes - 1) / lanes;
-  g = g < 1 ? 1 : g;
-  return (u32)(g < seg_len ? g : seg_len);
+  g = g < seg_len ? g : seg_len;
+  const u64 gcap = cap / ((u64)segs * sp);
+  g = g < gcap ? g : gcap;
+  return (u32)(g < 1 ? 1 : g);
+}
+
+template <int L>
+cudaError_t launch_mac_pm(dim3 grid, cudaStream_t st, const DevTables *T, const u64 *DN,
+                          u32 seg_len, u32 G, u32 sp, u32 pcn, const MulJob *jobs,
+                          const u64 *rlk, const u64 *rlk_s, const u64 *db, u64 *out) {
+  switch (pm_chunk(sp)) {
+    case 1: k_ks_mac_pm<L, 1><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
+    case 2: k_ks_mac_pm<L, 2><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
+    case 4: k_ks_mac_pm<L, 4><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
+    default: k_ks_mac_pm<L, 8><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                          u32 segs, const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
-                         const u64 *db, u64 *DN, u64 *out, cudaStream_t st) {
+                         const u64 *db, u32 sp, u32 cap, u64 *DN, u64 *out, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   const u64 LN = (u64)h.L * h.N;
   KsArgs A;
@@ -715,11 +758,17 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
   cudaError_t e = launch_ks_ntt(T, h, A, njobs, DN, st);
   if (e != cudaSuccess) return e;
   if (mode == ROOT_PM) {
-    const u32 seg_len = njobs / segs, G = pm_groups(h, segs, seg_len);
-    dim3 grid(h.N / 256, h.L, segs * G);
-    CW_DISPATCH_L(h.L, k_ks_mac_pm, grid, 256, 0, st, T, DN, 2u, seg_len, G, jobs, rlk, rlk_s, db,
-                  out);
-    return cudaGetLastError();
+    const u32 seg_len = njobs / segs, G = pm_groups(h, segs, seg_len, sp, cap);
+    const u32 pcn = (sp + pm_chunk(sp) - 1) / pm_chunk(sp);
+    dim3 grid(h.N / 256, h.L, segs * G * pcn);
+    switch (h.L) {
+#define CW_MAC_PM_CASE(LL) \
+  case LL: return launch_mac_pm<LL>(grid, st, T, DN, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out);
+      CW_MAC_PM_CASE(1) CW_MAC_PM_CASE(2) CW_MAC_PM_CASE(3) CW_MAC_PM_CASE(4)
+      CW_MAC_PM_CASE(5) CW_MAC_PM_CASE(6) CW_MAC_PM_CASE(7) CW_MAC_PM_CASE(8)
+#undef CW_MAC_PM_CASE
+      default: return cudaErrorInvalidValue;
+    }
   }
   dim3 grid(h.N / 256, h.L, njobs);
   const int internal = mode == INTERNAL ? 1 : 0;
@@ -730,21 +779,21 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
   return launch_intt_jobs(T, h, jobs, nullptr, njobs, 0, out, 1, nullptr, st);
 }
 
-u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len) {
-  return pm_groups(h, segs, seg_len);
+u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) {
+  return pm_groups(h, segs, seg_len, sp, cap);
 }
 
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
-                           u32 njobs, const u64 *db, u64 *P, cudaStream_t st) {
+                           u32 njobs, u32 sp, const u64 *db, u64 *P, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
-  k_pm_leaf<<<dim3(h.N / 256, h.L, njobs), 256, 0, st>>>(T, jobs, db, P);
+  k_pm_leaf<<<dim3(h.N / 256, sp * h.L, njobs), 256, 0, st>>>(T, jobs, sp, db, P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P, u32 segs,
-                              u32 per_seg, u64 *acc, cudaStream_t st) {
+                              u32 per_seg, u32 sp, u64 *acc, cudaStream_t st) {
   if (!segs || !per_seg) return cudaSuccess;
-  k_accumulate<<<dim3(h.N / 256, 2 * h.L, segs), 256, 0, st>>>(T, P, per_seg, acc);
+  k_accumulate<<<dim3(h.N / 256, 2 * h.L * sp, segs), 256, 0, st>>>(T, P, per_seg, sp, acc);
   return cudaGetLastError();
 }
 

@@ -40,8 +40,10 @@ enum RootMode : int {
 
 // ---- launchers (kernels.cu); all enqueue on `st` and return the launch
 // error.  Buffers are described in kernels.cu next to each kernel. ----
+// rows of plen payload coefficients, sp = ceil(plen / N) plaintexts each,
+// into db [rows][sp][L][N] (NTT form).
 cudaError_t launch_db_load(const DevTables *T, const DevTables &h, const u32 *items,
-                           u64 rows, u32 plen, u64 *db, cudaStream_t st);
+                           u64 rows, u32 plen, u32 sp, u64 *db, cudaStream_t st);
 cudaError_t launch_ntt(const DevTables *T, const DevTables &h, u64 *base, u32 units,
                        u64 unit_stride, u32 limb_begin, u32 limb_end, bool inverse,
                        const u64 *src, u64 src_unit_stride, cudaStream_t st);
@@ -58,20 +60,24 @@ cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf
                          u64 *E, int *err, cudaStream_t st);
 // Relinearisation of the scaled tensor E with its consumer.  DN: scratch
 // [njobs][L+2][L][N].  mode ROOT_PM: the jobs form `segs` equal segments
-// (one per query); out = partials [segs * G][2][L][N] with
-// G = relin_pm_groups(h, segs, njobs / segs) (sums of sel * DB over row
-// groups); INTERNAL: NTT-form Q limbs to jobs[].dst and coefficient form to
-// out ([njobs][2][L][N]); ROOT_SEL: coefficient form to jobs[].dst, out is
-// scratch [njobs][2][L][N].
+// (one per query), database rows hold sp plaintexts ([rows][sp][L][N]);
+// out = partials [segs * G][sp][2][L][N] with
+// G = relin_pm_groups(h, segs, njobs / segs, sp, cap) <= cap / (segs sp)
+// (sums of sel * DB over row groups); INTERNAL: NTT-form Q limbs to
+// jobs[].dst and coefficient form to out ([njobs][2][L][N]); ROOT_SEL:
+// coefficient form to jobs[].dst, out is scratch [njobs][2][L][N].
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                          u32 segs, const MulJob *jobs, int mode, const u64 *rlk,
-                         const u64 *rlk_s, const u64 *db, u64 *DN, u64 *out, cudaStream_t st);
-u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len);
+                         const u64 *rlk_s, const u64 *db, u32 sp, u32 cap, u64 *DN, u64 *out,
+                         cudaStream_t st);
+u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap);
+// k = 1: P[job][sp][2][L][N] = leaf * DB[row][p].
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
-                           u32 njobs, const u64 *db, u64 *P, cudaStream_t st);
-// acc[s] += sum of P[s * per_seg .. (s+1) * per_seg) for s < segs.
+                           u32 njobs, u32 sp, const u64 *db, u64 *P, cudaStream_t st);
+// acc[s] += sum of P[s * per_seg .. (s+1) * per_seg) for s < segs; each
+// entry is [sp][2][L][N].
 cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 *P, u32 segs,
-                              u32 per_seg, u64 *acc, cudaStream_t st);
+                              u32 per_seg, u32 sp, u64 *acc, cudaStream_t st);
 cudaError_t launch_automorph(const DevTables *T, const DevTables &h, const SubJob *jobs,
                              u32 njobs, u32 g, u64 *tau, cudaStream_t st);
 // Sub_g key switch: tau [njobs][2][L][N] (automorphism images) ->
