@@ -130,6 +130,7 @@ struct cwpir_ctx {
   // scratch
   u32 jmax = 0;
   DevBuf Tbuf, E, CP, DN, exp_tau, exp_DN, exp_O, tmp_ct, io_in, io_out;
+  DevBuf SEL;  // NTT-form selection entries [jmax][2][L][N] (rows of several plaintexts)
   bool capturing = false;
   int *d_err = nullptr;
   cw::SubJob *d_subjobs = nullptr;
@@ -361,6 +362,7 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
   if (root_mode == cw::ROOT_PM && (u64)nq * db->sp > J)
     return fail(c, CWPIR_EINVAL, "%u queries x %u plaintexts per row need more than %u partial "
                 "sums per launch (raise CWPIR_OPT_MAX_JOBS)", nq, db->sp, J);
+  if (db->sp > 1 && k > 1) CUDA_TRY(c, c->SEL.ensure((u64)J * ctw));
   CUDA_TRY(c, P->leaves.ensure((u64)nq * m * qp));
   CUDA_TRY(c, P->acc.ensure((u64)nq * db->sp * ctw));
   CUDA_TRY(c, P->q_in.ensure((u64)nq * P->h_in * ctw));
@@ -491,7 +493,7 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
     return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
-                            c->rlk_s.p, dbp, P->sp, c->jmax, c->DN.p, c->CP.p, st);
+                            c->rlk_s.p, dbp, P->sp, c->jmax, c->DN.p, c->SEL.p, c->CP.p, st);
   }));
   c->stats.kernel_launches += 4;  // tensor, scale, digit NTTs, key multiply-accumulate
   c->stats.mults += ch.count;
@@ -1212,6 +1214,7 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
   const bool memo = c->opt_share && top >= 2;
   const u64 h = cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
   w += (u64)nq * db->m * qp + 2ull * nq * db->sp * ctw + (u64)nq * h * ctw;
+  if (db->sp > 1 && db->k > 1 && c->SEL.n < J * ctw) w += J * ctw;
   if (memo) w += (u64)nq * db->n_pairs * qp;
   u64 widest = 1, internal_nodes = 0;
   for (u32 l = memo ? 2 : 1; l <= top; ++l) {
@@ -1276,6 +1279,7 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
       c->E.release();
       c->CP.release();
       c->DN.release();
+      c->SEL.release();
       for (auto &kv : c->dbs) kv.second->plans.clear();
       return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
@@ -1388,7 +1392,7 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
   CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
   CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
-                               c->rlk_s.p, nullptr, 1, 1, dn, ob, st));
+                               c->rlk_s.p, nullptr, 1, 1, dn, nullptr, ob, st));
   int h_err = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));

@@ -349,20 +349,30 @@ __device__ __forceinline__ void ks_mac(const u64 *DN, u64 job, u32 n_add, u32 j,
   }
 }
 
-// (B) for the answer's last level.  The launch's jobs form `segs` segments
-// of seg_len consecutive jobs (one segment per query); a database row holds
-// sp plaintexts ([row][sp][L][N]).  Block z = (s*G + g) * pcn + pc sums
-// (acc0, acc1) * DB[row][p] over jobs g, g+G, ... of segment s for the
-// plaintexts p of chunk pc (SP per chunk) into P[s*G + g][p][2][L][N]; the
-// key products are formed once per job and chunk.
-// grid (N/256, L, segs*G*pcn).
-template <int L, int SP>
+// Exact sum of products a * m of residues below q: 128-bit accumulation,
+// folded back below q every 15 terms (15 q^2 + q < 2^112).
+struct LazySum {
+  Acc128 acc;
+  __device__ __forceinline__ void mac(u64 a, u64 m) { acc.mac(a, m); }
+  __device__ __forceinline__ void fold(u64 q, u64 mu) {
+    acc.lo = barrett_reduce(acc.hi, acc.lo, q, mu);
+    acc.hi = 0;
+  }
+  __device__ __forceinline__ u64 value(u64 q, u64 mu) const {
+    return barrett_reduce(acc.hi, acc.lo, q, mu);
+  }
+};
+
+// (B) for the answer's last level, rows of one plaintext.  The launch's
+// jobs form `segs` segments of seg_len consecutive jobs (one segment per
+// query); block z = s*G + g sums (acc0, acc1) * DB[row] over jobs g, g+G,
+// ... of segment s into P[s*G + g][2][L][N].  grid (N/256, L, segs*G).
+template <int L>
 __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 seg_len, u32 G,
-                            u32 sp, u32 pcn, const MulJob *jobs, const u64 *key,
-                            const u64 *key_s, const u64 *db, u64 *P) {
+                            const MulJob *jobs, const u64 *key, const u64 *key_s,
+                            const u64 *db, u64 *P) {
   const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  const u32 pc = blockIdx.z % pcn, sg = blockIdx.z / pcn, seg = sg / G, g = sg % G;
-  const u32 p0 = pc * SP;
+  const u32 sg = blockIdx.z, seg = sg / G, g = sg % G;
   const NttPrime Pr = T->prime[j];
   const u64 q = Pr.q;
   const u64 LN = (u64)L * N;
@@ -375,29 +385,84 @@ __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 se
     ka[i] = key[oa];
     kas[i] = key_s[oa];
   }
-  u64 sum0[SP], sum1[SP];
-#pragma unroll
-  for (int p = 0; p < SP; ++p) sum0[p] = sum1[p] = 0;
-  for (u32 x = g; x < seg_len; x += G) {
-    const u64 job = (u64)seg * seg_len + x;
+  LazySum s0, s1;
+  u32 terms = 0;
+  // the next row's index is loaded one iteration ahead so that the row's
+  // database load issues together with the digit loads
+  u64 job = (u64)seg * seg_len + g;
+  u64 row = g < seg_len ? jobs[job].row : 0;
+  for (u32 x = g; x < seg_len; x += G, job += G) {
+    const u64 m = db[row * LN + (u64)j * N + c];
+    if (x + G < seg_len) row = jobs[job + G].row;
     u64 a0, a1;
     ks_mac<L>(DN, job, n_add, j, c, N, kb, kbs, ka, kas, q, a0, a1);
-    const u64 *dr = db + ((u64)jobs[job].row * sp + p0) * LN + (u64)j * N + c;
+    s0.mac(a0, m);
+    s1.mac(a1, m);
+    if (++terms == 15) {
+      s0.fold(q, Pr.mu);
+      s1.fold(q, Pr.mu);
+      terms = 1;  // the folded residue counts as one term
+    }
+  }
+  u64 *o = P + (u64)sg * 2 * LN + (u64)j * N + c;
+  o[0] = s0.value(q, Pr.mu);
+  o[LN] = s1.value(q, Pr.mu);
+}
+
+// Rows of sp > 1 plaintexts: the selection entries of the launch's jobs are
+// first formed in NTT form (k_ks_mac_out into S[job][2][L][N]); block
+// z = (s*G + g) * pcn + pc then sums S[job] * DB[row][p] over jobs g, g+G,
+// ... of segment s for the plaintexts p of chunk pc (at most PPT) into
+// P[s*G + g][p][2][L][N].  Two rows are loaded ahead of their products.
+// grid (N/256, L, segs*G*pcn).
+template <int PPT>
+__global__ void k_pm_rows(const DevTables *T, const u64 *S, u32 seg_len, u32 G, u32 sp,
+                          u32 pcn, const MulJob *jobs, const u64 *db, u64 *P) {
+  const u32 N = T->N, L = T->L, c = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  const u32 pc = blockIdx.z % pcn, sg = blockIdx.z / pcn, seg = sg / G, g = sg % G;
+  const u32 per = (sp + pcn - 1) / pcn, p0 = pc * per;
+  const u32 np = sp - p0 < per ? sp - p0 : per;
+  const NttPrime Pr = T->prime[j];
+  const u64 q = Pr.q;
+  const u64 LN = (u64)L * N, off = (u64)j * N + c;
+  LazySum s0[PPT], s1[PPT];
+  u32 terms = 0;
+  u64 job = (u64)seg * seg_len + g;
+  for (u32 x = g; x < seg_len; x += 2 * G, job += 2 * G) {
+    const bool two = x + G < seg_len;
+    const u64 r0 = jobs[job].row, r1 = two ? jobs[job + G].row : r0;
+    const u64 *e0 = S + job * 2 * LN + off, *e1 = S + (two ? job + G : job) * 2 * LN + off;
+    const u64 a00 = e0[0], a01 = e0[LN], a10 = e1[0], a11 = e1[LN];
+    const u64 *d0 = db + (r0 * sp + p0) * LN + off, *d1 = db + (r1 * sp + p0) * LN + off;
+    u64 m0[PPT], m1[PPT];
 #pragma unroll
-    for (int p = 0; p < SP; ++p) {
-      if (p0 + p < sp) {
-        const u64 m = dr[(u64)p * LN];
-        sum0[p] = addq(sum0[p], barrett(a0, m, q, Pr.mu), q);
-        sum1[p] = addq(sum1[p], barrett(a1, m, q, Pr.mu), q);
+    for (int k = 0; k < PPT; ++k) {
+      m0[k] = (u32)k < np ? d0[k * LN] : 0;
+      m1[k] = (u32)k < np && two ? d1[k * LN] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      s0[k].mac(a00, m0[k]);
+      s1[k].mac(a01, m0[k]);
+      s0[k].mac(a10, m1[k]);
+      s1[k].mac(a11, m1[k]);
+    }
+    terms += 2;
+    if (terms >= 14) {
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        s0[k].fold(q, Pr.mu);
+        s1[k].fold(q, Pr.mu);
       }
+      terms = 1;
     }
   }
 #pragma unroll
-  for (int p = 0; p < SP; ++p) {
-    if (p0 + p < sp) {
-      u64 *o = P + ((u64)sg * sp + p0 + p) * 2 * LN + (u64)j * N + c;
-      o[0] = sum0[p];
-      o[LN] = sum1[p];
+  for (int k = 0; k < PPT; ++k) {
+    if ((u32)k < np) {
+      u64 *o = P + ((u64)sg * sp + p0 + k) * 2 * LN + off;
+      o[0] = s0[k].value(q, Pr.mu);
+      o[LN] = s1[k].value(q, Pr.mu);
     }
   }
 }
@@ -713,15 +778,15 @@ static cudaError_t launch_intt_jobs(const DevTables *T, const DevTables &h, cons
   return cudaGetLastError();
 }
 
-// plaintexts per k_ks_mac_pm block
-u32 pm_chunk(u32 sp) { return sp <= 1 ? 1 : sp == 2 ? 2 : sp <= 4 ? 4 : 8; }
+// plaintexts per k_pm_rows thread (PPT) and the chunks covering sp
+constexpr u32 kPmPPT = 2;  // fewer per thread keeps more warps resident
+u32 pm_chunks(u32 sp) { return sp <= 1 ? 1 : (sp + kPmPPT - 1) / kPmPPT; }
 
 u32 pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) {
   // row groups per segment: about four waves of 2048 threads per SM over
-  // the segs * L * N * (plaintext chunks) lanes, at most seg_len, and at
+  // the segs * L * N * (plaintext chunks) threads, at most seg_len, and at
   // most cap partial slots of [sp][2][L][N] in all
-  const u32 pcn = (sp + pm_chunk(sp) - 1) / pm_chunk(sp);
-  u64 lanes = (u64)segs * h.L * h.N * pcn;
+  u64 lanes = (u64)segs * h.L * h.N * pm_chunks(sp);
   u64 g = (4 * 152ull * 2048 + lanes - 1) / lanes;
   g = g < seg_len ? g : seg_len;
   const u64 gcap = cap / ((u64)segs * sp);
@@ -729,22 +794,10 @@ u32 pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) {
   return (u32)(g < 1 ? 1 : g);
 }
 
-template <int L>
-cudaError_t launch_mac_pm(dim3 grid, cudaStream_t st, const DevTables *T, const u64 *DN,
-                          u32 seg_len, u32 G, u32 sp, u32 pcn, const MulJob *jobs,
-                          const u64 *rlk, const u64 *rlk_s, const u64 *db, u64 *out) {
-  switch (pm_chunk(sp)) {
-    case 1: k_ks_mac_pm<L, 1><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
-    case 2: k_ks_mac_pm<L, 2><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
-    case 4: k_ks_mac_pm<L, 4><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
-    default: k_ks_mac_pm<L, 8><<<grid, 256, 0, st>>>(T, DN, 2u, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out); break;
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                          u32 segs, const MulJob *jobs, int mode, const u64 *rlk, const u64 *rlk_s,
-                         const u64 *db, u32 sp, u32 cap, u64 *DN, u64 *out, cudaStream_t st) {
+                         const u64 *db, u32 sp, u32 cap, u64 *DN, u64 *S, u64 *out,
+                         cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   const u64 LN = (u64)h.L * h.N;
   KsArgs A;
@@ -759,16 +812,21 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
   if (e != cudaSuccess) return e;
   if (mode == ROOT_PM) {
     const u32 seg_len = njobs / segs, G = pm_groups(h, segs, seg_len, sp, cap);
-    const u32 pcn = (sp + pm_chunk(sp) - 1) / pm_chunk(sp);
-    dim3 grid(h.N / 256, h.L, segs * G * pcn);
-    switch (h.L) {
-#define CW_MAC_PM_CASE(LL) \
-  case LL: return launch_mac_pm<LL>(grid, st, T, DN, seg_len, G, sp, pcn, jobs, rlk, rlk_s, db, out);
-      CW_MAC_PM_CASE(1) CW_MAC_PM_CASE(2) CW_MAC_PM_CASE(3) CW_MAC_PM_CASE(4)
-      CW_MAC_PM_CASE(5) CW_MAC_PM_CASE(6) CW_MAC_PM_CASE(7) CW_MAC_PM_CASE(8)
-#undef CW_MAC_PM_CASE
-      default: return cudaErrorInvalidValue;
+    if (sp == 1) {
+      dim3 grid(h.N / 256, h.L, segs * G);
+      CW_DISPATCH_L(h.L, k_ks_mac_pm, grid, 256, 0, st, T, DN, 2u, seg_len, G, jobs, rlk, rlk_s,
+                    db, out);
+      return cudaGetLastError();
     }
+    // selection entries in NTT form into S, then the rows' plaintexts
+    dim3 grid_s(h.N / 256, h.L, njobs);
+    CW_DISPATCH_L(h.L, k_ks_mac_out, grid_s, 256, 0, st, T, DN, 2u, jobs, 0, rlk, rlk_s, S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const u32 pcn = pm_chunks(sp);
+    k_pm_rows<kPmPPT><<<dim3(h.N / 256, h.L, segs * G * pcn), 256, 0, st>>>(
+        T, S, seg_len, G, sp, pcn, jobs, db, out);
+    return cudaGetLastError();
   }
   dim3 grid(h.N / 256, h.L, njobs);
   const int internal = mode == INTERNAL ? 1 : 0;

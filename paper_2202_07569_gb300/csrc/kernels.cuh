@@ -63,13 +63,14 @@ cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf
 // (one per query), database rows hold sp plaintexts ([rows][sp][L][N]);
 // out = partials [segs * G][sp][2][L][N] with
 // G = relin_pm_groups(h, segs, njobs / segs, sp, cap) <= cap / (segs sp)
-// (sums of sel * DB over row groups); INTERNAL: NTT-form Q limbs to
-// jobs[].dst and coefficient form to out ([njobs][2][L][N]); ROOT_SEL:
-// coefficient form to jobs[].dst, out is scratch [njobs][2][L][N].
+// (sums of sel * DB over row groups); with sp > 1, S is scratch
+// [njobs][2][L][N] for the NTT-form selection entries.  INTERNAL: NTT-form
+// Q limbs to jobs[].dst and coefficient form to out ([njobs][2][L][N]);
+// ROOT_SEL: coefficient form to jobs[].dst, out is scratch [njobs][2][L][N].
 cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                          u32 segs, const MulJob *jobs, int mode, const u64 *rlk,
-                         const u64 *rlk_s, const u64 *db, u32 sp, u32 cap, u64 *DN, u64 *out,
-                         cudaStream_t st);
+                         const u64 *rlk_s, const u64 *db, u32 sp, u32 cap, u64 *DN, u64 *S,
+                         u64 *out, cudaStream_t st);
 u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap);
 // k = 1: P[job][sp][2][L][N] = leaf * DB[row][p].
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
