@@ -86,6 +86,36 @@ struct Acc128 {
   }
 };
 
+// Exact sum of a few products a * b with a < 2^55 and constants b < 2^54
+// given as 27-bit halves (b = b1 2^27 + b0): with a = a1 2^27 + a0 each
+// product is four 32 x 32 + 64 multiply-adds into the words
+// ll = sum a0 b0, x = sum (a0 b1 + a1 b0), hh = sum a1 b1 (partials below
+// 2^55, so up to 8 terms cannot overflow 64 bits), and the sum is
+// ll + x 2^27 + hh 2^54.
+constexpr u32 kMask27 = (1u << 27) - 1;
+CW_HD void split27(u64 b, u32 *out) {
+  out[0] = (u32)b & kMask27;
+  out[1] = (u32)(b >> 27);
+}
+struct Acc3 {
+  u64 ll = 0, x = 0, hh = 0;
+  CW_HDM void mac(u64 a, const u32 *b) {
+    const u32 a0 = (u32)a & kMask27, a1 = (u32)(a >> 27);
+    ll += (u64)a0 * b[0];
+    x += (u64)a0 * b[1];
+    x += (u64)a1 * b[0];
+    hh += (u64)a1 * b[1];
+  }
+  CW_HDM void add(u64 v) { ll += v; }
+  // the sum as hi 2^64 + lo (the caller bounds it below 2^112)
+  CW_HDM void get(u64 &hi, u64 &lo) const {
+    const u64 l1 = ll + (x << 27);
+    const u64 l2 = l1 + (hh << 54);
+    hi = (x >> 37) + (hh >> 10) + (l1 < ll ? 1 : 0) + (l2 < l1 ? 1 : 0);
+    lo = l2;
+  }
+};
+
 // ---------------------------------------------------------------------
 // NTT butterflies (negacyclic, psi = primitive 2N-th root of unity).
 // Twiddles are stored as (value, Shoup companion) pairs.
@@ -219,6 +249,9 @@ struct ScaleTab {
   u64 Cr[kMaxK];         // (P/p_k)^-1 mod p_k
   BaseConv q2b;  // Q -> P conversion data (fraction and Garner parts used)
   BaseConv b2q;  // P -> Q conversion
+  // the constants of the two multiply-accumulate stages as 27-bit halves
+  u32 A2[kMaxK][2], B2[kMaxL][kMaxK][2], Cr2[kMaxK][2];
+  u32 hat2[kMaxK][kMaxL][2], negs2[kMaxL][2];  // b2q.hat[k][j], b2q.negsmod[j]
 };
 
 // dq, dp: residues of f*d below 2^55 (lazy [0, 2q) values are fine).
@@ -238,21 +271,26 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
       eps[j] = shoup(dq[j], S.t_mod[j], S.t_mod_s[j], S.q2b.s[j]);
     rho += mr_greater_half<L>(eps, S.q2b);
   }
+  // L + 2 and K + 1 products below 2^55 * 2^54 each: sums below 2^112
   u64 yb[K];
   for (int k = 0; k < K; ++k) {
-    Acc128 a;
-    a.mac(dp[k], S.A[k]);
-    for (int j = 0; j < L; ++j) a.mac(y[j], S.B[j][k]);
-    a.mac(rho, S.Cr[k]);
-    yb[k] = barrett_reduce(a.hi, a.lo, S.b2q.s[k], S.q2b.d_mu[k]);
+    Acc3 a;
+    a.mac(dp[k], S.A2[k]);
+    for (int j = 0; j < L; ++j) a.mac(y[j], S.B2[j][k]);
+    a.mac(rho, S.Cr2[k]);
+    u64 hi, lo;
+    a.get(hi, lo);
+    yb[k] = barrett_reduce(hi, lo, S.b2q.s[k], S.q2b.d_mu[k]);
   }
   bool amb2;
   u64 rho2 = round_sum<K>(yb, S.b2q, &amb2);
   for (int j = 0; j < L; ++j) {
-    Acc128 a;
-    for (int k = 0; k < K; ++k) a.mac(yb[k], S.b2q.hat[k][j]);
-    a.mac(rho2, S.b2q.negsmod[j]);
-    out[j] = barrett_reduce(a.hi, a.lo, S.b2q.d[j], S.b2q.d_mu[j]);
+    Acc3 a;
+    for (int k = 0; k < K; ++k) a.mac(yb[k], S.hat2[k][j]);
+    a.mac(rho2, S.negs2[j]);
+    u64 hi, lo;
+    a.get(hi, lo);
+    out[j] = barrett_reduce(hi, lo, S.b2q.d[j], S.b2q.d_mu[j]);
   }
   return !amb2;
 }

@@ -173,6 +173,15 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
       S.B[j][k] = v ? pk - v : 0;
     }
   }
+  for (u32 k = 0; k < K; ++k) {
+    split27(S.A[k], S.A2[k]);
+    split27(S.Cr[k], S.Cr2[k]);
+    for (u32 j = 0; j < L; ++j) {
+      split27(S.B[j][k], S.B2[j][k]);
+      split27(S.b2q.hat[k][j], S.hat2[k][j]);
+    }
+  }
+  for (u32 j = 0; j < L; ++j) split27(S.b2q.negsmod[j], S.negs2[j]);
 }
 
 }  // namespace host
