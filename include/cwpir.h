@@ -96,6 +96,16 @@ int cwpir_default_primes(uint32_t N, uint32_t L, uint64_t *q_out);
  * x-th codeword of CW(m,k); writes its k one-positions in ascending order.
  * EINVAL if x >= C(m,k), k = 0, k > m or m > 65535. */
 int cwpir_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out);
+/* Lossy mapping (Alg. Lossy Mapping, App. A) for domains too large for a
+ * perfect mapping: draws H_1(x), H_2(x), ... in [m] and sets each new
+ * position until k are set; writes the k positions in ascending order.
+ * H_i(x) = (i-th output of a SplitMix64 generator seeded with x) mod m
+ * (Steele, Lea, Flood 2014: mix64(x + i * 0x9E3779B97F4A7C15)); not keyed,
+ * not cryptographic.  Two different x share a codeword with probability
+ * 1 / C(m,k) (Theorem lossy-coll-prob); rows whose codewords coincide are
+ * both selected by a query for either, so callers resolve collisions
+ * before cwpir_load_db.  EINVAL if k = 0, k > m or m > 65535. */
+int cwpir_map_lossy(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out);
 /* Smallest m with C(m,k) >= n (Sec. 3: "choose m such that C(m,k) >= n"). */
 int cwpir_code_length(uint64_t n, uint32_t k, uint32_t *m_out);
 

@@ -84,6 +84,7 @@ def lib():
                                 C.POINTER(C.c_double)]),
             "orc_binom": (None, [U64, U64, C.POINTER(U64), C.POINTER(U64)]),
             "orc_map_perfect": (I, [U64, U32, U32, u16p]),
+            "orc_map_lossy": (I, [U64, U32, U32, u16p]),
             "orc_map_inverse": (I, [u16p, U32, C.POINTER(U64)]),
             "orc_code_length": (U64, [U32, U32, U64]),
         }
@@ -131,6 +132,12 @@ def binom(n: int, r: int) -> int:
 def map_perfect(x: int, m: int, k: int) -> np.ndarray:
     pos = np.zeros(k, np.uint16)
     _check(lib().orc_map_perfect(x, m, k, pos), "perfect map")
+    return pos
+
+
+def map_lossy(x: int, m: int, k: int) -> np.ndarray:
+    pos = np.zeros(k, np.uint16)
+    _check(lib().orc_map_lossy(x, m, k, pos), "lossy map")
     return pos
 
 

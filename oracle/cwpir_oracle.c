@@ -1198,6 +1198,36 @@ int orc_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos) {
   return h == 0 ? 0 : -3;
 }
 
+/* Alg. Lossy Mapping (App. A).  The hash family: H_i(x) is the i-th output
+ * of a SplitMix64 generator seeded with x, reduced mod m.  SplitMix64 keeps
+ * a 64-bit state that advances by the odd constant 0x9E3779B97F4A7C15 and
+ * returns the state passed through a xor-shift-multiply mixer. */
+static uint64_t orc_splitmix_next(uint64_t *state) {
+  uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int orc_map_lossy(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos) {
+  if (k == 0 || k > m || m > 65535) return -1;
+  unsigned char *y = calloc(m, 1); /* the codeword y = 0^m */
+  uint64_t state = x;
+  uint32_t cnt = 0;
+  for (uint64_t draws = 0; cnt < k && draws < 64ull * m + 1024; ++draws) {
+    uint32_t mp = (uint32_t)(orc_splitmix_next(&state) % m); /* m' = H_i(x) */
+    if (y[mp] == 0) {
+      y[mp] = 1;
+      cnt += 1;
+    }
+  }
+  uint32_t h = 0;
+  for (uint32_t i = 0; i < m && cnt == k; ++i)
+    if (y[i]) pos[h++] = (uint16_t)i;
+  free(y);
+  return cnt == k ? 0 : -2;
+}
+
 /* Alg. Inverse Perfect Mapping: x = sum over ascending one-positions m' of
  * C(m', h) with h = 1, 2, ... */
 int orc_map_inverse(const uint16_t *pos, uint32_t k, uint64_t *x) {

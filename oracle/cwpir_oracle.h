@@ -133,6 +133,9 @@ int orc_decrypt(const orc_ctx *ctx, const uint64_t *ct, uint32_t size,
 void orc_binom(uint64_t n, uint64_t r, uint64_t *lo, uint64_t *hi);
 /* Perfect mapping x -> CW(m,k); writes the k one-positions ascending. */
 int orc_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos);
+/* Alg. Lossy Mapping (App. A) with H_i(x) = i-th SplitMix64 output of
+ * seed x, mod m; ascending positions. */
+int orc_map_lossy(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos);
 /* Inverse perfect mapping of k ascending positions. */
 int orc_map_inverse(const uint16_t *pos, uint32_t k, uint64_t *x);
 /* Smallest m with C(m,k) >= 2^bits (bits <= 64), or 0 if m > limit. */

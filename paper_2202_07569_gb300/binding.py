@@ -91,6 +91,7 @@ def lib():
             "cwpir_last_error": (C.c_char_p, [vp]),
             "cwpir_default_primes": (I, [U32, U32, u64p]),
             "cwpir_map_perfect": (I, [U64, U32, U32, u16p]),
+            "cwpir_map_lossy": (I, [U64, U32, U32, u16p]),
             "cwpir_code_length": (I, [U64, U32, C.POINTER(U32)]),
             "cwpir_setup": (I, [C.POINTER(_Params), C.POINTER(_Keys), C.POINTER(vp)]),
             "cwpir_destroy": (None, [vp]),
@@ -156,6 +157,15 @@ def map_perfect(x: int, m: int, k: int) -> np.ndarray:
     rc = lib().cwpir_map_perfect(int(x), m, k, pos)
     if rc:
         raise CwpirError(rc, f"perfect mapping of {x} into CW({m},{k})")
+    return pos
+
+
+def map_lossy(x: int, m: int, k: int) -> np.ndarray:
+    """Alg. Lossy Mapping of a 64-bit element into CW(m, k)."""
+    pos = np.zeros(k, np.uint16)
+    rc = lib().cwpir_map_lossy(int(x), m, k, pos)
+    if rc:
+        raise CwpirError(rc, f"lossy mapping of {x} into CW({m},{k})")
     return pos
 
 

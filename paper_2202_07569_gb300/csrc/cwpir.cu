@@ -753,6 +753,36 @@ int cwpir_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out) {
   return h == 0 ? CWPIR_OK : CWPIR_EINVAL;
 }
 
+// Alg. Lossy Mapping (App. A): draw positions H_1(x), H_2(x), ... and keep
+// each new one until k are set.  H_i(x) = (i-th output of SplitMix64 seeded
+// with x) mod m, i.e. mix64(x + i * 0x9E3779B97F4A7C15) mod m with the
+// SplitMix64 output mixer.
+static u64 splitmix64_output(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int cwpir_map_lossy(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out) {
+  if (!pos_out || k == 0 || k > m || m > 65535) return CWPIR_EINVAL;
+  std::vector<char> set(m, 0);
+  u32 cnt = 0;
+  // a bound on the draws: reached with probability below 2^-60 for any k <= m
+  const u64 limit = 64ull * m + 1024;
+  for (u64 i = 1; cnt < k && i <= limit; ++i) {
+    const u32 mp = (u32)(splitmix64_output(x + i * 0x9E3779B97F4A7C15ull) % m);
+    if (!set[mp]) {
+      set[mp] = 1;
+      ++cnt;
+    }
+  }
+  if (cnt < k) return CWPIR_EINVAL;
+  u32 h = 0;
+  for (u32 mp = 0; mp < m; ++mp)
+    if (set[mp]) pos_out[h++] = (uint16_t)mp;
+  return CWPIR_OK;
+}
+
 int cwpir_code_length(uint64_t n, uint32_t k, uint32_t *m_out) {
   if (!m_out || k == 0 || k > 64) return CWPIR_EINVAL;
   for (u64 m = k; m <= 65535; ++m)

@@ -51,3 +51,8 @@ def test_host_helpers_match_definitions(cudalib, orc):
     assert B.code_length(1 << 32, 8) == 64
     with pytest.raises(B.CwpirError):
         B.map_perfect(math.comb(24, 2), 24, 2)
+    for m, k in ((64, 8), (9, 2), (16, 16)):
+        for x in (0, 1, 12345, (1 << 64) - 1, 0x0123456789ABCDEF):
+            assert B.map_lossy(x, m, k).tolist() == orc.map_lossy(x, m, k).tolist()
+    with pytest.raises(B.CwpirError):
+        B.map_lossy(5, 4, 5)

@@ -279,3 +279,40 @@ def test_errors_are_reported():
     cw[1] = cw[1][::-1]
     with pytest.raises(B.CwpirError):
         cl.ctx.load_db(items, cw, 4)
+
+
+def test_keyword_pir_lossy_mapping_64bit_keywords():
+    """Alg. Lossy Mapping for a domain beyond a perfect mapping's reach:
+    64-bit keywords mapped into CW(12, 3) (220 codewords) with compressed
+    queries.  Keywords whose codewords collide are left out of the database
+    (they would be selected together); present keywords return their row,
+    an absent keyword's codeword not in the database returns zeros, and the
+    responses equal the oracle's bit for bit."""
+    from paper_2202_07569_gb300 import binding as B
+
+    N, L, k, m, c = 8192, 4, 3, 12, 2
+    cl = Client(N, L, seed=75, c_max=c)
+    ctx = cl.context()
+    st = syn.Stream(76)
+    words = [int(w) for w in st.words(40)]
+    cws, keep = {}, []
+    for w in words:
+        key = tuple(B.map_lossy(w, m, k).tolist())
+        if key not in cws:
+            cws[key] = w
+            keep.append(w)
+    items = syn.payload(st, len(keep), 300, 1 << 16)
+    cw = np.stack([B.map_lossy(w, m, k) for w in keep])
+    db = ctx.load_db(items, cw, m)
+    absent = next(int(w) for w in st.words(1000)
+                  if tuple(B.map_lossy(int(w), m, k).tolist()) not in cws)
+    for i, w in ((0, keep[0]), (len(keep) - 1, keep[-1]), (None, absent)):
+        q = cl.query(oracle.map_lossy(w, m, k), m, c, stream=77 + (i or 0))
+        got = ctx.answer(db, q, c)
+        assert np.array_equal(got, cl.O.answer(items, cw, m, q, cl.rlk, c=c, gkeys=cl.gkeys))
+        mu, budget = cl.decrypt(got)
+        want = np.zeros(N, np.uint32)
+        if i is not None:
+            want[:300] = items[i]
+        assert np.array_equal(mu, want) and budget > 0
+    ctx.close()

@@ -465,6 +465,59 @@ def read_golden(name):
     return rows
 
 
+def splitmix64_outputs(seed: int, count: int):
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) from its definition:
+    the 64-bit state advances by 0x9E3779B97F4A7C15 and each output is the
+    state through the xor-shift-multiply finaliser."""
+    mask = (1 << 64) - 1
+    st, out = seed, []
+    for _ in range(count):
+        st = (st + 0x9E3779B97F4A7C15) & mask
+        z = ((st ^ (st >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        out.append(z ^ (z >> 31))
+    return out
+
+
+@pytest.mark.parametrize("m,k", [(8, 2), (12, 5), (64, 8), (5, 5)])
+def test_lossy_mapping_keeps_first_k_distinct_hash_positions(orc, m, k):
+    """Alg. Lossy Mapping (App. A): the codeword's positions are the first k
+    distinct values of H_1(x), H_2(x), ... (here the SplitMix64 outputs of
+    seed x, mod m), ascending; exactly k positions below m."""
+    st = syn.Stream(71)
+    xs = [int(v) for v in st.words(200)] + [0, 1, (1 << 64) - 1]
+    for x in xs:
+        want = []
+        for h in splitmix64_outputs(x, 64 * m + 1024):
+            if h % m not in want:
+                want.append(h % m)
+            if len(want) == k:
+                break
+        assert orc.map_lossy(x, m, k).tolist() == sorted(want)
+
+
+@pytest.mark.parametrize("m,k", [(8, 2), (7, 3), (10, 4)])
+def test_lossy_mapping_codewords_are_uniform(orc, m, k):
+    """Theorem lossy-coll-prob: every codeword of CW(m,k) is hit with
+    probability 1/C(m,k), so two different elements collide with that
+    probability.  Chi-square of 100000 mapped elements against the uniform
+    distribution (bound about 8 standard deviations above its mean), and the
+    pairwise collision rate within 10% of 1/C(m,k)."""
+    from collections import Counter
+
+    n = 100000
+    xs = syn.Stream(72).words(n)
+    cnt = Counter(tuple(orc.map_lossy(int(x), m, k).tolist()) for x in xs)
+    cells = math.comb(m, k)
+    assert len(cnt) == cells
+    exp = n / cells
+    chi2 = sum((cnt.get(c, 0) - exp) ** 2 / exp for c in cnt)
+    df = cells - 1
+    assert chi2 < df + 8 * math.sqrt(2 * df), chi2
+    coll = sum(v * (v - 1) for v in cnt.values()) / (n * (n - 1))
+    assert abs(coll * cells - 1) < 0.1, coll * cells
+
+
 def test_code_lengths_reproduce_paper_encoding_size_table(orc):
     for row in read_golden("encoding_size.txt"):
         bits = int(row[0])
