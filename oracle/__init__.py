@@ -71,6 +71,8 @@ def lib():
             "orc_expand": (I, [vp, U32, u64p, U32, U32, u64p, u64p]),
             "orc_expand_sealpir": (I, [vp, u64p, U32, u64p, u64p]),
             "orc_scalar_mul": (I, [vp, u64p, U64, u64p]),
+            "orc_one_minus": (I, [vp, u64p, u64p]),
+            "orc_folklore_codeword": (I, [U64, U32, u16p]),
             "orc_plain_mul": (I, [vp, u64p, u32p, U32, u64p]),
             "orc_selection": (I, [vp, u64p, u16p, U32, u64p, u64p]),
             "orc_answer": (I, [vp, U64, U32, u32p, u16p, U32, U32, U32, u64p,
@@ -138,6 +140,12 @@ def map_perfect(x: int, m: int, k: int) -> np.ndarray:
 def map_lossy(x: int, m: int, k: int) -> np.ndarray:
     pos = np.zeros(k, np.uint16)
     _check(lib().orc_map_lossy(x, m, k, pos), "lossy map")
+    return pos
+
+
+def folklore_codeword(y: int, ell: int) -> np.ndarray:
+    pos = np.zeros(ell, np.uint16)
+    _check(lib().orc_folklore_codeword(y, ell, pos), "folklore codeword")
     return pos
 
 
@@ -263,6 +271,16 @@ class Oracle:
         out = np.zeros(self.ct_shape, np.uint64)
         _check(lib().orc_scalar_mul(self._ctx, self._ct(ct), scalar, out), "scalar")
         return out
+
+    def one_minus(self, ct) -> np.ndarray:
+        out = np.zeros(self.ct_shape, np.uint64)
+        _check(lib().orc_one_minus(self._ctx, self._ct(ct), out), "one minus")
+        return out
+
+    def folklore_leaves(self, query) -> np.ndarray:
+        """(1 - x[0], x[0], 1 - x[1], x[1], ...) from the ell bit ciphertexts."""
+        query = _c(query, np.uint64)
+        return np.stack([v for ct in query for v in (self.one_minus(ct), ct)])
 
     def plain_mul(self, ct, mu) -> np.ndarray:
         mu = _c(mu, np.uint32)

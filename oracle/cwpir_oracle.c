@@ -849,6 +849,36 @@ int orc_scalar_mul(const orc_ctx *c, const uint64_t *ct, uint64_t scalar,
   return 0;
 }
 
+/* Homomorphic 1 - mu: the constant plaintext 1 minus the ciphertext,
+ * (Delta * 1 - c0, -c1) in R_Q; decrypts to 1 - mu (mod t) with the noise
+ * negated.  The factor (1 - x[i]) of Eq. folklore-plain-eq. */
+int orc_one_minus(const orc_ctx *c, const uint64_t *ct, uint64_t *out) {
+  size_t ln = LN(c);
+  for (uint32_t j = 0; j < c->L; ++j) {
+    uint64_t q = c->q[j];
+    for (uint32_t i = 0; i < c->N; ++i) {
+      size_t x = (size_t)j * c->N + i;
+      uint64_t c0 = ct[x], c1 = ct[ln + x];
+      uint64_t d = i == 0 ? c->delta_mod[j] : 0; /* Delta times the constant 1 */
+      out[x] = d >= c0 ? d - c0 : d + q - c0;
+      out[ln + x] = c1 ? q - c1 : 0;
+    }
+  }
+  return 0;
+}
+
+/* Leaves of the plain folklore operator (Eq. folklore-plain-eq) for an
+ * ell-bit public operand y: the factor of bit i is (1 - x[i]) when y[i] = 0
+ * and x[i] when y[i] = 1.  With the 2*ell leaves ordered
+ * (1 - x[0], x[0], 1 - x[1], x[1], ...), the factors of y sit at positions
+ * 2i + y[i], ascending, so the product is a selection over a weight-ell
+ * codeword of length 2*ell. */
+int orc_folklore_codeword(uint64_t y, uint32_t ell, uint16_t *pos) {
+  if (ell == 0 || ell > 64 || (ell < 64 && (y >> ell))) return -1;
+  for (uint32_t i = 0; i < ell; ++i) pos[i] = (uint16_t)(2 * i + ((y >> i) & 1));
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Plain multiplication, selection vector, answer                      */
 /* ------------------------------------------------------------------ */

@@ -84,6 +84,11 @@ int orc_expand_sealpir(const orc_ctx *ctx, const uint64_t *ct, uint32_t c,
 /* Multiply a ciphertext by an integer scalar in [0, t). */
 int orc_scalar_mul(const orc_ctx *ctx, const uint64_t *ct, uint64_t scalar,
                    uint64_t *out);
+/* (Delta - c0, -c1): the constant plaintext 1 minus ct (decrypts to 1 - mu). */
+int orc_one_minus(const orc_ctx *ctx, const uint64_t *ct, uint64_t *out);
+/* Positions 2i + y[i], i < ell, of the plain folklore operator's factors
+ * among the leaves (1 - x[0], x[0], 1 - x[1], x[1], ...). */
+int orc_folklore_codeword(uint64_t y, uint32_t ell, uint16_t *pos);
 /* Plain multiplication by an item plaintext (payload_len coefficients < t,
  * zero-padded, centered lift). */
 int orc_plain_mul(const orc_ctx *ctx, const uint64_t *ct, const uint32_t *mu,

@@ -349,6 +349,39 @@ def test_cw_equality_operator_brute_force(orc, m, k):
             assert budget > 0
 
 
+def test_one_minus_decrypts_to_complement(orc):
+    """The factor (1 - x[i]) of Eq. folklore-plain-eq: the constant plaintext
+    1 minus a ciphertext of mu decrypts to 1 - mu (mod t), coefficient-wise."""
+    N = 64
+    O, q, cd, rlk = small_setup(orc, N, 2)
+    mu = syn.payload(syn.Stream(81), 1, N, T)[0]
+    ct = encrypt_many(O, cd, [mu], stream=5)[0]
+    got, budget = O.decrypt(O.one_minus(ct), cd.s)
+    want = [(-int(v)) % T for v in mu]
+    want[0] = (1 - int(mu[0])) % T
+    assert got.tolist() == want and budget > 0
+
+
+@pytest.mark.parametrize("ell", [1, 3])
+def test_folklore_equality_operator_brute_force(orc, ell):
+    """Eq. folklore-plain-eq: prod_{y[i]=0} (1 - Enc(x[i])) prod_{y[i]=1}
+    Enc(x[i]) decrypts to 1 iff x == y, for every pair of ell-bit values."""
+    N = 16
+    O, q, cd, rlk = small_setup(orc, N, 3)
+    for x in range(1 << ell):
+        mus = []
+        for i in range(ell):
+            v = np.zeros(N, np.uint32)
+            v[0] = (x >> i) & 1
+            mus.append(v)
+        leaves = O.folklore_leaves(np.stack(encrypt_many(O, cd, mus, stream=90 + x)))
+        for y in range(1 << ell):
+            pos = orc.folklore_codeword(y, ell)
+            assert pos.tolist() == [2 * i + ((y >> i) & 1) for i in range(ell)]
+            got, budget = O.decrypt(O.selection(leaves, pos, rlk), cd.s)
+            assert got[0] == (1 if x == y else 0) and not got[1:].any() and budget > 0
+
+
 # ------------------------------------------------------------ PIR answers
 def run_pir(orc, O, cd, rlk, items, ids, target_id, m, k, c, gk=None, nthreads=0):
     cw = np.stack([orc.map_perfect(int(i), m, k) for i in ids])
@@ -412,6 +445,26 @@ def test_multi_plaintext_rows_return_every_plaintext(orc):
         for p in range(3):
             got, budget = O.decrypt(resp[p], cd.s)
             assert np.array_equal(got, want[p * N:(p + 1) * N]) and budget > 0, (target, p)
+
+
+def test_folklore_pir_returns_selected_row(orc):
+    """Folklore PIR (Sec. 4): the query is the ell encrypted bits of the
+    index; the server forms the 2 ell leaves and the plain folklore operator
+    per row.  n = 13 rows (a ragged last power of two), ell = 4."""
+    N, L = 64, 3
+    O, q, cd, rlk = small_setup(orc, N, L)
+    n, ell = 13, 4
+    items = syn.payload(syn.Stream(82), n, N, T)
+    cw = np.stack([orc.folklore_codeword(i, ell) for i in range(n)])
+    for target in (0, 6, n - 1):
+        mus = []
+        for i in range(ell):
+            v = np.zeros(N, np.uint32)
+            v[0] = (target >> i) & 1
+            mus.append(v)
+        query = O.folklore_leaves(np.stack(encrypt_many(O, cd, mus, stream=100 + target)))
+        got, budget = O.decrypt(O.answer(items, cw, 2 * ell, query, rlk), cd.s)
+        assert np.array_equal(got, items[target]) and budget > 0
 
 
 def test_c1_full_answer_decrypts_with_positive_budget(orc):
