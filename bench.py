@@ -423,6 +423,56 @@ def run_lossy(args):
                                    % len(cw)}}
 
 
+def run_folklore(args):
+    """Folklore PIR against constant-weight PIR in the same engine (Sec. 4):
+    n = 4096 rows of 8192 16-bit coefficients at N = 16384, L = 7; folklore
+    selects each row by the plain folklore operator over ell = 12 index bits
+    (12 factors, depth 4), constant-weight PIR by CW(92, 2) (one
+    multiplication per row)."""
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+    from paper_2202_07569_gb300 import synthetic as syn
+
+    N, L, n, ell = 16384, 7, args.rows or 4096, 12
+    q = B.default_primes(N, L)
+    rlk = syn.uniform_residues(syn.Stream(71, 3), q, (L, 2), N)
+    ctx = B.Context(N, q, 65537, rlk)
+    items = syn.payload(syn.Stream(72), n, 8192, 1 << 16)
+    stream = torch.cuda.current_stream()
+    mb = payload_mb(n)
+    m2 = B.code_length(n, 2)
+    dbs = {"folklore": (ctx.load_db_folklore(items, ell), ell),
+           "constant_weight_k2": (ctx.load_db(items, np.stack([B.map_perfect(i, m2, 2)
+                                                               for i in range(n)]), m2), m2)}
+    del items
+    out = {}
+    for name, (db, h) in dbs.items():
+        query = syn.uniform_ciphertexts(73, q, h, N)
+        d_query = torch.from_numpy(query.view(np.int64)).cuda()
+        d_resp = torch.empty((2, L, N), dtype=torch.int64, device="cuda")
+        for _ in range(args.warmup):
+            ctx.answer_device(db, d_query.data_ptr(), d_resp.data_ptr(), 0, stream.cuda_stream)
+        torch.cuda.synchronize()
+        stats = ctx.last_stats()
+        with ClockSampler(0) as clk:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                ctx.answer_device(db, d_query.data_ptr(), d_resp.data_ptr(), 0, stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"query_cts": h, "ms_per_answer": ms, "value": mb / (ms / 1e3),
+                     "mults": int(stats["mults"]), "clocks": clk.summary()}
+    return {"metric": "PIR answer DB MB/s per query: folklore vs constant-weight (k=2)",
+            "unit": "MB/s", "value": out["folklore"]["value"], "runs": out,
+            "slowdown_folklore_vs_cw": out["folklore"]["ms_per_answer"]
+            / out["constant_weight_k2"]["ms_per_answer"],
+            "config": {"workload": "index PIR n=%d rows x 8192 16-bit coefficients, BFV N=16384 "
+                                   "L=7; folklore ell=12 vs CW(%d,2)" % (n, m2)}}
+
+
 def run_c4(args):
     """Configuration 4: 64 queries over four resident databases, batched
     (queries of one database share launches, replayed from CUDA graphs,
@@ -624,7 +674,7 @@ def main():
                     help="multiplications per kernel launch (0 = library default)")
     ap.add_argument("--batch", type=int, default=16,
                     help="queries per batched call in the batched-vs-plain comparison (0: skip)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "large", "lossy"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "large", "lossy", "folklore"],
                     help="c2: the metric's workload (default); c4: batched answering over "
                          "four databases")
     args = ap.parse_args()
@@ -673,10 +723,10 @@ def main():
         cuda_build.build()
     if dist:
         dist.barrier()
-    if args.workload in ("c4", "c5", "large", "lossy"):
+    if args.workload in ("c4", "c5", "large", "lossy", "folklore"):
         if rank == 0:
-            fn = {"c4": run_c4, "c5": run_c5, "large": run_large,
-                  "lossy": run_lossy}[args.workload]
+            fn = {"c4": run_c4, "c5": run_c5, "large": run_large, "lossy": run_lossy,
+                  "folklore": run_folklore}[args.workload]
             print(json.dumps(dict(fn(args), data="synthetic", n_gpus=1)), flush=True)
         return
     res = run_gpu(args, rank, world, dist)

@@ -106,6 +106,10 @@ int cwpir_map_perfect(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out);
  * both selected by a query for either, so callers resolve collisions
  * before cwpir_load_db.  EINVAL if k = 0, k > m or m > 65535. */
 int cwpir_map_lossy(uint64_t x, uint32_t m, uint32_t k, uint16_t *pos_out);
+/* Positions 2i + y[i] (i < ell) of the plain folklore operator's factors
+ * for the public ell-bit operand y.  EINVAL if ell is not in [1, 16] or
+ * y >= 2^ell. */
+int cwpir_map_folklore(uint64_t y, uint32_t ell, uint16_t *pos_out);
 /* Smallest m with C(m,k) >= n (Sec. 3: "choose m such that C(m,k) >= n"). */
 int cwpir_code_length(uint64_t n, uint32_t k, uint32_t *m_out);
 
@@ -133,6 +137,17 @@ int cwpir_load_db(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len, uint32_t k,
                   uint32_t m, const uint32_t *items, const uint16_t *codewords,
                   int32_t *db_id);
 int cwpir_free_db(cwpir_ctx *ctx, int32_t db_id);
+/* Folklore PIR (Sec. 4: the same architecture with the plain folklore
+ * equality operator, Eq. folklore-plain-eq, and the logarithmic binary
+ * encoding of indices): n <= 2^ell rows indexed 0 .. n-1, payloads as for
+ * cwpir_load_db.  Queries against the database are the ell ciphertexts of
+ * the index bits x[0..ell-1] (c = 0); the server forms the leaves
+ * (1 - x[0], x[0], 1 - x[1], x[1], ...) with 1 - x = (Delta - c0, -c1) and
+ * selects row y by the codeword of positions 2i + y[i] (cwpir_map_folklore),
+ * a product of ell factors of depth ceil(log2 ell).  1 <= ell <= 16.
+ * EINVAL, ENOMEM, ECUDA. */
+int cwpir_load_db_folklore(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len,
+                           uint32_t ell, const uint32_t *items, int32_t *db_id);
 
 /* ---- Process (server, online) ---- */
 /* Answer one query against a database (Sec. 3.3.3): expansion when c > 0
@@ -255,6 +270,9 @@ int cwpir_mul_noalloc(cwpir_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b,
 /* Shape of a loaded database: ring degree, number of primes, code length. */
 int cwpir_db_shape(const cwpir_ctx *ctx, int32_t db_id, uint32_t *N, uint32_t *L,
                    uint32_t *m);
+/* Query ciphertexts h of one query against a database with compression c:
+ * m (c = 0), ceil(m / 2^c), or ell for a folklore database (c = 0 only). */
+int cwpir_query_cts(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t *h);
 /* Plaintexts per row s of a loaded database (responses are [s][2][L][N]). */
 int cwpir_db_plaintexts(const cwpir_ctx *ctx, int32_t db_id, uint32_t *s);
 /* CUDA device of the context. */

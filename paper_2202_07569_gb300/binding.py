@@ -92,6 +92,9 @@ def lib():
             "cwpir_default_primes": (I, [U32, U32, u64p]),
             "cwpir_map_perfect": (I, [U64, U32, U32, u16p]),
             "cwpir_map_lossy": (I, [U64, U32, U32, u16p]),
+            "cwpir_map_folklore": (I, [U64, U32, u16p]),
+            "cwpir_load_db_folklore": (I, [vp, U64, U32, U32, u32p, C.POINTER(C.c_int32)]),
+            "cwpir_query_cts": (I, [vp, C.c_int32, U32, C.POINTER(U32)]),
             "cwpir_code_length": (I, [U64, U32, C.POINTER(U32)]),
             "cwpir_setup": (I, [C.POINTER(_Params), C.POINTER(_Keys), C.POINTER(vp)]),
             "cwpir_destroy": (None, [vp]),
@@ -169,6 +172,15 @@ def map_lossy(x: int, m: int, k: int) -> np.ndarray:
     return pos
 
 
+def map_folklore(y: int, ell: int) -> np.ndarray:
+    """Positions 2i + y[i] of the plain folklore operator's factors."""
+    pos = np.zeros(ell, np.uint16)
+    rc = lib().cwpir_map_folklore(int(y), ell, pos)
+    if rc:
+        raise CwpirError(rc, f"folklore codeword of {y} with {ell} bits")
+    return pos
+
+
 def code_length(n: int, k: int) -> int:
     m = C.c_uint32()
     rc = lib().cwpir_code_length(int(n), k, C.byref(m))
@@ -234,6 +246,21 @@ class Context:
                                         items.reshape(-1) if plen else np.zeros(1, np.uint32),
                                         cw.reshape(-1), C.byref(db)))
         return int(db.value)
+
+    def load_db_folklore(self, items, ell: int) -> int:
+        """Folklore PIR database: rows 0..n-1 indexed by ell bits."""
+        items = np.ascontiguousarray(items, dtype=np.uint32)
+        n, plen = items.shape
+        db = C.c_int32()
+        self._check(lib().cwpir_load_db_folklore(self._h, n, plen, ell, items.reshape(-1),
+                                                 C.byref(db)))
+        return int(db.value)
+
+    def query_cts(self, db: int, c: int = 0) -> int:
+        """Ciphertexts of one query against the database."""
+        h = C.c_uint32()
+        self._check(lib().cwpir_query_cts(self._h, db, c, C.byref(h)))
+        return int(h.value)
 
     def plaintexts(self, db: int) -> int:
         """Plaintexts per row s of a database (Sec. 3.3.1)."""

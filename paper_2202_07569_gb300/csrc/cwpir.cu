@@ -104,6 +104,7 @@ struct Db {
   u64 n = 0, n_pairs = 0;  // rows, distinct first-level position pairs
   u32 plen = 0, k = 0, m = 0;
   u32 sp = 1;                 // plaintexts per row (Sec. 3.3.1): ceil(plen / N)
+  bool folklore = false;      // rows indexed by the plain folklore operator
   DevBuf db;                  // [n][sp][L][N] NTT form
   std::vector<uint16_t> cw;   // [n][k]
   // answer plans over all rows, by (queries per call, compression factor)
@@ -203,6 +204,14 @@ int build_tables(cwpir_ctx *c) {
   h.L = c->L;
   h.K = c->K;
   h.t = c->t;
+  {  // Delta = (Q - r) / t with r = Q mod t, so Delta = -r t^-1 (mod q_j)
+    u64 r = 1;
+    for (u64 qj : c->q) r = (u64)((u128)r * (qj % c->t) % c->t);
+    for (u32 j = 0; j < c->L; ++j) {
+      const u64 qj = c->q[j], v = cw::host::hmul(r % qj, cw::host::hinv(c->t % qj, qj), qj);
+      h.delta[j] = v ? qj - v : 0;
+    }
+  }
   const u32 P = c->L + c->K, N = c->N;
   std::vector<u64> all(c->q);
   all.insert(all.end(), c->p.begin(), c->p.end());
@@ -356,8 +365,9 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
   P->m = m;
   P->top = ceil_log2(k);
   P->memo = memo_opt && P->top >= 2;
-  P->h_in = cfac ? (m + (1u << cfac) - 1) >> cfac : m;
+  P->h_in = db->folklore ? m / 2 : cfac ? (m + (1u << cfac) - 1) >> cfac : m;
   P->sp = db->sp;
+  if (db->folklore) CUDA_TRY(c, P->leaves_coef.ensure((u64)nq * m * ctw));
   const u32 J = c->jmax;
   if (root_mode == cw::ROOT_PM && (u64)nq * db->sp > J)
     return fail(c, CWPIR_EINVAL, "%u queries x %u plaintexts per row need more than %u partial "
@@ -601,16 +611,31 @@ Db *get_db(cwpir_ctx *c, int32_t id) {
   return it == c->dbs.end() ? nullptr : it->second.get();
 }
 
+// Coefficient-form leaves of a plan's queries: the query itself, its
+// expansion (c > 0) or, for a folklore database, (1 - x[i], x[i]) per bit.
+int leaf_coefs(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, cudaStream_t st,
+               const u64 **coef) {
+  int rc;
+  *coef = d_query;
+  if (P->cfac) {
+    if ((rc = enqueue_expand(c, P, d_query, st))) return rc;
+    *coef = P->leaves_coef.p;
+  } else if (db->folklore) {
+    CUDA_TRY(c, cw::launch_folklore_leaves(c->d_tab, c->h, d_query, P->nq * P->h_in,
+                                           P->leaves_coef.p, st));
+    c->stats.kernel_launches += 1;
+    *coef = P->leaves_coef.p;
+  }
+  return CWPIR_OK;
+}
+
 // The whole answer of a plan: expansion, leaves, tree, accumulation and the
 // final inverse transform into d_resp ([nq][sp][2][L][N]).  Capturable.
 int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_resp,
                    cudaStream_t st) {
   int rc;
-  const u64 *coef = d_query;
-  if (P->cfac) {
-    if ((rc = enqueue_expand(c, P, d_query, st))) return rc;
-    coef = P->leaves_coef.p;
-  }
+  const u64 *coef;
+  if ((rc = leaf_coefs(c, db, P, d_query, st, &coef))) return rc;
   if ((rc = prep_leaves(c, coef, P->nq * P->m, P->leaves.p, st))) return rc;
   CUDA_TRY(c, cudaMemsetAsync(P->acc.p, 0, (u64)P->nq * P->sp * c->ct() * sizeof(u64), st));
   for (const Chunk &ch : P->memo_chunks)
@@ -863,8 +888,9 @@ void cwpir_destroy(cwpir_ctx *ctx) {
   delete ctx;
 }
 
-int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t m,
-                  const uint32_t *items, const uint16_t *codewords, int32_t *db_id) {
+static int load_db_impl(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t m,
+                        const uint32_t *items, const uint16_t *codewords, bool folklore,
+                        int32_t *db_id) {
   if (!c) return CWPIR_EINVAL;
   c->err.clear();
   cudaSetDevice(c->device);
@@ -889,6 +915,7 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
   db->k = k;
   db->m = m;
   db->sp = plen ? (plen + c->N - 1) / c->N : 1;
+  db->folklore = folklore;
   db->cw.assign(codewords, codewords + n * k);
   {
     std::unordered_map<u32, char> seen;
@@ -927,6 +954,28 @@ int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t 
   return CWPIR_OK;
 }
 
+int cwpir_load_db(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uint32_t m,
+                  const uint32_t *items, const uint16_t *codewords, int32_t *db_id) {
+  return load_db_impl(c, n, plen, k, m, items, codewords, false, db_id);
+}
+
+int cwpir_map_folklore(uint64_t y, uint32_t ell, uint16_t *pos_out) {
+  if (!pos_out || ell == 0 || ell > 16 || (y >> ell)) return CWPIR_EINVAL;
+  for (u32 i = 0; i < ell; ++i) pos_out[i] = (uint16_t)(2 * i + ((y >> i) & 1));
+  return CWPIR_OK;
+}
+
+int cwpir_load_db_folklore(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t ell,
+                           const uint32_t *items, int32_t *db_id) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  if (ell < 1 || ell > 16 || n < 1 || n > (1ull << ell))
+    return fail(c, CWPIR_EINVAL, "folklore needs 1 <= ell <= 16 and 1 <= n <= 2^ell");
+  std::vector<uint16_t> cw(n * ell);
+  for (u64 i = 0; i < n; ++i) cwpir_map_folklore(i, ell, cw.data() + i * ell);
+  return load_db_impl(c, n, plen, ell, 2 * ell, items, cw.data(), true, db_id);
+}
+
 int cwpir_free_db(cwpir_ctx *c, int32_t id) {
   if (!c) return CWPIR_EINVAL;
   cudaSetDevice(c->device);
@@ -937,7 +986,23 @@ int cwpir_free_db(cwpir_ctx *c, int32_t id) {
 
 static int query_shape(cwpir_ctx *c, Db *db, u32 cfac, u64 *h) {
   if (cfac > c->logN) return fail(c, CWPIR_EINVAL, "c > log2 N");
+  if (db->folklore) {
+    if (cfac) return fail(c, CWPIR_EINVAL, "folklore queries are ell bit ciphertexts (c = 0)");
+    *h = db->m / 2;
+    return CWPIR_OK;
+  }
   *h = cfac == 0 ? db->m : (db->m + (1u << cfac) - 1) >> cfac;
+  return CWPIR_OK;
+}
+
+int cwpir_query_cts(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t *h) {
+  if (!c || !h) return CWPIR_EINVAL;
+  Db *db = get_db(c, db_id);
+  if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
+  u64 hh;
+  int rc = query_shape(c, db, cfac, &hh);
+  if (rc) return rc;
+  *h = (uint32_t)hh;
   return CWPIR_OK;
 }
 
@@ -1147,11 +1212,8 @@ int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *
   std::unique_ptr<Plan> P;
   if ((rc = build_plan(c, db, rv, 1, cfac, cw::ROOT_SEL, c->io_out.p, c->opt_share != 0, P)))
     return rc;
-  const u64 *coef = c->io_in.p;
-  if (cfac) {
-    if ((rc = enqueue_expand(c, P.get(), c->io_in.p, c->stream))) return rc;
-    coef = P->leaves_coef.p;
-  }
+  const u64 *coef;
+  if ((rc = leaf_coefs(c, db, P.get(), c->io_in.p, c->stream, &coef))) return rc;
   if (db->k == 1) {
     // the selection entry is the (expanded) query ciphertext itself
     for (u64 i = 0; i < count; ++i)
@@ -1242,8 +1304,9 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
   const u64 J = c->jmax ? c->jmax : 1024;
   const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();
   const bool memo = c->opt_share && top >= 2;
-  const u64 h = cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
+  const u64 h = db->folklore ? db->m / 2 : cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
   w += (u64)nq * db->m * qp + 2ull * nq * db->sp * ctw + (u64)nq * h * ctw;
+  if (db->folklore) w += (u64)nq * db->m * ctw;
   if (db->sp > 1 && db->k > 1 && c->SEL.n < J * ctw) w += J * ctw;
   if (memo) w += (u64)nq * db->n_pairs * qp;
   u64 widest = 1, internal_nodes = 0;

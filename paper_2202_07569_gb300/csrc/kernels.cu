@@ -573,6 +573,26 @@ __global__ void k_automorph(const DevTables *T, const SubJob *jobs, u32 g, u64 *
   tau[(job * 2 * L + pl) * N + e] = v;
 }
 
+// Folklore leaves: for query bit ciphertext src = s*ell + i, leaves 2 src
+// (the constant plaintext 1 minus x: Delta - c0 at x^0, -c0 elsewhere, and
+// -c1) and 2 src + 1 (x itself).  grid (N/256, 2L, nq * ell).
+__global__ void k_folklore_leaves(const DevTables *T, const u64 *query, u64 *out) {
+  const u32 N = T->N, L = T->L;
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y, j = pl % L;
+  const u64 src = blockIdx.z;
+  const u64 q = T->prime[j].q, ctw = 2ull * L * N, off = (u64)pl * N + i;
+  const u64 v = query[src * ctw + off];
+  u64 w;
+  if (pl < L) {
+    const u64 d = i == 0 ? T->delta[j] : 0;
+    w = d >= v ? d - v : d + q - v;
+  } else {
+    w = v ? q - v : 0;
+  }
+  out[2 * src * ctw + off] = w;
+  out[(2 * src + 1) * ctw + off] = v;
+}
+
 // One round a of Alg. Query Expansion for all (input j, entry b < 2^a):
 // next[b] = cur[b] + S_b, next[b + 2^a] = x^(-2^a) (cur[b] - S_b), where
 // S_b = Sub(cur[b]); entries are indexed j * 2^c + b.
@@ -852,6 +872,13 @@ cudaError_t launch_accumulate(const DevTables &h, const DevTables *T, const u64 
                               u32 per_seg, u32 sp, u64 *acc, cudaStream_t st) {
   if (!segs || !per_seg) return cudaSuccess;
   k_accumulate<<<dim3(h.N / 256, 2 * h.L * sp, segs), 256, 0, st>>>(T, P, per_seg, sp, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const u64 *query,
+                                   u32 count, u64 *out, cudaStream_t st) {
+  if (!count) return cudaSuccess;
+  k_folklore_leaves<<<dim3(h.N / 256, 2 * h.L, count), 256, 0, st>>>(T, query, out);
   return cudaGetLastError();
 }
 

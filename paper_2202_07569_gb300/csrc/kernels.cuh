@@ -11,6 +11,7 @@ namespace cw {
 struct DevTables {
   u32 N, logN, L, K;
   u64 t;
+  u64 delta[kMaxL];       // Delta = floor(Q / t) mod q_j
   NttPrime prime[kMaxP];  // q_0..q_{L-1}, then p_0..p_{K-1}
   BaseConv q2b;           // centered Q -> P conversion (leaves, nodes)
   ScaleTab scale;         // exact round(t d / Q)
@@ -92,6 +93,11 @@ cudaError_t launch_expand_combine(const DevTables *T, const DevTables &h, const 
                                   cudaStream_t st);
 cudaError_t launch_pm_ntt(const DevTables *T, const DevTables &h, const u64 *ct_ntt,
                           const u64 *db_row, u64 *out, cudaStream_t st);
+// Folklore leaves (Eq. folklore-plain-eq): query [nq][ell] bit ciphertexts
+// x[i] -> out [nq][2 ell] = (1 - x[0], x[0], 1 - x[1], x[1], ...) with
+// 1 - x = (Delta - c0, -c1), coefficient form.
+cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const u64 *query,
+                                   u32 count, u64 *out, cudaStream_t st);
 cudaError_t launch_key_prep(const DevTables *T, const DevTables &h, u64 *key, u64 *key_s,
                             u32 nkeys, cudaStream_t st);
 

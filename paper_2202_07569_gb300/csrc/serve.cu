@@ -193,13 +193,12 @@ int cwpir_server_create(const cwpir_target *targets, uint32_t n_targets, uint32_
   for (uint32_t i = 0; i < n_targets; ++i) {
     SrvTarget tg;
     tg.t = targets[i];
-    uint32_t N = 0, L = 0, m = 0, sp = 1;
+    uint32_t N = 0, L = 0, m = 0, sp = 1, h = 0;
     if (!tg.t.ctx || cwpir_db_shape(tg.t.ctx, tg.t.db_id, &N, &L, &m) != CWPIR_OK ||
-        cwpir_db_plaintexts(tg.t.ctx, tg.t.db_id, &sp) != CWPIR_OK)
+        cwpir_db_plaintexts(tg.t.ctx, tg.t.db_id, &sp) != CWPIR_OK ||
+        cwpir_query_cts(tg.t.ctx, tg.t.db_id, tg.t.c, &h) != CWPIR_OK)
       return CWPIR_EINVAL;
-    if (tg.t.c > 0 && (1u << tg.t.c) > N) return CWPIR_EINVAL;
-    const uint64_t h = tg.t.c ? (m + (1u << tg.t.c) - 1) >> tg.t.c : m;
-    tg.q_words = h * 2ull * L * N;
+    tg.q_words = (uint64_t)h * 2ull * L * N;
     tg.r_words = (uint64_t)sp * 2ull * L * N;
     auto it = lane_of.find(tg.t.ctx);
     if (it == lane_of.end()) {
