@@ -72,6 +72,9 @@ def lib():
             "orc_expand_sealpir": (I, [vp, u64p, U32, u64p, u64p]),
             "orc_scalar_mul": (I, [vp, u64p, U64, u64p]),
             "orc_one_minus": (I, [vp, u64p, u64p]),
+            "orc_arith_cw_eq": (I, [vp, U32, U32, u64p, u64p, u64p, u64p]),
+            "orc_batch_encode": (I, [vp, u32p, u32p]),
+            "orc_batch_decode": (I, [vp, u32p, u32p]),
             "orc_folklore_codeword": (I, [U64, U32, u16p]),
             "orc_plain_mul": (I, [vp, u64p, u32p, U32, u64p]),
             "orc_selection": (I, [vp, u64p, u16p, U32, u64p, u64p]),
@@ -271,6 +274,23 @@ class Oracle:
         out = np.zeros(self.ct_shape, np.uint64)
         _check(lib().orc_scalar_mul(self._ctx, self._ct(ct), scalar, out), "scalar")
         return out
+
+    def arith_cw_eq(self, m: int, k: int, x, y, rlk) -> np.ndarray:
+        out = np.zeros(self.ct_shape, np.uint64)
+        _check(lib().orc_arith_cw_eq(self._ctx, m, k, _c(x, np.uint64), _c(y, np.uint64),
+                                     _c(rlk, np.uint64), out), "arithmetic CW operator")
+        return out
+
+    def batch_encode(self, slots) -> np.ndarray:
+        slots = np.zeros(self.N, np.uint32) + _c(slots, np.uint32)
+        mu = np.zeros(self.N, np.uint32)
+        _check(lib().orc_batch_encode(self._ctx, slots, mu), "batch encode")
+        return mu
+
+    def batch_decode(self, mu) -> np.ndarray:
+        slots = np.zeros(self.N, np.uint32)
+        _check(lib().orc_batch_decode(self._ctx, _c(mu, np.uint32), slots), "batch decode")
+        return slots
 
     def one_minus(self, ct) -> np.ndarray:
         out = np.zeros(self.ct_shape, np.uint64)

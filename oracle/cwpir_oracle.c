@@ -936,6 +936,82 @@ int orc_selection(const orc_ctx *c, const uint64_t *ctxts,
   return 0;
 }
 
+/* Alg. Arithmetic Constant-weight Equality Operator on encrypted operands
+ * x, y ([m] ciphertexts each, bit i of every SIMD slot's codeword):
+ *   k' = sum_i x[i] * y[i]             (m multiplications M, then adds)
+ *   e  = (1/k!) prod_{i<k} (k' - i)     (k' - i: the constant plaintext i
+ *                                        subtracted; the product by the
+ *                                        balanced tree; 1/k! mod t as a
+ *                                        scalar)
+ * Depth 1 + ceil(log2 k). */
+int orc_arith_cw_eq(const orc_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
+                    const uint64_t *y, const uint64_t *rlk, uint64_t *out) {
+  size_t ctw = 2 * LN(c);
+  if (k == 0 || k > m) return -1;
+  uint64_t *kp = calloc(ctw, sizeof(uint64_t)), *prod = malloc(ctw * sizeof(uint64_t));
+  for (uint32_t i = 0; i < m; ++i) {
+    orc_bfv_mul(c, x + (size_t)i * ctw, y + (size_t)i * ctw, rlk, prod);
+    ct_add(c, kp, prod, kp);
+  }
+  uint64_t *fac = malloc((size_t)k * ctw * sizeof(uint64_t));
+  uint16_t *pos = malloc(k * sizeof(uint16_t));
+  for (uint32_t i = 0; i < k; ++i) {
+    uint64_t *f = fac + (size_t)i * ctw;
+    memcpy(f, kp, ctw * sizeof(uint64_t));
+    for (uint32_t j = 0; j < c->L; ++j) /* c0 - Delta * i at x^0 */
+      f[(size_t)j * c->N] = submod(f[(size_t)j * c->N], mulmod(c->delta_mod[j], i, c->q[j]),
+                                   c->q[j]);
+    pos[i] = (uint16_t)i;
+  }
+  orc_selection(c, fac, pos, k, rlk, prod);
+  uint64_t kf = 1; /* k! mod t */
+  for (uint32_t i = 2; i <= k; ++i) kf = mulmod(kf, i, c->t);
+  orc_scalar_mul(c, prod, invmod(kf, c->t), out);
+  free(kp);
+  free(prod);
+  free(fac);
+  free(pos);
+  return 0;
+}
+
+/* SIMD batch encoding over Z_t (t prime, t = 1 mod 2N): slot i of a
+ * plaintext mu is mu evaluated at psi^(2i+1), psi = 3^((t-1)/2N) a
+ * primitive 2N-th root of unity (3 generates Z_t^* for t = 65537).  The
+ * slots of a product mod (x^N + 1, t) are the slot-wise products.
+ * Evaluated directly, O(N^2). */
+static uint64_t batch_psi(const orc_ctx *c) {
+  return powmod(3, (c->t - 1) / (2 * c->N), c->t);
+}
+
+int orc_batch_decode(const orc_ctx *c, const uint32_t *mu, uint32_t *slots) {
+  uint64_t t = c->t, psi = batch_psi(c);
+  if ((t - 1) % (2 * c->N)) return -1;
+  for (uint32_t i = 0; i < c->N; ++i) {
+    uint64_t w = powmod(psi, 2 * i + 1, t), pw = 1, v = 0;
+    for (uint32_t j = 0; j < c->N; ++j) {
+      v = (v + mulmod(mu[j] % t, pw, t)) % t;
+      pw = mulmod(pw, w, t);
+    }
+    slots[i] = (uint32_t)v;
+  }
+  return 0;
+}
+
+int orc_batch_encode(const orc_ctx *c, const uint32_t *slots, uint32_t *mu) {
+  uint64_t t = c->t, psi = batch_psi(c);
+  if ((t - 1) % (2 * c->N)) return -1;
+  uint64_t ninv = invmod(c->N % t, t);
+  for (uint32_t j = 0; j < c->N; ++j) {
+    uint64_t v = 0;
+    for (uint32_t i = 0; i < c->N; ++i) {
+      uint64_t wi = powmod(psi, ((uint64_t)(2 * i + 1) * j) % (2 * c->N), t);
+      v = (v + mulmod(slots[i] % t, invmod(wi, t), t)) % t;
+    }
+    mu[j] = (uint32_t)mulmod(v, ninv, t);
+  }
+  return 0;
+}
+
 int orc_answer(const orc_ctx *c, uint64_t n, uint32_t payload_len,
                const uint32_t *items, const uint16_t *codewords, uint32_t k,
                uint32_t m, uint32_t cf, const uint64_t *query,

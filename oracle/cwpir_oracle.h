@@ -98,6 +98,13 @@ int orc_plain_mul(const orc_ctx *ctx, const uint64_t *ct, const uint32_t *mu,
 int orc_selection(const orc_ctx *ctx, const uint64_t *ctxts,
                   const uint16_t *positions, uint32_t k, const uint64_t *rlk,
                   uint64_t *out);
+/* Alg. Arithmetic Constant-weight Equality Operator on encrypted
+ * operands x, y ([m][2][L][N] each): (1/k!) prod_{i<k} (sum_j x_j y_j - i). */
+int orc_arith_cw_eq(const orc_ctx *ctx, uint32_t m, uint32_t k, const uint64_t *x,
+                    const uint64_t *y, const uint64_t *rlk, uint64_t *out);
+/* SIMD batch encoding: slot i = mu(psi^(2i+1)) mod t, psi = 3^((t-1)/2N). */
+int orc_batch_encode(const orc_ctx *ctx, const uint32_t *slots, uint32_t *mu);
+int orc_batch_decode(const orc_ctx *ctx, const uint32_t *mu, uint32_t *slots);
 /* Full server answer: expansion (c > 0), selection vector, inner product.
  * query: [h][2][L][N] with h = m when c = 0, else ceil(m / 2^c).
  * items: [n][payload_len]; a row is s = ceil(payload_len / N) plaintexts

@@ -382,6 +382,51 @@ def test_folklore_equality_operator_brute_force(orc, ell):
             assert got[0] == (1 if x == y else 0) and not got[1:].any() and budget > 0
 
 
+def test_batch_encoding_is_a_ring_isomorphism(orc):
+    """SIMD batch encoding (Sec. 4: all circuits run slot-wise): decoding
+    inverts encoding, the negacyclic product mod t of two encodings decodes
+    to the slot-wise product (schoolbook in Python integers), and the
+    constant polynomial j fills every slot with j."""
+    N = 64
+    O, q, cd, rlk = small_setup(orc, N, 2)
+    st = syn.Stream(83)
+    v = st.below(T, N).astype(np.uint32)
+    w = st.below(T, N).astype(np.uint32)
+    ev, ew = O.batch_encode(v), O.batch_encode(w)
+    assert np.array_equal(O.batch_decode(ev), v)
+    prod = np.array(schoolbook_nega([int(a) for a in ev], [int(b) for b in ew], T), np.uint32)
+    assert np.array_equal(O.batch_decode(prod), (v.astype(np.uint64) * w % T).astype(np.uint32))
+    const = np.zeros(N, np.uint32)
+    const[0] = 7
+    assert np.array_equal(O.batch_decode(const), np.full(N, 7, np.uint32))
+
+
+@pytest.mark.parametrize("m,k", [(6, 2), (5, 3)])
+def test_arith_cw_equality_operator_brute_force(orc, m, k):
+    """Alg. Arithmetic Constant-weight Equality Operator, Theorem: with both
+    operands encrypted and batch-encoded (slot s holds the pair (x_s, y_s)),
+    the output decrypts to 1 in exactly the slots where x_s == y_s, over
+    every pair of codewords of CW(m, k)."""
+    N = 256
+    O, q, cd, rlk = small_setup(orc, N, 3)
+    words = [orc.map_perfect(i, m, k) for i in range(orc.binom(m, k))]
+    pairs = [(a, b) for a in range(len(words)) for b in range(len(words))]
+    assert len(pairs) <= N
+    xb = np.zeros((m, N), np.uint32)
+    yb = np.zeros((m, N), np.uint32)
+    for s, (a, b) in enumerate(pairs):
+        xb[words[a], s] = 1
+        yb[words[b], s] = 1
+    x = np.stack(encrypt_many(O, cd, [O.batch_encode(r) for r in xb], stream=1))
+    y = np.stack(encrypt_many(O, cd, [O.batch_encode(r) for r in yb], stream=2))
+    mu, budget = O.decrypt(O.arith_cw_eq(m, k, x, y, rlk), cd.s)
+    e = O.batch_decode(mu)
+    want = np.zeros(N, np.uint32)
+    for s, (a, b) in enumerate(pairs):
+        want[s] = 1 if a == b else 0
+    assert np.array_equal(e, want) and budget > 0
+
+
 # ------------------------------------------------------------ PIR answers
 def run_pir(orc, O, cd, rlk, items, ids, target_id, m, k, c, gk=None, nthreads=0):
     cw = np.stack([orc.map_perfect(int(i), m, k) for i in ids])
