@@ -1000,15 +1000,24 @@ int orc_batch_decode(const orc_ctx *c, const uint32_t *mu, uint32_t *slots) {
 int orc_batch_encode(const orc_ctx *c, const uint32_t *slots, uint32_t *mu) {
   uint64_t t = c->t, psi = batch_psi(c);
   if ((t - 1) % (2 * c->N)) return -1;
+  /* mu_j = N^-1 sum_i slot_i w_i^-j with w_i = psi^(2i+1); cur[i] runs
+   * through slot_i w_i^-j as j grows */
   uint64_t ninv = invmod(c->N % t, t);
+  uint64_t *cur = malloc(c->N * sizeof(uint64_t)), *winv = malloc(c->N * sizeof(uint64_t));
+  for (uint32_t i = 0; i < c->N; ++i) {
+    cur[i] = slots[i] % t;
+    winv[i] = invmod(powmod(psi, 2 * i + 1, t), t);
+  }
   for (uint32_t j = 0; j < c->N; ++j) {
     uint64_t v = 0;
     for (uint32_t i = 0; i < c->N; ++i) {
-      uint64_t wi = powmod(psi, ((uint64_t)(2 * i + 1) * j) % (2 * c->N), t);
-      v = (v + mulmod(slots[i] % t, invmod(wi, t), t)) % t;
+      v += cur[i];
+      cur[i] = mulmod(cur[i], winv[i], t);
     }
-    mu[j] = (uint32_t)mulmod(v, ninv, t);
+    mu[j] = (uint32_t)mulmod(v % t, ninv, t);
   }
+  free(cur);
+  free(winv);
   return 0;
 }
 
