@@ -473,6 +473,41 @@ def run_folklore(args):
                                    "L=7; folklore ell=12 vs CW(%d,2)" % (n, m2)}}
 
 
+def run_arith(args):
+    """Arithmetic constant-weight equality operator on two encrypted,
+    batch-encoded operands (Sec. 4, Table arith-eq): N = 16384, L = 7,
+    (n, k, m) = (2^16, 8, 19) and (2^32, 16, 36), the rows k = log2(n)/2 of
+    the paper's table; one evaluation compares N pairs slot-wise.  Host
+    buffers in and out (end to end through cwpir_arith_cw_eq)."""
+    from paper_2202_07569_gb300 import binding as B
+    from paper_2202_07569_gb300 import synthetic as syn
+
+    N, L = 16384, 7
+    q = B.default_primes(N, L)
+    rlk = syn.uniform_residues(syn.Stream(81, 3), q, (L, 2), N)
+    ctx = B.Context(N, q, 65537, rlk)
+    runs = []
+    for logn, k, m in ((16, 8, 19), (32, 16, 36)):
+        x = syn.uniform_ciphertexts(82, q, m, N)
+        y = syn.uniform_ciphertexts(83, q, m, N)
+        for _ in range(args.warmup):
+            ctx.arith_cw_eq(m, k, x, y)
+        ts = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            ctx.arith_cw_eq(m, k, x, y)
+            ts.append(time.perf_counter() - t)
+        s = statistics.median(ts)
+        runs.append({"domain_bits": logn, "k": k, "m": m, "mults": m + k - 1,
+                     "depth": 1 + (k - 1).bit_length(), "ms_per_evaluation": s * 1e3,
+                     "comparisons_per_s": N / s, "h2d_bytes": int(x.nbytes + y.nbytes),
+                     "d2h_bytes": 2 * L * N * 8})
+    return {"metric": "arithmetic CW equality operator: comparisons per second (N slots per "
+                      "evaluation)", "unit": "comparisons/s", "value": runs[0]["comparisons_per_s"],
+            "runs": runs, "config": {"workload": "arithmetic CW operator, both operands "
+                                                 "encrypted, BFV N=16384 L=7, t=65537 batching"}}
+
+
 def run_c4(args):
     """Configuration 4: 64 queries over four resident databases, batched
     (queries of one database share launches, replayed from CUDA graphs,
@@ -674,7 +709,7 @@ def main():
                     help="multiplications per kernel launch (0 = library default)")
     ap.add_argument("--batch", type=int, default=16,
                     help="queries per batched call in the batched-vs-plain comparison (0: skip)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "large", "lossy", "folklore"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "large", "lossy", "folklore", "arith"],
                     help="c2: the metric's workload (default); c4: batched answering over "
                          "four databases")
     args = ap.parse_args()
@@ -723,10 +758,10 @@ def main():
         cuda_build.build()
     if dist:
         dist.barrier()
-    if args.workload in ("c4", "c5", "large", "lossy", "folklore"):
+    if args.workload in ("c4", "c5", "large", "lossy", "folklore", "arith"):
         if rank == 0:
             fn = {"c4": run_c4, "c5": run_c5, "large": run_large, "lossy": run_lossy,
-                  "folklore": run_folklore}[args.workload]
+                  "folklore": run_folklore, "arith": run_arith}[args.workload]
             print(json.dumps(dict(fn(args), data="synthetic", n_gpus=1)), flush=True)
         return
     res = run_gpu(args, rank, world, dist)

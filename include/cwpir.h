@@ -220,6 +220,16 @@ int cwpir_expand(cwpir_ctx *ctx, uint32_t c, uint32_t m, const uint64_t *query,
 int cwpir_selection(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                     const uint64_t *query, uint64_t count,
                     const uint64_t *rows, uint64_t *out);
+/* Arithmetic constant-weight equality operator (Alg. Arithmetic
+ * Constant-weight Equality Operator, Sec. 3.1) on two encrypted operands,
+ * slot-wise when the plaintexts are batch-encoded: x, y: [m][2][L][N]
+ * (ciphertext i holds bit i of the codewords), out: [2][L][N] =
+ * (1/k!) prod_{i<k} (sum_j x_j y_j - i), which decrypts to 1 where the
+ * codewords agree and 0 elsewhere; m + k - 1 multiplications, depth
+ * 1 + ceil(log2 k).  1 <= k <= 16, k <= m <= 8192.  Host buffers.
+ * EINVAL, ENOMEM, ECUDA, EINTERNAL. */
+int cwpir_arith_cw_eq(cwpir_ctx *ctx, uint32_t m, uint32_t k, const uint64_t *x,
+                      const uint64_t *y, uint64_t *out);
 /* Plain multiplication PM of a ciphertext by row `row` of a database: by
  * each of the row's s plaintexts, out: [s][2][L][N]. */
 int cwpir_plain_mul(cwpir_ctx *ctx, int32_t db_id, uint64_t row,

@@ -95,6 +95,7 @@ def lib():
             "cwpir_map_folklore": (I, [U64, U32, u16p]),
             "cwpir_load_db_folklore": (I, [vp, U64, U32, U32, u32p, C.POINTER(C.c_int32)]),
             "cwpir_query_cts": (I, [vp, C.c_int32, U32, C.POINTER(U32)]),
+            "cwpir_arith_cw_eq": (I, [vp, U32, U32, u64p, u64p, u64p]),
             "cwpir_code_length": (I, [U64, U32, C.POINTER(U32)]),
             "cwpir_setup": (I, [C.POINTER(_Params), C.POINTER(_Keys), C.POINTER(vp)]),
             "cwpir_destroy": (None, [vp]),
@@ -329,6 +330,12 @@ class Context:
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
         out = np.zeros((rows.size,) + self.ct_shape, np.uint64)
         self._check(lib().cwpir_selection(self._h, db, c, _u64(query), rows.size, rows, out))
+        return out
+
+    def arith_cw_eq(self, m: int, k: int, x, y) -> np.ndarray:
+        """Arithmetic constant-weight equality operator on encrypted operands."""
+        out = np.zeros(self.ct_shape, np.uint64)
+        self._check(lib().cwpir_arith_cw_eq(self._h, m, k, _u64(x), _u64(y), out))
         return out
 
     def plain_mul(self, db: int, row: int, ct) -> np.ndarray:

@@ -1234,6 +1234,83 @@ int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *
   return check_err_flag(c);
 }
 
+// Selection entries (coefficient form, [rows][2][L][N] at out) of the rows
+// of a database description d over the coefficient-form leaves `coef`
+// ([d.m][2][L][N]); the plan and its scratch are temporary.
+static int product_rows(cwpir_ctx *c, Db &d, const u64 *coef, u64 *out) {
+  std::vector<u64> rv(d.n);
+  for (u64 i = 0; i < d.n; ++i) rv[i] = i;
+  std::unique_ptr<Plan> P;
+  int rc = build_plan(c, &d, rv, 1, 0, cw::ROOT_SEL, out, false, P);
+  if (rc) return rc;
+  if ((rc = prep_leaves(c, coef, d.m, P->leaves.p, c->stream))) return rc;
+  for (const auto &batch : P->batches)
+    for (const Chunk &ch : batch)
+      if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_err_flag(c);
+}
+
+int cwpir_arith_cw_eq(cwpir_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
+                      const uint64_t *y, uint64_t *out) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!x || !y || !out) return fail(c, CWPIR_EINVAL, "null buffer");
+  if (k < 1 || k > 16 || k > m || m > 8192)
+    return fail(c, CWPIR_EINVAL, "need 1 <= k <= 16, k <= m <= 8192");
+  if (!valid_residues(x, c->L, c->N, c->q, 2ull * m) ||
+      !valid_residues(y, c->L, c->N, c->q, 2ull * m))
+    return fail(c, CWPIR_EINVAL, "residue out of range");
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  const u64 ctw = c->ct();
+  // leaves x_0 .. x_{m-1}, y_0 .. y_{m-1}; then m products, their sum, the
+  // k factors and their product
+  DevBuf leaves, prods, fac;
+  CUDA_TRY(c, leaves.ensure(2ull * m * ctw));
+  CUDA_TRY(c, prods.ensure((u64)m * ctw));
+  CUDA_TRY(c, fac.ensure((u64)(k + 2) * ctw));
+  CUDA_TRY(c, cudaMemcpyAsync(leaves.p, x, (u64)m * ctw * sizeof(u64), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(leaves.p + (u64)m * ctw, y, (u64)m * ctw * sizeof(u64),
+                              cudaMemcpyHostToDevice, c->stream));
+  // k' = sum_i x_i y_i: rows i with codewords {i, m + i}
+  Db d1;
+  d1.n = m;
+  d1.k = 2;
+  d1.m = 2 * m;
+  d1.cw.resize(2ull * m);
+  for (u32 i = 0; i < m; ++i) {
+    d1.cw[2 * i] = (uint16_t)i;
+    d1.cw[2 * i + 1] = (uint16_t)(m + i);
+  }
+  if ((rc = product_rows(c, d1, leaves.p, prods.p))) return rc;
+  u64 *kp = fac.p + (u64)k * ctw, *res = fac.p + (u64)(k + 1) * ctw;
+  CUDA_TRY(c, cw::launch_ct_sum(c->d_tab, c->h, prods.p, m, kp, c->stream));
+  // factors k' - i, i < k, and their product by the balanced tree
+  CUDA_TRY(c, cw::launch_minus_consts(c->d_tab, c->h, kp, k, fac.p, c->stream));
+  const u64 *prod = fac.p;
+  if (k > 1) {
+    Db d2;
+    d2.n = 1;
+    d2.k = k;
+    d2.m = k;
+    d2.cw.resize(k);
+    for (u32 i = 0; i < k; ++i) d2.cw[i] = (uint16_t)i;
+    if ((rc = product_rows(c, d2, fac.p, res))) return rc;
+    prod = res;
+  }
+  // times (k!)^-1 mod t
+  u64 kf = 1;
+  for (u32 i = 2; i <= k; ++i) kf = kf * i % c->t;
+  const u64 s = hpow(kf, c->t - 2, c->t);
+  CUDA_TRY(c, cw::launch_ct_scalar(c->d_tab, c->h, prod, s, kp, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(out, kp, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return CWPIR_OK;
+}
+
 int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *ct, uint64_t *out) {
   if (!c) return CWPIR_EINVAL;
   c->err.clear();

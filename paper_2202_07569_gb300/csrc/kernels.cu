@@ -593,6 +593,34 @@ __global__ void k_folklore_leaves(const DevTables *T, const u64 *query, u64 *out
   out[(2 * src + 1) * ctw + off] = v;
 }
 
+// Arithmetic operator steps, coefficient form; grid (N/256, 2L[, count]).
+__global__ void k_ct_sum(const DevTables *T, const u64 *in, u32 count, u64 *out) {
+  const u32 N = T->N, L = T->L, i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
+  const u64 q = T->prime[pl % L].q, ctw = 2ull * L * N, off = (u64)pl * N + i;
+  u64 a = 0;
+  for (u32 x = 0; x < count; ++x) a = addq(a, in[x * ctw + off], q);
+  out[off] = a;
+}
+
+__global__ void k_minus_consts(const DevTables *T, const u64 *in, u64 *out) {
+  const u32 N = T->N, L = T->L, i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
+  const u32 f = blockIdx.z, j = pl % L;
+  const u64 q = T->prime[j].q, off = (u64)pl * N + i;
+  u64 v = in[off];
+  if (pl < L && i == 0) {
+    const u64 d = (u64)(((unsigned __int128)T->delta[j] * f) % q);
+    v = subq(v, d, q);
+  }
+  out[(u64)f * 2 * L * N + off] = v;
+}
+
+__global__ void k_ct_scalar(const DevTables *T, const u64 *in, u64 s, u64 *out) {
+  const u32 N = T->N, L = T->L, i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
+  const NttPrime P = T->prime[pl % L];
+  const u64 off = (u64)pl * N + i;
+  out[off] = barrett(in[off], s % P.q, P.q, P.mu);
+}
+
 // One round a of Alg. Query Expansion for all (input j, entry b < 2^a):
 // next[b] = cur[b] + S_b, next[b + 2^a] = x^(-2^a) (cur[b] - S_b), where
 // S_b = Sub(cur[b]); entries are indexed j * 2^c + b.
@@ -879,6 +907,25 @@ cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const
                                    u32 count, u64 *out, cudaStream_t st) {
   if (!count) return cudaSuccess;
   k_folklore_leaves<<<dim3(h.N / 256, 2 * h.L, count), 256, 0, st>>>(T, query, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_sum(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
+                          u64 *out, cudaStream_t st) {
+  k_ct_sum<<<dim3(h.N / 256, 2 * h.L), 256, 0, st>>>(T, in, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minus_consts(const DevTables *T, const DevTables &h, const u64 *in,
+                                u32 count, u64 *out, cudaStream_t st) {
+  if (!count) return cudaSuccess;
+  k_minus_consts<<<dim3(h.N / 256, 2 * h.L, count), 256, 0, st>>>(T, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_scalar(const DevTables *T, const DevTables &h, const u64 *in, u64 s,
+                             u64 *out, cudaStream_t st) {
+  k_ct_scalar<<<dim3(h.N / 256, 2 * h.L), 256, 0, st>>>(T, in, s, out);
   return cudaGetLastError();
 }
 

@@ -98,6 +98,15 @@ cudaError_t launch_pm_ntt(const DevTables *T, const DevTables &h, const u64 *ct_
 // 1 - x = (Delta - c0, -c1), coefficient form.
 cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const u64 *query,
                                    u32 count, u64 *out, cudaStream_t st);
+// Element-wise ciphertext steps of the arithmetic operator (coefficient
+// form [2][L][N]): out = sum of `count` ciphertexts; out[f] = in minus the
+// constant plaintext f (Delta f off c0 at x^0), f < count; out = s * in.
+cudaError_t launch_ct_sum(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
+                          u64 *out, cudaStream_t st);
+cudaError_t launch_minus_consts(const DevTables *T, const DevTables &h, const u64 *in,
+                                u32 count, u64 *out, cudaStream_t st);
+cudaError_t launch_ct_scalar(const DevTables *T, const DevTables &h, const u64 *in, u64 s,
+                             u64 *out, cudaStream_t st);
 cudaError_t launch_key_prep(const DevTables *T, const DevTables &h, u64 *key, u64 *key_s,
                             u32 nkeys, cudaStream_t st);
 
