@@ -8,10 +8,10 @@
 //   scaled buffer  E         [jobs][3][L][N]   round(t d / Q) mod q_j
 //   partials       P         [jobs][2][L][N]   NTT-form sel * DB rows
 //
-// NTT kernels run one length-N transform per CTA of N/16 threads; each
-// thread holds 16 coefficients in registers (ntt_pass.cuh).  A forward
-// transform takes coefficient t + r N/16 in register r of thread t and
-// leaves NTT-domain value 16t + r there; the inverse goes the other way.
+// NTT kernels run one length-N transform per CTA of N/R threads; each
+// thread holds R = 2^RB coefficients in registers (ntt_pass.cuh, NttShape).
+// A forward transform takes coefficient t + r N/R in register r of thread t
+// and leaves NTT-domain value R t + r there; the inverse goes the other way.
 // NTT-domain arrays are stored permuted (ntt_pos) so that both ends of a
 // transform move through global memory coalesced.
 #include "kernels.cuh"
@@ -23,76 +23,85 @@ namespace {
 
 template <int LOGN>
 __device__ __forceinline__ u32 strided_idx(u32 t, u32 r) {
-  return t | (r << (LOGN - 4));
+  return t | (r << (LOGN - NttShape<LOGN>::RB));
 }
-// Storage position of NTT-domain coefficient 16t + r (the value thread t
-// holds in register r after a forward transform): t + r N/16, so that
+// Storage position of NTT-domain coefficient R t + r (the value thread t
+// holds in register r after a forward transform): t + r N/R, so that
 // stores after a forward transform and loads before an inverse transform
 // are coalesced.  Every NTT-domain array (database, keys, QP-NTT
 // ciphertexts, digit transforms, accumulators) uses this order; element-wise
 // kernels are indifferent to it and the ABI never exposes it.
 template <int LOGN>
 __device__ __forceinline__ u32 ntt_pos(u32 t, u32 r) {
-  return t | (r << (LOGN - 4));
+  return t | (r << (LOGN - NttShape<LOGN>::RB));
 }
 
-// Forward transform: x[r] = coefficient t + r N/16 (< 4q) -> x[r] = NTT
-// value 16t + r, canonical.  Uses s (smem_words(N) words) and all
+// registers of one transform per thread
+template <int LOGN>
+using NttRegs = u64[NttShape<LOGN>::R];
+
+// Forward transform: x[r] = coefficient t + r N/R (< 4q) -> x[r] = NTT
+// value R t + r, canonical.  Uses s (smem_words(N) words) and all
 // threads of the block; s may be reused after return.
 template <int LOGN>
-__device__ __forceinline__ void ntt_fwd(u64 (&x)[16], u64 *s, const NttPrime &P) {
-  constexpr int NP = Passes<LOGN>::count;
+__device__ __forceinline__ void ntt_fwd(NttRegs<LOGN> &x, u64 *s, const NttPrime &P) {
+  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int NP = Passes<LOGN, RB>::count;
   const u32 t = threadIdx.x;
   u32 wprev = 0;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     u32 lo, c, w;
-    Passes<LOGN>::fwd(p, lo, c, w);
+    Passes<LOGN, RB>::fwd(p, lo, c, w);
     if (p > 0) {
 #pragma unroll
-      for (u32 r = 0; r < 16; ++r) s[sidx(pass_idx(t, r, wprev))] = x[r];
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[r];
       __syncthreads();
 #pragma unroll
-      for (u32 r = 0; r < 16; ++r) x[r] = s[sidx(pass_idx(t, r, w))];
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
       __syncthreads();
     }
-    fwd_pass<LOGN>(x, t, lo, c, w, P.psi2, P.q);
+    fwd_pass<LOGN, RB>(x, t, lo, c, w, P.psi2, P.q);
     wprev = w;
   }
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) x[r] = reduce4(x[r], P.q);
+  for (u32 r = 0; r < R; ++r) x[r] = reduce4(x[r], P.q);
 }
 
-// Inverse transform: x[r] = NTT value 16t + r (< 2q) -> x[r] = coefficient
-// t + r N/16.  With SCALE the factor N^-1 is applied and the output is
+// Inverse transform: x[r] = NTT value R t + r (< 2q) -> x[r] = coefficient
+// t + r N/R.  With SCALE the factor N^-1 is applied and the output is
 // canonical; without it the output is N times the coefficient, in [0, 2q).
 template <int LOGN, bool SCALE = true>
-__device__ __forceinline__ void ntt_inv(u64 (&x)[16], u64 *s, const NttPrime &P) {
-  constexpr int NP = Passes<LOGN>::count;
+__device__ __forceinline__ void ntt_inv(NttRegs<LOGN> &x, u64 *s, const NttPrime &P) {
+  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int NP = Passes<LOGN, RB>::count;
   const u32 t = threadIdx.x;
   u32 wprev = 0;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     u32 lo, c, w;
-    Passes<LOGN>::inv(p, lo, c, w);
+    Passes<LOGN, RB>::inv(p, lo, c, w);
     if (p > 0) {
 #pragma unroll
-      for (u32 r = 0; r < 16; ++r) s[sidx(pass_idx(t, r, wprev))] = x[r];
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[r];
       __syncthreads();
 #pragma unroll
-      for (u32 r = 0; r < 16; ++r) x[r] = s[sidx(pass_idx(t, r, w))];
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
       __syncthreads();
     }
-    inv_pass<LOGN>(x, t, lo, c, w, P.ipsi2, P.q);
+    inv_pass<LOGN, RB>(x, t, lo, c, w, P.ipsi2, P.q);
     wprev = w;
   }
   if (SCALE) {
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) x[r] = shoup(x[r], P.ninv, P.ninv_s, P.q);
+    for (u32 r = 0; r < R; ++r) x[r] = shoup(x[r], P.ninv, P.ninv_s, P.q);
   }
 }
 
-inline size_t ntt_smem(const DevTables &h) { return (size_t)smem_words(h.N) * sizeof(u64); }
+template <int LOGN>
+constexpr size_t ntt_smem_bytes() {
+  return (size_t)((1u << LOGN) + ((1u << LOGN) >> NttShape<LOGN>::RB)) * sizeof(u64);
+}
 
 template <typename F>
 cudaError_t allow_smem(F *kernel, size_t bytes) {
@@ -106,7 +115,7 @@ cudaError_t allow_smem(F *kernel, size_t bytes) {
 // db[r][p][j].  grid (sp L, rows).
 // ---------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_db_load(const DevTables *T, const u32 *items, u32 plen, u32 sp, u64 *db) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
@@ -114,9 +123,10 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   const u64 row = blockIdx.y;
   const NttPrime P = T->prime[j];
   const u64 tt = T->t;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) {
+  for (u32 r = 0; r < R; ++r) {
     const u32 c = p * N + strided_idx<LOGN>(t, r);
     const u64 v = c < plen ? (u64)items[row * plen + c] : 0;
     x[r] = v > tt / 2 ? P.q - (tt - v) : v;
@@ -124,7 +134,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   ntt_fwd<LOGN>(x, s, P);
   u64 *out = db + ((row * sp + p) * L + j) * N;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -133,7 +143,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
 // grid (limb_end - limb_begin, units).
 // ---------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_ntt(const DevTables *T, u64 *base, u64 unit_stride, u32 limb_begin, int inverse,
           const u64 *src, u64 src_unit_stride) {
   extern __shared__ u64 s[];
@@ -143,26 +153,27 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   const NttPrime P = T->prime[l];
   const u64 *in = src ? src + u * src_unit_stride + (u64)l * N : base + u * unit_stride + (u64)l * N;
   u64 *out = base + u * unit_stride + (u64)l * N;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
   if (inverse) {
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
+    for (u32 r = 0; r < R; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
     ntt_inv<LOGN>(x, s, P);
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
+    for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
   } else {
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) x[r] = in[strided_idx<LOGN>(t, r)];
+    for (u32 r = 0; r < R; ++r) x[r] = in[strided_idx<LOGN>(t, r)];
     ntt_fwd<LOGN>(x, s, P);
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+    for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
   }
 }
 
 // Forward NTT of the P limbs of every job's destination (both polys),
 // in place.  grid (K, 2 * njobs).
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_ntt_jobs_p(const DevTables *T, const MulJob *jobs) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
@@ -170,12 +181,13 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const NttPrime P = T->prime[l];
   u64 *p = jobs[job].dst + ((u64)poly * (L + K) + l) * N;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
+  for (u32 r = 0; r < R; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
   ntt_fwd<LOGN>(x, s, P);  // contains barriers: all loads precede all stores
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) p[ntt_pos<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) p[ntt_pos<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -232,7 +244,7 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // blocks resident on one SM share one prime's twiddles in L1.
 // ---------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
@@ -243,9 +255,10 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   const u64 ps = (u64)LK * N;
   const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
   const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) {
+  for (u32 r = 0; r < R; ++r) {
     const u32 c = ntt_pos<LOGN>(t, r);
     u64 v;
     if (which == 0) v = barrett(a0[c], b0[c], P.q, P.mu);
@@ -256,7 +269,7 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   ntt_inv<LOGN, false>(x, s, P);  // N d in [0, 2q): the scale-down absorbs N^-1
   u64 *out = Tbuf + ((job * 3 + which) * LK + l) * N;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -304,7 +317,7 @@ struct KsArgs {
 };
 
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1)) k_ks_ntt(const DevTables *T, KsArgs A,
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks) k_ks_ntt(const DevTables *T, KsArgs A,
                                                              u64 *DN) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
@@ -312,11 +325,12 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1)) k_ks_nt
   const u64 job = blockIdx.y;
   const NttPrime P = T->prime[j];
   const u64 q = P.q;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
   if (d < L) {
     const u64 *zi = A.z + job * A.z_stride + (u64)d * N;
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) {
+    for (u32 r = 0; r < R; ++r) {
       const u64 v = zi[strided_idx<LOGN>(t, r)];
       x[r] = v >= q ? v - q : v;
     }
@@ -324,12 +338,12 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1)) k_ks_nt
     const u64 *ad = (d == L ? A.add0 + job * A.add0_stride : A.add1 + job * A.add1_stride) +
                     (u64)j * N;
 #pragma unroll
-    for (u32 r = 0; r < 16; ++r) x[r] = ad[strided_idx<LOGN>(t, r)];
+    for (u32 r = 0; r < R; ++r) x[r] = ad[strided_idx<LOGN>(t, r)];
   }
   ntt_fwd<LOGN>(x, s, P);
   u64 *o = DN + ((job * (L + A.n_add) + d) * L + j) * N;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) o[ntt_pos<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) o[ntt_pos<LOGN>(t, r)] = x[r];
 }
 
 // acc0/acc1 of one coefficient c of limb j for one job (see (B) above).
@@ -502,7 +516,7 @@ __global__ void k_ks_mac_out(const DevTables *T, const u64 *DN, u32 n_add, const
 // destination: C[job][2][L][N] (dst_to_jobs = 0), jobs[job].dst (1) or
 // sjobs[job].dst (2), both [2][L][N].  grid (L, 2 * njobs).
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_intt_jobs(const DevTables *T, const MulJob *jobs, const SubJob *sjobs, int src_from_jobs,
                 const u64 *O, int dst_to_jobs, u64 *C) {
   extern __shared__ u64 s[];
@@ -516,12 +530,13 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   if (dst_to_jobs == 1) out = jobs[job].dst + ((u64)poly * L + j) * N;
   else if (dst_to_jobs == 2) out = sjobs[job].dst + ((u64)poly * L + j) * N;
   else out = C + (((u64)job * 2 + poly) * L + j) * N;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
+  for (u32 r = 0; r < R; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
   ntt_inv<LOGN>(x, s, P);
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
 
 // k = 1: the selection entry is the leaf itself (Q limbs in NTT form);
@@ -661,7 +676,7 @@ __global__ void k_pm_ntt(const DevTables *T, const u64 *ct, const u64 *dbr, u64 
 // limb index) and the Shoup companion floor(w 2^64 / q) by long division.
 // grid (L, nkeys*2*L).
 template <int LOGN>
-__global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_key_prep(const DevTables *T, u64 *key, u64 *key_s) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
@@ -670,12 +685,13 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   const NttPrime P = T->prime[j];
   u64 *p = key + (unit * T->L + j) * N;
   u64 *ps = key_s + (unit * T->L + j) * N;
-  u64 x[16];
+  NttRegs<LOGN> x;
+  constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
+  for (u32 r = 0; r < R; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
   ntt_fwd<LOGN>(x, s, P);
 #pragma unroll
-  for (u32 r = 0; r < 16; ++r) {
+  for (u32 r = 0; r < R; ++r) {
     u64 w = x[r], rem = w, quo = 0;
     for (int b = 0; b < 64; ++b) {
       rem <<= 1;
@@ -688,8 +704,9 @@ __global__ void __launch_bounds__(1 << (LOGN - 4), (LOGN <= 13 ? 2 : 1))
   }
 }
 
-// blockDim = N / 16 for the transform kernels.
-inline dim3 ntt_block(const DevTables &h) { return dim3(h.N / 16); }
+// blockDim of the transform kernels: N / R threads.
+template <int LOGN>
+inline dim3 ntt_block() { return dim3(NttShape<LOGN>::threads); }
 
 #define CW_DISPATCH_LOGN(LOGN_, ...)                       \
   switch (LOGN_) {                                         \
@@ -725,9 +742,9 @@ cudaError_t launch_db_load(const DevTables *T, const DevTables &h, const u32 *it
   for (u64 r0 = 0; r0 < rows; r0 += chunk) {
     u64 nr = rows - r0 < chunk ? rows - r0 : chunk;
     CW_DISPATCH_LOGN(h.logN, {
-      cudaError_t e = allow_smem(k_db_load<LG>, ntt_smem(h));
+      cudaError_t e = allow_smem(k_db_load<LG>, ntt_smem_bytes<LG>());
       if (e != cudaSuccess) return e;
-      k_db_load<LG><<<dim3(sp * h.L, (u32)nr), ntt_block(h), ntt_smem(h), st>>>(
+      k_db_load<LG><<<dim3(sp * h.L, (u32)nr), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
           T, items + r0 * plen, plen, sp, db + r0 * sp * h.L * h.N);
     });
   }
@@ -742,9 +759,9 @@ cudaError_t launch_ntt(const DevTables *T, const DevTables &h, u64 *base, u32 un
   for (u32 u0 = 0; u0 < units; u0 += chunk) {
     u32 nu = units - u0 < chunk ? units - u0 : chunk;
     CW_DISPATCH_LOGN(h.logN, {
-      cudaError_t e = allow_smem(k_ntt<LG>, ntt_smem(h));
+      cudaError_t e = allow_smem(k_ntt<LG>, ntt_smem_bytes<LG>());
       if (e != cudaSuccess) return e;
-      k_ntt<LG><<<dim3(limb_end - limb_begin, nu), ntt_block(h), ntt_smem(h), st>>>(
+      k_ntt<LG><<<dim3(limb_end - limb_begin, nu), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
           T, base + (u64)u0 * unit_stride, unit_stride, limb_begin, inverse ? 1 : 0,
           src ? src + (u64)u0 * src_unit_stride : nullptr, src_unit_stride);
     });
@@ -777,9 +794,9 @@ cudaError_t launch_ntt_jobs_p(const DevTables *T, const DevTables &h, const MulJ
                               u32 njobs, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_ntt_jobs_p<LG>, ntt_smem(h));
+    cudaError_t e = allow_smem(k_ntt_jobs_p<LG>, ntt_smem_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_ntt_jobs_p<LG><<<dim3(h.K, 2 * njobs), ntt_block(h), ntt_smem(h), st>>>(T, jobs);
+    k_ntt_jobs_p<LG><<<dim3(h.K, 2 * njobs), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(T, jobs);
   });
   return cudaGetLastError();
 }
@@ -788,9 +805,9 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
                                u32 njobs, u64 *Tbuf, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_tensor_intt<LG>, ntt_smem(h));
+    cudaError_t e = allow_smem(k_tensor_intt<LG>, ntt_smem_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_tensor_intt<LG><<<dim3(njobs, 3, h.L + h.K), ntt_block(h), ntt_smem(h), st>>>(T, jobs,
+    k_tensor_intt<LG><<<dim3(njobs, 3, h.L + h.K), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(T, jobs,
                                                                                     Tbuf);
   });
   return cudaGetLastError();
@@ -807,9 +824,9 @@ cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf
 static cudaError_t launch_ks_ntt(const DevTables *T, const DevTables &h, const KsArgs &A,
                                  u32 njobs, u64 *DN, cudaStream_t st) {
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_ks_ntt<LG>, ntt_smem(h));
+    cudaError_t e = allow_smem(k_ks_ntt<LG>, ntt_smem_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_ks_ntt<LG><<<dim3(h.L + A.n_add, njobs, h.L), ntt_block(h), ntt_smem(h), st>>>(T, A, DN);
+    k_ks_ntt<LG><<<dim3(h.L + A.n_add, njobs, h.L), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(T, A, DN);
   });
   return cudaGetLastError();
 }
@@ -818,9 +835,9 @@ static cudaError_t launch_intt_jobs(const DevTables *T, const DevTables &h, cons
                                     const SubJob *sjobs, u32 njobs, int src_from_jobs,
                                     const u64 *O, int dst_to_jobs, u64 *C, cudaStream_t st) {
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_intt_jobs<LG>, ntt_smem(h));
+    cudaError_t e = allow_smem(k_intt_jobs<LG>, ntt_smem_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_intt_jobs<LG><<<dim3(h.L, 2 * njobs), ntt_block(h), ntt_smem(h), st>>>(
+    k_intt_jobs<LG><<<dim3(h.L, 2 * njobs), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
         T, jobs, sjobs, src_from_jobs, O, dst_to_jobs, C);
   });
   return cudaGetLastError();
@@ -977,9 +994,9 @@ cudaError_t launch_key_prep(const DevTables *T, const DevTables &h, u64 *key, u6
                             u32 nkeys, cudaStream_t st) {
   if (!nkeys) return cudaSuccess;
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_key_prep<LG>, ntt_smem(h));
+    cudaError_t e = allow_smem(k_key_prep<LG>, ntt_smem_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_key_prep<LG><<<dim3(h.L, nkeys * 2 * h.L), ntt_block(h), ntt_smem(h), st>>>(T, key,
+    k_key_prep<LG><<<dim3(h.L, nkeys * 2 * h.L), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(T, key,
                                                                                   key_s);
   });
   return cudaGetLastError();

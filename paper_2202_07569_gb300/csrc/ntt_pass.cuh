@@ -5,28 +5,31 @@
 // differs.  Index bit b of the transform is "butterfly bit" b: the forward
 // transform processes b = n-1 down to 0 (pairs idx, idx + 2^b, group
 // g = idx >> (b+1), twiddle psi[N/2^(b+1) + g]); the inverse processes
-// b = 0 up to n-1.  A pass takes up to four consecutive butterfly bits:
-// each of the N/16 threads holds 16 coefficients whose indices differ in a
-// 4-bit window [w, w+4) that contains the pass's bits, so all butterflies
-// of the pass are on registers.  Between passes the coefficients go
-// through shared memory, stored with one pad word after every 16 so that
-// the strided layouts of the passes are free of bank conflicts.
+// b = 0 up to n-1.  A pass takes up to RB consecutive butterfly bits: each
+// of the N/2^RB threads holds R = 2^RB coefficients whose indices differ in
+// an RB-bit window [w, w+RB) that contains the pass's bits, so all
+// butterflies of the pass are on registers.  Between passes the
+// coefficients go through shared memory, stored with one pad word after
+// every R so that the strided layouts of the passes are free of bank
+// conflicts.
 #pragma once
 #include "arith.cuh"
 
 namespace cw {
 
-// shared-memory slot of coefficient i (one pad word per 16)
-CW_HD u32 sidx(u32 i) { return i + (i >> 4); }
+// shared-memory slot of coefficient i (one pad word per 2^RB)
+template <int RB>
+CW_HD u32 sidx(u32 i) { return i + (i >> RB); }
 // words of shared memory for an N-point transform
-CW_HD u32 smem_words(u32 N) { return N + N / 16; }
+template <int RB>
+CW_HD u32 smem_words(u32 N) { return N + (N >> RB); }
 
-// coefficient index held in register r by thread t in a pass whose 4-bit
+// coefficient index held in register r by thread t in a pass whose RB-bit
 // window starts at bit w
+template <int RB>
 CW_HD u32 pass_idx(u32 t, u32 r, u32 w) {
-  return (t & ((1u << w) - 1)) | (r << w) | ((t >> w) << (w + 4));
+  return (t & ((1u << w) - 1)) | (r << w) | ((t >> w) << (w + RB));
 }
-
 // One (twiddle, Shoup companion) pair: a 16-byte read-only load on the
 // device.
 CW_HD void ld_pair(const u64 *p, u64 &a, u64 &b) {
@@ -45,22 +48,23 @@ CW_HD void ld_pair(const u64 *p, u64 &a, u64 &b) {
 CW_HD u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) { return a * w - mulhi(a, ws) * q; }
 
 // Forward butterflies (Harvey's lazy Cooley-Tukey) for bits lo+c-1 .. lo of
-// one thread's 16 values: values stay in [0, 4q) (q < 2^54 keeps 4q far
+// one thread's 2^RB values: values stay in [0, 4q) (q < 2^54 keeps 4q far
 // below 2^64); U is brought into [0, 2q), V = W x in [0, 2q), outputs
 // U + V and U - V + 2q.
-template <int LOGN>
+template <int LOGN, int RB>
 CW_HD void fwd_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *psi2, u64 q) {
   const u64 q2 = 2 * q;
+  constexpr u32 R = 1u << RB;
 #pragma unroll
-  for (int bi = 3; bi >= 0; --bi) {
+  for (int bi = RB - 1; bi >= 0; --bi) {
     if ((u32)bi >= c) continue;
     const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
     // registers r and r | 2^rb pair up; the twiddle depends only on the
     // bits of r above rb, so each distinct twiddle is loaded once
 #pragma unroll
-    for (u32 hv = 0; hv < (16u >> (rb + 1)); ++hv) {
+    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
       const u32 r0 = hv << (rb + 1);
-      const u32 g = pass_idx(t, r0, w) >> (b + 1);
+      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
       u64 W, Ws;
       ld_pair(psi2 + 2 * (m + g), W, Ws);
 #pragma unroll
@@ -79,17 +83,18 @@ CW_HD void fwd_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *psi2, u64 q)
 // Inverse butterflies (lazy Gentleman-Sande) for bits lo .. lo+c-1: inputs
 // and outputs in [0, 2q); U + V is brought back into [0, 2q), the difference
 // U - V + 2q < 4q goes through a lazy Shoup product.
-template <int LOGN>
+template <int LOGN, int RB>
 CW_HD void inv_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi2, u64 q) {
   const u64 q2 = 2 * q;
+  constexpr u32 R = 1u << RB;
 #pragma unroll
-  for (int bi = 0; bi < 4; ++bi) {
+  for (int bi = 0; bi < RB; ++bi) {
     if ((u32)bi >= c) continue;
     const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
 #pragma unroll
-    for (u32 hv = 0; hv < (16u >> (rb + 1)); ++hv) {
+    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
       const u32 r0 = hv << (rb + 1);
-      const u32 g = pass_idx(t, r0, w) >> (b + 1);
+      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
       u64 W, Ws;
       ld_pair(ipsi2 + 2 * (m + g), W, Ws);
 #pragma unroll
@@ -111,23 +116,37 @@ CW_HD u64 reduce4(u64 v, u64 q) {
   return v >= q ? v - q : v;
 }
 
-// Pass schedule: forward passes take bits from the top in chunks of four,
-// inverse passes from the bottom; a pass of c < 4 bits uses the window
+// Pass schedule: forward passes take bits from the top in chunks of RB,
+// inverse passes from the bottom; a pass of c < RB bits uses the window
 // clamped into [0, n).
-template <int LOGN>
+template <int LOGN, int RB>
 struct Passes {
-  static constexpr int count = (LOGN + 3) / 4;
+  static constexpr int count = (LOGN + RB - 1) / RB;
   CW_HDM static void fwd(int p, u32 &lo, u32 &c, u32 &w) {
-    int hi = LOGN - 4 * p;
-    c = hi >= 4 ? 4 : hi;
+    int hi = LOGN - RB * p;
+    c = hi >= RB ? RB : hi;
     lo = hi - c;
-    w = lo < LOGN - 4 ? lo : LOGN - 4;
+    w = lo < LOGN - RB ? lo : LOGN - RB;
   }
   CW_HDM static void inv(int p, u32 &lo, u32 &c, u32 &w) {
-    lo = 4 * p;
-    c = LOGN - (int)lo >= 4 ? 4 : LOGN - lo;
-    w = lo < LOGN - 4 ? lo : LOGN - 4;
+    lo = RB * p;
+    c = LOGN - (int)lo >= RB ? RB : LOGN - lo;
+    w = lo < LOGN - RB ? lo : LOGN - RB;
   }
+};
+
+// Shape of the device transforms of length 2^LOGN: 2^RB coefficients per
+// thread, N / 2^RB threads per block, at least min_blocks resident blocks
+// per SM (64 registers per thread up to N = 8192).  Sixteen coefficients
+// per thread: with 32 (256-thread blocks, 128 registers) a bare transform
+// is 10% faster, but the tensor kernel, which loads four operands per
+// coefficient before its transform, is 14% slower.
+template <int LOGN>
+struct NttShape {
+  static constexpr int RB = 4;
+  static constexpr int R = 1 << RB;
+  static constexpr int threads = (1 << LOGN) / R;
+  static constexpr int min_blocks = LOGN <= 13 ? 2 : 1;
 };
 
 }  // namespace cw

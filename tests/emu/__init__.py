@@ -36,7 +36,7 @@ def lib():
     l.emu_substitute.restype = None
     l.emu_scale.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p]
     l.emu_scale.restype = C.c_int
-    l.emu_ntt_compare.argtypes = [U32, U32, u64p, U64, u64p]
+    l.emu_ntt_compare.argtypes = [U32, U32, u64p, U64, u64p, U32]
     l.emu_ntt_compare.restype = C.c_uint64
     _lib = l
     return l

@@ -236,59 +236,61 @@ int emu_scale(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint6
 
 namespace {
 // The register-blocked schedule of the kernels, thread by thread: every
-// pass reads the thread's 16 slots, runs its butterflies, writes them back.
-template <int LOGN>
+// pass reads the thread's 2^RB slots, runs its butterflies, writes them back.
+template <int LOGN, int RB>
 void pass_ntt(u64 *a, const u64 *tw, u64 q, bool inverse, u64 ninv, u64 ninv_s) {
-  const u32 N = 1u << LOGN, T = N / 16;
-  std::vector<u64> s(smem_words(N));
-  for (u32 i = 0; i < N; ++i) s[sidx(i)] = a[i];
-  for (int p = 0; p < Passes<LOGN>::count; ++p) {
+  constexpr u32 R = 1u << RB;
+  const u32 N = 1u << LOGN, T = N / R;
+  std::vector<u64> s(smem_words<RB>(N));
+  for (u32 i = 0; i < N; ++i) s[sidx<RB>(i)] = a[i];
+  for (int p = 0; p < Passes<LOGN, RB>::count; ++p) {
     u32 lo, c, w;
-    if (inverse) Passes<LOGN>::inv(p, lo, c, w);
-    else Passes<LOGN>::fwd(p, lo, c, w);
+    if (inverse) Passes<LOGN, RB>::inv(p, lo, c, w);
+    else Passes<LOGN, RB>::fwd(p, lo, c, w);
     for (u32 t = 0; t < T; ++t) {
-      u64 x[16];
-      for (u32 r = 0; r < 16; ++r) x[r] = s[sidx(pass_idx(t, r, w))];
-      if (inverse) inv_pass<LOGN>(x, t, lo, c, w, tw + 2 * N, q);
-      else fwd_pass<LOGN>(x, t, lo, c, w, tw, q);
-      if (p == Passes<LOGN>::count - 1)
-        for (u32 r = 0; r < 16; ++r)
+      u64 x[R];
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
+      if (inverse) inv_pass<LOGN, RB>(x, t, lo, c, w, tw + 2 * N, q);
+      else fwd_pass<LOGN, RB>(x, t, lo, c, w, tw, q);
+      if (p == Passes<LOGN, RB>::count - 1)
+        for (u32 r = 0; r < R; ++r)
           x[r] = inverse ? shoup(x[r], ninv, ninv_s, q) : reduce4(x[r], q);
-      for (u32 r = 0; r < 16; ++r) s[sidx(pass_idx(t, r, w))] = x[r];
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, w))] = x[r];
     }
   }
-  for (u32 i = 0; i < N; ++i) a[i] = s[sidx(i)];
+  for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
+}
+
+template <int RB>
+void pass_ntt_n(u32 logN, u64 *a, const u64 *tw, u64 q, bool inverse, u64 ninv, u64 ninv_s) {
+  switch (logN) {
+    case 10: pass_ntt<10, RB>(a, tw, q, inverse, ninv, ninv_s); break;
+    case 11: pass_ntt<11, RB>(a, tw, q, inverse, ninv, ninv_s); break;
+    case 12: pass_ntt<12, RB>(a, tw, q, inverse, ninv, ninv_s); break;
+    case 13: pass_ntt<13, RB>(a, tw, q, inverse, ninv, ninv_s); break;
+    default: pass_ntt<14, RB>(a, tw, q, inverse, ninv, ninv_s); break;
+  }
 }
 }  // namespace
 
 extern "C" {
-// Runs the pass schedule and the stage-by-stage transform on the same data
-// for every prime of the parameter set; returns the number of mismatches.
+// Runs the pass schedule (windows of rb = 4 or 5 bits) and the stage-by-
+// stage transform on the same data for every prime of the parameter set;
+// returns the number of mismatches.
 uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
-                         const uint64_t *data) {
+                         const uint64_t *data, uint32_t rb) {
   Emu E(N, L, q, t);
   uint64_t bad = 0;
+  auto run = rb == 4 ? pass_ntt_n<4> : pass_ntt_n<5>;
   for (u32 l = 0; l < E.all.size(); ++l) {
     u64 pr = E.all[l];
     std::vector<u64> a(N), b(N);
     for (u32 i = 0; i < N; ++i) a[i] = b[i] = data[i] % pr;
     E.fwd(a.data(), l);
-    switch (E.logN) {
-      case 10: pass_ntt<10>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
-      case 11: pass_ntt<11>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
-      case 12: pass_ntt<12>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
-      case 13: pass_ntt<13>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
-      default: pass_ntt<14>(b.data(), E.tw[l].data(), pr, false, 0, 0); break;
-    }
+    run(E.logN, b.data(), E.tw[l].data(), pr, false, 0, 0);
     for (u32 i = 0; i < N; ++i) bad += a[i] != b[i];
     E.inv(a.data(), l);
-    switch (E.logN) {
-      case 10: pass_ntt<10>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
-      case 11: pass_ntt<11>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
-      case 12: pass_ntt<12>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
-      case 13: pass_ntt<13>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
-      default: pass_ntt<14>(b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]); break;
-    }
+    run(E.logN, b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]);
     for (u32 i = 0; i < N; ++i) bad += a[i] != b[i] || b[i] != data[i] % pr;
   }
   return bad;

@@ -115,11 +115,12 @@ def test_emulated_substitution_matches_oracle(orc):
         assert np.array_equal(out, O.substitute(g, ct, gk))
 
 
+@pytest.mark.parametrize("rb", [4, 5])
 @pytest.mark.parametrize("N,L", [(1024, 2), (2048, 1), (4096, 2), (8192, 4), (16384, 3)])
-def test_register_blocked_ntt_schedule_equals_stagewise(orc, N, L):
-    """The kernels' pass schedule (16 registers per thread, lazy reduction)
-    gives the same forward and inverse transforms as the level-by-level
-    butterflies, for every prime the library uses at this N."""
+def test_register_blocked_ntt_schedule_equals_stagewise(orc, N, L, rb):
+    """The kernels' pass schedule (2^rb registers per thread, lazy
+    reduction) gives the same forward and inverse transforms as the
+    level-by-level butterflies, for every prime the library uses at this N."""
     q = orc.primes(N, L)
     data = syn.Stream(10, N).below(1 << 62, N)
-    assert emu.lib().emu_ntt_compare(N, L, q, T, data) == 0
+    assert emu.lib().emu_ntt_compare(N, L, q, T, data, rb) == 0
