@@ -274,6 +274,83 @@ def run_gpu(args, rank: int, world: int, dist):
     return out
 
 
+def run_sharded(args, rank: int, world: int, dist):
+    """The metric's workload with the database's rows sharded over the
+    ranks (one GPU each): every rank answers the query over its block of
+    rows and the partial responses are summed modulo q_j after an
+    all-gather (paper_2202_07569_gb300/shard.py).  Total work is fixed:
+    strong scaling.  At one rank the step is the plain answer plus a sum of
+    one partial."""
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+    from paper_2202_07569_gb300.shard import ShardedDatabase
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    q, rlk, query, items, cw = make_inputs(12, args.rows)  # same database on every rank
+    ctx = B.Context(WL["N"], q, WL["t"], rlk)
+    if args.max_jobs:
+        ctx.set_option(B.OPT_MAX_JOBS, args.max_jobs)
+    sh = ShardedDatabase(ctx, items, cw, WL["m"])
+    del items
+    stream = torch.cuda.current_stream()
+    d_query = torch.from_numpy(query.view(np.int64)).to(f"cuda:{dev}")
+    d_resp = torch.empty((2, WL["L"], WL["N"]), dtype=torch.int64, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        sh.answer_device(d_query, d_resp)
+    torch.cuda.synchronize()
+    stats = ctx.last_stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            sh.answer_device(d_query, d_resp)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    # end to end: query from pinned host memory, response back to the host
+    h_query = torch.from_numpy(query.view(np.int64)).pin_memory()
+    h_resp = torch.empty((2, WL["L"], WL["N"]), dtype=torch.int64).pin_memory()
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        if dist:
+            dist.barrier()
+        t = time.perf_counter()
+        d_query.copy_(h_query, non_blocking=True)
+        sh.answer_device(d_query, d_resp)
+        h_resp.copy_(d_resp, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t)
+    mb = payload_mb(cw.shape[0])
+    out = {
+        "value": mb / (ms_per_step / 1e3),
+        "ms_per_step": ms_per_step,
+        "scaling": "strong",
+        "items_per_s": cw.shape[0] / (ms_per_step / 1e3),
+        "e2e": {"value": mb / statistics.median(e2e), "unit": "MB/s",
+                "h2d_bytes_per_step": int(query.nbytes), "d2h_bytes_per_step": int(d_resp.numel() * 8)},
+        "gpu_launches": (int(stats["kernel_launches"]) + 1) * args.steps,
+        "stats": stats,
+        "clocks": clk.summary(),
+        "shard": {"rank_rows": [sh.lo, sh.hi], "world": world},
+    }
+    sh.close()
+    ctx.close()
+    return out
+
+
 def run_large(args):
     """Large payloads (the paper's large-payload experiment, Sec. 4): index
     PIR over n = 16384 rows with k = 2 at N = 8192, L = 4, each row s
@@ -709,6 +786,9 @@ def main():
                     help="multiplications per kernel launch (0 = library default)")
     ap.add_argument("--batch", type=int, default=16,
                     help="queries per batched call in the batched-vs-plain comparison (0: skip)")
+    ap.add_argument("--shard-db", action="store_true",
+                    help="shard the database's rows over the ranks (strong scaling) instead of "
+                         "one replica per rank")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "large", "lossy", "folklore", "arith"],
                     help="c2: the metric's workload (default); c4: batched answering over "
                          "four databases")
@@ -763,6 +843,20 @@ def main():
             fn = {"c4": run_c4, "c5": run_c5, "large": run_large, "lossy": run_lossy,
                   "folklore": run_folklore, "arith": run_arith}[args.workload]
             print(json.dumps(dict(fn(args), data="synthetic", n_gpus=1)), flush=True)
+        return
+    if args.shard_db:
+        res = run_sharded(args, rank, world, dist)
+        if rank == 0:
+            line = dict(base, scaling="strong")
+            line["config"] = dict(base["config"], parallelism=(
+                f"database rows sharded over {world} GPU(s); partial responses all-gathered "
+                "and summed modulo q_j"))
+            if args.rows:
+                line["config"]["rows"] = args.rows
+            line.update(res)
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
         return
     res = run_gpu(args, rank, world, dist)
     if rank != 0:

@@ -183,6 +183,23 @@ int cwpir_answer_batch(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
 int cwpir_answer_batch_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                               uint32_t nq, const uint64_t *d_queries,
                               uint64_t *d_responses, void *stream);
+/* Exchange step of a database sharded by rows over several GPUs (one
+ * context per GPU, each holding a disjoint set of the rows with their own
+ * codewords).  The response is linear in the rows: r = sum over rows i of
+ * sel_i * DB_i mod Q (Eq. baseline-pir, Sec. 2.3; the Inner Product of
+ * Sec. 3.3.3), so each shard answers over its rows and the response is the
+ * sum of the partial responses modulo each q_j, bit-identical to answering
+ * over all rows on one GPU.  d_parts: [count][s][2][L][N] partial responses
+ * in coefficient form (residues below q_j, as returned by
+ * cwpir_answer_device), d_out: [s][2][L][N]; both device memory on ctx's
+ * GPU, owned by the caller, and d_out must not overlap d_parts.  stream: a
+ * cudaStream_t (NULL: legacy default stream); returns once enqueued.
+ * EINVAL for a null pointer, count = 0, or s = 0 or s > CWPIR_MAX_PLAINTEXTS.
+ * Moving the partials between GPUs (an all-gather) is the caller's. */
+int cwpir_sum_responses_device(cwpir_ctx *ctx, uint32_t count, uint32_t s,
+                               const uint64_t *d_parts, uint64_t *d_out,
+                               void *stream);
+
 /* Autotuner: times answers of the nq device queries (as for
  * cwpir_answer_batch_device) for each candidate number of multiplications
  * per launch in `candidates` (count entries, 0 = automatic), keeps the

@@ -103,6 +103,7 @@ def lib():
             "cwpir_free_db": (I, [vp, C.c_int32]),
             "cwpir_answer": (I, [vp, C.c_int32, U32, u64p, u64p]),
             "cwpir_answer_device": (I, [vp, C.c_int32, U32, vp, vp, vp]),
+            "cwpir_sum_responses_device": (I, [vp, U32, U32, vp, vp, vp]),
             "cwpir_mul": (I, [vp, u64p, u64p, u64p]),
             "cwpir_substitute": (I, [vp, U32, u64p, u64p]),
             "cwpir_expand": (I, [vp, U32, U32, u64p, u64p]),
@@ -286,6 +287,13 @@ class Context:
     def answer_device(self, db: int, query_ptr: int, resp_ptr: int, c: int = 0,
                       stream: int = 0):
         self._check(lib().cwpir_answer_device(self._h, db, c, query_ptr, resp_ptr, stream))
+
+    def sum_responses_device(self, count: int, s: int, parts_ptr: int, out_ptr: int,
+                             stream: int = 0):
+        """Sum of `count` partial responses [count][s][2][L][N] (device) into
+        [s][2][L][N] modulo each q_j: the exchange step of a sharded database."""
+        self._check(lib().cwpir_sum_responses_device(self._h, count, s, parts_ptr, out_ptr,
+                                                     stream))
 
     def answer_batch(self, db: int, queries, c: int = 0) -> np.ndarray:
         q = _u64(queries)

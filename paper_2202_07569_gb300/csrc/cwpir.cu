@@ -1056,6 +1056,21 @@ int cwpir_answer(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *que
   return cwpir_answer_batch(c, db_id, cfac, 1, query, response);
 }
 
+int cwpir_sum_responses_device(cwpir_ctx *c, uint32_t count, uint32_t s,
+                               const uint64_t *d_parts, uint64_t *d_out, void *stream) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!d_parts || !d_out) return fail(c, CWPIR_EINVAL, "null buffer");
+  if (count == 0 || s == 0 || s > CWPIR_MAX_PLAINTEXTS)
+    return fail(c, CWPIR_EINVAL, "need count >= 1 and 1 <= s <= %d", CWPIR_MAX_PLAINTEXTS);
+  const u64 ctw = c->ct();
+  for (u32 p = 0; p < s; ++p)
+    CUDA_TRY(c, cw::launch_ct_sum(c->d_tab, c->h, d_parts + p * ctw, count, (u64)s * ctw,
+                                  d_out + p * ctw, (cudaStream_t)stream));
+  return 0;
+}
+
 int cwpir_autotune(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
                    const uint64_t *d_queries, uint64_t *d_responses, const int64_t *cand,
                    uint32_t count, int64_t *best, double *best_ms) {
@@ -1287,7 +1302,7 @@ int cwpir_arith_cw_eq(cwpir_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
   }
   if ((rc = product_rows(c, d1, leaves.p, prods.p))) return rc;
   u64 *kp = fac.p + (u64)k * ctw, *res = fac.p + (u64)(k + 1) * ctw;
-  CUDA_TRY(c, cw::launch_ct_sum(c->d_tab, c->h, prods.p, m, kp, c->stream));
+  CUDA_TRY(c, cw::launch_ct_sum(c->d_tab, c->h, prods.p, m, c->ct(), kp, c->stream));
   // factors k' - i, i < k, and their product by the balanced tree
   CUDA_TRY(c, cw::launch_minus_consts(c->d_tab, c->h, kp, k, fac.p, c->stream));
   const u64 *prod = fac.p;

@@ -609,11 +609,12 @@ __global__ void k_folklore_leaves(const DevTables *T, const u64 *query, u64 *out
 }
 
 // Arithmetic operator steps, coefficient form; grid (N/256, 2L[, count]).
-__global__ void k_ct_sum(const DevTables *T, const u64 *in, u32 count, u64 *out) {
+__global__ void k_ct_sum(const DevTables *T, const u64 *in, u32 count, u64 in_stride,
+                         u64 *out) {
   const u32 N = T->N, L = T->L, i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
-  const u64 q = T->prime[pl % L].q, ctw = 2ull * L * N, off = (u64)pl * N + i;
+  const u64 q = T->prime[pl % L].q, off = (u64)pl * N + i;
   u64 a = 0;
-  for (u32 x = 0; x < count; ++x) a = addq(a, in[x * ctw + off], q);
+  for (u32 x = 0; x < count; ++x) a = addq(a, in[x * in_stride + off], q);
   out[off] = a;
 }
 
@@ -928,8 +929,8 @@ cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const
 }
 
 cudaError_t launch_ct_sum(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
-                          u64 *out, cudaStream_t st) {
-  k_ct_sum<<<dim3(h.N / 256, 2 * h.L), 256, 0, st>>>(T, in, count, out);
+                          u64 in_stride, u64 *out, cudaStream_t st) {
+  k_ct_sum<<<dim3(h.N / 256, 2 * h.L), 256, 0, st>>>(T, in, count, in_stride, out);
   return cudaGetLastError();
 }
 

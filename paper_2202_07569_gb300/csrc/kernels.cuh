@@ -99,10 +99,12 @@ cudaError_t launch_pm_ntt(const DevTables *T, const DevTables &h, const u64 *ct_
 cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const u64 *query,
                                    u32 count, u64 *out, cudaStream_t st);
 // Element-wise ciphertext steps of the arithmetic operator (coefficient
-// form [2][L][N]): out = sum of `count` ciphertexts; out[f] = in minus the
-// constant plaintext f (Delta f off c0 at x^0), f < count; out = s * in.
+// form [2][L][N]): out = sum of `count` ciphertexts in[x * in_stride]
+// (residues below q_j; also the sum of a sharded database's partial
+// responses); out[f] = in minus the constant plaintext f (Delta f off c0 at
+// x^0), f < count; out = s * in.
 cudaError_t launch_ct_sum(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
-                          u64 *out, cudaStream_t st);
+                          u64 in_stride, u64 *out, cudaStream_t st);
 cudaError_t launch_minus_consts(const DevTables *T, const DevTables &h, const u64 *in,
                                 u32 count, u64 *out, cudaStream_t st);
 cudaError_t launch_ct_scalar(const DevTables *T, const DevTables &h, const u64 *in, u64 s,
