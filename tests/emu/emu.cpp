@@ -285,10 +285,15 @@ uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
   for (u32 l = 0; l < E.all.size(); ++l) {
     u64 pr = E.all[l];
     std::vector<u64> a(N), b(N);
-    for (u32 i = 0; i < N; ++i) a[i] = b[i] = data[i] % pr;
+    // the schedule accepts lazy inputs: below 4q forward, below 2q inverse
+    for (u32 i = 0; i < N; ++i) {
+      a[i] = data[i] % pr;
+      b[i] = a[i] + (data[i] >> 62) * pr;
+    }
     E.fwd(a.data(), l);
     run(E.logN, b.data(), E.tw[l].data(), pr, false, 0, 0);
     for (u32 i = 0; i < N; ++i) bad += a[i] != b[i];
+    for (u32 i = 0; i < N; ++i) b[i] += ((data[i] >> 59) & 1) * pr;
     E.inv(a.data(), l);
     run(E.logN, b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]);
     for (u32 i = 0; i < N; ++i) bad += a[i] != b[i] || b[i] != data[i] % pr;

@@ -93,9 +93,11 @@ def test_exact_scale_down(orc, N, L):
     qa = np.array(q, np.uint64)
     for i, d in enumerate(ds):
         assert abs(d) <= dmax
-        # the kernels hand over N d in lazy form: residues in [0, 2q)
-        dq = np.array([(N * d) % v + (v if i % 2 else 0) for v in q], np.uint64)
-        dp = np.array([(N * d) % v + (v if i % 3 == 1 else 0) for v in p], np.uint64)
+        # the kernels hand over N d in lazy form: residues in [0, 2q),
+        # here each residue plus 0 or 1 times its prime
+        dq = np.array([(N * d) % v + (i + j) % 2 * v for j, v in enumerate(q)], np.uint64)
+        dp = np.array([(N * d) % v + (i + j + 1) % 2 * v for j, v in enumerate(p)],
+                      np.uint64)
         out = np.zeros(L, np.uint64)
         assert emu.lib().emu_scale(N, L, qa, T, dq, dp, out) == 1
         num = T * d
@@ -120,7 +122,8 @@ def test_emulated_substitution_matches_oracle(orc):
 def test_register_blocked_ntt_schedule_equals_stagewise(orc, N, L, rb):
     """The kernels' pass schedule (2^rb registers per thread, lazy
     reduction) gives the same forward and inverse transforms as the
-    level-by-level butterflies, for every prime the library uses at this N."""
+    level-by-level butterflies, for every prime the library uses at this N,
+    from lazy inputs below 4q (forward) and 2q (inverse)."""
     q = orc.primes(N, L)
-    data = syn.Stream(10, N).below(1 << 62, N)
+    data = syn.Stream(10, N).words(N)
     assert emu.lib().emu_ntt_compare(N, L, q, T, data, rb) == 0
