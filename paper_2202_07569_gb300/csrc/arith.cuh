@@ -2,9 +2,10 @@
 // the BFV multiplication (FV scheme, arXiv 2202.07569 Sec. 2.1.1), written
 // for the 32-bit integer pipes of sm_103a.  Every function is exact.
 //
-// Residues are u64 values below primes q < 2^54.  The functions are
-// __host__ __device__ so that the same arithmetic can be exercised on the
-// CPU by the test suite.
+// Ciphertext residues are u64 values below primes q < 2^54; the extension
+// basis of the tensor product uses 30-bit primes held in 32-bit words.  The
+// functions are __host__ __device__ so that the same arithmetic can be
+// exercised on the CPU by the test suite.
 #pragma once
 #include <stdint.h>
 
@@ -22,14 +23,29 @@ typedef uint64_t u64;
 typedef uint32_t u32;
 
 constexpr int kMaxL = 8;       // ciphertext primes
-constexpr int kMaxK = 9;       // extension primes (L + 1)
-constexpr int kMaxP = kMaxL + kMaxK;
+constexpr int kMaxK = 17;      // extension primes (30-bit)
+
+// Extension primes used with L ciphertext primes: the smallest count of
+// 30-bit primes (each above 2^29.99) whose product P exceeds 2^17 t N Q for
+// 54-bit q_j, t < 2^20 and N <= 2^14.  P > N Q makes the tensor exact in
+// the joint basis and P > t N Q the scale-down's quotient (below).
+CW_HD constexpr int ext_count(int L) {
+  return L <= 1 ? 4 : L == 2 ? 6 : L == 3 ? 8 : L == 4 ? 9 : L == 5 ? 11 : L == 6 ? 13
+       : L == 7 ? 15 : 17;
+}
 
 CW_HD u64 mulhi(u64 a, u64 b) {
 #if defined(__CUDA_ARCH__)
   return __umul64hi(a, b);
 #else
   return (u64)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+CW_HD u32 mulhi32(u32 a, u32 b) {
+#if defined(__CUDA_ARCH__)
+  return __umulhi(a, b);
+#else
+  return (u32)(((u64)a * b) >> 32);
 #endif
 }
 
@@ -86,35 +102,12 @@ struct Acc128 {
   }
 };
 
-// Exact sum of a few products a * b with a < 2^55 and constants b < 2^54
-// given as 27-bit halves (b = b1 2^27 + b0): with a = a1 2^27 + a0 each
-// product is four 32 x 32 + 64 multiply-adds into the words
-// ll = sum a0 b0, x = sum (a0 b1 + a1 b0), hh = sum a1 b1 (partials below
-// 2^55, so up to 8 terms cannot overflow 64 bits), and the sum is
-// ll + x 2^27 + hh 2^54.
+// 27-bit halves of a constant b < 2^54: b = out[1] 2^27 + out[0].
 constexpr u32 kMask27 = (1u << 27) - 1;
 CW_HD void split27(u64 b, u32 *out) {
   out[0] = (u32)b & kMask27;
   out[1] = (u32)(b >> 27);
 }
-struct Acc3 {
-  u64 ll = 0, x = 0, hh = 0;
-  CW_HDM void mac(u64 a, const u32 *b) {
-    const u32 a0 = (u32)a & kMask27, a1 = (u32)(a >> 27);
-    ll += (u64)a0 * b[0];
-    x += (u64)a0 * b[1];
-    x += (u64)a1 * b[0];
-    hh += (u64)a1 * b[1];
-  }
-  CW_HDM void add(u64 v) { ll += v; }
-  // the sum as hi 2^64 + lo (the caller bounds it below 2^112)
-  CW_HDM void get(u64 &hi, u64 &lo) const {
-    const u64 l1 = ll + (x << 27);
-    const u64 l2 = l1 + (hh << 54);
-    hi = (x >> 37) + (hh >> 10) + (l1 < ll ? 1 : 0) + (l2 < l1 ? 1 : 0);
-    lo = l2;
-  }
-};
 
 // ---------------------------------------------------------------------
 // NTT butterflies (negacyclic, psi = primitive 2N-th root of unity).
@@ -141,7 +134,7 @@ CW_HD void inv_bfly(u64 *a, u32 b, u32 logh, u32 m, const u64 *ipsi2, u64 q) {
   a[j + len] = shoup(subq(U, V, q), ipsi2[2 * (m + g)], ipsi2[2 * (m + g) + 1], q);
 }
 
-// Per-prime NTT data in device memory.
+// Per-prime NTT data of a ciphertext prime, in device memory.
 struct NttPrime {
   u64 q, mu;          // prime, Barrett constant floor(2^116/q)
   u64 ninv, ninv_s;   // N^-1 mod q and Shoup companion
@@ -150,57 +143,80 @@ struct NttPrime {
 };
 
 // ---------------------------------------------------------------------
-// Exact centered base conversion between RNS bases.
-//
-// x is given by residues x_j modulo the source primes s_j (product S).
-// With y_j = [x_j * (S/s_j)^-1]_{s_j}, sum_j y_j (S/s_j) = x + v S where
-// v = floor(sum_j y_j / s_j), and the centered representative of x is
-// x_c = sum_j y_j (S/s_j) - rho S with rho = round(sum_j y_j / s_j)
-// (S is odd, so sum_j y_j/s_j is never a half integer).
-//
-// rho is read from a 64.64 fixed-point sum of phi_j <= y_j 2^64 / s_j,
-// each low by less than 2 units, so the sum is low by less than 2*ns units:
-// rho = hi(2^63 + sum phi) unless the low word is within 2*ns of 2^64; in
-// that case x is within 2*ns*S/2^64 of S/2 and the exact comparison of x
-// with (S-1)/2 in mixed radix (Garner) decides.
+// 30-bit extension primes 2^29 < p < 2^30 in 32-bit words.
 // ---------------------------------------------------------------------
-struct BaseConv {
-  u32 ns, nd;
-  u64 s[kMaxK];                 // source primes
-  u64 theta[kMaxK], theta_s[kMaxK]; // (S/s_j)^-1 mod s_j
-  u64 w_hi[kMaxK], w_lo[kMaxK];     // floor(2^128 / s_j)
-  u64 d[kMaxK];                 // target primes
-  u64 hat[kMaxK][kMaxK], hat_s[kMaxK][kMaxK]; // (S/s_j) mod d_k
-  u64 smod[kMaxK], smod_s[kMaxK];   // S mod d_k
-  u64 negsmod[kMaxK];           // (-S) mod d_k
-  u64 d_mu[kMaxK];              // floor(2^116 / d_k)
-  u64 mrinv[kMaxK][kMaxK], mrinv_s[kMaxK][kMaxK]; // s_i^-1 mod s_j, i < j
-  u64 half_mr[kMaxK];           // mixed-radix digits of (S-1)/2
+struct ExtPrime {
+  u32 p;
+  u32 mu60;   // floor(2^60 / p), in (2^30, 2^31)
+  u64 mu64;   // floor(2^64 / p)
 };
 
-// 1 if x > (S-1)/2, by exact mixed-radix comparison.
-template <int NS>
-CW_HD u64 mr_greater_half(const u64 *x, const BaseConv &C) {
-  u64 a[NS];
-  for (int j = 0; j < NS; ++j) {
-    u64 sj = C.s[j], v = x[j];
+// v mod p for any v < 2^64: qh = floor(v mu64 / 2^64) lies in
+// (v/p - v/2^64 - 1, v/p], so v - qh p is in [0, 2p).
+CW_HD u32 reduce_ext(u64 v, const ExtPrime &E) {
+  const u32 r = (u32)(v - mulhi(v, E.mu64) * E.p);
+  return r >= E.p ? r - E.p : r;
+}
+
+// a b mod p in [0, 2p) for a, b < p (Barrett on 32-bit words): with
+// x = a b < 2^60 and x1 = floor(x / 2^28) < 2^32, qh = floor(x1 mu60 / 2^32)
+// satisfies x/p - 1.5 < qh <= x/p, so r = x - qh p is in [0, 3p) (below
+// 2^32: the low word suffices) and one subtraction of 2p brings it below 2p.
+CW_HD u32 mulmod_ext_lazy(u32 a, u32 b, const ExtPrime &E) {
+  const u64 x = (u64)a * b;
+  const u32 qh = mulhi32((u32)(x >> 28), E.mu60);
+  const u32 r = (u32)x - qh * E.p;
+  return r >= 2 * E.p ? r - 2 * E.p : r;
+}
+
+// ---------------------------------------------------------------------
+// Exact centered conversion out of the ciphertext basis Q = q_0 ... q_{L-1}.
+//
+// x is given by its residues x_j.  With y_j = [x_j (Q/q_j)^-1]_{q_j},
+// sum_j y_j (Q/q_j) = x + v Q with v = floor(sum_j y_j / q_j), and the
+// centered representative of x is x_c = sum_j y_j (Q/q_j) - rho Q with
+// rho = round(sum_j y_j / q_j) (Q is odd, so the sum is never a half
+// integer).
+//
+// rho is read from a 64.64 fixed-point sum of phi_j <= y_j 2^64 / q_j,
+// each low by less than 2 units, so the sum is low by less than 2L units:
+// rho = hi(2^63 + sum phi) unless the low word is within 2L of 2^64; in
+// that case x is within 2L Q/2^64 of Q/2 and the exact comparison of x
+// with (Q-1)/2 in mixed radix (Garner) decides.
+// ---------------------------------------------------------------------
+struct QConv {
+  u64 q[kMaxL];
+  u64 mu[kMaxL];                      // floor(2^116 / q_j)
+  u64 theta[kMaxL], theta_s[kMaxL];   // (Q/q_j)^-1 mod q_j
+  u64 w_hi[kMaxL], w_lo[kMaxL];       // floor(2^128 / q_j)
+  u64 mrinv[kMaxL][kMaxL], mrinv_s[kMaxL][kMaxL];  // q_i^-1 mod q_j, i < j
+  u64 half_mr[kMaxL];                 // mixed-radix digits of (Q-1)/2
+};
+
+// 1 if x > (Q-1)/2, by exact mixed-radix comparison (x_j < q_j).
+template <int L>
+CW_HD u64 mr_greater_half(const u64 *x, const QConv &C) {
+  u64 a[L];
+  for (int j = 0; j < L; ++j) {
+    u64 qj = C.q[j], v = x[j];
     for (int i = 0; i < j; ++i) {
-      u64 ai = a[i] >= sj ? a[i] - sj : a[i];
-      v = shoup(subq(v, ai, sj), C.mrinv[i][j], C.mrinv_s[i][j], sj);
+      u64 ai = a[i] >= qj ? a[i] - qj : a[i];
+      v = shoup(subq(v, ai, qj), C.mrinv[i][j], C.mrinv_s[i][j], qj);
     }
     a[j] = v;
   }
-  for (int j = NS - 1; j >= 0; --j)
+  for (int j = L - 1; j >= 0; --j)
     if (a[j] != C.half_mr[j]) return a[j] > C.half_mr[j] ? 1 : 0;
-  return 0;  // equal: x = (S-1)/2 is not greater
+  return 0;  // equal: x = (Q-1)/2 is not greater
 }
 
-// hi(2^63 + sum_j phi_j) and whether the low word is in the ambiguous zone.
+// hi(2^63 + sum_j phi_j) with phi_j = y_j w_j / 2^64 and w_j = floor(2^128 /
+// s_j) (y_j < s_j), and whether the low word is in the ambiguous zone.
 template <int NS>
-CW_HD u64 round_sum(const u64 *y, const BaseConv &C, bool *ambiguous) {
+CW_HD u64 round_sum(const u64 *y, const u64 *w_hi, const u64 *w_lo, bool *ambiguous) {
   u64 lo = 0x8000000000000000ull, hi = 0;
   for (int j = 0; j < NS; ++j) {
-    u64 phi = y[j] * C.w_hi[j] + mulhi(y[j], C.w_lo[j]);
+    u64 phi = y[j] * w_hi[j] + mulhi(y[j], w_lo[j]);
     lo += phi;
     hi += (lo < phi) ? 1 : 0;
   }
@@ -208,28 +224,37 @@ CW_HD u64 round_sum(const u64 *y, const BaseConv &C, bool *ambiguous) {
   return hi;
 }
 
-// Centered conversion of one coefficient: x (NS source residues) -> out
-// (ND target residues of x_c): out_k = [sum_j y_j (S/s_j) - rho S]_{d_k},
-// accumulated exactly in 128 bits and reduced once.
-template <int NS, int ND>
-CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
-  u64 y[NS];
-  for (int j = 0; j < NS; ++j) y[j] = shoup(x[j], C.theta[j], C.theta_s[j], C.s[j]);
+// Centered conversion Q -> extension primes of one coefficient:
+// out_k = [sum_j y_j (Q/q_j) - rho Q]_{p_k}.  Each y_j < 2^54 is split into
+// 27-bit halves, y_j = yh 2^27 + yl, so every product of a half with a
+// 30-bit constant is below 2^57 and the 2L products plus rho (-Q mod p_k)
+// sum below 2^62 in one 64-bit word, reduced once.
+struct LiftTab {
+  QConv Q;
+  ExtPrime ext[kMaxK];
+  u32 h[kMaxL][kMaxK], h27[kMaxL][kMaxK];  // (Q/q_j) mod p_k, 2^27 (Q/q_j) mod p_k
+  u32 negq[kMaxK];                         // (-Q) mod p_k
+};
+
+template <int L, int K>
+CW_HD void lift_ext(const u64 *x, u32 *out, const LiftTab &C) {
+  u64 y[L];
+  for (int j = 0; j < L; ++j) y[j] = shoup(x[j], C.Q.theta[j], C.Q.theta_s[j], C.Q.q[j]);
   bool amb;
-  u64 rho = round_sum<NS>(y, C, &amb);
-  if (amb) rho += mr_greater_half<NS>(x, C);
-  for (int k = 0; k < ND; ++k) {
-    Acc128 a;
-    for (int j = 0; j < NS; ++j) a.mac(y[j], C.hat[j][k]);
-    a.mac(rho, C.negsmod[k]);
-    out[k] = barrett_reduce(a.hi, a.lo, C.d[k], C.d_mu[k]);
+  u64 rho = round_sum<L>(y, C.Q.w_hi, C.Q.w_lo, &amb);
+  if (amb) rho += mr_greater_half<L>(x, C.Q);
+  for (int k = 0; k < K; ++k) {
+    u64 s = rho * C.negq[k];
+    for (int j = 0; j < L; ++j)
+      s += (y[j] & kMask27) * C.h[j][k] + (y[j] >> 27) * C.h27[j][k];
+    out[k] = reduce_ext(s, C.ext[k]);
   }
 }
 
 // ---------------------------------------------------------------------
 // Exact scale-down e = round(t d / Q) mod q_j of one tensor coefficient d,
 // known modulo Q (residues dq) and modulo P = prod p_k (residues dp), with
-// |d| < 2N(Q/2)^2 and P > t N Q + 1.
+// |d| < N Q^2 / 2 and P > 2^17 t N Q.
 //   eps = [t d]_Q centered: y_j = [d_j * t (Q/q_j)^-1]_{q_j}, rho as above,
 //   r = (t d - eps)/Q = round(t d / Q) exactly; modulo p_k:
 //   r_k = [t Q^-1]_{p_k} d_k - sum_j y_j [q_j^-1]_{p_k} + rho, and its
@@ -241,56 +266,59 @@ CW_HD void lift_centered(const u64 *x, u64 *out, const BaseConv &C) {
 // (f = N: the inverse transforms that produce d skip their N^-1); every
 // constant that multiplies d carries f^-1.
 struct ScaleTab {
+  QConv Q;
   u64 t_theta[kMaxL], t_theta_s[kMaxL]; // t f^-1 (Q/q_j)^-1 mod q_j
   u64 t_mod[kMaxL], t_mod_s[kMaxL];     // t f^-1 mod q_j (ambiguous path)
-  // yb_k = [r_k (P/p_k)^-1]_{p_k} = [A_k (f d)_k + sum_j B_jk y_j + C_k rho]_{p_k}
-  u64 A[kMaxK];          // t f^-1 Q^-1 (P/p_k)^-1 mod p_k
-  u64 B[kMaxL][kMaxK];   // -q_j^-1 (P/p_k)^-1 mod p_k
-  u64 Cr[kMaxK];         // (P/p_k)^-1 mod p_k
-  BaseConv q2b;  // Q -> P conversion data (fraction and Garner parts used)
-  BaseConv b2q;  // P -> Q conversion
-  // the constants of the two multiply-accumulate stages as 27-bit halves
-  u32 A2[kMaxK][2], B2[kMaxL][kMaxK][2], Cr2[kMaxK][2];
-  u32 hat2[kMaxK][kMaxL][2], negs2[kMaxL][2];  // b2q.hat[k][j], b2q.negsmod[j]
+  ExtPrime ext[kMaxK];
+  // yb_k = [A_k (f d)_k + sum_j (B_jk yl_j + B27_jk yh_j) + C_k rho]_{p_k}
+  u32 A[kMaxK];                          // t f^-1 Q^-1 (P/p_k)^-1 mod p_k
+  u32 B[kMaxL][kMaxK], B27[kMaxL][kMaxK]; // -q_j^-1 (P/p_k)^-1 mod p_k, times 2^27
+  u32 Cr[kMaxK];                         // (P/p_k)^-1 mod p_k
+  u64 pw_hi[kMaxK], pw_lo[kMaxK];        // floor(2^128 / p_k)
+  // e_j = [sum_k yb_k (P/p_k) + rho2 (-P)]_{q_j}, constants as 27-bit halves
+  u32 hat2[kMaxK][kMaxL][2], negp2[kMaxL][2];
 };
 
-// dq, dp: residues of f*d below 2^55 (lazy [0, 2q) values are fine).
-// Returns false if the P-basis rounding ever lands in the ambiguous zone,
-// which the bound on |r| rules out; callers record it as an internal error.
+// dq: residues of f*d below 2^55 (lazy [0, 2q) values are fine); dp:
+// residues below 2^31 (lazy [0, 2p)).  Returns false if the P-basis
+// rounding ever lands in the ambiguous zone, which the bound on |r| rules
+// out; callers record it as an internal error.
 template <int L>
 CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S) {
-  constexpr int K = L + 1;
+  constexpr int K = ext_count(L);
   u64 y[L];
   for (int j = 0; j < L; ++j)
-    y[j] = shoup(dq[j], S.t_theta[j], S.t_theta_s[j], S.q2b.s[j]);
+    y[j] = shoup(dq[j], S.t_theta[j], S.t_theta_s[j], S.Q.q[j]);
   bool amb;
-  u64 rho = round_sum<L>(y, S.q2b, &amb);
+  u64 rho = round_sum<L>(y, S.Q.w_hi, S.Q.w_lo, &amb);
   if (amb) {
     u64 eps[L];
     for (int j = 0; j < L; ++j)
-      eps[j] = shoup(dq[j], S.t_mod[j], S.t_mod_s[j], S.q2b.s[j]);
-    rho += mr_greater_half<L>(eps, S.q2b);
+      eps[j] = shoup(dq[j], S.t_mod[j], S.t_mod_s[j], S.Q.q[j]);
+    rho += mr_greater_half<L>(eps, S.Q);
   }
-  // L + 2 and K + 1 products below 2^55 * 2^54 each: sums below 2^112
+  // dp_k A_k < 2^61, 2L products of 27-bit halves with 30-bit constants
+  // below 2^57 each (2^61 for L = 8), rho C_k < 2^34: the sum fits 2^62
   u64 yb[K];
   for (int k = 0; k < K; ++k) {
-    Acc3 a;
-    a.mac(dp[k], S.A2[k]);
-    for (int j = 0; j < L; ++j) a.mac(y[j], S.B2[j][k]);
-    a.mac(rho, S.Cr2[k]);
-    u64 hi, lo;
-    a.get(hi, lo);
-    yb[k] = barrett_reduce(hi, lo, S.b2q.s[k], S.q2b.d_mu[k]);
+    u64 s = dp[k] * S.A[k] + rho * S.Cr[k];
+    for (int j = 0; j < L; ++j)
+      s += (y[j] & kMask27) * S.B[j][k] + (y[j] >> 27) * S.B27[j][k];
+    yb[k] = reduce_ext(s, S.ext[k]);
   }
   bool amb2;
-  u64 rho2 = round_sum<K>(yb, S.b2q, &amb2);
+  u64 rho2 = round_sum<K>(yb, S.pw_hi, S.pw_lo, &amb2);
+  // K + 1 <= 18 products of values below 2^30 with 27-bit halves: the words
+  // ll and x stay below 18 * 2^57 < 2^62.2; the sum ll + x 2^27 < 2^90
   for (int j = 0; j < L; ++j) {
-    Acc3 a;
-    for (int k = 0; k < K; ++k) a.mac(yb[k], S.hat2[k][j]);
-    a.mac(rho2, S.negs2[j]);
-    u64 hi, lo;
-    a.get(hi, lo);
-    out[j] = barrett_reduce(hi, lo, S.b2q.d[j], S.b2q.d_mu[j]);
+    u64 ll = rho2 * S.negp2[j][0], x = rho2 * S.negp2[j][1];
+    for (int k = 0; k < K; ++k) {
+      ll += yb[k] * S.hat2[k][j][0];
+      x += yb[k] * S.hat2[k][j][1];
+    }
+    const u64 lo = ll + (x << 27);
+    const u64 hi = (x >> 37) + (lo < ll ? 1 : 0);
+    out[j] = barrett_reduce(hi, lo, S.Q.q[j], S.Q.mu[j]);
   }
   return !amb2;
 }

@@ -118,7 +118,8 @@ struct cwpir_ctx {
   std::vector<u64> q, p;
   cw::DevTables h;          // host copy (device pointers inside)
   cw::DevTables *d_tab = nullptr;
-  DevBuf twiddles;
+  DevBuf twiddles;    // ciphertext primes: [L][4N] (value, Shoup) pairs
+  DevBuf twiddles32;  // extension primes: [K][4N] 32-bit pairs
   DevBuf rlk, rlk_s;        // [L][2][L][N] NTT form and Shoup companions
   std::map<u32, std::pair<std::shared_ptr<DevBuf>, std::shared_ptr<DevBuf>>> gal;
   std::map<int32_t, std::unique_ptr<Db>> dbs;
@@ -212,13 +213,11 @@ int build_tables(cwpir_ctx *c) {
       h.delta[j] = v ? qj - v : 0;
     }
   }
-  const u32 P = c->L + c->K, N = c->N;
-  std::vector<u64> all(c->q);
-  all.insert(all.end(), c->p.begin(), c->p.end());
-  std::vector<u64> host(4ull * P * N);
-  CUDA_TRY(c, c->twiddles.ensure(4ull * P * N));
-  for (u32 l = 0; l < P; ++l) {
-    u64 q = all[l];
+  const u32 L = c->L, K = c->K, N = c->N;
+  std::vector<u64> host(4ull * L * N);
+  CUDA_TRY(c, c->twiddles.ensure(4ull * L * N));
+  for (u32 l = 0; l < L; ++l) {
+    u64 q = c->q[l];
     u64 *tw = host.data() + 4ull * l * N;
     if (!make_twiddles(q, N, c->logN, tw))
       return fail(c, CWPIR_EINTERNAL, "no 2N-th root of unity mod %llu", (unsigned long long)q);
@@ -233,7 +232,21 @@ int build_tables(cwpir_ctx *c) {
   }
   CUDA_TRY(c, cudaMemcpy(c->twiddles.p, host.data(), host.size() * sizeof(u64),
                          cudaMemcpyHostToDevice));
-  fill_conv(h.q2b, c->q, c->p);
+  std::vector<u32> host32(4ull * K * N);
+  CUDA_TRY(c, c->twiddles32.ensure(2ull * K * N));  // 4KN 32-bit words
+  u32 *d32 = reinterpret_cast<u32 *>(c->twiddles32.p);
+  for (u32 k = 0; k < K; ++k) {
+    const u64 p = c->p[k];
+    if (!cw::host::make_twiddles32(p, N, c->logN, host32.data() + 4ull * k * N))
+      return fail(c, CWPIR_EINTERNAL, "no 2N-th root of unity mod %llu", (unsigned long long)p);
+    cw::ExtNtt &e = h.ext[k];
+    e.e = cw::host::ext_prime(p);
+    e.psi2 = d32 + 4ull * k * N;
+    e.ipsi2 = d32 + 4ull * k * N + 2 * N;
+  }
+  CUDA_TRY(c, cudaMemcpy(d32, host32.data(), host32.size() * sizeof(u32),
+                         cudaMemcpyHostToDevice));
+  fill_lift(h.lift, c->q, c->p);
   fill_scale(h.scale, c->q, c->p, c->t, N);
   CUDA_TRY(c, cudaMalloc(&c->d_tab, sizeof(cw::DevTables)));
   CUDA_TRY(c, cudaMemcpy(c->d_tab, &h, sizeof h, cudaMemcpyHostToDevice));
@@ -845,9 +858,9 @@ int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys, cwpir_ctx **
   c->L = L;
   c->t = params->t;
   c->q = q;
-  // Extension basis P: K = L + 1 primes, P > 2^16 t N Q (checked below).
-  c->K = L + 1;
-  c->p = ntt_primes(N, c->K, q);
+  // Extension basis P: 30-bit primes, P > 2^17 t N Q (checked below).
+  c->K = (u32)cw::ext_count((int)L);
+  c->p = cw::host::ext_primes(N, c->K);
   if (c->p.size() != c->K) return fail(nullptr, CWPIR_EINVAL, "not enough extension primes");
   long double lq = 0, lp = 0;
   for (u64 v : q) lq += log2l((long double)v);
@@ -1519,9 +1532,9 @@ int cwpir_last_stats(const cwpir_ctx *c, cwpir_stats *out) {
 // ---------------------------------------------------------------------
 namespace {
 
-// 2^20 words (8 MiB) of intermediates plus a 64-word header (error flag at
+// 2^21 words (16 MiB) of intermediates plus a 64-word header (error flag at
 // word 0, the job descriptor at words 8..11).
-constexpr size_t kNoAllocWords = size_t(1) << 20;
+constexpr size_t kNoAllocWords = size_t(1) << 21;
 constexpr size_t kNoAllocHeader = 64;
 static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocHeader + kNoAllocWords];
 
@@ -1555,9 +1568,11 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   const u64 need = 2 * qp + 3 * LK * N + 3 * L * N + (L + 2) * L * N + 2 * L * N;
   if (need > kNoAllocWords)
     return fail(c, CWPIR_EINVAL,
-                "N=%u, L=%u needs (L^2+21L+7)N = %llu scratch words; the static array holds "
-                "%llu (N = 8192 allows L <= 4, N = 16384 allows L <= 2)",
-                c->N, c->L, (unsigned long long)need, (unsigned long long)kNoAllocWords);
+                "N=%u, L=%u needs (7(L+K) + L^2 + 7L)N = %llu scratch words (K = %u extension "
+                "primes); the static array holds %llu (N = 8192 allows L <= 7, N = 16384 "
+                "allows L <= 3)",
+                c->N, c->L, (unsigned long long)need, c->K,
+                (unsigned long long)kNoAllocWords);
   cudaSetDevice(c->device);
   u64 *base = nullptr;
   int rc = noalloc_scratch(c, &base);

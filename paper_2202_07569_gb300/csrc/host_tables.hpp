@@ -63,6 +63,15 @@ inline std::vector<u64> ntt_primes(u32 N, u32 count, const std::vector<u64> &avo
   return out;
 }
 
+// extension primes: p = 1 mod 2N with 2^29 < p < 2^30, descending.
+inline std::vector<u64> ext_primes(u32 N, u32 count) {
+  std::vector<u64> out;
+  const u64 step = 2ull * N;
+  for (u64 p = (1ull << 30) - step + 1; out.size() < count && p > (1ull << 29); p -= step)
+    if (miller_rabin(p)) out.push_back(p);
+  return out;
+}
+
 inline u64 primitive_2n_root(u64 p, u32 N) {
   for (u64 g = 2; g < 100000; ++g) {
     u64 r = hpow(g, (p - 1) / (2ull * N), p);
@@ -77,56 +86,77 @@ inline u32 bitrev(u32 x, u32 bits) {
   return r;
 }
 
-// Exact centered base conversion data (see BaseConv in arith.cuh).
-inline void fill_conv(cw::BaseConv &C, const std::vector<u64> &src, const std::vector<u64> &dst) {
+// Centered conversion data of the ciphertext basis (see QConv in arith.cuh).
+inline void fill_qconv(cw::QConv &C, const std::vector<u64> &q) {
   memset(&C, 0, sizeof C);
-  C.ns = (u32)src.size();
-  C.nd = (u32)dst.size();
-  for (u32 j = 0; j < C.ns; ++j) {
-    u64 s = src[j];
-    C.s[j] = s;
+  const u32 L = (u32)q.size();
+  for (u32 j = 0; j < L; ++j) {
+    const u64 qj = q[j];
+    C.q[j] = qj;
+    C.mu[j] = (u64)(((u128)1 << 116) / qj);
     u64 hat = 1;
-    for (u32 l = 0; l < C.ns; ++l)
-      if (l != j) hat = hmul(hat, src[l] % s, s);
-    C.theta[j] = hinv(hat, s);
-    C.theta_s[j] = shoup_of(C.theta[j], s);
-    u128 W = (~(u128)0) / s;  // floor((2^128 - 1)/s) = floor(2^128/s): s is not a power of 2
+    for (u32 l = 0; l < L; ++l)
+      if (l != j) hat = hmul(hat, q[l] % qj, qj);
+    C.theta[j] = hinv(hat, qj);
+    C.theta_s[j] = shoup_of(C.theta[j], qj);
+    const u128 W = (~(u128)0) / qj;  // floor(2^128 / q_j): q_j is not a power of 2
     C.w_hi[j] = (u64)(W >> 64);
     C.w_lo[j] = (u64)W;
   }
-  for (u32 k = 0; k < C.nd; ++k) {
-    u64 d = dst[k];
-    C.d[k] = d;
-    u64 smod = 1;
-    for (u32 j = 0; j < C.ns; ++j) smod = hmul(smod, src[j] % d, d);
-    C.smod[k] = smod;
-    C.smod_s[k] = shoup_of(smod, d);
-    C.negsmod[k] = smod ? d - smod : 0;
-    C.d_mu[k] = (u64)(((u128)1 << 116) / d);
-    for (u32 j = 0; j < C.ns; ++j) {
-      u64 hat = 1;
-      for (u32 l = 0; l < C.ns; ++l)
-        if (l != j) hat = hmul(hat, src[l] % d, d);
-      C.hat[j][k] = hat;
-      C.hat_s[j][k] = shoup_of(hat, d);
-    }
-  }
-  // Garner data: s_i^-1 mod s_j (i < j) and the mixed-radix digits of
-  // (S-1)/2, whose residue mod s_j is (s_j - 1)/2.
-  for (u32 j = 0; j < C.ns; ++j)
+  // Garner data: q_i^-1 mod q_j (i < j) and the mixed-radix digits of
+  // (Q-1)/2, whose residue mod q_j is (q_j - 1)/2.
+  for (u32 j = 0; j < L; ++j)
     for (u32 i = 0; i < j; ++i) {
-      C.mrinv[i][j] = hinv(src[i] % src[j], src[j]);
-      C.mrinv_s[i][j] = shoup_of(C.mrinv[i][j], src[j]);
+      C.mrinv[i][j] = hinv(q[i] % q[j], q[j]);
+      C.mrinv_s[i][j] = shoup_of(C.mrinv[i][j], q[j]);
     }
-  u64 a[cw::kMaxK];
-  for (u32 j = 0; j < C.ns; ++j) {
-    u64 sj = src[j], v = (sj - 1) / 2;
-    for (u32 i = 0; i < j; ++i) v = hmul((v + sj - a[i] % sj) % sj, C.mrinv[i][j], sj);
+  u64 a[cw::kMaxL];
+  for (u32 j = 0; j < L; ++j) {
+    const u64 qj = q[j];
+    u64 v = (qj - 1) / 2;
+    for (u32 i = 0; i < j; ++i) v = hmul((v + qj - a[i] % qj) % qj, C.mrinv[i][j], qj);
     a[j] = v;
     C.half_mr[j] = v;
   }
 }
 
+inline cw::ExtPrime ext_prime(u64 p) {
+  cw::ExtPrime E;
+  E.p = (u32)p;
+  E.mu60 = (u32)((1ull << 60) / p);
+  E.mu64 = (u64)(((u128)1 << 64) / p);
+  return E;
+}
+
+// (product of src) / src[j] mod m
+inline u64 hat_mod(const std::vector<u64> &src, u32 j, u64 m) {
+  u64 h = 1;
+  for (u32 l = 0; l < src.size(); ++l)
+    if (l != j) h = hmul(h, src[l] % m, m);
+  return h;
+}
+inline u64 prod_mod(const std::vector<u64> &src, u64 m) {
+  u64 h = 1;
+  for (u64 v : src) h = hmul(h, v % m, m);
+  return h;
+}
+
+// Centered Q -> P conversion constants (see LiftTab in arith.cuh).
+inline void fill_lift(cw::LiftTab &T, const std::vector<u64> &q, const std::vector<u64> &p) {
+  memset(&T, 0, sizeof T);
+  fill_qconv(T.Q, q);
+  for (u32 k = 0; k < p.size(); ++k) {
+    const u64 pk = p[k];
+    T.ext[k] = ext_prime(pk);
+    for (u32 j = 0; j < q.size(); ++j) {
+      const u64 h = hat_mod(q, j, pk);
+      T.h[j][k] = (u32)h;
+      T.h27[j][k] = (u32)hmul(h, 1ull << 27, pk);
+    }
+    const u64 Qm = prod_mod(q, pk);
+    T.negq[k] = (u32)(Qm ? pk - Qm : 0);
+  }
+}
 
 // Forward pairs (psi^bitrev(i), Shoup) at tw[0..2N), inverse pairs
 // (psi^-bitrev(i), Shoup) at tw[2N..4N).  Returns false if q has no
@@ -146,42 +176,61 @@ inline bool make_twiddles(u64 q, u32 N, u32 logN, u64 *tw) {
   return true;
 }
 
+// 32-bit twiddles of an extension prime: forward pairs (psi^bitrev(i),
+// floor(psi^bitrev(i) 2^32 / p)) at tw[0..2N), inverse pairs at tw[2N..4N).
+inline bool make_twiddles32(u64 p, u32 N, u32 logN, u32 *tw) {
+  const u64 psi = primitive_2n_root(p, N);
+  if (!psi) return false;
+  const u64 ipsi = hinv(psi, p);
+  for (u32 i = 0; i < N; ++i) {
+    const u32 e = bitrev(i, logN);
+    const u64 f = hpow(psi, e, p), b = hpow(ipsi, e, p);
+    tw[2 * i] = (u32)f;
+    tw[2 * i + 1] = (u32)((f << 32) / p);
+    tw[2 * N + 2 * i] = (u32)b;
+    tw[2 * N + 2 * i + 1] = (u32)((b << 32) / p);
+  }
+  return true;
+}
+
 // Scale-down constants for round(t d / Q) (see ScaleTab in arith.cuh),
 // for residues given as f*d: the constants that multiply d carry f^-1 (the
 // tensor kernel leaves the factor N of its inverse transforms in place).
 inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::vector<u64> &p,
                        u64 t, u64 f) {
+  memset(&S, 0, sizeof S);
   const u32 L = (u32)q.size(), K = (u32)p.size();
-  fill_conv(S.q2b, q, p);
-  fill_conv(S.b2q, p, q);
+  fill_qconv(S.Q, q);
   for (u32 j = 0; j < L; ++j) {
-    u64 qj = q[j];
+    const u64 qj = q[j];
     S.t_mod[j] = hmul(t % qj, hinv(f % qj, qj), qj);
     S.t_mod_s[j] = shoup_of(S.t_mod[j], qj);
-    S.t_theta[j] = hmul(S.t_mod[j], S.q2b.theta[j], qj);
+    S.t_theta[j] = hmul(S.t_mod[j], S.Q.theta[j], qj);
     S.t_theta_s[j] = shoup_of(S.t_theta[j], qj);
   }
   for (u32 k = 0; k < K; ++k) {
-    u64 pk = p[k];
-    u64 Qm = 1;
-    for (u32 j = 0; j < L; ++j) Qm = hmul(Qm, q[j] % pk, pk);
-    const u64 th = S.b2q.theta[k];  // (P/p_k)^-1 mod p_k
-    S.A[k] = hmul(hmul(hmul(t % pk, hinv(Qm, pk), pk), th, pk), hinv(f % pk, pk), pk);
-    S.Cr[k] = th;
+    const u64 pk = p[k];
+    S.ext[k] = ext_prime(pk);
+    const u64 th = hinv(hat_mod(p, k, pk), pk);  // (P/p_k)^-1 mod p_k
+    const u64 Qm = prod_mod(q, pk);
+    S.A[k] = (u32)hmul(hmul(hmul(t % pk, hinv(Qm, pk), pk), th, pk), hinv(f % pk, pk), pk);
+    S.Cr[k] = (u32)th;
     for (u32 j = 0; j < L; ++j) {
-      u64 v = hmul(hinv(q[j] % pk, pk), th, pk);
-      S.B[j][k] = v ? pk - v : 0;
+      const u64 v = hmul(hinv(q[j] % pk, pk), th, pk);
+      const u64 b = v ? pk - v : 0;
+      S.B[j][k] = (u32)b;
+      S.B27[j][k] = (u32)hmul(b, 1ull << 27, pk);
     }
+    const u128 W = (~(u128)0) / pk;  // floor(2^128 / p_k)
+    S.pw_hi[k] = (u64)(W >> 64);
+    S.pw_lo[k] = (u64)W;
   }
-  for (u32 k = 0; k < K; ++k) {
-    split27(S.A[k], S.A2[k]);
-    split27(S.Cr[k], S.Cr2[k]);
-    for (u32 j = 0; j < L; ++j) {
-      split27(S.B[j][k], S.B2[j][k]);
-      split27(S.b2q.hat[k][j], S.hat2[k][j]);
-    }
+  for (u32 j = 0; j < L; ++j) {
+    const u64 qj = q[j];
+    for (u32 k = 0; k < K; ++k) split27(hat_mod(p, k, qj), S.hat2[k][j]);
+    const u64 Pm = prod_mod(p, qj);
+    split27(Pm ? qj - Pm : 0, S.negp2[j]);
   }
-  for (u32 j = 0; j < L; ++j) split27(S.b2q.negsmod[j], S.negs2[j]);
 }
 
 }  // namespace host

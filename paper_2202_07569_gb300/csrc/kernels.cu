@@ -3,6 +3,8 @@
 // Layout conventions (u64 residues, limb-major):
 //   coefficient ciphertext   [2][L][N]
 //   QP-NTT ciphertext        [2][L+K][N]  NTT form over q_0..q_{L-1}, p_0..p_{K-1}
+//                                         (30-bit p_k: 32-bit arithmetic, values
+//                                         in the low half of the word)
 //   database                 [rows][L][N] NTT form (centered plaintext lift)
 //   tensor buffer  Tbuf      [jobs][3][L+K][N] N d0, N d1, N d2 (lazy residues)
 //   scaled buffer  E         [jobs][3][L][N]   round(t d / Q) mod q_j
@@ -98,6 +100,61 @@ __device__ __forceinline__ void ntt_inv(NttRegs<LOGN> &x, u64 *s, const NttPrime
   }
 }
 
+// The same transforms on 32-bit words for a 30-bit extension prime: the
+// forward one from [0, 4p) to canonical values, the inverse one from
+// [0, 2p) to N times the coefficient in [0, 2p) (no N^-1: the scale-down
+// absorbs it).
+template <int LOGN>
+using NttRegs32 = u32[NttShape<LOGN>::R];
+
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd32(NttRegs32<LOGN> &x, u32 *s, const ExtNtt &P) {
+  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int NP = Passes<LOGN, RB>::count;
+  const u32 t = threadIdx.x;
+  u32 wprev = 0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    u32 lo, c, w;
+    Passes<LOGN, RB>::fwd(p, lo, c, w);
+    if (p > 0) {
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[r];
+      __syncthreads();
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
+      __syncthreads();
+    }
+    fwd_pass32<LOGN, RB>(x, t, lo, c, w, P.psi2, P.e.p);
+    wprev = w;
+  }
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) x[r] = reduce4_32(x[r], P.e.p);
+}
+
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv32(NttRegs32<LOGN> &x, u32 *s, const ExtNtt &P) {
+  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int NP = Passes<LOGN, RB>::count;
+  const u32 t = threadIdx.x;
+  u32 wprev = 0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    u32 lo, c, w;
+    Passes<LOGN, RB>::inv(p, lo, c, w);
+    if (p > 0) {
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[r];
+      __syncthreads();
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
+      __syncthreads();
+    }
+    inv_pass32<LOGN, RB>(x, t, lo, c, w, P.ipsi2, P.e.p);
+    wprev = w;
+  }
+}
+
 template <int LOGN>
 constexpr size_t ntt_smem_bytes() {
   return (size_t)((1u << LOGN) + ((1u << LOGN) >> NttShape<LOGN>::RB)) * sizeof(u64);
@@ -150,11 +207,21 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
   constexpr u32 N = 1u << LOGN;
   const u32 l = limb_begin + blockIdx.x, t = threadIdx.x;
   const u64 u = blockIdx.y;
-  const NttPrime P = T->prime[l];
+  const NttPrime P = T->prime[l < T->L ? l : 0];
   const u64 *in = src ? src + u * src_unit_stride + (u64)l * N : base + u * unit_stride + (u64)l * N;
   u64 *out = base + u * unit_stride + (u64)l * N;
-  NttRegs<LOGN> x;
   constexpr u32 R = NttShape<LOGN>::R;
+  if (l >= T->L) {  // extension limb, forward only (launch_ntt checks)
+    const ExtNtt E = T->ext[l - T->L];
+    NttRegs32<LOGN> y;
+#pragma unroll
+    for (u32 r = 0; r < R; ++r) y[r] = (u32)in[strided_idx<LOGN>(t, r)];
+    ntt_fwd32<LOGN>(y, reinterpret_cast<u32 *>(s), E);
+#pragma unroll
+    for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = y[r];
+    return;
+  }
+  NttRegs<LOGN> x;
   if (inverse) {
 #pragma unroll
     for (u32 r = 0; r < R; ++r) x[r] = in[ntt_pos<LOGN>(t, r)];
@@ -179,13 +246,14 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
   constexpr u32 N = 1u << LOGN;
   const u32 L = T->L, K = T->K, l = L + blockIdx.x, t = threadIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
-  const NttPrime P = T->prime[l];
+  const ExtNtt E = T->ext[blockIdx.x];
   u64 *p = jobs[job].dst + ((u64)poly * (L + K) + l) * N;
-  NttRegs<LOGN> x;
+  NttRegs32<LOGN> x;
   constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
-  ntt_fwd<LOGN>(x, s, P);  // contains barriers: all loads precede all stores
+  for (u32 r = 0; r < R; ++r) x[r] = (u32)p[strided_idx<LOGN>(t, r)];
+  // contains barriers: all loads precede all stores
+  ntt_fwd32<LOGN>(x, reinterpret_cast<u32 *>(s), E);
 #pragma unroll
   for (u32 r = 0; r < R; ++r) p[ntt_pos<LOGN>(t, r)] = x[r];
 }
@@ -199,17 +267,18 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 // in the constant bank and the integer multiplies read them as operands.
 template <int L>
 __global__ void k_lift(const DevTables *T, const u64 *src, u64 src_stride, u64 *dst,
-                       u64 dst_stride, int copy_q, const __grid_constant__ BaseConv C) {
-  constexpr int K = L + 1;
+                       u64 dst_stride, int copy_q, const __grid_constant__ LiftTab C) {
+  constexpr int K = ext_count(L);
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 u = blockIdx.y;
   const u64 *in = src + u * src_stride;
   u64 *out = dst + u * dst_stride;
-  u64 x[L], y[K];
+  u64 x[L];
+  u32 y[K];
 #pragma unroll
   for (int j = 0; j < L; ++j) x[j] = in[(u64)j * N + c];
-  lift_centered<L, K>(x, y, C);
+  lift_ext<L, K>(x, y, C);
   if (copy_q) {
 #pragma unroll
     for (int j = 0; j < L; ++j) out[(u64)j * N + c] = x[j];
@@ -222,17 +291,18 @@ __global__ void k_lift(const DevTables *T, const u64 *src, u64 src_stride, u64 *
 // of jobs[j].dst.  grid (N/256, 2 * njobs).
 template <int L>
 __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs,
-                            const __grid_constant__ BaseConv Cv) {
-  constexpr int K = L + 1;
+                            const __grid_constant__ LiftTab Cv) {
+  constexpr int K = ext_count(L);
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const u64 *in = C + ((u64)job * 2 + poly) * L * N;
   u64 *out = jobs[job].dst + (u64)poly * (L + K) * N;
-  u64 x[L], y[K];
+  u64 x[L];
+  u32 y[K];
 #pragma unroll
   for (int j = 0; j < L; ++j) x[j] = in[(u64)j * N + c];
-  lift_centered<L, K>(x, y, Cv);
+  lift_ext<L, K>(x, y, Cv);
 #pragma unroll
   for (int k = 0; k < K; ++k) out[(u64)(L + k) * N + c] = y[k];
 }
@@ -241,7 +311,8 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // Tensor of two QP-NTT ciphertexts, one output polynomial and limb per
 // CTA, followed by the inverse NTT: d0 = a0 b0, d1 = a0 b1 + a1 b0,
 // d2 = a1 b1.  grid (njobs, 3, L+K): the limb varies slowest so that the
-// blocks resident on one SM share one prime's twiddles in L1.
+// blocks resident on one SM share one prime's twiddles in L1.  Extension
+// limbs run on 32-bit words.
 // ---------------------------------------------------------------------
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
@@ -250,13 +321,36 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
   constexpr u32 N = 1u << LOGN;
   const u32 LK = T->L + T->K, l = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
   const u64 job = blockIdx.x;
-  const NttPrime P = T->prime[l];
   const MulJob J = jobs[job];
   const u64 ps = (u64)LK * N;
   const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
   const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
-  NttRegs<LOGN> x;
+  u64 *out = Tbuf + ((job * 3 + which) * LK + l) * N;
   constexpr u32 R = NttShape<LOGN>::R;
+  if (l >= T->L) {  // extension limb: products in [0, 2p), 32-bit transform
+    const ExtNtt E = T->ext[l - T->L];
+    const u32 p2 = 2 * E.e.p;
+    NttRegs32<LOGN> y;
+#pragma unroll
+    for (u32 r = 0; r < R; ++r) {
+      const u32 c = ntt_pos<LOGN>(t, r);
+      u32 v;
+      if (which == 0) v = mulmod_ext_lazy((u32)a0[c], (u32)b0[c], E.e);
+      else if (which == 2) v = mulmod_ext_lazy((u32)a1[c], (u32)b1[c], E.e);
+      else {
+        v = mulmod_ext_lazy((u32)a0[c], (u32)b1[c], E.e) +
+            mulmod_ext_lazy((u32)a1[c], (u32)b0[c], E.e);
+        v = v >= p2 ? v - p2 : v;
+      }
+      y[r] = v;
+    }
+    ntt_inv32<LOGN>(y, reinterpret_cast<u32 *>(s), E);  // N d in [0, 2p)
+#pragma unroll
+    for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = y[r];
+    return;
+  }
+  const NttPrime P = T->prime[l];
+  NttRegs<LOGN> x;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) {
     const u32 c = ntt_pos<LOGN>(t, r);
@@ -267,7 +361,6 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
     x[r] = v;
   }
   ntt_inv<LOGN, false>(x, s, P);  // N d in [0, 2q): the scale-down absorbs N^-1
-  u64 *out = Tbuf + ((job * 3 + which) * LK + l) * N;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
@@ -278,7 +371,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 template <int L>
 __global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err,
                         const __grid_constant__ ScaleTab S) {
-  constexpr int K = L + 1;
+  constexpr int K = ext_count(L);
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 jw = blockIdx.y;
@@ -756,6 +849,7 @@ cudaError_t launch_ntt(const DevTables *T, const DevTables &h, u64 *base, u32 un
                        u64 unit_stride, u32 limb_begin, u32 limb_end, bool inverse,
                        const u64 *src, u64 src_unit_stride, cudaStream_t st) {
   if (!units || limb_end <= limb_begin) return cudaSuccess;
+  if (inverse && limb_end > h.L) return cudaErrorInvalidValue;  // extension limbs: forward only
   const u32 chunk = 32768;
   for (u32 u0 = 0; u0 < units; u0 += chunk) {
     u32 nu = units - u0 < chunk ? units - u0 : chunk;
@@ -778,7 +872,7 @@ cudaError_t launch_lift(const DevTables *T, const DevTables &h, const u64 *src,
     u32 nu = units - u0 < chunk ? units - u0 : chunk;
     dim3 grid(h.N / 256, nu);
     CW_DISPATCH_L(h.L, k_lift, grid, 256, 0, st, T, src + (u64)u0 * src_stride, src_stride,
-                  dst + (u64)u0 * dst_stride, dst_stride, copy_q ? 1 : 0, h.q2b);
+                  dst + (u64)u0 * dst_stride, dst_stride, copy_q ? 1 : 0, h.lift);
   }
   return cudaGetLastError();
 }
@@ -787,7 +881,7 @@ cudaError_t launch_lift_jobs(const DevTables *T, const DevTables &h, const u64 *
                              const MulJob *jobs, u32 njobs, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   dim3 grid(h.N / 256, 2 * njobs);
-  CW_DISPATCH_L(h.L, k_lift_jobs, grid, 256, 0, st, T, C, jobs, h.q2b);
+  CW_DISPATCH_L(h.L, k_lift_jobs, grid, 256, 0, st, T, C, jobs, h.lift);
   return cudaGetLastError();
 }
 

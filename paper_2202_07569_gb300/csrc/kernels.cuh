@@ -7,18 +7,27 @@
 
 namespace cw {
 
+// 32-bit NTT data of a 30-bit extension prime, in device memory.
+struct ExtNtt {
+  ExtPrime e;
+  const u32 *psi2;   // [N][2]: psi^bitrev(i) and floor(psi^bitrev(i) 2^32 / p)
+  const u32 *ipsi2;  // [N][2]: the same for psi^-1
+};
+
 // All per-context constants the kernels read, in device memory.
 struct DevTables {
   u32 N, logN, L, K;
   u64 t;
   u64 delta[kMaxL];       // Delta = floor(Q / t) mod q_j
-  NttPrime prime[kMaxP];  // q_0..q_{L-1}, then p_0..p_{K-1}
-  BaseConv q2b;           // centered Q -> P conversion (leaves, nodes)
+  NttPrime prime[kMaxL];  // ciphertext primes q_0..q_{L-1}
+  ExtNtt ext[kMaxK];      // extension primes p_0..p_{K-1} (30-bit)
+  LiftTab lift;           // centered Q -> P conversion (leaves, nodes)
   ScaleTab scale;         // exact round(t d / Q)
 };
 
 // One homomorphic multiplication of two ciphertexts held in "QP-NTT" form:
-// [2][L+K][N] residues, NTT domain, Q limbs then P limbs.
+// [2][L+K][N] residues, NTT domain, Q limbs then P limbs (the P residues,
+// below 2^30, in the low half of their 64-bit words).
 struct MulJob {
   const u64 *a;
   const u64 *b;

@@ -116,6 +116,81 @@ CW_HD u64 reduce4(u64 v, u64 q) {
   return v >= q ? v - q : v;
 }
 
+// ---- the same passes on 32-bit words, for the 30-bit extension primes
+// (p < 2^30 keeps 4p below 2^32); twiddles are (w, floor(w 2^32 / p)) pairs.
+CW_HD void ld_pair32(const u32 *p, u32 &a, u32 &b) {
+#if defined(__CUDA_ARCH__)
+  const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+  a = v.x;
+  b = v.y;
+#else
+  a = p[0];
+  b = p[1];
+#endif
+}
+
+// a*w mod p in [0, 2p) for any a < 2^32
+CW_HD u32 shoup32_lazy(u32 a, u32 w, u32 ws, u32 p) { return a * w - mulhi32(a, ws) * p; }
+
+template <int LOGN, int RB>
+CW_HD void fwd_pass32(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *psi2, u32 p) {
+  const u32 p2 = 2 * p;
+  constexpr u32 R = 1u << RB;
+#pragma unroll
+  for (int bi = RB - 1; bi >= 0; --bi) {
+    if ((u32)bi >= c) continue;
+    const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
+#pragma unroll
+    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
+      const u32 r0 = hv << (rb + 1);
+      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
+      u32 W, Ws;
+      ld_pair32(psi2 + 2 * (m + g), W, Ws);
+#pragma unroll
+      for (u32 lv = 0; lv < (1u << rb); ++lv) {
+        const u32 r = r0 | lv;
+        u32 U = x[r];
+        U = U >= p2 ? U - p2 : U;
+        const u32 V = shoup32_lazy(x[r | (1u << rb)], W, Ws, p);
+        x[r] = U + V;
+        x[r | (1u << rb)] = U - V + p2;
+      }
+    }
+  }
+}
+
+template <int LOGN, int RB>
+CW_HD void inv_pass32(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *ipsi2, u32 p) {
+  const u32 p2 = 2 * p;
+  constexpr u32 R = 1u << RB;
+#pragma unroll
+  for (int bi = 0; bi < RB; ++bi) {
+    if ((u32)bi >= c) continue;
+    const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
+#pragma unroll
+    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
+      const u32 r0 = hv << (rb + 1);
+      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
+      u32 W, Ws;
+      ld_pair32(ipsi2 + 2 * (m + g), W, Ws);
+#pragma unroll
+      for (u32 lv = 0; lv < (1u << rb); ++lv) {
+        const u32 r = r0 | lv;
+        const u32 U = x[r], V = x[r | (1u << rb)];
+        const u32 S = U + V;
+        x[r] = S >= p2 ? S - p2 : S;
+        x[r | (1u << rb)] = shoup32_lazy(U - V + p2, W, Ws, p);
+      }
+    }
+  }
+}
+
+CW_HD u32 reduce4_32(u32 v, u32 p) {
+  const u32 p2 = 2 * p;
+  v = v >= p2 ? v - p2 : v;
+  return v >= p ? v - p : v;
+}
+
 // Pass schedule: forward passes take bits from the top in chunks of RB,
 // inverse passes from the bottom; a pass of c < RB bits uses the window
 // clamped into [0, n).

@@ -32,6 +32,8 @@ def lib():
     l.emu_lift.restype = None
     l.emu_ext_primes.argtypes = [U32, U32, u64p, u64p]
     l.emu_ext_primes.restype = None
+    l.emu_ext_count.argtypes = [U32]
+    l.emu_ext_count.restype = U32
     l.emu_substitute.argtypes = [U32, U32, u64p, U64, U32, u64p, u64p, u64p]
     l.emu_substitute.restype = None
     l.emu_scale.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p]

@@ -21,17 +21,19 @@ struct Emu {
   u32 N, logN, L, K;
   u64 t;
   std::vector<u64> q, p, all;
-  std::vector<std::vector<u64>> tw;  // per prime: 4N
+  std::vector<std::vector<u64>> tw;   // per prime: 4N (value, 64-bit Shoup) pairs
+  std::vector<std::vector<u32>> tw32;  // per extension prime: 4N (value, 32-bit Shoup)
   std::vector<u64> ninv, ninv_s, mu;
-  BaseConv q2b;
+  std::vector<ExtPrime> ext;
+  LiftTab LT;
   ScaleTab S;
 
   Emu(u32 N_, u32 L_, const u64 *q_, u64 t_) : N(N_), L(L_), t(t_) {
     logN = 0;
     while ((1u << logN) < N) ++logN;
     q.assign(q_, q_ + L);
-    K = L + 1;
-    p = ntt_primes(N, K, q);
+    K = (u32)ext_count((int)L);
+    p = ext_primes(N, K);
     all = q;
     all.insert(all.end(), p.begin(), p.end());
     for (u64 pr : all) {
@@ -42,7 +44,13 @@ struct Emu {
       ninv_s.push_back(shoup_of(ninv.back(), pr));
       mu.push_back((u64)(((u128)1 << 116) / pr));
     }
-    fill_conv(q2b, q, p);
+    for (u64 pr : p) {
+      std::vector<u32> w(4 * N);
+      make_twiddles32(pr, N, logN, w.data());
+      tw32.push_back(w);
+      ext.push_back(ext_prime(pr));
+    }
+    fill_lift(LT, q, p);
     fill_scale(S, q, p, t, N);
   }
   void fwd(u64 *a, u32 l) {
@@ -71,16 +79,18 @@ struct Emu {
     }
   }
   void lift(const u64 *x, u64 *y) {
+    u32 y32[kMaxK];
     switch (L) {
-      case 1: lift_centered<1, 2>(x, y, q2b); break;
-      case 2: lift_centered<2, 3>(x, y, q2b); break;
-      case 3: lift_centered<3, 4>(x, y, q2b); break;
-      case 4: lift_centered<4, 5>(x, y, q2b); break;
-      case 5: lift_centered<5, 6>(x, y, q2b); break;
-      case 6: lift_centered<6, 7>(x, y, q2b); break;
-      case 7: lift_centered<7, 8>(x, y, q2b); break;
-      default: lift_centered<8, 9>(x, y, q2b); break;
+      case 1: lift_ext<1, ext_count(1)>(x, y32, LT); break;
+      case 2: lift_ext<2, ext_count(2)>(x, y32, LT); break;
+      case 3: lift_ext<3, ext_count(3)>(x, y32, LT); break;
+      case 4: lift_ext<4, ext_count(4)>(x, y32, LT); break;
+      case 5: lift_ext<5, ext_count(5)>(x, y32, LT); break;
+      case 6: lift_ext<6, ext_count(6)>(x, y32, LT); break;
+      case 7: lift_ext<7, ext_count(7)>(x, y32, LT); break;
+      default: lift_ext<8, ext_count(8)>(x, y32, LT); break;
     }
+    for (u32 k = 0; k < K; ++k) y[k] = y32[k];
   }
   bool scale(const u64 *dq, const u64 *dp, u64 *e) {
     switch (L) {
@@ -163,10 +173,25 @@ int emu_bfv_mul(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uin
       const u64 *a0 = A.data() + (u64)l * N, *a1 = a0 + (u64)LK * N;
       const u64 *b0 = B.data() + (u64)l * N, *b1 = b0 + (u64)LK * N;
       u64 *o = Tb.data() + ((u64)which * LK + l) * N;
-      for (u32 c = 0; c < N; ++c) {
-        if (which == 0) o[c] = barrett(a0[c], b0[c], pr, m);
-        else if (which == 2) o[c] = barrett(a1[c], b1[c], pr, m);
-        else o[c] = addq(barrett(a0[c], b1[c], pr, m), barrett(a1[c], b0[c], pr, m), pr);
+      if (l < L) {
+        for (u32 c = 0; c < N; ++c) {
+          if (which == 0) o[c] = barrett(a0[c], b0[c], pr, m);
+          else if (which == 2) o[c] = barrett(a1[c], b1[c], pr, m);
+          else o[c] = addq(barrett(a0[c], b1[c], pr, m), barrett(a1[c], b0[c], pr, m), pr);
+        }
+      } else {  // extension limb: the kernels' 32-bit products, lazy [0, 2p)
+        const ExtPrime &X = E.ext[l - L];
+        const u32 p2 = 2 * X.p;
+        for (u32 c = 0; c < N; ++c) {
+          u32 v;
+          if (which == 0) v = mulmod_ext_lazy((u32)a0[c], (u32)b0[c], X);
+          else if (which == 2) v = mulmod_ext_lazy((u32)a1[c], (u32)b1[c], X);
+          else {
+            v = mulmod_ext_lazy((u32)a0[c], (u32)b1[c], X) + mulmod_ext_lazy((u32)a1[c], (u32)b0[c], X);
+            v = v >= p2 ? v - p2 : v;
+          }
+          o[c] = v >= X.p ? v - X.p : v;
+        }
       }
       E.inv(o, l);  // canonical d; the scale-down takes N d as the kernels hand it over
       for (u32 c = 0; c < N; ++c) o[c] = hmul(o[c], N % pr, pr) + ((c & 1) ? pr : 0);
@@ -194,10 +219,13 @@ void emu_lift(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint6
   E.lift(x, y);
 }
 
-// The extension primes the library chooses for these parameters.
+// The number of extension primes and the primes the library chooses for
+// these parameters (p holds ext_count(L) entries).
+uint32_t emu_ext_count(uint32_t L) { return (uint32_t)ext_count((int)L); }
 void emu_ext_primes(uint32_t N, uint32_t L, const uint64_t *q, uint64_t *p) {
-  std::vector<u64> v = ntt_primes(N, L + 1, std::vector<u64>(q, q + L));
-  for (u32 i = 0; i < L + 1; ++i) p[i] = v[i];
+  (void)q;
+  std::vector<u64> v = ext_primes(N, (u32)ext_count((int)L));
+  for (u32 i = 0; i < v.size(); ++i) p[i] = v[i];
 }
 
 // Sub_g: automorphism then key switch with the Galois key (coefficient form).
@@ -261,6 +289,42 @@ void pass_ntt(u64 *a, const u64 *tw, u64 q, bool inverse, u64 ninv, u64 ninv_s) 
   for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
 }
 
+// The 32-bit schedule of the extension primes (forward from [0, 4p) to
+// canonical; inverse from [0, 2p) to N times the coefficient in [0, 2p)).
+template <int LOGN, int RB>
+void pass_ntt32(u32 *a, const u32 *tw, u32 p, bool inverse) {
+  constexpr u32 R = 1u << RB;
+  const u32 N = 1u << LOGN, T = N / R;
+  std::vector<u32> s(smem_words<RB>(N));
+  for (u32 i = 0; i < N; ++i) s[sidx<RB>(i)] = a[i];
+  for (int pp = 0; pp < Passes<LOGN, RB>::count; ++pp) {
+    u32 lo, c, w;
+    if (inverse) Passes<LOGN, RB>::inv(pp, lo, c, w);
+    else Passes<LOGN, RB>::fwd(pp, lo, c, w);
+    for (u32 t = 0; t < T; ++t) {
+      u32 x[R];
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
+      if (inverse) inv_pass32<LOGN, RB>(x, t, lo, c, w, tw + 2 * N, p);
+      else fwd_pass32<LOGN, RB>(x, t, lo, c, w, tw, p);
+      if (pp == Passes<LOGN, RB>::count - 1 && !inverse)
+        for (u32 r = 0; r < R; ++r) x[r] = reduce4_32(x[r], p);
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, w))] = x[r];
+    }
+  }
+  for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
+}
+
+template <int RB>
+void pass_ntt32_n(u32 logN, u32 *a, const u32 *tw, u32 p, bool inverse) {
+  switch (logN) {
+    case 10: pass_ntt32<10, RB>(a, tw, p, inverse); break;
+    case 11: pass_ntt32<11, RB>(a, tw, p, inverse); break;
+    case 12: pass_ntt32<12, RB>(a, tw, p, inverse); break;
+    case 13: pass_ntt32<13, RB>(a, tw, p, inverse); break;
+    default: pass_ntt32<14, RB>(a, tw, p, inverse); break;
+  }
+}
+
 template <int RB>
 void pass_ntt_n(u32 logN, u64 *a, const u64 *tw, u64 q, bool inverse, u64 ninv, u64 ninv_s) {
   switch (logN) {
@@ -282,8 +346,28 @@ uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
   Emu E(N, L, q, t);
   uint64_t bad = 0;
   auto run = rb == 4 ? pass_ntt_n<4> : pass_ntt_n<5>;
+  auto run32 = rb == 4 ? pass_ntt32_n<4> : pass_ntt32_n<5>;
   for (u32 l = 0; l < E.all.size(); ++l) {
     u64 pr = E.all[l];
+    if (l >= L) {  // extension prime: the 32-bit schedule
+      std::vector<u64> a(N);
+      std::vector<u32> b(N);
+      for (u32 i = 0; i < N; ++i) {
+        a[i] = data[i] % pr;
+        b[i] = (u32)(a[i] + (data[i] >> 62) * pr);  // lazy input below 4p
+      }
+      E.fwd(a.data(), l);
+      run32(E.logN, b.data(), E.tw32[l - L].data(), (u32)pr, false);
+      for (u32 i = 0; i < N; ++i) bad += a[i] != b[i];
+      for (u32 i = 0; i < N; ++i) b[i] += (u32)(((data[i] >> 59) & 1) * pr);  // below 2p
+      E.inv(a.data(), l);
+      run32(E.logN, b.data(), E.tw32[l - L].data(), (u32)pr, true);
+      // the 32-bit inverse leaves N times the coefficient in [0, 2p)
+      for (u32 i = 0; i < N; ++i)
+        bad += b[i] >= 2 * pr || b[i] % pr != hmul(a[i], N % pr, pr) ||
+               a[i] != data[i] % pr;
+      continue;
+    }
     std::vector<u64> a(N), b(N);
     // the schedule accepts lazy inputs: below 4q forward, below 2q inverse
     for (u32 i = 0; i < N; ++i) {

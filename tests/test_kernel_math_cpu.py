@@ -20,6 +20,18 @@ def centered(x, M):
     return x - M if x > M // 2 else x
 
 
+def _ext_primes(N, L, q):
+    """The library's extension primes: 30-bit, = 1 mod 2N, with product
+    above 2^17 t N Q (the scale-down's bound)."""
+    k = emu.lib().emu_ext_count(L)
+    p = np.zeros(k, np.uint64)
+    emu.lib().emu_ext_primes(N, L, np.array(q, np.uint64), p)
+    p = [int(v) for v in p]
+    assert all((1 << 29) < v < (1 << 30) and v % (2 * N) == 1 for v in p)
+    assert math.prod(p) > (1 << 17) * T * N * math.prod(q)
+    return p
+
+
 def _setup(orc, N, L, seed=3):
     q = orc.primes(N, L)
     O = orc.Oracle(N, q)
@@ -51,35 +63,31 @@ def test_emulated_multiplication_matches_oracle_n16384(orc):
     assert np.array_equal(out, O.bfv_mul(a, b, rlk))
 
 
-@pytest.mark.parametrize("N,L", [(1024, 2), (8192, 4), (16384, 7)])
+@pytest.mark.parametrize("N,L", [(1024, 2), (2048, 3), (8192, 4), (16384, 7), (16384, 8)])
 def test_centered_lift_near_half(orc, N, L):
     """Values next to Q/2 and 0 take the exact mixed-radix branch."""
     q = [int(v) for v in orc.primes(N, L)]
     Q = math.prod(q)
-    p = np.zeros(L + 1, np.uint64)
-    emu.lib().emu_ext_primes(N, L, np.array(q, np.uint64), p)
-    p = [int(v) for v in p]
+    p = _ext_primes(N, L, q)
     vals = [0, 1, Q - 1, (Q - 1) // 2, (Q + 1) // 2, (Q - 3) // 2, (Q + 3) // 2]
     vals += [(Q >> 1) + d for d in (-(1 << 12), 1 << 12)]
     st = syn.Stream(7)
     vals += [int(w) * (Q >> 64) for w in st.words(5)]
     for x in vals:
         res = np.array([x % qq for qq in q], np.uint64)
-        y = np.zeros(L + 1, np.uint64)
+        y = np.zeros(len(p), np.uint64)
         emu.lib().emu_lift(N, L, np.array(q, np.uint64), T, res, y)
         xc = centered(x, Q)
         assert [int(v) for v in y] == [xc % pp for pp in p], x
 
 
-@pytest.mark.parametrize("N,L", [(1024, 2), (8192, 4), (16384, 7)])
+@pytest.mark.parametrize("N,L", [(1024, 2), (2048, 3), (8192, 4), (16384, 7), (16384, 8)])
 def test_exact_scale_down(orc, N, L):
     """round(t d / Q) for extreme and near-tie d, including t d = (Q +- 1)/2
     (mod Q), which takes the mixed-radix branch."""
     q = [int(v) for v in orc.primes(N, L)]
     Q = math.prod(q)
-    p = np.zeros(L + 1, np.uint64)
-    emu.lib().emu_ext_primes(N, L, np.array(q, np.uint64), p)
-    p = [int(v) for v in p]
+    p = _ext_primes(N, L, q)
     dmax = 2 * N * (Q // 2) ** 2
     inv_t = pow(T, -1, Q)
     ds = [0, 1, -1, dmax, -dmax, dmax - 12345, -(dmax // 3)]
