@@ -281,12 +281,12 @@ int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
  * d_a, d_b: [2][L][N] ciphertexts, d_out: [2][L][N], device memory owned by
  * the caller; stream: a cudaStream_t (NULL: legacy default stream).  The
  * call returns when the result is complete.
- * Intermediates live in one file-scope device array of 2^21 u64 words
- * (16 MiB) plus a 64-word header, held by every GPU that loads the library
- * until the process exits.  One multiplication needs (7(L + K) + L^2 + 7L)
- * * N words, K the extension primes of the tensor (K = 4, 6, 8, 9, 11, 13,
- * 15, 17 for L = 1 ... 8): N = 4096 allows L <= 8, N = 8192 allows L <= 7,
- * N = 16384 allows L <= 3; larger sizes are rejected with EINVAL.  The first call on a device looks
+ * Intermediates live in one file-scope device array of 2^20 u64 words
+ * (8 MiB) plus a 64-word header, held by every GPU that loads the library
+ * until the process exits.  One multiplication needs (L^2 + 14L + 7K/2) * N
+ * words, K the 30-bit extension primes of the tensor (K = 4, 6, 8, 9, 11,
+ * 13, 15, 17 for L = 1 ... 8): N = 4096 allows L <= 8, N = 8192 allows
+ * L <= 4, N = 16384 allows L <= 2; larger sizes are rejected with EINVAL.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  All calls share the array and it keeps
  * the previous call's contents (the error flag is cleared each call): calls

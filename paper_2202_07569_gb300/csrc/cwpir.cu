@@ -152,7 +152,10 @@ struct cwpir_ctx {
     if (d_subjobs) cudaFree(d_subjobs);
     if (stream) cudaStreamDestroy(stream);
   }
-  u64 qp_ct() const { return 2ull * (L + K) * N; }
+  // u64 words of a QP-layout polynomial (L u64 limbs, K u32 limbs) and of a
+  // QP-NTT ciphertext
+  u64 qp_poly() const { return cw::qp_poly_words(L, K, N); }
+  u64 qp_ct() const { return 2 * qp_poly(); }
   u64 ct() const { return 2ull * L * N; }
 };
 
@@ -278,14 +281,14 @@ int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
 // ---- scratch ----
 int ensure_scratch(cwpir_ctx *c) {
   if (c->jmax) return CWPIR_OK;
-  const u64 N = c->N, L = c->L, K = c->K;
-  const u64 per_job = (3 * (L + K) + 3 * L + 2 * L + (L + 2) * L) * N * sizeof(u64);
+  const u64 N = c->N, L = c->L;
+  const u64 per_job = (3 * c->qp_poly() + (3 * L + 2 * L + (L + 2) * L) * N) * sizeof(u64);
   const u64 budget = 4ull << 30;
   u64 j = budget / per_job;
   j = std::max<u64>(32, std::min<u64>(1024, j));
   if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
   c->jmax = (u32)j;
-  CUDA_TRY(c, c->Tbuf.ensure(j * 3 * (L + K) * N));
+  CUDA_TRY(c, c->Tbuf.ensure(j * 3 * c->qp_poly()));
   CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
   CUDA_TRY(c, c->CP.ensure(j * 2 * L * N));
   CUDA_TRY(c, c->DN.ensure(j * (L + 2) * L * N));
@@ -597,12 +600,12 @@ int enqueue_expand(cwpir_ctx *c, Plan *P, const u64 *d_query, cudaStream_t st) {
 int prep_leaves(cwpir_ctx *c, const u64 *coef, u32 count, u64 *dst, cudaStream_t st) {
   const u64 LK = c->L + c->K;
   CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] {
-    return cw::launch_lift(c->d_tab, c->h, coef, (u64)c->L * c->N, dst, LK * c->N, 2 * count,
-                           true, st);
+    return cw::launch_lift(c->d_tab, c->h, coef, (u64)c->L * c->N, dst, c->qp_poly(),
+                           2 * count, true, st);
   }));
   CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] {
-    return cw::launch_ntt(c->d_tab, c->h, dst, 2 * count, LK * c->N, 0, (u32)LK, false, nullptr,
-                          0, st);
+    return cw::launch_ntt(c->d_tab, c->h, dst, 2 * count, c->qp_poly(), 0, (u32)LK, false,
+                          nullptr, 0, st);
   }));
   c->stats.kernel_launches += 2;
   c->stats.ntt_polys += 2ull * count * LK;
@@ -1398,10 +1401,10 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
     *bytes = 0;
     return CWPIR_OK;
   }
-  const u64 N = c->N, L = c->L, K = c->K, qp = c->qp_ct(), ctw = c->ct();
+  const u64 N = c->N, L = c->L, qp = c->qp_ct(), ctw = c->ct();
   u64 w = 0;
   if (!c->jmax) {  // the context's scratch comes first
-    const u64 per_job = (3 * (L + K) + 3 * L + 2 * L + (L + 2) * L) * N;
+    const u64 per_job = 3 * c->qp_poly() + (3 * L + 2 * L + (L + 2) * L) * N;
     u64 j = std::max<u64>(32, std::min<u64>(1024, (4ull << 30) / (per_job * 8)));
     if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
     w += j * per_job;
@@ -1532,9 +1535,9 @@ int cwpir_last_stats(const cwpir_ctx *c, cwpir_stats *out) {
 // ---------------------------------------------------------------------
 namespace {
 
-// 2^21 words (16 MiB) of intermediates plus a 64-word header (error flag at
+// 2^20 words (8 MiB) of intermediates plus a 64-word header (error flag at
 // word 0, the job descriptor at words 8..11).
-constexpr size_t kNoAllocWords = size_t(1) << 21;
+constexpr size_t kNoAllocWords = size_t(1) << 20;
 constexpr size_t kNoAllocHeader = 64;
 static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocHeader + kNoAllocWords];
 
@@ -1564,13 +1567,13 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   c->err.clear();
   if (!d_a || !d_b || !d_out) return fail(c, CWPIR_EINVAL, "null buffer");
   const u64 LK = c->L + c->K, N = c->N, L = c->L;
-  const u64 qp = 2 * LK * N;
-  const u64 need = 2 * qp + 3 * LK * N + 3 * L * N + (L + 2) * L * N + 2 * L * N;
+  const u64 pw = c->qp_poly(), qp = 2 * pw;
+  const u64 need = 2 * qp + 3 * pw + 3 * L * N + (L + 2) * L * N + 2 * L * N;
   if (need > kNoAllocWords)
     return fail(c, CWPIR_EINVAL,
-                "N=%u, L=%u needs (7(L+K) + L^2 + 7L)N = %llu scratch words (K = %u extension "
-                "primes); the static array holds %llu (N = 8192 allows L <= 7, N = 16384 "
-                "allows L <= 3)",
+                "N=%u, L=%u needs (L^2 + 14L + 7K/2)N = %llu scratch words (K = %u extension "
+                "primes); the static array holds %llu (N = 8192 allows L <= 4, N = 16384 "
+                "allows L <= 2)",
                 c->N, c->L, (unsigned long long)need, c->K,
                 (unsigned long long)kNoAllocWords);
   cudaSetDevice(c->device);
@@ -1580,15 +1583,15 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   cudaStream_t st = (cudaStream_t)stream;
   int *err = (int *)base;
   cw::MulJob *job_dev = (cw::MulJob *)(base + 8);
-  u64 *qa = base + kNoAllocHeader, *qb = qa + qp, *tb = qb + qp, *eb = tb + 3 * LK * N;
+  u64 *qa = base + kNoAllocHeader, *qb = qa + qp, *tb = qb + qp, *eb = tb + 3 * pw;
   u64 *dn = eb + 3 * L * N, *ob = dn + (L + 2) * L * N;
   cw::MulJob job{qa, qb, d_out, 0};
   // the array keeps the previous call's contents: clear the error flag
   CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int), st));
   CUDA_TRY(c, cudaMemcpyAsync(job_dev, &job, sizeof job, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_a, (u64)c->L * N, qa, LK * N, 2, true, st));
-  CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_b, (u64)c->L * N, qb, LK * N, 2, true, st));
-  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, qa, 4, LK * N, 0, (u32)LK, false, nullptr, 0, st));
+  CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_a, (u64)c->L * N, qa, pw, 2, true, st));
+  CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_b, (u64)c->L * N, qb, pw, 2, true, st));
+  CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, qa, 4, pw, 0, (u32)LK, false, nullptr, 0, st));
   CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
   CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
   CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, 1, job_dev, cw::ROOT_SEL, c->rlk.p,

@@ -1,12 +1,13 @@
 // kernels.cu -- sm_103a kernels of the constant-weight PIR answer path.
 //
-// Layout conventions (u64 residues, limb-major):
+// Layout conventions (u64 residues mod q_j, u32 residues mod the 30-bit
+// extension primes p_k, limb-major):
 //   coefficient ciphertext   [2][L][N]
-//   QP-NTT ciphertext        [2][L+K][N]  NTT form over q_0..q_{L-1}, p_0..p_{K-1}
-//                                         (30-bit p_k: 32-bit arithmetic, values
-//                                         in the low half of the word)
+//   QP-NTT ciphertext        [2] polynomials in QP layout (kernels.cuh): L limbs
+//                            of u64, then K limbs of u32; NTT form
 //   database                 [rows][L][N] NTT form (centered plaintext lift)
-//   tensor buffer  Tbuf      [jobs][3][L+K][N] N d0, N d1, N d2 (lazy residues)
+//   tensor buffer  Tbuf      [jobs][3] QP-layout polynomials N d0, N d1, N d2
+//                            (lazy residues)
 //   scaled buffer  E         [jobs][3][L][N]   round(t d / Q) mod q_j
 //   partials       P         [jobs][2][L][N]   NTT-form sel * DB rows
 //
@@ -196,7 +197,8 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 
 // ---------------------------------------------------------------------
 // Batched NTT: unit u, limb l (prime l): base + u*unit_stride + l*N, read
-// from src (same limb offset, src_unit_stride) when src != nullptr.
+// from src (same limb offset, src_unit_stride) when src != nullptr.  Limbs
+// l >= L (extension primes, forward only) address units in QP layout.
 // grid (limb_end - limb_begin, units).
 // ---------------------------------------------------------------------
 template <int LOGN>
@@ -205,22 +207,26 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
           const u64 *src, u64 src_unit_stride) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 l = limb_begin + blockIdx.x, t = threadIdx.x;
+  const u32 L = T->L, l = limb_begin + blockIdx.x, t = threadIdx.x;
   const u64 u = blockIdx.y;
-  const NttPrime P = T->prime[l < T->L ? l : 0];
-  const u64 *in = src ? src + u * src_unit_stride + (u64)l * N : base + u * unit_stride + (u64)l * N;
-  u64 *out = base + u * unit_stride + (u64)l * N;
   constexpr u32 R = NttShape<LOGN>::R;
-  if (l >= T->L) {  // extension limb, forward only (launch_ntt checks)
-    const ExtNtt E = T->ext[l - T->L];
+  const u64 *unit_in = src ? src + u * src_unit_stride : base + u * unit_stride;
+  u64 *unit_out = base + u * unit_stride;
+  if (l >= L) {  // extension limb, forward only (launch_ntt checks)
+    const ExtNtt E = T->ext[l - L];
+    const u32 *in = ext_limb(unit_in, L, N, l - L);
+    u32 *out = ext_limb(unit_out, L, N, l - L);
     NttRegs32<LOGN> y;
 #pragma unroll
-    for (u32 r = 0; r < R; ++r) y[r] = (u32)in[strided_idx<LOGN>(t, r)];
+    for (u32 r = 0; r < R; ++r) y[r] = in[strided_idx<LOGN>(t, r)];
     ntt_fwd32<LOGN>(y, reinterpret_cast<u32 *>(s), E);
 #pragma unroll
     for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = y[r];
     return;
   }
+  const NttPrime P = T->prime[l];
+  const u64 *in = unit_in + (u64)l * N;
+  u64 *out = unit_out + (u64)l * N;
   NttRegs<LOGN> x;
   if (inverse) {
 #pragma unroll
@@ -244,14 +250,14 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
     k_ntt_jobs_p(const DevTables *T, const MulJob *jobs) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 L = T->L, K = T->K, l = L + blockIdx.x, t = threadIdx.x;
+  const u32 L = T->L, t = threadIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const ExtNtt E = T->ext[blockIdx.x];
-  u64 *p = jobs[job].dst + ((u64)poly * (L + K) + l) * N;
+  u32 *p = ext_limb(jobs[job].dst + poly * qp_poly_words(L, T->K, N), L, N, blockIdx.x);
   NttRegs32<LOGN> x;
   constexpr u32 R = NttShape<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = (u32)p[strided_idx<LOGN>(t, r)];
+  for (u32 r = 0; r < R; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
   // contains barriers: all loads precede all stores
   ntt_fwd32<LOGN>(x, reinterpret_cast<u32 *>(s), E);
 #pragma unroll
@@ -284,7 +290,7 @@ __global__ void k_lift(const DevTables *T, const u64 *src, u64 src_stride, u64 *
     for (int j = 0; j < L; ++j) out[(u64)j * N + c] = x[j];
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) out[(u64)(L + k) * N + c] = y[k];
+  for (int k = 0; k < K; ++k) ext_limb(out, L, N, k)[c] = y[k];
 }
 
 // Internal tree nodes: C ([jobs][2][L][N] coefficient form) -> the P limbs
@@ -297,14 +303,14 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const u64 *in = C + ((u64)job * 2 + poly) * L * N;
-  u64 *out = jobs[job].dst + (u64)poly * (L + K) * N;
+  u64 *out = jobs[job].dst + poly * qp_poly_words(L, K, N);
   u64 x[L];
   u32 y[K];
 #pragma unroll
   for (int j = 0; j < L; ++j) x[j] = in[(u64)j * N + c];
   lift_ext<L, K>(x, y, Cv);
 #pragma unroll
-  for (int k = 0; k < K; ++k) out[(u64)(L + k) * N + c] = y[k];
+  for (int k = 0; k < K; ++k) ext_limb(out, L, N, k)[c] = y[k];
 }
 
 // ---------------------------------------------------------------------
@@ -319,37 +325,41 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
     k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 LK = T->L + T->K, l = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
+  const u32 L = T->L, l = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
   const u64 job = blockIdx.x;
   const MulJob J = jobs[job];
-  const u64 ps = (u64)LK * N;
-  const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
-  const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
-  u64 *out = Tbuf + ((job * 3 + which) * LK + l) * N;
+  const u64 ps = qp_poly_words(L, T->K, N);
+  u64 *outp = Tbuf + (job * 3 + which) * ps;
   constexpr u32 R = NttShape<LOGN>::R;
-  if (l >= T->L) {  // extension limb: products in [0, 2p), 32-bit transform
-    const ExtNtt E = T->ext[l - T->L];
+  if (l >= L) {  // extension limb: products in [0, 2p), 32-bit transform
+    const u32 k = l - L;
+    const ExtNtt E = T->ext[k];
     const u32 p2 = 2 * E.e.p;
+    const u32 *a0 = ext_limb(J.a, L, N, k), *a1 = ext_limb(J.a + ps, L, N, k);
+    const u32 *b0 = ext_limb(J.b, L, N, k), *b1 = ext_limb(J.b + ps, L, N, k);
     NttRegs32<LOGN> y;
 #pragma unroll
     for (u32 r = 0; r < R; ++r) {
       const u32 c = ntt_pos<LOGN>(t, r);
       u32 v;
-      if (which == 0) v = mulmod_ext_lazy((u32)a0[c], (u32)b0[c], E.e);
-      else if (which == 2) v = mulmod_ext_lazy((u32)a1[c], (u32)b1[c], E.e);
+      if (which == 0) v = mulmod_ext_lazy(a0[c], b0[c], E.e);
+      else if (which == 2) v = mulmod_ext_lazy(a1[c], b1[c], E.e);
       else {
-        v = mulmod_ext_lazy((u32)a0[c], (u32)b1[c], E.e) +
-            mulmod_ext_lazy((u32)a1[c], (u32)b0[c], E.e);
+        v = mulmod_ext_lazy(a0[c], b1[c], E.e) + mulmod_ext_lazy(a1[c], b0[c], E.e);
         v = v >= p2 ? v - p2 : v;
       }
       y[r] = v;
     }
     ntt_inv32<LOGN>(y, reinterpret_cast<u32 *>(s), E);  // N d in [0, 2p)
+    u32 *out = ext_limb(outp, L, N, k);
 #pragma unroll
     for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = y[r];
     return;
   }
   const NttPrime P = T->prime[l];
+  const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
+  const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
+  u64 *out = outp + (u64)l * N;
   NttRegs<LOGN> x;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) {
@@ -375,12 +385,12 @@ __global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err,
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 jw = blockIdx.y;
-  const u64 *in = Tbuf + jw * (L + K) * N;
+  const u64 *in = Tbuf + jw * qp_poly_words(L, K, N);
   u64 dq[L], dp[K], e[L];
 #pragma unroll
   for (int j = 0; j < L; ++j) dq[j] = in[(u64)j * N + c];
 #pragma unroll
-  for (int k = 0; k < K; ++k) dp[k] = in[(u64)(L + k) * N + c];
+  for (int k = 0; k < K; ++k) dp[k] = ext_limb(in, L, N, k)[c];
   if (!scale_coeff<L>(dq, dp, e, S)) atomicOr(err, 1);
   u64 *out = E + jw * L * N;
 #pragma unroll
@@ -597,7 +607,7 @@ __global__ void k_ks_mac_out(const DevTables *T, const u64 *DN, u32 n_add, const
   if (internal) {
     u64 *d = jobs[job].dst;
     d[(u64)j * N + c] = a0;
-    d[((u64)(L + T->K) + j) * N + c] = a1;
+    d[qp_poly_words(L, T->K, N) + (u64)j * N + c] = a1;
   } else {
     O[(job * 2 + 0) * L * N + (u64)j * N + c] = a0;
     O[(job * 2 + 1) * L * N + (u64)j * N + c] = a1;
@@ -617,7 +627,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
   const u32 L = T->L, t = threadIdx.x, j = blockIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const NttPrime P = T->prime[j];
-  const u64 *in = src_from_jobs ? jobs[job].dst + ((u64)poly * (L + T->K) + j) * N
+  const u64 *in = src_from_jobs ? jobs[job].dst + poly * qp_poly_words(L, T->K, N) + (u64)j * N
                                 : O + (((u64)job * 2 + poly) * L + j) * N;
   u64 *out;
   if (dst_to_jobs == 1) out = jobs[job].dst + ((u64)poly * L + j) * N;
@@ -643,7 +653,7 @@ __global__ void k_pm_leaf(const DevTables *T, const MulJob *jobs, u32 sp, const 
   const MulJob J = jobs[job];
   const u64 LN = (u64)L * N;
   const u64 m = db[((u64)J.row * sp + p) * LN + (u64)j * N + c];
-  const u64 ps = (u64)(L + K) * N;
+  const u64 ps = qp_poly_words(L, K, N);
   u64 *o = P + (job * sp + p) * 2 * LN + (u64)j * N + c;
   o[0] = barrett(J.a[(u64)j * N + c], m, Pr.q, Pr.mu);
   o[LN] = barrett(J.a[ps + (u64)j * N + c], m, Pr.q, Pr.mu);

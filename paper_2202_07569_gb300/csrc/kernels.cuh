@@ -25,9 +25,19 @@ struct DevTables {
   ScaleTab scale;         // exact round(t d / Q)
 };
 
+// QP layout of one polynomial (NTT domain or, for the tensor buffer,
+// coefficients): L limbs of N u64 residues mod q_j, then K limbs of N u32
+// residues mod the 30-bit p_k; L N + K N / 2 u64 words in all.
+CW_HD u64 qp_poly_words(u32 L, u32 K, u32 N) { return (u64)L * N + (u64)K * N / 2; }
+CW_HD u32 *ext_limb(u64 *poly, u32 L, u32 N, u32 k) {
+  return reinterpret_cast<u32 *>(poly + (u64)L * N) + (u64)k * N;
+}
+CW_HD const u32 *ext_limb(const u64 *poly, u32 L, u32 N, u32 k) {
+  return reinterpret_cast<const u32 *>(poly + (u64)L * N) + (u64)k * N;
+}
+
 // One homomorphic multiplication of two ciphertexts held in "QP-NTT" form:
-// [2][L+K][N] residues, NTT domain, Q limbs then P limbs (the P residues,
-// below 2^30, in the low half of their 64-bit words).
+// two polynomials in QP layout, NTT domain.
 struct MulJob {
   const u64 *a;
   const u64 *b;
