@@ -37,7 +37,13 @@ METRIC = "PIR answer DB MB/s per query (N=8192,k=4); batched vs plain; p50/p99 l
 WL = dict(N=8192, L=4, n=65536, k=4, m=37, plen=8192, t=65537, coef_bytes=2)
 WORKLOAD_NAME = ("index PIR n=65536 rows x 8192 16-bit coefficients, k=4, m=37, "
                  "BFV N=8192 L=4 (54-bit primes) t=65537, one query per step")
-IMAD_PER_MODMUL = 10  # one 64x64 high product (4 IMAD) + two low products (3 each)
+# 32-bit integer multiply-adds implied by one modular multiplication: a
+# 54-bit residue in a 64-bit word needs one 64 x 64 high product (4 IMAD)
+# and two low products (3 each); a 30-bit residue in a 32-bit word needs a
+# high and two low 32-bit products
+IMAD_PER_MODMUL54 = 10
+IMAD_PER_MODMUL30 = 3
+EXT_PRIMES = {1: 4, 2: 6, 3: 8, 4: 9, 5: 11, 6: 13, 7: 15, 8: 17}  # 30-bit primes per L
 IMAD_PER_SM_CLK = 64
 SMS = 152
 
@@ -111,20 +117,26 @@ def make_inputs(seed: int = 12, rows: int | None = None):
     return q, rlk, query, items, cw
 
 
-def modmuls_per_job(kind: str) -> float:
-    """Algorithmic 54-bit modular multiplications per job of a kernel class."""
+def imad_per_job(kind: str) -> float:
+    """Algorithmic work per job of a kernel class, in IMAD-equivalents:
+    54-bit modular multiplications (one per butterfly, product or
+    reduction) times 10, 30-bit ones times 3, and the scale-down's 32 x 32
+    products of 27-bit halves with 30-bit constants times 1."""
     N, L = WL["N"], WL["L"]
-    K = L + 1
+    K = EXT_PRIMES[L]
     logN = N.bit_length() - 1
-    ntt = N // 2 * logN + N
-    if kind == "tensor_intt":
-        return 3 * (L + K) * ntt + 4 * (L + K) * N
-    if kind == "relin_pm":
-        return L * ((L + 2) * (N // 2 * logN) + 2 * L * N + 2 * N)
-    if kind == "scale":
-        return 3 * N * (2 * L * K + 3 * L + 3 * K)
+    bf = N // 2 * logN
+    m54, m30 = IMAD_PER_MODMUL54, IMAD_PER_MODMUL30
+    if kind == "tensor_intt":  # 3 outputs x (L + K) limbs: 4 products + inverse transform
+        return 3 * (L * bf * m54 + K * bf * m30) + 4 * N * (L * m54 + K * m30)
+    if kind == "relin_pm":  # L(L + 2) forward transforms, 2L^2 key and 2L DB products
+        return m54 * L * ((L + 2) * bf + 2 * L * N + 2 * N)
+    if kind == "scale":  # per coefficient of 3 polynomials
+        per = (m54 * L + K * (2 * L + 2) + m54 * K   # y_j, first stage and its reductions
+               + L * (2 * K + 2) + m54 * L)          # second stage and its reductions
+        return 3 * N * per
     if kind == "lift":
-        return 2 * N * (2 * L + L * K + K)
+        return 2 * N * (m54 * L + K * 2 * L + m54 * K)
     return 0.0
 
 
@@ -134,9 +146,9 @@ def modmuls_per_job(kind: str) -> float:
 # traffic grows in proportion to the jobs of a launch, so a full launch's
 # traffic is this figure times its jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor_intt": (74429952 + 179669504) / 128,
-    "scale": (226552320 + 73764096) / 128,
-    "relin_pm": (187928832 + 153922304 + 239259392 + 14970880) / 128,
+    "tensor_intt": (70331136 + 164536832) / 128,
+    "scale": (213965056 + 71994880) / 128,
+    "relin_pm": (187106560 + 153571584 + 239268864 + 13915392) / 128,
 }
 
 
@@ -230,19 +242,20 @@ def run_gpu(args, rank: int, world: int, dist):
     jobs_per_launch = {"tensor_intt": stats["mults"], "relin_pm": stats["mults"],
                        "scale": stats["mults"], "lift": 0}.get(dom, 0)
     launches_per_step = launches / args.steps
-    work_per_launch = modmuls_per_job(dom) * jobs_per_launch / max(1.0, launches_per_step)
+    work_per_launch = imad_per_job(dom) * jobs_per_launch / max(1.0, launches_per_step)
     avg_launch_s = ms / launches / 1e3
     sm_max = out["clocks"].get("sm_max_mhz") or 2070.0
-    peak = SMS * IMAD_PER_SM_CLK * sm_max * 1e6 / IMAD_PER_MODMUL / 1e12
+    peak = SMS * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
     achieved = work_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else 0.0
     out["roofline"] = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                       "unit": "Tmodmul/s", "frac": achieved / peak if peak else None,
+                       "unit": "TIMAD/s", "frac": achieved / peak if peak else None,
                        "traffic": (DRAM_BYTES_PER_JOB[dom] * jobs_per_launch
                                    / max(1.0, launches_per_step)
                                    if dom in DRAM_BYTES_PER_JOB else None),
                        "traffic_unit": "bytes per launch",
-                       "peak_basis": f"{SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
-                                     f"/ {IMAD_PER_MODMUL} IMAD per 54-bit modmul"}
+                       "peak_basis": f"{SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz; "
+                                     f"work = {IMAD_PER_MODMUL54} IMAD per 54-bit and "
+                                     f"{IMAD_PER_MODMUL30} per 30-bit modular multiplication"}
     # batched vs plain: 16 queries in one batched call replayed from a CUDA
     # graph, against the plain one-query calls timed above
     if args.batch:

@@ -316,10 +316,52 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // ---------------------------------------------------------------------
 // Tensor of two QP-NTT ciphertexts, one output polynomial and limb per
 // CTA, followed by the inverse NTT: d0 = a0 b0, d1 = a0 b1 + a1 b0,
-// d2 = a1 b1.  grid (njobs, 3, L+K): the limb varies slowest so that the
-// blocks resident on one SM share one prime's twiddles in L1.  Extension
-// limbs run on 32-bit words.
+// d2 = a1 b1.  k_tensor_intt covers the L ciphertext limbs, grid
+// (njobs, 3, L); k_tensor_ext the K extension limbs on 32-bit words, grid
+// (njobs, 3, K), with a smaller register budget and more resident blocks
+// so that the operand loads of some blocks overlap the transforms of
+// others.  The limb varies slowest so that the blocks resident on one SM
+// share one prime's twiddles in L1.
 // ---------------------------------------------------------------------
+template <int LOGN>
+struct ExtShape {  // 32-bit transforms: up to 2048 threads per SM
+  static constexpr int min_blocks = 2048 / NttShape<LOGN>::threads > 4
+                                        ? 4 : 2048 / NttShape<LOGN>::threads;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+    k_tensor_ext(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
+  extern __shared__ u32 s32[];
+  constexpr u32 N = 1u << LOGN;
+  const u32 L = T->L, k = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
+  const u64 job = blockIdx.x;
+  const MulJob J = jobs[job];
+  const u64 ps = qp_poly_words(L, T->K, N);
+  constexpr u32 R = NttShape<LOGN>::R;
+  const ExtNtt E = T->ext[k];
+  const u32 p2 = 2 * E.e.p;
+  const u32 *a0 = ext_limb(J.a, L, N, k), *a1 = ext_limb(J.a + ps, L, N, k);
+  const u32 *b0 = ext_limb(J.b, L, N, k), *b1 = ext_limb(J.b + ps, L, N, k);
+  NttRegs32<LOGN> y;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) {  // products in [0, 2p)
+    const u32 c = ntt_pos<LOGN>(t, r);
+    u32 v;
+    if (which == 0) v = mulmod_ext_lazy(a0[c], b0[c], E.e);
+    else if (which == 2) v = mulmod_ext_lazy(a1[c], b1[c], E.e);
+    else {
+      v = mulmod_ext_lazy(a0[c], b1[c], E.e) + mulmod_ext_lazy(a1[c], b0[c], E.e);
+      v = v >= p2 ? v - p2 : v;
+    }
+    y[r] = v;
+  }
+  ntt_inv32<LOGN>(y, s32, E);  // N d in [0, 2p)
+  u32 *out = ext_limb(Tbuf + (job * 3 + which) * ps, L, N, k);
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = y[r];
+}
+
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
@@ -331,31 +373,6 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
   const u64 ps = qp_poly_words(L, T->K, N);
   u64 *outp = Tbuf + (job * 3 + which) * ps;
   constexpr u32 R = NttShape<LOGN>::R;
-  if (l >= L) {  // extension limb: products in [0, 2p), 32-bit transform
-    const u32 k = l - L;
-    const ExtNtt E = T->ext[k];
-    const u32 p2 = 2 * E.e.p;
-    const u32 *a0 = ext_limb(J.a, L, N, k), *a1 = ext_limb(J.a + ps, L, N, k);
-    const u32 *b0 = ext_limb(J.b, L, N, k), *b1 = ext_limb(J.b + ps, L, N, k);
-    NttRegs32<LOGN> y;
-#pragma unroll
-    for (u32 r = 0; r < R; ++r) {
-      const u32 c = ntt_pos<LOGN>(t, r);
-      u32 v;
-      if (which == 0) v = mulmod_ext_lazy(a0[c], b0[c], E.e);
-      else if (which == 2) v = mulmod_ext_lazy(a1[c], b1[c], E.e);
-      else {
-        v = mulmod_ext_lazy(a0[c], b1[c], E.e) + mulmod_ext_lazy(a1[c], b0[c], E.e);
-        v = v >= p2 ? v - p2 : v;
-      }
-      y[r] = v;
-    }
-    ntt_inv32<LOGN>(y, reinterpret_cast<u32 *>(s), E);  // N d in [0, 2p)
-    u32 *out = ext_limb(outp, L, N, k);
-#pragma unroll
-    for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = y[r];
-    return;
-  }
   const NttPrime P = T->prime[l];
   const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
   const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
@@ -912,8 +929,12 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_tensor_intt<LG>, ntt_smem_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_tensor_intt<LG><<<dim3(njobs, 3, h.L + h.K), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(T, jobs,
-                                                                                    Tbuf);
+    k_tensor_intt<LG><<<dim3(njobs, 3, h.L), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
+        T, jobs, Tbuf);
+    const size_t smem32 = ntt_smem_bytes<LG>() / 2;
+    e = allow_smem(k_tensor_ext<LG>, smem32);
+    if (e != cudaSuccess) return e;
+    k_tensor_ext<LG><<<dim3(njobs, 3, h.K), ntt_block<LG>(), smem32, st>>>(T, jobs, Tbuf);
   });
   return cudaGetLastError();
 }
