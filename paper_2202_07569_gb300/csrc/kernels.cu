@@ -499,8 +499,14 @@ struct LazySum {
 
 // (B) for the answer's last level, rows of one plaintext.  The launch's
 // jobs form `segs` segments of seg_len consecutive jobs (one segment per
-// query); block z = s*G + g sums (acc0, acc1) * DB[row] over jobs g, g+G,
-// ... of segment s into P[s*G + g][2][L][N].  grid (N/256, L, segs*G).
+// query); block z = s*G + g handles jobs g, g+G, ... of segment s.  The key
+// switch is linear in the digits, so its key products move out of the row
+// sum: modulo q_j, exactly,
+//   sum_rows sel * DB = (sum_rows e0 DB + sum_d b_d sum_rows D_d DB,
+//                        sum_rows e1 DB + sum_d a_d sum_rows D_d DB),
+// so each thread keeps L + 2 row sums (digits d < L, then e0, e1) and
+// multiplies the digit sums by the key once at the end.  Output
+// P[s*G + g][2][L][N].  grid (N/256, L, segs*G).
 template <int L>
 __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 seg_len, u32 G,
                             const MulJob *jobs, const u64 *key, const u64 *key_s,
@@ -510,16 +516,7 @@ __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 se
   const NttPrime Pr = T->prime[j];
   const u64 q = Pr.q;
   const u64 LN = (u64)L * N;
-  u64 kb[L], kbs[L], ka[L], kas[L];
-#pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const u64 ob = ((u64)(i * 2 + 0) * L + j) * N + c, oa = ((u64)(i * 2 + 1) * L + j) * N + c;
-    kb[i] = key[ob];
-    kbs[i] = key_s[ob];
-    ka[i] = key[oa];
-    kas[i] = key_s[oa];
-  }
-  LazySum s0, s1;
+  LazySum acc[L + 2];
   u32 terms = 0;
   // the next row's index is loaded one iteration ahead so that the row's
   // database load issues together with the digit loads
@@ -528,19 +525,26 @@ __global__ void k_ks_mac_pm(const DevTables *T, const u64 *DN, u32 n_add, u32 se
   for (u32 x = g; x < seg_len; x += G, job += G) {
     const u64 m = db[row * LN + (u64)j * N + c];
     if (x + G < seg_len) row = jobs[job + G].row;
-    u64 a0, a1;
-    ks_mac<L>(DN, job, n_add, j, c, N, kb, kbs, ka, kas, q, a0, a1);
-    s0.mac(a0, m);
-    s1.mac(a1, m);
+    const u64 *dn = DN + job * (L + n_add) * LN + (u64)j * N + c;
+#pragma unroll
+    for (int d = 0; d < L + 2; ++d) acc[d].mac(dn[d * LN], m);
     if (++terms == 15) {
-      s0.fold(q, Pr.mu);
-      s1.fold(q, Pr.mu);
+#pragma unroll
+      for (int d = 0; d < L + 2; ++d) acc[d].fold(q, Pr.mu);
       terms = 1;  // the folded residue counts as one term
     }
   }
+  u64 o0 = acc[L].value(q, Pr.mu), o1 = acc[L + 1].value(q, Pr.mu);
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const u64 v = acc[i].value(q, Pr.mu);
+    const u64 ob = ((u64)(i * 2 + 0) * L + j) * N + c, oa = ((u64)(i * 2 + 1) * L + j) * N + c;
+    o0 = addq(o0, shoup(v, key[ob], key_s[ob], q), q);
+    o1 = addq(o1, shoup(v, key[oa], key_s[oa], q), q);
+  }
   u64 *o = P + (u64)sg * 2 * LN + (u64)j * N + c;
-  o[0] = s0.value(q, Pr.mu);
-  o[LN] = s1.value(q, Pr.mu);
+  o[0] = o0;
+  o[LN] = o1;
 }
 
 // Rows of sp > 1 plaintexts: the selection entries of the launch's jobs are
