@@ -274,15 +274,21 @@ struct ScaleTab {
   u32 A[kMaxK];                          // t f^-1 Q^-1 (P/p_k)^-1 mod p_k
   u32 B[kMaxL][kMaxK], B27[kMaxL][kMaxK]; // -q_j^-1 (P/p_k)^-1 mod p_k, times 2^27
   u32 Cr[kMaxK];                         // (P/p_k)^-1 mod p_k
-  u64 pw_hi[kMaxK], pw_lo[kMaxK];        // floor(2^128 / p_k)
+  u32 pw58[kMaxK];                       // floor(2^58 / p_k)
   // e_j = [sum_k yb_k (P/p_k) + rho2 (-P)]_{q_j}, constants as 27-bit halves
   u32 hat2[kMaxK][kMaxL][2], negp2[kMaxL][2];
 };
 
 // dq: residues of f*d below 2^55 (lazy [0, 2q) values are fine); dp:
-// residues below 2^31 (lazy [0, 2p)).  Returns false if the P-basis
-// rounding ever lands in the ambiguous zone, which the bound on |r| rules
-// out; callers record it as an internal error.
+// residues below 2^31 (lazy [0, 2p)).
+//
+// The conversion of r back to Q needs rho2 = round(sum_k yb_k / p_k).  As
+// sum_k yb_k / p_k = rho2 + r/P with |r|/P < 2^-18 (P > 2^17 t N Q), the sum
+// lies within 2^-18 of the integer rho2, and a 6.58 fixed-point sum of
+// yb_k floor(2^58 / p_k), each term low by less than yb_k < 2^30 units of
+// 2^-58, i.e. the sum low by less than 17 * 2^-28, rounds to it exactly.
+// Returns false if that sum is ever 2^-17 or more away from an integer
+// (which the bound rules out); callers record it as an internal error.
 template <int L>
 CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S) {
   constexpr int K = ext_count(L);
@@ -306,8 +312,11 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
       s += (y[j] & kMask27) * S.B[j][k] + (y[j] >> 27) * S.B27[j][k];
     yb[k] = reduce_ext(s, S.ext[k]);
   }
-  bool amb2;
-  u64 rho2 = round_sum<K>(yb, S.pw_hi, S.pw_lo, &amb2);
+  u64 fix = 0;
+  for (int k = 0; k < K; ++k) fix += yb[k] * S.pw58[k];  // each < 2^58: sum < 2^63
+  const u64 rho2 = (fix + (1ull << 57)) >> 58;
+  const u64 frac = (fix + (1ull << 57)) & ((1ull << 58) - 1);  // offset + 1/2, in 2^-58
+  const bool far = frac < (1ull << 57) - (1ull << 41) || frac > (1ull << 57) + (1ull << 41);
   // K + 1 <= 18 products of values below 2^30 with 27-bit halves: the words
   // ll and x stay below 18 * 2^57 < 2^62.2; the sum ll + x 2^27 < 2^90
   for (int j = 0; j < L; ++j) {
@@ -320,7 +329,7 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
     const u64 hi = (x >> 37) + (lo < ll ? 1 : 0);
     out[j] = barrett_reduce(hi, lo, S.Q.q[j], S.Q.mu[j]);
   }
-  return !amb2;
+  return !far;
 }
 
 }  // namespace cw

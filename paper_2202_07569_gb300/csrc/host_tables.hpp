@@ -221,9 +221,7 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
       S.B[j][k] = (u32)b;
       S.B27[j][k] = (u32)hmul(b, 1ull << 27, pk);
     }
-    const u128 W = (~(u128)0) / pk;  // floor(2^128 / p_k)
-    S.pw_hi[k] = (u64)(W >> 64);
-    S.pw_lo[k] = (u64)W;
+    S.pw58[k] = (u32)((1ull << 58) / pk);
   }
   for (u32 j = 0; j < L; ++j) {
     const u64 qj = q[j];
