@@ -266,7 +266,7 @@ enum {
    * the durations per kernel class (read with cwpir_kernel_times); 0
    * (default): no events */
   CWPIR_OPT_KERNEL_TIMING = 4,
-  /* multiplications per kernel launch (0 = automatic, at most 1024); sizes
+  /* multiplications per kernel launch (0 = automatic, at most 2048); sizes
    * the context's scratch: setting it waits for the device, frees the
    * scratch and the answer plans, which the next call rebuilds */
   CWPIR_OPT_MAX_JOBS = 5

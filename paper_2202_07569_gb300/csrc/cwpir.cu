@@ -279,13 +279,18 @@ int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
 }
 
 // ---- scratch ----
+// Multiplications per launch: as many as kScratchBytes of per-job scratch
+// allows, between 32 and kMaxJobs (larger launches measured faster: 96,
+// 256, ~940 and ~1800 jobs per launch for the configuration-2 answer).
+constexpr u64 kMaxJobs = 2048;
+constexpr u64 kScratchBytes = 8ull << 30;
+
 int ensure_scratch(cwpir_ctx *c) {
   if (c->jmax) return CWPIR_OK;
   const u64 N = c->N, L = c->L;
   const u64 per_job = (3 * c->qp_poly() + (3 * L + 2 * L + (L + 2) * L) * N) * sizeof(u64);
-  const u64 budget = 4ull << 30;
-  u64 j = budget / per_job;
-  j = std::max<u64>(32, std::min<u64>(1024, j));
+  u64 j = kScratchBytes / per_job;
+  j = std::max<u64>(32, std::min<u64>(kMaxJobs, j));
   if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
   c->jmax = (u32)j;
   CUDA_TRY(c, c->Tbuf.ensure(j * 3 * c->qp_poly()));
@@ -1405,11 +1410,11 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
   u64 w = 0;
   if (!c->jmax) {  // the context's scratch comes first
     const u64 per_job = 3 * c->qp_poly() + (3 * L + 2 * L + (L + 2) * L) * N;
-    u64 j = std::max<u64>(32, std::min<u64>(1024, (4ull << 30) / (per_job * 8)));
+    u64 j = std::max<u64>(32, std::min<u64>(kMaxJobs, kScratchBytes / (per_job * 8)));
     if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
     w += j * per_job;
   }
-  const u64 J = c->jmax ? c->jmax : 1024;
+  const u64 J = c->jmax ? c->jmax : kMaxJobs;
   const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();
   const bool memo = c->opt_share && top >= 2;
   const u64 h = db->folklore ? db->m / 2 : cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
@@ -1470,7 +1475,8 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
       return CWPIR_OK;
     case CWPIR_OPT_KERNEL_TIMING: c->opt_timing = value ? 1 : 0; return CWPIR_OK;
     case CWPIR_OPT_MAX_JOBS:
-      if (value < 0 || value > 1024) return fail(c, CWPIR_EINVAL, "max jobs must be in [0, 1024]");
+      if (value < 0 || value > (int64_t)kMaxJobs)
+        return fail(c, CWPIR_EINVAL, "max jobs must be in [0, %llu]", (unsigned long long)kMaxJobs);
       cudaSetDevice(c->device);
       cudaStreamSynchronize(c->stream);
       cudaDeviceSynchronize();
