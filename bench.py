@@ -147,9 +147,9 @@ def imad_per_job(kind: str) -> float:
 # traffic grows in proportion to the jobs of a launch, so a full launch's
 # traffic is this figure times its jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor_intt": (70331136 + 164536832) / 128,
-    "scale": (213965056 + 71994880) / 128,
-    "relin_pm": (187106560 + 153571584 + 239268864 + 13915392) / 128,
+    "tensor_intt": (33144064 + 45691136 + 37215488 + 55372032) / 128,
+    "scale": (213961472 + 72368128) / 128,
+    "relin_pm": (187631616 + 153526528 + 239120896 + 13793792) / 128,
 }
 
 
