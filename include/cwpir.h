@@ -130,7 +130,10 @@ void cwpir_destroy(cwpir_ctx *ctx);
  * against the database returns s ciphertexts, the inner products of the one
  * selection vector with each plaintext column (Sec. 3.3.3).  For index PIR the codeword of row i is the perfect mapping of
  * i; for keyword PIR (Sec. 3.3.6) the mapping of the row's keyword.  The
- * rows are lifted to centered residues and kept in HBM in NTT form.
+ * rows are lifted to centered integers and kept in HBM in NTT form: rows of
+ * one plaintext with k >= 2 modulo four internal 30-bit primes (16 bytes a
+ * coefficient; the answer multiplies them exactly as integers), otherwise
+ * modulo the ciphertext primes (8 L bytes a coefficient and plaintext).
  * 1 <= k <= 16, k <= m <= 16384, 1 <= n <= 2^24.  *db_id receives a handle.
  * EINVAL (including a coefficient >= t or a bad codeword), ENOMEM, ECUDA. */
 int cwpir_load_db(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len, uint32_t k,
@@ -248,7 +251,8 @@ int cwpir_selection(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
 int cwpir_arith_cw_eq(cwpir_ctx *ctx, uint32_t m, uint32_t k, const uint64_t *x,
                       const uint64_t *y, uint64_t *out);
 /* Plain multiplication PM of a ciphertext by row `row` of a database: by
- * each of the row's s plaintexts, out: [s][2][L][N]. */
+ * each of the row's s plaintexts, out: [s][2][L][N].  EINTERNAL if a device
+ * consistency check fails. */
 int cwpir_plain_mul(cwpir_ctx *ctx, int32_t db_id, uint64_t row,
                     const uint64_t *ct, uint64_t *out);
 

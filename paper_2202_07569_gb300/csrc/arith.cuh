@@ -332,4 +332,60 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
   return !far;
 }
 
+// ---------------------------------------------------------------------
+// Exact products with database rows in a four-prime "row basis".
+//
+// The plaintext rows are small integers (|v| <= t/2 after the centered
+// lift), and the inputs of the last tree level's key switch (the limbs of
+// e0, e1 and the digits of e2) are residues below 2^54.  A sum over at most
+// 2048 rows of their negacyclic products with rows is therefore an integer
+// x with |x| <= 2^11 N 2^54 2^19 <= 2^98 (N <= 2^14, t < 2^20), exactly
+// representable by its residues modulo the first four 30-bit extension
+// primes r_k (product R > 2^119.9): |x| / R < 2^-21.  row_crt recovers x
+// modulo the ciphertext primes from N x mod r_k (the inverse transforms
+// leave the factor N): y_k = [(N x)_k (R/r_k)^-1 N^-1]_{r_k},
+// x = sum_k y_k (R/r_k) - rho R with rho = round(sum_k y_k / r_k), and
+// sum_k y_k / r_k lies within 2^-21 of rho, so a 6.58 fixed-point sum
+// rounds to it exactly (as in scale_coeff).
+// ---------------------------------------------------------------------
+constexpr int kRowPrimes = 4;
+
+struct RowTab {
+  ExtPrime r[kRowPrimes];
+  u32 theta[kRowPrimes];              // (R/r_k)^-1 N^-1 mod r_k
+  u32 rw58[kRowPrimes];               // floor(2^58 / r_k)
+  u32 hat2[kRowPrimes][kMaxL][2];     // (R/r_k) mod q_j, 27-bit halves
+  u32 negr2[kMaxL][2];                // (-R) mod q_j, 27-bit halves
+  u64 q[kMaxL], q_mu[kMaxL];          // ciphertext primes, floor(2^116 / q_j)
+};
+
+// xr: N x mod r_k, below 2^31 (lazy [0, 2r)); y: the digits y_k; returns
+// rho, and false in *far if the fixed-point sum is 2^-17 or more away from
+// an integer (ruled out by the bound on |x|).
+CW_HD u64 row_digits(const u32 *xr, u32 *y, const RowTab &T, bool *far) {
+  u64 fix = 0;
+  for (int k = 0; k < kRowPrimes; ++k) {
+    const u32 v = xr[k] >= T.r[k].p ? xr[k] - T.r[k].p : xr[k];
+    const u32 m = mulmod_ext_lazy(v, T.theta[k], T.r[k]);
+    y[k] = m >= T.r[k].p ? m - T.r[k].p : m;
+    fix += (u64)y[k] * T.rw58[k];
+  }
+  const u64 frac = (fix + (1ull << 57)) & ((1ull << 58) - 1);
+  *far = frac < (1ull << 57) - (1ull << 41) || frac > (1ull << 57) + (1ull << 41);
+  return (fix + (1ull << 57)) >> 58;
+}
+
+// x mod q_j from the digits: sum_k y_k (R/r_k) - rho R (five products of
+// values below 2^30 with 27-bit halves, sum below 2^88).
+CW_HD u64 row_to_q(const u32 *y, u64 rho, int j, const RowTab &T) {
+  u64 ll = rho * T.negr2[j][0], x = rho * T.negr2[j][1];
+  for (int k = 0; k < kRowPrimes; ++k) {
+    ll += (u64)y[k] * T.hat2[k][j][0];
+    x += (u64)y[k] * T.hat2[k][j][1];
+  }
+  const u64 lo = ll + (x << 27);
+  const u64 hi = (x >> 37) + (lo < ll ? 1 : 0);
+  return barrett_reduce(hi, lo, T.q[j], T.q_mu[j]);
+}
+
 }  // namespace cw

@@ -78,6 +78,7 @@ struct ExpRound {
 struct Plan {
   u32 nq = 1, cfac = 0, k = 0, top = 0, m = 0, h_in = 0, sp = 1;
   bool memo = false, leaf_root = false;
+  bool rows_db = false;  // the database is held in the row basis
   u64 n_memo = 0, mults = 0;
   std::vector<Chunk> memo_chunks;
   std::vector<std::vector<Chunk>> batches;  // per row batch, levels bottom-up
@@ -105,7 +106,12 @@ struct Db {
   u32 plen = 0, k = 0, m = 0;
   u32 sp = 1;                 // plaintexts per row (Sec. 3.3.1): ceil(plen / N)
   bool folklore = false;      // rows indexed by the plain folklore operator
-  DevBuf db;                  // [n][sp][L][N] NTT form
+  // One plaintext per row and k >= 2: the rows are held in the row basis
+  // ([n][4][N] u32, NTT form modulo the first four extension primes; the
+  // last tree level multiplies them exactly as integers).  Otherwise
+  // [n][sp][L][N] u64, NTT form modulo the ciphertext primes.
+  bool rows = false;
+  DevBuf db;
   std::vector<uint16_t> cw;   // [n][k]
   // answer plans over all rows, by (queries per call, compression factor)
   std::map<std::pair<u32, u32>, std::unique_ptr<Plan>> plans;
@@ -132,6 +138,7 @@ struct cwpir_ctx {
   // scratch
   u32 jmax = 0;
   DevBuf Tbuf, E, CP, DN, exp_tau, exp_DN, exp_O, tmp_ct, io_in, io_out;
+  DevBuf RS, DNQ, one_job;  // row-basis row sums and their Q-basis forms
   DevBuf SEL;  // NTT-form selection entries [jmax][2][L][N] (rows of several plaintexts)
   bool capturing = false;
   int *d_err = nullptr;
@@ -251,6 +258,7 @@ int build_tables(cwpir_ctx *c) {
                          cudaMemcpyHostToDevice));
   fill_lift(h.lift, c->q, c->p);
   fill_scale(h.scale, c->q, c->p, c->t, N);
+  fill_rows(h.rows, c->q, c->p, N);
   CUDA_TRY(c, cudaMalloc(&c->d_tab, sizeof(cw::DevTables)));
   CUDA_TRY(c, cudaMemcpy(c->d_tab, &h, sizeof h, cudaMemcpyHostToDevice));
   return CWPIR_OK;
@@ -284,11 +292,22 @@ int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
 // 256, ~940 and ~1800 jobs per launch for the configuration-2 answer).
 constexpr u64 kMaxJobs = 2048;
 constexpr u64 kScratchBytes = 8ull << 30;
+// Row groups finished at a time on row-basis databases.
+constexpr u32 kRowGroups = 64;
+
+// u64 words per job of the digit transforms: (L+2) L N for the ciphertext
+// basis, 3L x 4 x N u32 for the row basis
+u64 dn_words(u64 L, u64 N) { return std::max<u64>((L + 2) * L, 6 * L) * N; }
+// u64 words of the row-basis group buffers: row sums [kRowGroups][3L][4][N]
+// u32 and their Q-basis forms [kRowGroups][L+2][L][N]
+u64 rs_words(u64 L, u64 N) { return (u64)kRowGroups * 6 * L * N; }
+u64 dnq_words(u64 L, u64 N) { return (u64)kRowGroups * (L + 2) * L * N; }
 
 int ensure_scratch(cwpir_ctx *c) {
   if (c->jmax) return CWPIR_OK;
   const u64 N = c->N, L = c->L;
-  const u64 per_job = (3 * c->qp_poly() + (3 * L + 2 * L + (L + 2) * L) * N) * sizeof(u64);
+  const u64 per_job =
+      (3 * c->qp_poly() + (3 * L + 2 * L) * N + dn_words(L, N)) * sizeof(u64);
   u64 j = kScratchBytes / per_job;
   j = std::max<u64>(32, std::min<u64>(kMaxJobs, j));
   if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
@@ -296,7 +315,10 @@ int ensure_scratch(cwpir_ctx *c) {
   CUDA_TRY(c, c->Tbuf.ensure(j * 3 * c->qp_poly()));
   CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
   CUDA_TRY(c, c->CP.ensure(j * 2 * L * N));
-  CUDA_TRY(c, c->DN.ensure(j * (L + 2) * L * N));
+  CUDA_TRY(c, c->DN.ensure(j * dn_words(L, N)));
+  CUDA_TRY(c, c->RS.ensure(rs_words(L, N)));
+  CUDA_TRY(c, c->DNQ.ensure(dnq_words(L, N)));
+  CUDA_TRY(c, c->one_job.ensure((sizeof(cw::MulJob) + 7) / 8));
   if (!c->d_err) {
     CUDA_TRY(c, cudaMalloc(&c->d_err, sizeof(int)));
     CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
@@ -388,6 +410,7 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
   P->memo = memo_opt && P->top >= 2;
   P->h_in = db->folklore ? m / 2 : cfac ? (m + (1u << cfac) - 1) >> cfac : m;
   P->sp = db->sp;
+  P->rows_db = db->rows;
   if (db->folklore) CUDA_TRY(c, P->leaves_coef.ensure((u64)nq * m * ctw));
   const u32 J = c->jmax;
   if (root_mode == cw::ROOT_PM && (u64)nq * db->sp > J)
@@ -522,13 +545,33 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
   }
   CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, c->Tbuf.p, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
+  const bool rows = ch.mode == cw::ROOT_PM && P->rows_db;
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
+    if (rows)
+      return cw::launch_relin_rows(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, c->rlk.p,
+                                   c->rlk_s.p, reinterpret_cast<const u32 *>(dbp), kRowGroups,
+                                   reinterpret_cast<u32 *>(c->DN.p),
+                                   reinterpret_cast<u32 *>(c->RS.p), c->DNQ.p, c->d_err,
+                                   c->CP.p, st);
     return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
                             c->rlk_s.p, dbp, P->sp, c->jmax, c->DN.p, c->SEL.p, c->CP.p, st);
   }));
-  c->stats.kernel_launches += 4;  // tensor, scale, digit NTTs, key multiply-accumulate
+  c->stats.kernel_launches += 3;  // tensor (ciphertext and extension limbs), scale-down
   c->stats.mults += ch.count;
-  c->stats.ntt_polys += (u64)ch.count * (3 * (c->L + c->K) + c->L * (c->L + 2));
+  c->stats.ntt_polys += (u64)ch.count * 3 * (c->L + c->K);
+  if (rows) {
+    const u32 seg_len = ch.count / ch.segs;
+    const u32 G = cw::relin_pm_groups(c->h, ch.segs, seg_len, 1, kRowGroups);
+    const u32 spp = G >= kRowGroups ? 1 : kRowGroups / G, passes = (ch.segs + spp - 1) / spp;
+    // row transforms; per pass: row sums, inverse NTT, CRT, NTT, key products
+    c->stats.kernel_launches += 1 + 5ull * passes;
+    c->stats.ntt_polys += (u64)ch.count * 3 * c->L * cw::kRowPrimes;
+  } else {
+    // digit NTTs, key multiply-accumulate (and, for rows of several
+    // plaintexts, their products)
+    c->stats.kernel_launches += (ch.mode == cw::ROOT_PM && P->sp > 1) ? 3 : 2;
+    c->stats.ntt_polys += (u64)ch.count * c->L * (c->L + 2);
+  }
   if (ch.mode == cw::INTERNAL) {
     CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, c->CP.p, jobs, ch.count, st); }));
     CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_p(c->d_tab, c->h, jobs, ch.count, st); }));
@@ -536,10 +579,12 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
     c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
   } else if (ch.mode == cw::ROOT_PM) {
     const u32 seg_len = ch.count / ch.segs;
-    const u32 groups = cw::relin_pm_groups(c->h, ch.segs, seg_len, P->sp, c->jmax);
+    const u32 groups =
+        cw::relin_pm_groups(c->h, ch.segs, seg_len, P->sp, rows ? kRowGroups : c->jmax);
     CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, groups, P->sp, P->acc.p, st); }));
     c->stats.kernel_launches += 1;
-    c->stats.db_bytes_read += (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
+    c->stats.db_bytes_read += rows ? (u64)ch.count * cw::kRowPrimes * c->N * sizeof(u32)
+                                   : (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
   } else {
     c->stats.kernel_launches += 1;  // inverse NTT
     c->stats.ntt_polys += (u64)ch.count * 2 * c->L;
@@ -622,7 +667,7 @@ int check_err_flag(cwpir_ctx *c) {
   CUDA_TRY(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
     CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
-    return fail(c, CWPIR_EINTERNAL, "device consistency check failed (scale-down rounding)");
+    return fail(c, CWPIR_EINTERNAL, "device consistency check failed (scale-down or row-basis rounding)");
   }
   return CWPIR_OK;
 }
@@ -945,7 +990,9 @@ static int load_db_impl(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uin
         seen.emplace(((u32)codewords[i * k + 2 * r] << 16) | codewords[i * k + 2 * r + 1], 0);
     db->n_pairs = seen.size();
   }
-  const u64 row_words = (u64)db->sp * c->L * c->N;
+  db->rows = db->sp == 1 && k >= 2;
+  // u64 words per row: [4][N] u32 in the row basis, [sp][L][N] otherwise
+  const u64 row_words = db->rows ? (u64)cw::kRowPrimes * c->N / 2 : (u64)db->sp * c->L * c->N;
   CUDA_TRY(c, db->db.ensure(n * row_words));
   // upload rows in chunks and transform
   const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));
@@ -958,8 +1005,12 @@ static int load_db_impl(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uin
     if (plen) {
       cudaError_t e = cudaMemcpyAsync(d_items, items + r0 * plen, nr * plen * sizeof(uint32_t),
                                       cudaMemcpyHostToDevice, c->stream);
-      if (e == cudaSuccess) e = cw::launch_db_load(c->d_tab, c->h, d_items, nr, plen, db->sp,
-                                                   db->db.p + r0 * row_words, c->stream);
+      if (e == cudaSuccess)
+        e = db->rows ? cw::launch_db_load_rows(c->d_tab, c->h, d_items, nr, plen,
+                                               reinterpret_cast<u32 *>(db->db.p + r0 * row_words),
+                                               c->stream)
+                     : cw::launch_db_load(c->d_tab, c->h, d_items, nr, plen, db->sp,
+                                          db->db.p + r0 * row_words, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) {
         cudaFree(d_items);
@@ -1360,6 +1411,21 @@ int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *c
   CUDA_TRY(c, c->io_out.ensure(sp * ctw));
   CUDA_TRY(c, c->tmp_ct.ensure(ctw));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, ct, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
+  if (db->rows) {  // the exact integer product in the row basis, back to each q_j
+    int rc = ensure_scratch(c);
+    if (rc) return rc;
+    const cw::MulJob job{nullptr, nullptr, nullptr, row};
+    CUDA_TRY(c, cudaMemcpyAsync(c->one_job.p, &job, sizeof job, cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cw::launch_plain_mul_rows(
+                    c->d_tab, c->h, c->io_in.p, reinterpret_cast<const cw::MulJob *>(c->one_job.p),
+                    reinterpret_cast<const u32 *>(db->db.p), reinterpret_cast<u32 *>(c->DN.p),
+                    reinterpret_cast<u32 *>(c->RS.p), c->d_err, c->io_out.p, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_err_flag(c);
+  }
   CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, c->tmp_ct.p, 2, LN, 0, c->L, false, c->io_in.p, LN,
                              c->stream));
   for (u64 p = 0; p < sp; ++p)
@@ -1409,10 +1475,10 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
   const u64 N = c->N, L = c->L, qp = c->qp_ct(), ctw = c->ct();
   u64 w = 0;
   if (!c->jmax) {  // the context's scratch comes first
-    const u64 per_job = 3 * c->qp_poly() + (3 * L + 2 * L + (L + 2) * L) * N;
+    const u64 per_job = 3 * c->qp_poly() + (3 * L + 2 * L) * N + dn_words(L, N);
     u64 j = std::max<u64>(32, std::min<u64>(kMaxJobs, kScratchBytes / (per_job * 8)));
     if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
-    w += j * per_job;
+    w += j * per_job + rs_words(L, N) + dnq_words(L, N);
   }
   const u64 J = c->jmax ? c->jmax : kMaxJobs;
   const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();

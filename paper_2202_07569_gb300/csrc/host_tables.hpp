@@ -231,5 +231,26 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
   }
 }
 
+// Row-basis constants (see RowTab in arith.cuh): r = the first four
+// extension primes, N the transform length.
+inline void fill_rows(cw::RowTab &T, const std::vector<u64> &q, const std::vector<u64> &p,
+                      u64 N) {
+  memset(&T, 0, sizeof T);
+  std::vector<u64> r(p.begin(), p.begin() + cw::kRowPrimes);
+  for (int k = 0; k < cw::kRowPrimes; ++k) {
+    const u64 rk = r[k];
+    T.r[k] = ext_prime(rk);
+    T.theta[k] = (u32)hmul(hinv(hat_mod(r, k, rk), rk), hinv(N % rk, rk), rk);
+    T.rw58[k] = (u32)((1ull << 58) / rk);
+    for (u32 j = 0; j < q.size(); ++j) split27(hat_mod(r, k, q[j]), T.hat2[k][j]);
+  }
+  for (u32 j = 0; j < q.size(); ++j) {
+    const u64 Rm = prod_mod(r, q[j]);
+    split27(Rm ? q[j] - Rm : 0, T.negr2[j]);
+    T.q[j] = q[j];
+    T.q_mu[j] = (u64)(((u128)1 << 116) / q[j]);
+  }
+}
+
 }  // namespace host
 }  // namespace cw

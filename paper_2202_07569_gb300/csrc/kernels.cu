@@ -605,6 +605,136 @@ __global__ void k_pm_rows(const DevTables *T, const u64 *S, u32 seg_len, u32 G, 
   }
 }
 
+// ---------------------------------------------------------------------
+// Row basis (RowTab in arith.cuh): the database rows and the last tree
+// level's key-switch inputs multiply exactly as integers modulo the first
+// four extension primes r_k, on 32-bit words.
+// ---------------------------------------------------------------------
+// Database load: row `row`, prime k: centered lift of the payload (at most
+// N coefficients, zero-padded), forward NTT into dbr[row][k][N].
+// grid (4, rows).
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+    k_db_load_rows(const DevTables *T, const u32 *items, u32 plen, u32 *dbr) {
+  extern __shared__ u32 s32[];
+  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  const u32 k = blockIdx.x, t = threadIdx.x;
+  const u64 row = blockIdx.y;
+  const ExtNtt E = T->ext[k];
+  const u32 tt = (u32)T->t, p = E.e.p;
+  NttRegs32<LOGN> x;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) {
+    const u32 c = strided_idx<LOGN>(t, r);
+    const u32 v = c < plen ? items[row * plen + c] : 0;
+    x[r] = v > tt / 2 ? p - (tt - v) : v;
+  }
+  ntt_fwd32<LOGN>(x, s32, E);
+  u32 *out = dbr + (row * kRowPrimes + k) * N;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+}
+
+// Limb l of unit u of E ([units][nl][N] u64, residues below 2^54) reduced
+// modulo r_k and transformed: D[u][l][k][N] u32.  grid (4, nl, units).
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+    k_rows_ntt(const DevTables *T, const u64 *Ein, u32 nl, u32 *D) {
+  extern __shared__ u32 s32[];
+  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+  const u64 u = blockIdx.z;
+  const ExtNtt E = T->ext[k];
+  const u64 *in = Ein + (u * nl + l) * N;
+  NttRegs32<LOGN> x;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext(in[strided_idx<LOGN>(t, r)], E.e);
+  ntt_fwd32<LOGN>(x, s32, E);
+  u32 *out = D + ((u * nl + l) * kRowPrimes + k) * N;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+}
+
+// Row sums: block z = s*G + g sums D[job][l][k] * dbr[row][k] over the jobs
+// g, g+G, ... of segment seg0 + s, for every limb l < NL, modulo r_k, into
+// S[s*G + g][NL][4][N].  Products of residues below 2^30 are below 2^60,
+// so fifteen of them and a folded residue fit 64 bits.  grid (N/256, 4,
+// nseg * G).
+template <int NL>
+__global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_len, u32 G,
+                           const MulJob *jobs, const u32 *dbr, u32 *S) {
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  const u32 sg = blockIdx.z, seg = seg0 + sg / G, g = sg % G;
+  const ExtPrime E = T->ext[k].e;
+  const u64 kN = (u64)kRowPrimes * N;
+  u64 acc[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) acc[l] = 0;
+  u32 terms = 0;
+  u64 job = (u64)seg * seg_len + g;
+  u64 row = g < seg_len ? jobs[job].row : 0;
+  for (u32 x = g; x < seg_len; x += G, job += G) {
+    const u64 m = dbr[row * kN + (u64)k * N + c];
+    if (x + G < seg_len) row = jobs[job + G].row;
+    const u32 *d = D + job * NL * kN + (u64)k * N + c;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) acc[l] += d[l * kN] * m;
+    if (++terms == 15) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l) acc[l] = reduce_ext(acc[l], E);
+      terms = 1;  // the folded residue counts as one term
+    }
+  }
+  u32 *o = S + (u64)sg * NL * kN + (u64)k * N + c;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) o[l * kN] = reduce_ext(acc[l], E);
+}
+
+// Inverse transform (without N^-1) of S[u][l][k] in place: coefficient
+// order, values N x mod r_k below 2r_k.  grid (4, nl, units).
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+    k_rows_intt(const DevTables *T, u32 *S, u32 nl) {
+  extern __shared__ u32 s32[];
+  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+  const u64 u = blockIdx.z;
+  const ExtNtt E = T->ext[k];
+  u32 *p = S + ((u * nl + l) * kRowPrimes + k) * N;
+  NttRegs32<LOGN> x;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) x[r] = p[ntt_pos<LOGN>(t, r)];
+  ntt_inv32<LOGN>(x, s32, E);  // contains barriers: all loads precede all stores
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) p[strided_idx<LOGN>(t, r)] = x[r];
+}
+
+// Row sums back to the ciphertext primes (row_digits, row_to_q): limb
+// l < 2L (e0 and e1, or the two polynomials of a plain product) goes to
+// Eo[u][l] modulo q_{l mod L}; limb l >= 2L (digit i = l - 2L of e2) to
+// Do[u][i][j] for every j < L.  Eo, Do: [.][N] u64 rows with unit strides.
+// grid (N/256, nl, units).
+template <int L>
+__global__ void k_rows_crt(const DevTables *T, const u32 *S, u32 nl, u64 *Eo, u64 eo_stride,
+                           u64 *Do, u64 do_stride, int *err, const __grid_constant__ RowTab RT) {
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, l = blockIdx.y;
+  const u64 u = blockIdx.z;
+  const u32 *src = S + (u * nl + l) * kRowPrimes * N + c;
+  u32 xr[kRowPrimes], y[kRowPrimes];
+#pragma unroll
+  for (int k = 0; k < kRowPrimes; ++k) xr[k] = src[(u64)k * N];
+  bool far;
+  const u64 rho = row_digits(xr, y, RT, &far);
+  if (far) atomicOr(err, 2);
+  if (l < 2 * L) {
+    Eo[u * eo_stride + (u64)l * N + c] = row_to_q(y, rho, (int)(l % L), RT);
+  } else {
+    u64 *o = Do + u * do_stride + (u64)(l - 2 * L) * L * N + c;
+#pragma unroll
+    for (int j = 0; j < L; ++j) o[(u64)j * N] = row_to_q(y, rho, j, RT);
+  }
+}
+
 // (B) producing the NTT-form result: INTERNAL mode writes it to the Q
 // limbs of jobs[job].dst (QP layout), other modes to O[job][2][L][N].
 // grid (N/256, L, njobs).
@@ -1034,6 +1164,113 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
 
 u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) {
   return pm_groups(h, segs, seg_len, sp, cap);
+}
+
+// ---- row basis ----
+template <int LOGN>
+constexpr size_t smem32_bytes() {
+  return (size_t)((1u << LOGN) + ((1u << LOGN) >> NttShape<LOGN>::RB)) * sizeof(u32);
+}
+
+#define CW_DISPATCH_NL(NL_, GRID, BLOCK, STREAM, ...)                                  \
+  switch (NL_) {                                                                       \
+    case 2: k_rows_mac<2><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
+    case 3: k_rows_mac<3><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
+    case 4: k_rows_mac<4><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
+    case 6: k_rows_mac<6><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
+    case 8: k_rows_mac<8><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
+    case 9: k_rows_mac<9><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
+    case 10: k_rows_mac<10><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 12: k_rows_mac<12><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 14: k_rows_mac<14><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 15: k_rows_mac<15><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 16: k_rows_mac<16><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 18: k_rows_mac<18><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 21: k_rows_mac<21><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    case 24: k_rows_mac<24><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
+    default: return cudaErrorInvalidValue;                                            \
+  }
+
+cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u32 *items,
+                                u64 rows, u32 plen, u32 *dbr, cudaStream_t st) {
+  const u64 chunk = 32768;
+  for (u64 r0 = 0; r0 < rows; r0 += chunk) {
+    const u64 nr = rows - r0 < chunk ? rows - r0 : chunk;
+    CW_DISPATCH_LOGN(h.logN, {
+      cudaError_t e = allow_smem(k_db_load_rows<LG>, smem32_bytes<LG>());
+      if (e != cudaSuccess) return e;
+      k_db_load_rows<LG><<<dim3(kRowPrimes, (u32)nr), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+          T, items + r0 * plen, plen, dbr + r0 * kRowPrimes * h.N);
+    });
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t rows_ntt(const DevTables *T, const DevTables &h, const u64 *E, u32 nl,
+                            u32 units, u32 *D, cudaStream_t st) {
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_rows_ntt<LG>, smem32_bytes<LG>());
+    if (e != cudaSuccess) return e;
+    k_rows_ntt<LG><<<dim3(kRowPrimes, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+        T, E, nl, D);
+  });
+  return cudaGetLastError();
+}
+
+static cudaError_t rows_intt(const DevTables *T, const DevTables &h, u32 *S, u32 nl, u32 units,
+                             cudaStream_t st) {
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_rows_intt<LG>, smem32_bytes<LG>());
+    if (e != cudaSuccess) return e;
+    k_rows_intt<LG><<<dim3(kRowPrimes, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+        T, S, nl);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
+                              u32 segs, const MulJob *jobs, const u64 *rlk, const u64 *rlk_s,
+                              const u32 *dbr, u32 gcap, u32 *D, u32 *S, u64 *DNQ, int *err,
+                              u64 *out, cudaStream_t st) {
+  if (!njobs) return cudaSuccess;
+  const u32 L = h.L, nl = 3 * L, N = h.N;
+  const u64 LN = (u64)L * N, unit = (u64)(L + 2) * LN;
+  cudaError_t e = rows_ntt(T, h, E, nl, njobs, D, st);
+  if (e != cudaSuccess) return e;
+  const u32 seg_len = njobs / segs, G = pm_groups(h, segs, seg_len, 1, gcap);
+  const u32 spp = G >= gcap ? 1 : gcap / G;  // segments per pass
+  for (u32 s0 = 0; s0 < segs; s0 += spp) {
+    const u32 nseg = segs - s0 < spp ? segs - s0 : spp, units = nseg * G;
+    CW_DISPATCH_NL(nl, dim3(N / 256, kRowPrimes, units), 256, st, T, D, s0, seg_len, G, jobs,
+                   dbr, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rows_intt(T, h, S, nl, units, st)) != cudaSuccess) return e;
+    CW_DISPATCH_L(L, k_rows_crt, dim3(N / 256, nl, units), 256, 0, st, T, S, nl, DNQ + L * LN,
+                  unit, DNQ, unit, err, h.rows);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // digit sums, e0 and e1 sums to NTT form modulo q_j, then the key
+    if ((e = launch_ntt(T, h, DNQ, units * (L + 2), LN, 0, L, false, nullptr, 0, st)) !=
+        cudaSuccess)
+      return e;
+    CW_DISPATCH_L(L, k_ks_mac_out, dim3(N / 256, L, units), 256, 0, st, T, DNQ, 2u, nullptr, 0,
+                  rlk, rlk_s, out + (u64)s0 * G * 2 * LN);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_plain_mul_rows(const DevTables *T, const DevTables &h, const u64 *ct,
+                                  const MulJob *job, const u32 *dbr, u32 *D, u32 *S, int *err,
+                                  u64 *out, cudaStream_t st) {
+  const u32 L = h.L, nl = 2 * L, N = h.N;
+  cudaError_t e = rows_ntt(T, h, ct, nl, 1, D, st);
+  if (e != cudaSuccess) return e;
+  CW_DISPATCH_NL(nl, dim3(N / 256, kRowPrimes, 1), 256, st, T, D, 0u, 1u, 1u, job, dbr, S);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rows_intt(T, h, S, nl, 1, st)) != cudaSuccess) return e;
+  CW_DISPATCH_L(L, k_rows_crt, dim3(N / 256, nl, 1), 256, 0, st, T, S, nl, out,
+                (u64)2 * L * N, (u64 *)nullptr, (u64)0, err, h.rows);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,

@@ -253,6 +253,20 @@ void emu_substitute(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint3
 }  // extern "C"
 
 extern "C" {
+// x mod q_j (j < L) from N x mod the four row primes (lazy below 2r);
+// returns 1 if the fixed-point check tripped.
+int emu_row_crt(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint32_t *xr,
+                uint64_t *out) {
+  Emu E(N, L, q, t);
+  RowTab T;
+  fill_rows(T, E.q, E.p, N);
+  u32 y[kRowPrimes];
+  bool far;
+  const u64 rho = row_digits(xr, y, T, &far);
+  for (u32 j = 0; j < L; ++j) out[j] = row_to_q(y, rho, (int)j, T);
+  return far ? 1 : 0;
+}
+
 // round(t d / Q) mod q_j for one coefficient given by its residues mod the
 // q_j (dq) and the extension primes (dp); returns 0 if the check tripped.
 int emu_scale(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *dq,

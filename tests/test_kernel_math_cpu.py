@@ -113,6 +113,29 @@ def test_exact_scale_down(orc, N, L):
         assert [int(v) for v in out] == [want % v for v in q], d
 
 
+@pytest.mark.parametrize("N,L", [(1024, 1), (8192, 4), (16384, 7), (16384, 8)])
+def test_row_basis_crt(orc, N, L):
+    """Sums of row products, |x| <= 2^98, recovered modulo the ciphertext
+    primes from N x modulo the four row primes (the first four extension
+    primes), including the extremes and lazy residues below 2r."""
+    q = [int(v) for v in orc.primes(N, L)]
+    r = _ext_primes(N, L, q)[:4]
+    R = math.prod(r)
+    xmax = 1 << 98
+    assert xmax * (1 << 21) <= R
+    xs = [0, 1, -1, xmax, -xmax, xmax - 77, -(xmax // 3)]
+    st = syn.Stream(11, N + L)
+    for w in st.words(12).tolist():
+        xs.append((int(w) * xmax) >> 64)
+        xs.append(-((int(w) * xmax) >> 63))
+    for i, x in enumerate(xs):
+        xr = np.array([(N * x) % rk + (rk if (i + k) % 3 == 0 else 0)
+                       for k, rk in enumerate(r)], np.uint32)
+        out = np.zeros(L, np.uint64)
+        assert emu.lib().emu_row_crt(N, L, np.array(q, np.uint64), T, xr, out) == 0
+        assert [int(v) for v in out] == [x % qq for qq in q], x
+
+
 def test_emulated_substitution_matches_oracle(orc):
     N, L = 1024, 3
     q, O, cd, rlk = _setup(orc, N, L)
