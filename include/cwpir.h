@@ -273,7 +273,12 @@ enum {
   /* multiplications per kernel launch (0 = automatic, at most 2048); sizes
    * the context's scratch: setting it waits for the device, frees the
    * scratch and the answer plans, which the next call rebuilds */
-  CWPIR_OPT_MAX_JOBS = 5
+  CWPIR_OPT_MAX_JOBS = 5,
+  /* 1 (default): databases loaded afterwards with one plaintext per row and
+   * k >= 2 are held in the four-prime row basis (see cwpir_load_db); 0:
+   * modulo the ciphertext primes.  The response bits are identical either
+   * way; already loaded databases keep their form. */
+  CWPIR_OPT_ROW_BASIS = 6
 };
 int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
 

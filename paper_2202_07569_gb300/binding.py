@@ -26,6 +26,7 @@ OPT_BATCH_ROWS = 2
 OPT_USE_GRAPH = 3
 OPT_KERNEL_TIMING = 4
 OPT_MAX_JOBS = 5
+OPT_ROW_BASIS = 6
 K_CLASSES = 7
 
 

@@ -134,6 +134,7 @@ struct cwpir_ctx {
   int opt_share = 1, opt_graph = 0;
   u32 opt_batch_rows = 0;
   u32 opt_max_jobs = 0;
+  int opt_row_basis = 1;
   cudaStream_t stream = nullptr;
   // scratch
   u32 jmax = 0;
@@ -990,7 +991,7 @@ static int load_db_impl(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uin
         seen.emplace(((u32)codewords[i * k + 2 * r] << 16) | codewords[i * k + 2 * r + 1], 0);
     db->n_pairs = seen.size();
   }
-  db->rows = db->sp == 1 && k >= 2;
+  db->rows = c->opt_row_basis && db->sp == 1 && k >= 2;
   // u64 words per row: [4][N] u32 in the row basis, [sp][L][N] otherwise
   const u64 row_words = db->rows ? (u64)cw::kRowPrimes * c->N / 2 : (u64)db->sp * c->L * c->N;
   CUDA_TRY(c, db->db.ensure(n * row_words));
@@ -1540,6 +1541,7 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
       c->opt_graph = value ? 1 : 0;
       return CWPIR_OK;
     case CWPIR_OPT_KERNEL_TIMING: c->opt_timing = value ? 1 : 0; return CWPIR_OK;
+    case CWPIR_OPT_ROW_BASIS: c->opt_row_basis = value ? 1 : 0; return CWPIR_OK;
     case CWPIR_OPT_MAX_JOBS:
       if (value < 0 || value > (int64_t)kMaxJobs)
         return fail(c, CWPIR_EINVAL, "max jobs must be in [0, %llu]", (unsigned long long)kMaxJobs);

@@ -176,6 +176,42 @@ def test_c2_params_answer_bit_exact(share, batch):
     ctx.free_db(db)
 
 
+@pytest.mark.parametrize("N,L,n,k,m,nq", [(4096, 2, 61, 2, 12, 1), (8192, 4, 100, 4, 9, 3),
+                                           (16384, 3, 40, 3, 8, 2)])
+def test_row_basis_equals_ciphertext_basis(N, L, n, k, m, nq):
+    """Databases of one plaintext per row answered through the four-prime
+    row basis (default) and modulo the ciphertext primes
+    (CWPIR_OPT_ROW_BASIS = 0) give the same bits: single and batched
+    answers, plain multiplications, and the oracle's answer."""
+    from paper_2202_07569_gb300 import binding as B
+
+    cl = Client(N, L, seed=300 + L)
+    ctx = cl.context()
+    items, cw, _ = database(n, N, T if N == 4096 else 1 << 16, k, m, seed=310 + L)
+    dbs = []
+    for rb in (1, 0):
+        ctx.set_option(B.OPT_ROW_BASIS, rb)
+        dbs.append(ctx.load_db(items, cw, m))
+    ctx.set_option(B.OPT_ROW_BASIS, 1)
+    targets = [n - 1 - 7 * i for i in range(nq)]
+    queries = np.stack([cl.query(cw[r], m, 0, stream=40 + i) for i, r in enumerate(targets)])
+    want = [cl.O.answer(items, cw, m, queries[i], cl.rlk) for i in range(nq)]
+    for db in dbs:
+        for i in range(nq):
+            assert np.array_equal(ctx.answer(db, queries[i]), want[i])
+        got = ctx.answer_batch(db, queries)
+        for i in range(nq):
+            assert np.array_equal(got[i], want[i])
+    ct = syn.uniform_residues(syn.Stream(320), cl.q, (2,), N)
+    for row in (0, n - 1):
+        pm = cl.O.plain_mul(ct, items[row])
+        for db in dbs:
+            assert np.array_equal(ctx.plain_mul(db, row, ct), pm)
+    mu, budget = cl.decrypt(want[0])
+    assert np.array_equal(mu, items[targets[0]]) and budget > 0
+    ctx.close()
+
+
 def _sparse_rows(n, count, seed):
     rows = syn.Stream(seed, 9).below(n, 4 * count)
     return np.array(sorted(set(rows.tolist())))[:count]
