@@ -149,9 +149,11 @@ def imad_per_job(kind: str) -> float:
 # traffic grows in proportion to the jobs of a launch, so a full launch's
 # traffic is this figure times its jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor_intt": (33144064 + 45691136 + 37215488 + 55372032) / 128,
-    "scale": (213961472 + 72368128) / 128,
-    "relin_pm": (187631616 + 153526528 + 239120896 + 13793792) / 128,
+    "tensor_intt": (45717760 + 47470592 + 37217536 + 55555072) / 128,
+    "scale": (213959680 + 71992832) / 128,
+    # per-job kernels of the row-basis key switch (k_rows_ntt, k_rows_mac);
+    # the once-per-row-group conversions are left out
+    "relin_pm": (100992000 + 144530432 + 218128896 + 38547712) / 128,
 }
 
 
