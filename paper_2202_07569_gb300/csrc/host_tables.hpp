@@ -125,6 +125,8 @@ inline cw::ExtPrime ext_prime(u64 p) {
   E.p = (u32)p;
   E.mu60 = (u32)((1ull << 60) / p);
   E.mu64 = (u64)(((u128)1 << 64) / p);
+  E.c32 = (u32)((1ull << 32) % p);
+  E.mu61 = (u32)((1ull << 61) / p);
   return E;
 }
 

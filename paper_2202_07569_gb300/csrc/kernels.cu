@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
   const u64 *in = Ein + (u * nl + l) * N;
   NttRegs32<LOGN> x;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext(in[strided_idx<LOGN>(t, r)], E.e);
+  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62(in[strided_idx<LOGN>(t, r)], E.e);
   ntt_fwd32<LOGN>(x, s32, E);
   u32 *out = D + ((u * nl + l) * kRowPrimes + k) * N;
 #pragma unroll

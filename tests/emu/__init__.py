@@ -37,6 +37,9 @@ def lib():
     l.emu_row_crt.argtypes = [U32, U32, u64p, U64,
                               np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), u64p]
     l.emu_row_crt.restype = C.c_int
+    l.emu_reduce62.argtypes = [U64, u64p, U64,
+                               np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")]
+    l.emu_reduce62.restype = None
     l.emu_substitute.argtypes = [U32, U32, u64p, U64, U32, u64p, u64p, u64p]
     l.emu_substitute.restype = None
     l.emu_scale.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p]

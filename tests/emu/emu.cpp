@@ -253,6 +253,12 @@ void emu_substitute(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint3
 }  // extern "C"
 
 extern "C" {
+// reduce_ext62 on `count` values below 2^62 for the 30-bit prime p.
+void emu_reduce62(uint64_t p, const uint64_t *v, uint64_t count, uint32_t *out) {
+  const ExtPrime E = ext_prime(p);
+  for (uint64_t i = 0; i < count; ++i) out[i] = reduce_ext62(v[i], E);
+}
+
 // x mod q_j (j < L) from N x mod the four row primes (lazy below 2r);
 // returns 1 if the fixed-point check tripped.
 int emu_row_crt(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint32_t *xr,

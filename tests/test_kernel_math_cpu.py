@@ -113,6 +113,21 @@ def test_exact_scale_down(orc, N, L):
         assert [int(v) for v in out] == [want % v for v in q], d
 
 
+def test_reduction_below_2_62(orc):
+    """The 32-bit reduction of sums below 2^62 modulo a 30-bit extension
+    prime: values at 0, 2^62 - 1, next to multiples of p and of 2^32, and
+    random ones, against Python integers."""
+    for N, L in ((1024, 1), (16384, 8)):
+        for p in _ext_primes(N, L, [int(v) for v in orc.primes(N, L)]):
+            vals = [0, 1, p - 1, p, p + 1, (1 << 32) - 1, 1 << 32, (1 << 62) - 1,
+                    ((1 << 62) // p) * p, ((1 << 62) // p) * p - 1, (1 << 61) + 12345]
+            vals += [int(w) >> 2 for w in syn.Stream(12, p % 1000).words(64).tolist()]
+            v = np.array(vals, np.uint64)
+            out = np.zeros(len(vals), np.uint32)
+            emu.lib().emu_reduce62(p, v, len(vals), out)
+            assert [int(x) for x in out] == [x % p for x in vals]
+
+
 @pytest.mark.parametrize("N,L", [(1024, 1), (8192, 4), (16384, 7), (16384, 8)])
 def test_row_basis_crt(orc, N, L):
     """Sums of row products, |x| <= 2^98, recovered modulo the ciphertext
