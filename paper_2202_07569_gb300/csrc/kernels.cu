@@ -266,8 +266,9 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 
 // ---------------------------------------------------------------------
 // Centered Q -> P conversion of coefficient-form polynomials.
-// unit u: src + u*src_stride ([L][N]) -> dst + u*dst_stride ([L+K][N], P
-// limbs written; Q limbs copied when copy_q).  grid (N/256, units).
+// unit u: src + u*src_stride ([L][N]) -> dst + u*dst_stride (a polynomial
+// in QP layout: P limbs written; Q limbs copied when copy_q).
+// grid (N/256, units).
 // ---------------------------------------------------------------------
 // The conversion tables are passed by value (__grid_constant__): they sit
 // in the constant bank and the integer multiplies read them as operands.
