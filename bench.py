@@ -129,11 +129,12 @@ def imad_per_job(kind: str) -> float:
     m54, m30 = IMAD_PER_MODMUL54, IMAD_PER_MODMUL30
     if kind == "tensor_intt":  # 3 outputs x (L + K) limbs: 4 products + inverse transform
         return 3 * (L * bf * m54 + K * bf * m30) + 4 * N * (L * m54 + K * m30)
-    if kind == "relin_pm":  # row basis: 3L limbs x 4 primes, each reduced (one 64-bit
-        # high product, counted as 5) and transformed on 32-bit words, and one
-        # 32 x 32-bit product with the row per coefficient; the per-group
-        # conversions and key products are left out
-        return 3 * L * 4 * (bf * m30 + 5 * N + N)
+    if kind == "relin_pm":  # row basis of 3 primes (t = 65537, N = 8192): 3L limbs x 3
+        # primes, each reduced (a 32-bit fold and Barrett step, counted as 3)
+        # and transformed on 32-bit words, and one 32 x 32-bit product with
+        # the row per coefficient; the per-group conversions and key products
+        # are left out
+        return 3 * L * 3 * (bf * m30 + 3 * N + N)
     if kind == "scale":  # per coefficient of 3 polynomials
         per = (m54 * L + K * (2 * L + 2) + m54 * K   # y_j, first stage and its reductions
                + L * (2 * K + 2) + m54 * L)          # second stage and its reductions

@@ -131,9 +131,10 @@ void cwpir_destroy(cwpir_ctx *ctx);
  * selection vector with each plaintext column (Sec. 3.3.3).  For index PIR the codeword of row i is the perfect mapping of
  * i; for keyword PIR (Sec. 3.3.6) the mapping of the row's keyword.  The
  * rows are lifted to centered integers and kept in HBM in NTT form: rows of
- * one plaintext with k >= 2 modulo four internal 30-bit primes (16 bytes a
- * coefficient; the answer multiplies them exactly as integers), otherwise
- * modulo the ciphertext primes (8 L bytes a coefficient and plaintext).
+ * one plaintext with k >= 2 modulo three (four for a large t) internal
+ * 30-bit primes (12 or 16 bytes a coefficient; the answer multiplies them
+ * exactly as integers), otherwise modulo the ciphertext primes (8 L bytes a
+ * coefficient and plaintext).
  * 1 <= k <= 16, k <= m <= 16384, 1 <= n <= 2^24.  *db_id receives a handle.
  * EINVAL (including a coefficient >= t or a bad codeword), ENOMEM, ECUDA. */
 int cwpir_load_db(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len, uint32_t k,
@@ -275,7 +276,7 @@ enum {
    * scratch and the answer plans, which the next call rebuilds */
   CWPIR_OPT_MAX_JOBS = 5,
   /* 1 (default): databases loaded afterwards with one plaintext per row and
-   * k >= 2 are held in the four-prime row basis (see cwpir_load_db); 0:
+   * k >= 2 are held in the row basis of internal primes (cwpir_load_db); 0:
    * modulo the ciphertext primes.  The response bits are identical either
    * way; already loaded databases keep their form. */
   CWPIR_OPT_ROW_BASIS = 6

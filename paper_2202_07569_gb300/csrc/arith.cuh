@@ -351,24 +351,26 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
 }
 
 // ---------------------------------------------------------------------
-// Exact products with database rows in a four-prime "row basis".
+// Exact products with database rows in a "row basis" of nr = 3 or 4 primes.
 //
-// The plaintext rows are small integers (|v| <= t/2 after the centered
+// The plaintext rows are small integers (|v| <= (t-1)/2 after the centered
 // lift), and the inputs of the last tree level's key switch (the limbs of
-// e0, e1 and the digits of e2) are residues below 2^54.  A sum over at most
-// 2048 rows of their negacyclic products with rows is therefore an integer
-// x with |x| <= 2^11 N 2^54 2^19 <= 2^98 (N <= 2^14, t < 2^20), exactly
-// representable by its residues modulo the first four 30-bit extension
-// primes r_k (product R > 2^119.9): |x| / R < 2^-21.  row_crt recovers x
-// modulo the ciphertext primes from N x mod r_k (the inverse transforms
+// e0, e1 and the digits of e2) are residues below the largest ciphertext
+// prime.  A sum over a group of rows of their negacyclic products with the
+// rows is an integer x with |x| <= rows N q_max (t-1)/2; the library keeps
+// the rows per group low enough that |x| < (1 - 2^-23) R/2 (R the product
+// of the first nr extension primes), so the residues modulo the r_k hold x
+// exactly.  row_digits recovers x from N x mod r_k (the inverse transforms
 // leave the factor N): y_k = [(N x)_k (R/r_k)^-1 N^-1]_{r_k},
-// x = sum_k y_k (R/r_k) - rho R with rho = round(sum_k y_k / r_k), and
-// sum_k y_k / r_k lies within 2^-21 of rho, so a 6.58 fixed-point sum
-// rounds to it exactly (as in scale_coeff).
+// x = sum_k y_k (R/r_k) - rho R with rho = round(sum_k y_k / r_k); the sum
+// is at least 2^-24 away from a half integer, and a 6.58 fixed-point sum of
+// y_k floor(2^58 / r_k), low by less than nr 2^-28, rounds to rho exactly.
 // ---------------------------------------------------------------------
-constexpr int kRowPrimes = 4;
+constexpr int kRowPrimes = 4;  // at most
 
 struct RowTab {
+  u32 nr;                             // row primes in use: 3 or 4
+  u32 rmax;                           // rows per group the basis holds exactly
   ExtPrime r[kRowPrimes];
   u32 theta[kRowPrimes];              // (R/r_k)^-1 N^-1 mod r_k
   u32 rw58[kRowPrimes];               // floor(2^58 / r_k)
@@ -377,27 +379,29 @@ struct RowTab {
   u64 q[kMaxL], q_mu[kMaxL];          // ciphertext primes, floor(2^116 / q_j)
 };
 
-// xr: N x mod r_k, below 2^31 (lazy [0, 2r)); y: the digits y_k; returns
-// rho, and false in *far if the fixed-point sum is 2^-17 or more away from
-// an integer (ruled out by the bound on |x|).
+// xr: N x mod r_k (k < nr), below 2^31 (lazy [0, 2r)); y: the digits y_k;
+// returns rho, and true in *far if the fixed-point sum comes within 2^-25 of
+// a half integer (ruled out by the bound on |x|).
 CW_HD u64 row_digits(const u32 *xr, u32 *y, const RowTab &T, bool *far) {
   u64 fix = 0;
   for (int k = 0; k < kRowPrimes; ++k) {
+    if ((u32)k >= T.nr) break;
     const u32 v = xr[k] >= T.r[k].p ? xr[k] - T.r[k].p : xr[k];
     const u32 m = mulmod_ext_lazy(v, T.theta[k], T.r[k]);
     y[k] = m >= T.r[k].p ? m - T.r[k].p : m;
     fix += (u64)y[k] * T.rw58[k];
   }
   const u64 frac = (fix + (1ull << 57)) & ((1ull << 58) - 1);
-  *far = frac < (1ull << 57) - (1ull << 41) || frac > (1ull << 57) + (1ull << 41);
+  *far = frac < (1ull << 33) || frac > (1ull << 58) - (1ull << 33);
   return (fix + (1ull << 57)) >> 58;
 }
 
-// x mod q_j from the digits: sum_k y_k (R/r_k) - rho R (five products of
-// values below 2^30 with 27-bit halves, sum below 2^88).
+// x mod q_j from the digits: sum_k y_k (R/r_k) - rho R (at most five
+// products of values below 2^30 with 27-bit halves, sum below 2^88).
 CW_HD u64 row_to_q(const u32 *y, u64 rho, int j, const RowTab &T) {
   u64 ll = rho * T.negr2[j][0], x = rho * T.negr2[j][1];
   for (int k = 0; k < kRowPrimes; ++k) {
+    if ((u32)k >= T.nr) break;
     ll += (u64)y[k] * T.hat2[k][j][0];
     x += (u64)y[k] * T.hat2[k][j][1];
   }

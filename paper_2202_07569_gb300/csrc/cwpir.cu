@@ -259,7 +259,12 @@ int build_tables(cwpir_ctx *c) {
                          cudaMemcpyHostToDevice));
   fill_lift(h.lift, c->q, c->p);
   fill_scale(h.scale, c->q, c->p, c->t, N);
-  fill_rows(h.rows, c->q, c->p, N);
+  // row basis: three primes when a group of 32 rows or more fits, else four
+  const u64 lim3 = row_group_limit(c->q, c->p, 3, N, c->t);
+  const u32 nr = lim3 >= 32 ? 3 : 4;
+  fill_rows(h.rows, c->q, c->p, N, nr);
+  h.rows.rmax = (u32)std::min<u64>(row_group_limit(c->q, c->p, nr, N, c->t), 2048);
+  if (h.rows.rmax < 32) return fail(c, CWPIR_EINTERNAL, "row basis too small");
   CUDA_TRY(c, cudaMalloc(&c->d_tab, sizeof(cw::DevTables)));
   CUDA_TRY(c, cudaMemcpy(c->d_tab, &h, sizeof h, cudaMemcpyHostToDevice));
   return CWPIR_OK;
@@ -297,9 +302,9 @@ constexpr u64 kScratchBytes = 8ull << 30;
 constexpr u32 kRowGroups = 64;
 
 // u64 words per job of the digit transforms: (L+2) L N for the ciphertext
-// basis, 3L x 4 x N u32 for the row basis
+// basis, 3L x nr x N u32 for the row basis of nr <= 4 primes
 u64 dn_words(u64 L, u64 N) { return std::max<u64>((L + 2) * L, 6 * L) * N; }
-// u64 words of the row-basis group buffers: row sums [kRowGroups][3L][4][N]
+// u64 words of the row-basis group buffers: row sums [kRowGroups][3L][nr][N]
 // u32 and their Q-basis forms [kRowGroups][L+2][L][N]
 u64 rs_words(u64 L, u64 N) { return (u64)kRowGroups * 6 * L * N; }
 u64 dnq_words(u64 L, u64 N) { return (u64)kRowGroups * (L + 2) * L * N; }
@@ -562,11 +567,11 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
   c->stats.ntt_polys += (u64)ch.count * 3 * (c->L + c->K);
   if (rows) {
     const u32 seg_len = ch.count / ch.segs;
-    const u32 G = cw::relin_pm_groups(c->h, ch.segs, seg_len, 1, kRowGroups);
+    const u32 G = cw::relin_rows_groups(c->h, ch.segs, seg_len, kRowGroups);
     const u32 spp = G >= kRowGroups ? 1 : kRowGroups / G, passes = (ch.segs + spp - 1) / spp;
     // row transforms; per pass: row sums, inverse NTT, CRT, NTT, key products
     c->stats.kernel_launches += 1 + 5ull * passes;
-    c->stats.ntt_polys += (u64)ch.count * 3 * c->L * cw::kRowPrimes;
+    c->stats.ntt_polys += (u64)ch.count * 3 * c->L * c->h.rows.nr;
   } else {
     // digit NTTs, key multiply-accumulate (and, for rows of several
     // plaintexts, their products)
@@ -580,11 +585,11 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
     c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
   } else if (ch.mode == cw::ROOT_PM) {
     const u32 seg_len = ch.count / ch.segs;
-    const u32 groups =
-        cw::relin_pm_groups(c->h, ch.segs, seg_len, P->sp, rows ? kRowGroups : c->jmax);
+    const u32 groups = rows ? cw::relin_rows_groups(c->h, ch.segs, seg_len, kRowGroups)
+                            : cw::relin_pm_groups(c->h, ch.segs, seg_len, P->sp, c->jmax);
     CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, groups, P->sp, P->acc.p, st); }));
     c->stats.kernel_launches += 1;
-    c->stats.db_bytes_read += rows ? (u64)ch.count * cw::kRowPrimes * c->N * sizeof(u32)
+    c->stats.db_bytes_read += rows ? (u64)ch.count * c->h.rows.nr * c->N * sizeof(u32)
                                    : (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
   } else {
     c->stats.kernel_launches += 1;  // inverse NTT
@@ -993,7 +998,7 @@ static int load_db_impl(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uin
   }
   db->rows = c->opt_row_basis && db->sp == 1 && k >= 2;
   // u64 words per row: [4][N] u32 in the row basis, [sp][L][N] otherwise
-  const u64 row_words = db->rows ? (u64)cw::kRowPrimes * c->N / 2 : (u64)db->sp * c->L * c->N;
+  const u64 row_words = db->rows ? (u64)c->h.rows.nr * c->N / 2 : (u64)db->sp * c->L * c->N;
   CUDA_TRY(c, db->db.ensure(n * row_words));
   // upload rows in chunks and transform
   const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));

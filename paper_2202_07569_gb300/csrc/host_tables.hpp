@@ -4,6 +4,7 @@
 // Header-only C++, no CUDA runtime dependency.
 #pragma once
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -233,13 +234,29 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
   }
 }
 
-// Row-basis constants (see RowTab in arith.cuh): r = the first four
+// Largest number of rows per group for which the row basis of the first nr
+// extension primes holds the group sums exactly: rows N q_max (t-1)/2 <=
+// (1 - 2^-23) R/2 (see RowTab in arith.cuh).
+inline u64 row_group_limit(const std::vector<u64> &q, const std::vector<u64> &p, u32 nr,
+                           u64 N, u64 t) {
+  long double lr = 0;
+  for (u32 k = 0; k < nr; ++k) lr += log2l((long double)p[k]);
+  const u64 qmax = *std::max_element(q.begin(), q.end());
+  const long double lim =
+      lr - 1 + log2l(1.0L - 1.0L / (1 << 23)) - log2l((long double)N) -
+      log2l((long double)qmax) - log2l((long double)((t - 1) / 2));
+  if (lim >= 40) return 1ull << 40;
+  return lim < 0 ? 0 : (u64)floorl(exp2l(lim));
+}
+
+// Row-basis constants (see RowTab in arith.cuh): r = the first nr
 // extension primes, N the transform length.
 inline void fill_rows(cw::RowTab &T, const std::vector<u64> &q, const std::vector<u64> &p,
-                      u64 N) {
+                      u64 N, u32 nr) {
   memset(&T, 0, sizeof T);
-  std::vector<u64> r(p.begin(), p.begin() + cw::kRowPrimes);
-  for (int k = 0; k < cw::kRowPrimes; ++k) {
+  T.nr = nr;
+  std::vector<u64> r(p.begin(), p.begin() + nr);
+  for (u32 k = 0; k < nr; ++k) {
     const u64 rk = r[k];
     T.r[k] = ext_prime(rk);
     T.theta[k] = (u32)hmul(hinv(hat_mod(r, k, rk), rk), hinv(N % rk, rk), rk);

@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
     k_db_load_rows(const DevTables *T, const u32 *items, u32 plen, u32 *dbr) {
   extern __shared__ u32 s32[];
   constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
-  const u32 k = blockIdx.x, t = threadIdx.x;
+  const u32 k = blockIdx.x, t = threadIdx.x, nr = T->rows.nr;
   const u64 row = blockIdx.y;
   const ExtNtt E = T->ext[k];
   const u32 tt = (u32)T->t, p = E.e.p;
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
     x[r] = v > tt / 2 ? p - (tt - v) : v;
   }
   ntt_fwd32<LOGN>(x, s32, E);
-  u32 *out = dbr + (row * kRowPrimes + k) * N;
+  u32 *out = dbr + (row * nr + k) * N;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
 }
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
     k_rows_ntt(const DevTables *T, const u64 *Ein, u32 nl, u32 *D) {
   extern __shared__ u32 s32[];
   constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
-  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x, nr = T->rows.nr;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
   const u64 *in = Ein + (u * nl + l) * N;
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
 #pragma unroll
   for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62(in[strided_idx<LOGN>(t, r)], E.e);
   ntt_fwd32<LOGN>(x, s32, E);
-  u32 *out = D + ((u * nl + l) * kRowPrimes + k) * N;
+  u32 *out = D + ((u * nl + l) * nr + k) * N;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
 }
@@ -667,7 +667,7 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
   const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
   const u32 sg = blockIdx.z, seg = seg0 + sg / G, g = sg % G;
   const ExtPrime E = T->ext[k].e;
-  const u64 kN = (u64)kRowPrimes * N;
+  const u64 kN = (u64)T->rows.nr * N;
   u64 acc[NL];
 #pragma unroll
   for (int l = 0; l < NL; ++l) acc[l] = 0;
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
   const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
-  u32 *p = S + ((u * nl + l) * kRowPrimes + k) * N;
+  u32 *p = S + ((u * nl + l) * T->rows.nr + k) * N;
   NttRegs32<LOGN> x;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) x[r] = p[ntt_pos<LOGN>(t, r)];
@@ -720,10 +720,10 @@ __global__ void k_rows_crt(const DevTables *T, const u32 *S, u32 nl, u64 *Eo, u6
                            u64 *Do, u64 do_stride, int *err, const __grid_constant__ RowTab RT) {
   const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, l = blockIdx.y;
   const u64 u = blockIdx.z;
-  const u32 *src = S + (u * nl + l) * kRowPrimes * N + c;
+  const u32 *src = S + (u * nl + l) * RT.nr * N + c;
   u32 xr[kRowPrimes], y[kRowPrimes];
 #pragma unroll
-  for (int k = 0; k < kRowPrimes; ++k) xr[k] = src[(u64)k * N];
+  for (int k = 0; k < kRowPrimes; ++k) xr[k] = (u32)k < RT.nr ? src[(u64)k * N] : 0;
   bool far;
   const u64 rho = row_digits(xr, y, RT, &far);
   if (far) atomicOr(err, 2);
@@ -1168,6 +1168,14 @@ u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) 
 }
 
 // ---- row basis ----
+// Row groups per segment: as for the ciphertext basis (at most gcap / segs),
+// and at least enough that no group sums more rows than the basis holds.
+u32 relin_rows_groups(const DevTables &h, u32 segs, u32 seg_len, u32 gcap) {
+  const u32 g = pm_groups(h, segs, seg_len, 1, gcap);
+  const u32 need = (seg_len + h.rows.rmax - 1) / h.rows.rmax;
+  return g > need ? g : need;
+}
+
 template <int LOGN>
 constexpr size_t smem32_bytes() {
   return (size_t)((1u << LOGN) + ((1u << LOGN) >> NttShape<LOGN>::RB)) * sizeof(u32);
@@ -1200,8 +1208,8 @@ cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u3
     CW_DISPATCH_LOGN(h.logN, {
       cudaError_t e = allow_smem(k_db_load_rows<LG>, smem32_bytes<LG>());
       if (e != cudaSuccess) return e;
-      k_db_load_rows<LG><<<dim3(kRowPrimes, (u32)nr), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
-          T, items + r0 * plen, plen, dbr + r0 * kRowPrimes * h.N);
+      k_db_load_rows<LG><<<dim3(h.rows.nr, (u32)nr), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+          T, items + r0 * plen, plen, dbr + r0 * h.rows.nr * h.N);
     });
   }
   return cudaGetLastError();
@@ -1212,7 +1220,7 @@ static cudaError_t rows_ntt(const DevTables *T, const DevTables &h, const u64 *E
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_rows_ntt<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_rows_ntt<LG><<<dim3(kRowPrimes, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+    k_rows_ntt<LG><<<dim3(h.rows.nr, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
         T, E, nl, D);
   });
   return cudaGetLastError();
@@ -1223,7 +1231,7 @@ static cudaError_t rows_intt(const DevTables *T, const DevTables &h, u32 *S, u32
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_rows_intt<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_rows_intt<LG><<<dim3(kRowPrimes, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+    k_rows_intt<LG><<<dim3(h.rows.nr, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
         T, S, nl);
   });
   return cudaGetLastError();
@@ -1238,11 +1246,11 @@ cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 
   const u64 LN = (u64)L * N, unit = (u64)(L + 2) * LN;
   cudaError_t e = rows_ntt(T, h, E, nl, njobs, D, st);
   if (e != cudaSuccess) return e;
-  const u32 seg_len = njobs / segs, G = pm_groups(h, segs, seg_len, 1, gcap);
+  const u32 seg_len = njobs / segs, G = relin_rows_groups(h, segs, seg_len, gcap);
   const u32 spp = G >= gcap ? 1 : gcap / G;  // segments per pass
   for (u32 s0 = 0; s0 < segs; s0 += spp) {
     const u32 nseg = segs - s0 < spp ? segs - s0 : spp, units = nseg * G;
-    CW_DISPATCH_NL(nl, dim3(N / 256, kRowPrimes, units), 256, st, T, D, s0, seg_len, G, jobs,
+    CW_DISPATCH_NL(nl, dim3(N / 256, h.rows.nr, units), 256, st, T, D, s0, seg_len, G, jobs,
                    dbr, S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = rows_intt(T, h, S, nl, units, st)) != cudaSuccess) return e;
@@ -1266,7 +1274,7 @@ cudaError_t launch_plain_mul_rows(const DevTables *T, const DevTables &h, const 
   const u32 L = h.L, nl = 2 * L, N = h.N;
   cudaError_t e = rows_ntt(T, h, ct, nl, 1, D, st);
   if (e != cudaSuccess) return e;
-  CW_DISPATCH_NL(nl, dim3(N / 256, kRowPrimes, 1), 256, st, T, D, 0u, 1u, 1u, job, dbr, S);
+  CW_DISPATCH_NL(nl, dim3(N / 256, h.rows.nr, 1), 256, st, T, D, 0u, 1u, 1u, job, dbr, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = rows_intt(T, h, S, nl, 1, st)) != cudaSuccess) return e;
   CW_DISPATCH_L(L, k_rows_crt, dim3(N / 256, nl, 1), 256, 0, st, T, S, nl, out,

@@ -23,7 +23,7 @@ struct DevTables {
   ExtNtt ext[kMaxK];      // extension primes p_0..p_{K-1} (30-bit)
   LiftTab lift;           // centered Q -> P conversion (leaves, nodes)
   ScaleTab scale;         // exact round(t d / Q)
-  RowTab rows;            // row basis: first four extension primes -> Q
+  RowTab rows;            // row basis: first nr extension primes -> Q
 };
 
 // QP layout of one polynomial (NTT domain or, for the tensor buffer,
@@ -95,7 +95,8 @@ cudaError_t launch_relin(const DevTables *T, const DevTables &h, const u64 *E, u
 u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap);
 
 // ---- row basis (RowTab): databases of one plaintext per row held as
-// [rows][4][N] u32, NTT form modulo the first four extension primes ----
+// [rows][nr][N] u32, NTT form modulo the first nr extension primes ----
+u32 relin_rows_groups(const DevTables &h, u32 segs, u32 seg_len, u32 gcap);
 cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u32 *items,
                                 u64 rows, u32 plen, u32 *dbr, cudaStream_t st);
 // Relinearisation of the scaled tensor E ([njobs][3][L][N]) with the plain
@@ -104,15 +105,15 @@ cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u3
 // rows exactly in the row basis, summed, brought back to the ciphertext
 // primes and multiplied by the key once per group.  The jobs form `segs`
 // segments (one per query); out = partials [segs * G][2][L][N], NTT form,
-// G = relin_pm_groups(h, segs, njobs / segs, 1, gcap).  Scratch: D
-// [njobs][3L][4][N] u32; S [gcap][3L][4][N] u32; DNQ [gcap][L+2][L][N].
+// G = relin_rows_groups(h, segs, njobs / segs, gcap) <= gcap.  Scratch: D
+// [njobs][3L][nr][N] u32; S [gcap][3L][nr][N] u32; DNQ [gcap][L+2][L][N].
 cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                               u32 segs, const MulJob *jobs, const u64 *rlk, const u64 *rlk_s,
                               const u32 *dbr, u32 gcap, u32 *D, u32 *S, u64 *DNQ, int *err,
                               u64 *out, cudaStream_t st);
 // Plain multiplication of ct ([2][L][N] coefficient form) by row `row` of a
-// row-basis database: out [2][L][N] coefficient form.  D: [2L][4][N] u32,
-// S: [2L][4][N] u32; job: one device MulJob whose row is read.
+// row-basis database: out [2][L][N] coefficient form.  D: [2L][nr][N] u32,
+// S: [2L][nr][N] u32; job: one device MulJob whose row is read.
 cudaError_t launch_plain_mul_rows(const DevTables *T, const DevTables &h, const u64 *ct,
                                   const MulJob *job, const u32 *dbr, u32 *D, u32 *S, int *err,
                                   u64 *out, cudaStream_t st);

@@ -34,8 +34,10 @@ def lib():
     l.emu_ext_primes.restype = None
     l.emu_ext_count.argtypes = [U32]
     l.emu_ext_count.restype = U32
-    l.emu_row_crt.argtypes = [U32, U32, u64p, U64,
+    l.emu_row_crt.argtypes = [U32, U32, u64p, U64, U32,
                               np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), u64p]
+    l.emu_row_limit.argtypes = [U32, U32, u64p, U64, U32]
+    l.emu_row_limit.restype = U64
     l.emu_row_crt.restype = C.c_int
     l.emu_reduce62.argtypes = [U64, u64p, U64,
                                np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")]

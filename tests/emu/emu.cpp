@@ -253,19 +253,25 @@ void emu_substitute(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint3
 }  // extern "C"
 
 extern "C" {
+// Rows per group that the row basis of nr primes holds exactly.
+uint64_t emu_row_limit(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint32_t nr) {
+  Emu E(N, L, q, t);
+  return row_group_limit(E.q, E.p, nr, N, t);
+}
+
 // reduce_ext62 on `count` values below 2^62 for the 30-bit prime p.
 void emu_reduce62(uint64_t p, const uint64_t *v, uint64_t count, uint32_t *out) {
   const ExtPrime E = ext_prime(p);
   for (uint64_t i = 0; i < count; ++i) out[i] = reduce_ext62(v[i], E);
 }
 
-// x mod q_j (j < L) from N x mod the four row primes (lazy below 2r);
+// x mod q_j (j < L) from N x mod the nr row primes (lazy below 2r);
 // returns 1 if the fixed-point check tripped.
-int emu_row_crt(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint32_t *xr,
-                uint64_t *out) {
+int emu_row_crt(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint32_t nr,
+                const uint32_t *xr, uint64_t *out) {
   Emu E(N, L, q, t);
   RowTab T;
-  fill_rows(T, E.q, E.p, N);
+  fill_rows(T, E.q, E.p, N, nr);
   u32 y[kRowPrimes];
   bool far;
   const u64 rho = row_digits(xr, y, T, &far);

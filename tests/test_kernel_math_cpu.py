@@ -128,26 +128,30 @@ def test_reduction_below_2_62(orc):
             assert [int(x) for x in out] == [x % p for x in vals]
 
 
+@pytest.mark.parametrize("nr", [3, 4])
 @pytest.mark.parametrize("N,L", [(1024, 1), (8192, 4), (16384, 7), (16384, 8)])
-def test_row_basis_crt(orc, N, L):
-    """Sums of row products, |x| <= 2^98, recovered modulo the ciphertext
-    primes from N x modulo the four row primes (the first four extension
-    primes), including the extremes and lazy residues below 2r."""
+def test_row_basis_crt(orc, N, L, nr):
+    """Sums of row products recovered modulo the ciphertext primes from N x
+    modulo the nr row primes (the first nr extension primes), for |x| up to
+    the bound that the rows-per-group limit guarantees (rows N q_max (t-1)/2
+    for that many rows), including the extremes and lazy residues below 2r."""
     q = [int(v) for v in orc.primes(N, L)]
-    r = _ext_primes(N, L, q)[:4]
+    r = _ext_primes(N, L, q)[:nr]
     R = math.prod(r)
-    xmax = 1 << 98
-    assert xmax * (1 << 21) <= R
+    rows = int(emu.lib().emu_row_limit(N, L, np.array(q, np.uint64), T, nr))
+    assert rows >= (32 if nr == 3 else 2048)
+    xmax = min(rows, 1 << 30) * N * max(q) * ((T - 1) // 2)
+    assert 2 * xmax < R  # the limit keeps the sums inside the basis
     xs = [0, 1, -1, xmax, -xmax, xmax - 77, -(xmax // 3)]
-    st = syn.Stream(11, N + L)
+    st = syn.Stream(11, N + L + nr)
     for w in st.words(12).tolist():
         xs.append((int(w) * xmax) >> 64)
-        xs.append(-((int(w) * xmax) >> 63))
+        xs.append(-((int(w) * xmax) >> 64))
     for i, x in enumerate(xs):
         xr = np.array([(N * x) % rk + (rk if (i + k) % 3 == 0 else 0)
-                       for k, rk in enumerate(r)], np.uint32)
+                       for k, rk in enumerate(r)] + [0] * (4 - nr), np.uint32)
         out = np.zeros(L, np.uint64)
-        assert emu.lib().emu_row_crt(N, L, np.array(q, np.uint64), T, xr, out) == 0
+        assert emu.lib().emu_row_crt(N, L, np.array(q, np.uint64), T, nr, xr, out) == 0
         assert [int(v) for v in out] == [x % qq for qq in q], x
 
 
