@@ -672,19 +672,36 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
 #pragma unroll
   for (int l = 0; l < NL; ++l) acc[l] = 0;
   u32 terms = 0;
+  const u64 kc = (u64)k * N + c, jstride = (u64)NL * kN;
   u64 job = (u64)seg * seg_len + g;
-  u64 row = g < seg_len ? jobs[job].row : 0;
-  for (u32 x = g; x < seg_len; x += G, job += G) {
-    const u64 m = dbr[row * kN + (u64)k * N + c];
-    if (x + G < seg_len) row = jobs[job + G].row;
-    const u32 *d = D + job * NL * kN + (u64)k * N + c;
+  u32 x = g;
+  u64 row0 = x < seg_len ? jobs[job].row : 0;
+  // two rows per iteration: both rows' loads issue before the products
+  for (; x + G < seg_len; x += 2 * G, job += 2 * G) {
+    const u64 row1 = jobs[job + G].row;
+    const u64 m0 = dbr[row0 * kN + kc], m1 = dbr[row1 * kN + kc];
+    if (x + 2 * G < seg_len) row0 = jobs[job + 2 * G].row;
+    const u32 *d0 = D + job * jstride + kc, *d1 = d0 + G * jstride;
+    u32 a[NL], b[NL];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) acc[l] += d[l * kN] * m;
-    if (++terms == 15) {
+    for (int l = 0; l < NL; ++l) {
+      a[l] = d0[l * kN];
+      b[l] = d1[l * kN];
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) acc[l] += a[l] * m0 + b[l] * m1;
+    terms += 2;
+    if (terms >= 14) {  // at most 14 products and a folded residue: below 2^64
 #pragma unroll
       for (int l = 0; l < NL; ++l) acc[l] = reduce_ext(acc[l], E);
       terms = 1;  // the folded residue counts as one term
     }
+  }
+  if (x < seg_len) {  // the last row of an odd count
+    const u64 m0 = dbr[row0 * kN + kc];
+    const u32 *d0 = D + job * jstride + kc;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) acc[l] += d0[l * kN] * m0;
   }
   u32 *o = S + (u64)sg * NL * kN + (u64)k * N + c;
 #pragma unroll
