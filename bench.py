@@ -150,11 +150,11 @@ def imad_per_job(kind: str) -> float:
 # traffic grows in proportion to the jobs of a launch, so a full launch's
 # traffic is this figure times its jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor_intt": (45717760 + 47470592 + 37217536 + 55555072) / 128,
-    "scale": (213959680 + 71992832) / 128,
+    "tensor_intt": (45726464 + 47533312 + 37214976 + 55348224) / 128,
+    "scale": (213959168 + 72737536) / 128,
     # per-job kernels of the row-basis key switch (k_rows_ntt, k_rows_mac);
     # the once-per-row-group conversions are left out
-    "relin_pm": (100992000 + 144530432 + 218128896 + 38547712) / 128,
+    "relin_pm": (100940800 + 96588800 + 163607296 + 23501824) / 128,
 }
 
 
