@@ -1,8 +1,8 @@
 """Benchmark of the constant-weight PIR server answer path on GB300.
 
 Workload (the metric's configuration): index PIR over n = 65536 rows of
-8192 16-bit coefficients (1 GiB of payload, 8 GiB resident in NTT form),
-codewords of weight k = 4 and length m = 37, BFV with N = 8192, four 54-bit
+8192 16-bit coefficients (1 GiB of payload, 6 GiB resident in NTT form in
+the row basis), codewords of weight k = 4 and length m = 37, BFV with N = 8192, four 54-bit
 primes, t = 65537; one query of 37 ciphertexts per step.  Keys and queries
 are uniform residues (the distribution of RLWE keys and ciphertexts); the
 answer path does the same work on them as on real encryptions.
@@ -830,7 +830,7 @@ def main():
             "config": {"workload": WORKLOAD_NAME, "rows": WL["n"], "k": WL["k"], "m": WL["m"],
                        "N": WL["N"], "L": WL["L"],
                        "payload_mb_per_query": payload_mb(WL["n"]),
-                       "l2": "inputs larger than L2 (8 GiB NTT-form database streamed per step)",
+                       "l2": "inputs larger than L2 (6 GiB NTT-form database, three 30-bit row primes, streamed per step)",
                        "parallelism": "one query stream per GPU (replicas)"}}
 
     if args.impl == "reference":
