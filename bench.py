@@ -4,9 +4,9 @@ Workload (the metric's configuration): index PIR over n = 65536 rows of
 8192 16-bit coefficients (1 GiB of payload, 6 GiB resident in NTT form in
 the row basis), codewords of weight k = 4 and length m = 37, BFV with
 N = 8192, four 54-bit primes, t = 65537; one query of 37 ciphertexts per
-step.  Keys and queries
-are uniform residues (the distribution of RLWE keys and ciphertexts); the
-answer path does the same work on them as on real encryptions.
+step.  Keys and queries are uniform residues (the distribution of RLWE keys
+and ciphertexts); the answer path does the same work on them as on real
+encryptions.
 
 A step is one full answer: selection vector (product tree with
 relinearisation), plain multiplication and accumulation over all rows.
