@@ -528,6 +528,51 @@ def test_c1_full_answer_decrypts_with_positive_budget(orc):
     assert budget > 0
 
 
+@pytest.mark.parametrize("N,L,n,k,m,c,seeds,domain", [
+    (8192, 4, 65536, 4, 37, 0, (11, 12, 13), 65536),   # index PIR, configuration 2
+    (16384, 7, 16384, 8, 64, 6, (21, 22, 23), 1 << 32),  # keyword PIR, configuration 3
+])
+def test_full_size_answers_keep_a_positive_budget(orc, N, L, n, k, m, c, seeds, domain):
+    """Decryption of the full answers of the second and third
+    configurations, bounded without computing them.  The answer is the sum
+    over the n rows of sel_i * DB_i (Sec. 3.3.3); the invariant noise of a
+    sum of ciphertexts is the sum of their invariant noises while that sum
+    stays below Q/2, so its budget is at least the smallest row term's
+    budget minus log2 n.  The row terms are computed for the target row and
+    rows whose codewords share 0 ... k-1 positions with the target's (the
+    number of factors that encrypt 1); each must decrypt to the row or to
+    zero and leave more than 16 bits after the log2 n of the sum."""
+    q = [int(p) for p in orc.primes(N, L)]
+    O = orc.Oracle(N, q)
+    cd = syn.ClientDraws(seeds[0], q, N)
+    a, e = cd.relin()
+    rlk = O.keygen_relin(cd.s, a, e)
+    st = syn.Stream(seeds[2])
+    target = int(st.below(domain, 1)[0])
+    qpos = orc.map_perfect(target, m, k)
+    a, e = cd.encryption(-(-m // (1 << c)), 77)
+    query = O.make_query(qpos, m, c, cd.s, a, e)
+    cts = O.expand(query, c, m, galois_keys(O, cd, N, c)) if c else query
+    rows, overlaps = [target], {k}
+    for x in st.below(domain, 4096).tolist():
+        ov = len(set(orc.map_perfect(int(x), m, k).tolist()) & set(qpos.tolist()))
+        if ov not in overlaps and len(rows) < 4:
+            overlaps.add(ov)
+            rows.append(int(x))
+    assert len(rows) == 4
+    payload = syn.payload(syn.Stream(seeds[1]), len(rows), 8192, 1 << 16)
+    worst = math.inf
+    for i, x in enumerate(rows):
+        term = O.plain_mul(O.selection(cts, orc.map_perfect(x, m, k), rlk), payload[i])
+        mu, budget = O.decrypt(term, cd.s)
+        want = np.zeros(N, np.uint32)
+        if x == target:
+            want[:8192] = payload[i]
+        assert np.array_equal(mu, want), x
+        worst = min(worst, budget)
+    assert worst - math.log2(n) > 16
+
+
 # ------------------------------------------------------------ mappings
 @pytest.mark.parametrize("m,k", [(10, 3), (12, 5), (9, 1), (7, 7)])
 def test_perfect_mapping_roundtrip_and_order(orc, m, k):
