@@ -128,13 +128,14 @@ void cwpir_destroy(cwpir_ctx *ctx);
  * payload_len <= CWPIR_MAX_PLAINTEXTS * N): plaintext p holds payload
  * coefficients p*N .. p*N + N - 1, the last one zero-padded; every answer
  * against the database returns s ciphertexts, the inner products of the one
- * selection vector with each plaintext column (Sec. 3.3.3).  For index PIR the codeword of row i is the perfect mapping of
- * i; for keyword PIR (Sec. 3.3.6) the mapping of the row's keyword.  The
- * rows are lifted to centered integers and kept in HBM in NTT form: rows of
- * one plaintext with k >= 2 modulo three (four for a large t) internal
- * 30-bit primes (12 or 16 bytes a coefficient; the answer multiplies them
- * exactly as integers), otherwise modulo the ciphertext primes (8 L bytes a
- * coefficient and plaintext).
+ * selection vector with each plaintext column (Sec. 3.3.3).  For index PIR
+ * the codeword of row i is the perfect mapping of i; for keyword PIR
+ * (Sec. 3.3.6) the mapping of the row's keyword.  The rows are lifted to
+ * centered integers and kept in HBM in NTT form: rows of one plaintext with
+ * k >= 2 modulo three (four for a large t) internal 30-bit primes (12 or 16
+ * bytes a coefficient; the answer multiplies them exactly as integers),
+ * otherwise modulo the ciphertext primes (8 L bytes a coefficient and
+ * plaintext).
  * 1 <= k <= 16, k <= m <= 16384, 1 <= n <= 2^24.  *db_id receives a handle.
  * EINVAL (including a coefficient >= t or a bad codeword), ENOMEM, ECUDA. */
 int cwpir_load_db(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len, uint32_t k,
@@ -296,9 +297,10 @@ int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
  * until the process exits.  One multiplication needs (L^2 + 14L + 7K/2) * N
  * words, K the 30-bit extension primes of the tensor (K = 4, 6, 8, 9, 11,
  * 13, 15, 17 for L = 1 ... 8): N = 4096 allows L <= 8, N = 8192 allows
- * L <= 4, N = 16384 allows L <= 2; larger sizes are rejected with EINVAL.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the array and it keeps
+ * L <= 4, N = 16384 allows L <= 2; larger sizes are rejected with EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps
  * the previous call's contents (the error flag is cleared each call): calls
  * that overlap on the GPU, from any context or stream, race.  ctx must be a
  * set-up context (it supplies the tables and the relinearisation key). */
