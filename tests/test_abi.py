@@ -56,3 +56,46 @@ def test_host_helpers_match_definitions(cudalib, orc):
             assert B.map_lossy(x, m, k).tolist() == orc.map_lossy(x, m, k).tolist()
     with pytest.raises(B.CwpirError):
         B.map_lossy(5, 4, 5)
+
+
+def test_folklore_codewords_match_definition(cudalib, orc):
+    """cwpir_map_folklore: positions 2i + y[i] (the plain folklore operator,
+    Eq. folklore-plain-eq), against the oracle; y >= 2^ell is rejected."""
+    from paper_2202_07569_gb300 import binding as B
+
+    for ell in (1, 2, 7, 12, 16):
+        for y in sorted({0, 1, (1 << ell) - 1, 0x5A5A & ((1 << ell) - 1)}):
+            got = B.map_folklore(y, ell).tolist()
+            assert got == orc.folklore_codeword(y, ell).tolist()
+            assert got == [2 * i + ((y >> i) & 1) for i in range(ell)]
+    with pytest.raises(B.CwpirError):
+        B.map_folklore(1 << 5, 5)
+
+
+def test_setup_rejects_bad_parameters(cudalib):
+    """cwpir_setup checks N, L, t and the primes before it touches the
+    device: each bad set returns EINVAL with a message naming the problem."""
+    import numpy as np
+
+    from paper_2202_07569_gb300 import binding as B
+
+    q8 = [int(v) for v in B.default_primes(8192, 4)]
+    composite = next(x for x in range(q8[0] - 16384, 1 << 53, -16384)
+                     if any(x % d == 0 for d in (3, 5, 7, 11, 13)))
+    cases = [
+        (1000, q8, 65537, "N must be"),
+        (32768, q8, 65537, "N must be"),
+        (8192, [int(v) for v in B.default_primes(8192, 9)], 65537, "L must be"),
+        (8192, q8, 65536, "t must be"),
+        (8192, q8, (1 << 20) + 7, "t must be"),
+        (8192, q8, 2, "t must be"),
+        (16384, q8, 65537, "q[2] must be"),           # not 1 mod 2N at N = 16384
+        (8192, [composite] + q8[1:], 65537, "q[0] must be"),
+        (8192, [q8[0], q8[0]], 65537, "distinct"),
+    ]
+    for N, q, t, msg in cases:
+        L = max(len(q), 1)
+        relin = np.zeros(L * 2 * L * N, np.uint64)
+        with pytest.raises(B.CwpirError) as ei:
+            B.Context(N, np.array(q, np.uint64), t, relin)
+        assert ei.value.code == -1 and msg in str(ei.value), (N, len(q), t, str(ei.value))
