@@ -42,6 +42,9 @@ def lib():
     l.emu_reduce62.argtypes = [U64, u64p, U64,
                                np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")]
     l.emu_reduce62.restype = None
+    l.emu_row_sum.argtypes = [U32, U32, u64p, U64, U32, U64, u64p,
+                              np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), u64p]
+    l.emu_row_sum.restype = U64
     l.emu_substitute.argtypes = [U32, U32, u64p, U64, U32, u64p, u64p, u64p]
     l.emu_substitute.restype = None
     l.emu_scale.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p]

@@ -411,3 +411,49 @@ uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
   return bad;
 }
 }
+
+extern "C" {
+// The row-basis path of the last tree level for one polynomial limb: out =
+// sum_r z_r * lift(db_r) mod q_j (negacyclic, j < L) through the row
+// primes, in the order of the row kernels: each limb z_r (below 2^62)
+// reduced modulo r_k and transformed, each row centered-lifted and
+// transformed, the pointwise products summed modulo r_k, the sum inverse-
+// transformed (N x in [0, 2r)), and the exact CRT to the q_j.  z:
+// [rows][N] u64, db: [rows][N] u32 below t, out: [L][N].  Returns the
+// number of coefficients whose fixed-point check tripped.
+uint64_t emu_row_sum(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint32_t nr,
+                     uint64_t rows, const uint64_t *z, const uint32_t *db, uint64_t *out) {
+  Emu E(N, L, q, t);
+  RowTab T;
+  fill_rows(T, E.q, E.p, N, nr);
+  std::vector<u32> x((u64)nr * N), a(N), b(N);
+  for (u32 k = 0; k < nr; ++k) {
+    const ExtPrime &P = T.r[k];
+    const u32 p = P.p;
+    std::vector<u64> acc(N, 0);
+    for (u64 r = 0; r < rows; ++r) {
+      for (u32 c = 0; c < N; ++c) {
+        a[c] = reduce_ext62(z[r * N + c], P);
+        const u32 v = db[r * N + c];
+        b[c] = v > (u32)t / 2 ? p - (u32)(t - v) : v;
+      }
+      pass_ntt32_n<4>(E.logN, a.data(), E.tw32[k].data(), p, false);
+      pass_ntt32_n<4>(E.logN, b.data(), E.tw32[k].data(), p, false);
+      for (u32 c = 0; c < N; ++c) acc[c] = reduce_ext(acc[c] + (u64)a[c] * b[c], P);
+    }
+    for (u32 c = 0; c < N; ++c) a[c] = (u32)acc[c];
+    pass_ntt32_n<4>(E.logN, a.data(), E.tw32[k].data(), p, true);
+    for (u32 c = 0; c < N; ++c) x[(u64)c * nr + k] = a[c];
+  }
+  uint64_t tripped = 0;
+  for (u32 c = 0; c < N; ++c) {
+    u32 xr[kRowPrimes] = {0, 0, 0, 0}, y[kRowPrimes];
+    for (u32 k = 0; k < nr; ++k) xr[k] = x[(u64)c * nr + k];
+    bool far;
+    const u64 rho = row_digits(xr, y, T, &far);
+    tripped += far;
+    for (u32 j = 0; j < L; ++j) out[(u64)j * N + c] = row_to_q(y, rho, (int)j, T);
+  }
+  return tripped;
+}
+}

@@ -155,6 +155,57 @@ def test_row_basis_crt(orc, N, L, nr):
         assert [int(v) for v in out] == [x % qq for qq in q], x
 
 
+@pytest.mark.parametrize("N,L,nr", [(8192, 4, 3), (16384, 7, 3), (1024, 2, 4)])
+def test_row_basis_sums_at_the_group_limit(orc, N, L, nr):
+    """The row path of the last tree level (transforms modulo the row
+    primes, row products summed over a group, inverse transform, exact CRT)
+    returns sum_r z_r * lift(db_r) mod q_j for a full group of rows at the
+    extremes the limit allows: every limb word at q_max - 1 and every row
+    coefficient at +-(t-1)/2, whose negacyclic sum has the closed form
+    x_i = rows z d (2i + 2 - N), reaching rows N q_max (t-1)/2 at i = N-1.
+    Twice the rows overflow the basis there, so the limit is within a factor
+    two of the largest group the basis holds.  A random group is checked
+    against the oracle's products."""
+    q = [int(v) for v in orc.primes(N, L)]
+    qa = np.array(q, np.uint64)
+    rows = min(int(emu.lib().emu_row_limit(N, L, qa, T, nr)), 2048)
+    zmax = max(q) - 1
+    i = np.arange(N, dtype=object)
+
+    def run(nrows, zval, v):
+        z = np.full((nrows, N), zval, np.uint64)
+        db = np.full((nrows, N), v, np.uint32)
+        out = np.zeros((L, N), np.uint64)
+        tripped = emu.lib().emu_row_sum(N, L, qa, T, nr, nrows, z, db, out)
+        d = v - T if v > T // 2 else v
+        x = nrows * zval * d * (2 * i + 2 - N)
+        return out, tripped, x
+
+    for v in ((T - 1) // 2, (T + 1) // 2):  # d = +(t-1)/2 and -(t-1)/2
+        out, tripped, x = run(rows, zmax, v)
+        assert tripped == 0
+        for j, qj in enumerate(q):
+            assert [int(w) for w in out[j]] == [int(w) % qj for w in x], (v, j)
+    if nr == 3:
+        out, tripped, x = run(2 * rows, zmax, (T - 1) // 2)
+        assert tripped > 0 or int(out[0][N - 1]) != int(x[N - 1]) % q[0]
+
+    st = syn.Stream(12, N + nr)
+    nrand = 6
+    z = st.below(max(q), nrand * N).reshape(nrand, N)
+    db = syn.payload(st, nrand, N, T)
+    out = np.zeros((L, N), np.uint64)
+    assert emu.lib().emu_row_sum(N, L, qa, T, nr, nrand, z, db, out) == 0
+    lift = [[int(v) - T if v > T // 2 else int(v) for v in row] for row in db]
+    for j, qj in enumerate(q):
+        want = np.zeros(N, np.uint64)
+        for r in range(nrand):
+            zr = np.array([int(w) % qj for w in z[r]], np.uint64)
+            dr = np.array([w % qj for w in lift[r]], np.uint64)
+            want = (want + orc.negacyclic_mul_mod(zr, dr, qj)) % np.uint64(qj)
+        assert np.array_equal(out[j], want), j
+
+
 def test_emulated_substitution_matches_oracle(orc):
     N, L = 1024, 3
     q, O, cd, rlk = _setup(orc, N, L)
