@@ -27,6 +27,15 @@ def shard_rows(n: int, world: int, rank: int) -> tuple[int, int]:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def partial_shape(payload_len: int, N: int, L: int) -> tuple:
+    """Shape of one rank's partial response: [2][L][N], or [s][2][L][N] for
+    rows of s = ceil(payload_len / N) > 1 plaintexts (Sec. 3.3.1).  It
+    depends on the database alone, so a rank with no rows gathers the same
+    shape as the others."""
+    s = max(1, -(-int(payload_len) // int(N)))
+    return ((s,) if s > 1 else ()) + (2, int(L), int(N))
+
+
 def _group_info(group):
     import torch.distributed as dist
 
@@ -68,7 +77,8 @@ class ShardedDatabase:
         if self.hi > self.lo:
             self.db = ctx.load_db(np.ascontiguousarray(items[self.lo:self.hi]),
                                   np.ascontiguousarray(codewords[self.lo:self.hi]), m)
-        self.resp_shape = ctx.resp_shape(self.db) if self.db is not None else ctx.ct_shape
+        plen = int(np.shape(items)[1]) if np.ndim(items) == 2 else 0
+        self.resp_shape = partial_shape(plen, ctx.N, ctx.L)
 
     def answer_device(self, d_query, d_resp, c: int = 0, stream=None):
         """Answer the query (device tensor [h][2][L][N], int64 view of the

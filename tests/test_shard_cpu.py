@@ -28,6 +28,18 @@ def test_shard_rows_cover_every_row_once(n, world):
     assert max(sizes) - min(sizes) <= 1
 
 
+def test_partial_shape_depends_on_the_database_only():
+    """Every rank, with or without rows, gathers partials of one shape:
+    [2][L][N] for rows of one plaintext, [s][2][L][N] for s > 1."""
+    from paper_2202_07569_gb300.shard import partial_shape
+
+    assert partial_shape(0, 8192, 4) == (2, 4, 8192)
+    assert partial_shape(8192, 8192, 4) == (2, 4, 8192)
+    assert partial_shape(8193, 8192, 4) == (2, 2, 4, 8192)
+    assert partial_shape(17 * 8192, 8192, 4) == (17, 2, 4, 8192)
+    assert partial_shape(5000, 4096, 2) == (2, 2, 2, 4096)
+
+
 def test_shard_rows_rejects_bad_ranks():
     for args in [(5, 0, 0), (5, 2, 2), (5, 2, -1), (-1, 2, 0)]:
         with pytest.raises(ValueError):
