@@ -1,7 +1,8 @@
 """Python handle on the plain C oracle (``cwpir_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke``
-and by the CPU-baseline leg of ``bench.py``.  The product package never
+(``__graft_entry__.build`` compiles it) and by the CPU legs of ``bench.py``
+(the CPU baseline and ``--impl reference``).  The product package never
 imports this module, and this module never imports the product package.
 
 The oracle follows the paper (arXiv 2202.07569) step by step; see the C
