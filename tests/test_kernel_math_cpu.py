@@ -32,6 +32,25 @@ def _ext_primes(N, L, q):
     return p
 
 
+@pytest.mark.parametrize("L", range(1, 9))
+def test_extension_basis_covers_every_accepted_parameter_set(L):
+    """The scale-down is exact while P > 2^17 t N Q.  The library accepts
+    t < 2^20, N <= 16384 and ciphertext primes below 2^54, so the K(L)
+    extension primes must exceed 2^17 2^20 N 2^(54 L) at every N, and be
+    distinct 30-bit primes = 1 mod 2N."""
+    k = emu.lib().emu_ext_count(L)
+    for logn in range(10, 15):
+        N = 1 << logn
+        p = np.zeros(k, np.uint64)
+        emu.lib().emu_ext_primes(N, L, np.zeros(L, np.uint64), p)
+        p = [int(v) for v in p]
+        assert len(set(p)) == k
+        for v in p:
+            assert (1 << 29) < v < (1 << 30) and v % (2 * N) == 1
+            assert all(v % d for d in range(3, 1 << 15, 2)), v
+        assert math.prod(p) > 1 << (17 + 20 + logn + 54 * L), (N, L)
+
+
 def _setup(orc, N, L, seed=3):
     q = orc.primes(N, L)
     O = orc.Oracle(N, q)
