@@ -51,6 +51,20 @@ def test_extension_basis_covers_every_accepted_parameter_set(L):
         assert math.prod(p) > 1 << (17 + 20 + logn + 54 * L), (N, L)
 
 
+@pytest.mark.parametrize("L", range(1, 9))
+def test_row_basis_group_sizes_over_the_accepted_parameters(orc, L):
+    """Rows per group that the row basis holds exactly: with four row
+    primes at least 2048 (a whole launch's group cap) for every N and the
+    largest t the library accepts; with three primes at t = 65537 at least
+    63, so the three-prime basis serves the default t everywhere."""
+    t_max = max(v for v in range((1 << 20) - 64, 1 << 20) if orc.is_prime(v))
+    for logn in range(10, 15):
+        N = 1 << logn
+        q = np.array(orc.primes(N, L), np.uint64)
+        assert emu.lib().emu_row_limit(N, L, q, t_max, 4) >= 2048, (N, L)
+        assert emu.lib().emu_row_limit(N, L, q, T, 3) >= 63, (N, L)
+
+
 def _setup(orc, N, L, seed=3):
     q = orc.primes(N, L)
     O = orc.Oracle(N, q)
