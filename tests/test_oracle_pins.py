@@ -221,6 +221,40 @@ def test_encrypt_decrypt_roundtrip(orc):
         assert np.array_equal(got, mu) and budget > 50
 
 
+def invariant_budget(ct, s, q):
+    """log2 Q - 1 - log2 max_i |t x_i - Q round(t x_i / Q)| with
+    x = c0 + c1 s (mod Q), computed with Python integers from the secret."""
+    Q = math.prod(q)
+    c0, c1 = lift_poly(ct[0], q), lift_poly(ct[1], q)
+    x = [(a + b) % Q for a, b in zip(c0, schoolbook_nega(c1, [int(v) for v in s]))]
+    worst = 0
+    for v in x:
+        r = (T * v + Q // 2) // Q  # round half up; t x / Q is never a half integer
+        worst = max(worst, abs(T * v - Q * r))
+    return math.log2(Q) - 1 - math.log2(worst)
+
+
+def test_noise_budget_matches_its_definition(orc):
+    """The budget that decryption reports is log2 Q - 1 - log2 of the largest
+    |t (c0 + c1 s) - Q mu'| (mu' the rounded quotient), recomputed here from
+    the secret with exact integers at N = 16, L = 3: for a fresh ciphertext,
+    a product M(a, b) and a plain product.  Each step adds noise, so the
+    budgets also decrease in that order."""
+    N, L = 16, 3
+    O, q, cd, rlk = small_setup(orc, N, L)
+    st = syn.Stream(34)
+    mus = [st.below(T, N).astype(np.uint32) for _ in range(2)]
+    ca, cb = encrypt_many(O, cd, mus, stream=3)
+    prod = O.bfv_mul(ca, cb, rlk)
+    pm = O.plain_mul(prod, st.below(T, N).astype(np.uint32))
+    budgets = []
+    for ct in (ca, prod, pm):
+        _, got = O.decrypt(ct, cd.s)
+        assert abs(got - invariant_budget(ct, cd.s, q)) < 1e-9
+        budgets.append(got)
+    assert budgets[0] > budgets[1] > budgets[2] > 0
+
+
 @pytest.mark.parametrize("N,L", [(64, 2), (4096, 2)])
 def test_multiplication_decrypts_to_ring_product(orc, N, L):
     """Dec(M(a,b)) = Dec(a) Dec(b) in R_t; the size-3 tensor decrypts the
