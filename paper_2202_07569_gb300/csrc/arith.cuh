@@ -311,12 +311,14 @@ template <int L>
 CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S) {
   constexpr int K = ext_count(L);
   u64 y[L];
+#pragma unroll
   for (int j = 0; j < L; ++j)
     y[j] = shoup(dq[j], S.t_theta[j], S.t_theta_s[j], S.Q.q[j]);
   bool amb;
   u64 rho = round_sum<L>(y, S.Q.w_hi, S.Q.w_lo, &amb);
   if (amb) {
     u64 eps[L];
+#pragma unroll
     for (int j = 0; j < L; ++j)
       eps[j] = shoup(dq[j], S.t_mod[j], S.t_mod_s[j], S.Q.q[j]);
     rho += mr_greater_half<L>(eps, S.Q);
@@ -324,21 +326,26 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
   // dp_k A_k < 2^61, 2L products of 27-bit halves with 30-bit constants
   // below 2^57 each (2^61 for L = 8), rho C_k < 2^34: the sum fits 2^62
   u64 yb[K];
+#pragma unroll
   for (int k = 0; k < K; ++k) {
     u64 s = dp[k] * S.A[k] + rho * S.Cr[k];
+#pragma unroll
     for (int j = 0; j < L; ++j)
       s += (y[j] & kMask27) * S.B[j][k] + (y[j] >> 27) * S.B27[j][k];
     yb[k] = reduce_ext(s, S.ext[k]);
   }
   u64 fix = 0;
+#pragma unroll
   for (int k = 0; k < K; ++k) fix += yb[k] * S.pw58[k];  // each < 2^58: sum < 2^63
   const u64 rho2 = (fix + (1ull << 57)) >> 58;
   const u64 frac = (fix + (1ull << 57)) & ((1ull << 58) - 1);  // offset + 1/2, in 2^-58
   const bool far = frac < (1ull << 57) - (1ull << 41) || frac > (1ull << 57) + (1ull << 41);
   // K + 1 <= 18 products of values below 2^30 with 27-bit halves: the words
   // ll and x stay below 18 * 2^57 < 2^62.2; the sum ll + x 2^27 < 2^90
+#pragma unroll
   for (int j = 0; j < L; ++j) {
     u64 ll = rho2 * S.negp2[j][0], x = rho2 * S.negp2[j][1];
+#pragma unroll
     for (int k = 0; k < K; ++k) {
       ll += yb[k] * S.hat2[k][j][0];
       x += yb[k] * S.hat2[k][j][1];
