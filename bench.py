@@ -38,15 +38,19 @@ METRIC = "PIR answer DB MB/s per query (N=8192,k=4); batched vs plain; p50/p99 l
 WL = dict(N=8192, L=4, n=65536, k=4, m=37, plen=8192, t=65537, coef_bytes=2)
 WORKLOAD_NAME = ("index PIR n=65536 rows x 8192 16-bit coefficients, k=4, m=37, "
                  "BFV N=8192 L=4 (54-bit primes) t=65537, one query per step")
-# 32-bit integer multiply-adds implied by one modular multiplication: a
-# 54-bit residue in a 64-bit word needs one 64 x 64 high product (4 IMAD)
-# and two low products (3 each); a 30-bit residue in a 32-bit word needs a
-# high and two low 32-bit products
-IMAD_PER_MODMUL54 = 10
-IMAD_PER_MODMUL30 = 3
 EXT_PRIMES = {1: 4, 2: 6, 3: 8, 4: 9, 5: 11, 6: 13, 7: 15, 8: 17}  # 30-bit primes per L
-IMAD_PER_SM_CLK = 64
-SMS = 152
+
+
+def modmul_weights(pk: dict):
+    """IMAD-equivalents of one modular multiplication, from the measured
+    integer rates (cwpir_measure_int_peaks): a 54-bit residue in a 64-bit
+    word takes two 64 x 64 low products and one high product (Shoup or
+    Barrett), a 30-bit residue two 32-bit low products and one high one;
+    each product weighs the IMAD rate over its own measured rate."""
+    imad = pk["imad32_per_s"]
+    w54 = 2 * imad / pk["mullo64_per_s"] + imad / pk["mulhi64_per_s"]
+    w30 = 2 + imad / pk["mulhi32_per_s"]
+    return w54, w30
 
 
 def payload_mb(rows: int) -> float:
@@ -105,29 +109,37 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def make_inputs(seed: int = 12, rows: int | None = None):
-    from paper_2202_07569_gb300 import binding as B
+def make_inputs(seed: int = 12, rows: int | None = None, oracle_side: bool = False):
+    """The workload's seeded inputs.  The primes and codewords come from the
+    library's host helpers, or, for the CPU oracle's legs (oracle_side), from
+    the oracle's own, so that those legs load nothing of the product."""
     from paper_2202_07569_gb300 import synthetic as syn
 
+    if oracle_side:
+        import oracle as H
+        primes = H.primes
+    else:
+        from paper_2202_07569_gb300 import binding as H
+        primes = H.default_primes
     N, L, n, k, m = WL["N"], WL["L"], rows or WL["n"], WL["k"], WL["m"]
-    q = B.default_primes(N, L)
+    q = np.asarray(primes(N, L), dtype=np.uint64)
     rlk = syn.uniform_residues(syn.Stream(seed, 3), q, (L, 2), N)
     query = syn.uniform_ciphertexts(seed + 1, q, m, N)
     items = syn.payload(syn.Stream(seed, 1), n, WL["plen"], 1 << 16)
-    cw = np.stack([B.map_perfect(i, m, k) for i in range(n)])
+    cw = np.stack([H.map_perfect(i, m, k) for i in range(n)])
     return q, rlk, query, items, cw
 
 
-def imad_per_job(kind: str) -> float:
+def imad_per_job(kind: str, m54: float, m30: float) -> float:
     """Algorithmic work per job of a kernel class, in IMAD-equivalents:
     54-bit modular multiplications (one per butterfly, product or
-    reduction) times 10, 30-bit ones times 3, and the scale-down's 32 x 32
-    products of 27-bit halves with 30-bit constants times 1."""
+    reduction) times m54, 30-bit ones times m30 (modmul_weights), and the
+    scale-down's 32 x 32 products of 27-bit halves with 30-bit constants
+    times 1."""
     N, L = WL["N"], WL["L"]
     K = EXT_PRIMES[L]
     logN = N.bit_length() - 1
     bf = N // 2 * logN
-    m54, m30 = IMAD_PER_MODMUL54, IMAD_PER_MODMUL30
     if kind == "tensor_intt":  # 3 outputs x (L + K) limbs: 4 products + inverse transform
         return 3 * (L * bf * m54 + K * bf * m30) + 4 * N * (L * m54 + K * m30)
     if kind == "relin_pm":  # row basis of 3 primes (t = 65537, N = 8192): 3L limbs x 3
@@ -147,9 +159,9 @@ def imad_per_job(kind: str) -> float:
 
 # DRAM bytes (read + write) per job of each kernel class, from one ncu
 # capture of the current kernels on the profiling size (4096 rows, 128
-# multiplications per launch; profiles/ncu_full_c2_4096rows.md).  DRAM
-# traffic grows in proportion to the jobs of a launch, so a full launch's
-# traffic is this figure times its jobs.
+# multiplications per launch).  DRAM traffic grows in proportion to the
+# jobs of a launch, so a full launch's traffic is this figure times its
+# jobs.
 DRAM_BYTES_PER_JOB = {
     "tensor_intt": (45726464 + 47533312 + 37214976 + 55348224) / 128,
     "scale": (213959168 + 72737536) / 128,
@@ -194,6 +206,7 @@ def run_gpu(args, rank: int, world: int, dist):
         step()
     torch.cuda.synchronize()
     stats = ctx.last_stats()
+    peaks = B.measure_int_peaks(dev)  # the roofline's integer denominator, this device now
 
     # device-timed region: per-step events on the launching stream
     ctx.set_option(B.OPT_KERNEL_TIMING, 1)
@@ -260,10 +273,10 @@ def run_gpu(args, rank: int, world: int, dist):
     jobs_per_launch = {"tensor_intt": stats["mults"], "relin_pm": stats["mults"],
                        "scale": stats["mults"], "lift": 0}.get(dom, 0)
     launches_per_step = launches / args.steps
-    work_per_launch = imad_per_job(dom) * jobs_per_launch / max(1.0, launches_per_step)
+    m54, m30 = modmul_weights(peaks)
+    work_per_launch = imad_per_job(dom, m54, m30) * jobs_per_launch / max(1.0, launches_per_step)
     avg_launch_s = ms / launches / 1e3
-    sm_max = out["clocks"].get("sm_max_mhz") or 2070.0
-    peak = SMS * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
+    peak = peaks["imad32_per_s"] / 1e12
     achieved = work_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else 0.0
     out["roofline"] = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                        "unit": "TIMAD/s", "frac": achieved / peak if peak else None,
@@ -271,9 +284,13 @@ def run_gpu(args, rank: int, world: int, dist):
                                    / max(1.0, launches_per_step)
                                    if dom in DRAM_BYTES_PER_JOB else None),
                        "traffic_unit": "bytes per launch",
-                       "peak_basis": f"{SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz; "
-                                     f"work = {IMAD_PER_MODMUL54} IMAD per 54-bit and "
-                                     f"{IMAD_PER_MODMUL30} per 30-bit modular multiplication"}
+                       "peak_basis": (
+                           "measured in this run (cwpir_measure_int_peaks: independent IMAD "
+                           f"chains on all {peaks['sms']} SMs, CUDA events): "
+                           f"{peaks['imad32_per_s'] / 1e12:.2f} T IMAD/s; work counted as "
+                           f"{m54:.2f} IMAD per 54-bit and {m30:.2f} per 30-bit modular "
+                           "multiplication from the measured 64-bit and high-product rates"),
+                       "int_peaks_measured": peaks}
     # batched vs plain: 16 queries in one batched call replayed from a CUDA
     # graph, against the plain one-query calls timed above
     if args.batch:
@@ -746,7 +763,7 @@ def run_c5(args, per_rate: int = 24, rates=(0.25, 0.5, 1, 10, 30, 100, 300, 1000
         targets.append((ctx, db, c))
         pools.append((qs, alone))
         mbs.append(payload_mb(n))
-    srv = B.Server(targets, max_batch=8, hbm_reserve=8 << 30)
+    srv = B.Server(targets, max_batch=8, hbm_reserve=8 << 30, lanes_per_target=2)
     mix = [0, 2, 1]  # index : keyword = 2 : 1
     results = []
     all_same = True
@@ -792,7 +809,7 @@ def cpu_baseline(rows_per_step: int | None = None, reps: int = 1):
     import oracle
 
     cores = os.cpu_count() or 1
-    q, rlk, query, items, cw = make_inputs(12)
+    q, rlk, query, items, cw = make_inputs(12, oracle_side=True)
     O = oracle.Oracle(WL["N"], q, WL["t"])
     rows = rows_per_step or 2 * cores
     times = []

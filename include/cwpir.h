@@ -32,8 +32,9 @@
  *    The library owns all device memory it allocates until cwpir_free_db or
  *    cwpir_destroy.
  *  - Calls on one context are not thread-safe; use one context per thread
- *    or serialise.  Every call returns CWPIR_OK (0) or a negative code; the
- *    message of the last failure is available from cwpir_last_error.
+ *    or serialise (the slot calls below are the exception).  Every call
+ *    returns CWPIR_OK (0) or a negative code; the message of the last
+ *    failure is available from cwpir_last_error.
  */
 #ifndef CWPIR_H
 #define CWPIR_H
@@ -45,7 +46,7 @@
 extern "C" {
 #endif
 
-#define CWPIR_ABI_VERSION 2
+#define CWPIR_ABI_VERSION 3
 /* Largest number of plaintexts per database row (payload_len <= this * N). */
 #define CWPIR_MAX_PLAINTEXTS 256
 
@@ -168,7 +169,8 @@ int cwpir_load_db_folklore(cwpir_ctx *ctx, uint64_t n, uint32_t payload_len,
 int cwpir_answer(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                  const uint64_t *query, uint64_t *response);
 /* Same with device buffers, enqueued on `stream` (a cudaStream_t, NULL for
- * the legacy default stream).  Returns once the work is enqueued. */
+ * the legacy default stream), on slot 0.  Returns once the work is enqueued;
+ * the device checks of that work are read with cwpir_device_status. */
 int cwpir_answer_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                         const uint64_t *d_query, uint64_t *d_response,
                         void *stream);
@@ -266,7 +268,9 @@ enum {
   CWPIR_OPT_SHARE_LEVEL1 = 1,
   /* rows per device batch (0 = automatic) */
   CWPIR_OPT_BATCH_ROWS = 2,
-  /* 1 (default): replay the answer as a captured CUDA graph */
+  /* 0 (default): enqueue every kernel of an answer; 1: capture the launch
+   * sequence of each (database, queries per call, c, slot) once into a CUDA
+   * graph and replay it (the batched and served paths switch it on) */
   CWPIR_OPT_USE_GRAPH = 3,
   /* 1: bracket every kernel launch with CUDA events on its stream and add
    * the durations per kernel class (read with cwpir_kernel_times); 0
@@ -280,9 +284,62 @@ enum {
    * k >= 2 are held in the row basis of internal primes (cwpir_load_db); 0:
    * modulo the ciphertext primes.  The response bits are identical either
    * way; already loaded databases keep their form. */
-  CWPIR_OPT_ROW_BASIS = 6
+  CWPIR_OPT_ROW_BASIS = 6,
+  /* cap, in bytes, on the device memory the context's buffers may hold
+   * (databases, scratch, plans; 0 = no cap, the default): an allocation
+   * that would pass it fails with CWPIR_ENOMEM before cudaMalloc is
+   * called, and the context stays usable.  Lowering it frees nothing. */
+  CWPIR_OPT_MEM_LIMIT = 7,
+  /* row sums of the last tree level: split into row groups until about
+   * this many waves of the device's resident threads cover it (0 = the
+   * default, 4); drops the cached plans.  Response bits are unchanged. */
+  CWPIR_OPT_ROW_GROUP_WAVES = 8
 };
+/* Both return EINVAL for an unknown option or a value out of range. */
 int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
+int cwpir_get_option(cwpir_ctx *ctx, int option, int64_t *value);
+/* Device bytes the context's buffers hold now (what CWPIR_OPT_MEM_LIMIT
+ * caps). */
+int cwpir_mem_used(const cwpir_ctx *ctx, uint64_t *bytes);
+
+/* ---- slots: concurrent answers on one context ----
+ * A slot is one set of the multiplication kernels' scratch buffers (up to
+ * 8 GiB, sized by CWPIR_OPT_MAX_JOBS) with its own device consistency
+ * flag; answers on different slots may run at the same time on different
+ * streams.  Slot 0 exists from cwpir_setup on and serves every call that
+ * takes no slot.  The calls in this group may be made from several threads
+ * on one context (they serialise their host-side work on a per-context
+ * lock; the device work of different slots overlaps); one slot must not be
+ * used by two streams at once. */
+/* Adds a slot; *slot receives its index.  Its buffers are allocated by its
+ * first answer.  ENOMEM, ECUDA. */
+int cwpir_slot_create(cwpir_ctx *ctx, uint32_t *slot);
+/* Waits for the device, frees the slot's buffers and its cached plans; the
+ * index may be handed out again by cwpir_slot_create.  EINVAL for slot 0
+ * or a slot not in use. */
+int cwpir_slot_release(cwpir_ctx *ctx, uint32_t slot);
+/* cwpir_answer_batch_device with the scratch of `slot`; the plans (and
+ * graphs) it builds are cached per slot. */
+int cwpir_answer_batch_slot(cwpir_ctx *ctx, uint32_t slot, int32_t db_id, uint32_t c,
+                            uint32_t nq, const uint64_t *d_queries, uint64_t *d_responses,
+                            void *stream);
+/* cwpir_plan_bytes for a slot: includes the slot's scratch if it has none
+ * yet. */
+int cwpir_plan_bytes_slot(cwpir_ctx *ctx, uint32_t slot, int32_t db_id, uint32_t nq,
+                          uint32_t c, uint64_t *bytes);
+/* Status of the device work of a slot: waits for `stream` (a cudaStream_t;
+ * NULL: the legacy default stream), then reads and clears the slot's
+ * consistency flag.  CWPIR_EINTERNAL if one of the device checks of the
+ * scale-down or of the row-basis rounding failed since the flag was last
+ * read (the responses computed meanwhile must not be used), else CWPIR_OK.
+ * The *_device and *_slot answer calls return once their work is enqueued
+ * and cannot report it themselves: call this after them.  The host-buffer
+ * calls read and clear slot 0's flag themselves. */
+int cwpir_device_status(cwpir_ctx *ctx, uint32_t slot, void *stream);
+/* Test hook for the path above: sets the slot's consistency flag as a
+ * failed device check would (a host-to-device copy of one word; no kernel
+ * runs, nothing faults).  The next status read reports CWPIR_EINTERNAL. */
+int cwpir_inject_status(cwpir_ctx *ctx, uint32_t slot);
 
 /* Homomorphic multiplication M (as cwpir_mul) on device buffers that
  * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
@@ -290,8 +347,11 @@ int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
  * allocate device memory where they multiply (a fixed pre-partitioned
  * memory pool, a section where an allocation would stall or is forbidden).
  * d_a, d_b: [2][L][N] ciphertexts, d_out: [2][L][N], device memory owned by
- * the caller; stream: a cudaStream_t (NULL: legacy default stream).  The
- * call returns when the result is complete.
+ * the caller; every residue of limb j must be below q_j, as for the other
+ * device-buffer calls (not checked here: the inputs are never copied to the
+ * host; an unreduced residue gives a wrong product, not an error).
+ * stream: a cudaStream_t (NULL: legacy default stream).  The call blocks
+ * until the result is complete.
  * Intermediates live in one file-scope device array of 2^20 u64 words
  * (8 MiB) plus a 64-word header, held by every GPU that loads the library
  * until the process exits.  One multiplication needs (L^2 + 14L + 7K/2) * N
@@ -299,7 +359,10 @@ int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
  * 13, 15, 17 for L = 1 ... 8): N = 4096 allows L <= 8, N = 8192 allows
  * L <= 4, N = 16384 allows L <= 2; larger sizes are rejected with EINVAL.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the rest of the process; make
+ * that first call before any stream capture.  The address belongs to the
+ * device's primary context: after cudaDeviceReset on that device the call
+ * must not be used again in the process.
  * All calls share the array and it keeps
  * the previous call's contents (the error flag is cleared each call): calls
  * that overlap on the GPU, from any context or stream, race.  ctx must be a
@@ -320,18 +383,25 @@ int cwpir_ctx_device(const cwpir_ctx *ctx, int *device);
 
 /* ---- online serving (configuration 5 of the benchmark) ---- */
 /* A server answers queries for registered targets (a context, one of its
- * databases, and the compression factor c of that target's queries).  One
- * worker thread per distinct context ("lane") takes, whenever it is free,
- * the waiting requests of its target with the oldest request, up to the
- * largest power of two <= max_batch whose answer plan fits in free device
- * memory minus hbm_reserve_bytes (cached plans of the context are released
- * when nothing fits), and answers them with one cwpir_answer_batch_device
- * call replayed from a CUDA graph; requests arriving meanwhile wait for the
- * next batch (continuous batching).  Lanes of different contexts run
- * concurrently on their own streams.  Each response is bit-identical to
- * cwpir_answer for the same query.  While a server runs, its contexts must
- * not be used by other threads.  Requests beyond max_pending waiting or
- * running are refused with EBUSY. */
+ * databases, and the compression factor c of that target's queries).  Each
+ * target gets lanes_per_target worker lanes: a host thread with its own
+ * stream and its own slot on the target's context (cwpir_slot_create, so
+ * up to 8 GiB of scratch per lane, held until the server is destroyed).
+ * Whenever a lane is free it takes the waiting requests of its target, up
+ * to the largest power of two <= max_batch whose answer plan fits in free
+ * device memory minus hbm_reserve_bytes (the target's cached plans are
+ * released when nothing fits), and answers them with one
+ * cwpir_answer_batch_slot call replayed from a CUDA graph (continuous
+ * batching).  Lanes of all targets run concurrently, so a request that
+ * arrives while others are on the GPU starts at once on an idle lane of
+ * its target and its kernels overlap with theirs; when every lane of its
+ * target is busy it joins the next batch of the first lane to finish.
+ * After each batch the lane reads its slot's device check flag
+ * (cwpir_device_status): a failed check fails that batch's requests with
+ * CWPIR_EINTERNAL.  Each response is bit-identical to cwpir_answer for the
+ * same query.  While a server runs, its contexts may be used by other
+ * threads only through the slot calls.  Requests beyond max_pending
+ * waiting or running are refused with EBUSY. */
 typedef struct cwpir_server cwpir_server;
 typedef struct {
   cwpir_ctx *ctx;
@@ -339,12 +409,20 @@ typedef struct {
   uint32_t c;
 } cwpir_target;
 typedef struct {
+  uint32_t max_batch;         /* most requests one lane answers at once, >= 1 */
+  uint32_t lanes_per_target;  /* 1 .. 16 */
+  uint32_t max_pending;       /* requests waiting or running, >= 1 */
+  uint64_t hbm_reserve_bytes; /* free device memory admission leaves untouched */
+} cwpir_server_config;
+typedef struct {
   uint64_t submitted, completed, batches, max_batch_seen, rejected_busy;
-  double busy_s; /* summed wall time of the lanes' batches */
+  uint64_t failed;         /* requests completed with an error status */
+  uint64_t max_concurrent; /* most batches running at the same time */
+  double busy_s;           /* summed wall time of the lanes' batches */
 } cwpir_server_stats;
+/* EINVAL for a bad target or configuration; ENOMEM; the slot errors. */
 int cwpir_server_create(const cwpir_target *targets, uint32_t n_targets,
-                        uint32_t max_batch, uint64_t hbm_reserve_bytes,
-                        uint32_t max_pending, cwpir_server **out);
+                        const cwpir_server_config *cfg, cwpir_server **out);
 /* Queues one query ([h][2][L][N] host memory, copied) for a target;
  * *ticket identifies it.  Non-blocking; EBUSY when max_pending is reached. */
 int cwpir_submit(cwpir_server *srv, uint32_t target, const uint64_t *query,
@@ -360,6 +438,26 @@ int cwpir_wait(cwpir_server *srv, uint64_t ticket, uint64_t *response,
 int cwpir_server_get_stats(cwpir_server *srv, cwpir_server_stats *out);
 /* Finishes the waiting requests, stops the lanes and frees the server. */
 void cwpir_server_destroy(cwpir_server *srv);
+
+/* ---- measurement ---- */
+/* Integer-pipe throughput of a device, measured (no counterpart in the
+ * paper: the denominator of the answer kernels' roofline, whose work is
+ * modular multiplication on the integer pipes).  Each rate is operations
+ * per second over all SMs, from a probe kernel of independent dependency
+ * chains on every SM (2048 threads per SM) timed with CUDA events; the
+ * multiply probes pair each multiply with one XOR, which runs on another
+ * pipe.  Takes well under a second; uses the current clocks. */
+typedef struct {
+  double imad32_per_s;   /* 32-bit multiply-add, low word (IMAD) */
+  double mulhi32_per_s;  /* high word of a 32 x 32-bit product */
+  double mullo64_per_s;  /* low 64 bits of a 64 x 64-bit product */
+  double mulhi64_per_s;  /* high 64 bits of a 64 x 64-bit product */
+  double iadd32_per_s;   /* three-input 32-bit add (IADD3) */
+  int sms;               /* streaming multiprocessors */
+  double max_sm_mhz;     /* the device's maximum SM clock */
+} cwpir_int_peaks;
+/* EINVAL for a bad device or null out; ENOMEM; ECUDA. */
+int cwpir_measure_int_peaks(int device, cwpir_int_peaks *out);
 
 /* Work counters of the last answer on ctx (for throughput accounting). */
 typedef struct {

@@ -27,7 +27,10 @@ OPT_USE_GRAPH = 3
 OPT_KERNEL_TIMING = 4
 OPT_MAX_JOBS = 5
 OPT_ROW_BASIS = 6
+OPT_MEM_LIMIT = 7
+OPT_ROW_GROUP_WAVES = 8
 K_CLASSES = 7
+EINTERNAL = -8
 
 
 class CwpirError(RuntimeError):
@@ -50,14 +53,29 @@ class _Target(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("db_id", C.c_int32), ("c", C.c_uint32)]
 
 
+class _ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_uint32), ("lanes_per_target", C.c_uint32),
+                ("max_pending", C.c_uint32), ("hbm_reserve_bytes", C.c_uint64)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
                 ("max_batch_seen", C.c_uint64), ("rejected_busy", C.c_uint64),
+                ("failed", C.c_uint64), ("max_concurrent", C.c_uint64),
                 ("busy_s", C.c_double)]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if f == "busy_s" else int(getattr(self, f)))
                 for f, _ in self._fields_}
+
+
+class IntPeaks(C.Structure):
+    _fields_ = [("imad32_per_s", C.c_double), ("mulhi32_per_s", C.c_double),
+                ("mullo64_per_s", C.c_double), ("mulhi64_per_s", C.c_double),
+                ("iadd32_per_s", C.c_double), ("sms", C.c_int), ("max_sm_mhz", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -111,18 +129,27 @@ def lib():
             "cwpir_selection": (I, [vp, C.c_int32, U32, u64p, U64, u64p, u64p]),
             "cwpir_plain_mul": (I, [vp, C.c_int32, U64, u64p, u64p]),
             "cwpir_set_option": (I, [vp, I, C.c_int64]),
+            "cwpir_get_option": (I, [vp, I, C.POINTER(C.c_int64)]),
+            "cwpir_mem_used": (I, [vp, C.POINTER(U64)]),
+            "cwpir_slot_create": (I, [vp, C.POINTER(U32)]),
+            "cwpir_answer_batch_slot": (I, [vp, U32, C.c_int32, U32, U32, vp, vp, vp]),
+            "cwpir_plan_bytes_slot": (I, [vp, U32, C.c_int32, U32, U32, C.POINTER(U64)]),
+            "cwpir_device_status": (I, [vp, U32, vp]),
+            "cwpir_inject_status": (I, [vp, U32]),
             "cwpir_last_stats": (I, [vp, C.POINTER(Stats)]),
             "cwpir_kernel_times": (I, [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "cwpir_kernel_class_name": (C.c_char_p, [I]),
             "cwpir_mul_noalloc": (I, [vp, vp, vp, vp, vp]),
+            "cwpir_measure_int_peaks": (I, [C.c_int, C.POINTER(IntPeaks)]),
             "cwpir_plan_bytes": (I, [vp, C.c_int32, U32, U32, C.POINTER(U64)]),
             "cwpir_release_plans": (I, [vp, C.c_int32]),
             "cwpir_db_shape": (I, [vp, C.c_int32, C.POINTER(U32), C.POINTER(U32),
                                    C.POINTER(U32)]),
             "cwpir_db_plaintexts": (I, [vp, C.c_int32, C.POINTER(U32)]),
             "cwpir_ctx_device": (I, [vp, C.POINTER(C.c_int)]),
-            "cwpir_server_create": (I, [C.POINTER(_Target), U32, U32, U64, U32,
+            "cwpir_server_create": (I, [C.POINTER(_Target), U32, C.POINTER(_ServerConfig),
                                         C.POINTER(vp)]),
+            "cwpir_slot_release": (I, [vp, U32]),
             "cwpir_submit": (I, [vp, U32, u64p, C.POINTER(U64)]),
             "cwpir_poll": (I, [vp, U64, u64p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
             "cwpir_wait": (I, [vp, U64, u64p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
@@ -182,6 +209,15 @@ def map_folklore(y: int, ell: int) -> np.ndarray:
     if rc:
         raise CwpirError(rc, f"folklore codeword of {y} with {ell} bits")
     return pos
+
+
+def measure_int_peaks(device: int = 0) -> dict:
+    """Measured integer-pipe rates of a device (operations per second)."""
+    p = IntPeaks()
+    rc = lib().cwpir_measure_int_peaks(device, C.byref(p))
+    if rc:
+        raise CwpirError(rc, "integer peak probe")
+    return p.as_dict()
 
 
 def code_length(n: int, k: int) -> int:
@@ -355,6 +391,48 @@ class Context:
     def set_option(self, option: int, value: int):
         self._check(lib().cwpir_set_option(self._h, option, value))
 
+    def get_option(self, option: int) -> int:
+        v = C.c_int64()
+        self._check(lib().cwpir_get_option(self._h, option, C.byref(v)))
+        return int(v.value)
+
+    def mem_used(self) -> int:
+        """Device bytes held by the context's buffers."""
+        v = C.c_uint64()
+        self._check(lib().cwpir_mem_used(self._h, C.byref(v)))
+        return int(v.value)
+
+    def slot_create(self) -> int:
+        """A new scratch slot for answers concurrent with other slots."""
+        v = C.c_uint32()
+        self._check(lib().cwpir_slot_create(self._h, C.byref(v)))
+        return int(v.value)
+
+    def answer_batch_slot(self, slot: int, db: int, nq: int, queries_ptr: int, resp_ptr: int,
+                          c: int = 0, stream: int = 0):
+        self._check(lib().cwpir_answer_batch_slot(self._h, slot, db, c, nq, queries_ptr,
+                                                  resp_ptr, stream))
+
+    def plan_bytes(self, db: int, nq: int, c: int = 0, slot: int = 0) -> int:
+        v = C.c_uint64()
+        self._check(lib().cwpir_plan_bytes_slot(self._h, slot, db, nq, c, C.byref(v)))
+        return int(v.value)
+
+    def device_status(self, slot: int = 0, stream: int = 0) -> int:
+        """Waits for `stream`, reads and clears the slot's device check flag:
+        0, or EINTERNAL (returned, not raised)."""
+        rc = lib().cwpir_device_status(self._h, slot, stream)
+        if rc not in (0, EINTERNAL):
+            self._check(rc)
+        return int(rc)
+
+    def slot_release(self, slot: int):
+        self._check(lib().cwpir_slot_release(self._h, slot))
+
+    def inject_status(self, slot: int = 0):
+        """Test hook: marks the slot's device check flag as failed."""
+        self._check(lib().cwpir_inject_status(self._h, slot))
+
     def last_stats(self) -> dict:
         s = Stats()
         self._check(lib().cwpir_last_stats(self._h, C.byref(s)))
@@ -371,18 +449,18 @@ class Context:
 
 class Server:
     """cwpir_server: continuous batching over registered (context, database,
-    c) targets."""
+    c) targets, lanes_per_target concurrent lanes each."""
 
     def __init__(self, targets, max_batch: int = 16, hbm_reserve: int = 1 << 30,
-                 max_pending: int = 4096):
+                 max_pending: int = 4096, lanes_per_target: int = 1):
         arr = (_Target * len(targets))()
         self._shapes = []
         for i, (ctx, db, c) in enumerate(targets):
             arr[i] = _Target(ctx._h, db, c)
             self._shapes.append(ctx.resp_shape(db))
+        cfg = _ServerConfig(max_batch, lanes_per_target, max_pending, hbm_reserve)
         h = C.c_void_p()
-        rc = lib().cwpir_server_create(arr, len(targets), max_batch, hbm_reserve, max_pending,
-                                       C.byref(h))
+        rc = lib().cwpir_server_create(arr, len(targets), C.byref(cfg), C.byref(h))
         if rc:
             raise CwpirError(rc, "server create")
         self._h = h

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <memory>
 #include <new>
+#include <tuple>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -34,24 +35,40 @@ thread_local std::string g_setup_error;
 // ---------------------------------------------------------------------
 // Context and database state
 // ---------------------------------------------------------------------
+// Device bytes a context holds in its buffers and the cap set by
+// CWPIR_OPT_MEM_LIMIT (0: none).  A buffer that would pass the cap is
+// refused as cudaErrorMemoryAllocation, i.e. CWPIR_ENOMEM, before any
+// cudaMalloc.
+struct MemAcct {
+  u64 used = 0, limit = 0;
+};
+
 struct DevBuf {
   u64 *p = nullptr;
   size_t n = 0;  // u64 count
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
+  MemAcct *acct = nullptr;
+  ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      if (acct) acct->used -= n * sizeof(u64);
+    }
     p = nullptr;
     n = 0;
   }
-  cudaError_t ensure(size_t count) {
+  cudaError_t ensure(size_t count, MemAcct *a) {
     if (count <= n) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
+    release();
+    acct = a;
+    if (a && a->limit && a->used + count * sizeof(u64) > a->limit)
+      return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&p, count * sizeof(u64));
-    if (e == cudaSuccess) n = count;
+    if (e == cudaSuccess) {
+      n = count;
+      if (a) a->used += count * sizeof(u64);
+    } else {
+      p = nullptr;
+    }
     return e;
   }
 };
@@ -113,11 +130,37 @@ struct Db {
   bool rows = false;
   DevBuf db;
   std::vector<uint16_t> cw;   // [n][k]
-  // answer plans over all rows, by (queries per call, compression factor)
-  std::map<std::pair<u32, u32>, std::unique_ptr<Plan>> plans;
+  // answer plans over all rows, by (queries per call, compression factor,
+  // scratch slot)
+  std::map<std::tuple<u32, u32, u32>, std::unique_ptr<Plan>> plans;
+};
+
+// Scratch of the multiplication kernels for one stream of answers at a
+// time ("slot"): answers on different slots of one context may run
+// concurrently on different streams.  Sized for c->jmax multiplications per
+// launch, the same for every slot of a context.
+struct Scratch {
+  DevBuf Tbuf, E, CP, DN;  // tensor, scaled tensor, partial products, digit transforms
+  DevBuf RS, DNQ;          // row-basis row sums and their Q-basis forms
+  DevBuf SEL;  // NTT-form selection entries [jmax][2][L][N] (rows of several plaintexts)
+  int *d_err = nullptr;    // device consistency flag of the slot's kernels
+  bool in_use = true;      // false once released (slot 0 never is)
+  ~Scratch() {
+    if (d_err) cudaFree(d_err);
+  }
+  void release() {
+    Tbuf.release();
+    E.release();
+    CP.release();
+    DN.release();
+    RS.release();
+    DNQ.release();
+    SEL.release();
+  }
 };
 
 struct cwpir_ctx {
+  MemAcct acct;  // first member: destroyed after every buffer that counts in it
   int device = 0;
   u32 N = 0, logN = 0, L = 0, K = 0;
   u64 t = 0;
@@ -136,13 +179,18 @@ struct cwpir_ctx {
   u32 opt_max_jobs = 0;
   int opt_row_basis = 1;
   cudaStream_t stream = nullptr;
-  // scratch
+  // scratch: jmax multiplications per launch (0: not sized yet), one
+  // Scratch per slot (slot 0 serves every call without a slot argument);
+  // scratch_gen counts re-sizings, so that objects holding captured graphs
+  // over a slot's buffers notice them
   u32 jmax = 0;
-  DevBuf Tbuf, E, CP, DN, exp_tau, exp_DN, exp_O, tmp_ct, io_in, io_out;
-  DevBuf RS, DNQ, one_job;  // row-basis row sums and their Q-basis forms
-  DevBuf SEL;  // NTT-form selection entries [jmax][2][L][N] (rows of several plaintexts)
+  u64 scratch_gen = 0;
+  std::vector<std::unique_ptr<Scratch>> slots;
+  // buffers of the single-step host calls
+  DevBuf exp_tau, exp_DN, exp_O, tmp_ct, io_in, io_out, one_job;
   bool capturing = false;
-  int *d_err = nullptr;
+  // serialises the slot calls, which several threads may make on one context
+  std::recursive_mutex mu;
   cw::SubJob *d_subjobs = nullptr;
   size_t n_subjobs = 0;
   cwpir_stats stats{};
@@ -156,7 +204,6 @@ struct cwpir_ctx {
   ~cwpir_ctx() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (d_tab) cudaFree(d_tab);
-    if (d_err) cudaFree(d_err);
     if (d_subjobs) cudaFree(d_subjobs);
     if (stream) cudaStreamDestroy(stream);
   }
@@ -216,6 +263,14 @@ int build_tables(cwpir_ctx *c) {
   h.L = c->L;
   h.K = c->K;
   h.t = c->t;
+  {
+    int sms = 0, thr = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    CUDA_TRY(c, cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, c->device));
+    h.sms = (u32)sms;
+    h.sm_threads = (u32)thr;
+    h.row_waves = cw::kDefaultRowWaves;
+  }
   {  // Delta = (Q - r) / t with r = Q mod t, so Delta = -r t^-1 (mod q_j)
     u64 r = 1;
     for (u64 qj : c->q) r = (u64)((u128)r * (qj % c->t) % c->t);
@@ -226,7 +281,7 @@ int build_tables(cwpir_ctx *c) {
   }
   const u32 L = c->L, K = c->K, N = c->N;
   std::vector<u64> host(4ull * L * N);
-  CUDA_TRY(c, c->twiddles.ensure(4ull * L * N));
+  CUDA_TRY(c, c->twiddles.ensure(4ull * L * N, &c->acct));
   for (u32 l = 0; l < L; ++l) {
     u64 q = c->q[l];
     u64 *tw = host.data() + 4ull * l * N;
@@ -244,7 +299,7 @@ int build_tables(cwpir_ctx *c) {
   CUDA_TRY(c, cudaMemcpy(c->twiddles.p, host.data(), host.size() * sizeof(u64),
                          cudaMemcpyHostToDevice));
   std::vector<u32> host32(4ull * K * N);
-  CUDA_TRY(c, c->twiddles32.ensure(2ull * K * N));  // 4KN 32-bit words
+  CUDA_TRY(c, c->twiddles32.ensure(2ull * K * N, &c->acct));  // 4KN 32-bit words
   u32 *d32 = reinterpret_cast<u32 *>(c->twiddles32.p);
   for (u32 k = 0; k < K; ++k) {
     const u64 p = c->p[k];
@@ -284,8 +339,8 @@ int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
   const u64 words = 2ull * c->L * c->L * c->N;
   if (!valid_residues(key, c->L, c->N, c->q, 2ull * c->L))
     return fail(c, CWPIR_EINVAL, "switching key residue out of range");
-  CUDA_TRY(c, kb.ensure(words));
-  CUDA_TRY(c, ks.ensure(words));
+  CUDA_TRY(c, kb.ensure(words, &c->acct));
+  CUDA_TRY(c, ks.ensure(words, &c->acct));
   CUDA_TRY(c, cudaMemcpy(kb.p, key, words * sizeof(u64), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cw::launch_key_prep(c->d_tab, c->h, kb.p, ks.p, 1, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -309,26 +364,54 @@ u64 dn_words(u64 L, u64 N) { return std::max<u64>((L + 2) * L, 6 * L) * N; }
 u64 rs_words(u64 L, u64 N) { return (u64)kRowGroups * 6 * L * N; }
 u64 dnq_words(u64 L, u64 N) { return (u64)kRowGroups * (L + 2) * L * N; }
 
-int ensure_scratch(cwpir_ctx *c) {
-  if (c->jmax) return CWPIR_OK;
+// Multiplications per launch of a context: as many as kScratchBytes of
+// per-job scratch allows, between 32 and kMaxJobs, at most
+// CWPIR_OPT_MAX_JOBS when set.
+u32 jobs_per_launch(const cwpir_ctx *c) {
   const u64 N = c->N, L = c->L;
   const u64 per_job =
       (3 * c->qp_poly() + (3 * L + 2 * L) * N + dn_words(L, N)) * sizeof(u64);
   u64 j = kScratchBytes / per_job;
   j = std::max<u64>(32, std::min<u64>(kMaxJobs, j));
   if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
-  c->jmax = (u32)j;
-  CUDA_TRY(c, c->Tbuf.ensure(j * 3 * c->qp_poly()));
-  CUDA_TRY(c, c->E.ensure(j * 3 * L * N));
-  CUDA_TRY(c, c->CP.ensure(j * 2 * L * N));
-  CUDA_TRY(c, c->DN.ensure(j * dn_words(L, N)));
-  CUDA_TRY(c, c->RS.ensure(rs_words(L, N)));
-  CUDA_TRY(c, c->DNQ.ensure(dnq_words(L, N)));
-  CUDA_TRY(c, c->one_job.ensure((sizeof(cw::MulJob) + 7) / 8));
-  if (!c->d_err) {
-    CUDA_TRY(c, cudaMalloc(&c->d_err, sizeof(int)));
-    CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
-  }
+  return (u32)j;
+}
+
+// A new slot (or a released one again) with its device flag cleared; its
+// buffers come with the first ensure_scratch on it.
+int add_slot(cwpir_ctx *c, u32 *id) {
+  for (u32 i = 1; i < c->slots.size(); ++i)
+    if (!c->slots[i]->in_use) {
+      CUDA_TRY(c, cudaMemset(c->slots[i]->d_err, 0, sizeof(int)));
+      c->slots[i]->in_use = true;
+      *id = i;
+      return CWPIR_OK;
+    }
+  std::unique_ptr<Scratch> S(new (std::nothrow) Scratch());
+  if (!S) return fail(c, CWPIR_ENOMEM, "host allocation");
+  CUDA_TRY(c, cudaMalloc(&S->d_err, sizeof(int)));
+  CUDA_TRY(c, cudaMemset(S->d_err, 0, sizeof(int)));
+  *id = (u32)c->slots.size();
+  c->slots.push_back(std::move(S));
+  return CWPIR_OK;
+}
+
+bool slot_ok(const cwpir_ctx *c, u32 slot) {
+  return slot < c->slots.size() && c->slots[slot]->in_use;
+}
+
+// The buffers of slot `slot` for c->jmax multiplications per launch.
+int ensure_scratch(cwpir_ctx *c, u32 slot = 0) {
+  if (!slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "unknown slot %u", slot);
+  Scratch &S = *c->slots[slot];
+  if (!c->jmax) c->jmax = jobs_per_launch(c);
+  const u64 N = c->N, L = c->L, j = c->jmax;
+  CUDA_TRY(c, S.Tbuf.ensure(j * 3 * c->qp_poly(), &c->acct));
+  CUDA_TRY(c, S.E.ensure(j * 3 * L * N, &c->acct));
+  CUDA_TRY(c, S.CP.ensure(j * 2 * L * N, &c->acct));
+  CUDA_TRY(c, S.DN.ensure(j * dn_words(L, N), &c->acct));
+  CUDA_TRY(c, S.RS.ensure(rs_words(L, N), &c->acct));
+  CUDA_TRY(c, S.DNQ.ensure(dnq_words(L, N), &c->acct));
   return CWPIR_OK;
 }
 
@@ -377,13 +460,13 @@ u32 ceil_log2(u32 k) {
 int setup_expand(cwpir_ctx *c, Plan *P) {
   const u64 ctw = c->ct();
   const u64 B = 1ull << P->cfac, inputs = (u64)P->nq * P->h_in;
-  CUDA_TRY(c, P->exp_a.ensure(inputs * B * ctw));
-  CUDA_TRY(c, P->exp_b.ensure(inputs * B * ctw));
-  CUDA_TRY(c, P->exp_tau.ensure(inputs * (B / 2) * ctw));
-  CUDA_TRY(c, P->exp_S.ensure(inputs * (B / 2) * ctw));
-  CUDA_TRY(c, P->exp_O.ensure(inputs * (B / 2) * ctw));
-  CUDA_TRY(c, P->exp_DN.ensure(inputs * (B / 2) * (c->L + 1) * c->L * c->N));
-  CUDA_TRY(c, P->leaves_coef.ensure((u64)P->nq * P->m * ctw));
+  CUDA_TRY(c, P->exp_a.ensure(inputs * B * ctw, &c->acct));
+  CUDA_TRY(c, P->exp_b.ensure(inputs * B * ctw, &c->acct));
+  CUDA_TRY(c, P->exp_tau.ensure(inputs * (B / 2) * ctw, &c->acct));
+  CUDA_TRY(c, P->exp_S.ensure(inputs * (B / 2) * ctw, &c->acct));
+  CUDA_TRY(c, P->exp_O.ensure(inputs * (B / 2) * ctw, &c->acct));
+  CUDA_TRY(c, P->exp_DN.ensure(inputs * (B / 2) * (c->L + 1) * c->L * c->N, &c->acct));
+  CUDA_TRY(c, P->leaves_coef.ensure((u64)P->nq * P->m * ctw, &c->acct));
   std::vector<cw::SubJob> sj;
   u64 *cur = P->exp_a.p, *nxt = P->exp_b.p;
   for (u32 a = 0; a < P->cfac; ++a) {
@@ -403,7 +486,7 @@ int setup_expand(cwpir_ctx *c, Plan *P) {
 // Plan over `rows` for nq query slots with compression factor cfac.
 // root_mode ROOT_PM (answers into the plan's accumulators) or ROOT_SEL
 // (nq = 1; selection entries in coefficient form to sel_out, [rows][2][L][N]).
-int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 cfac,
+int build_plan(cwpir_ctx *c, u32 slot, Db *db, const std::vector<u64> &rows, u32 nq, u32 cfac,
                int root_mode, u64 *sel_out, bool memo_opt, std::unique_ptr<Plan> &out) {
   std::unique_ptr<Plan> P(new Plan());
   const u32 k = db->k, m = db->m;
@@ -417,16 +500,16 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
   P->h_in = db->folklore ? m / 2 : cfac ? (m + (1u << cfac) - 1) >> cfac : m;
   P->sp = db->sp;
   P->rows_db = db->rows;
-  if (db->folklore) CUDA_TRY(c, P->leaves_coef.ensure((u64)nq * m * ctw));
+  if (db->folklore) CUDA_TRY(c, P->leaves_coef.ensure((u64)nq * m * ctw, &c->acct));
   const u32 J = c->jmax;
   if (root_mode == cw::ROOT_PM && (u64)nq * db->sp > J)
     return fail(c, CWPIR_EINVAL, "%u queries x %u plaintexts per row need more than %u partial "
                 "sums per launch (raise CWPIR_OPT_MAX_JOBS)", nq, db->sp, J);
-  if (db->sp > 1 && k > 1) CUDA_TRY(c, c->SEL.ensure((u64)J * ctw));
-  CUDA_TRY(c, P->leaves.ensure((u64)nq * m * qp));
-  CUDA_TRY(c, P->acc.ensure((u64)nq * db->sp * ctw));
-  CUDA_TRY(c, P->q_in.ensure((u64)nq * P->h_in * ctw));
-  CUDA_TRY(c, P->resp.ensure((u64)nq * db->sp * ctw));
+  if (db->sp > 1 && k > 1) CUDA_TRY(c, c->slots[slot]->SEL.ensure((u64)J * ctw, &c->acct));
+  CUDA_TRY(c, P->leaves.ensure((u64)nq * m * qp, &c->acct));
+  CUDA_TRY(c, P->acc.ensure((u64)nq * db->sp * ctw, &c->acct));
+  CUDA_TRY(c, P->q_in.ensure((u64)nq * P->h_in * ctw, &c->acct));
+  CUDA_TRY(c, P->resp.ensure((u64)nq * db->sp * ctw, &c->acct));
 
   if (cfac) {
     int rc = setup_expand(c, P.get());
@@ -466,7 +549,7 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
         }
       }
       P->n_memo = Bd.n_memo = pairs.size();
-      CUDA_TRY(c, P->memo_buf.ensure(std::max<u64>(1, (u64)nq * P->n_memo) * qp));
+      CUDA_TRY(c, P->memo_buf.ensure(std::max<u64>(1, (u64)nq * P->n_memo) * qp, &c->acct));
       Bd.memo_base = P->memo_buf.p;
       std::vector<cw::MulJob> mj;
       for (u32 s = 0; s < nq; ++s)
@@ -501,7 +584,7 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
       Bd.level_off[l] = lvl_cts;
       lvl_cts += (u64)nq * rpb * Bd.level_nodes[l];
     }
-    CUDA_TRY(c, P->level_buf.ensure(std::max<u64>(1, lvl_cts) * qp));
+    CUDA_TRY(c, P->level_buf.ensure(std::max<u64>(1, lvl_cts) * qp, &c->acct));
     Bd.level_base = P->level_buf.p;
     for (u64 x = 0; x < rows.size(); x += rpb) {
       u64 cnt = std::min<u64>(rpb, rows.size() - x);
@@ -540,27 +623,28 @@ int build_plan(cwpir_ctx *c, Db *db, const std::vector<u64> &rows, u32 nq, u32 c
 
 // One chunk of multiplications: tensor, scale-down, relinearisation and
 // the consumer of the result.
-int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream_t st) {
+int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp,
+              cudaStream_t st) {
   const cw::MulJob *jobs = P->d_jobs + ch.off;
   if (P->leaf_root) {
-    CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] { return cw::launch_pm_leaf(c->d_tab, c->h, jobs, ch.count, P->sp, dbp, c->CP.p, st); }));
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, ch.count / ch.segs, P->sp, P->acc.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] { return cw::launch_pm_leaf(c->d_tab, c->h, jobs, ch.count, P->sp, dbp, S.CP.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, S.CP.p, ch.segs, ch.count / ch.segs, P->sp, P->acc.p, st); }));
     c->stats.kernel_launches += 2;
     c->stats.db_bytes_read += (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
     return CWPIR_OK;
   }
-  CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, c->Tbuf.p, st); }));
-  CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, c->Tbuf.p, ch.count, c->E.p, c->d_err, st); }));
+  CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, S.Tbuf.p, st); }));
+  CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, S.Tbuf.p, ch.count, S.E.p, S.d_err, st); }));
   const bool rows = ch.mode == cw::ROOT_PM && P->rows_db;
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
     if (rows)
-      return cw::launch_relin_rows(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, c->rlk.p,
+      return cw::launch_relin_rows(c->d_tab, c->h, S.E.p, ch.count, ch.segs, jobs, c->rlk.p,
                                    c->rlk_s.p, reinterpret_cast<const u32 *>(dbp), kRowGroups,
-                                   reinterpret_cast<u32 *>(c->DN.p),
-                                   reinterpret_cast<u32 *>(c->RS.p), c->DNQ.p, c->d_err,
-                                   c->CP.p, st);
-    return cw::launch_relin(c->d_tab, c->h, c->E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
-                            c->rlk_s.p, dbp, P->sp, c->jmax, c->DN.p, c->SEL.p, c->CP.p, st);
+                                   reinterpret_cast<u32 *>(S.DN.p),
+                                   reinterpret_cast<u32 *>(S.RS.p), S.DNQ.p, S.d_err,
+                                   S.CP.p, st);
+    return cw::launch_relin(c->d_tab, c->h, S.E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
+                            c->rlk_s.p, dbp, P->sp, c->jmax, S.DN.p, S.SEL.p, S.CP.p, st);
   }));
   c->stats.kernel_launches += 3;  // tensor (ciphertext and extension limbs), scale-down
   c->stats.mults += ch.count;
@@ -579,7 +663,7 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
     c->stats.ntt_polys += (u64)ch.count * c->L * (c->L + 2);
   }
   if (ch.mode == cw::INTERNAL) {
-    CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, c->CP.p, jobs, ch.count, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, S.CP.p, jobs, ch.count, st); }));
     CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_p(c->d_tab, c->h, jobs, ch.count, st); }));
     c->stats.kernel_launches += 3;  // inverse NTT, lift, P-limb NTT
     c->stats.ntt_polys += (u64)ch.count * (2 * c->L + 2 * c->K);
@@ -587,7 +671,7 @@ int run_chunk(cwpir_ctx *c, Plan *P, const Chunk &ch, const u64 *dbp, cudaStream
     const u32 seg_len = ch.count / ch.segs;
     const u32 groups = rows ? cw::relin_rows_groups(c->h, ch.segs, seg_len, kRowGroups)
                             : cw::relin_pm_groups(c->h, ch.segs, seg_len, P->sp, c->jmax);
-    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, c->CP.p, ch.segs, groups, P->sp, P->acc.p, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_ACC, st, [&] { return cw::launch_accumulate(c->h, c->d_tab, S.CP.p, ch.segs, groups, P->sp, P->acc.p, st); }));
     c->stats.kernel_launches += 1;
     c->stats.db_bytes_read += rows ? (u64)ch.count * c->h.rows.nr * c->N * sizeof(u32)
                                    : (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
@@ -668,12 +752,17 @@ int prep_leaves(cwpir_ctx *c, const u64 *coef, u32 count, u64 *dst, cudaStream_t
   return CWPIR_OK;
 }
 
-int check_err_flag(cwpir_ctx *c) {
+// Reads and clears the device consistency flag of a slot (after the work
+// that sets it is complete): CWPIR_EINTERNAL if a check failed.
+int check_err_flag(cwpir_ctx *c, u32 slot = 0) {
+  if (!slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "unknown slot %u", slot);
+  int *flag = c->slots[slot]->d_err;
   int h = 0;
-  CUDA_TRY(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
-    CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
-    return fail(c, CWPIR_EINTERNAL, "device consistency check failed (scale-down or row-basis rounding)");
+    CUDA_TRY(c, cudaMemset(flag, 0, sizeof(int)));
+    return fail(c, CWPIR_EINTERNAL,
+                "device consistency check failed (scale-down or row-basis rounding)");
   }
   return CWPIR_OK;
 }
@@ -703,7 +792,7 @@ int leaf_coefs(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, cudaStream_t s
 
 // The whole answer of a plan: expansion, leaves, tree, accumulation and the
 // final inverse transform into d_resp ([nq][sp][2][L][N]).  Capturable.
-int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_resp,
+int enqueue_answer(cwpir_ctx *c, Scratch &S, Db *db, Plan *P, const u64 *d_query, u64 *d_resp,
                    cudaStream_t st) {
   int rc;
   const u64 *coef;
@@ -711,10 +800,10 @@ int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_res
   if ((rc = prep_leaves(c, coef, P->nq * P->m, P->leaves.p, st))) return rc;
   CUDA_TRY(c, cudaMemsetAsync(P->acc.p, 0, (u64)P->nq * P->sp * c->ct() * sizeof(u64), st));
   for (const Chunk &ch : P->memo_chunks)
-    if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
+    if ((rc = run_chunk(c, S, P, ch, db->db.p, st))) return rc;
   for (const auto &batch : P->batches)
     for (const Chunk &ch : batch)
-      if ((rc = run_chunk(c, P, ch, db->db.p, st))) return rc;
+      if ((rc = run_chunk(c, S, P, ch, db->db.p, st))) return rc;
   CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] {
     return cw::launch_ntt(c->d_tab, c->h, d_resp, 2 * P->nq * P->sp, (u64)c->L * c->N, 0, c->L,
                           true, P->acc.p, (u64)c->L * c->N, st);
@@ -725,17 +814,18 @@ int enqueue_answer(cwpir_ctx *c, Db *db, Plan *P, const u64 *d_query, u64 *d_res
   return CWPIR_OK;
 }
 
-// The cached all-rows plan of a database for (nq, cfac).
-int get_plan(cwpir_ctx *c, Db *db, u32 nq, u32 cfac, Plan **out) {
-  int rc = ensure_scratch(c);
+// The cached all-rows plan of a database for (nq, cfac) on a slot.
+int get_plan(cwpir_ctx *c, u32 slot, Db *db, u32 nq, u32 cfac, Plan **out) {
+  int rc = ensure_scratch(c, slot);
   if (rc) return rc;
-  auto key = std::make_pair(nq, cfac);
+  auto key = std::make_tuple(nq, cfac, slot);
   auto it = db->plans.find(key);
   if (it == db->plans.end()) {
     std::vector<u64> rows(db->n);
     for (u64 i = 0; i < db->n; ++i) rows[i] = i;
     std::unique_ptr<Plan> P;
-    if ((rc = build_plan(c, db, rows, nq, cfac, cw::ROOT_PM, nullptr, c->opt_share != 0, P)))
+    if ((rc = build_plan(c, slot, db, rows, nq, cfac, cw::ROOT_PM, nullptr, c->opt_share != 0,
+                         P)))
       return rc;
     it = db->plans.emplace(key, std::move(P)).first;
   }
@@ -743,38 +833,45 @@ int get_plan(cwpir_ctx *c, Db *db, u32 nq, u32 cfac, Plan **out) {
   return CWPIR_OK;
 }
 
-// Answers nq queries (d_query: [nq][h_in] cts) into d_resp ([nq][sp][2][L][N]).
-// With CWPIR_OPT_USE_GRAPH the plan's sequence is captured once into a
-// CUDA graph (on the context's stream) and replayed on `st`, staging the
-// queries and responses through the plan's fixed buffers.
-int answer_batch_enqueue(cwpir_ctx *c, Db *db, u32 cfac, u32 nq, const u64 *d_query,
+// Captures a plan's whole answer (from its staging buffers q_in to resp)
+// into a CUDA graph on the context's stream.
+int capture_plan(cwpir_ctx *c, Scratch &S, Db *db, Plan *P) {
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  cudaGraph_t g = nullptr;
+  c->capturing = true;
+  int rc = CWPIR_OK;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = enqueue_answer(c, S, db, P, P->q_in.p, P->resp.p, c->stream);
+    e = cudaStreamEndCapture(c->stream, &g);
+  }
+  c->capturing = false;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, CWPIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  P->graph_stats = c->stats;
+  return CWPIR_OK;
+}
+
+// Answers nq queries (d_query: [nq][h_in] cts) into d_resp ([nq][sp][2][L][N])
+// with the scratch of `slot`.  With CWPIR_OPT_USE_GRAPH the plan's sequence
+// is captured once into a CUDA graph (on the context's stream) and replayed
+// on `st`, staging the queries and responses through the plan's fixed
+// buffers.
+int answer_batch_enqueue(cwpir_ctx *c, u32 slot, Db *db, u32 cfac, u32 nq, const u64 *d_query,
                          u64 *d_resp, cudaStream_t st) {
   Plan *P;
-  int rc = get_plan(c, db, nq, cfac, &P);
+  int rc = get_plan(c, slot, db, nq, cfac, &P);
   if (rc) return rc;
+  Scratch &S = *c->slots[slot];
   c->stats = cwpir_stats{};
-  if (!c->opt_graph) return enqueue_answer(c, db, P, d_query, d_resp, st);
+  if (!c->opt_graph) return enqueue_answer(c, S, db, P, d_query, d_resp, st);
   const u64 ctw = c->ct();
-  if (!P->graph) {
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    cudaGraph_t g = nullptr;
-    c->capturing = true;
-    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      rc = enqueue_answer(c, db, P, P->q_in.p, P->resp.p, c->stream);
-      e = cudaStreamEndCapture(c->stream, &g);
-    }
-    c->capturing = false;
-    if (rc) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess)
-      return fail(c, CWPIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    P->graph_stats = c->stats;
-  }
+  if (!P->graph && (rc = capture_plan(c, S, db, P))) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(P->q_in.p, d_query, (u64)nq * P->h_in * ctw * sizeof(u64),
                               cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(c, cudaGraphLaunch(P->graph, st));
@@ -929,6 +1026,8 @@ int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys, cwpir_ctx **
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(nullptr, CWPIR_ECUDA, "stream: %s", cudaGetErrorString(e));
   int rc = build_tables(c.get());
+  u32 slot0 = 0;
+  if (!rc) rc = add_slot(c.get(), &slot0);
   if (rc) {
     g_setup_error = c->err;
     return rc;
@@ -999,7 +1098,7 @@ static int load_db_impl(cwpir_ctx *c, uint64_t n, uint32_t plen, uint32_t k, uin
   db->rows = c->opt_row_basis && db->sp == 1 && k >= 2;
   // u64 words per row: [4][N] u32 in the row basis, [sp][L][N] otherwise
   const u64 row_words = db->rows ? (u64)c->h.rows.nr * c->N / 2 : (u64)db->sp * c->L * c->N;
-  CUDA_TRY(c, db->db.ensure(n * row_words));
+  CUDA_TRY(c, db->db.ensure(n * row_words, &c->acct));
   // upload rows in chunks and transform
   const u64 chunk_rows = std::max<u64>(1, (256ull << 20) / (std::max<u32>(plen, 1) * 4ull));
   uint32_t *d_items = nullptr;
@@ -1084,18 +1183,73 @@ int cwpir_query_cts(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t *h) {
   return CWPIR_OK;
 }
 
-int cwpir_answer_batch_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
-                              const uint64_t *d_queries, uint64_t *d_responses, void *stream) {
+int cwpir_answer_batch_slot(cwpir_ctx *c, uint32_t slot, int32_t db_id, uint32_t cfac,
+                            uint32_t nq, const uint64_t *d_queries, uint64_t *d_responses,
+                            void *stream) {
   if (!c) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   c->err.clear();
   cudaSetDevice(c->device);
+  if (!slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "unknown slot %u", slot);
   Db *db = get_db(c, db_id);
   if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
   if (!d_queries || !d_responses || nq == 0) return fail(c, CWPIR_EINVAL, "null buffer or nq = 0");
   u64 h;
   int rc = query_shape(c, db, cfac, &h);
   if (rc || (rc = check_keys(c, cfac))) return rc;
-  return answer_batch_enqueue(c, db, cfac, nq, d_queries, d_responses, (cudaStream_t)stream);
+  return answer_batch_enqueue(c, slot, db, cfac, nq, d_queries, d_responses,
+                              (cudaStream_t)stream);
+}
+
+int cwpir_answer_batch_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
+                              const uint64_t *d_queries, uint64_t *d_responses, void *stream) {
+  return cwpir_answer_batch_slot(c, 0, db_id, cfac, nq, d_queries, d_responses, stream);
+}
+
+int cwpir_slot_create(cwpir_ctx *c, uint32_t *slot) {
+  if (!c || !slot) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return add_slot(c, slot);
+}
+
+int cwpir_slot_release(cwpir_ctx *c, uint32_t slot) {
+  if (!c) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->err.clear();
+  if (slot == 0 || !slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "slot %u cannot be released", slot);
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaDeviceSynchronize());
+  for (auto &kv : c->dbs)
+    for (auto it = kv.second->plans.begin(); it != kv.second->plans.end();)
+      it = std::get<2>(it->first) == slot ? kv.second->plans.erase(it) : std::next(it);
+  c->slots[slot]->release();
+  c->slots[slot]->in_use = false;
+  return CWPIR_OK;
+}
+
+int cwpir_device_status(cwpir_ctx *c, uint32_t slot, void *stream) {
+  if (!c) return CWPIR_EINVAL;
+  cudaSetDevice(c->device);
+  // the wait comes before the context lock, so that other threads keep
+  // enqueueing on their slots meanwhile
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->err.clear();
+  if (e != cudaSuccess) return fail(c, CWPIR_ECUDA, "stream: %s", cudaGetErrorString(e));
+  if (!slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "unknown slot %u", slot);
+  return check_err_flag(c, slot);
+}
+
+int cwpir_inject_status(cwpir_ctx *c, uint32_t slot) {
+  if (!c) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (!slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "unknown slot %u", slot);
+  const int one = 1;
+  CUDA_TRY(c, cudaMemcpy(c->slots[slot]->d_err, &one, sizeof one, cudaMemcpyHostToDevice));
+  return CWPIR_OK;
 }
 
 int cwpir_answer_device(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *d_query,
@@ -1117,11 +1271,11 @@ int cwpir_answer_batch(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
   if (!valid_residues(queries, c->L, c->N, c->q, 2 * h * nq))
     return fail(c, CWPIR_EINVAL, "query residue out of range");
   const u64 ctw = c->ct();
-  CUDA_TRY(c, c->io_in.ensure(h * nq * ctw));
-  CUDA_TRY(c, c->io_out.ensure((u64)nq * db->sp * ctw));
+  CUDA_TRY(c, c->io_in.ensure(h * nq * ctw, &c->acct));
+  CUDA_TRY(c, c->io_out.ensure((u64)nq * db->sp * ctw, &c->acct));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, queries, h * nq * ctw * sizeof(u64),
                               cudaMemcpyHostToDevice, c->stream));
-  rc = answer_batch_enqueue(c, db, cfac, nq, c->io_in.p, c->io_out.p, c->stream);
+  rc = answer_batch_enqueue(c, 0, db, cfac, nq, c->io_in.p, c->io_out.p, c->stream);
   if (rc) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(responses, c->io_out.p, (u64)nq * db->sp * ctw * sizeof(u64),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -1207,9 +1361,9 @@ int cwpir_mul(cwpir_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out)
   int rc = ensure_scratch(c);
   if (rc) return rc;
   const u64 ctw = c->ct(), qp = c->qp_ct();
-  CUDA_TRY(c, c->io_in.ensure(2 * ctw));
-  CUDA_TRY(c, c->io_out.ensure(ctw));
-  CUDA_TRY(c, c->tmp_ct.ensure(2 * qp));
+  CUDA_TRY(c, c->io_in.ensure(2 * ctw, &c->acct));
+  CUDA_TRY(c, c->io_out.ensure(ctw, &c->acct));
+  CUDA_TRY(c, c->tmp_ct.ensure(2 * qp, &c->acct));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, a, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p + ctw, b, ctw * sizeof(u64), cudaMemcpyHostToDevice,
                               c->stream));
@@ -1218,7 +1372,8 @@ int cwpir_mul(cwpir_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out)
   cw::MulJob job{c->tmp_ct.p, c->tmp_ct.p + qp, c->io_out.p, 0};
   CUDA_TRY(c, cudaMalloc(&P.d_jobs, sizeof job));
   CUDA_TRY(c, cudaMemcpy(P.d_jobs, &job, sizeof job, cudaMemcpyHostToDevice));
-  if ((rc = run_chunk(c, &P, Chunk{0, 1, cw::ROOT_SEL, 1}, nullptr, c->stream))) return rc;
+  if ((rc = run_chunk(c, *c->slots[0], &P, Chunk{0, 1, cw::ROOT_SEL, 1}, nullptr, c->stream)))
+    return rc;
   CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return check_err_flag(c);
@@ -1233,11 +1388,11 @@ int cwpir_substitute(cwpir_ctx *c, uint32_t g, const uint64_t *ct, uint64_t *out
   if (!key) return fail(c, CWPIR_ENOKEY, "no Galois key for element %u", g);
   if (!valid_residues(ct, c->L, c->N, c->q, 2)) return fail(c, CWPIR_EINVAL, "residue out of range");
   const u64 ctw = c->ct();
-  CUDA_TRY(c, c->io_in.ensure(ctw));
-  CUDA_TRY(c, c->io_out.ensure(ctw));
-  CUDA_TRY(c, c->exp_tau.ensure(ctw));
-  CUDA_TRY(c, c->exp_DN.ensure((u64)(c->L + 1) * c->L * c->N));
-  CUDA_TRY(c, c->exp_O.ensure(ctw));
+  CUDA_TRY(c, c->io_in.ensure(ctw, &c->acct));
+  CUDA_TRY(c, c->io_out.ensure(ctw, &c->acct));
+  CUDA_TRY(c, c->exp_tau.ensure(ctw, &c->acct));
+  CUDA_TRY(c, c->exp_DN.ensure((u64)(c->L + 1) * c->L * c->N, &c->acct));
+  CUDA_TRY(c, c->exp_O.ensure(ctw, &c->acct));
   int rc = ensure_subjobs(c, 1);
   if (rc) return rc;
   cw::SubJob sj{c->io_in.p, c->io_out.p};
@@ -1261,8 +1416,8 @@ int cwpir_expand(cwpir_ctx *c, uint32_t cfac, uint32_t m, const uint64_t *query,
     return fail(c, CWPIR_EINVAL, "need 1 <= c <= log2 N and 1 <= m <= 16384");
   const u64 h = (m + (1u << cfac) - 1) >> cfac, ctw = c->ct();
   if (!valid_residues(query, c->L, c->N, c->q, 2 * h)) return fail(c, CWPIR_EINVAL, "residue out of range");
-  CUDA_TRY(c, c->io_in.ensure(h * ctw));
-  CUDA_TRY(c, c->io_out.ensure((u64)m * ctw));
+  CUDA_TRY(c, c->io_in.ensure(h * ctw, &c->acct));
+  CUDA_TRY(c, c->io_out.ensure((u64)m * ctw, &c->acct));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
                               c->stream));
   int rc = check_keys(c, cfac);
@@ -1296,14 +1451,14 @@ int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *
   if (!valid_residues(query, c->L, c->N, c->q, 2 * h)) return fail(c, CWPIR_EINVAL, "residue out of range");
   if ((rc = ensure_scratch(c))) return rc;
   const u64 ctw = c->ct();
-  CUDA_TRY(c, c->io_in.ensure(h * ctw));
-  CUDA_TRY(c, c->io_out.ensure(count * ctw));
+  CUDA_TRY(c, c->io_in.ensure(h * ctw, &c->acct));
+  CUDA_TRY(c, c->io_out.ensure(count * ctw, &c->acct));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, query, h * ctw * sizeof(u64), cudaMemcpyHostToDevice,
                               c->stream));
   if ((rc = check_keys(c, cfac))) return rc;
   std::vector<u64> rv(rows, rows + count);
   std::unique_ptr<Plan> P;
-  if ((rc = build_plan(c, db, rv, 1, cfac, cw::ROOT_SEL, c->io_out.p, c->opt_share != 0, P)))
+  if ((rc = build_plan(c, 0, db, rv, 1, cfac, cw::ROOT_SEL, c->io_out.p, c->opt_share != 0, P)))
     return rc;
   const u64 *coef;
   if ((rc = leaf_coefs(c, db, P.get(), c->io_in.p, c->stream, &coef))) return rc;
@@ -1317,10 +1472,10 @@ int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *
   }
   if ((rc = prep_leaves(c, coef, db->m, P->leaves.p, c->stream))) return rc;
   for (const Chunk &ch : P->memo_chunks)
-    if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
+    if ((rc = run_chunk(c, *c->slots[0], P.get(), ch, nullptr, c->stream))) return rc;
   for (const auto &batch : P->batches)
     for (const Chunk &ch : batch)
-      if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
+      if ((rc = run_chunk(c, *c->slots[0], P.get(), ch, nullptr, c->stream))) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, count * ctw * sizeof(u64), cudaMemcpyDeviceToHost,
                               c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1334,12 +1489,12 @@ static int product_rows(cwpir_ctx *c, Db &d, const u64 *coef, u64 *out) {
   std::vector<u64> rv(d.n);
   for (u64 i = 0; i < d.n; ++i) rv[i] = i;
   std::unique_ptr<Plan> P;
-  int rc = build_plan(c, &d, rv, 1, 0, cw::ROOT_SEL, out, false, P);
+  int rc = build_plan(c, 0, &d, rv, 1, 0, cw::ROOT_SEL, out, false, P);
   if (rc) return rc;
   if ((rc = prep_leaves(c, coef, d.m, P->leaves.p, c->stream))) return rc;
   for (const auto &batch : P->batches)
     for (const Chunk &ch : batch)
-      if ((rc = run_chunk(c, P.get(), ch, nullptr, c->stream))) return rc;
+      if ((rc = run_chunk(c, *c->slots[0], P.get(), ch, nullptr, c->stream))) return rc;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return check_err_flag(c);
 }
@@ -1361,9 +1516,9 @@ int cwpir_arith_cw_eq(cwpir_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
   // leaves x_0 .. x_{m-1}, y_0 .. y_{m-1}; then m products, their sum, the
   // k factors and their product
   DevBuf leaves, prods, fac;
-  CUDA_TRY(c, leaves.ensure(2ull * m * ctw));
-  CUDA_TRY(c, prods.ensure((u64)m * ctw));
-  CUDA_TRY(c, fac.ensure((u64)(k + 2) * ctw));
+  CUDA_TRY(c, leaves.ensure(2ull * m * ctw, &c->acct));
+  CUDA_TRY(c, prods.ensure((u64)m * ctw, &c->acct));
+  CUDA_TRY(c, fac.ensure((u64)(k + 2) * ctw, &c->acct));
   CUDA_TRY(c, cudaMemcpyAsync(leaves.p, x, (u64)m * ctw * sizeof(u64), cudaMemcpyHostToDevice,
                               c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(leaves.p + (u64)m * ctw, y, (u64)m * ctw * sizeof(u64),
@@ -1413,20 +1568,22 @@ int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *c
   if (!ct || !out || row >= db->n) return fail(c, CWPIR_EINVAL, "null buffer or row out of range");
   if (!valid_residues(ct, c->L, c->N, c->q, 2)) return fail(c, CWPIR_EINVAL, "residue out of range");
   const u64 ctw = c->ct(), LN = (u64)c->L * c->N, sp = db->sp;
-  CUDA_TRY(c, c->io_in.ensure(sp * ctw));
-  CUDA_TRY(c, c->io_out.ensure(sp * ctw));
-  CUDA_TRY(c, c->tmp_ct.ensure(ctw));
+  CUDA_TRY(c, c->io_in.ensure(sp * ctw, &c->acct));
+  CUDA_TRY(c, c->io_out.ensure(sp * ctw, &c->acct));
+  CUDA_TRY(c, c->tmp_ct.ensure(ctw, &c->acct));
   CUDA_TRY(c, cudaMemcpyAsync(c->io_in.p, ct, ctw * sizeof(u64), cudaMemcpyHostToDevice, c->stream));
   if (db->rows) {  // the exact integer product in the row basis, back to each q_j
     int rc = ensure_scratch(c);
     if (rc) return rc;
+    Scratch &S = *c->slots[0];
+    CUDA_TRY(c, c->one_job.ensure((sizeof(cw::MulJob) + 7) / 8, &c->acct));
     const cw::MulJob job{nullptr, nullptr, nullptr, row};
     CUDA_TRY(c, cudaMemcpyAsync(c->one_job.p, &job, sizeof job, cudaMemcpyHostToDevice,
                                 c->stream));
     CUDA_TRY(c, cw::launch_plain_mul_rows(
                     c->d_tab, c->h, c->io_in.p, reinterpret_cast<const cw::MulJob *>(c->one_job.p),
-                    reinterpret_cast<const u32 *>(db->db.p), reinterpret_cast<u32 *>(c->DN.p),
-                    reinterpret_cast<u32 *>(c->RS.p), c->d_err, c->io_out.p, c->stream));
+                    reinterpret_cast<const u32 *>(db->db.p), reinterpret_cast<u32 *>(S.DN.p),
+                    reinterpret_cast<u32 *>(S.RS.p), S.d_err, c->io_out.p, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(out, c->io_out.p, ctw * sizeof(u64), cudaMemcpyDeviceToHost,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1469,30 +1626,31 @@ int cwpir_ctx_device(const cwpir_ctx *c, int *device) {
   return CWPIR_OK;
 }
 
-int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
-                     uint64_t *bytes) {
+int cwpir_plan_bytes_slot(cwpir_ctx *c, uint32_t slot, int32_t db_id, uint32_t nq,
+                          uint32_t cfac, uint64_t *bytes) {
   if (!c || !bytes || !nq) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  if (!slot_ok(c, slot)) return fail(c, CWPIR_EINVAL, "unknown slot %u", slot);
   Db *db = get_db(c, db_id);
   if (!db) return fail(c, CWPIR_ENODB, "unknown database %d", db_id);
-  if (db->plans.count(std::make_pair(nq, cfac))) {
+  if (db->plans.count(std::make_tuple(nq, cfac, slot))) {
     *bytes = 0;
     return CWPIR_OK;
   }
   const u64 N = c->N, L = c->L, qp = c->qp_ct(), ctw = c->ct();
+  const u64 J = c->jmax ? c->jmax : jobs_per_launch(c);
+  const Scratch &S = *c->slots[slot];
   u64 w = 0;
-  if (!c->jmax) {  // the context's scratch comes first
+  if (!S.Tbuf.n) {  // the slot's scratch comes first
     const u64 per_job = 3 * c->qp_poly() + (3 * L + 2 * L) * N + dn_words(L, N);
-    u64 j = std::max<u64>(32, std::min<u64>(kMaxJobs, kScratchBytes / (per_job * 8)));
-    if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
-    w += j * per_job + rs_words(L, N) + dnq_words(L, N);
+    w += J * per_job + rs_words(L, N) + dnq_words(L, N);
   }
-  const u64 J = c->jmax ? c->jmax : kMaxJobs;
   const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();
   const bool memo = c->opt_share && top >= 2;
   const u64 h = db->folklore ? db->m / 2 : cfac ? (db->m + (1u << cfac) - 1) >> cfac : db->m;
   w += (u64)nq * db->m * qp + 2ull * nq * db->sp * ctw + (u64)nq * h * ctw;
   if (db->folklore) w += (u64)nq * db->m * ctw;
-  if (db->sp > 1 && db->k > 1 && c->SEL.n < J * ctw) w += J * ctw;
+  if (db->sp > 1 && db->k > 1 && S.SEL.n < J * ctw) w += J * ctw;
   if (memo) w += (u64)nq * db->n_pairs * qp;
   u64 widest = 1, internal_nodes = 0;
   for (u32 l = memo ? 2 : 1; l <= top; ++l) {
@@ -1511,8 +1669,14 @@ int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
   return CWPIR_OK;
 }
 
+int cwpir_plan_bytes(cwpir_ctx *c, int32_t db_id, uint32_t nq, uint32_t cfac,
+                     uint64_t *bytes) {
+  return cwpir_plan_bytes_slot(c, 0, db_id, nq, cfac, bytes);
+}
+
 int cwpir_release_plans(cwpir_ctx *c, int32_t db_id) {
   if (!c) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
@@ -1526,21 +1690,28 @@ int cwpir_release_plans(cwpir_ctx *c, int32_t db_id) {
   return CWPIR_OK;
 }
 
+// Waits for the device and drops every cached plan (their graphs and job
+// lists depend on the option being changed).
+static void drop_plans(cwpir_ctx *c) {
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
+  for (auto &kv : c->dbs) kv.second->plans.clear();
+}
+
 int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
   if (!c) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   switch (option) {
     case CWPIR_OPT_SHARE_LEVEL1:
-      cudaSetDevice(c->device);
-      cudaDeviceSynchronize();
+      drop_plans(c);
       c->opt_share = value ? 1 : 0;
-      for (auto &kv : c->dbs) kv.second->plans.clear();
       return CWPIR_OK;
     case CWPIR_OPT_BATCH_ROWS:
-      if (value < 0) return fail(c, CWPIR_EINVAL, "batch rows must be >= 0");
-      cudaSetDevice(c->device);
-      cudaDeviceSynchronize();
+      if (value < 0 || value > 0xffffffffll)
+        return fail(c, CWPIR_EINVAL, "batch rows must be in [0, 2^32)");
+      drop_plans(c);
       c->opt_batch_rows = (u32)value;
-      for (auto &kv : c->dbs) kv.second->plans.clear();
       return CWPIR_OK;
     case CWPIR_OPT_USE_GRAPH:
       c->opt_graph = value ? 1 : 0;
@@ -1550,20 +1721,45 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
     case CWPIR_OPT_MAX_JOBS:
       if (value < 0 || value > (int64_t)kMaxJobs)
         return fail(c, CWPIR_EINVAL, "max jobs must be in [0, %llu]", (unsigned long long)kMaxJobs);
-      cudaSetDevice(c->device);
-      cudaStreamSynchronize(c->stream);
-      cudaDeviceSynchronize();
+      drop_plans(c);
       c->opt_max_jobs = (u32)value;
       c->jmax = 0;  // scratch is re-sized on the next call that needs it
-      c->Tbuf.release();
-      c->E.release();
-      c->CP.release();
-      c->DN.release();
-      c->SEL.release();
-      for (auto &kv : c->dbs) kv.second->plans.clear();
+      for (auto &S : c->slots) S->release();
+      c->scratch_gen += 1;
+      return CWPIR_OK;
+    case CWPIR_OPT_MEM_LIMIT:
+      if (value < 0) return fail(c, CWPIR_EINVAL, "memory limit must be >= 0");
+      c->acct.limit = (u64)value;
+      return CWPIR_OK;
+    case CWPIR_OPT_ROW_GROUP_WAVES:
+      if (value < 0 || value > 64) return fail(c, CWPIR_EINVAL, "row-group waves must be in [0, 64]");
+      drop_plans(c);
+      c->h.row_waves = value ? (u32)value : cw::kDefaultRowWaves;
       return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
   }
+}
+
+int cwpir_get_option(cwpir_ctx *c, int option, int64_t *value) {
+  if (!c || !value) return CWPIR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  switch (option) {
+    case CWPIR_OPT_SHARE_LEVEL1: *value = c->opt_share; return CWPIR_OK;
+    case CWPIR_OPT_BATCH_ROWS: *value = c->opt_batch_rows; return CWPIR_OK;
+    case CWPIR_OPT_USE_GRAPH: *value = c->opt_graph; return CWPIR_OK;
+    case CWPIR_OPT_KERNEL_TIMING: *value = c->opt_timing; return CWPIR_OK;
+    case CWPIR_OPT_MAX_JOBS: *value = c->opt_max_jobs; return CWPIR_OK;
+    case CWPIR_OPT_ROW_BASIS: *value = c->opt_row_basis; return CWPIR_OK;
+    case CWPIR_OPT_MEM_LIMIT: *value = (int64_t)c->acct.limit; return CWPIR_OK;
+    case CWPIR_OPT_ROW_GROUP_WAVES: *value = c->h.row_waves; return CWPIR_OK;
+    default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
+  }
+}
+
+int cwpir_mem_used(const cwpir_ctx *c, uint64_t *bytes) {
+  if (!c || !bytes) return CWPIR_EINVAL;
+  *bytes = c->acct.used;
+  return CWPIR_OK;
 }
 
 int cwpir_kernel_times(cwpir_ctx *c, double *ms, uint64_t *launches) {

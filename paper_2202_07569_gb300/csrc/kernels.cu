@@ -1126,11 +1126,11 @@ constexpr u32 kPmPPT = 2;  // fewer per thread keeps more warps resident
 u32 pm_chunks(u32 sp) { return sp <= 1 ? 1 : (sp + kPmPPT - 1) / kPmPPT; }
 
 u32 pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap) {
-  // row groups per segment: about four waves of 2048 threads per SM over
-  // the segs * L * N * (plaintext chunks) threads, at most seg_len, and at
-  // most cap partial slots of [sp][2][L][N] in all
+  // row groups per segment: about row_waves waves of the device's resident
+  // threads over the segs * L * N * (plaintext chunks) threads, at most
+  // seg_len, and at most cap partial slots of [sp][2][L][N] in all
   u64 lanes = (u64)segs * h.L * h.N * pm_chunks(sp);
-  u64 g = (4 * 152ull * 2048 + lanes - 1) / lanes;
+  u64 g = ((u64)h.row_waves * h.sms * h.sm_threads + lanes - 1) / lanes;
   g = g < seg_len ? g : seg_len;
   const u64 gcap = cap / ((u64)segs * sp);
   g = g < gcap ? g : gcap;

@@ -14,9 +14,16 @@ struct ExtNtt {
   const u32 *ipsi2;  // [N][2]: the same for psi^-1
 };
 
-// All per-context constants the kernels read, in device memory.
+// Row-sum waves: the row sums of the last tree level are split into row
+// groups until about this many waves of resident threads cover the device.
+constexpr u32 kDefaultRowWaves = 4;
+
+// All per-context constants the kernels read, in device memory.  sms,
+// sm_threads (read from the device at setup) and row_waves size launch
+// grids on the host.
 struct DevTables {
   u32 N, logN, L, K;
+  u32 sms, sm_threads, row_waves;
   u64 t;
   u64 delta[kMaxL];       // Delta = floor(Q / t) mod q_j
   NttPrime prime[kMaxL];  // ciphertext primes q_0..q_{L-1}

@@ -1,25 +1,28 @@
 // serve.cu -- online serving of PIR queries over resident databases.
 //
 // Requests for registered targets (a context, one of its databases and the
-// query compression factor) are queued on the host and answered by one
-// worker thread per context ("lane").  Continuous batching: whenever a lane
-// is free it takes the waiting requests of the target whose oldest request
-// has waited longest, up to the largest power of two that is at most the
-// configured maximum and whose answer plan fits in free device memory
-// (cached plans of the context are released when nothing fits), and
-// answers them in one batched call replayed from a CUDA graph; requests
-// that arrive meanwhile wait for the next batch.  Lanes of different
-// contexts run concurrently on their own streams.  Every response is the
-// response of cwpir_answer for the same query.
+// query compression factor) are queued on the host and answered by worker
+// lanes.  Every target has lanes_per_target lanes; a lane is a host thread
+// with its own stream, its own scratch slot on the target's context
+// (cwpir_slot_create) and its own staging buffers, so the lanes of all
+// targets run at the same time and their kernels overlap on the device.
+// Continuous batching: whenever a lane is free it takes the waiting
+// requests of its target, up to the largest power of two that is at most
+// the configured maximum and whose answer plan fits in free device memory
+// (the target's cached plans are released when nothing fits), and answers
+// them in one batched call replayed from a CUDA graph.  A request that
+// arrives while a lane is busy starts at once on an idle lane of its target
+// or, when all of them are busy, with the next batch of the first lane to
+// finish.  Every response is the response of cwpir_answer for the same
+// query; after each batch the lane reads its slot's device check flag, and
+// a failed check fails the batch's requests with CWPIR_EINTERNAL.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
-#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -45,18 +48,16 @@ struct SrvRequest {
 
 struct SrvTarget {
   cwpir_target t;
-  uint32_t lane = 0;
+  int device = 0;
   uint64_t q_words = 0, r_words = 0;
   std::deque<SrvRequest *> waiting;
 };
 
 struct SrvLane {
-  cwpir_ctx *ctx = nullptr;
-  int device = 0;
+  uint32_t target = 0, slot = 0;
   cudaStream_t st = nullptr;
   std::thread th;
   uint64_t *d_q = nullptr, *d_r = nullptr, *h_q = nullptr, *h_r = nullptr;
-  uint64_t q_cap = 0, r_cap = 0;  // words
 };
 
 }  // namespace
@@ -69,8 +70,8 @@ struct cwpir_server {
   std::unordered_map<uint64_t, std::unique_ptr<SrvRequest>> reqs;
   uint64_t next_ticket = 1;
   bool stop = false;
-  uint32_t max_batch = 16, max_pending = 1024, n_pending = 0;
-  uint64_t reserve = 0;
+  cwpir_server_config cfg{};
+  uint32_t n_pending = 0, running = 0;
   cwpir_server_stats stats{};
 };
 
@@ -82,56 +83,62 @@ uint32_t pow2_floor(uint32_t x) {
   return p;
 }
 
-// Largest power-of-two batch <= want whose plan fits in free memory.
-uint32_t admit(cwpir_server *s, const SrvTarget &tg, uint32_t want) {
+// Largest power-of-two batch <= want whose plan on the lane's slot fits in
+// free device memory minus the reserve; 0 if none does, even after the
+// target's cached plans were released.
+uint32_t admit(cwpir_server *s, const SrvTarget &tg, const SrvLane &ln, uint32_t want) {
   for (int pass = 0; pass < 2; ++pass) {
     for (uint32_t b = pow2_floor(want); b >= 1; b /= 2) {
       uint64_t need = 0;
-      if (cwpir_plan_bytes(tg.t.ctx, tg.t.db_id, b, tg.t.c, &need) != CWPIR_OK) continue;
+      if (cwpir_plan_bytes_slot(tg.t.ctx, ln.slot, tg.t.db_id, b, tg.t.c, &need) != CWPIR_OK)
+        continue;
       if (need == 0) return b;
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
-      if (need + s->reserve <= free_b) return b;
+      if (need + s->cfg.hbm_reserve_bytes <= free_b) return b;
     }
-    // nothing fits: drop this context's cached plans and retry once
-    cwpir_release_plans(tg.t.ctx, -1);
+    cwpir_release_plans(tg.t.ctx, tg.t.db_id);
   }
   return 0;
 }
 
+// One batch of b requests on a lane: staging, the batched answer on the
+// lane's slot, the response copy and the slot's device check.
+int run_batch(SrvLane &ln, const SrvTarget &tg, const std::vector<SrvRequest *> &batch) {
+  const uint32_t b = (uint32_t)batch.size();
+  for (uint32_t i = 0; i < b; ++i)
+    memcpy(ln.h_q + i * tg.q_words, batch[i]->query.data(), tg.q_words * sizeof(uint64_t));
+  if (cudaMemcpyAsync(ln.d_q, ln.h_q, b * tg.q_words * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                      ln.st) != cudaSuccess)
+    return CWPIR_ECUDA;
+  int rc = cwpir_answer_batch_slot(tg.t.ctx, ln.slot, tg.t.db_id, tg.t.c, b, ln.d_q, ln.d_r,
+                                   ln.st);
+  if (rc == CWPIR_OK &&
+      cudaMemcpyAsync(ln.h_r, ln.d_r, b * tg.r_words * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                      ln.st) != cudaSuccess)
+    rc = CWPIR_ECUDA;
+  // waits for the lane's stream and reads (and clears) the slot's flag, so
+  // that a failed check fails this batch and no later one
+  const int st = cwpir_device_status(tg.t.ctx, ln.slot, ln.st);
+  return rc != CWPIR_OK ? rc : st;
+}
+
 void lane_loop(cwpir_server *s, uint32_t lane_id) {
   SrvLane &ln = *s->lanes[lane_id];
-  cudaSetDevice(ln.device);
+  SrvTarget &tg = s->targets[ln.target];
+  cudaSetDevice(tg.device);
   for (;;) {
-    std::vector<SrvRequest *> batch;
-    uint32_t ti = 0;
-    {
-      std::unique_lock<std::mutex> lk(s->mu);
-      auto has_work = [&] {
-        for (const auto &t : s->targets)
-          if (t.lane == lane_id && !t.waiting.empty()) return true;
-        return false;
-      };
-      s->cv_work.wait(lk, [&] { return s->stop || has_work(); });
-      if (s->stop && !has_work()) return;
-      double oldest = 1e300;
-      for (uint32_t i = 0; i < s->targets.size(); ++i) {
-        const auto &t = s->targets[i];
-        if (t.lane == lane_id && !t.waiting.empty() && t.waiting.front()->t_submit < oldest) {
-          oldest = t.waiting.front()->t_submit;
-          ti = i;
-        }
-      }
-    }
-    SrvTarget &tg = s->targets[ti];
     uint32_t want;
     {
-      std::lock_guard<std::mutex> lk(s->mu);
-      want = (uint32_t)std::min<size_t>(tg.waiting.size(), s->max_batch);
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return s->stop || !tg.waiting.empty(); });
+      if (tg.waiting.empty()) return;  // stopping with nothing left
+      want = (uint32_t)std::min<size_t>(tg.waiting.size(), s->cfg.max_batch);
     }
     // admission by free device memory (outside the lock: may wait for the GPU)
-    uint32_t b = admit(s, tg, want);
+    uint32_t b = admit(s, tg, ln, want);
     if (b == 0) b = 1;  // nothing else can free memory for this lane: try alone
+    std::vector<SrvRequest *> batch;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       b = std::min<uint32_t>(b, (uint32_t)tg.waiting.size());
@@ -139,26 +146,18 @@ void lane_loop(cwpir_server *s, uint32_t lane_id) {
         batch.push_back(tg.waiting.front());
         tg.waiting.pop_front();
       }
+      if (!batch.empty()) {
+        s->running += 1;
+        s->stats.max_concurrent = std::max<uint64_t>(s->stats.max_concurrent, s->running);
+      }
     }
-    if (batch.empty()) continue;
-    for (uint32_t i = 0; i < b; ++i)
-      memcpy(ln.h_q + i * tg.q_words, batch[i]->query.data(), tg.q_words * sizeof(uint64_t));
-    double t0 = now_s();
-    int rc = CWPIR_OK;
-    cudaError_t e = cudaMemcpyAsync(ln.d_q, ln.h_q, b * tg.q_words * sizeof(uint64_t),
-                                    cudaMemcpyHostToDevice, ln.st);
-    if (e != cudaSuccess) rc = CWPIR_ECUDA;
-    if (rc == CWPIR_OK)
-      rc = cwpir_answer_batch_device(ln.ctx, tg.t.db_id, tg.t.c, b, ln.d_q, ln.d_r, ln.st);
-    if (rc == CWPIR_OK &&
-        cudaMemcpyAsync(ln.h_r, ln.d_r, b * tg.r_words * sizeof(uint64_t),
-                        cudaMemcpyDeviceToHost, ln.st) != cudaSuccess)
-      rc = CWPIR_ECUDA;
-    if (cudaStreamSynchronize(ln.st) != cudaSuccess && rc == CWPIR_OK) rc = CWPIR_ECUDA;
-    double t1 = now_s();
+    if (batch.empty()) continue;  // another lane of the target took them
+    const double t0 = now_s();
+    const int rc = run_batch(ln, tg, batch);
+    const double t1 = now_s();
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      for (uint32_t i = 0; i < b; ++i) {
+      for (uint32_t i = 0; i < batch.size(); ++i) {
         SrvRequest *r = batch[i];
         if (rc == CWPIR_OK) {
           r->resp.assign(ln.h_r + i * tg.r_words, ln.h_r + (i + 1) * tg.r_words);
@@ -168,11 +167,13 @@ void lane_loop(cwpir_server *s, uint32_t lane_id) {
         }
         r->t_done = t1;
       }
-      s->n_pending -= b;
-      s->stats.completed += b;
+      s->running -= 1;
+      s->n_pending -= (uint32_t)batch.size();
+      s->stats.completed += batch.size();
       s->stats.batches += 1;
-      s->stats.max_batch_seen = std::max<uint64_t>(s->stats.max_batch_seen, b);
+      s->stats.max_batch_seen = std::max<uint64_t>(s->stats.max_batch_seen, batch.size());
       s->stats.busy_s += t1 - t0;
+      if (rc != CWPIR_OK) s->stats.failed += batch.size();
     }
     s->cv_done.notify_all();
   }
@@ -182,48 +183,47 @@ void lane_loop(cwpir_server *s, uint32_t lane_id) {
 
 extern "C" {
 
-int cwpir_server_create(const cwpir_target *targets, uint32_t n_targets, uint32_t max_batch,
-                        uint64_t hbm_reserve_bytes, uint32_t max_pending, cwpir_server **out) {
-  if (!targets || !n_targets || !out || max_batch < 1 || max_pending < 1) return CWPIR_EINVAL;
+int cwpir_server_create(const cwpir_target *targets, uint32_t n_targets,
+                        const cwpir_server_config *cfg, cwpir_server **out) {
+  if (!targets || !n_targets || !cfg || !out || cfg->max_batch < 1 ||
+      cfg->lanes_per_target < 1 || cfg->lanes_per_target > 16 || cfg->max_pending < 1)
+    return CWPIR_EINVAL;
   std::unique_ptr<cwpir_server> s(new cwpir_server());
-  s->max_batch = max_batch;
-  s->max_pending = max_pending;
-  s->reserve = hbm_reserve_bytes;
-  std::map<cwpir_ctx *, uint32_t> lane_of;
+  s->cfg = *cfg;
   for (uint32_t i = 0; i < n_targets; ++i) {
     SrvTarget tg;
     tg.t = targets[i];
     uint32_t N = 0, L = 0, m = 0, sp = 1, h = 0;
     if (!tg.t.ctx || cwpir_db_shape(tg.t.ctx, tg.t.db_id, &N, &L, &m) != CWPIR_OK ||
         cwpir_db_plaintexts(tg.t.ctx, tg.t.db_id, &sp) != CWPIR_OK ||
-        cwpir_query_cts(tg.t.ctx, tg.t.db_id, tg.t.c, &h) != CWPIR_OK)
+        cwpir_query_cts(tg.t.ctx, tg.t.db_id, tg.t.c, &h) != CWPIR_OK ||
+        cwpir_ctx_device(tg.t.ctx, &tg.device) != CWPIR_OK)
       return CWPIR_EINVAL;
     tg.q_words = (uint64_t)h * 2ull * L * N;
     tg.r_words = (uint64_t)sp * 2ull * L * N;
-    auto it = lane_of.find(tg.t.ctx);
-    if (it == lane_of.end()) {
-      it = lane_of.emplace(tg.t.ctx, (uint32_t)s->lanes.size()).first;
-      s->lanes.emplace_back(new SrvLane());
-      s->lanes.back()->ctx = tg.t.ctx;
-    }
-    tg.lane = it->second;
-    SrvLane &ln = *s->lanes[tg.lane];
-    ln.q_cap = std::max<uint64_t>(ln.q_cap, tg.q_words * max_batch);
-    ln.r_cap = std::max<uint64_t>(ln.r_cap, tg.r_words * max_batch);
     s->targets.push_back(tg);
   }
-  for (auto &lp : s->lanes) {
-    SrvLane &ln = *lp;
-    if (cwpir_ctx_device(ln.ctx, &ln.device) != CWPIR_OK) return CWPIR_EINVAL;
-    cudaSetDevice(ln.device);
-    cwpir_set_option(ln.ctx, CWPIR_OPT_USE_GRAPH, 1);
-    if (cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc(&ln.d_q, ln.q_cap * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&ln.d_r, ln.r_cap * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMallocHost(&ln.h_q, ln.q_cap * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMallocHost(&ln.h_r, ln.r_cap * sizeof(uint64_t)) != cudaSuccess) {
-      cwpir_server_destroy(s.release());
-      return CWPIR_ENOMEM;
+  for (uint32_t i = 0; i < n_targets; ++i) {
+    const SrvTarget &tg = s->targets[i];
+    cwpir_set_option(tg.t.ctx, CWPIR_OPT_USE_GRAPH, 1);
+    for (uint32_t k = 0; k < cfg->lanes_per_target; ++k) {
+      std::unique_ptr<SrvLane> ln(new SrvLane());
+      ln->target = i;
+      cudaSetDevice(tg.device);
+      const uint64_t qb = tg.q_words * cfg->max_batch * sizeof(uint64_t);
+      const uint64_t rb = tg.r_words * cfg->max_batch * sizeof(uint64_t);
+      int rc = cwpir_slot_create(tg.t.ctx, &ln->slot);
+      if (rc != CWPIR_OK) return rc;
+      const bool ok = cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaMalloc(&ln->d_q, qb) == cudaSuccess &&
+                      cudaMalloc(&ln->d_r, rb) == cudaSuccess &&
+                      cudaMallocHost(&ln->h_q, qb) == cudaSuccess &&
+                      cudaMallocHost(&ln->h_r, rb) == cudaSuccess;
+      s->lanes.push_back(std::move(ln));
+      if (!ok) {
+        cwpir_server_destroy(s.release());
+        return CWPIR_ENOMEM;
+      }
     }
   }
   for (uint32_t i = 0; i < s->lanes.size(); ++i)
@@ -240,7 +240,7 @@ int cwpir_submit(cwpir_server *s, uint32_t target, const uint64_t *query, uint64
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return CWPIR_EINVAL;
-    if (s->n_pending >= s->max_pending) {
+    if (s->n_pending >= s->cfg.max_pending) {
       s->stats.rejected_busy += 1;
       return CWPIR_EBUSY;
     }
@@ -256,7 +256,8 @@ int cwpir_submit(cwpir_server *s, uint32_t target, const uint64_t *query, uint64
   return CWPIR_OK;
 }
 
-static int take_result(cwpir_server *s, std::unordered_map<uint64_t, std::unique_ptr<SrvRequest>>::iterator it,
+static int take_result(cwpir_server *s,
+                       std::unordered_map<uint64_t, std::unique_ptr<SrvRequest>>::iterator it,
                        uint64_t *response, int32_t *status, double *latency_s) {
   SrvRequest *r = it->second.get();
   *status = r->status;
@@ -314,13 +315,14 @@ void cwpir_server_destroy(cwpir_server *s) {
     if (lp->th.joinable()) lp->th.join();
   for (auto &lp : s->lanes) {
     SrvLane &ln = *lp;
-    cudaSetDevice(ln.device);
+    cudaSetDevice(s->targets[ln.target].device);
     if (ln.st) cudaStreamSynchronize(ln.st);
     if (ln.d_q) cudaFree(ln.d_q);
     if (ln.d_r) cudaFree(ln.d_r);
     if (ln.h_q) cudaFreeHost(ln.h_q);
     if (ln.h_r) cudaFreeHost(ln.h_r);
     if (ln.st) cudaStreamDestroy(ln.st);
+    if (ln.slot) cwpir_slot_release(s->targets[ln.target].t.ctx, ln.slot);
   }
   delete s;
 }

@@ -280,6 +280,90 @@ def test_c3_keyword_full_size_sparse_parity_present_and_absent():
     ctx.free_db(db)
 
 
+def _overlap_rows(cw, qpos, rng_rows, want_each):
+    """Rows of rng_rows grouped by how many codeword positions they share
+    with the query's, at most want_each of every overlap."""
+    qs = set(int(x) for x in qpos)
+    by = {}
+    for r in rng_rows:
+        ov = len(qs & set(int(x) for x in cw[r]))
+        if len(by.setdefault(ov, [])) < want_each:
+            by[ov].append(int(r))
+    return by
+
+
+def test_c2_full_size_selection_entries_bit_exact():
+    """Selection-vector entries (Alg. Selection Vector Calculation: the
+    balanced product tree of Eq. plain-cw-eq) of 80 rows of the full
+    configuration-2 database (n=65536, k=4, m=37, N=8192, L=4), each equal
+    to the oracle's bit for bit: the target row, rows sharing 0 ... 3
+    positions with the query (the number of factors that encrypt 1), rows
+    that reuse one shared first-level pair product with another sampled row
+    (same first pair, or same second pair), and uniform rows.  The entries
+    come from the shared pair products of the sampled rows, the context's
+    multiplications per launch and the same kernels as the answer."""
+    cfg = CONFIGS["c2"]
+    cl = client(cfg["N"], cfg["L"], seed=cfg["seed"])
+    ctx = cl.ctx
+    n, k, m = cfg["n"], cfg["k"], cfg["m"]
+    cw = np.stack([oracle.map_perfect(i, m, k) for i in range(n)])
+    db = ctx.load_db(np.zeros((n, 1), np.uint32), cw, m)
+    st = syn.Stream(cfg["seed"] + 40)
+    target = int(st.below(n, 1)[0])
+    query = cl.query(cw[target], m, 0, stream=41)
+    rows = [target]
+    by = _overlap_rows(cw, cw[target], st.below(n, 20000).tolist(), 6)
+    assert set(by) >= {0, 1, 2}
+    for ov in sorted(by):
+        rows += by[ov]
+    for r in st.below(n, 12).tolist():  # partners sharing a first-level pair
+        p = [int(x) for x in cw[r]]
+        for alt in ([p[0], p[1], p[2], p[3] + 1], [p[0] - 1, p[1], p[2], p[3]]):
+            if 0 <= alt[0] and alt[3] < m and len(set(alt)) == 4 and alt == sorted(alt):
+                x = int(oracle.map_inverse(np.array(alt, np.uint16)))
+                if x < n:
+                    rows += [int(r), x]
+    rows += [int(r) for r in st.below(n, 80).tolist()]
+    rows = np.array(list(dict.fromkeys(rows))[:80], np.uint64)
+    assert rows.size == 80 and target in rows.tolist()
+    got = ctx.selection(db, query, rows)
+    for i, r in enumerate(rows.tolist()):
+        assert np.array_equal(got[i], cl.O.selection(query, cw[r], cl.rlk)), r
+    ctx.free_db(db)
+
+
+def test_c3_full_size_selection_entries_bit_exact():
+    """Selection entries of 16 rows of the full configuration-3 keyword
+    database (16384 uniform 32-bit keywords, k=8, m=64, N=16384, L=7) for a
+    compressed query (c=6, expanded on the GPU by Alg. Query Expansion):
+    the present keyword's row, rows sharing several positions with it, and
+    uniform rows, each equal to the oracle's entry over the oracle's
+    expansion of the same query."""
+    cfg = CONFIGS["c3"]
+    cl = client(cfg["N"], cfg["L"], seed=cfg["seed"], c_max=cfg["c"])
+    ctx = cl.ctx
+    n, k, m, c = cfg["n"], cfg["k"], cfg["m"], cfg["c"]
+    ids = syn.distinct_u32(syn.Stream(cfg["seed"] + 1, 2), n)
+    cw = np.stack([oracle.map_perfect(int(x), m, k) for x in ids])
+    db = ctx.load_db(np.zeros((n, 1), np.uint32), cw, m)
+    st = syn.Stream(cfg["seed"] + 50)
+    target = int(st.below(n, 1)[0])
+    query = cl.query(cw[target], m, c, stream=51)
+    rows = [target]
+    by = _overlap_rows(cw, cw[target], range(n), 2)
+    for ov in sorted(by, reverse=True):
+        if ov < k:
+            rows += by[ov]
+    rows += [int(r) for r in st.below(n, 32).tolist()]
+    rows = np.array(list(dict.fromkeys(rows))[:16], np.uint64)
+    assert rows.size == 16
+    got = ctx.selection(db, query, rows, c)
+    cts = cl.O.expand(query, c, m, cl.gkeys)
+    for i, r in enumerate(rows.tolist()):
+        assert np.array_equal(got[i], cl.O.selection(cts, cw[r], cl.rlk)), r
+    ctx.free_db(db)
+
+
 # ------------------------------------------------------------ edge cases and errors
 def test_single_row_and_unary_code():
     cl = client(4096, 2)

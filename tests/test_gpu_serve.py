@@ -1,7 +1,9 @@
 """Online serving (configuration 5's pattern): continuous batching over
-resident databases of two parameter sets.  Every response must be the same
-as the query answered alone (and, for sampled queries, the oracle's)."""
+resident databases of two parameter sets, several lanes per target.  Every
+response must be the same as the query answered alone (and, for sampled
+queries, the oracle's)."""
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -51,7 +53,7 @@ def test_serving_mix_equals_alone_and_oracle():
     assert np.array_equal(pools[0][2], ca.O.answer(ia, cwa, 12, pools[0][1], ca.rlk))
     assert np.array_equal(pools[2][2], cb.O.answer(ik, cwk, 12, pools[2][1], cb.rlk, c=2,
                                                    gkeys=cb.gkeys))
-    srv = B.Server(targets, max_batch=8)
+    srv = B.Server(targets, max_batch=8, lanes_per_target=2)
     tickets = []
     lock = threading.Lock()
 
@@ -101,3 +103,67 @@ def test_serving_backpressure():
     assert srv.stats()["rejected_busy"] == busy
     srv.close()
     xb.close()
+
+
+def test_request_arriving_mid_batch_completes_before_that_batch():
+    """A request for another database that arrives while a long batch runs
+    starts at once on its own lane: it completes before the batch it arrived
+    during, and both give the responses of the queries answered alone."""
+    from paper_2202_07569_gb300 import binding as B
+
+    cl = Client(8192, 4, seed=98)
+    ctx = cl.context()
+    ibig, cwbig, _ = database(12000, 200, T, 4, 25, seed=99)
+    ismall, cwsmall, _ = database(8, 200, T, 2, 5, seed=100)
+    dbig, dsmall = ctx.load_db(ibig, cwbig, 25), ctx.load_db(ismall, cwsmall, 5)
+    qbig = [cl.query(cwbig[7 * i + 1], 25, 0, stream=500 + i) for i in range(4)]
+    qsmall = cl.query(cwsmall[3], 5, 0, stream=510)
+    alone_big = [ctx.answer(dbig, q) for q in qbig]
+    alone_small = ctx.answer(dsmall, qsmall)
+    srv = B.Server([(ctx, dbig, 0), (ctx, dsmall, 0)], max_batch=4)
+    for q in qbig:  # warm both lanes' plans and graphs
+        srv.wait(srv.submit(0, q), 0)
+    srv.wait(srv.submit(1, qsmall), 1)
+    t_big = time.perf_counter()
+    big = [srv.submit(0, q) for q in qbig]
+    time.sleep(0.005)  # the big batch is on the GPU by now
+    t_small = time.perf_counter()
+    small = srv.submit(1, qsmall)
+    st, resp, lat_small = srv.wait(small, 1)
+    assert st == 1 and np.array_equal(resp, alone_small)
+    done_small = t_small + lat_small
+    done_big = []
+    for tk, want in zip(big, alone_big):
+        st, resp, lat = srv.wait(tk, 0)
+        assert st == 1 and np.array_equal(resp, want)
+        done_big.append(t_big + lat)
+    assert done_small < min(done_big), (done_small - t_big, [d - t_big for d in done_big])
+    stats = srv.stats()
+    srv.close()
+    assert stats["max_concurrent"] >= 2 and stats["failed"] == 0
+    ctx.close()
+
+
+def test_failed_device_check_fails_its_batch_only():
+    """A device check that fails (raised here by the test hook on the
+    lane's slot flag, no kernel involved) fails the requests of the batch
+    that reads it with EINTERNAL; the next batch is answered normally."""
+    from paper_2202_07569_gb300 import binding as B
+
+    cl = Client(4096, 2, seed=101)
+    ctx = cl.context()
+    items, cw, _ = database(30, 100, T, 2, 9, seed=102)
+    db = ctx.load_db(items, cw, 9)
+    q = cl.query(cw[4], 9, 0, stream=520)
+    want = ctx.answer(db, q)
+    srv = B.Server([(ctx, db, 0)], max_batch=1)
+    st, resp, _ = srv.wait(srv.submit(0, q), 0)
+    assert st == 1 and np.array_equal(resp, want)
+    ctx.inject_status(1)  # the server's one lane holds slot 1
+    st, resp, _ = srv.wait(srv.submit(0, q), 0)
+    assert st == B.EINTERNAL and resp is None
+    st, resp, _ = srv.wait(srv.submit(0, q), 0)
+    assert st == 1 and np.array_equal(resp, want)
+    assert srv.stats()["failed"] == 1
+    srv.close()
+    ctx.close()
