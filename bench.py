@@ -182,7 +182,7 @@ def max_over_ranks(dist, x: float, device) -> float:
     return float(t.item())
 
 
-def run_gpu(args, rank: int, world: int, dist):
+def run_gpu(args, rank: int, world: int, dist, keep: bool = False):
     import torch
 
     from paper_2202_07569_gb300 import binding as B
@@ -291,35 +291,11 @@ def run_gpu(args, rank: int, world: int, dist):
                            f"{m54:.2f} IMAD per 54-bit and {m30:.2f} per 30-bit modular "
                            "multiplication from the measured 64-bit and high-product rates"),
                        "int_peaks_measured": peaks}
-    # batched vs plain: 16 queries in one batched call replayed from a CUDA
-    # graph, against the plain one-query calls timed above
-    if args.batch:
-        nq = args.batch
-        qs = np.concatenate([query] * nq)
-        d_qs = torch.from_numpy(qs.view(np.int64)).to(f"cuda:{dev}")
-        d_rs = torch.empty((nq, 2, WL["L"], WL["N"]), dtype=torch.int64, device=f"cuda:{dev}")
-        ctx.set_option(B.OPT_USE_GRAPH, 1)
-        ctx.answer_batch_device(db, nq, d_qs.data_ptr(), d_rs.data_ptr(), 0, stream.cuda_stream)
-        torch.cuda.synchronize()
-        b0 = torch.cuda.Event(enable_timing=True)
-        b1 = torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        for _ in range(2):
-            ctx.answer_batch_device(db, nq, d_qs.data_ptr(), d_rs.data_ptr(), 0, stream.cuda_stream)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        bms = max_over_ranks(dist, b0.elapsed_time(b1) / 2, f"cuda:{dev}")
-        bstats = ctx.last_stats()
-        ctx.set_option(B.OPT_USE_GRAPH, 0)
-        out["batched"] = {
-            "queries_per_call": nq, "ms_per_call": bms, "ms_per_query": bms / nq,
-            "value": world * mb * nq / (bms / 1e3), "unit": "MB/s",
-            "plain_ms_per_query": ms_per_step, "speedup_vs_plain": ms_per_step * nq / bms,
-            "graph": True, "gpu_launches_per_call": int(bstats["kernel_launches"])}
-        del d_qs, d_rs
+    if keep:
+        return out, (ctx, db, q)
     ctx.free_db(db)
     ctx.close()
-    return out
+    return out, None
 
 
 def run_sharded(args, rank: int, world: int, dist):
@@ -634,173 +610,289 @@ def run_arith(args):
                                                  "encrypted, BFV N=16384 L=7, t=65537 batching"}}
 
 
-def run_c4(args):
-    """Configuration 4: 64 queries over four resident databases, batched
-    (queries of one database share launches, replayed from CUDA graphs,
-    multiplications per launch picked by the autotuner) against 64
-    sequential one-query answers."""
+# The batching workload's four databases (configuration 4); the serving
+# workload uses three of them.  name, rows, k, m, N, L, c, keyword?
+SYS_SPECS = [
+    ("n1024_k2", 1024, 2, 46, 8192, 4, 0, False),
+    ("n4096_k2", 4096, 2, 92, 8192, 4, 0, False),
+    ("n16384_k8_keyword", 16384, 8, 64, 16384, 7, 6, True),
+    ("n65536_k4", 65536, 4, 37, 8192, 4, 0, False),
+]
+
+
+def build_system_dbs(c2=None):
+    """One context per database (keys seeded per ring degree), so that each
+    database's launch shape is tuned on its own; `c2` = (ctx, db, primes) of
+    the metric's workload stands in for n65536_k4 (the same database
+    shape).  Every database gets 16 seeded queries resident on the GPU."""
     import torch
 
     from paper_2202_07569_gb300 import binding as B
     from paper_2202_07569_gb300 import synthetic as syn
 
-    specs = [  # name, n, k, m, N, L, c, keyword
-        ("n1024_k2", 1024, 2, 46, 8192, 4, 0, False),
-        ("n4096_k2", 4096, 2, 92, 8192, 4, 0, False),
-        ("n16384_k8_keyword", 16384, 8, 64, 16384, 7, 6, True),
-        ("n65536_k4", 65536, 4, 37, 8192, 4, 0, False),
-    ]
-    ctxs = {}
-    for N, L in ((8192, 4), (16384, 7)):
-        q = B.default_primes(N, L)
-        rlk = syn.uniform_residues(syn.Stream(31, N), q, (L, 2), N)
-        gal = {}
-        if N == 16384:
-            for a in range(6):
-                g = N // (1 << a) + 1
-                gal[g] = syn.uniform_residues(syn.Stream(32, g), q, (L, 2), N)
-        ctxs[N] = (B.Context(N, q, 65537, rlk, gal), q)
     dbs = []
-    for i, (name, n, k, m, N, L, c, kw) in enumerate(specs):
-        ctx, q = ctxs[N]
-        items = syn.payload(syn.Stream(33, i), n, 8192, 1 << 16)
-        ids = (syn.distinct_u32(syn.Stream(34, i), n) if kw else np.arange(n, dtype=np.uint64))
-        cw = np.stack([B.map_perfect(int(x), m, k) for x in ids])
-        db = ctx.load_db(items, cw, m)
-        del items
+    for i, (name, n, k, m, N, L, c, kw) in enumerate(SYS_SPECS):
+        if name == "n65536_k4" and c2 is not None:
+            ctx, db, q = c2
+        else:
+            q = B.default_primes(N, L)
+            rlk = syn.uniform_residues(syn.Stream(31, N), q, (L, 2), N)
+            gal = {}
+            if c:
+                for a in range(c):
+                    g = N // (1 << a) + 1
+                    gal[g] = syn.uniform_residues(syn.Stream(32, g), q, (L, 2), N)
+            ctx = B.Context(N, q, 65537, rlk, gal)
+            items = syn.payload(syn.Stream(33, i), n, 8192, 1 << 16)
+            ids = (syn.distinct_u32(syn.Stream(34, i), n) if kw else np.arange(n, dtype=np.uint64))
+            cw = np.stack([B.map_perfect(int(x), m, k) for x in ids])
+            db = ctx.load_db(items, cw, m)
+            del items
         h = m if c == 0 else -(-m // (1 << c))
         qs = syn.uniform_ciphertexts(35 + i, q, 16 * h, N).reshape(16, h, 2, L, N)
-        d_qs = torch.from_numpy(qs.view(np.int64)).cuda()
-        d_rs = torch.empty((16, 2, L, N), dtype=torch.int64, device="cuda")
-        nq = 4 if N == 16384 else 16  # bounds the per-query first-level products in HBM
-        dbs.append(dict(name=name, ctx=ctx, db=db, c=c, h=h, L=L, N=N, d_qs=d_qs, d_rs=d_rs,
-                        nq=nq, mb=payload_mb(n)))
-    st = torch.cuda.current_stream()
+        dbs.append(dict(name=name, ctx=ctx, db=db, c=c, h=h, L=L, N=N, n=n, k=k, m=m,
+                        nq_call=4 if N == 16384 else 16, mb=payload_mb(n), qs=qs,
+                        d_qs=torch.from_numpy(qs.view(np.int64)).cuda(),
+                        d_rs=torch.empty((16, 2, L, N), dtype=torch.int64, device="cuda")))
+    return dbs
+
+
+def _events():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_c3(d, args):
+    """The keyword workload (configuration 3): one compressed query (c = 6,
+    expanded by Alg. Query Expansion) against n = 16384 rows keyed by
+    32-bit keywords, k = 8, m = 64, N = 16384, L = 7.  The answer is
+    data-oblivious, so present and absent keywords cost the same work; the
+    queries here are uniform ciphertexts."""
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+
+    ctx, db, st = d["ctx"], d["db"], torch.cuda.current_stream()
+    ctx.set_option(B.OPT_USE_GRAPH, 0)
+    q0, r0 = d["d_qs"][0].data_ptr(), d["d_rs"][0].data_ptr()
+    ctx.answer_device(db, q0, r0, d["c"], st.cuda_stream)
     torch.cuda.synchronize()
-    # plain: 64 one-query calls, no graph
+    ctx.set_option(B.OPT_KERNEL_TIMING, 1)
+    ctx.kernel_times()
+    steps = 3
+    e0, e1 = _events()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(st)
+        for i in range(steps):
+            ctx.answer_device(db, d["d_qs"][i].data_ptr(), d["d_rs"][i].data_ptr(), d["c"],
+                              st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+    kt = ctx.kernel_times()
+    ctx.set_option(B.OPT_KERNEL_TIMING, 0)
+    status = ctx.device_status(0, st.cuda_stream)
+    stats = ctx.last_stats()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "keyword PIR n=16384 rows x 8192 16-bit coefficients, 32-bit keywords, "
+                        "CW(64,8), BFV N=16384 L=7, one compressed query (c=6, 1 ciphertext)",
+            "ms_per_answer": ms, "value": d["mb"] / (ms / 1e3), "unit": "MB/s",
+            "items_per_s": d["n"] / (ms / 1e3), "steps": steps, "device_status": status,
+            "stats": stats, "clocks": clk.summary(),
+            "kernels": {k: {"ms": v[0] / steps, "launches": v[1] // steps}
+                        for k, v in kt.items() if v[1]}}
+
+
+def run_c4_blocks(dbs, args):
+    """Configuration 4: 64 queries, 16 per database, over the four resident
+    databases.  plain: 64 one-query calls, each database's 16 in sequence;
+    batched per database: its 16 queries in batched calls (16 at a time, 4 at
+    N = 16384) replayed from a CUDA graph, the launch shape of the two small
+    databases picked by the autotuner (multiplications per launch x row-group
+    waves); all: the 64 queries in one forked launch sequence captured into
+    one CUDA graph (one branch per database, cwpir_multi).  Every batched
+    response is compared with the plain one bit for bit."""
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+
+    st = torch.cuda.current_stream()
     for d in dbs:
         d["ctx"].set_option(B.OPT_USE_GRAPH, 0)
         d["ctx"].answer_device(d["db"], d["d_qs"][0].data_ptr(), d["d_rs"][0].data_ptr(), d["c"],
                                st.cuda_stream)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
+    per = {}
+    ev = {d["name"]: _events() for d in dbs}
+    with ClockSampler(torch.cuda.current_device()) as clk_plain:
+        for d in dbs:
+            e0, e1 = ev[d["name"]]
+            e0.record(st)
+            for i in range(16):
+                d["ctx"].answer_device(d["db"], d["d_qs"][i].data_ptr(), d["d_rs"][i].data_ptr(),
+                                       d["c"], st.cuda_stream)
+            e1.record(st)
+        torch.cuda.synchronize()
+    plain_total = 0.0
+    plain = {}
     for d in dbs:
-        for i in range(16):
-            d["ctx"].answer_device(d["db"], d["d_qs"][i].data_ptr(), d["d_rs"][i].data_ptr(),
-                                   d["c"], st.cuda_stream)
-    e1.record(st)
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
-    plain = [t.clone() for t in (d["d_rs"] for d in dbs)]
-    # batched: autotune per database, graphs on
-    tuned = {}
+        ms = ev[d["name"]][0].elapsed_time(ev[d["name"]][1])
+        plain_total += ms
+        plain[d["name"]] = d["d_rs"].clone()
+        per[d["name"]] = {"N": d["N"], "rows": d["n"], "k": d["k"], "c": d["c"],
+                          "plain_ms_16": ms, "plain_launches_per_query":
+                          int(d["ctx"].last_stats()["kernel_launches"])}
+    # autotuner on the small databases (cheap calls); the large ones keep
+    # the default launch shape
     for d in dbs:
-        d["ctx"].set_option(B.OPT_USE_GRAPH, 1)
-        best, ms = d["ctx"].autotune(d["db"], d["nq"], d["d_qs"].data_ptr(), d["d_rs"].data_ptr(),
-                                     [256, 512, 0], d["c"])
-        tuned[d["name"]] = {"max_jobs": best, "ms_per_call": ms}
-        for j in range(16 // d["nq"]):  # build and capture
-            d["ctx"].answer_batch_device(d["db"], d["nq"], d["d_qs"][j * d["nq"]].data_ptr(),
-                                         d["d_rs"][j * d["nq"]].data_ptr(), d["c"], st.cuda_stream)
+        ctx = d["ctx"]
+        ctx.set_option(B.OPT_USE_GRAPH, 1)
+        if d["n"] <= 4096:
+            bj, bw, bms = ctx.autotune_grid(d["db"], 16, d["d_qs"].data_ptr(), d["d_rs"].data_ptr(),
+                                            [256, 512, 1024, 2048], [2, 4, 8], d["c"])
+            per[d["name"]]["autotuned"] = {"max_jobs": bj, "row_group_waves": bw,
+                                           "ms_per_call": bms,
+                                           "grid": "jobs {256,512,1024,2048} x waves {2,4,8}"}
+    same = True
+    batched_total = 0.0
+    launches = 0
+    with ClockSampler(torch.cuda.current_device()) as clk_b:
+        for d in dbs:
+            ctx, nqc = d["ctx"], d["nq_call"]
+            for j in range(16 // nqc):  # build and capture
+                ctx.answer_batch_device(d["db"], nqc, d["d_qs"][j * nqc].data_ptr(),
+                                        d["d_rs"][j * nqc].data_ptr(), d["c"], st.cuda_stream)
+            torch.cuda.synchronize()
+            d["d_rs"].zero_()
+            e0, e1 = _events()
+            e0.record(st)
+            for j in range(16 // nqc):
+                ctx.answer_batch_device(d["db"], nqc, d["d_qs"][j * nqc].data_ptr(),
+                                        d["d_rs"][j * nqc].data_ptr(), d["c"], st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            launches += (16 // nqc) * int(ctx.last_stats()["kernel_launches"])
+            ms = e0.elapsed_time(e1)
+            batched_total += ms
+            ok = bool(torch.equal(d["d_rs"], plain[d["name"]])) and ctx.device_status(0, 0) == 0
+            same &= ok
+            p = per[d["name"]]
+            p.update({"queries_per_call": nqc, "batched_ms_16": ms,
+                      "speedup_vs_plain": p["plain_ms_16"] / ms, "identical_to_plain": ok})
+            ctx.release_plans(d["db"])
+    # all 64 queries in one forked sequence, one graph
+    mb = B.Multi([(d["ctx"], d["db"], d["c"], 16, d["nq_call"]) for d in dbs])
+    outs = [torch.zeros_like(d["d_rs"]) for d in dbs]
+    qp, rp = [d["d_qs"].data_ptr() for d in dbs], [o.data_ptr() for o in outs]
+    mb.answer_device(qp, rp, True, st.cuda_stream)  # capture
     torch.cuda.synchronize()
-    e0.record(st)
+    for o in outs:
+        o.zero_()
+    e0, e1 = _events()
+    with ClockSampler(torch.cuda.current_device()) as clk_m:
+        e0.record(st)
+        mb.answer_device(qp, rp, True, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+    multi_ms = e0.elapsed_time(e1)
+    multi_same = all(bool(torch.equal(o, plain[d["name"]])) for o, d in zip(outs, dbs))
+    multi_same &= mb.status(st.cuda_stream) == 0
+    mstats = mb.stats()
+    mb.close()
+    del outs
     for d in dbs:
-        for j in range(16 // d["nq"]):
-            d["ctx"].answer_batch_device(d["db"], d["nq"], d["d_qs"][j * d["nq"]].data_ptr(),
-                                         d["d_rs"][j * d["nq"]].data_ptr(), d["c"], st.cuda_stream)
-    e1.record(st)
-    torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1)
-    same = all(bool(torch.equal(a, d["d_rs"])) for a, d in zip(plain, dbs))
+        d["ctx"].set_option(B.OPT_USE_GRAPH, 0)
     total_mb = sum(16 * d["mb"] for d in dbs)
     return {"metric": "batched PIR answer DB MB/s, 64 queries over 4 resident databases",
-            "value": total_mb / (batched_ms / 1e3), "unit": "MB/s",
-            "ms_per_64_queries": batched_ms, "plain_ms_per_64_queries": plain_ms,
-            "plain_value": total_mb / (plain_ms / 1e3), "speedup_vs_plain": plain_ms / batched_ms,
-            "responses_identical_to_plain": same, "autotuned": tuned,
-            "databases": [{k: d[k] for k in ("name", "N", "L", "c", "nq", "mb")} for d in dbs]}
+            "value": total_mb / (multi_ms / 1e3), "unit": "MB/s",
+            "ms_64_queries_one_graph": multi_ms, "ms_64_queries_batched_per_db": batched_total,
+            "ms_64_queries_plain": plain_total,
+            "plain_value": total_mb / (plain_total / 1e3),
+            "speedup_one_graph_vs_plain": plain_total / multi_ms,
+            "speedup_batched_per_db_vs_plain": plain_total / batched_total,
+            "responses_identical_to_plain": bool(same and multi_same),
+            "gpu_launches_one_graph": int(mstats["kernel_launches"]),
+            "gpu_launches_batched_per_db": launches,
+            "per_db": per,
+            "clocks": {"plain": clk_plain.summary(), "batched": clk_b.summary(),
+                       "one_graph": clk_m.summary()}}
 
 
-def run_c5(args, per_rate: int = 24, rates=(0.25, 0.5, 1, 10, 30, 100, 300, 1000, 2000)):
+def run_c5_blocks(dbs, args, rates=(0.5, 1.0, 2.0, 4.0), per_rate: int = 12):
     """Configuration 5: Poisson arrivals of index and keyword queries (2:1)
-    over three resident databases, served with continuous batching; per
-    offered rate the p50/p99 latency (submission to completion) and the
-    sustained DB MB/s.  Every response is compared with the same query
-    answered alone.  The rates below the service capacity (about one query
-    per second for this mix) show the latency of a lightly loaded server;
-    they send 12 queries each to bound the run time."""
-
+    over three resident databases (n65536_k4, n4096_k2, n16384_k8_keyword),
+    served with continuous batching on two lanes per database (each its own
+    stream and scratch slot, so queries of all databases overlap on the
+    device); per offered rate the p50/p99 latency (submission to
+    completion) and the sustained DB MB/s.  Every response is compared with
+    the same query answered alone.  The rates bracket the service capacity
+    of this mix (about one and a half queries per second)."""
     from paper_2202_07569_gb300 import binding as B
     from paper_2202_07569_gb300 import synthetic as syn
 
-    specs = [  # name, n, k, m, N, L, c, keyword
-        ("n65536_k4", 65536, 4, 37, 8192, 4, 0, False),
-        ("n4096_k2", 4096, 2, 92, 8192, 4, 0, False),
-        ("n16384_k8_keyword", 16384, 8, 64, 16384, 7, 6, True),
-    ]
-    ctxs = {}
-    for N, L in ((8192, 4), (16384, 7)):
-        q = B.default_primes(N, L)
-        rlk = syn.uniform_residues(syn.Stream(41, N), q, (L, 2), N)
-        gal = {}
-        if N == 16384:
-            for a in range(6):
-                g = N // (1 << a) + 1
-                gal[g] = syn.uniform_residues(syn.Stream(42, g), q, (L, 2), N)
-        ctxs[N] = (B.Context(N, q, 65537, rlk, gal), q)
-    targets, pools, mbs = [], [], []
-    for i, (name, n, k, m, N, L, c, kw) in enumerate(specs):
-        ctx, q = ctxs[N]
-        items = syn.payload(syn.Stream(43, i), n, 8192, 1 << 16)
-        ids = syn.distinct_u32(syn.Stream(44, i), n) if kw else np.arange(n, dtype=np.uint64)
-        cw = np.stack([B.map_perfect(int(x), m, k) for x in ids])
-        db = ctx.load_db(items, cw, m)
-        del items
-        h = m if c == 0 else -(-m // (1 << c))
-        qs = syn.uniform_ciphertexts(45 + i, q, 4 * h, N).reshape(4, h, 2, L, N)
-        alone = [ctx.answer(db, qs[j], c) for j in range(4)]
-        targets.append((ctx, db, c))
-        pools.append((qs, alone))
-        mbs.append(payload_mb(n))
-    srv = B.Server(targets, max_batch=8, hbm_reserve=8 << 30, lanes_per_target=2)
+    by = {d["name"]: d for d in dbs}
+    tg_names = ["n65536_k4", "n4096_k2", "n16384_k8_keyword"]
+    targets = [(by[nm]["ctx"], by[nm]["db"], by[nm]["c"]) for nm in tg_names]
+    pools = []
+    for nm in tg_names:
+        d = by[nm]
+        qs = d["qs"][:4]
+        pools.append((qs, [d["ctx"].answer(d["db"], qs[j], d["c"]) for j in range(4)]))
+    srv = B.Server(targets, max_batch=4, hbm_reserve=16 << 30, lanes_per_target=2)
     mix = [0, 2, 1]  # index : keyword = 2 : 1
     results = []
     all_same = True
     st = syn.Stream(46)
     for rate in rates:
-        count = per_rate if rate >= 10 else 12
-        gaps = -np.log((st.below(1 << 53, count).astype(np.float64) + 0.5) / 2.0 ** 53) / rate
+        gaps = -np.log((st.below(1 << 53, per_rate).astype(np.float64) + 0.5) / 2.0 ** 53) / rate
         sent = []
         t0 = time.perf_counter()
         t_next = t0
-        for i in range(count):
+        for i in range(per_rate):
             t_next += gaps[i]
             delay = t_next - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
             tg = mix[i % 3]
-            j = i % 4
+            j = (i // 3) % 4
             sent.append((srv.submit(tg, pools[tg][0][j]), tg, j))
         lat, mb = [], 0.0
+        by_tg = {0: [], 1: [], 2: []}
         for tk, tg, j in sent:
             status, resp, l = srv.wait(tk, tg, timeout=3600)
             all_same &= status == 1 and bool(np.array_equal(resp, pools[tg][1][j]))
             lat.append(l)
-            mb += mbs[tg]
+            by_tg[tg].append(l)
+            mb += by[tg_names[tg]]["mb"]
         wall = time.perf_counter() - t0
         lat.sort()
-        results.append({"offered_qps": rate, "queries": count, "wall_s": wall,
-                        "achieved_qps": count / wall, "db_mb_per_s": mb / wall,
-                        "p50_ms": 1e3 * lat[len(lat) // 2],
-                        "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))]})
+
+        def pct(v, p):
+            v = sorted(v)
+            return 1e3 * v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
+
+        results.append({"offered_qps": rate, "queries": per_rate, "wall_s": wall,
+                        "achieved_qps": per_rate / wall, "db_mb_per_s": mb / wall,
+                        "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+                        "p50_ms_by_db": {tg_names[t]: pct(v, 0.5) for t, v in by_tg.items()},
+                        "p99_ms_by_db": {tg_names[t]: pct(v, 0.99) for t, v in by_tg.items()}})
     stats = srv.stats()
     srv.close()
     return {"metric": "served PIR: p50/p99 latency and sustained DB MB/s vs offered rate",
             "value": max(r["db_mb_per_s"] for r in results), "unit": "MB/s",
-            "rates": results, "responses_identical_to_alone": all_same,
-            "server": stats, "max_batch": 8,
-            "databases": [s[0] for s in specs], "mix": "index:keyword = 2:1"}
+            "rates": results, "responses_identical_to_alone": bool(all_same),
+            "server": stats, "max_batch": 4, "lanes_per_target": 2,
+            "databases": tg_names, "mix": "index:keyword = 2:1"}
+
+
+def run_c4(args):
+    dbs = build_system_dbs()
+    return run_c4_blocks(dbs, args)
+
+
+def run_c5(args):
+    dbs = build_system_dbs()
+    return run_c5_blocks(dbs, args)
 
 
 def cpu_baseline(rows_per_step: int | None = None, reps: int = 1):
@@ -833,8 +925,9 @@ def main():
                     help="profiling only: answer over the first ROWS rows instead of 65536")
     ap.add_argument("--max-jobs", type=int, default=0,
                     help="multiplications per kernel launch (0 = library default)")
-    ap.add_argument("--batch", type=int, default=16,
-                    help="queries per batched call in the batched-vs-plain comparison (0: skip)")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="only the metric's workload: skip the keyword, batching and serving "
+                         "blocks that follow its timed region")
     ap.add_argument("--shard-db", action="store_true",
                     help="shard the database's rows over the ranks (strong scaling) instead of "
                          "one replica per rank")
@@ -907,7 +1000,8 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    res = run_gpu(args, rank, world, dist)
+    systems = world == 1 and not args.no_systems and not args.rows
+    res, keep = run_gpu(args, rank, world, dist, keep=systems)
     if rank != 0:
         return
     line = dict(base)
@@ -917,6 +1011,26 @@ def main():
     if args.max_jobs:
         line["config"]["max_jobs"] = args.max_jobs
     line.update(res)
+    if systems:
+        # the other configurations on the same GPU, after the metric's timed
+        # region: the keyword workload, batching over four databases and
+        # serving; the metric's database serves as n65536_k4
+        dbs = build_system_dbs(c2=keep)
+        line["c3"] = run_c3(next(d for d in dbs if d["name"] == "n16384_k8_keyword"), args)
+        line["c4"] = run_c4_blocks(dbs, args)
+        c2b = line["c4"]["per_db"]["n65536_k4"]
+        line["batched"] = {"workload": "the metric's database, 16 distinct queries per "
+                                       "batched call replayed from a CUDA graph",
+                           "ms_per_query": c2b["batched_ms_16"] / 16,
+                           "plain_ms_per_query": c2b["plain_ms_16"] / 16,
+                           "value": payload_mb(WL["n"]) * 16 / (c2b["batched_ms_16"] / 1e3),
+                           "unit": "MB/s", "speedup_vs_plain": c2b["speedup_vs_plain"],
+                           "identical_to_plain": c2b["identical_to_plain"]}
+        line["c5"] = run_c5_blocks(dbs, args)
+        for d in dbs:
+            if d["ctx"] is not keep[0]:
+                d["ctx"].close()
+        keep[0].close()
     if world == 1 and not args.no_cpu_baseline:
         mbps, cores, sample = cpu_baseline(None, 1)
         line["cpu_baseline"] = {"value": mbps[0], "unit": "MB/s", "cores": cores,

@@ -84,6 +84,16 @@ typedef struct {
   const uint64_t *galois;
 } cwpir_keys;
 
+/* Work counters of an answer (for throughput accounting). */
+typedef struct {
+  uint64_t rows;            /* database rows processed */
+  uint64_t mults;           /* homomorphic multiplications executed */
+  uint64_t substitutions;   /* substitutions executed (expansion) */
+  uint64_t ntt_polys;       /* length-N NTTs/INTTs executed (per limb) */
+  uint64_t kernel_launches; /* kernels launched */
+  uint64_t db_bytes_read;   /* NTT-form database bytes streamed */
+} cwpir_stats;
+
 /* ---- library information and host helpers ---- */
 int cwpir_abi_version(void);
 const char *cwpir_strerror(int code);
@@ -190,6 +200,48 @@ int cwpir_answer_batch(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
 int cwpir_answer_batch_device(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
                               uint32_t nq, const uint64_t *d_queries,
                               uint64_t *d_responses, void *stream);
+/* Batched answering across databases (configuration 4 of the benchmark):
+ * the queries of several resident databases, possibly of different
+ * contexts (ring degrees, primes, code weights) on one device, in one
+ * launch sequence.  Each item is (context, database, c, nq queries, answered
+ * nq_call at a time, nq_call dividing nq; 0 = all nq at once) and gets its
+ * own branch: a stream and a slot of its context (cwpir_slot_create, held
+ * until cwpir_multi_destroy) with its own plan over all rows.  A call forks
+ * the branches from `stream`, runs each item's sub-batches in order on its
+ * branch, so that the small databases' launches fill the device while the
+ * large ones run, and joins them back into `stream`; with use_graph the
+ * whole forked sequence is captured once into one CUDA graph and replayed
+ * afterwards (recaptured when a context's scratch was re-sized).  Every
+ * response is bit-identical to cwpir_answer of the same query.  Contexts
+ * and databases must outlive the object; no other call may use these
+ * contexts while a cwpir_multi call runs, except the slot calls. */
+typedef struct {
+  cwpir_ctx *ctx;
+  int32_t db_id;
+  uint32_t c;        /* compression factor of the item's queries */
+  uint32_t nq;       /* queries of the item per call */
+  uint32_t nq_call;  /* queries per batched answer in the branch (0 = nq) */
+} cwpir_multi_item;
+typedef struct cwpir_multi cwpir_multi;
+/* EINVAL (contexts on different devices, nq not a multiple of nq_call, a
+ * bad c), ENODB, ENOKEY, ENOMEM, ECUDA. */
+int cwpir_multi_create(const cwpir_multi_item *items, uint32_t count,
+                       cwpir_multi **out);
+/* d_queries[i]: item i's [nq][h][2][L][N] device queries, d_responses[i]:
+ * its [nq][s][2][L][N] responses; enqueued on `stream` (a cudaStream_t,
+ * NULL: legacy default stream), returns once enqueued.  ENODB if a database
+ * was freed. */
+int cwpir_multi_answer_device(cwpir_multi *mb, const uint64_t *const *d_queries,
+                              uint64_t *const *d_responses, int use_graph,
+                              void *stream);
+/* Waits for `stream` and reads every branch's device check flag
+ * (cwpir_device_status): CWPIR_EINTERNAL if any check failed. */
+int cwpir_multi_status(cwpir_multi *mb, void *stream);
+/* Work counters of the last enqueued (or captured) sequence, all items. */
+int cwpir_multi_stats(const cwpir_multi *mb, cwpir_stats *out);
+const char *cwpir_multi_last_error(const cwpir_multi *mb);
+void cwpir_multi_destroy(cwpir_multi *mb);
+
 /* Exchange step of a database sharded by rows over several GPUs (one
  * context per GPU, each holding a disjoint set of the rows with their own
  * codewords).  The response is linear in the rows: r = sum over rows i of
@@ -216,6 +268,16 @@ int cwpir_autotune(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
                    const uint64_t *d_queries, uint64_t *d_responses,
                    const int64_t *candidates, uint32_t count, int64_t *best,
                    double *best_ms);
+/* The autotuner over a grid: every (multiplications per launch, row-group
+ * waves) pair of jobs[n_jobs] x waves[n_waves] (n_waves = 0: the default
+ * waves only); keeps the fastest pair on ctx (CWPIR_OPT_MAX_JOBS,
+ * CWPIR_OPT_ROW_GROUP_WAVES) and writes it (best_waves may be NULL) with
+ * its time per call.  Reads slot 0's device check flag at the end. */
+int cwpir_autotune_grid(cwpir_ctx *ctx, int32_t db_id, uint32_t c, uint32_t nq,
+                        const uint64_t *d_queries, uint64_t *d_responses,
+                        const int64_t *jobs, uint32_t n_jobs, const int64_t *waves,
+                        uint32_t n_waves, int64_t *best_jobs, int64_t *best_waves,
+                        double *best_ms);
 
 /* Device memory (bytes, an upper estimate) that the first
  * cwpir_answer_batch(_device) call for (db_id, nq, c) would allocate for
@@ -459,15 +521,7 @@ typedef struct {
 /* EINVAL for a bad device or null out; ENOMEM; ECUDA. */
 int cwpir_measure_int_peaks(int device, cwpir_int_peaks *out);
 
-/* Work counters of the last answer on ctx (for throughput accounting). */
-typedef struct {
-  uint64_t rows;            /* database rows processed */
-  uint64_t mults;           /* homomorphic multiplications executed */
-  uint64_t substitutions;   /* substitutions executed (expansion) */
-  uint64_t ntt_polys;       /* length-N NTTs/INTTs executed (per limb) */
-  uint64_t kernel_launches; /* kernels launched */
-  uint64_t db_bytes_read;   /* NTT-form database bytes streamed */
-} cwpir_stats;
+/* Work counters of the last answer on ctx (cwpir_stats, above). */
 int cwpir_last_stats(const cwpir_ctx *ctx, cwpir_stats *out);
 
 /* Kernel classes of the answer path, for cwpir_kernel_times. */

@@ -69,6 +69,11 @@ class ServerStats(C.Structure):
                 for f, _ in self._fields_}
 
 
+class _MultiItem(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("db_id", C.c_int32), ("c", C.c_uint32),
+                ("nq", C.c_uint32), ("nq_call", C.c_uint32)]
+
+
 class IntPeaks(C.Structure):
     _fields_ = [("imad32_per_s", C.c_double), ("mulhi32_per_s", C.c_double),
                 ("mullo64_per_s", C.c_double), ("mulhi64_per_s", C.c_double),
@@ -141,6 +146,12 @@ def lib():
             "cwpir_kernel_class_name": (C.c_char_p, [I]),
             "cwpir_mul_noalloc": (I, [vp, vp, vp, vp, vp]),
             "cwpir_measure_int_peaks": (I, [C.c_int, C.POINTER(IntPeaks)]),
+            "cwpir_multi_create": (I, [C.POINTER(_MultiItem), U32, C.POINTER(vp)]),
+            "cwpir_multi_answer_device": (I, [vp, C.POINTER(vp), C.POINTER(vp), I, vp]),
+            "cwpir_multi_status": (I, [vp, vp]),
+            "cwpir_multi_stats": (I, [vp, C.POINTER(Stats)]),
+            "cwpir_multi_last_error": (C.c_char_p, [vp]),
+            "cwpir_multi_destroy": (None, [vp]),
             "cwpir_plan_bytes": (I, [vp, C.c_int32, U32, U32, C.POINTER(U64)]),
             "cwpir_release_plans": (I, [vp, C.c_int32]),
             "cwpir_db_shape": (I, [vp, C.c_int32, C.POINTER(U32), C.POINTER(U32),
@@ -160,6 +171,9 @@ def lib():
             "cwpir_answer_batch_device": (I, [vp, C.c_int32, U32, U32, vp, vp, vp]),
             "cwpir_autotune": (I, [vp, C.c_int32, U32, U32, vp, vp, C.POINTER(C.c_int64), U32,
                                    C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+            "cwpir_autotune_grid": (I, [vp, C.c_int32, U32, U32, vp, vp, C.POINTER(C.c_int64),
+                                        U32, C.POINTER(C.c_int64), U32, C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(l, name)
@@ -352,6 +366,17 @@ class Context:
                                          len(candidates), C.byref(best), C.byref(ms)))
         return int(best.value), float(ms.value)
 
+    def autotune_grid(self, db: int, nq: int, queries_ptr: int, resp_ptr: int, jobs, waves,
+                      c: int = 0):
+        """(best jobs per launch, best row-group waves, ms per call)."""
+        ja = (C.c_int64 * len(jobs))(*jobs)
+        wa = (C.c_int64 * max(1, len(waves)))(*(waves or [0]))
+        bj, bw, ms = C.c_int64(), C.c_int64(), C.c_double()
+        self._check(lib().cwpir_autotune_grid(self._h, db, c, nq, queries_ptr, resp_ptr, ja,
+                                              len(jobs), wa, len(waves), C.byref(bj),
+                                              C.byref(bw), C.byref(ms)))
+        return int(bj.value), int(bw.value), float(ms.value)
+
     def mul(self, a, b) -> np.ndarray:
         out = np.zeros(self.ct_shape, np.uint64)
         self._check(lib().cwpir_mul(self._h, _u64(a), _u64(b), out))
@@ -426,6 +451,11 @@ class Context:
             self._check(rc)
         return int(rc)
 
+    def release_plans(self, db: int = -1):
+        """Frees the cached answer plans (and graphs) of a database, or of all
+        databases when db < 0."""
+        self._check(lib().cwpir_release_plans(self._h, db))
+
     def slot_release(self, slot: int):
         self._check(lib().cwpir_slot_release(self._h, slot))
 
@@ -499,6 +529,59 @@ class Server:
     def close(self):
         if getattr(self, "_h", None):
             lib().cwpir_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """cwpir_multi: the queries of several resident databases (of one or
+    more contexts) answered in one forked launch sequence, one branch per
+    item, optionally captured into one CUDA graph.  items: (ctx, db, c, nq,
+    nq_call) tuples."""
+
+    def __init__(self, items):
+        arr = (_MultiItem * len(items))()
+        self.items = []
+        for i, (ctx, db, c, nq, nq_call) in enumerate(items):
+            arr[i] = _MultiItem(ctx._h, db, c, nq, nq_call)
+            self.items.append((ctx, db, c, nq))
+        h = C.c_void_p()
+        rc = lib().cwpir_multi_create(arr, len(items), C.byref(h))
+        if rc:
+            msg = items[0][0] and lib().cwpir_last_error(items[0][0]._h).decode()
+            raise CwpirError(rc, f"multi create: {msg}")
+        self._h = h
+        self._ctxs = [it[0] for it in items]  # contexts must outlive the object
+
+    def _check(self, rc):
+        if rc:
+            raise CwpirError(rc, lib().cwpir_multi_last_error(self._h).decode())
+
+    def answer_device(self, query_ptrs, resp_ptrs, use_graph: bool = True, stream: int = 0):
+        qa = (C.c_void_p * len(query_ptrs))(*query_ptrs)
+        ra = (C.c_void_p * len(resp_ptrs))(*resp_ptrs)
+        self._check(lib().cwpir_multi_answer_device(self._h, qa, ra, int(bool(use_graph)),
+                                                    stream))
+
+    def status(self, stream: int = 0) -> int:
+        rc = lib().cwpir_multi_status(self._h, stream)
+        if rc not in (0, EINTERNAL):
+            self._check(rc)
+        return int(rc)
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(lib().cwpir_multi_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cwpir_multi_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -102,8 +102,16 @@ struct Acc128 {
   }
 };
 
+// Full 64-bit product of two 32-bit words: one wide multiply-add on the
+// integer pipe, where a product of u64 operands would take three.  The
+// callers narrow to u32 only values they know to be below 2^32.
+CW_HD u64 wmul(u32 a, u32 b) { return (u64)a * b; }
+
 // 27-bit halves of a constant b < 2^54: b = out[1] 2^27 + out[0].
 constexpr u32 kMask27 = (1u << 27) - 1;
+// the halves of a residue below 2^54
+CW_HD u32 lo27(u64 y) { return (u32)y & kMask27; }
+CW_HD u32 hi27(u64 y) { return (u32)(y >> 27); }
 CW_HD void split27(u64 b, u32 *out) {
   out[0] = (u32)b & kMask27;
   out[1] = (u32)(b >> 27);
@@ -261,10 +269,10 @@ CW_HD void lift_ext(const u64 *x, u32 *out, const LiftTab &C) {
   bool amb;
   u64 rho = round_sum<L>(y, C.Q.w_hi, C.Q.w_lo, &amb);
   if (amb) rho += mr_greater_half<L>(x, C.Q);
+  // rho <= L: one 32-bit word; the halves of y_j are below 2^27
   for (int k = 0; k < K; ++k) {
-    u64 s = rho * C.negq[k];
-    for (int j = 0; j < L; ++j)
-      s += (y[j] & kMask27) * C.h[j][k] + (y[j] >> 27) * C.h27[j][k];
+    u64 s = wmul((u32)rho, C.negq[k]);
+    for (int j = 0; j < L; ++j) s += wmul(lo27(y[j]), C.h[j][k]) + wmul(hi27(y[j]), C.h27[j][k]);
     out[k] = reduce_ext(s, C.ext[k]);
   }
 }
@@ -325,30 +333,31 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
   }
   // dp_k A_k < 2^61, 2L products of 27-bit halves with 30-bit constants
   // below 2^57 each (2^61 for L = 8), rho C_k < 2^34: the sum fits 2^62
-  u64 yb[K];
+  // every factor is below 2^32: dp_k < 2^31, rho <= L, the halves of y_j,
+  // so each product is one wide 32 x 32-bit multiply
+  u32 yb[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    u64 s = dp[k] * S.A[k] + rho * S.Cr[k];
+    u64 s = wmul((u32)dp[k], S.A[k]) + wmul((u32)rho, S.Cr[k]);
 #pragma unroll
-    for (int j = 0; j < L; ++j)
-      s += (y[j] & kMask27) * S.B[j][k] + (y[j] >> 27) * S.B27[j][k];
+    for (int j = 0; j < L; ++j) s += wmul(lo27(y[j]), S.B[j][k]) + wmul(hi27(y[j]), S.B27[j][k]);
     yb[k] = reduce_ext(s, S.ext[k]);
   }
   u64 fix = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) fix += yb[k] * S.pw58[k];  // each < 2^58: sum < 2^63
+  for (int k = 0; k < K; ++k) fix += wmul(yb[k], S.pw58[k]);  // each < 2^58: sum < 2^63
   const u64 rho2 = (fix + (1ull << 57)) >> 58;
   const u64 frac = (fix + (1ull << 57)) & ((1ull << 58) - 1);  // offset + 1/2, in 2^-58
   const bool far = frac < (1ull << 57) - (1ull << 41) || frac > (1ull << 57) + (1ull << 41);
   // K + 1 <= 18 products of values below 2^30 with 27-bit halves: the words
   // ll and x stay below 18 * 2^57 < 2^62.2; the sum ll + x 2^27 < 2^90
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    u64 ll = rho2 * S.negp2[j][0], x = rho2 * S.negp2[j][1];
+  for (int j = 0; j < L; ++j) {  // rho2 <= K
+    u64 ll = wmul((u32)rho2, S.negp2[j][0]), x = wmul((u32)rho2, S.negp2[j][1]);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      ll += yb[k] * S.hat2[k][j][0];
-      x += yb[k] * S.hat2[k][j][1];
+      ll += wmul(yb[k], S.hat2[k][j][0]);
+      x += wmul(yb[k], S.hat2[k][j][1]);
     }
     const u64 lo = ll + (x << 27);
     const u64 hi = (x >> 37) + (lo < ll ? 1 : 0);
@@ -406,7 +415,7 @@ CW_HD u64 row_digits(const u32 *xr, u32 *y, const RowTab &T, bool *far) {
 // x mod q_j from the digits: sum_k y_k (R/r_k) - rho R (at most five
 // products of values below 2^30 with 27-bit halves, sum below 2^88).
 CW_HD u64 row_to_q(const u32 *y, u64 rho, int j, const RowTab &T) {
-  u64 ll = rho * T.negr2[j][0], x = rho * T.negr2[j][1];
+  u64 ll = wmul((u32)rho, T.negr2[j][0]), x = wmul((u32)rho, T.negr2[j][1]);  // rho <= nr
   for (int k = 0; k < kRowPrimes; ++k) {
     if ((u32)k >= T.nr) break;
     ll += (u64)y[k] * T.hat2[k][j][0];

@@ -47,6 +47,9 @@ struct DevBuf {
   u64 *p = nullptr;
   size_t n = 0;  // u64 count
   MemAcct *acct = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
   ~DevBuf() { release(); }
   void release() {
     if (p) {
@@ -1303,52 +1306,71 @@ int cwpir_sum_responses_device(cwpir_ctx *c, uint32_t count, uint32_t s,
   return 0;
 }
 
-int cwpir_autotune(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
-                   const uint64_t *d_queries, uint64_t *d_responses, const int64_t *cand,
-                   uint32_t count, int64_t *best, double *best_ms) {
+int cwpir_autotune_grid(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
+                        const uint64_t *d_queries, uint64_t *d_responses, const int64_t *jobs,
+                        uint32_t n_jobs, const int64_t *waves, uint32_t n_waves,
+                        int64_t *best_jobs, int64_t *best_waves, double *best_ms) {
   if (!c) return CWPIR_EINVAL;
-  if (!cand || !count || !best || !best_ms) return fail(c, CWPIR_EINVAL, "null argument");
+  if (!jobs || !n_jobs || !best_jobs || !best_ms || (n_waves && !waves))
+    return fail(c, CWPIR_EINVAL, "null argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   cudaSetDevice(c->device);
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));
   CUDA_TRY(c, cudaEventCreate(&e1));
+  const int64_t no_wave = 0;
+  const int64_t *wv = n_waves ? waves : &no_wave;
+  const uint32_t nw = n_waves ? n_waves : 1;
   double best_t = 1e300;
-  int64_t best_v = -1;
+  int64_t bj = -1, bw = 0;
   int rc = CWPIR_OK;
-  for (uint32_t i = 0; i < count && rc == CWPIR_OK; ++i) {
-    if ((rc = cwpir_set_option(c, CWPIR_OPT_MAX_JOBS, cand[i]))) break;
-    // first call builds the plan (and the graph when enabled)
-    rc = cwpir_answer_batch_device(c, db_id, cfac, nq, d_queries, d_responses, c->stream);
-    if (rc == CWPIR_EINVAL) {  // this size cannot hold nq queries: skip it
-      rc = CWPIR_OK;
-      continue;
-    }
-    if (rc) break;
-    cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < 2 && rc == CWPIR_OK; ++r)
+  for (uint32_t i = 0; i < n_jobs && rc == CWPIR_OK; ++i)
+    for (uint32_t w = 0; w < nw && rc == CWPIR_OK; ++w) {
+      if ((rc = cwpir_set_option(c, CWPIR_OPT_MAX_JOBS, jobs[i]))) break;
+      if ((rc = cwpir_set_option(c, CWPIR_OPT_ROW_GROUP_WAVES, wv[w]))) break;
+      // the first call builds the plan (and the graph when enabled)
       rc = cwpir_answer_batch_device(c, db_id, cfac, nq, d_queries, d_responses, c->stream);
-    cudaEventRecord(e1, c->stream);
-    if (rc) break;
-    cudaError_t e = cudaEventSynchronize(e1);
-    float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      rc = fail(c, CWPIR_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
-      break;
+      if (rc == CWPIR_EINVAL) {  // this size cannot hold nq queries: skip it
+        rc = CWPIR_OK;
+        continue;
+      }
+      if (rc) break;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 2 && rc == CWPIR_OK; ++r)
+        rc = cwpir_answer_batch_device(c, db_id, cfac, nq, d_queries, d_responses, c->stream);
+      cudaEventRecord(e1, c->stream);
+      if (rc) break;
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rc = fail(c, CWPIR_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+        break;
+      }
+      if (ms / 2 < best_t) {
+        best_t = ms / 2;
+        bj = jobs[i];
+        bw = wv[w];
+      }
     }
-    if (ms / 2 < best_t) {
-      best_t = ms / 2;
-      best_v = cand[i];
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if (best_v < 0) return fail(c, CWPIR_EINVAL, "no candidate could hold %u queries", nq);
-  if ((rc = cwpir_set_option(c, CWPIR_OPT_MAX_JOBS, best_v))) return rc;
-  *best = best_v;
+  if (bj < 0) return fail(c, CWPIR_EINVAL, "no candidate could hold %u queries", nq);
+  if ((rc = cwpir_set_option(c, CWPIR_OPT_MAX_JOBS, bj))) return rc;
+  if ((rc = cwpir_set_option(c, CWPIR_OPT_ROW_GROUP_WAVES, bw))) return rc;
+  if ((rc = check_err_flag(c, 0))) return rc;
+  *best_jobs = bj;
+  if (best_waves) *best_waves = bw;
   *best_ms = best_t;
   return CWPIR_OK;
+}
+
+int cwpir_autotune(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
+                   const uint64_t *d_queries, uint64_t *d_responses, const int64_t *cand,
+                   uint32_t count, int64_t *best, double *best_ms) {
+  return cwpir_autotune_grid(c, db_id, cfac, nq, d_queries, d_responses, cand, count, nullptr, 0,
+                             best, nullptr, best_ms);
 }
 
 int cwpir_mul(cwpir_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *out) {
@@ -1793,6 +1815,262 @@ int cwpir_last_stats(const cwpir_ctx *c, cwpir_stats *out) {
   if (!c || !out) return CWPIR_EINVAL;
   *out = c->stats;
   return CWPIR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------
+// Batched answering across databases (configuration 4): one launch
+// sequence for the queries of several resident databases, one branch per
+// database on its own stream and scratch slot, forked from and joined into
+// the caller's stream, captured once into a single CUDA graph.
+// ---------------------------------------------------------------------
+struct MultiItem {
+  cwpir_ctx *c = nullptr;
+  int32_t db_id = 0;
+  Db *db = nullptr;
+  u32 cfac = 0, nq = 0, nq_call = 0, slot = 0;
+  u64 qw = 0, rw = 0;  // u64 words of one query and of one response
+  u64 gen = 0;         // the context's scratch_gen when the plan was built
+  std::unique_ptr<Plan> plan;
+  DevBuf qstage, rstage;  // [nq][h][2][L][N] and [nq][s][2][L][N]
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+struct cwpir_multi {
+  std::vector<std::unique_ptr<MultiItem>> items;
+  int device = 0;
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr, sync = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cwpir_stats stats{};
+  std::string err;
+  ~cwpir_multi() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (auto &ip : items) {
+      MultiItem &it = *ip;
+      if (it.st) cudaStreamDestroy(it.st);
+      if (it.done) cudaEventDestroy(it.done);
+      it.plan.reset();
+      if (it.slot) cwpir_slot_release(it.c, it.slot);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (sync) cudaEventDestroy(sync);
+    if (main) cudaStreamDestroy(main);
+  }
+};
+
+namespace {
+
+// Locks the contexts of a multi object in address order.
+struct MultiLock {
+  std::vector<std::unique_lock<std::recursive_mutex>> locks;
+  explicit MultiLock(const cwpir_multi *mb) {
+    std::vector<cwpir_ctx *> cs;
+    for (const auto &it : mb->items) cs.push_back(it->c);
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    for (cwpir_ctx *c : cs) locks.emplace_back(c->mu);
+  }
+};
+
+int multi_fail(cwpir_multi *mb, int code, const cwpir_ctx *c) {
+  mb->err = c ? c->err : std::string("invalid argument");
+  return code;
+}
+
+// (Re)builds an item's plan when it has none or its context's scratch was
+// re-sized since.
+int multi_plan(MultiItem &it, bool *rebuilt) {
+  cwpir_ctx *c = it.c;
+  if (get_db(c, it.db_id) != it.db) return fail(c, CWPIR_ENODB, "database %d was freed", it.db_id);
+  int rc = ensure_scratch(c, it.slot);
+  if (rc) return rc;
+  if (it.plan && it.gen == c->scratch_gen) return CWPIR_OK;
+  std::vector<u64> rows(it.db->n);
+  for (u64 i = 0; i < it.db->n; ++i) rows[i] = i;
+  it.plan.reset();
+  if ((rc = build_plan(c, it.slot, it.db, rows, it.nq_call, it.cfac, cw::ROOT_PM, nullptr,
+                       c->opt_share != 0, it.plan)))
+    return rc;
+  it.gen = c->scratch_gen;
+  *rebuilt = true;
+  return CWPIR_OK;
+}
+
+// Every item's branch: fork from `main`, the item's sub-batches of nq_call
+// queries from qstage to rstage on the item's stream, join into `main`.
+int multi_enqueue(cwpir_multi *mb) {
+  CUDA_TRY(mb->items[0]->c, cudaEventRecord(mb->fork, mb->main));
+  mb->stats = cwpir_stats{};
+  for (auto &ip : mb->items) {
+    MultiItem &it = *ip;
+    cwpir_ctx *c = it.c;
+    CUDA_TRY(c, cudaStreamWaitEvent(it.st, mb->fork, 0));
+    Scratch &S = *c->slots[it.slot];
+    for (u32 j = 0; j < it.nq / it.nq_call; ++j) {
+      c->stats = cwpir_stats{};
+      int rc = enqueue_answer(c, S, it.db, it.plan.get(), it.qstage.p + (u64)j * it.nq_call * it.qw,
+                              it.rstage.p + (u64)j * it.nq_call * it.rw, it.st);
+      if (rc) return rc;
+      mb->stats.rows += c->stats.rows;
+      mb->stats.mults += c->stats.mults;
+      mb->stats.substitutions += c->stats.substitutions;
+      mb->stats.ntt_polys += c->stats.ntt_polys;
+      mb->stats.kernel_launches += c->stats.kernel_launches;
+      mb->stats.db_bytes_read += c->stats.db_bytes_read;
+    }
+    CUDA_TRY(c, cudaEventRecord(it.done, it.st));
+    CUDA_TRY(c, cudaStreamWaitEvent(mb->main, it.done, 0));
+  }
+  return CWPIR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cwpir_multi_create(const cwpir_multi_item *items, uint32_t count, cwpir_multi **out) {
+  if (!items || !count || !out) return CWPIR_EINVAL;
+  std::unique_ptr<cwpir_multi> mb(new (std::nothrow) cwpir_multi());
+  if (!mb) return CWPIR_ENOMEM;
+  for (uint32_t i = 0; i < count; ++i) {
+    cwpir_ctx *c = items[i].ctx;
+    if (!c) return CWPIR_EINVAL;
+    if (i == 0) mb->device = c->device;
+    if (c->device != mb->device) return fail(c, CWPIR_EINVAL, "items on different devices");
+  }
+  cudaSetDevice(mb->device);
+  for (uint32_t i = 0; i < count; ++i) {
+    cwpir_ctx *c = items[i].ctx;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    c->err.clear();
+    mb->items.emplace_back(new MultiItem());
+    MultiItem &it = *mb->items.back();
+    it.c = c;
+    it.db_id = items[i].db_id;
+    it.cfac = items[i].c;
+    it.nq = items[i].nq;
+    it.nq_call = items[i].nq_call ? items[i].nq_call : items[i].nq;
+    if (!(it.db = get_db(c, it.db_id))) return fail(c, CWPIR_ENODB, "unknown database %d", it.db_id);
+    if (!it.nq || it.nq % it.nq_call)
+      return fail(c, CWPIR_EINVAL, "nq must be a positive multiple of nq_call");
+    u64 h;
+    int rc = query_shape(c, it.db, it.cfac, &h);
+    if (rc || (rc = check_keys(c, it.cfac))) return rc;
+    it.qw = h * c->ct();
+    it.rw = (u64)it.db->sp * c->ct();
+    if ((rc = add_slot(c, &it.slot))) return rc;
+    CUDA_TRY(c, it.qstage.ensure((u64)it.nq * it.qw, &c->acct));
+    CUDA_TRY(c, it.rstage.ensure((u64)it.nq * it.rw, &c->acct));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&it.st, cudaStreamNonBlocking));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming));
+    bool rebuilt = false;
+    if ((rc = multi_plan(it, &rebuilt))) return rc;
+  }
+  if (cudaStreamCreateWithFlags(&mb->main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&mb->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&mb->sync, cudaEventDisableTiming) != cudaSuccess)
+    return CWPIR_ECUDA;
+  *out = mb.release();
+  return CWPIR_OK;
+}
+
+int cwpir_multi_answer_device(cwpir_multi *mb, const uint64_t *const *d_queries,
+                              uint64_t *const *d_responses, int use_graph, void *stream) {
+  if (!mb || !d_queries || !d_responses) return CWPIR_EINVAL;
+  MultiLock lk(mb);
+  cudaSetDevice(mb->device);
+  mb->err.clear();
+  const cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = mb->items.size();
+  cwpir_ctx *c0 = mb->items[0]->c;
+  bool rebuilt = false;
+  for (size_t i = 0; i < n; ++i) {
+    MultiItem &it = *mb->items[i];
+    it.c->err.clear();
+    if (!d_queries[i] || !d_responses[i]) return CWPIR_EINVAL;
+    int rc = multi_plan(it, &rebuilt);
+    if (rc) return multi_fail(mb, rc, it.c);
+  }
+  if (rebuilt && mb->graph) {
+    cudaGraphExecDestroy(mb->graph);
+    mb->graph = nullptr;
+  }
+  // queries in on the caller's stream, which `main` then follows
+  for (size_t i = 0; i < n; ++i) {
+    MultiItem &it = *mb->items[i];
+    CUDA_TRY(it.c, cudaMemcpyAsync(it.qstage.p, d_queries[i], it.nq * it.qw * sizeof(u64),
+                                   cudaMemcpyDeviceToDevice, st));
+  }
+  CUDA_TRY(c0, cudaEventRecord(mb->sync, st));
+  CUDA_TRY(c0, cudaStreamWaitEvent(mb->main, mb->sync, 0));
+  int rc = CWPIR_OK;
+  if (!use_graph) {
+    rc = multi_enqueue(mb);
+    if (rc) return multi_fail(mb, rc, c0);
+  } else {
+    if (!mb->graph) {
+      for (auto &ip : mb->items) ip->c->capturing = true;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(mb->main, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        rc = multi_enqueue(mb);
+        e = cudaStreamEndCapture(mb->main, &g);
+      }
+      for (auto &ip : mb->items) ip->c->capturing = false;
+      if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&mb->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (rc) return multi_fail(mb, rc, c0);
+      if (e != cudaSuccess) {
+        mb->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        return CWPIR_ECUDA;
+      }
+    }
+    const cudaError_t e = cudaGraphLaunch(mb->graph, mb->main);
+    if (e != cudaSuccess) {
+      mb->err = std::string("graph launch: ") + cudaGetErrorString(e);
+      return CWPIR_ECUDA;
+    }
+  }
+  // responses out on the caller's stream, after `main`
+  CUDA_TRY(c0, cudaEventRecord(mb->sync, mb->main));
+  CUDA_TRY(c0, cudaStreamWaitEvent(st, mb->sync, 0));
+  for (size_t i = 0; i < n; ++i) {
+    MultiItem &it = *mb->items[i];
+    CUDA_TRY(it.c, cudaMemcpyAsync(d_responses[i], it.rstage.p, it.nq * it.rw * sizeof(u64),
+                                   cudaMemcpyDeviceToDevice, st));
+  }
+  return CWPIR_OK;
+}
+
+int cwpir_multi_status(cwpir_multi *mb, void *stream) {
+  if (!mb) return CWPIR_EINVAL;
+  int worst = CWPIR_OK;
+  for (auto &ip : mb->items) {
+    const int rc = cwpir_device_status(ip->c, ip->slot, stream);
+    if (rc && !worst) {
+      worst = rc;
+      mb->err = ip->c->err;
+    }
+  }
+  return worst;
+}
+
+int cwpir_multi_stats(const cwpir_multi *mb, cwpir_stats *out) {
+  if (!mb || !out) return CWPIR_EINVAL;
+  *out = mb->stats;
+  return CWPIR_OK;
+}
+
+const char *cwpir_multi_last_error(const cwpir_multi *mb) { return mb ? mb->err.c_str() : ""; }
+
+void cwpir_multi_destroy(cwpir_multi *mb) {
+  if (!mb) return;
+  cudaSetDevice(mb->device);
+  if (mb->main) cudaStreamSynchronize(mb->main);
+  delete mb;
 }
 
 }  // extern "C"

@@ -679,7 +679,7 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
   // two rows per iteration: both rows' loads issue before the products
   for (; x + G < seg_len; x += 2 * G, job += 2 * G) {
     const u64 row1 = jobs[job + G].row;
-    const u64 m0 = dbr[row0 * kN + kc], m1 = dbr[row1 * kN + kc];
+    const u32 m0 = dbr[row0 * kN + kc], m1 = dbr[row1 * kN + kc];
     if (x + 2 * G < seg_len) row0 = jobs[job + 2 * G].row;
     const u32 *d0 = D + job * jstride + kc, *d1 = d0 + G * jstride;
     u32 a[NL], b[NL];
@@ -689,7 +689,7 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
       b[l] = d1[l * kN];
     }
 #pragma unroll
-    for (int l = 0; l < NL; ++l) acc[l] += a[l] * m0 + b[l] * m1;
+    for (int l = 0; l < NL; ++l) acc[l] += wmul(a[l], m0) + wmul(b[l], m1);
     terms += 2;
     if (terms >= 14) {  // at most 14 products and a folded residue: below 2^64
 #pragma unroll
@@ -698,10 +698,10 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
     }
   }
   if (x < seg_len) {  // the last row of an odd count
-    const u64 m0 = dbr[row0 * kN + kc];
+    const u32 m0 = dbr[row0 * kN + kc];
     const u32 *d0 = D + job * jstride + kc;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) acc[l] += d0[l * kN] * m0;
+    for (int l = 0; l < NL; ++l) acc[l] += wmul(d0[l * kN], m0);
   }
   u32 *o = S + (u64)sg * NL * kN + (u64)k * N + c;
 #pragma unroll

@@ -103,3 +103,47 @@ def test_batch_full_size_c2_graph_and_autotune():
     torch.cuda.synchronize()
     assert np.array_equal(dr.cpu().numpy().view(np.uint64), got)
     ctx.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_multi_database_batch_equals_alone(graph):
+    """Queries of three databases over two contexts (N = 4096 and N = 8192,
+    k = 2, 3 and a compressed keyword query) in one forked launch sequence,
+    one item answered two queries at a time: every response equals the
+    query answered alone, on two calls in a row (the second replays the
+    graph), and one equals the oracle's."""
+    import torch
+
+    from paper_2202_07569_gb300 import binding as B
+
+    ca, cb = Client(4096, 2, seed=121), Client(8192, 4, seed=122, c_max=2)
+    xa, xb = ca.context(), cb.context()
+    ia, cwa, _ = database(70, 300, T, 2, 13, seed=123)
+    ib, cwb, _ = database(90, 500, T, 3, 12, seed=124)
+    ik, cwk, _ = database(40, 200, T, 4, 12, seed=125)
+    dba, dbb, dbk = xa.load_db(ia, cwa, 13), xb.load_db(ib, cwb, 12), xb.load_db(ik, cwk, 12)
+    specs = [(xa, dba, 0, 4, 2, ca, cwa, 13), (xb, dbb, 0, 3, 0, cb, cwb, 12),
+             (xb, dbk, 2, 2, 0, cb, cwk, 12)]
+    qs, alone = [], []
+    for j, (ctx, db, c, nq, _, cl, cw, m) in enumerate(specs):
+        q = np.stack([cl.query(cw[(11 * i + 3 * j) % len(cw)], m, c, stream=130 + 10 * j + i)
+                      for i in range(nq)])
+        qs.append(q)
+        alone.append(np.stack([ctx.answer(db, q[i], c) for i in range(nq)]))
+    assert np.array_equal(alone[0][1], ca.O.answer(ia, cwa, 13, qs[0][1], ca.rlk))
+    mb = B.Multi([(ctx, db, c, nq, nqc) for ctx, db, c, nq, nqc, *_ in specs])
+    dq = [torch.from_numpy(q.view(np.int64)).cuda() for q in qs]
+    dr = [torch.zeros(a.shape, dtype=torch.int64, device="cuda") for a in alone]
+    st = torch.cuda.current_stream()
+    for rep in range(2):
+        for r in dr:
+            r.zero_()
+        mb.answer_device([t.data_ptr() for t in dq], [t.data_ptr() for t in dr], graph,
+                         st.cuda_stream)
+        assert mb.status(st.cuda_stream) == 0
+        for j in range(3):
+            assert np.array_equal(dr[j].cpu().numpy().view(np.uint64), alone[j]), (rep, j)
+    assert mb.stats()["mults"] > 0
+    mb.close()
+    xa.close()
+    xb.close()
