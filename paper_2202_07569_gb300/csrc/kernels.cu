@@ -39,6 +39,16 @@ __device__ __forceinline__ u32 ntt_pos(u32 t, u32 r) {
   return t | (r << (LOGN - NttShape<LOGN>::RB));
 }
 
+// The same two orders for the arrays of the 32-bit primes (NttShape32).
+template <int LOGN>
+__device__ __forceinline__ u32 strided_idx32(u32 t, u32 r) {
+  return t | (r << (LOGN - NttShape32<LOGN>::RB));
+}
+template <int LOGN>
+__device__ __forceinline__ u32 ntt_pos32(u32 t, u32 r) {
+  return t | (r << (LOGN - NttShape32<LOGN>::RB));
+}
+
 // registers of one transform per thread
 template <int LOGN>
 using NttRegs = u64[NttShape<LOGN>::R];
@@ -106,11 +116,11 @@ __device__ __forceinline__ void ntt_inv(NttRegs<LOGN> &x, u64 *s, const NttPrime
 // [0, 2p) to N times the coefficient in [0, 2p) (no N^-1: the scale-down
 // absorbs it).
 template <int LOGN>
-using NttRegs32 = u32[NttShape<LOGN>::R];
+using NttRegs32 = u32[NttShape32<LOGN>::R];
 
 template <int LOGN>
 __device__ __forceinline__ void ntt_fwd32(NttRegs32<LOGN> &x, u32 *s, const ExtNtt &P) {
-  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int RB = NttShape32<LOGN>::RB, R = NttShape32<LOGN>::R;
   constexpr int NP = Passes<LOGN, RB>::count;
   const u32 t = threadIdx.x;
   u32 wprev = 0;
@@ -135,7 +145,7 @@ __device__ __forceinline__ void ntt_fwd32(NttRegs32<LOGN> &x, u32 *s, const ExtN
 
 template <int LOGN>
 __device__ __forceinline__ void ntt_inv32(NttRegs32<LOGN> &x, u32 *s, const ExtNtt &P) {
-  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int RB = NttShape32<LOGN>::RB, R = NttShape32<LOGN>::R;
   constexpr int NP = Passes<LOGN, RB>::count;
   const u32 t = threadIdx.x;
   u32 wprev = 0;
@@ -196,34 +206,43 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 }
 
 // ---------------------------------------------------------------------
-// Batched NTT: unit u, limb l (prime l): base + u*unit_stride + l*N, read
-// from src (same limb offset, src_unit_stride) when src != nullptr.  Limbs
-// l >= L (extension primes, forward only) address units in QP layout.
-// grid (limb_end - limb_begin, units).
+// Batched NTT: unit u, limb l (prime l < L): base + u*unit_stride + l*N,
+// read from src (same limb offset, src_unit_stride) when src != nullptr.
+// grid (limb_end - limb_begin, units).  k_ntt32: the forward transform of
+// extension limb k (limbs L + k of units in QP layout), grid (k_end -
+// k_begin, units).
 // ---------------------------------------------------------------------
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
+    k_ntt32(const DevTables *T, u64 *base, u64 unit_stride, u32 k_begin, const u64 *src,
+            u64 src_unit_stride) {
+  extern __shared__ u32 s32[];
+  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
+  const u32 L = T->L, k = k_begin + blockIdx.x, t = threadIdx.x;
+  const u64 u = blockIdx.y;
+  const u64 *unit_in = src ? src + u * src_unit_stride : base + u * unit_stride;
+  const ExtNtt E = T->ext[k];
+  const u32 *in = ext_limb(unit_in, L, N, k);
+  u32 *out = ext_limb(base + u * unit_stride, L, N, k);
+  NttRegs32<LOGN> y;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) y[r] = in[strided_idx32<LOGN>(t, r)];
+  ntt_fwd32<LOGN>(y, s32, E);  // contains barriers: all loads precede all stores
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = y[r];
+}
+
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
     k_ntt(const DevTables *T, u64 *base, u64 unit_stride, u32 limb_begin, int inverse,
           const u64 *src, u64 src_unit_stride) {
   extern __shared__ u64 s[];
   constexpr u32 N = 1u << LOGN;
-  const u32 L = T->L, l = limb_begin + blockIdx.x, t = threadIdx.x;
+  const u32 l = limb_begin + blockIdx.x, t = threadIdx.x;
   const u64 u = blockIdx.y;
   constexpr u32 R = NttShape<LOGN>::R;
   const u64 *unit_in = src ? src + u * src_unit_stride : base + u * unit_stride;
   u64 *unit_out = base + u * unit_stride;
-  if (l >= L) {  // extension limb, forward only (launch_ntt checks)
-    const ExtNtt E = T->ext[l - L];
-    const u32 *in = ext_limb(unit_in, L, N, l - L);
-    u32 *out = ext_limb(unit_out, L, N, l - L);
-    NttRegs32<LOGN> y;
-#pragma unroll
-    for (u32 r = 0; r < R; ++r) y[r] = in[strided_idx<LOGN>(t, r)];
-    ntt_fwd32<LOGN>(y, reinterpret_cast<u32 *>(s), E);
-#pragma unroll
-    for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = y[r];
-    return;
-  }
   const NttPrime P = T->prime[l];
   const u64 *in = unit_in + (u64)l * N;
   u64 *out = unit_out + (u64)l * N;
@@ -246,22 +265,22 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 // Forward NTT of the P limbs of every job's destination (both polys),
 // in place.  grid (K, 2 * njobs).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
     k_ntt_jobs_p(const DevTables *T, const MulJob *jobs) {
-  extern __shared__ u64 s[];
+  extern __shared__ u32 s32[];
   constexpr u32 N = 1u << LOGN;
   const u32 L = T->L, t = threadIdx.x;
   const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
   const ExtNtt E = T->ext[blockIdx.x];
   u32 *p = ext_limb(jobs[job].dst + poly * qp_poly_words(L, T->K, N), L, N, blockIdx.x);
   NttRegs32<LOGN> x;
-  constexpr u32 R = NttShape<LOGN>::R;
+  constexpr u32 R = NttShape32<LOGN>::R;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = p[strided_idx<LOGN>(t, r)];
+  for (u32 r = 0; r < R; ++r) x[r] = p[strided_idx32<LOGN>(t, r)];
   // contains barriers: all loads precede all stores
-  ntt_fwd32<LOGN>(x, reinterpret_cast<u32 *>(s), E);
+  ntt_fwd32<LOGN>(x, s32, E);
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) p[ntt_pos<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) p[ntt_pos32<LOGN>(t, r)] = x[r];
 }
 
 // ---------------------------------------------------------------------
@@ -325,13 +344,7 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // share one prime's twiddles in L1.
 // ---------------------------------------------------------------------
 template <int LOGN>
-struct ExtShape {  // 32-bit transforms: up to 2048 threads per SM
-  static constexpr int min_blocks = 2048 / NttShape<LOGN>::threads > 4
-                                        ? 4 : 2048 / NttShape<LOGN>::threads;
-};
-
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
     k_tensor_ext(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
   extern __shared__ u32 s32[];
   constexpr u32 N = 1u << LOGN;
@@ -339,7 +352,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
   const u64 job = blockIdx.x;
   const MulJob J = jobs[job];
   const u64 ps = qp_poly_words(L, T->K, N);
-  constexpr u32 R = NttShape<LOGN>::R;
+  constexpr u32 R = NttShape32<LOGN>::R;
   const ExtNtt E = T->ext[k];
   const u32 p2 = 2 * E.e.p;
   const u32 *a0 = ext_limb(J.a, L, N, k), *a1 = ext_limb(J.a + ps, L, N, k);
@@ -347,7 +360,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
   NttRegs32<LOGN> y;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) {  // products in [0, 2p)
-    const u32 c = ntt_pos<LOGN>(t, r);
+    const u32 c = ntt_pos32<LOGN>(t, r);
     u32 v;
     if (which == 0) v = mulmod_ext_lazy(a0[c], b0[c], E.e);
     else if (which == 2) v = mulmod_ext_lazy(a1[c], b1[c], E.e);
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
   ntt_inv32<LOGN>(y, s32, E);  // N d in [0, 2p)
   u32 *out = ext_limb(Tbuf + (job * 3 + which) * ps, L, N, k);
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = y[r];
+  for (u32 r = 0; r < R; ++r) out[strided_idx32<LOGN>(t, r)] = y[r];
 }
 
 template <int LOGN>
@@ -615,10 +628,10 @@ __global__ void k_pm_rows(const DevTables *T, const u64 *S, u32 seg_len, u32 G, 
 // N coefficients, zero-padded), forward NTT into dbr[row][k][N].
 // grid (4, rows).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
     k_db_load_rows(const DevTables *T, const u32 *items, u32 plen, u32 *dbr) {
   extern __shared__ u32 s32[];
-  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
   const u32 k = blockIdx.x, t = threadIdx.x, nr = T->rows.nr;
   const u64 row = blockIdx.y;
   const ExtNtt E = T->ext[k];
@@ -626,34 +639,34 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_b
   NttRegs32<LOGN> x;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) {
-    const u32 c = strided_idx<LOGN>(t, r);
+    const u32 c = strided_idx32<LOGN>(t, r);
     const u32 v = c < plen ? items[row * plen + c] : 0;
     x[r] = v > tt / 2 ? p - (tt - v) : v;
   }
   ntt_fwd32<LOGN>(x, s32, E);
   u32 *out = dbr + (row * nr + k) * N;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = x[r];
 }
 
 // Limb l of unit u of E ([units][nl][N] u64, residues below 2^54) reduced
 // modulo r_k and transformed: D[u][l][k][N] u32.  grid (4, nl, units).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
     k_rows_ntt(const DevTables *T, const u64 *Ein, u32 nl, u32 *D) {
   extern __shared__ u32 s32[];
-  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
   const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x, nr = T->rows.nr;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
   const u64 *in = Ein + (u * nl + l) * N;
   NttRegs32<LOGN> x;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62(in[strided_idx<LOGN>(t, r)], E.e);
+  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62(in[strided_idx32<LOGN>(t, r)], E.e);
   ntt_fwd32<LOGN>(x, s32, E);
   u32 *out = D + ((u * nl + l) * nr + k) * N;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = x[r];
 }
 
 // Row sums: block z = s*G + g sums D[job][l][k] * dbr[row][k] over the jobs
@@ -711,20 +724,20 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
 // Inverse transform (without N^-1) of S[u][l][k] in place: coefficient
 // order, values N x mod r_k below 2r_k.  grid (4, nl, units).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, ExtShape<LOGN>::min_blocks)
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
     k_rows_intt(const DevTables *T, u32 *S, u32 nl) {
   extern __shared__ u32 s32[];
-  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
   const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
   u32 *p = S + ((u * nl + l) * T->rows.nr + k) * N;
   NttRegs32<LOGN> x;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = p[ntt_pos<LOGN>(t, r)];
+  for (u32 r = 0; r < R; ++r) x[r] = p[ntt_pos32<LOGN>(t, r)];
   ntt_inv32<LOGN>(x, s32, E);  // contains barriers: all loads precede all stores
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) p[strided_idx<LOGN>(t, r)] = x[r];
+  for (u32 r = 0; r < R; ++r) p[strided_idx32<LOGN>(t, r)] = x[r];
 }
 
 // Row sums back to the ciphertext primes (row_digits, row_to_q): limb
@@ -980,6 +993,13 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
 // blockDim of the transform kernels: N / R threads.
 template <int LOGN>
 inline dim3 ntt_block() { return dim3(NttShape<LOGN>::threads); }
+template <int LOGN>
+inline dim3 ntt_block32() { return dim3(NttShape32<LOGN>::threads); }
+// shared memory of one 32-bit transform (one pad word per 2^RB)
+template <int LOGN>
+constexpr size_t smem32_bytes() {
+  return (size_t)((1u << LOGN) + ((1u << LOGN) >> NttShape32<LOGN>::RB)) * sizeof(u32);
+}
 
 #define CW_DISPATCH_LOGN(LOGN_, ...)                       \
   switch (LOGN_) {                                         \
@@ -1030,14 +1050,26 @@ cudaError_t launch_ntt(const DevTables *T, const DevTables &h, u64 *base, u32 un
   if (!units || limb_end <= limb_begin) return cudaSuccess;
   if (inverse && limb_end > h.L) return cudaErrorInvalidValue;  // extension limbs: forward only
   const u32 chunk = 32768;
+  const u32 qb = limb_begin, qe = limb_end < h.L ? limb_end : h.L;   // ciphertext limbs
+  const u32 kb = (limb_begin > h.L ? limb_begin : h.L) - h.L;         // extension limbs
+  const u32 ke = limb_end > h.L ? limb_end - h.L : 0;
   for (u32 u0 = 0; u0 < units; u0 += chunk) {
     u32 nu = units - u0 < chunk ? units - u0 : chunk;
+    u64 *b0 = base + (u64)u0 * unit_stride;
+    const u64 *s0 = src ? src + (u64)u0 * src_unit_stride : nullptr;
     CW_DISPATCH_LOGN(h.logN, {
-      cudaError_t e = allow_smem(k_ntt<LG>, ntt_smem_bytes<LG>());
-      if (e != cudaSuccess) return e;
-      k_ntt<LG><<<dim3(limb_end - limb_begin, nu), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
-          T, base + (u64)u0 * unit_stride, unit_stride, limb_begin, inverse ? 1 : 0,
-          src ? src + (u64)u0 * src_unit_stride : nullptr, src_unit_stride);
+      if (qe > qb) {
+        cudaError_t e = allow_smem(k_ntt<LG>, ntt_smem_bytes<LG>());
+        if (e != cudaSuccess) return e;
+        k_ntt<LG><<<dim3(qe - qb, nu), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
+            T, b0, unit_stride, qb, inverse ? 1 : 0, s0, src_unit_stride);
+      }
+      if (ke > kb) {
+        cudaError_t e = allow_smem(k_ntt32<LG>, smem32_bytes<LG>());
+        if (e != cudaSuccess) return e;
+        k_ntt32<LG><<<dim3(ke - kb, nu), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
+            T, b0, unit_stride, kb, s0, src_unit_stride);
+      }
     });
   }
   return cudaGetLastError();
@@ -1068,9 +1100,9 @@ cudaError_t launch_ntt_jobs_p(const DevTables *T, const DevTables &h, const MulJ
                               u32 njobs, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_ntt_jobs_p<LG>, ntt_smem_bytes<LG>());
+    cudaError_t e = allow_smem(k_ntt_jobs_p<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_ntt_jobs_p<LG><<<dim3(h.K, 2 * njobs), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(T, jobs);
+    k_ntt_jobs_p<LG><<<dim3(h.K, 2 * njobs), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(T, jobs);
   });
   return cudaGetLastError();
 }
@@ -1083,10 +1115,10 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
     if (e != cudaSuccess) return e;
     k_tensor_intt<LG><<<dim3(njobs, 3, h.L), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
         T, jobs, Tbuf);
-    const size_t smem32 = ntt_smem_bytes<LG>() / 2;
-    e = allow_smem(k_tensor_ext<LG>, smem32);
+    e = allow_smem(k_tensor_ext<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_tensor_ext<LG><<<dim3(njobs, 3, h.K), ntt_block<LG>(), smem32, st>>>(T, jobs, Tbuf);
+    k_tensor_ext<LG><<<dim3(njobs, 3, h.K), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
+        T, jobs, Tbuf);
   });
   return cudaGetLastError();
 }
@@ -1193,10 +1225,6 @@ u32 relin_rows_groups(const DevTables &h, u32 segs, u32 seg_len, u32 gcap) {
   return g > need ? g : need;
 }
 
-template <int LOGN>
-constexpr size_t smem32_bytes() {
-  return (size_t)((1u << LOGN) + ((1u << LOGN) >> NttShape<LOGN>::RB)) * sizeof(u32);
-}
 
 #define CW_DISPATCH_NL(NL_, GRID, BLOCK, STREAM, ...)                                  \
   switch (NL_) {                                                                       \
@@ -1225,7 +1253,7 @@ cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u3
     CW_DISPATCH_LOGN(h.logN, {
       cudaError_t e = allow_smem(k_db_load_rows<LG>, smem32_bytes<LG>());
       if (e != cudaSuccess) return e;
-      k_db_load_rows<LG><<<dim3(h.rows.nr, (u32)nr), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+      k_db_load_rows<LG><<<dim3(h.rows.nr, (u32)nr), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
           T, items + r0 * plen, plen, dbr + r0 * h.rows.nr * h.N);
     });
   }
@@ -1237,7 +1265,7 @@ static cudaError_t rows_ntt(const DevTables *T, const DevTables &h, const u64 *E
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_rows_ntt<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_rows_ntt<LG><<<dim3(h.rows.nr, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+    k_rows_ntt<LG><<<dim3(h.rows.nr, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
         T, E, nl, D);
   });
   return cudaGetLastError();
@@ -1248,7 +1276,7 @@ static cudaError_t rows_intt(const DevTables *T, const DevTables &h, u32 *S, u32
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_rows_intt<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_rows_intt<LG><<<dim3(h.rows.nr, nl, units), ntt_block<LG>(), smem32_bytes<LG>(), st>>>(
+    k_rows_intt<LG><<<dim3(h.rows.nr, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
         T, S, nl);
   });
   return cudaGetLastError();

@@ -224,4 +224,18 @@ struct NttShape {
   static constexpr int min_blocks = LOGN <= 13 ? 2 : 1;
 };
 
+// Shape of the 32-bit transforms (30-bit extension and row primes): 2^RB
+// coefficients per thread, N / 2^RB threads per block and up to 2048
+// resident threads per SM (at most four blocks), so that the operand loads
+// of some blocks overlap the transforms of others.  NTT-domain arrays of
+// these primes are produced and consumed by 32-bit kernels only, so their
+// storage order may differ from the 54-bit one.
+template <int LOGN>
+struct NttShape32 {
+  static constexpr int RB = 4;
+  static constexpr int R = 1 << RB;
+  static constexpr int threads = (1 << LOGN) / R;
+  static constexpr int min_blocks = 2048 / threads > 4 ? 4 : 2048 / threads;
+};
+
 }  // namespace cw
