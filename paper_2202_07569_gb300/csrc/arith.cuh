@@ -49,6 +49,17 @@ CW_HD u32 mulhi32(u32 a, u32 b) {
 #endif
 }
 
+// v - m if v >= m, else v (m <= 2^31): the unsigned minimum of v and
+// v - m, since v - m wraps above v exactly when v < m (one IADD and one
+// IMNMX instead of a compare, a subtraction and a select).
+CW_HD u32 csub32(u32 v, u32 m) {
+#if defined(__CUDA_ARCH__)
+  return umin(v, v - m);
+#else
+  return v >= m ? v - m : v;
+#endif
+}
+
 CW_HD u64 addq(u64 a, u64 b, u64 q) {
   u64 s = a + b;
   return s >= q ? s - q : s;
@@ -164,8 +175,7 @@ struct ExtPrime {
 // v mod p for any v < 2^64: qh = floor(v mu64 / 2^64) lies in
 // (v/p - v/2^64 - 1, v/p], so v - qh p is in [0, 2p).
 CW_HD u32 reduce_ext(u64 v, const ExtPrime &E) {
-  const u32 r = (u32)(v - mulhi(v, E.mu64) * E.p);
-  return r >= E.p ? r - E.p : r;
+  return csub32((u32)(v - mulhi(v, E.mu64) * E.p), E.p);
 }
 
 // v mod p for v < 2^62, on 32-bit words (the row transforms' loads; in the
@@ -176,12 +186,16 @@ CW_HD u32 reduce_ext(u64 v, const ExtPrime &E) {
 // x/p - x/2^61 - 2^29/p < qh <= x/p, i.e. x/p - 1.51 < qh, so
 // r = x - qh p is in [0, 3p) (the low word suffices) and two subtractions
 // finish it.
+// The same reduction left lazy in [0, 3p) (below 2^32): the input of a
+// forward 32-bit transform, which accepts values below 4p.
+CW_HD u32 reduce_ext62_lazy(u64 v, const ExtPrime &E) {
+  const u64 x = (u64)(u32)(v >> 32) * E.c32 + (u32)v;
+  return (u32)x - mulhi32((u32)(x >> 29), E.mu61) * E.p;
+}
 CW_HD u32 reduce_ext62(u64 v, const ExtPrime &E) {
   const u64 x = (u64)(u32)(v >> 32) * E.c32 + (u32)v;
   const u32 qh = mulhi32((u32)(x >> 29), E.mu61);
-  u32 r = (u32)x - qh * E.p;
-  r = r >= 2 * E.p ? r - 2 * E.p : r;
-  return r >= E.p ? r - E.p : r;
+  return csub32(csub32((u32)x - qh * E.p, 2 * E.p), E.p);
 }
 
 // a b mod p in [0, 2p) for a, b < p (Barrett on 32-bit words): with
@@ -191,8 +205,7 @@ CW_HD u32 reduce_ext62(u64 v, const ExtPrime &E) {
 CW_HD u32 mulmod_ext_lazy(u32 a, u32 b, const ExtPrime &E) {
   const u64 x = (u64)a * b;
   const u32 qh = mulhi32((u32)(x >> 28), E.mu60);
-  const u32 r = (u32)x - qh * E.p;
-  return r >= 2 * E.p ? r - 2 * E.p : r;
+  return csub32((u32)x - qh * E.p, 2 * E.p);
 }
 
 // ---------------------------------------------------------------------
@@ -382,10 +395,10 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
 // is at least 2^-24 away from a half integer, and a 6.58 fixed-point sum of
 // y_k floor(2^58 / r_k), low by less than nr 2^-28, rounds to rho exactly.
 // ---------------------------------------------------------------------
-constexpr int kRowPrimes = 4;  // at most
+constexpr int kRowPrimes = 5;  // at most (the key-switch basis uses five)
 
 struct RowTab {
-  u32 nr;                             // row primes in use: 3 or 4
+  u32 nr;                             // primes in use: 3 or 4 (rows), 5 (key switch)
   u32 rmax;                           // rows per group the basis holds exactly
   ExtPrime r[kRowPrimes];
   u32 theta[kRowPrimes];              // (R/r_k)^-1 N^-1 mod r_k
@@ -412,7 +425,7 @@ CW_HD u64 row_digits(const u32 *xr, u32 *y, const RowTab &T, bool *far) {
   return (fix + (1ull << 57)) >> 58;
 }
 
-// x mod q_j from the digits: sum_k y_k (R/r_k) - rho R (at most five
+// x mod q_j from the digits: sum_k y_k (R/r_k) - rho R (at most six
 // products of values below 2^30 with 27-bit halves, sum below 2^88).
 CW_HD u64 row_to_q(const u32 *y, u64 rho, int j, const RowTab &T) {
   u64 ll = wmul((u32)rho, T.negr2[j][0]), x = wmul((u32)rho, T.negr2[j][1]);  // rho <= nr

@@ -178,6 +178,10 @@ struct cwpir_ctx {
   int32_t next_db = 1;
   std::string err;
   int opt_share = 1, opt_graph = 0;
+  // internal tree nodes switch keys in the key-switch basis (DevTables ksr)
+  // with the relinearisation key in that basis: [L][2][L][5][N] u32
+  bool ksr = false;
+  DevBuf ksr_key;
   u32 opt_batch_rows = 0;
   u32 opt_max_jobs = 0;
   int opt_row_basis = 1;
@@ -323,6 +327,19 @@ int build_tables(cwpir_ctx *c) {
   fill_rows(h.rows, c->q, c->p, N, nr);
   h.rows.rmax = (u32)std::min<u64>(row_group_limit(c->q, c->p, nr, N, c->t), 2048);
   if (h.rows.rmax < 32) return fail(c, CWPIR_EINTERNAL, "row basis too small");
+  // key-switch basis: the first five extension primes, when there are five
+  // and their product R holds |sum_i D_i key_ij| < L N q_max^2 with the
+  // row-digit margin (|x| < (1 - 2^-23) R / 2)
+  if (K >= cw::kKsrPrimes) {
+    long double lr = 0;
+    for (u32 k = 0; k < cw::kKsrPrimes; ++k) lr += log2l((long double)c->p[k]);
+    const long double need = log2l((long double)L) + log2l((long double)N) +
+                             2 * log2l((long double)*std::max_element(c->q.begin(), c->q.end()));
+    if (lr - 1 + log2l(1.0L - 1.0L / (1 << 23)) > need) {
+      fill_rows(h.ksr, c->q, c->p, N, cw::kKsrPrimes);
+      c->ksr = true;
+    }
+  }
   CUDA_TRY(c, cudaMalloc(&c->d_tab, sizeof(cw::DevTables)));
   CUDA_TRY(c, cudaMemcpy(c->d_tab, &h, sizeof h, cudaMemcpyHostToDevice));
   return CWPIR_OK;
@@ -338,13 +355,20 @@ bool valid_residues(const u64 *v, u32 L, u32 N, const std::vector<u64> &q, u64 c
   return true;
 }
 
-int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks) {
+// A switching key to the device: NTT form modulo each q_j with Shoup
+// companions (kb, ks) and, with ksr_out, also in the key-switch basis.
+int upload_key(cwpir_ctx *c, const u64 *key, DevBuf &kb, DevBuf &ks, DevBuf *ksr_out) {
   const u64 words = 2ull * c->L * c->L * c->N;
   if (!valid_residues(key, c->L, c->N, c->q, 2ull * c->L))
     return fail(c, CWPIR_EINVAL, "switching key residue out of range");
   CUDA_TRY(c, kb.ensure(words, &c->acct));
   CUDA_TRY(c, ks.ensure(words, &c->acct));
   CUDA_TRY(c, cudaMemcpy(kb.p, key, words * sizeof(u64), cudaMemcpyHostToDevice));
+  if (ksr_out) {  // from the coefficient form, before kb is transformed
+    CUDA_TRY(c, ksr_out->ensure(words * cw::kKsrPrimes / 2, &c->acct));
+    CUDA_TRY(c, cw::launch_ksr_key(c->d_tab, c->h, kb.p, reinterpret_cast<u32 *>(ksr_out->p),
+                                   c->stream));
+  }
   CUDA_TRY(c, cw::launch_key_prep(c->d_tab, c->h, kb.p, ks.p, 1, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return CWPIR_OK;
@@ -639,6 +663,25 @@ int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp
   CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, S.Tbuf.p, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, S.Tbuf.p, ch.count, S.E.p, S.d_err, st); }));
   const bool rows = ch.mode == cw::ROOT_PM && P->rows_db;
+  if (ch.mode == cw::INTERNAL && c->ksr) {
+    // key switch in the key-switch basis (digits in the dead tensor buffer,
+    // the basis sums in the digit-transform buffer), the result in
+    // coefficient form to CP, then both parts of the QP-NTT destination
+    CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
+      return cw::launch_relin_ksr(c->d_tab, c->h, S.E.p, ch.count,
+                                  reinterpret_cast<const u32 *>(c->ksr_key.p),
+                                  reinterpret_cast<u32 *>(S.Tbuf.p), reinterpret_cast<u32 *>(S.DN.p),
+                                  S.d_err, S.CP.p, st);
+    }));
+    CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, S.CP.p, jobs, ch.count, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_q(c->d_tab, c->h, S.CP.p, jobs, ch.count, st); }));
+    CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_p(c->d_tab, c->h, jobs, ch.count, st); }));
+    c->stats.kernel_launches += 3 + 4 + 3;  // tensor, scale; key switch; lift, NTTs
+    c->stats.mults += ch.count;
+    c->stats.ntt_polys += (u64)ch.count * (3 * (c->L + c->K) + 3 * c->L * cw::kKsrPrimes +
+                                           2 * (c->L + c->K));
+    return CWPIR_OK;
+  }
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
     if (rows)
       return cw::launch_relin_rows(c->d_tab, c->h, S.E.p, ch.count, ch.segs, jobs, c->rlk.p,
@@ -1035,7 +1078,7 @@ int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys, cwpir_ctx **
     g_setup_error = c->err;
     return rc;
   }
-  rc = upload_key(c.get(), keys->relin, c->rlk, c->rlk_s);
+  rc = upload_key(c.get(), keys->relin, c->rlk, c->rlk_s, c->ksr ? &c->ksr_key : nullptr);
   if (rc) {
     g_setup_error = c->err;
     return rc;
@@ -1044,7 +1087,7 @@ int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys, cwpir_ctx **
     u32 g = keys->galois_elts[i];
     if (!(g & 1) || g >= 2 * N) return fail(nullptr, CWPIR_EINVAL, "bad Galois element %u", g);
     auto kb = std::make_shared<DevBuf>(), ks = std::make_shared<DevBuf>();
-    rc = upload_key(c.get(), keys->galois + (u64)i * 2 * L * L * N, *kb, *ks);
+    rc = upload_key(c.get(), keys->galois + (u64)i * 2 * L * L * N, *kb, *ks, nullptr);
     if (rc) {
       g_setup_error = c->err;
       return rc;

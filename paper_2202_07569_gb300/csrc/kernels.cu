@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::m
     else if (which == 2) v = mulmod_ext_lazy(a1[c], b1[c], E.e);
     else {
       v = mulmod_ext_lazy(a0[c], b1[c], E.e) + mulmod_ext_lazy(a1[c], b0[c], E.e);
-      v = v >= p2 ? v - p2 : v;
+      v = csub32(v, p2);
     }
     y[r] = v;
   }
@@ -649,22 +649,23 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::m
   for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = x[r];
 }
 
-// Limb l of unit u of E ([units][nl][N] u64, residues below 2^54) reduced
-// modulo r_k and transformed: D[u][l][k][N] u32.  grid (4, nl, units).
+// Limb l of unit u of E (unit stride ustride u64 words, limbs of N
+// residues below 2^54) reduced modulo the extension prime k < np and
+// transformed: D[u][l][k][N] u32.  grid (np, nl, units).
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
-    k_rows_ntt(const DevTables *T, const u64 *Ein, u32 nl, u32 *D) {
+    k_rows_ntt(const DevTables *T, const u64 *Ein, u64 ustride, u32 nl, u32 np, u32 *D) {
   extern __shared__ u32 s32[];
   constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
-  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x, nr = T->rows.nr;
+  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
-  const u64 *in = Ein + (u * nl + l) * N;
+  const u64 *in = Ein + u * ustride + (u64)l * N;
   NttRegs32<LOGN> x;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62(in[strided_idx32<LOGN>(t, r)], E.e);
+  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62_lazy(in[strided_idx32<LOGN>(t, r)], E.e);
   ntt_fwd32<LOGN>(x, s32, E);
-  u32 *out = D + ((u * nl + l) * nr + k) * N;
+  u32 *out = D + ((u * nl + l) * np + k) * N;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = x[r];
 }
@@ -721,17 +722,17 @@ __global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_l
   for (int l = 0; l < NL; ++l) o[l * kN] = reduce_ext(acc[l], E);
 }
 
-// Inverse transform (without N^-1) of S[u][l][k] in place: coefficient
-// order, values N x mod r_k below 2r_k.  grid (4, nl, units).
+// Inverse transform (without N^-1) of S[u][l][k] (k < np) in place:
+// coefficient order, values N x mod p_k below 2p_k.  grid (np, nl, units).
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
-    k_rows_intt(const DevTables *T, u32 *S, u32 nl) {
+    k_rows_intt(const DevTables *T, u32 *S, u32 nl, u32 np) {
   extern __shared__ u32 s32[];
   constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
   const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
-  u32 *p = S + ((u * nl + l) * T->rows.nr + k) * N;
+  u32 *p = S + ((u * nl + l) * np + k) * N;
   NttRegs32<LOGN> x;
 #pragma unroll
   for (u32 r = 0; r < R; ++r) x[r] = p[ntt_pos32<LOGN>(t, r)];
@@ -764,6 +765,72 @@ __global__ void k_rows_crt(const DevTables *T, const u32 *S, u32 nl, u64 *Eo, u6
 #pragma unroll
     for (int j = 0; j < L; ++j) o[(u64)j * N] = row_to_q(y, rho, j, RT);
   }
+}
+
+// Key switch in the key-switch basis (launch_relin_ksr), the pointwise
+// step: O[job][c L + j][k] = sum_i D[job][i][k] * ks[i][c][j][k] modulo
+// p_k, k < 5, for c < 2 and j < L.  The L products of residues below 2^30
+// sum below L 2^60 <= 2^63 and are reduced once.  grid (N/256, 5, njobs).
+template <int L>
+__global__ void k_ksr_mac(const DevTables *T, const u32 *D, const u32 *ks, u32 *O) {
+  constexpr u32 NP = kKsrPrimes;
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  const u64 job = blockIdx.z;
+  const ExtPrime E = T->ext[k].e;
+  const u64 kc = (u64)k * N + c;
+  u32 d[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) d[i] = D[(job * L + i) * NP * N + kc];
+#pragma unroll
+  for (int o = 0; o < 2 * L; ++o) {
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc += wmul(d[i], ks[((u64)i * 2 * L + o) * NP * N + kc]);
+    O[(job * 2 * L + o) * NP * N + kc] = reduce_ext(acc, E);
+  }
+}
+
+// Key switch in the key-switch basis, the way back: the five residues of
+// N x (x = sum_i D_i key_i, an integer below 2^125 in magnitude) give x
+// modulo q_j exactly (row_digits, row_to_q with the basis tables), and
+// C[job][c][j] = (x + e_c,j) mod q_j.  grid (N/256, 2L, njobs).
+template <int L>
+__global__ void k_ksr_crt(const DevTables *T, const u32 *O, const u64 *E, int *err, u64 *C,
+                          const __grid_constant__ RowTab KT) {
+  constexpr u32 NP = kKsrPrimes;
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, o = blockIdx.y;
+  const u32 j = o % L, comp = o / L;
+  const u64 job = blockIdx.z;
+  const u32 *src = O + (job * 2 * L + o) * NP * N + c;
+  u32 xr[kRowPrimes], y[kRowPrimes];
+#pragma unroll
+  for (int k = 0; k < kRowPrimes; ++k) xr[k] = (u32)k < NP ? src[(u64)k * N] : 0;
+  bool far;
+  const u64 rho = row_digits(xr, y, KT, &far);
+  if (far) atomicOr(err, 4);
+  const u64 x = row_to_q(y, rho, (int)j, KT);
+  const u64 e = E[(job * 3 + comp) * L * N + (u64)j * N + c];
+  C[(job * 2 + comp) * L * N + (u64)j * N + c] = addq(x, e, KT.q[j]);
+}
+
+// Forward NTT of the Q limbs of C[job][poly][j] (coefficient form) into
+// jobs[job].dst (QP layout, NTT form).  grid (L, 2 * njobs).
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
+    k_ntt_jobs_q(const DevTables *T, const u64 *C, const MulJob *jobs) {
+  extern __shared__ u64 s[];
+  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
+  const u32 L = T->L, t = threadIdx.x, j = blockIdx.x;
+  const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
+  const NttPrime P = T->prime[j];
+  const u64 *in = C + (((u64)job * 2 + poly) * L + j) * N;
+  u64 *out = jobs[job].dst + poly * qp_poly_words(L, T->K, N) + (u64)j * N;
+  NttRegs<LOGN> x;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) x[r] = in[strided_idx<LOGN>(t, r)];
+  ntt_fwd<LOGN>(x, s, P);
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
 }
 
 // (B) producing the NTT-form result: INTERNAL mode writes it to the Q
@@ -1260,24 +1327,68 @@ cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u3
   return cudaGetLastError();
 }
 
-static cudaError_t rows_ntt(const DevTables *T, const DevTables &h, const u64 *E, u32 nl,
-                            u32 units, u32 *D, cudaStream_t st) {
+// units of nl limbs (unit stride ustride) -> D[u][l][k < np] (k_rows_ntt)
+static cudaError_t rns_ntt(const DevTables *T, const DevTables &h, const u64 *E, u64 ustride,
+                           u32 nl, u32 np, u32 units, u32 *D, cudaStream_t st) {
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_rows_ntt<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_rows_ntt<LG><<<dim3(h.rows.nr, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
-        T, E, nl, D);
+    k_rows_ntt<LG><<<dim3(np, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
+        T, E, ustride, nl, np, D);
   });
   return cudaGetLastError();
 }
 
-static cudaError_t rows_intt(const DevTables *T, const DevTables &h, u32 *S, u32 nl, u32 units,
-                             cudaStream_t st) {
+static cudaError_t rns_intt(const DevTables *T, const DevTables &h, u32 *S, u32 nl, u32 np,
+                            u32 units, cudaStream_t st) {
   CW_DISPATCH_LOGN(h.logN, {
     cudaError_t e = allow_smem(k_rows_intt<LG>, smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_rows_intt<LG><<<dim3(h.rows.nr, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
-        T, S, nl);
+    k_rows_intt<LG><<<dim3(np, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
+        T, S, nl, np);
+  });
+  return cudaGetLastError();
+}
+
+static cudaError_t rows_ntt(const DevTables *T, const DevTables &h, const u64 *E, u32 nl,
+                            u32 units, u32 *D, cudaStream_t st) {
+  return rns_ntt(T, h, E, (u64)nl * h.N, nl, h.rows.nr, units, D, st);
+}
+
+static cudaError_t rows_intt(const DevTables *T, const DevTables &h, u32 *S, u32 nl, u32 units,
+                             cudaStream_t st) {
+  return rns_intt(T, h, S, nl, h.rows.nr, units, st);
+}
+
+cudaError_t launch_relin_ksr(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
+                             const u32 *ks, u32 *D, u32 *O, int *err, u64 *C, cudaStream_t st) {
+  if (!njobs) return cudaSuccess;
+  const u32 L = h.L, N = h.N;
+  const u64 LN = (u64)L * N;
+  // the digits of e2 (its limbs) into the basis
+  cudaError_t e = rns_ntt(T, h, E + 2 * LN, 3 * LN, L, kKsrPrimes, njobs, D, st);
+  if (e != cudaSuccess) return e;
+  CW_DISPATCH_L(L, k_ksr_mac, dim3(N / 256, kKsrPrimes, njobs), 256, 0, st, T, D, ks, O);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rns_intt(T, h, O, 2 * L, kKsrPrimes, njobs, st)) != cudaSuccess) return e;
+  CW_DISPATCH_L(L, k_ksr_crt, dim3(N / 256, 2 * L, njobs), 256, 0, st, T, O, E, err, C, h.ksr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ksr_key(const DevTables *T, const DevTables &h, const u64 *key, u32 *ks,
+                           cudaStream_t st) {
+  // every [N] limb of the key is one unit of one limb
+  return rns_ntt(T, h, key, h.N, 1, kKsrPrimes, 2 * h.L * h.L, ks, st);
+}
+
+cudaError_t launch_ntt_jobs_q(const DevTables *T, const DevTables &h, const u64 *C,
+                              const MulJob *jobs, u32 njobs, cudaStream_t st) {
+  if (!njobs) return cudaSuccess;
+  CW_DISPATCH_LOGN(h.logN, {
+    cudaError_t e = allow_smem(k_ntt_jobs_q<LG>, ntt_smem_bytes<LG>());
+    if (e != cudaSuccess) return e;
+    k_ntt_jobs_q<LG><<<dim3(h.L, 2 * njobs), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
+        T, C, jobs);
   });
   return cudaGetLastError();
 }

@@ -31,7 +31,11 @@ struct DevTables {
   LiftTab lift;           // centered Q -> P conversion (leaves, nodes)
   ScaleTab scale;         // exact round(t d / Q)
   RowTab rows;            // row basis: first nr extension primes -> Q
+  RowTab ksr;             // key-switch basis: first five extension primes -> Q
 };
+
+// Primes of the key-switch basis (the first kKsrPrimes extension primes).
+constexpr u32 kKsrPrimes = 5;
 
 // QP layout of one polynomial (NTT domain or, for the tensor buffer,
 // coefficients): L limbs of N u64 residues mod q_j, then K limbs of N u32
@@ -124,6 +128,25 @@ cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 
 cudaError_t launch_plain_mul_rows(const DevTables *T, const DevTables &h, const u64 *ct,
                                   const MulJob *job, const u32 *dbr, u32 *D, u32 *S, int *err,
                                   u64 *out, cudaStream_t st);
+// Key switching of the internal tree nodes through the key-switch basis
+// (RowTab ksr): the digits of e2 (its limbs, integers below q_i) and the
+// switching key (integers below q_j) multiply exactly as integer
+// polynomials modulo five 30-bit primes, |sum_i D_i * key_ij| < L N q^2 <
+// 2^125 < R/2, and the sums come back to each q_j by an exact CRT.  The
+// result C[job][2][L][N] = (e0 + sum_i D_i b_i, e1 + sum_i D_i a_i) mod q_j
+// is in coefficient form.  ks: the key in the basis ([L][2][L][5][N] u32,
+// NTT form); D: scratch [njobs][L][5][N] u32; O: scratch
+// [njobs][2L][5][N] u32.
+cudaError_t launch_relin_ksr(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
+                             const u32 *ks, u32 *D, u32 *O, int *err, u64 *C, cudaStream_t st);
+// The switching key [L][2][L][N] (coefficient form, residues below q_j)
+// into the key-switch basis: ks [L][2][L][5][N] u32, NTT form.
+cudaError_t launch_ksr_key(const DevTables *T, const DevTables &h, const u64 *key, u32 *ks,
+                           cudaStream_t st);
+// Forward NTT of the Q limbs of C[job][2][L][N] (coefficient form) into
+// the Q limbs of jobs[job].dst (QP layout).
+cudaError_t launch_ntt_jobs_q(const DevTables *T, const DevTables &h, const u64 *C,
+                              const MulJob *jobs, u32 njobs, cudaStream_t st);
 // k = 1: P[job][sp][2][L][N] = leaf * DB[row][p].
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
                            u32 njobs, u32 sp, const u64 *db, u64 *P, cudaStream_t st);

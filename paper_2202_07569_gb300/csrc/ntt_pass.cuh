@@ -129,6 +129,23 @@ CW_HD void ld_pair32(const u32 *p, u32 &a, u32 &b) {
 #endif
 }
 
+// Two consecutive (twiddle, Shoup) pairs from an even pair index: one
+// 16-byte load on the device.
+CW_HD void ld_pair32x2(const u32 *p, u32 &a0, u32 &b0, u32 &a1, u32 &b1) {
+#if defined(__CUDA_ARCH__)
+  const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+  a0 = v.x;
+  b0 = v.y;
+  a1 = v.z;
+  b1 = v.w;
+#else
+  a0 = p[0];
+  b0 = p[1];
+  a1 = p[2];
+  b1 = p[3];
+#endif
+}
+
 // a*w mod p in [0, 2p) for any a < 2^32
 CW_HD u32 shoup32_lazy(u32 a, u32 w, u32 ws, u32 p) { return a * w - mulhi32(a, ws) * p; }
 
@@ -140,20 +157,27 @@ CW_HD void fwd_pass32(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *psi2, u32 
   for (int bi = RB - 1; bi >= 0; --bi) {
     if ((u32)bi >= c) continue;
     const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
+    // the level's twiddles of this thread: R >> (rb + 1) consecutive pairs
+    // from m + ((t >> w) << (RB - 1 - rb)) (hv fills the low bits of
+    // pass_idx >> (b + 1)); with two or more of them b <= LOGN - 2, so m
+    // and the start are even and two pairs come in one 16-byte load
+    const u32 nh = R >> (rb + 1), g0 = m + ((t >> w) << (RB - 1 - rb));
 #pragma unroll
-    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
-      const u32 r0 = hv << (rb + 1);
-      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
-      u32 W, Ws;
-      ld_pair32(psi2 + 2 * (m + g), W, Ws);
+    for (u32 hv = 0; hv < nh; hv += 2) {
+      u32 W[2], Ws[2];
+      if (nh == 1) ld_pair32(psi2 + 2 * g0, W[0], Ws[0]);
+      else ld_pair32x2(psi2 + 2 * (g0 + hv), W[0], Ws[0], W[1], Ws[1]);
 #pragma unroll
-      for (u32 lv = 0; lv < (1u << rb); ++lv) {
-        const u32 r = r0 | lv;
-        u32 U = x[r];
-        U = U >= p2 ? U - p2 : U;
-        const u32 V = shoup32_lazy(x[r | (1u << rb)], W, Ws, p);
-        x[r] = U + V;
-        x[r | (1u << rb)] = U - V + p2;
+      for (u32 h = 0; h < 2 && hv + h < nh; ++h) {
+        const u32 r0 = (hv + h) << (rb + 1);
+#pragma unroll
+        for (u32 lv = 0; lv < (1u << rb); ++lv) {
+          const u32 r = r0 | lv;
+          const u32 U = csub32(x[r], p2);
+          const u32 V = shoup32_lazy(x[r | (1u << rb)], W[h], Ws[h], p);
+          x[r] = U + V;
+          x[r | (1u << rb)] = U - V + p2;
+        }
       }
     }
   }
@@ -167,29 +191,29 @@ CW_HD void inv_pass32(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *ipsi2, u32
   for (int bi = 0; bi < RB; ++bi) {
     if ((u32)bi >= c) continue;
     const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
+    const u32 nh = R >> (rb + 1), g0 = m + ((t >> w) << (RB - 1 - rb));
 #pragma unroll
-    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
-      const u32 r0 = hv << (rb + 1);
-      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
-      u32 W, Ws;
-      ld_pair32(ipsi2 + 2 * (m + g), W, Ws);
+    for (u32 hv = 0; hv < nh; hv += 2) {
+      u32 W[2], Ws[2];
+      if (nh == 1) ld_pair32(ipsi2 + 2 * g0, W[0], Ws[0]);
+      else ld_pair32x2(ipsi2 + 2 * (g0 + hv), W[0], Ws[0], W[1], Ws[1]);
 #pragma unroll
-      for (u32 lv = 0; lv < (1u << rb); ++lv) {
-        const u32 r = r0 | lv;
-        const u32 U = x[r], V = x[r | (1u << rb)];
-        const u32 S = U + V;
-        x[r] = S >= p2 ? S - p2 : S;
-        x[r | (1u << rb)] = shoup32_lazy(U - V + p2, W, Ws, p);
+      for (u32 h = 0; h < 2 && hv + h < nh; ++h) {
+        const u32 r0 = (hv + h) << (rb + 1);
+#pragma unroll
+        for (u32 lv = 0; lv < (1u << rb); ++lv) {
+          const u32 r = r0 | lv;
+          const u32 U = x[r], V = x[r | (1u << rb)];
+          const u32 S = U + V;
+          x[r] = csub32(S, p2);
+          x[r | (1u << rb)] = shoup32_lazy(U - V + p2, W[h], Ws[h], p);
+        }
       }
     }
   }
 }
 
-CW_HD u32 reduce4_32(u32 v, u32 p) {
-  const u32 p2 = 2 * p;
-  v = v >= p2 ? v - p2 : v;
-  return v >= p ? v - p : v;
-}
+CW_HD u32 reduce4_32(u32 v, u32 p) { return csub32(csub32(v, 2 * p), p); }
 
 // Pass schedule: forward passes take bits from the top in chunks of RB,
 // inverse passes from the bottom; a pass of c < RB bits uses the window

@@ -188,6 +188,31 @@ def test_row_basis_crt(orc, N, L, nr):
         assert [int(v) for v in out] == [x % qq for qq in q], x
 
 
+@pytest.mark.parametrize("N,L", [(1024, 2), (8192, 4), (16384, 7), (16384, 8)])
+def test_key_switch_basis_crt(orc, N, L):
+    """The key switch of the internal tree nodes sums the products of the
+    L digits D_i < q_i with the key limbs < q_j as integer polynomials in
+    the basis of the first five extension primes: |x| < L N q_max^2.  x is
+    recovered modulo every q_j from N x modulo the five primes at that
+    bound, its negative and values in between, with lazy residues."""
+    q = [int(v) for v in orc.primes(N, L)]
+    r = _ext_primes(N, L, q)[:5]
+    R = math.prod(r)
+    xmax = L * N * max(q) ** 2
+    assert 2 * xmax < R * (1 - 2.0 ** -23)  # the basis holds every sum
+    xs = [0, 1, -1, xmax, -xmax, xmax - 12345, -(xmax // 7)]
+    st = syn.Stream(12, N + L)
+    for w in st.words(12).tolist():
+        xs.append((int(w) * xmax) >> 64)
+        xs.append(-((int(w) * xmax) >> 64))
+    for i, x in enumerate(xs):
+        xr = np.array([(N * x) % rk + (rk if (i + k) % 2 == 0 else 0)
+                       for k, rk in enumerate(r)], np.uint32)
+        out = np.zeros(L, np.uint64)
+        assert emu.lib().emu_row_crt(N, L, np.array(q, np.uint64), T, 5, xr, out) == 0
+        assert [int(v) for v in out] == [x % qq for qq in q], x
+
+
 @pytest.mark.parametrize("N,L,nr", [(8192, 4, 3), (16384, 7, 3), (1024, 2, 4)])
 def test_row_basis_sums_at_the_group_limit(orc, N, L, nr):
     """The row path of the last tree level (transforms modulo the row
