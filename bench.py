@@ -301,10 +301,11 @@ def run_gpu(args, rank: int, world: int, dist, keep: bool = False):
 def run_sharded(args, rank: int, world: int, dist):
     """The metric's workload with the database's rows sharded over the
     ranks (one GPU each): every rank answers the query over its block of
-    rows and the partial responses are summed modulo q_j after an
-    all-gather (paper_2202_07569_gb300/shard.py).  Total work is fixed:
-    strong scaling.  At one rank the step is the plain answer plus a sum of
-    one partial."""
+    rows and the partial responses meet in one exchange (--exchange: a SUM
+    all-reduce of the u64 residues then the reduction modulo q_j, or an
+    all-gather then the modular sum; paper_2202_07569_gb300/shard.py).
+    Total work is fixed: strong scaling.  At one rank the step is the plain
+    answer plus the reduction of one partial."""
     import torch
 
     from paper_2202_07569_gb300 import binding as B
@@ -322,7 +323,7 @@ def run_sharded(args, rank: int, world: int, dist):
     d_query = torch.from_numpy(query.view(np.int64)).to(f"cuda:{dev}")
     d_resp = torch.empty((2, WL["L"], WL["N"]), dtype=torch.int64, device=f"cuda:{dev}")
     for _ in range(args.warmup):
-        sh.answer_device(d_query, d_resp)
+        sh.answer_device(d_query, d_resp, exchange=args.exchange)
     torch.cuda.synchronize()
     stats = ctx.last_stats()
     if dist:
@@ -333,7 +334,7 @@ def run_sharded(args, rank: int, world: int, dist):
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(args.steps):
-            sh.answer_device(d_query, d_resp)
+            sh.answer_device(d_query, d_resp, exchange=args.exchange)
         t1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -353,7 +354,7 @@ def run_sharded(args, rank: int, world: int, dist):
             dist.barrier()
         t = time.perf_counter()
         d_query.copy_(h_query, non_blocking=True)
-        sh.answer_device(d_query, d_resp)
+        sh.answer_device(d_query, d_resp, exchange=args.exchange)
         h_resp.copy_(d_resp, non_blocking=True)
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t)
@@ -369,7 +370,7 @@ def run_sharded(args, rank: int, world: int, dist):
         "gpu_launches": (int(stats["kernel_launches"]) + 1) * args.steps,
         "stats": stats,
         "clocks": clk.summary(),
-        "shard": {"rank_rows": [sh.lo, sh.hi], "world": world},
+        "shard": {"rank_rows": [sh.lo, sh.hi], "world": world, "exchange": args.exchange},
     }
     sh.close()
     ctx.close()
@@ -389,7 +390,7 @@ def run_large(args):
     from paper_2202_07569_gb300 import binding as B
     from paper_2202_07569_gb300 import synthetic as syn
 
-    N, L, n, k = 8192, 4, 16384, 2
+    N, L, n, k = 8192, 4, args.rows or 16384, 2  # --rows: a profiling size
     m = B.code_length(n, k)
     q = B.default_primes(N, L)
     rlk = syn.uniform_residues(syn.Stream(51, 3), q, (L, 2), N)
@@ -457,8 +458,8 @@ def run_large(args):
             "unit": "MB/s", "value": runs[-1]["value"], "runs": runs,
             "time_ratio_s17_vs_s1": ratio, "payload_ratio": 17.0,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
-            "config": {"workload": "index PIR n=16384 rows, k=2, m=%d, BFV N=8192 L=4, "
-                                   "rows of s plaintexts of 8192 16-bit coefficients" % m}}
+            "config": {"workload": "index PIR n=%d rows, k=2, m=%d, BFV N=8192 L=4, "
+                                   "rows of s plaintexts of 8192 16-bit coefficients" % (n, m)}}
 
 
 def run_lossy(args):
@@ -925,6 +926,9 @@ def main():
                     help="profiling only: answer over the first ROWS rows instead of 65536")
     ap.add_argument("--max-jobs", type=int, default=0,
                     help="multiplications per kernel launch (0 = library default)")
+    ap.add_argument("--exchange", default="allreduce", choices=["allreduce", "allgather"],
+                    help="exchange step of the row-sharded answer: one SUM all-reduce of the "
+                         "u64 residues, or an all-gather of the partial responses")
     ap.add_argument("--no-systems", action="store_true",
                     help="only the metric's workload: skip the keyword, batching and serving "
                          "blocks that follow its timed region")
@@ -1002,7 +1006,15 @@ def main():
         return
     systems = world == 1 and not args.no_systems and not args.rows
     res, keep = run_gpu(args, rank, world, dist, keep=systems)
+    sharded = None
+    if world > 1:
+        # the same workload with the rows sharded over the ranks, so that a
+        # multi-GPU run also exercises the exchange step (after the replicas'
+        # timed region, which the line's value reports)
+        sharded = run_sharded(args, rank, world, dist)
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return
     line = dict(base)
     if args.rows:
@@ -1011,6 +1023,10 @@ def main():
     if args.max_jobs:
         line["config"]["max_jobs"] = args.max_jobs
     line.update(res)
+    if sharded is not None:
+        line["sharded"] = {k: sharded[k] for k in ("value", "ms_per_step", "scaling", "e2e",
+                                                    "gpu_launches", "clocks", "shard")}
+        line["sharded"]["unit"] = "MB/s"
     if systems:
         # the other configurations on the same GPU, after the metric's timed
         # region: the keyword workload, batching over four databases and

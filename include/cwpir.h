@@ -259,6 +259,15 @@ int cwpir_sum_responses_device(cwpir_ctx *ctx, uint32_t count, uint32_t s,
                                const uint64_t *d_parts, uint64_t *d_out,
                                void *stream);
 
+/* The same exchange as one all-reduce: d_sums [s][2][L][N] holds the
+ * element-wise u64 sums (wrapping modulo 2^64 is the caller's to avoid: at
+ * most 1023 partial responses of residues below 2^54) of the partial
+ * responses of the shards; d_out [s][2][L][N] = d_sums mod q_j, the
+ * response.  d_out may equal d_sums.  Device memory on ctx's GPU; returns
+ * once enqueued on `stream`.  EINVAL for a null pointer or s out of range. */
+int cwpir_reduce_responses_device(cwpir_ctx *ctx, uint32_t s, const uint64_t *d_sums,
+                                  uint64_t *d_out, void *stream);
+
 /* Autotuner: times answers of the nq device queries (as for
  * cwpir_answer_batch_device) for each candidate number of multiplications
  * per launch in `candidates` (count entries, 0 = automatic), keeps the

@@ -128,6 +128,7 @@ def lib():
             "cwpir_answer": (I, [vp, C.c_int32, U32, u64p, u64p]),
             "cwpir_answer_device": (I, [vp, C.c_int32, U32, vp, vp, vp]),
             "cwpir_sum_responses_device": (I, [vp, U32, U32, vp, vp, vp]),
+            "cwpir_reduce_responses_device": (I, [vp, U32, vp, vp, vp]),
             "cwpir_mul": (I, [vp, u64p, u64p, u64p]),
             "cwpir_substitute": (I, [vp, U32, u64p, u64p]),
             "cwpir_expand": (I, [vp, U32, U32, u64p, u64p]),
@@ -345,6 +346,11 @@ class Context:
         [s][2][L][N] modulo each q_j: the exchange step of a sharded database."""
         self._check(lib().cwpir_sum_responses_device(self._h, count, s, parts_ptr, out_ptr,
                                                      stream))
+
+    def reduce_responses_device(self, s: int, sums_ptr: int, out_ptr: int, stream: int = 0):
+        """Element-wise u64 sums of partial responses [s][2][L][N] (device)
+        modulo each q_j: the all-reduce form of the sharded exchange."""
+        self._check(lib().cwpir_reduce_responses_device(self._h, s, sums_ptr, out_ptr, stream))
 
     def answer_batch(self, db: int, queries, c: int = 0) -> np.ndarray:
         q = _u64(queries)

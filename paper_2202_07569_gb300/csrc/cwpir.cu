@@ -1349,6 +1349,18 @@ int cwpir_sum_responses_device(cwpir_ctx *c, uint32_t count, uint32_t s,
   return 0;
 }
 
+int cwpir_reduce_responses_device(cwpir_ctx *c, uint32_t s, const uint64_t *d_sums,
+                                  uint64_t *d_out, void *stream) {
+  if (!c) return CWPIR_EINVAL;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  if (!d_sums || !d_out) return fail(c, CWPIR_EINVAL, "null buffer");
+  if (s == 0 || s > CWPIR_MAX_PLAINTEXTS)
+    return fail(c, CWPIR_EINVAL, "need 1 <= s <= %d", CWPIR_MAX_PLAINTEXTS);
+  CUDA_TRY(c, cw::launch_ct_reduce(c->d_tab, c->h, d_sums, s, d_out, (cudaStream_t)stream));
+  return CWPIR_OK;
+}
+
 int cwpir_autotune_grid(cwpir_ctx *c, int32_t db_id, uint32_t cfac, uint32_t nq,
                         const uint64_t *d_queries, uint64_t *d_responses, const int64_t *jobs,
                         uint32_t n_jobs, const int64_t *waves, uint32_t n_waves,

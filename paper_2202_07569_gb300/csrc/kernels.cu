@@ -970,6 +970,15 @@ __global__ void k_ct_sum(const DevTables *T, const u64 *in, u32 count, u64 in_st
   out[off] = a;
 }
 
+// Element-wise sums v < 2^64 of residues (one all-reduce of partial
+// responses) -> v mod q_j (Barrett on v below 2^112).  grid (N/256, 2L, s).
+__global__ void k_ct_reduce(const DevTables *T, const u64 *in, u64 *out) {
+  const u32 N = T->N, L = T->L, i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
+  const NttPrime P = T->prime[pl % L];
+  const u64 off = ((u64)blockIdx.z * 2 * L + pl) * N + i;
+  out[off] = barrett_reduce(0, in[off], P.q, P.mu);
+}
+
 __global__ void k_minus_consts(const DevTables *T, const u64 *in, u64 *out) {
   const u32 N = T->N, L = T->L, i = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
   const u32 f = blockIdx.z, j = pl % L;
@@ -1462,6 +1471,13 @@ cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const
 cudaError_t launch_ct_sum(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
                           u64 in_stride, u64 *out, cudaStream_t st) {
   k_ct_sum<<<dim3(h.N / 256, 2 * h.L), 256, 0, st>>>(T, in, count, in_stride, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_reduce(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
+                            u64 *out, cudaStream_t st) {
+  if (!count) return cudaSuccess;
+  k_ct_reduce<<<dim3(h.N / 256, 2 * h.L, count), 256, 0, st>>>(T, in, out);
   return cudaGetLastError();
 }
 

@@ -179,6 +179,10 @@ cudaError_t launch_folklore_leaves(const DevTables *T, const DevTables &h, const
 // x^0), f < count; out = s * in.
 cudaError_t launch_ct_sum(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
                           u64 in_stride, u64 *out, cudaStream_t st);
+// out[x] = in[x] mod q_j for `count` ciphertexts [2][L][N] of u64 values
+// (sums of residues below 2^64).
+cudaError_t launch_ct_reduce(const DevTables *T, const DevTables &h, const u64 *in, u32 count,
+                             u64 *out, cudaStream_t st);
 cudaError_t launch_minus_consts(const DevTables *T, const DevTables &h, const u64 *in,
                                 u32 count, u64 *out, cudaStream_t st);
 cudaError_t launch_ct_scalar(const DevTables *T, const DevTables &h, const u64 *in, u64 s,

@@ -5,8 +5,12 @@ Constant-weight PIR answers with r = sum over rows i of sel_i * DB_i mod Q
 independent and the sum is exact ring arithmetic, so each rank (one GPU)
 holds a contiguous block of the rows with their own codewords, answers the
 query over them, and the one exchange step is the modular sum of the
-partial responses: an all-gather of one response per rank, then
-``cwpir_sum_responses_device`` on the gathered block.  The result is bit
+partial responses.  Two forms of it: an all-gather of one response per
+rank, then ``cwpir_sum_responses_device`` on the gathered block; or one
+all-reduce (SUM) of the u64 residues, exact while at most 1023 ranks add
+values below 2^54 (the sum stays below 2^64; the int64 sum of the
+collective wraps like the unsigned one), then
+``cwpir_reduce_responses_device`` modulo each q_j.  Either result is bit
 identical to answering over all rows on one GPU.
 
 torch.distributed carries the partials (NCCL for device tensors, gloo for
@@ -59,6 +63,23 @@ def gather_partials(partial, group=None):
     return torch.stack(parts)
 
 
+MAX_ALLREDUCE_RANKS = 1023
+
+
+def allreduce_partials(partial, group=None):
+    """Sums one partial response per rank in place (SUM over int64 views of
+    the u64 residues) and returns it: element-wise sums below 2^64 for at
+    most MAX_ALLREDUCE_RANKS ranks, to be reduced modulo each q_j."""
+    import torch.distributed as dist
+
+    rank, world = _group_info(group)
+    if world > MAX_ALLREDUCE_RANKS:
+        raise ValueError(f"{world} ranks: the u64 sum of the residues could wrap")
+    if world > 1:
+        dist.all_reduce(partial, op=dist.ReduceOp.SUM, group=group)
+    return partial
+
+
 class ShardedDatabase:
     """This rank's block of a database and the sharded answer.
 
@@ -80,23 +101,33 @@ class ShardedDatabase:
         plen = int(np.shape(items)[1]) if np.ndim(items) == 2 else 0
         self.resp_shape = partial_shape(plen, ctx.N, ctx.L)
 
-    def answer_device(self, d_query, d_resp, c: int = 0, stream=None):
+    def answer_device(self, d_query, d_resp, c: int = 0, stream=None,
+                      exchange: str = "allgather"):
         """Answer the query (device tensor [h][2][L][N], int64 view of the
         residues) over the whole database into d_resp ([s][2][L][N] or
         [2][L][N], device, int64 view).  Every rank of the group must call
-        this with the same query; the result is on every rank."""
+        this with the same query; the result is on every rank.  exchange:
+        "allgather" (gather the partials, sum them modulo q_j) or
+        "allreduce" (one SUM collective, then the reduction modulo q_j)."""
         import torch
 
         st = stream if stream is not None else torch.cuda.current_stream()
+        s = self.resp_shape[0] if len(self.resp_shape) == 4 else 1
         with torch.cuda.stream(st):
             partial = torch.zeros(self.resp_shape, dtype=torch.int64, device=d_resp.device)
             if self.db is not None:
                 self.ctx.answer_device(self.db, d_query.data_ptr(), partial.data_ptr(), c,
                                        st.cuda_stream)
-            gathered = gather_partials(partial, self.group)
-            s = self.resp_shape[0] if len(self.resp_shape) == 4 else 1
-            self.ctx.sum_responses_device(self.world, s, gathered.data_ptr(), d_resp.data_ptr(),
-                                          st.cuda_stream)
+            if exchange == "allreduce":
+                summed = allreduce_partials(partial, self.group)
+                self.ctx.reduce_responses_device(s, summed.data_ptr(), d_resp.data_ptr(),
+                                                 st.cuda_stream)
+            elif exchange == "allgather":
+                gathered = gather_partials(partial, self.group)
+                self.ctx.sum_responses_device(self.world, s, gathered.data_ptr(),
+                                              d_resp.data_ptr(), st.cuda_stream)
+            else:
+                raise ValueError(f"unknown exchange {exchange!r}")
         return d_resp
 
     def close(self):

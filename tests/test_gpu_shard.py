@@ -55,6 +55,16 @@ def test_shard_partials_sum_to_full_answer(N, L, n, k, m, plen, world):
         torch.cuda.synchronize()
         got = out.cpu().numpy().view(np.uint64)
         assert np.array_equal(got, want)
+    # the all-reduce form: the element-wise u64 sum of the partials (what one
+    # SUM collective over the ranks leaves), reduced modulo each q_j
+    sums = parts.sum(dim=0)  # int64 wraps like the u64 sum; here no wrap occurs
+    red = torch.empty(shape, dtype=torch.int64, device=dev)
+    ctx.reduce_responses_device(s, sums.data_ptr(), red.data_ptr(), st.cuda_stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(red.cpu().numpy().view(np.uint64), want)
+    ctx.reduce_responses_device(s, sums.data_ptr(), sums.data_ptr(), st.cuda_stream)  # in place
+    torch.cuda.synchronize()
+    assert np.array_equal(sums.cpu().numpy().view(np.uint64), want)
     # no partial alone is the answer
     for r in range(world):
         assert not np.array_equal(parts[r].cpu().numpy().view(np.uint64), want)
@@ -87,5 +97,9 @@ def test_sharded_database_without_process_group_is_the_plain_answer():
     got = out.cpu().numpy().view(np.uint64)
     assert np.array_equal(got, ctx.answer(sh.db, query))
     assert np.array_equal(got, cl.O.answer(items, cw, 11, query, cl.rlk))
+    out.zero_()
+    sh.answer_device(d_query, out, exchange="allreduce")
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), got)
     sh.close()
     ctx.close()

@@ -98,3 +98,56 @@ def test_two_gloo_ranks_sum_of_partials_is_the_answer(tmp_path, orc):
     assert not np.array_equal(blocks[0][0], want) and not np.array_equal(blocks[0][1], want)
     mu, budget = cl.decrypt(total)
     assert np.array_equal(mu, items[TARGET]) and budget > 0
+
+
+WORLD3, ROWS3 = 3, 2  # three ranks over two rows: rank 2 holds none
+
+
+def _rank_main_allreduce(rank: int, port: int, out_dir: str):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_07569_gb300.shard import allreduce_partials
+    from tests.workloads import T, Client, database
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD3)
+    try:
+        cl = Client(N, L, seed=9)
+        items, cw, _ = database(ROWS3, N, T, K, M, seed=10)
+        query = cl.query(cw[1], M, 0)
+        lo, hi = shard_rows(ROWS3, WORLD3, rank)
+        if hi > lo:
+            partial = cl.O.answer(items[lo:hi], cw[lo:hi], M, query, cl.rlk)
+        else:  # a rank without rows contributes zeros of the same shape
+            partial = np.zeros((2, L, N), np.uint64)
+        t = torch.from_numpy(partial.view(np.int64).copy())
+        allreduce_partials(t)
+        np.save(os.path.join(out_dir, f"summed{rank}.npy"), t.numpy().view(np.uint64))
+        np.save(os.path.join(out_dir, f"span{rank}.npy"), np.array([lo, hi]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_three_gloo_ranks_allreduce_with_an_empty_shard(tmp_path, orc):
+    """The all-reduce form of the exchange over three ranks, one of them
+    without rows: every rank holds the same element-wise sum, whose residues
+    modulo each q_j are the oracle's answer over all rows."""
+    import torch.multiprocessing as mp
+
+    from tests.workloads import T, Client, database
+
+    mp.start_processes(_rank_main_allreduce, args=(_free_port(), str(tmp_path)), nprocs=WORLD3,
+                       join=True, start_method="spawn")
+    spans = [tuple(np.load(tmp_path / f"span{r}.npy")) for r in range(WORLD3)]
+    assert spans[2][0] == spans[2][1]  # the empty shard
+    sums = [np.load(tmp_path / f"summed{r}.npy") for r in range(WORLD3)]
+    assert all(np.array_equal(sums[0], x) for x in sums[1:])
+    cl = Client(N, L, seed=9)
+    items, cw, _ = database(ROWS3, N, T, K, M, seed=10)
+    query = cl.query(cw[1], M, 0)
+    want = cl.O.answer(items, cw, M, query, cl.rlk)
+    q = cl.q.reshape(1, L, 1)
+    assert np.array_equal(sums[0] % q, want)
+    mu, budget = cl.decrypt(sums[0] % q)
+    assert np.array_equal(mu, items[1]) and budget > 0
