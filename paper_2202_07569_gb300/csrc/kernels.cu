@@ -111,6 +111,34 @@ __device__ __forceinline__ void ntt_inv(NttRegs<LOGN> &x, u64 *s, const NttPrime
   }
 }
 
+// The tensor's inverse transform (without N^-1) through inv_pass_aq:
+// x[r] = NTT value R t + r (< 4q) -> N times the coefficient, in [0, 2q).
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_aq(NttRegs<LOGN> &x, u64 *s, const NttPrime &P) {
+  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
+  constexpr int NP = Passes<LOGN, RB>::count;
+  const u32 t = threadIdx.x;
+  u32 wprev = 0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    u32 lo, c, w;
+    Passes<LOGN, RB>::inv(p, lo, c, w);
+    if (p > 0) {
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[r];
+      __syncthreads();
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
+      __syncthreads();
+    }
+    inv_pass_aq<LOGN, RB>(x, t, lo, c, w, P.ipsi2, P.q);
+    wprev = w;
+  }
+  const u64 q2 = 2 * P.q;
+#pragma unroll
+  for (u32 r = 0; r < R; ++r) x[r] = x[r] >= q2 ? x[r] - q2 : x[r];
+}
+
 // The same transforms on 32-bit words for a 30-bit extension prime: the
 // forward one from [0, 4p) to canonical values, the inverse one from
 // [0, 2p) to N times the coefficient in [0, 2p) (no N^-1: the scale-down
@@ -344,36 +372,56 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 // share one prime's twiddles in L1.
 // ---------------------------------------------------------------------
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
     k_tensor_ext(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
   extern __shared__ u32 s32[];
-  constexpr u32 N = 1u << LOGN;
-  const u32 L = T->L, k = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
+  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R, RB = NttShape32<LOGN>::RB;
+  constexpr int NP = Passes<LOGN, RB>::count;
+  constexpr u32 SW = (1u << LOGN) + ((1u << LOGN) >> RB);  // one transform's shared words
+  const u32 L = T->L, k = blockIdx.y, t = threadIdx.x;
   const u64 job = blockIdx.x;
   const MulJob J = jobs[job];
   const u64 ps = qp_poly_words(L, T->K, N);
-  constexpr u32 R = NttShape32<LOGN>::R;
   const ExtNtt E = T->ext[k];
   const u32 p2 = 2 * E.e.p;
   const u32 *a0 = ext_limb(J.a, L, N, k), *a1 = ext_limb(J.a + ps, L, N, k);
   const u32 *b0 = ext_limb(J.b, L, N, k), *b1 = ext_limb(J.b + ps, L, N, k);
-  NttRegs32<LOGN> y;
+  u32 y[3 * R];  // the three outputs' registers
 #pragma unroll
   for (u32 r = 0; r < R; ++r) {  // products in [0, 2p)
     const u32 c = ntt_pos32<LOGN>(t, r);
-    u32 v;
-    if (which == 0) v = mulmod_ext_lazy(a0[c], b0[c], E.e);
-    else if (which == 2) v = mulmod_ext_lazy(a1[c], b1[c], E.e);
-    else {
-      v = mulmod_ext_lazy(a0[c], b1[c], E.e) + mulmod_ext_lazy(a1[c], b0[c], E.e);
-      v = csub32(v, p2);
-    }
-    y[r] = v;
+    const u32 x0 = a0[c], x1 = a1[c], z0 = b0[c], z1 = b1[c];
+    y[r] = mulmod_ext_lazy(x0, z0, E.e);
+    y[R + r] = csub32(mulmod_ext_lazy(x0, z1, E.e) + mulmod_ext_lazy(x1, z0, E.e), p2);
+    y[2 * R + r] = mulmod_ext_lazy(x1, z1, E.e);
   }
-  ntt_inv32<LOGN>(y, s32, E);  // N d in [0, 2p)
-  u32 *out = ext_limb(Tbuf + (job * 3 + which) * ps, L, N, k);
+  // the three inverse transforms in lock-step: N d in [0, 2p)
+  u32 wprev = 0;
 #pragma unroll
-  for (u32 r = 0; r < R; ++r) out[strided_idx32<LOGN>(t, r)] = y[r];
+  for (int pp = 0; pp < NP; ++pp) {
+    u32 lo, c, w;
+    Passes<LOGN, RB>::inv(pp, lo, c, w);
+    if (pp > 0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (u32 r = 0; r < R; ++r) s32[i * SW + sidx<RB>(pass_idx<RB>(t, r, wprev))] = y[i * R + r];
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (u32 r = 0; r < R; ++r) y[i * R + r] = s32[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))];
+      __syncthreads();
+    }
+    inv_pass32m<LOGN, RB, 3>(y, t, lo, c, w, E.ipsi2, E.e.p);
+    wprev = w;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    u32 *out = ext_limb(Tbuf + (job * 3 + i) * ps, L, N, k);
+#pragma unroll
+    for (u32 r = 0; r < R; ++r) out[strided_idx32<LOGN>(t, r)] = y[i * R + r];
+  }
 }
 
 template <int LOGN>
@@ -401,7 +449,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_b
     else v = addq(barrett(a0[c], b1[c], P.q, P.mu), barrett(a1[c], b0[c], P.q, P.mu), P.q);
     x[r] = v;
   }
-  ntt_inv<LOGN, false>(x, s, P);  // N d in [0, 2q): the scale-down absorbs N^-1
+  ntt_inv_aq<LOGN>(x, s, P);  // N d in [0, 2q): the scale-down absorbs N^-1
 #pragma unroll
   for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
 }
@@ -671,55 +719,64 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::m
 }
 
 // Row sums: block z = s*G + g sums D[job][l][k] * dbr[row][k] over the jobs
-// g, g+G, ... of segment seg0 + s, for every limb l < NL, modulo r_k, into
-// S[s*G + g][NL][4][N].  Products of residues below 2^30 are below 2^60,
-// so fifteen of them and a folded residue fit 64 bits.  grid (N/256, 4,
-// nseg * G).
-template <int NL>
-__global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 seg0, u32 seg_len, u32 G,
-                           const MulJob *jobs, const u32 *dbr, u32 *S) {
-  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+// g, g+G, ... of segment seg0 + s, modulo r_k, into S[s*G + g][nl][nr][N];
+// a thread takes one coefficient of one prime and NLT of the nl limbs
+// (blockIdx.y = k * (nl / NLT) + part, limbs part * NLT ...).  RPI rows per
+// iteration: all their loads are in flight before the products (the loop
+// waits on memory: twelve rows and four limbs a thread took the metric's
+// row sums from 27 to 15 ms a query against two rows and all twelve limbs).
+// Products of residues below 2^30 are below 2^60, so fifteen terms fit 64
+// bits.  grid (N/256, nr * nl / NLT, nseg * G).
+constexpr int kMacRows = 12;  // rows per iteration
+constexpr int kMacLimbs = 4;  // most limbs per thread
+
+template <int NLT, int RPI>
+__global__ void k_rows_mac(const DevTables *T, const u32 *D, u32 nl, u32 seg0, u32 seg_len,
+                           u32 G, const MulJob *jobs, const u32 *dbr, u32 *S) {
+  const u32 N = T->N, c = blockIdx.x * blockDim.x + threadIdx.x, parts = nl / NLT;
+  const u32 k = blockIdx.y / parts, l0 = (blockIdx.y % parts) * NLT;
   const u32 sg = blockIdx.z, seg = seg0 + sg / G, g = sg % G;
   const ExtPrime E = T->ext[k].e;
   const u64 kN = (u64)T->rows.nr * N;
-  u64 acc[NL];
+  u64 acc[NLT];
 #pragma unroll
-  for (int l = 0; l < NL; ++l) acc[l] = 0;
+  for (int l = 0; l < NLT; ++l) acc[l] = 0;
+  static_assert(RPI >= 1 && RPI <= 14, "RPI products and a folded residue must fit 64 bits");
   u32 terms = 0;
-  const u64 kc = (u64)k * N + c, jstride = (u64)NL * kN;
+  const u64 kc = (u64)k * N + c + l0 * kN, jstride = (u64)nl * kN;
   u64 job = (u64)seg * seg_len + g;
   u32 x = g;
-  u64 row0 = x < seg_len ? jobs[job].row : 0;
-  // two rows per iteration: both rows' loads issue before the products
-  for (; x + G < seg_len; x += 2 * G, job += 2 * G) {
-    const u64 row1 = jobs[job + G].row;
-    const u32 m0 = dbr[row0 * kN + kc], m1 = dbr[row1 * kN + kc];
-    if (x + 2 * G < seg_len) row0 = jobs[job + 2 * G].row;
-    const u32 *d0 = D + job * jstride + kc, *d1 = d0 + G * jstride;
-    u32 a[NL], b[NL];
+  for (; x + (RPI - 1) * G < seg_len; x += RPI * G, job += RPI * G) {
+    u32 m[RPI], a[RPI][NLT];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      a[l] = d0[l * kN];
-      b[l] = d1[l * kN];
+    for (int i = 0; i < RPI; ++i) m[i] = dbr[jobs[job + i * G].row * kN + (u64)k * N + c];
+#pragma unroll
+    for (int i = 0; i < RPI; ++i)
+#pragma unroll
+      for (int l = 0; l < NLT; ++l) a[i][l] = D[(job + i * G) * jstride + kc + l * kN];
+#pragma unroll
+    for (int l = 0; l < NLT; ++l) {
+      u64 s = 0;
+#pragma unroll
+      for (int i = 0; i < RPI; ++i) s += wmul(a[i][l], m[i]);
+      acc[l] += s;
     }
+    terms += RPI;
+    if (terms + RPI > 15) {  // at most 15 terms below 2^60 each: below 2^64
 #pragma unroll
-    for (int l = 0; l < NL; ++l) acc[l] += wmul(a[l], m0) + wmul(b[l], m1);
-    terms += 2;
-    if (terms >= 14) {  // at most 14 products and a folded residue: below 2^64
-#pragma unroll
-      for (int l = 0; l < NL; ++l) acc[l] = reduce_ext(acc[l], E);
+      for (int l = 0; l < NLT; ++l) acc[l] = reduce_ext(acc[l], E);
       terms = 1;  // the folded residue counts as one term
     }
   }
-  if (x < seg_len) {  // the last row of an odd count
-    const u32 m0 = dbr[row0 * kN + kc];
+  for (; x < seg_len; x += G, job += G) {  // the last rows (fewer than RPI)
+    const u32 m0 = dbr[jobs[job].row * kN + (u64)k * N + c];
     const u32 *d0 = D + job * jstride + kc;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) acc[l] += wmul(d0[l * kN], m0);
+    for (int l = 0; l < NLT; ++l) acc[l] += wmul(d0[l * kN], m0);
   }
-  u32 *o = S + (u64)sg * NL * kN + (u64)k * N + c;
+  u32 *o = S + (u64)sg * nl * kN + kc;
 #pragma unroll
-  for (int l = 0; l < NL; ++l) o[l * kN] = reduce_ext(acc[l], E);
+  for (int l = 0; l < NLT; ++l) o[l * kN] = reduce_ext(acc[l], E);
 }
 
 // Inverse transform (without N^-1) of S[u][l][k] (k < np) in place:
@@ -1191,9 +1248,9 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
     if (e != cudaSuccess) return e;
     k_tensor_intt<LG><<<dim3(njobs, 3, h.L), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
         T, jobs, Tbuf);
-    e = allow_smem(k_tensor_ext<LG>, smem32_bytes<LG>());
+    e = allow_smem(k_tensor_ext<LG>, 3 * smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
-    k_tensor_ext<LG><<<dim3(njobs, 3, h.K), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
+    k_tensor_ext<LG><<<dim3(njobs, h.K), ntt_block32<LG>(), 3 * smem32_bytes<LG>(), st>>>(
         T, jobs, Tbuf);
   });
   return cudaGetLastError();
@@ -1302,24 +1359,24 @@ u32 relin_rows_groups(const DevTables &h, u32 segs, u32 seg_len, u32 gcap) {
 }
 
 
-#define CW_DISPATCH_NL(NL_, GRID, BLOCK, STREAM, ...)                                  \
-  switch (NL_) {                                                                       \
-    case 2: k_rows_mac<2><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 3: k_rows_mac<3><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 4: k_rows_mac<4><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 6: k_rows_mac<6><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 8: k_rows_mac<8><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 9: k_rows_mac<9><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 10: k_rows_mac<10><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 12: k_rows_mac<12><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 14: k_rows_mac<14><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 15: k_rows_mac<15><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 16: k_rows_mac<16><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 18: k_rows_mac<18><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 21: k_rows_mac<21><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    case 24: k_rows_mac<24><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;           \
-    default: return cudaErrorInvalidValue;                                            \
+// Row sums for nl limbs: NLT = the largest divisor of nl that is at most
+// kMacLimbs, nr * nl / NLT blocks in y.
+static cudaError_t rows_mac(const DevTables &h, const DevTables *T, const u32 *D, u32 nl,
+                            u32 seg0, u32 seg_len, u32 G, const MulJob *jobs, const u32 *dbr,
+                            u32 *S, u32 units, cudaStream_t st) {
+  u32 nlt = kMacLimbs < (int)nl ? kMacLimbs : nl;
+  while (nl % nlt) --nlt;
+  const dim3 grid(h.N / 256, h.rows.nr * (nl / nlt), units);
+  switch (nlt) {
+#define CW_MAC_CASE(V) \
+    case V: k_rows_mac<V, kMacRows><<<grid, 256, 0, st>>>(T, D, nl, seg0, seg_len, G, jobs, dbr, S); break;
+    CW_MAC_CASE(1) CW_MAC_CASE(2) CW_MAC_CASE(3) CW_MAC_CASE(4) CW_MAC_CASE(5) CW_MAC_CASE(6)
+    CW_MAC_CASE(7) CW_MAC_CASE(8) CW_MAC_CASE(9) CW_MAC_CASE(10) CW_MAC_CASE(11) CW_MAC_CASE(12)
+#undef CW_MAC_CASE
+    default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u32 *items,
                                 u64 rows, u32 plen, u32 *dbr, cudaStream_t st) {
@@ -1415,9 +1472,8 @@ cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 
   const u32 spp = G >= gcap ? 1 : gcap / G;  // segments per pass
   for (u32 s0 = 0; s0 < segs; s0 += spp) {
     const u32 nseg = segs - s0 < spp ? segs - s0 : spp, units = nseg * G;
-    CW_DISPATCH_NL(nl, dim3(N / 256, h.rows.nr, units), 256, st, T, D, s0, seg_len, G, jobs,
-                   dbr, S);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rows_mac(h, T, D, nl, s0, seg_len, G, jobs, dbr, S, units, st)) != cudaSuccess)
+      return e;
     if ((e = rows_intt(T, h, S, nl, units, st)) != cudaSuccess) return e;
     CW_DISPATCH_L(L, k_rows_crt, dim3(N / 256, nl, units), 256, 0, st, T, S, nl, DNQ + L * LN,
                   unit, DNQ, unit, err, h.rows);
@@ -1439,8 +1495,7 @@ cudaError_t launch_plain_mul_rows(const DevTables *T, const DevTables &h, const 
   const u32 L = h.L, nl = 2 * L, N = h.N;
   cudaError_t e = rows_ntt(T, h, ct, nl, 1, D, st);
   if (e != cudaSuccess) return e;
-  CW_DISPATCH_NL(nl, dim3(N / 256, h.rows.nr, 1), 256, st, T, D, 0u, 1u, 1u, job, dbr, S);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = rows_mac(h, T, D, nl, 0, 1, 1, job, dbr, S, 1, st)) != cudaSuccess) return e;
   if ((e = rows_intt(T, h, S, nl, 1, st)) != cudaSuccess) return e;
   CW_DISPATCH_L(L, k_rows_crt, dim3(N / 256, nl, 1), 256, 0, st, T, S, nl, out,
                 (u64)2 * L * N, (u64 *)nullptr, (u64)0, err, h.rows);

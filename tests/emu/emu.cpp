@@ -340,6 +340,54 @@ void pass_ntt32(u32 *a, const u32 *tw, u32 p, bool inverse) {
   for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
 }
 
+// The tensor's inverse schedule with the approximate Shoup quotient
+// (inv_pass_aq, values below 4q), ending with one subtraction of 2q.
+template <int LOGN, int RB>
+void pass_ntt_aq(u64 *a, const u64 *tw, u64 q) {
+  constexpr u32 R = 1u << RB;
+  const u32 N = 1u << LOGN, T = N / R;
+  std::vector<u64> s(smem_words<RB>(N));
+  for (u32 i = 0; i < N; ++i) s[sidx<RB>(i)] = a[i];
+  for (int p = 0; p < Passes<LOGN, RB>::count; ++p) {
+    u32 lo, c, w;
+    Passes<LOGN, RB>::inv(p, lo, c, w);
+    for (u32 t = 0; t < T; ++t) {
+      u64 x[R];
+      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
+      inv_pass_aq<LOGN, RB>(x, t, lo, c, w, tw + 2 * N, q);
+      if (p == Passes<LOGN, RB>::count - 1)
+        for (u32 r = 0; r < R; ++r) x[r] = x[r] >= 2 * q ? x[r] - 2 * q : x[r];
+      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, w))] = x[r];
+    }
+  }
+  for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
+}
+
+// Three 32-bit inverse transforms of one prime in lock-step (inv_pass32m).
+template <int LOGN, int RB>
+void pass_ntt32_x3(u32 *a, const u32 *tw, u32 p) {
+  constexpr u32 R = 1u << RB;
+  const u32 N = 1u << LOGN, T = N / R;
+  std::vector<u32> s(3 * smem_words<RB>(N));
+  const u32 SW = smem_words<RB>(N);
+  for (int i = 0; i < 3; ++i)
+    for (u32 j = 0; j < N; ++j) s[i * SW + sidx<RB>(j)] = a[i * N + j];
+  for (int pp = 0; pp < Passes<LOGN, RB>::count; ++pp) {
+    u32 lo, c, w;
+    Passes<LOGN, RB>::inv(pp, lo, c, w);
+    for (u32 t = 0; t < T; ++t) {
+      u32 x[3 * R];
+      for (int i = 0; i < 3; ++i)
+        for (u32 r = 0; r < R; ++r) x[i * R + r] = s[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))];
+      inv_pass32m<LOGN, RB, 3>(x, t, lo, c, w, tw + 2 * N, p);
+      for (int i = 0; i < 3; ++i)
+        for (u32 r = 0; r < R; ++r) s[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))] = x[i * R + r];
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (u32 j = 0; j < N; ++j) a[i * N + j] = s[i * SW + sidx<RB>(j)];
+}
+
 template <int RB>
 void pass_ntt32_n(u32 logN, u32 *a, const u32 *tw, u32 p, bool inverse) {
   switch (logN) {
@@ -407,6 +455,45 @@ uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
     E.inv(a.data(), l);
     run(E.logN, b.data(), E.tw[l].data(), pr, true, E.ninv[l], E.ninv_s[l]);
     for (u32 i = 0; i < N; ++i) bad += a[i] != b[i] || b[i] != data[i] % pr;
+  }
+  return bad;
+}
+}
+
+extern "C" {
+// The tensor kernels' inverse transforms against the stage-by-stage one
+// (N = 8192, 16 coefficients a thread): the approximate-quotient schedule on
+// every ciphertext prime from lazy inputs below 4q must leave N times the
+// coefficients in [0, 2q); the three-transform 32-bit schedule on every
+// extension prime must leave each of three inputs (below 2p) as the single
+// schedule does.  Returns the number of mismatches.
+uint64_t emu_tensor_intt_compare(uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *data) {
+  const u32 N = 8192;
+  Emu E(N, L, q, t);
+  uint64_t bad = 0;
+  for (u32 l = 0; l < L; ++l) {
+    const u64 pr = E.all[l];
+    std::vector<u64> a(N), b(N);
+    for (u32 i = 0; i < N; ++i) {
+      a[i] = data[i] % pr;
+      b[i] = a[i] + (data[i] >> 62) * pr;  // lazy input below 4q
+    }
+    E.inv(a.data(), l);
+    pass_ntt_aq<13, 4>(b.data(), E.tw[l].data(), pr);
+    for (u32 i = 0; i < N; ++i)
+      bad += b[i] >= 2 * pr || b[i] % pr != hmul(a[i], N % pr, pr);
+  }
+  for (u32 k = 0; k < E.K; ++k) {
+    const u64 pr = E.p[k];
+    std::vector<u32> x3(3 * N), x1(N);
+    for (u32 i = 0; i < 3 * N; ++i) x3[i] = (u32)(data[(7 * i + 3) % N] % (2 * pr));  // below 2p
+    for (int j = 0; j < 3; ++j) {
+      for (u32 i = 0; i < N; ++i) x1[i] = x3[j * N + i];
+      pass_ntt32<13, 4>(x1.data(), E.tw32[k].data(), (u32)pr, true);
+      std::vector<u32> y(x3);
+      pass_ntt32_x3<13, 4>(y.data(), E.tw32[k].data(), (u32)pr);
+      for (u32 i = 0; i < N; ++i) bad += y[j * N + i] != x1[i];
+    }
   }
   return bad;
 }
