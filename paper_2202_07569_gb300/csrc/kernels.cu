@@ -697,54 +697,25 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::m
   for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = x[r];
 }
 
-// Limbs M l' .. M l' + M - 1 of unit u of E (unit stride ustride u64
-// words, limbs of N residues below 2^54) reduced modulo the extension prime
-// k < np and transformed, the M transforms in lock-step (one twiddle load
-// serves M butterflies): D[u][l][k][N] u32.  grid (np, nl / M, units).
-template <int LOGN, int M>
-__global__ void __launch_bounds__(NttShape32<LOGN>::threads,
-                                  M == 1 ? NttShape32<LOGN>::min_blocks : LOGN <= 13 ? 2 : 1)
+// Limb l of unit u of E (unit stride ustride u64 words, limbs of N
+// residues below 2^54) reduced modulo the extension prime k < np and
+// transformed: D[u][l][k][N] u32.  grid (np, nl, units).
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape32<LOGN>::threads, NttShape32<LOGN>::min_blocks)
     k_rows_ntt(const DevTables *T, const u64 *Ein, u64 ustride, u32 nl, u32 np, u32 *D) {
   extern __shared__ u32 s32[];
-  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R, RB = NttShape32<LOGN>::RB;
-  constexpr int NP = Passes<LOGN, RB>::count;
-  constexpr u32 SW = (1u << LOGN) + ((1u << LOGN) >> RB);  // one transform's shared words
-  const u32 k = blockIdx.x, l0 = blockIdx.y * M, t = threadIdx.x;
+  constexpr u32 N = 1u << LOGN, R = NttShape32<LOGN>::R;
+  const u32 k = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
   const u64 u = blockIdx.z;
   const ExtNtt E = T->ext[k];
-  const u64 *in = Ein + u * ustride + (u64)l0 * N;
-  u32 x[M * R];
+  const u64 *in = Ein + u * ustride + (u64)l * N;
+  NttRegs32<LOGN> x;
 #pragma unroll
-  for (int i = 0; i < M; ++i)
+  for (u32 r = 0; r < R; ++r) x[r] = reduce_ext62_lazy(in[strided_idx32<LOGN>(t, r)], E.e);
+  ntt_fwd32<LOGN>(x, s32, E);
+  u32 *out = D + ((u * nl + l) * np + k) * N;
 #pragma unroll
-    for (u32 r = 0; r < R; ++r)  // below 3p: the forward transform takes inputs below 4p
-      x[i * R + r] = reduce_ext62_lazy(in[(u64)i * N + strided_idx32<LOGN>(t, r)], E.e);
-  u32 wprev = 0;
-#pragma unroll
-  for (int pp = 0; pp < NP; ++pp) {
-    u32 lo, c, w;
-    Passes<LOGN, RB>::fwd(pp, lo, c, w);
-    if (pp > 0) {
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-#pragma unroll
-        for (u32 r = 0; r < R; ++r) s32[i * SW + sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[i * R + r];
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-#pragma unroll
-        for (u32 r = 0; r < R; ++r) x[i * R + r] = s32[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))];
-      __syncthreads();
-    }
-    fwd_pass32m<LOGN, RB, M>(x, t, lo, c, w, E.psi2, E.e.p);
-    wprev = w;
-  }
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    u32 *out = D + ((u * nl + l0 + i) * np + k) * N;
-#pragma unroll
-    for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = reduce4_32(x[i * R + r], E.e.p);
-  }
+  for (u32 r = 0; r < R; ++r) out[ntt_pos32<LOGN>(t, r)] = x[r];
 }
 
 // Row sums: block z = s*G + g sums D[job][l][k] * dbr[row][k] over the jobs
@@ -1423,22 +1394,13 @@ cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u3
 }
 
 // units of nl limbs (unit stride ustride) -> D[u][l][k < np] (k_rows_ntt)
-// (three limbs a block when nl allows: one twiddle load serves three
-// butterflies)
 static cudaError_t rns_ntt(const DevTables *T, const DevTables &h, const u64 *E, u64 ustride,
                            u32 nl, u32 np, u32 units, u32 *D, cudaStream_t st) {
   CW_DISPATCH_LOGN(h.logN, {
-    if (nl % 3 == 0) {
-      cudaError_t e = allow_smem(k_rows_ntt<LG, 3>, 3 * smem32_bytes<LG>());
-      if (e != cudaSuccess) return e;
-      k_rows_ntt<LG, 3><<<dim3(np, nl / 3, units), ntt_block32<LG>(), 3 * smem32_bytes<LG>(),
-                          st>>>(T, E, ustride, nl, np, D);
-    } else {
-      cudaError_t e = allow_smem(k_rows_ntt<LG, 1>, smem32_bytes<LG>());
-      if (e != cudaSuccess) return e;
-      k_rows_ntt<LG, 1><<<dim3(np, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
-          T, E, ustride, nl, np, D);
-    }
+    cudaError_t e = allow_smem(k_rows_ntt<LG>, smem32_bytes<LG>());
+    if (e != cudaSuccess) return e;
+    k_rows_ntt<LG><<<dim3(np, nl, units), ntt_block32<LG>(), smem32_bytes<LG>(), st>>>(
+        T, E, ustride, nl, np, D);
   });
   return cudaGetLastError();
 }

@@ -189,11 +189,8 @@ CW_HD void ld_pair32x2(const u32 *p, u32 &a0, u32 &b0, u32 &a1, u32 &b1) {
 // a*w mod p in [0, 2p) for any a < 2^32
 CW_HD u32 shoup32_lazy(u32 a, u32 w, u32 ws, u32 p) { return a * w - mulhi32(a, ws) * p; }
 
-// Forward butterflies on M transforms of the same prime at once (one
-// twiddle load serves the M butterflies): x[i * R + r] is register r of
-// transform i.
-template <int LOGN, int RB, int M>
-CW_HD void fwd_pass32m(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *psi2, u32 p) {
+template <int LOGN, int RB>
+CW_HD void fwd_pass32(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *psi2, u32 p) {
   const u32 p2 = 2 * p;
   constexpr u32 R = 1u << RB;
 #pragma unroll
@@ -215,23 +212,15 @@ CW_HD void fwd_pass32m(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *psi2, u32
         const u32 r0 = (hv + h) << (rb + 1);
 #pragma unroll
         for (u32 lv = 0; lv < (1u << rb); ++lv) {
-#pragma unroll
-          for (int i = 0; i < M; ++i) {
-            const u32 r = i * R + (r0 | lv);
-            const u32 U = csub32(x[r], p2);
-            const u32 V = shoup32_lazy(x[r + (1u << rb)], W[h], Ws[h], p);
-            x[r] = U + V;
-            x[r + (1u << rb)] = U - V + p2;
-          }
+          const u32 r = r0 | lv;
+          const u32 U = csub32(x[r], p2);
+          const u32 V = shoup32_lazy(x[r | (1u << rb)], W[h], Ws[h], p);
+          x[r] = U + V;
+          x[r | (1u << rb)] = U - V + p2;
         }
       }
     }
   }
-}
-
-template <int LOGN, int RB>
-CW_HD void fwd_pass32(u32 *x, u32 t, u32 lo, u32 c, u32 w, const u32 *psi2, u32 p) {
-  fwd_pass32m<LOGN, RB, 1>(x, t, lo, c, w, psi2, p);
 }
 
 // Inverse butterflies on M transforms of the same prime at once (one

@@ -363,34 +363,6 @@ void pass_ntt_aq(u64 *a, const u64 *tw, u64 q) {
   for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
 }
 
-// Three 32-bit forward transforms of one prime in lock-step (fwd_pass32m),
-// inputs below 4p, outputs canonical.
-template <int LOGN, int RB>
-void pass_ntt32_fwd_x3(u32 *a, const u32 *tw, u32 p) {
-  constexpr u32 R = 1u << RB;
-  const u32 N = 1u << LOGN, T = N / R;
-  const u32 SW = smem_words<RB>(N);
-  std::vector<u32> s(3 * SW);
-  for (int i = 0; i < 3; ++i)
-    for (u32 j = 0; j < N; ++j) s[i * SW + sidx<RB>(j)] = a[i * N + j];
-  for (int pp = 0; pp < Passes<LOGN, RB>::count; ++pp) {
-    u32 lo, c, w;
-    Passes<LOGN, RB>::fwd(pp, lo, c, w);
-    for (u32 t = 0; t < T; ++t) {
-      u32 x[3 * R];
-      for (int i = 0; i < 3; ++i)
-        for (u32 r = 0; r < R; ++r) x[i * R + r] = s[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))];
-      fwd_pass32m<LOGN, RB, 3>(x, t, lo, c, w, tw, p);
-      if (pp == Passes<LOGN, RB>::count - 1)
-        for (u32 r = 0; r < 3 * R; ++r) x[r] = reduce4_32(x[r], p);
-      for (int i = 0; i < 3; ++i)
-        for (u32 r = 0; r < R; ++r) s[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))] = x[i * R + r];
-    }
-  }
-  for (int i = 0; i < 3; ++i)
-    for (u32 j = 0; j < N; ++j) a[i * N + j] = s[i * SW + sidx<RB>(j)];
-}
-
 // Three 32-bit inverse transforms of one prime in lock-step (inv_pass32m).
 template <int LOGN, int RB>
 void pass_ntt32_x3(u32 *a, const u32 *tw, u32 p) {
@@ -521,13 +493,6 @@ uint64_t emu_tensor_intt_compare(uint32_t L, const uint64_t *q, uint64_t t, cons
       std::vector<u32> y(x3);
       pass_ntt32_x3<13, 4>(y.data(), E.tw32[k].data(), (u32)pr);
       for (u32 i = 0; i < N; ++i) bad += y[j * N + i] != x1[i];
-      // forward: three inputs below 4p at once against one at a time
-      for (u32 i = 0; i < N; ++i) x1[i] = x3[j * N + i] + (u32)((data[i] >> 63) * 2 * pr);
-      std::vector<u32> z(x3);
-      for (u32 i = 0; i < N; ++i) z[j * N + i] = x1[i];
-      pass_ntt32<13, 4>(x1.data(), E.tw32[k].data(), (u32)pr, false);
-      pass_ntt32_fwd_x3<13, 4>(z.data(), E.tw32[k].data(), (u32)pr);
-      for (u32 i = 0; i < N; ++i) bad += z[j * N + i] != x1[i];
     }
   }
   return bad;

@@ -188,14 +188,13 @@ def test_row_basis_crt(orc, N, L, nr):
         assert [int(v) for v in out] == [x % qq for qq in q], x
 
 
-def test_tensor_and_lockstep_transform_schedules(orc):
+def test_tensor_inverse_schedules(orc):
     """The tensor kernels' inverse transforms at N = 8192: the 54-bit one with
     the approximate Shoup quotient (values below 4q, three of the four
     partial products of the quotient) leaves N times the stage-by-stage
     inverse in [0, 2q) for every ciphertext prime, from lazy inputs below
-    4q; the 32-bit ones that run three transforms in lock-step (the three
-    tensor outputs inverse, three row limbs forward) equal three single
-    transforms for every extension prime."""
+    4q; the 32-bit one that runs three outputs in lock-step equals three
+    single transforms for every extension prime."""
     q = orc.primes(8192, 4)
     data = syn.Stream(13).words(8192)
     assert emu.lib().emu_tensor_intt_compare(4, np.array(q, np.uint64), T, data) == 0
