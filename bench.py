@@ -163,11 +163,11 @@ def imad_per_job(kind: str, m54: float, m30: float) -> float:
 # jobs of a launch, so a full launch's traffic is this figure times its
 # jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor_intt": (45726464 + 47533312 + 37214976 + 55348224) / 128,
-    "scale": (213959168 + 72737536) / 128,
+    "tensor_intt": (42578432 + 49798912 + 41368064 + 55229184) / 128,
+    "scale": (213987072 + 72763136) / 128,
     # per-job kernels of the row-basis key switch (k_rows_ntt, k_rows_mac);
     # the once-per-row-group conversions are left out
-    "relin_pm": (100940800 + 96588800 + 163607296 + 23501824) / 128,
+    "relin_pm": (108978176 + 100567296 + 163604480 + 25714944) / 128,
 }
 
 
