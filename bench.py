@@ -38,7 +38,7 @@ METRIC = "PIR answer DB MB/s per query (N=8192,k=4); batched vs plain; p50/p99 l
 WL = dict(N=8192, L=4, n=65536, k=4, m=37, plen=8192, t=65537, coef_bytes=2)
 WORKLOAD_NAME = ("index PIR n=65536 rows x 8192 16-bit coefficients, k=4, m=37, "
                  "BFV N=8192 L=4 (54-bit primes) t=65537, one query per step")
-EXT_PRIMES = {1: 4, 2: 6, 3: 8, 4: 9, 5: 11, 6: 13, 7: 15, 8: 17}  # 30-bit primes per L
+EXT_PRIMES = {1: 5, 2: 8, 3: 12, 4: 15, 5: 19, 6: 23, 7: 26, 8: 30}  # 30-bit primes per L
 
 
 def modmul_weights(pk: dict):
@@ -140,17 +140,17 @@ def imad_per_job(kind: str, m54: float, m30: float) -> float:
     K = EXT_PRIMES[L]
     logN = N.bit_length() - 1
     bf = N // 2 * logN
-    if kind == "tensor_intt":  # 3 outputs x (L + K) limbs: 4 products + inverse transform
-        return 3 * (L * bf * m54 + K * bf * m30) + 4 * N * (L * m54 + K * m30)
+    if kind == "tensor_intt":  # 3 outputs x K extension limbs, inverse transforms; 4 products
+        return 3 * K * bf * m30 + 4 * N * K * m30
     if kind == "relin_pm":  # row basis of 3 primes (t = 65537, N = 8192): 3L limbs x 3
         # primes, each reduced (a 32-bit fold and Barrett step, counted as 3)
         # and transformed on 32-bit words, and one 32 x 32-bit product with
         # the row per coefficient; the per-group conversions and key products
         # are left out
         return 3 * L * 3 * (bf * m30 + 3 * N + N)
-    if kind == "scale":  # per coefficient of 3 polynomials
-        per = (m54 * L + K * (2 * L + 2) + m54 * K   # y_j, first stage and its reductions
-               + L * (2 * K + 2) + m54 * L)          # second stage and its reductions
+    if kind == "scale":  # per coefficient of 3 polynomials, from the K extension residues
+        per = (m30 * K + 3 * K          # the digits x_k; the fixed-point sums for v and G
+               + L * (2 * K + 2) + m54 * L)  # the sums modulo q_j and their reductions
         return 3 * N * per
     if kind == "lift":
         return 2 * N * (m54 * L + K * 2 * L + m54 * K)
@@ -163,8 +163,6 @@ def imad_per_job(kind: str, m54: float, m30: float) -> float:
 # jobs of a launch, so a full launch's traffic is this figure times its
 # jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor_intt": (42578432 + 49798912 + 41368064 + 55229184) / 128,
-    "scale": (213987072 + 72763136) / 128,
     # per-job kernels of the row-basis key switch (k_rows_ntt, k_rows_mac);
     # the once-per-row-group conversions are left out
     "relin_pm": (108978176 + 100567296 + 163604480 + 25714944) / 128,

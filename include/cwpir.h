@@ -364,7 +364,13 @@ enum {
   /* row sums of the last tree level: split into row groups until about
    * this many waves of the device's resident threads cover it (0 = the
    * default, 4); drops the cached plans.  Response bits are unchanged. */
-  CWPIR_OPT_ROW_GROUP_WAVES = 8
+  CWPIR_OPT_ROW_GROUP_WAVES = 8,
+  /* 0 (default): the scale-down after each multiplication rounds t d / Q
+   * with a fixed-point sum and hands the rare coefficients it cannot decide
+   * (about one in 2^21) to an exact path; 1: every coefficient takes the
+   * exact path (slower: a check of that path).  Drops the cached plans.
+   * Response bits are unchanged. */
+  CWPIR_OPT_SCALE_EXACT = 9
 };
 /* Both return EINVAL for an unknown option or a value out of range. */
 int cwpir_set_option(cwpir_ctx *ctx, int option, int64_t value);
@@ -426,8 +432,8 @@ int cwpir_inject_status(cwpir_ctx *ctx, uint32_t slot);
  * Intermediates live in one file-scope device array of 2^20 u64 words
  * (8 MiB) plus a 64-word header, held by every GPU that loads the library
  * until the process exits.  One multiplication needs (L^2 + 14L + 7K/2) * N
- * words, K the 30-bit extension primes of the tensor (K = 4, 6, 8, 9, 11,
- * 13, 15, 17 for L = 1 ... 8): N = 4096 allows L <= 8, N = 8192 allows
+ * words, K the 30-bit extension primes of the tensor (K = 5, 8, 12, 15, 19,
+ * 23, 26, 30 for L = 1 ... 8): N = 4096 allows L <= 7, N = 8192 allows
  * L <= 4, N = 16384 allows L <= 2; larger sizes are rejected with EINVAL.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and keeps it for the rest of the process; make

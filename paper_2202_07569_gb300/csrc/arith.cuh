@@ -23,15 +23,17 @@ typedef uint64_t u64;
 typedef uint32_t u32;
 
 constexpr int kMaxL = 8;       // ciphertext primes
-constexpr int kMaxK = 17;      // extension primes (30-bit)
+constexpr int kMaxK = 30;      // extension primes (30-bit)
 
 // Extension primes used with L ciphertext primes: the smallest count of
-// 30-bit primes (each above 2^29.99) whose product P exceeds 2^17 t N Q for
-// 54-bit q_j, t < 2^20 and N <= 2^14.  P > N Q makes the tensor exact in
-// the joint basis and P > t N Q the scale-down's quotient (below).
+// 30-bit primes (each above 2^29.98) whose product P is at least 2 N Q^2
+// for 54-bit q_j and N <= 2^14.  The tensor of two centered lifts
+// (|d| <= N Q^2 / 2) then lies within P/4 of zero, so the extension basis
+// alone holds it exactly; P >= 2^17 t N Q (t < 2^20) follows as well, the
+// bound of the exact scale-down scale_coeff.
 CW_HD constexpr int ext_count(int L) {
-  return L <= 1 ? 4 : L == 2 ? 6 : L == 3 ? 8 : L == 4 ? 9 : L == 5 ? 11 : L == 6 ? 13
-       : L == 7 ? 15 : 17;
+  return L <= 1 ? 5 : L == 2 ? 8 : L == 3 ? 12 : L == 4 ? 15 : L == 5 ? 19 : L == 6 ? 23
+       : L == 7 ? 26 : 30;
 }
 
 CW_HD u64 mulhi(u64 a, u64 b) {
@@ -325,21 +327,21 @@ struct ScaleTab {
 // sum_k yb_k / p_k = rho2 + r/P with |r|/P < 2^-18 (P > 2^17 t N Q), the sum
 // lies within 2^-18 of the integer rho2, and a 6.58 fixed-point sum of
 // yb_k floor(2^58 / p_k), each term low by less than yb_k < 2^30 units of
-// 2^-58, i.e. the sum low by less than 17 * 2^-28, rounds to it exactly.
+// 2^-58, i.e. the sum low by less than 30 * 2^-28, rounds to it exactly.
 // Returns false if that sum is ever 2^-17 or more away from an integer
 // (which the bound rules out); callers record it as an internal error.
 template <int L>
 CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S) {
   constexpr int K = ext_count(L);
   u64 y[L];
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < L; ++j)
     y[j] = shoup(dq[j], S.t_theta[j], S.t_theta_s[j], S.Q.q[j]);
   bool amb;
   u64 rho = round_sum<L>(y, S.Q.w_hi, S.Q.w_lo, &amb);
   if (amb) {
     u64 eps[L];
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < L; ++j)
       eps[j] = shoup(dq[j], S.t_mod[j], S.t_mod_s[j], S.Q.q[j]);
     rho += mr_greater_half<L>(eps, S.Q);
@@ -349,25 +351,25 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
   // every factor is below 2^32: dp_k < 2^31, rho <= L, the halves of y_j,
   // so each product is one wide 32 x 32-bit multiply
   u32 yb[K];
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < K; ++k) {
     u64 s = wmul((u32)dp[k], S.A[k]) + wmul((u32)rho, S.Cr[k]);
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < L; ++j) s += wmul(lo27(y[j]), S.B[j][k]) + wmul(hi27(y[j]), S.B27[j][k]);
     yb[k] = reduce_ext(s, S.ext[k]);
   }
   u64 fix = 0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) fix += wmul(yb[k], S.pw58[k]);  // each < 2^58: sum < 2^63
+#pragma unroll 1
+  for (int k = 0; k < K; ++k) fix += wmul(yb[k], S.pw58[k]);  // each < 2^58: sum < 2^63 (K <= 30)
   const u64 rho2 = (fix + (1ull << 57)) >> 58;
   const u64 frac = (fix + (1ull << 57)) & ((1ull << 58) - 1);  // offset + 1/2, in 2^-58
   const bool far = frac < (1ull << 57) - (1ull << 41) || frac > (1ull << 57) + (1ull << 41);
-  // K + 1 <= 18 products of values below 2^30 with 27-bit halves: the words
-  // ll and x stay below 18 * 2^57 < 2^62.2; the sum ll + x 2^27 < 2^90
-#pragma unroll
+  // K + 1 <= 31 products of values below 2^30 with 27-bit halves: the words
+  // ll and x stay below 31 * 2^57 < 2^62; the sum ll + x 2^27 < 2^90
+#pragma unroll 1
   for (int j = 0; j < L; ++j) {  // rho2 <= K
     u64 ll = wmul((u32)rho2, S.negp2[j][0]), x = wmul((u32)rho2, S.negp2[j][1]);
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < K; ++k) {
       ll += wmul(yb[k], S.hat2[k][j][0]);
       x += wmul(yb[k], S.hat2[k][j][1]);
@@ -377,6 +379,133 @@ CW_HD bool scale_coeff(const u64 *dq, const u64 *dp, u64 *out, const ScaleTab &S
     out[j] = barrett_reduce(hi, lo, S.Q.q[j], S.Q.mu[j]);
   }
   return !far;
+}
+
+// ---------------------------------------------------------------------
+// Exact scale-down e = round(t d / Q) mod q_j from the extension basis
+// alone.  The tensor of two centered lifts, |d| <= N Q^2 / 2, is held
+// exactly by its residues modulo the K extension primes (P >= 2 N Q^2):
+//   x_k = [d (P/p_k)^-1]_{p_k},   d = sum_k x_k (P/p_k) - v P,
+//   v = round(sum_k x_k / p_k)    (the sum lies within |d|/P <= 1/4 of v).
+// Split t (P/p_k) / Q = I_k + f_k and t P / Q = I_P + f_P into integer
+// and fractional parts; then t d / Q = sum_k x_k I_k - v I_P + G with
+// G = sum_k x_k f_k - v f_P, so that exactly
+//   round(t d / Q) = sum_k x_k I_k - v I_P + round(G).
+// G comes from a 58-bit fixed-point sum of x_k floor(f_k 2^58) - v
+// floor(f_P 2^58), which errs by less than sum_k x_k + v < 2^35 units of
+// 2^-58 (below 2^-23); the rounding is taken from it unless its fraction
+// lies within 2^-22 of 1/2, which happens for about one coefficient in 2^21.
+// Those go to scale_exact, which forms N d mod q_j from the same digits and
+// runs scale_coeff.  Q is odd and t d / Q never a half integer, so the
+// rounding is unique.
+//
+// The residues handed over are those of N d (the inverse transforms skip
+// N^-1): c_k carries N^-1.
+// ---------------------------------------------------------------------
+struct ScaleTabP {
+  ExtPrime ext[kMaxK];
+  u32 c[kMaxK], cs[kMaxK];    // N^-1 (P/p_k)^-1 mod p_k, floor(c_k 2^32 / p_k)
+  u32 pw58[kMaxK];            // floor(2^58 / p_k)
+  u32 fh[kMaxK], fl[kMaxK];   // floor(f_k 2^58) = fh_k 2^29 + fl_k
+  u64 fP;                     // floor(f_P 2^58)
+  u32 I2[kMaxK][kMaxL][2];    // I_k mod q_j, 27-bit halves
+  u32 nIP2[kMaxL][2];         // -I_P mod q_j, 27-bit halves
+  u64 q[kMaxL], mu[kMaxL];    // q_j, floor(2^116 / q_j)
+  u64 nq[kMaxL], nq_s[kMaxL]; // N mod q_j and its Shoup companion (exact path)
+  u32 exact_all;              // 1: every coefficient takes the exact path
+};
+
+// Sum of x_k times 27-bit halves h[k][j] of residues modulo q_j, plus
+// `extra` (below 2^61 - (K + 1) 2^57) and v times the halves g: the words
+// stay below 2^62 and their combination below 2^90; reduced modulo q_j.
+template <int K>
+CW_HD u64 sum_to_q(const u32 *x, const u32 (*h)[kMaxL][2], int j, u64 v, const u32 *g,
+                   u64 extra, u64 q, u64 mu) {
+  u64 ll = extra + wmul((u32)v, g[0]), hh = wmul((u32)v, g[1]);  // v <= K
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    ll += wmul(x[k], h[k][j][0]);
+    hh += wmul(x[k], h[k][j][1]);
+  }
+  const u64 lo = ll + (hh << 27);
+  const u64 hi = (hh >> 37) + (lo < ll ? 1 : 0);
+  return barrett_reduce(hi, lo, q, mu);
+}
+
+// The digits x_k of d from dp_k = N d mod p_k below 2^31 (lazy [0, 2p)),
+// and v; false if the sum for v is not within 1/4 + 2^-20 of an integer
+// (which the bound on |d| rules out).  A and B: the two halves of the
+// fixed-point sum for G.
+template <int K>
+CW_HD bool scale_digits(const u32 *dp, u32 *x, u64 *v, u64 *A, u64 *B, const ScaleTabP &S) {
+  u64 fix = 0, a = 0, b = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const u32 d = dp[k], p = S.ext[k].p;
+    x[k] = csub32(d * S.c[k] - mulhi32(d, S.cs[k]) * p, p);  // Shoup: [0, 2p) -> [0, p)
+    fix += wmul(x[k], S.pw58[k]);  // each < 2^58
+    a += wmul(x[k], S.fh[k]);      // each < 2^59: K <= 30 terms fit 64 bits
+    b += wmul(x[k], S.fl[k]);
+  }
+  *A = a;
+  *B = b;
+  const u64 vs = fix + (1ull << 57), vfrac = vs & ((1ull << 58) - 1);
+  *v = vs >> 58;
+  // fix / 2^58 is in (v + d/P - 2^-23, v + d/P] with |d/P| <= 1/4
+  return vfrac >= (1ull << 56) - (1ull << 38) && vfrac <= 3 * (1ull << 56);
+}
+
+// The fast path: writes e and returns 0, or returns 1 when the rounding is
+// left to the exact path (e not written), or 2 when scale_digits fails.
+template <int L>
+CW_HD int scale_fast(const u32 *dp, u64 *e, const ScaleTabP &S) {
+  constexpr int K = ext_count(L);
+  u32 x[K];
+  u64 v, A, B;
+  if (!scale_digits<K>(dp, x, &v, &A, &B, S)) return 2;
+  // T = A 2^29 + B + 2^57 + 64 2^58 - v fP >= 0 (128-bit): the rounding
+  // of G offset by 64
+  u64 lo = A << 29, hi = (A >> 35) + 1;
+  lo += B;
+  hi += lo < B ? 1 : 0;
+  lo += 1ull << 57;
+  hi += lo < (1ull << 57) ? 1 : 0;
+  const u64 vf = v * S.fP;  // v <= K, fP < 2^58
+  hi -= lo < vf ? 1 : 0;
+  lo -= vf;
+  const u64 phi = lo & ((1ull << 58) - 1);
+  if (S.exact_all || phi < (1ull << 36) || phi > (1ull << 58) - (1ull << 36)) return 1;
+  const u64 r64 = (hi << 6) | (lo >> 58);  // round(G) + 64 < 2^36 + 64
+#pragma unroll
+  for (int j = 0; j < L; ++j)  // + (q_j - 64) takes the offset back out
+    e[j] = sum_to_q<K>(x, S.I2, j, v, S.nIP2[j], r64 + S.q[j] - 64, S.q[j], S.mu[j]);
+  return 0;
+}
+
+// The exact path: N d mod q_j = N (sum_k x_k (P/p_k) - v P) mod q_j from
+// scale_coeff's own constants (P/p_k and -P modulo q_j), then scale_coeff
+// on the residues of N d modulo Q and P.
+template <int L>
+CW_HD bool scale_exact(const u32 *dp, u64 *e, const ScaleTabP &SP, const ScaleTab &S) {
+  constexpr int K = ext_count(L);
+  u32 x[K];
+  u64 v, A, B, dq[L], dp64[K];
+  if (!scale_digits<K>(dp, x, &v, &A, &B, SP)) return false;
+#pragma unroll 1
+  for (int j = 0; j < L; ++j) {  // sum_to_q, kept rolled up on this rare path
+    u64 ll = wmul((u32)v, S.negp2[j][0]), hh = wmul((u32)v, S.negp2[j][1]);
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+      ll += wmul(x[k], S.hat2[k][j][0]);
+      hh += wmul(x[k], S.hat2[k][j][1]);
+    }
+    const u64 lo = ll + (hh << 27);
+    const u64 hi = (hh >> 37) + (lo < ll ? 1 : 0);
+    dq[j] = shoup(barrett_reduce(hi, lo, SP.q[j], SP.mu[j]), SP.nq[j], SP.nq_s[j], SP.q[j]);
+  }
+#pragma unroll 1
+  for (int k = 0; k < K; ++k) dp64[k] = dp[k];
+  return scale_coeff<L>(dq, dp64, e, S);
 }
 
 // ---------------------------------------------------------------------

@@ -321,6 +321,7 @@ int build_tables(cwpir_ctx *c) {
                          cudaMemcpyHostToDevice));
   fill_lift(h.lift, c->q, c->p);
   fill_scale(h.scale, c->q, c->p, c->t, N);
+  fill_scale_p(h.scalep, c->q, c->p, c->t, N);
   // row basis: three primes when a group of 32 rows or more fits, else four
   const u64 lim3 = row_group_limit(c->q, c->p, 3, N, c->t);
   const u32 nr = lim3 >= 32 ? 3 : 4;
@@ -666,7 +667,8 @@ int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp
   if (ch.mode == cw::INTERNAL && c->ksr) {
     // key switch in the key-switch basis (digits in the dead tensor buffer,
     // the basis sums in the digit-transform buffer), the result in
-    // coefficient form to CP, then both parts of the QP-NTT destination
+    // coefficient form to CP, then the extension limbs of the QP-NTT
+    // destination: the tensor of the next level reads nothing else
     CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
       return cw::launch_relin_ksr(c->d_tab, c->h, S.E.p, ch.count,
                                   reinterpret_cast<const u32 *>(c->ksr_key.p),
@@ -674,12 +676,10 @@ int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp
                                   S.d_err, S.CP.p, st);
     }));
     CUDA_TRY(c, timed(c, CWPIR_K_LIFT, st, [&] { return cw::launch_lift_jobs(c->d_tab, c->h, S.CP.p, jobs, ch.count, st); }));
-    CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_q(c->d_tab, c->h, S.CP.p, jobs, ch.count, st); }));
     CUDA_TRY(c, timed(c, CWPIR_K_NTT, st, [&] { return cw::launch_ntt_jobs_p(c->d_tab, c->h, jobs, ch.count, st); }));
-    c->stats.kernel_launches += 3 + 4 + 3;  // tensor, scale; key switch; lift, NTTs
+    c->stats.kernel_launches += 2 + 4 + 2;  // tensor, scale; key switch; lift, NTT
     c->stats.mults += ch.count;
-    c->stats.ntt_polys += (u64)ch.count * (3 * (c->L + c->K) + 3 * c->L * cw::kKsrPrimes +
-                                           2 * (c->L + c->K));
+    c->stats.ntt_polys += (u64)ch.count * (3 * c->K + 3 * c->L * cw::kKsrPrimes + 2 * c->K);
     return CWPIR_OK;
   }
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
@@ -692,9 +692,9 @@ int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp
     return cw::launch_relin(c->d_tab, c->h, S.E.p, ch.count, ch.segs, jobs, ch.mode, c->rlk.p,
                             c->rlk_s.p, dbp, P->sp, c->jmax, S.DN.p, S.SEL.p, S.CP.p, st);
   }));
-  c->stats.kernel_launches += 3;  // tensor (ciphertext and extension limbs), scale-down
+  c->stats.kernel_launches += 2;  // tensor, scale-down
   c->stats.mults += ch.count;
-  c->stats.ntt_polys += (u64)ch.count * 3 * (c->L + c->K);
+  c->stats.ntt_polys += (u64)ch.count * 3 * c->K;
   if (rows) {
     const u32 seg_len = ch.count / ch.segs;
     const u32 G = cw::relin_rows_groups(c->h, ch.segs, seg_len, kRowGroups);
@@ -1060,14 +1060,16 @@ int cwpir_setup(const cwpir_params *params, const cwpir_keys *keys, cwpir_ctx **
   c->L = L;
   c->t = params->t;
   c->q = q;
-  // Extension basis P: 30-bit primes, P > 2^17 t N Q (checked below).
+  // Extension basis P: 30-bit primes with P >= 2 N Q^2 (the tensor alone)
+  // and P > 2^17 t N Q (the exact scale-down), checked below.
   c->K = (u32)cw::ext_count((int)L);
   c->p = cw::host::ext_primes(N, c->K);
   if (c->p.size() != c->K) return fail(nullptr, CWPIR_EINVAL, "not enough extension primes");
   long double lq = 0, lp = 0;
   for (u64 v : q) lq += log2l((long double)v);
   for (u64 v : c->p) lp += log2l((long double)v);
-  if (lp < lq + log2l((long double)N) + log2l((long double)params->t) + 17)
+  if (lp < lq + log2l((long double)N) + log2l((long double)params->t) + 17 ||
+      lp < 2 * lq + log2l((long double)N) + 1)
     return fail(nullptr, CWPIR_EINVAL, "extension basis too small");
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(nullptr, CWPIR_ECUDA, "stream: %s", cudaGetErrorString(e));
@@ -1813,6 +1815,11 @@ int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {
       drop_plans(c);
       c->h.row_waves = value ? (u32)value : cw::kDefaultRowWaves;
       return CWPIR_OK;
+    case CWPIR_OPT_SCALE_EXACT:
+      if (value < 0 || value > 1) return fail(c, CWPIR_EINVAL, "scale-exact must be 0 or 1");
+      drop_plans(c);
+      c->h.scalep.exact_all = (u32)value;  // read from the launch parameters
+      return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
   }
 }
@@ -1829,6 +1836,7 @@ int cwpir_get_option(cwpir_ctx *c, int option, int64_t *value) {
     case CWPIR_OPT_ROW_BASIS: *value = c->opt_row_basis; return CWPIR_OK;
     case CWPIR_OPT_MEM_LIMIT: *value = (int64_t)c->acct.limit; return CWPIR_OK;
     case CWPIR_OPT_ROW_GROUP_WAVES: *value = c->h.row_waves; return CWPIR_OK;
+    case CWPIR_OPT_SCALE_EXACT: *value = c->h.scalep.exact_all; return CWPIR_OK;
     default: return fail(c, CWPIR_EINVAL, "unknown option %d", option);
   }
 }
@@ -2180,8 +2188,8 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   if (need > kNoAllocWords)
     return fail(c, CWPIR_EINVAL,
                 "N=%u, L=%u needs (L^2 + 14L + 7K/2)N = %llu scratch words (K = %u extension "
-                "primes); the static array holds %llu (N = 8192 allows L <= 4, N = 16384 "
-                "allows L <= 2)",
+                "primes); the static array holds %llu (N = 4096 allows L <= 7, N = 8192 "
+                "allows L <= 4, N = 16384 allows L <= 2)",
                 c->N, c->L, (unsigned long long)need, c->K,
                 (unsigned long long)kNoAllocWords);
   cudaSetDevice(c->device);

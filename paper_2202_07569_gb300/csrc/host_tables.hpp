@@ -234,6 +234,145 @@ inline void fill_scale(cw::ScaleTab &S, const std::vector<u64> &q, const std::ve
   }
 }
 
+// Unsigned multi-precision integers (32-bit words, least significant
+// first), for the few setup constants that need exact products and
+// quotients of the moduli.
+struct Big {
+  std::vector<u32> w;
+  static Big of(u64 v) {
+    Big b;
+    b.w = {(u32)v, (u32)(v >> 32)};
+    b.trim();
+    return b;
+  }
+  void trim() {
+    while (!w.empty() && w.back() == 0) w.pop_back();
+  }
+  u32 bits() const {
+    if (w.empty()) return 0;
+    u32 n = 32 * (u32)(w.size() - 1), top = w.back();
+    while (top) ++n, top >>= 1;
+    return n;
+  }
+  bool bit(u32 i) const { return i / 32 < w.size() && ((w[i / 32] >> (i % 32)) & 1u); }
+  void mul(u64 m) {  // *= m
+    u128 carry = 0;
+    for (u32 &x : w) {
+      const u128 v = (u128)x * m + carry;
+      x = (u32)v;
+      carry = v >> 32;
+    }
+    while (carry) w.push_back((u32)carry), carry >>= 32;
+    trim();
+  }
+  void shl1_or(u32 b) {  // = 2 * this + b
+    u32 carry = b;
+    for (u32 &x : w) {
+      const u32 top = x >> 31;
+      x = (x << 1) | carry;
+      carry = top;
+    }
+    if (carry) w.push_back(carry);
+  }
+  bool geq(const Big &o) const {
+    if (w.size() != o.w.size()) return w.size() > o.w.size();
+    for (size_t i = w.size(); i-- > 0;)
+      if (w[i] != o.w[i]) return w[i] > o.w[i];
+    return true;
+  }
+  void sub(const Big &o) {  // this >= o
+    u64 borrow = 0;
+    for (size_t i = 0; i < w.size(); ++i) {
+      const u64 d = (u64)w[i] - (i < o.w.size() ? o.w[i] : 0) - borrow;
+      w[i] = (u32)d;
+      borrow = (d >> 63) & 1;
+    }
+    trim();
+  }
+  u64 mod(u64 m) const {
+    u128 r = 0;
+    for (size_t i = w.size(); i-- > 0;) r = ((r << 32) | w[i]) % m;
+    return (u64)r;
+  }
+  u64 low64() const {
+    return (w.size() > 0 ? w[0] : 0) | (w.size() > 1 ? (u64)w[1] << 32 : 0);
+  }
+};
+
+// a = quo b + rem, 0 <= rem < b (b > 0), by binary long division.
+inline void big_divmod(const Big &a, const Big &b, Big &quo, Big &rem) {
+  quo.w.assign(a.w.size(), 0);
+  rem.w.clear();
+  for (u32 i = a.bits(); i-- > 0;) {
+    rem.shl1_or(a.bit(i) ? 1u : 0u);
+    if (rem.geq(b)) {
+      rem.sub(b);
+      quo.w[i / 32] |= 1u << (i % 32);
+    }
+  }
+  quo.trim();
+}
+
+inline Big big_prod(const std::vector<u64> &v, int skip = -1) {
+  Big b = Big::of(1);
+  for (size_t i = 0; i < v.size(); ++i)
+    if ((int)i != skip) b.mul(v[i]);
+  return b;
+}
+
+// floor(num / den) mod each q_j into 27-bit halves, and floor(frac(num /
+// den) 2^58).
+inline u64 split_quotient(const Big &num, const Big &den, const std::vector<u64> &q,
+                          u32 (*halves)[2]) {
+  Big quo, rem;
+  big_divmod(num, den, quo, rem);
+  for (size_t j = 0; j < q.size(); ++j) split27(quo.mod(q[j]), halves[j]);
+  for (int b = 0; b < 58; ++b) rem.mul(2);
+  Big f, r2;
+  big_divmod(rem, den, f, r2);
+  return f.low64();
+}
+
+// Constants of the scale-down from the extension basis (ScaleTabP in
+// arith.cuh); N is the factor the residues carry.
+inline void fill_scale_p(cw::ScaleTabP &S, const std::vector<u64> &q, const std::vector<u64> &p,
+                         u64 t, u64 N) {
+  memset(&S, 0, sizeof S);
+  const u32 L = (u32)q.size(), K = (u32)p.size();
+  const Big Q = big_prod(q);
+  for (u32 k = 0; k < K; ++k) {
+    const u64 pk = p[k];
+    S.ext[k] = ext_prime(pk);
+    const u64 c = hmul(hinv(hat_mod(p, k, pk), pk), hinv(N % pk, pk), pk);
+    S.c[k] = (u32)c;
+    S.cs[k] = (u32)((c << 32) / pk);
+    S.pw58[k] = (u32)((1ull << 58) / pk);
+    Big num = big_prod(p, (int)k);
+    num.mul(t);
+    u32 halves[cw::kMaxL][2];
+    const u64 f = split_quotient(num, Q, q, halves);
+    S.fh[k] = (u32)(f >> 29);
+    S.fl[k] = (u32)(f & ((1u << 29) - 1));
+    for (u32 j = 0; j < L; ++j) {
+      S.I2[k][j][0] = halves[j][0];
+      S.I2[k][j][1] = halves[j][1];
+    }
+  }
+  Big num = big_prod(p);
+  num.mul(t);
+  u32 halves[cw::kMaxL][2];
+  S.fP = split_quotient(num, Q, q, halves);
+  for (u32 j = 0; j < L; ++j) {
+    const u64 qj = q[j];
+    const u64 ip = ((u64)halves[j][1] << 27) | halves[j][0];
+    split27(ip ? qj - ip : 0, S.nIP2[j]);
+    S.q[j] = qj;
+    S.mu[j] = (u64)(((u128)1 << 116) / qj);
+    S.nq[j] = N % qj;
+    S.nq_s[j] = shoup_of(S.nq[j], qj);
+  }
+}
+
 // Largest number of rows per group for which the row basis of the first nr
 // extension primes holds the group sums exactly: rows N q_max (t-1)/2 <=
 // (1 - 2^-23) R/2 (see RowTab in arith.cuh).

@@ -111,34 +111,6 @@ __device__ __forceinline__ void ntt_inv(NttRegs<LOGN> &x, u64 *s, const NttPrime
   }
 }
 
-// The tensor's inverse transform (without N^-1) through inv_pass_aq:
-// x[r] = NTT value R t + r (< 4q) -> N times the coefficient, in [0, 2q).
-template <int LOGN>
-__device__ __forceinline__ void ntt_inv_aq(NttRegs<LOGN> &x, u64 *s, const NttPrime &P) {
-  constexpr int RB = NttShape<LOGN>::RB, R = NttShape<LOGN>::R;
-  constexpr int NP = Passes<LOGN, RB>::count;
-  const u32 t = threadIdx.x;
-  u32 wprev = 0;
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    u32 lo, c, w;
-    Passes<LOGN, RB>::inv(p, lo, c, w);
-    if (p > 0) {
-#pragma unroll
-      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, wprev))] = x[r];
-      __syncthreads();
-#pragma unroll
-      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
-      __syncthreads();
-    }
-    inv_pass_aq<LOGN, RB>(x, t, lo, c, w, P.ipsi2, P.q);
-    wprev = w;
-  }
-  const u64 q2 = 2 * P.q;
-#pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = x[r] >= q2 ? x[r] - q2 : x[r];
-}
-
 // The same transforms on 32-bit words for a 30-bit extension prime: the
 // forward one from [0, 4p) to canonical values, the inverse one from
 // [0, 2p) to N times the coefficient in [0, 2p) (no N^-1: the scale-down
@@ -362,14 +334,14 @@ __global__ void k_lift_jobs(const DevTables *T, const u64 *C, const MulJob *jobs
 }
 
 // ---------------------------------------------------------------------
-// Tensor of two QP-NTT ciphertexts, one output polynomial and limb per
-// CTA, followed by the inverse NTT: d0 = a0 b0, d1 = a0 b1 + a1 b0,
-// d2 = a1 b1.  k_tensor_intt covers the L ciphertext limbs, grid
-// (njobs, 3, L); k_tensor_ext the K extension limbs on 32-bit words, grid
-// (njobs, 3, K), with a smaller register budget and more resident blocks
-// so that the operand loads of some blocks overlap the transforms of
-// others.  The limb varies slowest so that the blocks resident on one SM
-// share one prime's twiddles in L1.
+// Tensor of two QP-NTT ciphertexts followed by the inverse NTT:
+// d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1, on the K extension limbs
+// alone (their product P >= 2 N Q^2 holds the tensor of two centered lifts
+// exactly, and the scale-down reads nothing else).  One block per job and
+// prime computes all three outputs, so that the four operand loads of a
+// coefficient serve its three products and one twiddle load serves three
+// butterflies.  grid (njobs, K); the prime varies slowest so that the
+// blocks resident on one SM share its twiddles in L1.
 // ---------------------------------------------------------------------
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
@@ -424,56 +396,46 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
   }
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
-    k_tensor_intt(const DevTables *T, const MulJob *jobs, u64 *Tbuf) {
-  extern __shared__ u64 s[];
-  constexpr u32 N = 1u << LOGN;
-  const u32 L = T->L, l = blockIdx.z, which = blockIdx.y, t = threadIdx.x;
-  const u64 job = blockIdx.x;
-  const MulJob J = jobs[job];
-  const u64 ps = qp_poly_words(L, T->K, N);
-  u64 *outp = Tbuf + (job * 3 + which) * ps;
-  constexpr u32 R = NttShape<LOGN>::R;
-  const NttPrime P = T->prime[l];
-  const u64 *a0 = J.a + (u64)l * N, *a1 = a0 + ps;
-  const u64 *b0 = J.b + (u64)l * N, *b1 = b0 + ps;
-  u64 *out = outp + (u64)l * N;
-  NttRegs<LOGN> x;
-#pragma unroll
-  for (u32 r = 0; r < R; ++r) {
-    const u32 c = ntt_pos<LOGN>(t, r);
-    u64 v;
-    if (which == 0) v = barrett(a0[c], b0[c], P.q, P.mu);
-    else if (which == 2) v = barrett(a1[c], b1[c], P.q, P.mu);
-    else v = addq(barrett(a0[c], b1[c], P.q, P.mu), barrett(a1[c], b0[c], P.q, P.mu), P.q);
-    x[r] = v;
-  }
-  ntt_inv_aq<LOGN>(x, s, P);  // N d in [0, 2q): the scale-down absorbs N^-1
-#pragma unroll
-  for (u32 r = 0; r < R; ++r) out[strided_idx<LOGN>(t, r)] = x[r];
+// ---------------------------------------------------------------------
+// Exact scale-down of every tensor coefficient from its K extension
+// residues (scale_fast); the few coefficients whose fixed-point rounding is
+// too close to call go through scale_exact, kept out of line so that its
+// registers do not weigh on the common path.  grid (N/256, 3*njobs).
+// ---------------------------------------------------------------------
+// the exact path for coefficient c of the polynomial at `in`, out of line:
+// it reloads its residues, so that nothing of the caller's stays live
+template <int L>
+__device__ __noinline__ bool scale_exact_at(const DevTables *T, const u64 *in, u64 *out, u32 c) {
+  constexpr int K = ext_count(L);
+  const u32 N = T->N;
+  u32 dp[K];
+  u64 e[L];
+  for (int k = 0; k < K; ++k) dp[k] = ext_limb(in, L, N, k)[c];
+  const bool ok = scale_exact<L>(dp, e, T->scalep, T->scale);
+  for (int j = 0; j < L; ++j) out[(u64)j * N + c] = e[j];
+  return ok;
 }
 
-// ---------------------------------------------------------------------
-// Exact scale-down of every tensor coefficient.  grid (N/256, 3*njobs).
-// ---------------------------------------------------------------------
 template <int L>
 __global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err,
-                        const __grid_constant__ ScaleTab S) {
+                        const __grid_constant__ ScaleTabP S) {
   constexpr int K = ext_count(L);
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 jw = blockIdx.y;
   const u64 *in = Tbuf + jw * qp_poly_words(L, K, N);
-  u64 dq[L], dp[K], e[L];
-#pragma unroll
-  for (int j = 0; j < L; ++j) dq[j] = in[(u64)j * N + c];
+  u64 *out = E + jw * L * N;
+  u32 dp[K];
+  u64 e[L];
 #pragma unroll
   for (int k = 0; k < K; ++k) dp[k] = ext_limb(in, L, N, k)[c];
-  if (!scale_coeff<L>(dq, dp, e, S)) atomicOr(err, 1);
-  u64 *out = E + jw * L * N;
+  const int r = scale_fast<L>(dp, e, S);
+  if (r == 0) {
 #pragma unroll
-  for (int j = 0; j < L; ++j) out[(u64)j * N + c] = e[j];
+    for (int j = 0; j < L; ++j) out[(u64)j * N + c] = e[j];
+  } else if (r == 2 || !scale_exact_at<L>(T, in, out, c)) {
+    atomicOr(err, 1);
+  }
 }
 
 // ---------------------------------------------------------------------
@@ -870,26 +832,6 @@ __global__ void k_ksr_crt(const DevTables *T, const u32 *O, const u64 *E, int *e
   C[(job * 2 + comp) * L * N + (u64)j * N + c] = addq(x, e, KT.q[j]);
 }
 
-// Forward NTT of the Q limbs of C[job][poly][j] (coefficient form) into
-// jobs[job].dst (QP layout, NTT form).  grid (L, 2 * njobs).
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::threads, NttShape<LOGN>::min_blocks)
-    k_ntt_jobs_q(const DevTables *T, const u64 *C, const MulJob *jobs) {
-  extern __shared__ u64 s[];
-  constexpr u32 N = 1u << LOGN, R = NttShape<LOGN>::R;
-  const u32 L = T->L, t = threadIdx.x, j = blockIdx.x;
-  const u32 job = blockIdx.y >> 1, poly = blockIdx.y & 1;
-  const NttPrime P = T->prime[j];
-  const u64 *in = C + (((u64)job * 2 + poly) * L + j) * N;
-  u64 *out = jobs[job].dst + poly * qp_poly_words(L, T->K, N) + (u64)j * N;
-  NttRegs<LOGN> x;
-#pragma unroll
-  for (u32 r = 0; r < R; ++r) x[r] = in[strided_idx<LOGN>(t, r)];
-  ntt_fwd<LOGN>(x, s, P);
-#pragma unroll
-  for (u32 r = 0; r < R; ++r) out[ntt_pos<LOGN>(t, r)] = x[r];
-}
-
 // (B) producing the NTT-form result: INTERNAL mode writes it to the Q
 // limbs of jobs[job].dst (QP layout), other modes to O[job][2][L][N].
 // grid (N/256, L, njobs).
@@ -1244,11 +1186,7 @@ cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const Mul
                                u32 njobs, u64 *Tbuf, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_tensor_intt<LG>, ntt_smem_bytes<LG>());
-    if (e != cudaSuccess) return e;
-    k_tensor_intt<LG><<<dim3(njobs, 3, h.L), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
-        T, jobs, Tbuf);
-    e = allow_smem(k_tensor_ext<LG>, 3 * smem32_bytes<LG>());
+    cudaError_t e = allow_smem(k_tensor_ext<LG>, 3 * smem32_bytes<LG>());
     if (e != cudaSuccess) return e;
     k_tensor_ext<LG><<<dim3(njobs, h.K), ntt_block32<LG>(), 3 * smem32_bytes<LG>(), st>>>(
         T, jobs, Tbuf);
@@ -1260,7 +1198,7 @@ cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf
                          u64 *E, int *err, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   dim3 grid(h.N / 256, 3 * njobs);
-  CW_DISPATCH_L(h.L, k_scale, grid, 256, 0, st, T, Tbuf, E, err, h.scale);
+  CW_DISPATCH_L(h.L, k_scale, grid, 256, 0, st, T, Tbuf, E, err, h.scalep);
   return cudaGetLastError();
 }
 
@@ -1447,17 +1385,6 @@ cudaError_t launch_ksr_key(const DevTables *T, const DevTables &h, const u64 *ke
   return rns_ntt(T, h, key, h.N, 1, kKsrPrimes, 2 * h.L * h.L, ks, st);
 }
 
-cudaError_t launch_ntt_jobs_q(const DevTables *T, const DevTables &h, const u64 *C,
-                              const MulJob *jobs, u32 njobs, cudaStream_t st) {
-  if (!njobs) return cudaSuccess;
-  CW_DISPATCH_LOGN(h.logN, {
-    cudaError_t e = allow_smem(k_ntt_jobs_q<LG>, ntt_smem_bytes<LG>());
-    if (e != cudaSuccess) return e;
-    k_ntt_jobs_q<LG><<<dim3(h.L, 2 * njobs), ntt_block<LG>(), ntt_smem_bytes<LG>(), st>>>(
-        T, C, jobs);
-  });
-  return cudaGetLastError();
-}
 
 cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                               u32 segs, const MulJob *jobs, const u64 *rlk, const u64 *rlk_s,

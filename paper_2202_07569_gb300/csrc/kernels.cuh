@@ -29,7 +29,8 @@ struct DevTables {
   NttPrime prime[kMaxL];  // ciphertext primes q_0..q_{L-1}
   ExtNtt ext[kMaxK];      // extension primes p_0..p_{K-1} (30-bit)
   LiftTab lift;           // centered Q -> P conversion (leaves, nodes)
-  ScaleTab scale;         // exact round(t d / Q)
+  ScaleTab scale;         // exact round(t d / Q) from residues modulo Q and P
+  ScaleTabP scalep;       // round(t d / Q) from residues modulo P alone
   RowTab rows;            // row basis: first nr extension primes -> Q
   RowTab ksr;             // key-switch basis: first five extension primes -> Q
 };
@@ -39,7 +40,8 @@ constexpr u32 kKsrPrimes = 5;
 
 // QP layout of one polynomial (NTT domain or, for the tensor buffer,
 // coefficients): L limbs of N u64 residues mod q_j, then K limbs of N u32
-// residues mod the 30-bit p_k; L N + K N / 2 u64 words in all.
+// residues mod the 30-bit p_k; L N + K N / 2 u64 words in all.  The
+// tensor buffer uses the K limbs alone.
 CW_HD u64 qp_poly_words(u32 L, u32 K, u32 N) { return (u64)L * N + (u64)K * N / 2; }
 CW_HD u32 *ext_limb(u64 *poly, u32 L, u32 N, u32 k) {
   return reinterpret_cast<u32 *>(poly + (u64)L * N) + (u64)k * N;
@@ -66,7 +68,7 @@ struct SubJob {
 enum RootMode : int {
   ROOT_PM = 0,    // sel * DB[row] -> partial products
   ROOT_SEL = 1,   // sel in coefficient form -> dst ([2][L][N])
-  INTERNAL = 2    // sel -> QP-NTT form at dst (Q limbs here, P limbs later)
+  INTERNAL = 2    // sel -> the extension limbs of a QP-NTT ciphertext at dst
 };
 
 
@@ -143,10 +145,6 @@ cudaError_t launch_relin_ksr(const DevTables *T, const DevTables &h, const u64 *
 // into the key-switch basis: ks [L][2][L][5][N] u32, NTT form.
 cudaError_t launch_ksr_key(const DevTables *T, const DevTables &h, const u64 *key, u32 *ks,
                            cudaStream_t st);
-// Forward NTT of the Q limbs of C[job][2][L][N] (coefficient form) into
-// the Q limbs of jobs[job].dst (QP layout).
-cudaError_t launch_ntt_jobs_q(const DevTables *T, const DevTables &h, const u64 *C,
-                              const MulJob *jobs, u32 njobs, cudaStream_t st);
 // k = 1: P[job][sp][2][L][N] = leaf * DB[row][p].
 cudaError_t launch_pm_leaf(const DevTables *T, const DevTables &h, const MulJob *jobs,
                            u32 njobs, u32 sp, const u64 *db, u64 *P, cudaStream_t st);

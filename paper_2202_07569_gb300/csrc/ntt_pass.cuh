@@ -109,46 +109,6 @@ CW_HD void inv_pass(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi2, u64 q
   }
 }
 
-// Shoup product a*w mod q from three of the four 32 x 32-bit partial
-// products of the quotient (the low x low one dropped, both cross terms
-// floored): qa <= floor(a ws / 2^64) <= qa + 2, so a*w - qa*q lies in
-// [0, 4q) for a < 2^57 (one wide and two high 32-bit products instead of a
-// 64 x 64 high product).
-CW_HD u64 shoup_aq(u64 a, u64 w, u64 ws, u64 q) {
-  const u32 a0 = (u32)a, a1 = (u32)(a >> 32), w0 = (u32)ws, w1 = (u32)(ws >> 32);
-  const u64 qa = (u64)a1 * w1 + mulhi32(a1, w0) + mulhi32(a0, w1);
-  return a * w - qa * q;
-}
-
-// Inverse butterflies with values in [0, 4q) throughout (the tensor's
-// inverse transforms): U + V < 8q comes back below 4q, U - V + 4q < 8q <
-// 2^57 goes through shoup_aq.
-template <int LOGN, int RB>
-CW_HD void inv_pass_aq(u64 *x, u32 t, u32 lo, u32 c, u32 w, const u64 *ipsi2, u64 q) {
-  const u64 q4 = 4 * q;
-  constexpr u32 R = 1u << RB;
-#pragma unroll
-  for (int bi = 0; bi < RB; ++bi) {
-    if ((u32)bi >= c) continue;
-    const u32 b = lo + bi, rb = b - w, m = 1u << (LOGN - 1 - b);
-#pragma unroll
-    for (u32 hv = 0; hv < (R >> (rb + 1)); ++hv) {
-      const u32 r0 = hv << (rb + 1);
-      const u32 g = pass_idx<RB>(t, r0, w) >> (b + 1);
-      u64 W, Ws;
-      ld_pair(ipsi2 + 2 * (m + g), W, Ws);
-#pragma unroll
-      for (u32 lv = 0; lv < (1u << rb); ++lv) {
-        const u32 r = r0 | lv;
-        const u64 U = x[r], V = x[r | (1u << rb)];
-        const u64 S = U + V;
-        x[r] = S >= q4 ? S - q4 : S;
-        x[r | (1u << rb)] = shoup_aq(U - V + q4, W, Ws, q);
-      }
-    }
-  }
-}
-
 // [0, 4q) -> [0, q)
 CW_HD u64 reduce4(u64 v, u64 q) {
   const u64 q2 = 2 * q;

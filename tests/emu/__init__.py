@@ -28,7 +28,11 @@ def lib():
     U32, U64 = C.c_uint32, C.c_uint64
     l.emu_tensor_intt_compare.argtypes = [U32, u64p, U64, u64p]
     l.emu_tensor_intt_compare.restype = U64
-    l.emu_bfv_mul.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p, u64p]
+    l.emu_bfv_mul.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p, u64p, C.c_int]
+    l.emu_scale_p.argtypes = [U32, U32, u64p, U64, U64,
+                              np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), u64p, C.c_int,
+                              np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")]
+    l.emu_scale_p.restype = None
     l.emu_bfv_mul.restype = C.c_int
     l.emu_lift.argtypes = [U32, U32, u64p, U64, u64p, u64p]
     l.emu_lift.restype = None

@@ -27,6 +27,7 @@ struct Emu {
   std::vector<ExtPrime> ext;
   LiftTab LT;
   ScaleTab S;
+  ScaleTabP SP;
 
   Emu(u32 N_, u32 L_, const u64 *q_, u64 t_) : N(N_), L(L_), t(t_) {
     logN = 0;
@@ -52,6 +53,7 @@ struct Emu {
     }
     fill_lift(LT, q, p);
     fill_scale(S, q, p, t, N);
+    fill_scale_p(SP, q, p, t, N);
   }
   void fwd(u64 *a, u32 l) {
     const u64 *w = tw[l].data();
@@ -103,6 +105,23 @@ struct Emu {
       case 7: return scale_coeff<7>(dq, dp, e, S);
       default: return scale_coeff<8>(dq, dp, e, S);
     }
+  }
+  // The kernels' scale-down from the extension residues dp (N d mod p_k,
+  // lazy): 0 = fast path, 1 = exact path (always with force_exact), -1 =
+  // a failed check.
+  int scale_p(const u32 *dp, u64 *e, bool force_exact) {
+    int r = 1;
+    switch (L) {
+#define CW_EMU_SCALE(LL)                                                          \
+  case LL:                                                                        \
+    if (!force_exact) r = scale_fast<LL>(dp, e, SP);                              \
+    if (r == 1) return scale_exact<LL>(dp, e, SP, S) ? 1 : -1;                    \
+    return r == 0 ? 0 : -1;
+      CW_EMU_SCALE(1) CW_EMU_SCALE(2) CW_EMU_SCALE(3) CW_EMU_SCALE(4)
+      CW_EMU_SCALE(5) CW_EMU_SCALE(6) CW_EMU_SCALE(7) CW_EMU_SCALE(8)
+#undef CW_EMU_SCALE
+    }
+    return -1;
   }
   // key [L][2][L][N] coefficient -> NTT + Shoup companions
   void prep_key(const u64 *key, std::vector<u64> &k, std::vector<u64> &ks) {
@@ -157,59 +176,65 @@ struct Emu {
 
 extern "C" {
 
-// One homomorphic multiplication, returns 0 or 1 if the scale-down check
-// tripped.
+// One homomorphic multiplication in the kernels' order: the tensor on the
+// extension limbs alone, the scale-down from them (every coefficient through
+// the exact path when force_exact), the key switch.  Returns 0, or 1 if a
+// scale-down check tripped.
 int emu_bfv_mul(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *rlk,
-                const uint64_t *a, const uint64_t *b, uint64_t *out) {
+                const uint64_t *a, const uint64_t *b, uint64_t *out, int force_exact) {
   Emu E(N, L, q, t);
   const u32 LK = L + E.K;
   std::vector<u64> A(2ull * LK * N), B(2ull * LK * N);
   E.to_qp(a, A.data());
   E.to_qp(b, B.data());
-  std::vector<u64> Tb(3ull * LK * N), Eb(3ull * L * N);
+  std::vector<u32> Tb(3ull * E.K * N);
+  std::vector<u64> o(N), Eb(3ull * L * N);
   for (u32 which = 0; which < 3; ++which)
-    for (u32 l = 0; l < LK; ++l) {
-      u64 pr = E.all[l], m = E.mu[l];
+    for (u32 k = 0; k < E.K; ++k) {
+      const u32 l = L + k;
+      const u64 pr = E.all[l];
       const u64 *a0 = A.data() + (u64)l * N, *a1 = a0 + (u64)LK * N;
       const u64 *b0 = B.data() + (u64)l * N, *b1 = b0 + (u64)LK * N;
-      u64 *o = Tb.data() + ((u64)which * LK + l) * N;
-      if (l < L) {
-        for (u32 c = 0; c < N; ++c) {
-          if (which == 0) o[c] = barrett(a0[c], b0[c], pr, m);
-          else if (which == 2) o[c] = barrett(a1[c], b1[c], pr, m);
-          else o[c] = addq(barrett(a0[c], b1[c], pr, m), barrett(a1[c], b0[c], pr, m), pr);
+      // the kernels' 32-bit products, lazy [0, 2p)
+      const ExtPrime &X = E.ext[k];
+      const u32 p2 = 2 * X.p;
+      for (u32 c = 0; c < N; ++c) {
+        u32 v;
+        if (which == 0) v = mulmod_ext_lazy((u32)a0[c], (u32)b0[c], X);
+        else if (which == 2) v = mulmod_ext_lazy((u32)a1[c], (u32)b1[c], X);
+        else {
+          v = mulmod_ext_lazy((u32)a0[c], (u32)b1[c], X) + mulmod_ext_lazy((u32)a1[c], (u32)b0[c], X);
+          v = v >= p2 ? v - p2 : v;
         }
-      } else {  // extension limb: the kernels' 32-bit products, lazy [0, 2p)
-        const ExtPrime &X = E.ext[l - L];
-        const u32 p2 = 2 * X.p;
-        for (u32 c = 0; c < N; ++c) {
-          u32 v;
-          if (which == 0) v = mulmod_ext_lazy((u32)a0[c], (u32)b0[c], X);
-          else if (which == 2) v = mulmod_ext_lazy((u32)a1[c], (u32)b1[c], X);
-          else {
-            v = mulmod_ext_lazy((u32)a0[c], (u32)b1[c], X) + mulmod_ext_lazy((u32)a1[c], (u32)b0[c], X);
-            v = v >= p2 ? v - p2 : v;
-          }
-          o[c] = v >= X.p ? v - X.p : v;
-        }
+        o[c] = v >= X.p ? v - X.p : v;
       }
-      E.inv(o, l);  // canonical d; the scale-down takes N d as the kernels hand it over
-      for (u32 c = 0; c < N; ++c) o[c] = hmul(o[c], N % pr, pr) + ((c & 1) ? pr : 0);
+      E.inv(o.data(), l);  // canonical d; the scale-down takes N d as the kernels hand it over
+      for (u32 c = 0; c < N; ++c)
+        Tb[((u64)which * E.K + k) * N + c] = (u32)(hmul(o[c], N % pr, pr) + ((c & 1) ? pr : 0));
     }
   int bad = 0;
-  u64 dq[kMaxL], dp[kMaxK], e[kMaxL];
+  u32 dp[kMaxK];
+  u64 e[kMaxL];
   for (u32 which = 0; which < 3; ++which)
     for (u32 c = 0; c < N; ++c) {
-      const u64 *in = Tb.data() + (u64)which * LK * N;
-      for (u32 j = 0; j < L; ++j) dq[j] = in[(u64)j * N + c];
-      for (u32 k = 0; k < E.K; ++k) dp[k] = in[(u64)(L + k) * N + c];
-      if (!E.scale(dq, dp, e)) bad = 1;
+      for (u32 k = 0; k < E.K; ++k) dp[k] = Tb[((u64)which * E.K + k) * N + c];
+      if (E.scale_p(dp, e, force_exact != 0) < 0) bad = 1;
       for (u32 j = 0; j < L; ++j) Eb[((u64)which * L + j) * N + c] = e[j];
     }
   std::vector<u64> k, ks;
   E.prep_key(rlk, k, ks);
   E.keyswitch(Eb.data() + 2ull * L * N, Eb.data(), Eb.data() + (u64)L * N, k, ks, out);
   return bad;
+}
+
+// The scale-down from the extension residues for n coefficients: dp [n][K]
+// (N d mod p_k, below 2^31), out [n][L]; path[i] = 0 (fast), 1 (exact),
+// -1 (a failed check).
+void emu_scale_p(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, uint64_t n,
+                 const uint32_t *dp, uint64_t *out, int force_exact, int32_t *path) {
+  Emu E(N, L, q, t);
+  for (u64 i = 0; i < n; ++i)
+    path[i] = E.scale_p(dp + i * E.K, out + i * L, force_exact != 0);
 }
 
 // Centered Q -> P conversion of one coefficient vector ([L] residues).
@@ -340,29 +365,6 @@ void pass_ntt32(u32 *a, const u32 *tw, u32 p, bool inverse) {
   for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
 }
 
-// The tensor's inverse schedule with the approximate Shoup quotient
-// (inv_pass_aq, values below 4q), ending with one subtraction of 2q.
-template <int LOGN, int RB>
-void pass_ntt_aq(u64 *a, const u64 *tw, u64 q) {
-  constexpr u32 R = 1u << RB;
-  const u32 N = 1u << LOGN, T = N / R;
-  std::vector<u64> s(smem_words<RB>(N));
-  for (u32 i = 0; i < N; ++i) s[sidx<RB>(i)] = a[i];
-  for (int p = 0; p < Passes<LOGN, RB>::count; ++p) {
-    u32 lo, c, w;
-    Passes<LOGN, RB>::inv(p, lo, c, w);
-    for (u32 t = 0; t < T; ++t) {
-      u64 x[R];
-      for (u32 r = 0; r < R; ++r) x[r] = s[sidx<RB>(pass_idx<RB>(t, r, w))];
-      inv_pass_aq<LOGN, RB>(x, t, lo, c, w, tw + 2 * N, q);
-      if (p == Passes<LOGN, RB>::count - 1)
-        for (u32 r = 0; r < R; ++r) x[r] = x[r] >= 2 * q ? x[r] - 2 * q : x[r];
-      for (u32 r = 0; r < R; ++r) s[sidx<RB>(pass_idx<RB>(t, r, w))] = x[r];
-    }
-  }
-  for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
-}
-
 // Three 32-bit inverse transforms of one prime in lock-step (inv_pass32m).
 template <int LOGN, int RB>
 void pass_ntt32_x3(u32 *a, const u32 *tw, u32 p) {
@@ -461,28 +463,14 @@ uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
 }
 
 extern "C" {
-// The tensor kernels' inverse transforms against the stage-by-stage one
-// (N = 8192, 16 coefficients a thread): the approximate-quotient schedule on
-// every ciphertext prime from lazy inputs below 4q must leave N times the
-// coefficients in [0, 2q); the three-transform 32-bit schedule on every
-// extension prime must leave each of three inputs (below 2p) as the single
-// schedule does.  Returns the number of mismatches.
+// The tensor kernel's inverse transforms (N = 8192, 16 coefficients a
+// thread): the three-transform 32-bit schedule on every extension prime
+// must leave each of three inputs (below 2p) as the single schedule does.
+// Returns the number of mismatches.
 uint64_t emu_tensor_intt_compare(uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *data) {
   const u32 N = 8192;
   Emu E(N, L, q, t);
   uint64_t bad = 0;
-  for (u32 l = 0; l < L; ++l) {
-    const u64 pr = E.all[l];
-    std::vector<u64> a(N), b(N);
-    for (u32 i = 0; i < N; ++i) {
-      a[i] = data[i] % pr;
-      b[i] = a[i] + (data[i] >> 62) * pr;  // lazy input below 4q
-    }
-    E.inv(a.data(), l);
-    pass_ntt_aq<13, 4>(b.data(), E.tw[l].data(), pr);
-    for (u32 i = 0; i < N; ++i)
-      bad += b[i] >= 2 * pr || b[i] % pr != hmul(a[i], N % pr, pr);
-  }
   for (u32 k = 0; k < E.K; ++k) {
     const u64 pr = E.p[k];
     std::vector<u32> x3(3 * N), x1(N);

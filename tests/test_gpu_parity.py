@@ -44,6 +44,34 @@ def test_mul_matches_oracle(N, L):
         assert np.array_equal(got, cl.O.bfv_mul(a, b, cl.rlk)), trial
 
 
+@pytest.mark.parametrize("N,L", [(1024, 1), (8192, 4), (16384, 7)])
+def test_scale_down_exact_path_matches_oracle(N, L):
+    """The scale-down's exact path, forced for every coefficient
+    (CWPIR_OPT_SCALE_EXACT = 1): products and a selection entry equal the
+    oracle's, and the default again afterwards."""
+    from paper_2202_07569_gb300 import binding as B
+
+    cl = client(N, L)
+    st = syn.Stream(102, N + L)
+    a = syn.uniform_residues(st, cl.q, (2,), N)
+    b = syn.uniform_residues(st, cl.q, (2,), N)
+    want = cl.O.bfv_mul(a, b, cl.rlk)
+    cl.ctx.set_option(B.OPT_SCALE_EXACT, 1)
+    try:
+        assert cl.ctx.get_option(B.OPT_SCALE_EXACT) == 1
+        assert np.array_equal(cl.ctx.mul(a, b), want)
+        items, cw, _ = database(20, 16, T, 3, 8, seed=9)
+        db = cl.ctx.load_db(items, cw, 8)
+        query = cl.query(cw[5], 8, 0, stream=7)
+        got = cl.ctx.selection(db, query, np.array([5, 11], np.uint64))
+        for i, r in enumerate((5, 11)):
+            assert np.array_equal(got[i], cl.O.selection(query, cw[r], cl.rlk)), r
+        cl.ctx.free_db(db)
+    finally:
+        cl.ctx.set_option(B.OPT_SCALE_EXACT, 0)
+    assert np.array_equal(cl.ctx.mul(a, b), want)
+
+
 def test_mul_edge_coefficients():
     """Coefficients at 0, 1, Q-1 and next to Q/2 (mixed-radix branch)."""
     import math

@@ -22,22 +22,28 @@ def centered(x, M):
 
 def _ext_primes(N, L, q):
     """The library's extension primes: 30-bit, = 1 mod 2N, with product
-    above 2^17 t N Q (the scale-down's bound)."""
+    at least 2 N Q^2 (the tensor alone) and above 2^17 t N Q (the exact
+    scale-down's bound)."""
     k = emu.lib().emu_ext_count(L)
     p = np.zeros(k, np.uint64)
     emu.lib().emu_ext_primes(N, L, np.array(q, np.uint64), p)
     p = [int(v) for v in p]
     assert all((1 << 29) < v < (1 << 30) and v % (2 * N) == 1 for v in p)
     assert math.prod(p) > (1 << 17) * T * N * math.prod(q)
+    assert math.prod(p) >= 2 * N * math.prod(q) ** 2
     return p
 
 
 @pytest.mark.parametrize("L", range(1, 9))
 def test_extension_basis_covers_every_accepted_parameter_set(L):
-    """The scale-down is exact while P > 2^17 t N Q.  The library accepts
-    t < 2^20, N <= 16384 and ciphertext primes below 2^54, so the K(L)
-    extension primes must exceed 2^17 2^20 N 2^(54 L) at every N, and be
-    distinct 30-bit primes = 1 mod 2N."""
+    """The tensor of two centered lifts is at most N Q^2 / 2 in magnitude,
+    so the extension basis alone holds it exactly, with v read by rounding,
+    while P >= 2 N Q^2; the exact scale-down needs P > 2^17 t N Q.  The
+    library accepts t < 2^20, N <= 16384 and ciphertext primes below 2^54,
+    so the K(L) extension primes must exceed 2 N 2^(108 L) and
+    2^17 2^20 N 2^(54 L) at every N, and be distinct 30-bit primes = 1 mod
+    2N; one prime fewer must not reach the first bound at N = 16384 (K is
+    the smallest such count)."""
     k = emu.lib().emu_ext_count(L)
     for logn in range(10, 15):
         N = 1 << logn
@@ -49,6 +55,9 @@ def test_extension_basis_covers_every_accepted_parameter_set(L):
             assert (1 << 29) < v < (1 << 30) and v % (2 * N) == 1
             assert all(v % d for d in range(3, 1 << 15, 2)), v
         assert math.prod(p) > 1 << (17 + 20 + logn + 54 * L), (N, L)
+        assert math.prod(p) >= 1 << (1 + logn + 108 * L), (N, L)
+        if logn == 14:
+            assert math.prod(p[:-1]) < 1 << (1 + logn + 108 * L), (N, L)
 
 
 @pytest.mark.parametrize("L", range(1, 9))
@@ -75,13 +84,17 @@ def _setup(orc, N, L, seed=3):
 
 
 @pytest.mark.parametrize("N,L", [(1024, 1), (1024, 3), (4096, 2), (8192, 4)])
-def test_emulated_multiplication_matches_oracle(orc, N, L):
+@pytest.mark.parametrize("force_exact", [0, 1])
+def test_emulated_multiplication_matches_oracle(orc, N, L, force_exact):
+    """The kernels' multiplication (tensor on the extension limbs alone,
+    scale-down from them, key switch) equals the oracle's; with force_exact
+    every scale-down coefficient takes the exact path instead."""
     q, O, cd, rlk = _setup(orc, N, L)
     st = syn.Stream(5, N + L)
     a = syn.uniform_residues(st, q, (2,), N)
     b = syn.uniform_residues(st, q, (2,), N)
     out = np.zeros((2, L, N), np.uint64)
-    bad = emu.lib().emu_bfv_mul(N, L, q, T, np.ascontiguousarray(rlk), a, b, out)
+    bad = emu.lib().emu_bfv_mul(N, L, q, T, np.ascontiguousarray(rlk), a, b, out, force_exact)
     assert bad == 0
     assert np.array_equal(out, O.bfv_mul(a, b, rlk))
 
@@ -92,7 +105,7 @@ def test_emulated_multiplication_matches_oracle_n16384(orc):
     a = syn.uniform_residues(st, q, (2,), 16384)
     b = syn.uniform_residues(st, q, (2,), 16384)
     out = np.zeros((2, 7, 16384), np.uint64)
-    assert emu.lib().emu_bfv_mul(16384, 7, q, T, np.ascontiguousarray(rlk), a, b, out) == 0
+    assert emu.lib().emu_bfv_mul(16384, 7, q, T, np.ascontiguousarray(rlk), a, b, out, 0) == 0
     assert np.array_equal(out, O.bfv_mul(a, b, rlk))
 
 
@@ -146,6 +159,45 @@ def test_exact_scale_down(orc, N, L):
         assert [int(v) for v in out] == [want % v for v in q], d
 
 
+@pytest.mark.parametrize("N,L", [(1024, 1), (2048, 3), (8192, 4), (16384, 7), (16384, 8)])
+def test_scale_down_from_the_extension_basis(orc, N, L):
+    """round(t d / Q) mod q_j from the residues of N d modulo the extension
+    primes alone.  Extreme d, random d, and d whose t d / Q lies within
+    t / Q of a half integer (the fast path must hand those to the exact
+    path); each through the fast path with its hand-over and, separately,
+    through the exact path alone, against exact integers."""
+    q = [int(v) for v in orc.primes(N, L)]
+    Q = math.prod(q)
+    p = _ext_primes(N, L, q)
+    K = len(p)
+    dmax = N * Q * Q // 2
+    ds = [0, 1, -1, dmax, -dmax, dmax - 1, 1 - dmax]
+    st = syn.Stream(9)
+    ties = []
+    for w in st.words(12).tolist():
+        n = (int(w) * (T * dmax // Q)) >> 64  # t d / Q next to n + 1/2
+        base = ((2 * n + 1) * Q) // (2 * T)
+        for d in (base - 1, base, base + 1, -base, -base - 1):
+            if abs(d) <= dmax:
+                ties.append(len(ds))
+                ds.append(d)
+    for w in st.words(60).tolist():
+        ds.append(((int(w) * 2 * dmax) >> 64) - dmax)
+    # lazy residues as the tensor kernel leaves them: [0, 2p)
+    dp = np.array([[(N * d) % v + (i + k) % 2 * v for k, v in enumerate(p)]
+                   for i, d in enumerate(ds)], np.uint32)
+    want = [[((T * d + Q // 2) // Q) % v for v in q] for d in ds]
+    qa = np.array(q, np.uint64)
+    for force in (0, 1):
+        out = np.zeros((len(ds), L), np.uint64)
+        path = np.zeros(len(ds), np.int32)
+        emu.lib().emu_scale_p(N, L, qa, T, len(ds), dp, out, force, path)
+        assert [[int(v) for v in row] for row in out] == want
+        assert set(path.tolist()) <= ({0, 1} if not force else {1})
+        if not force:
+            assert all(path[i] == 1 for i in ties)
+            assert (path[len(ds) - 60:] == 0).all()
+
 def test_reduction_below_2_62(orc):
     """The 32-bit reduction of sums below 2^62 modulo a 30-bit extension
     prime: values at 0, 2^62 - 1, next to multiples of p and of 2^32, and
@@ -189,12 +241,9 @@ def test_row_basis_crt(orc, N, L, nr):
 
 
 def test_tensor_inverse_schedules(orc):
-    """The tensor kernels' inverse transforms at N = 8192: the 54-bit one with
-    the approximate Shoup quotient (values below 4q, three of the four
-    partial products of the quotient) leaves N times the stage-by-stage
-    inverse in [0, 2q) for every ciphertext prime, from lazy inputs below
-    4q; the 32-bit one that runs three outputs in lock-step equals three
-    single transforms for every extension prime."""
+    """The tensor kernel's inverse transforms at N = 8192: the 32-bit
+    schedule that runs the three outputs in lock-step equals three single
+    transforms for every extension prime."""
     q = orc.primes(8192, 4)
     data = syn.Stream(13).words(8192)
     assert emu.lib().emu_tensor_intt_compare(4, np.array(q, np.uint64), T, data) == 0
