@@ -163,6 +163,8 @@ def imad_per_job(kind: str, m54: float, m30: float) -> float:
 # jobs of a launch, so a full launch's traffic is this figure times its
 # jobs.
 DRAM_BYTES_PER_JOB = {
+    "tensor_intt": (79725824 + 131447552) / 128,  # k_tensor_ext, K = 15
+    "scale": (188808704 + 70000384) / 128,
     # per-job kernels of the row-basis key switch (k_rows_ntt, k_rows_mac);
     # the once-per-row-group conversions are left out
     "relin_pm": (108978176 + 100567296 + 163604480 + 25714944) / 128,
