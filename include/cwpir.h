@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define CWPIR_ABI_VERSION 3
+#define CWPIR_ABI_VERSION 4
 /* Largest number of plaintexts per database row (payload_len <= this * N). */
 #define CWPIR_MAX_PLAINTEXTS 256
 
@@ -363,7 +363,7 @@ enum {
   CWPIR_OPT_MEM_LIMIT = 7,
   /* row sums of the last tree level: split into row groups until about
    * this many waves of the device's resident threads cover it (0 = the
-   * default, 4); drops the cached plans.  Response bits are unchanged. */
+   * default, 2); drops the cached plans.  Response bits are unchanged. */
   CWPIR_OPT_ROW_GROUP_WAVES = 8,
   /* 0 (default): the scale-down after each multiplication rounds t d / Q
    * with a fixed-point sum and hands the rare coefficients it cannot decide
@@ -541,14 +541,19 @@ int cwpir_last_stats(const cwpir_ctx *ctx, cwpir_stats *out);
 
 /* Kernel classes of the answer path, for cwpir_kernel_times. */
 enum {
-  CWPIR_K_TENSOR = 0,  /* tensor product + inverse NTT */
-  CWPIR_K_SCALE = 1,   /* exact scale-down round(t d / Q) */
-  CWPIR_K_RELIN = 2,   /* key switching fused with plain multiplication */
-  CWPIR_K_LIFT = 3,    /* centered base conversion Q -> P */
-  CWPIR_K_NTT = 4,     /* stand-alone NTTs */
-  CWPIR_K_ACC = 5,     /* accumulation of partial products */
-  CWPIR_K_EXPAND = 6,  /* automorphisms, substitution key switches, combine */
-  CWPIR_K_CLASSES = 7
+  CWPIR_K_TENSOR = 0,  /* tensor product + inverse NTT ("tensor") */
+  CWPIR_K_SCALE = 1,   /* exact scale-down round(t d / Q) ("scale") */
+  CWPIR_K_RELIN = 2,   /* key switching fused with plain multiplication
+                          ("relin_pm"; on a row-basis database: the row sums
+                          and the once-per-group conversions) */
+  CWPIR_K_LIFT = 3,    /* centered base conversion Q -> P ("lift") */
+  CWPIR_K_NTT = 4,     /* stand-alone NTTs ("ntt") */
+  CWPIR_K_ACC = 5,     /* accumulation of partial products ("accumulate") */
+  CWPIR_K_EXPAND = 6,  /* automorphisms, substitution key switches, combine
+                          ("expand") */
+  CWPIR_K_ROWS = 7,    /* the row transforms of the last tree level on a
+                          row-basis database ("row_ntt") */
+  CWPIR_K_CLASSES = 8
 };
 /* With CWPIR_OPT_KERNEL_TIMING on: waits for the recorded work, then writes
  * per class the summed milliseconds (ms) and launch counts (launches),

@@ -30,7 +30,7 @@ OPT_ROW_BASIS = 6
 OPT_MEM_LIMIT = 7
 OPT_ROW_GROUP_WAVES = 8
 OPT_SCALE_EXACT = 9
-K_CLASSES = 7
+K_CLASSES = 8
 EINTERNAL = -8
 
 

@@ -398,7 +398,7 @@ u64 dnq_words(u64 L, u64 N) { return (u64)kRowGroups * (L + 2) * L * N; }
 u32 jobs_per_launch(const cwpir_ctx *c) {
   const u64 N = c->N, L = c->L;
   const u64 per_job =
-      (3 * c->qp_poly() + (3 * L + 2 * L) * N + dn_words(L, N)) * sizeof(u64);
+      (3 * cw::tensor_poly_words(c->K, c->N) + (3 * L + 2 * L) * N + dn_words(L, N)) * sizeof(u64);
   u64 j = kScratchBytes / per_job;
   j = std::max<u64>(32, std::min<u64>(kMaxJobs, j));
   if (c->opt_max_jobs) j = std::min<u64>(j, c->opt_max_jobs);
@@ -434,7 +434,7 @@ int ensure_scratch(cwpir_ctx *c, u32 slot = 0) {
   Scratch &S = *c->slots[slot];
   if (!c->jmax) c->jmax = jobs_per_launch(c);
   const u64 N = c->N, L = c->L, j = c->jmax;
-  CUDA_TRY(c, S.Tbuf.ensure(j * 3 * c->qp_poly(), &c->acct));
+  CUDA_TRY(c, S.Tbuf.ensure(j * 3 * cw::tensor_poly_words(c->K, c->N), &c->acct));
   CUDA_TRY(c, S.E.ensure(j * 3 * L * N, &c->acct));
   CUDA_TRY(c, S.CP.ensure(j * 2 * L * N, &c->acct));
   CUDA_TRY(c, S.DN.ensure(j * dn_words(L, N), &c->acct));
@@ -682,6 +682,11 @@ int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp
     c->stats.ntt_polys += (u64)ch.count * (3 * c->K + 3 * c->L * cw::kKsrPrimes + 2 * c->K);
     return CWPIR_OK;
   }
+  if (rows)
+    CUDA_TRY(c, timed(c, CWPIR_K_ROWS, st, [&] {
+      return cw::launch_rows_transforms(c->d_tab, c->h, S.E.p, ch.count,
+                                        reinterpret_cast<u32 *>(S.DN.p), st);
+    }));
   CUDA_TRY(c, timed(c, CWPIR_K_RELIN, st, [&] {
     if (rows)
       return cw::launch_relin_rows(c->d_tab, c->h, S.E.p, ch.count, ch.segs, jobs, c->rlk.p,
@@ -1721,7 +1726,7 @@ int cwpir_plan_bytes_slot(cwpir_ctx *c, uint32_t slot, int32_t db_id, uint32_t n
   const Scratch &S = *c->slots[slot];
   u64 w = 0;
   if (!S.Tbuf.n) {  // the slot's scratch comes first
-    const u64 per_job = 3 * c->qp_poly() + (3 * L + 2 * L) * N + dn_words(L, N);
+    const u64 per_job = 3 * cw::tensor_poly_words(c->K, c->N) + (3 * L + 2 * L) * N + dn_words(L, N);
     w += J * per_job + rs_words(L, N) + dnq_words(L, N);
   }
   const u32 top = [&] { u32 l = 0; while ((1u << l) < db->k) ++l; return l; }();
@@ -1869,8 +1874,8 @@ int cwpir_kernel_times(cwpir_ctx *c, double *ms, uint64_t *launches) {
 }
 
 const char *cwpir_kernel_class_name(int cls) {
-  static const char *names[CWPIR_K_CLASSES] = {"tensor_intt", "scale", "relin_pm", "lift",
-                                                "ntt", "accumulate", "expand"};
+  static const char *names[CWPIR_K_CLASSES] = {"tensor", "scale", "relin_pm", "lift",
+                                                "ntt", "accumulate", "expand", "row_ntt"};
   return (cls >= 0 && cls < CWPIR_K_CLASSES) ? names[cls] : "unknown";
 }
 

@@ -6,8 +6,8 @@
 //   QP-NTT ciphertext        [2] polynomials in QP layout (kernels.cuh): L limbs
 //                            of u64, then K limbs of u32; NTT form
 //   database                 [rows][L][N] NTT form (centered plaintext lift)
-//   tensor buffer  Tbuf      [jobs][3] QP-layout polynomials N d0, N d1, N d2
-//                            (lazy residues)
+//   tensor buffer  Tbuf      [jobs][3][K][N] u32: N d0, N d1, N d2 modulo the
+//                            extension primes (lazy residues)
 //   scaled buffer  E         [jobs][3][L][N]   round(t d / Q) mod q_j
 //   partials       P         [jobs][2][L][N]   NTT-form sel * DB rows
 //
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
   const u32 L = T->L, k = blockIdx.y, t = threadIdx.x;
   const u64 job = blockIdx.x;
   const MulJob J = jobs[job];
-  const u64 ps = qp_poly_words(L, T->K, N);
+  const u64 ps = qp_poly_words(L, T->K, N), ts = 2 * tensor_poly_words(T->K, N);
   const ExtNtt E = T->ext[k];
   const u32 p2 = 2 * E.e.p;
   const u32 *a0 = ext_limb(J.a, L, N, k), *a1 = ext_limb(J.a + ps, L, N, k);
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    u32 *out = ext_limb(Tbuf + (job * 3 + i) * ps, L, N, k);
+    u32 *out = reinterpret_cast<u32 *>(Tbuf) + (job * 3 + i) * ts + (u64)k * N;
 #pragma unroll
     for (u32 r = 0; r < R; ++r) out[strided_idx32<LOGN>(t, r)] = y[i * R + r];
   }
@@ -405,12 +405,12 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
 // the exact path for coefficient c of the polynomial at `in`, out of line:
 // it reloads its residues, so that nothing of the caller's stays live
 template <int L>
-__device__ __noinline__ bool scale_exact_at(const DevTables *T, const u64 *in, u64 *out, u32 c) {
+__device__ __noinline__ bool scale_exact_at(const DevTables *T, const u32 *in, u64 *out, u32 c) {
   constexpr int K = ext_count(L);
   const u32 N = T->N;
   u32 dp[K];
   u64 e[L];
-  for (int k = 0; k < K; ++k) dp[k] = ext_limb(in, L, N, k)[c];
+  for (int k = 0; k < K; ++k) dp[k] = in[(u64)k * N + c];
   const bool ok = scale_exact<L>(dp, e, T->scalep, T->scale);
   for (int j = 0; j < L; ++j) out[(u64)j * N + c] = e[j];
   return ok;
@@ -423,12 +423,12 @@ __global__ void k_scale(const DevTables *T, const u64 *Tbuf, u64 *E, int *err,
   const u32 N = T->N;
   const u32 c = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 jw = blockIdx.y;
-  const u64 *in = Tbuf + jw * qp_poly_words(L, K, N);
+  const u32 *in = reinterpret_cast<const u32 *>(Tbuf) + jw * K * N;
   u64 *out = E + jw * L * N;
   u32 dp[K];
   u64 e[L];
 #pragma unroll
-  for (int k = 0; k < K; ++k) dp[k] = ext_limb(in, L, N, k)[c];
+  for (int k = 0; k < K; ++k) dp[k] = in[(u64)k * N + c];
   const int r = scale_fast<L>(dp, e, S);
   if (r == 0) {
 #pragma unroll
@@ -1386,6 +1386,12 @@ cudaError_t launch_ksr_key(const DevTables *T, const DevTables &h, const u64 *ke
 }
 
 
+cudaError_t launch_rows_transforms(const DevTables *T, const DevTables &h, const u64 *E,
+                                   u32 njobs, u32 *D, cudaStream_t st) {
+  if (!njobs) return cudaSuccess;
+  return rows_ntt(T, h, E, 3 * h.L, njobs, D, st);
+}
+
 cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                               u32 segs, const MulJob *jobs, const u64 *rlk, const u64 *rlk_s,
                               const u32 *dbr, u32 gcap, u32 *D, u32 *S, u64 *DNQ, int *err,
@@ -1393,8 +1399,7 @@ cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 
   if (!njobs) return cudaSuccess;
   const u32 L = h.L, nl = 3 * L, N = h.N;
   const u64 LN = (u64)L * N, unit = (u64)(L + 2) * LN;
-  cudaError_t e = rows_ntt(T, h, E, nl, njobs, D, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   const u32 seg_len = njobs / segs, G = relin_rows_groups(h, segs, seg_len, gcap);
   const u32 spp = G >= gcap ? 1 : gcap / G;  // segments per pass
   for (u32 s0 = 0; s0 < segs; s0 += spp) {

@@ -16,7 +16,7 @@ struct ExtNtt {
 
 // Row-sum waves: the row sums of the last tree level are split into row
 // groups until about this many waves of resident threads cover the device.
-constexpr u32 kDefaultRowWaves = 4;
+constexpr u32 kDefaultRowWaves = 2;
 
 // All per-context constants the kernels read, in device memory.  sms,
 // sm_threads (read from the device at setup) and row_waves size launch
@@ -40,9 +40,12 @@ constexpr u32 kKsrPrimes = 5;
 
 // QP layout of one polynomial (NTT domain or, for the tensor buffer,
 // coefficients): L limbs of N u64 residues mod q_j, then K limbs of N u32
-// residues mod the 30-bit p_k; L N + K N / 2 u64 words in all.  The
-// tensor buffer uses the K limbs alone.
+// residues mod the 30-bit p_k; L N + K N / 2 u64 words in all.
 CW_HD u64 qp_poly_words(u32 L, u32 K, u32 N) { return (u64)L * N + (u64)K * N / 2; }
+// The tensor buffer: per job three polynomials (N d0, N d1, N d2) of K
+// limbs of N u32 residues modulo the extension primes, K N / 2 u64 words
+// each.
+CW_HD u64 tensor_poly_words(u32 K, u32 N) { return (u64)K * N / 2; }
 CW_HD u32 *ext_limb(u64 *poly, u32 L, u32 N, u32 k) {
   return reinterpret_cast<u32 *>(poly + (u64)L * N) + (u64)k * N;
 }
@@ -112,14 +115,20 @@ u32 relin_pm_groups(const DevTables &h, u32 segs, u32 seg_len, u32 sp, u32 cap);
 u32 relin_rows_groups(const DevTables &h, u32 segs, u32 seg_len, u32 gcap);
 cudaError_t launch_db_load_rows(const DevTables *T, const DevTables &h, const u32 *items,
                                 u64 rows, u32 plen, u32 *dbr, cudaStream_t st);
-// Relinearisation of the scaled tensor E ([njobs][3][L][N]) with the plain
-// multiplication by the rows of a row-basis database, summed over row
-// groups: the limbs of e0, e1 and the digits of e2 are multiplied with the
-// rows exactly in the row basis, summed, brought back to the ciphertext
-// primes and multiplied by the key once per group.  The jobs form `segs`
-// segments (one per query); out = partials [segs * G][2][L][N], NTT form,
-// G = relin_rows_groups(h, segs, njobs / segs, gcap) <= gcap.  Scratch: D
-// [njobs][3L][nr][N] u32; S [gcap][3L][nr][N] u32; DNQ [gcap][L+2][L][N].
+// The row transforms of the scaled tensor E ([njobs][3][L][N]): the limbs
+// of e0, e1 and the digits of e2 (the limbs of e2) reduced modulo each row
+// prime and transformed, D = [njobs][3L][nr][N] u32 (NTT form).
+cudaError_t launch_rows_transforms(const DevTables *T, const DevTables &h, const u64 *E,
+                                   u32 njobs, u32 *D, cudaStream_t st);
+// Relinearisation of the scaled tensor with the plain multiplication by the
+// rows of a row-basis database, summed over row groups, from its row
+// transforms D (launch_rows_transforms of the same jobs): the transforms
+// are multiplied with the rows exactly in the row basis, summed, brought
+// back to the ciphertext primes and multiplied by the key once per group.
+// The jobs form `segs` segments (one per query); out = partials
+// [segs * G][2][L][N], NTT form, G = relin_rows_groups(h, segs, njobs /
+// segs, gcap) <= gcap.  Scratch: S [gcap][3L][nr][N] u32; DNQ
+// [gcap][L+2][L][N].  E is not read.
 cudaError_t launch_relin_rows(const DevTables *T, const DevTables &h, const u64 *E, u32 njobs,
                               u32 segs, const MulJob *jobs, const u64 *rlk, const u64 *rlk_s,
                               const u32 *dbr, u32 gcap, u32 *D, u32 *S, u64 *DNQ, int *err,

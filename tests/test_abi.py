@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(cudalib):
 def test_host_helpers_match_definitions(cudalib, orc):
     from paper_2202_07569_gb300 import binding as B
 
-    assert B.abi_version() == 3
+    assert B.abi_version() == 4
     for N, L in ((4096, 2), (8192, 4), (16384, 7)):
         assert B.default_primes(N, L).tolist() == orc.primes(N, L).tolist()
     for m, k in ((24, 2), (10, 4), (12, 5)):
