@@ -33,8 +33,11 @@ def client(N, L, seed=3, c_max=0):
 
 
 # ------------------------------------------------------------ multiplication
-@pytest.mark.parametrize("N,L", [(1024, 1), (4096, 2), (8192, 4), (16384, 7)])
+@pytest.mark.parametrize("N,L", [(1024, 1), (4096, 2), (2048, 3), (8192, 4), (4096, 5),
+                                 (4096, 6), (16384, 7), (4096, 8)])
 def test_mul_matches_oracle(N, L):
+    """M for every count of ciphertext primes (extension bases of 5 to 30
+    primes, each scale-down instantiation) against the oracle."""
     cl = client(N, L)
     st = syn.Stream(100, N + L)
     for trial in range(2):
