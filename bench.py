@@ -589,7 +589,9 @@ def run_arith(args):
     batch-encoded operands (Sec. 4, Table arith-eq): N = 16384, L = 7,
     (n, k, m) = (2^16, 8, 19) and (2^32, 16, 36), the rows k = log2(n)/2 of
     the paper's table; one evaluation compares N pairs slot-wise.  Host
-    buffers in and out (end to end through cwpir_arith_cw_eq)."""
+    buffers in (pinned) and out, end to end through cwpir_arith_cw_eq."""
+    import torch
+
     from paper_2202_07569_gb300 import binding as B
     from paper_2202_07569_gb300 import synthetic as syn
 
@@ -599,8 +601,8 @@ def run_arith(args):
     ctx = B.Context(N, q, 65537, rlk)
     runs = []
     for logn, k, m in ((16, 8, 19), (32, 16, 36)):
-        x = syn.uniform_ciphertexts(82, q, m, N)
-        y = syn.uniform_ciphertexts(83, q, m, N)
+        x = torch.from_numpy(syn.uniform_ciphertexts(82, q, m, N)).pin_memory().numpy()
+        y = torch.from_numpy(syn.uniform_ciphertexts(83, q, m, N)).pin_memory().numpy()
         for _ in range(args.warmup):
             ctx.arith_cw_eq(m, k, x, y)
         ts = []

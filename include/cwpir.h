@@ -321,7 +321,11 @@ int cwpir_selection(cwpir_ctx *ctx, int32_t db_id, uint32_t c,
  * (ciphertext i holds bit i of the codewords), out: [2][L][N] =
  * (1/k!) prod_{i<k} (sum_j x_j y_j - i), which decrypts to 1 where the
  * codewords agree and 0 elsewhere; m + k - 1 multiplications, depth
- * 1 + ceil(log2 k).  1 <= k <= 16, k <= m <= 8192.  Host buffers.
+ * 1 + ceil(log2 k).  1 <= k <= 16, k <= m <= 8192.  Host buffers (pinned
+ * ones copy fastest).  The residues are checked on the device (EINVAL once
+ * the call has run).  The call keeps its device buffers and product plans
+ * for the next call with the same (m, k), until cwpir_release_plans(ctx,
+ * -1) or an option change that drops the answer plans.
  * EINVAL, ENOMEM, ECUDA, EINTERNAL. */
 int cwpir_arith_cw_eq(cwpir_ctx *ctx, uint32_t m, uint32_t k, const uint64_t *x,
                       const uint64_t *y, uint64_t *out);

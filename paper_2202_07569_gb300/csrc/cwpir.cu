@@ -195,6 +195,19 @@ struct cwpir_ctx {
   std::vector<std::unique_ptr<Scratch>> slots;
   // buffers of the single-step host calls
   DevBuf exp_tau, exp_DN, exp_O, tmp_ct, io_in, io_out, one_job;
+  // the arithmetic operator's operands, intermediates and plans, kept for
+  // the next call with the same (m, k); dropped with the answer plans
+  struct ArithCache {
+    u32 m = 0, k = 0;
+    DevBuf leaves, prods, fac, flag;
+    Db d1, d2;
+    std::unique_ptr<Plan> p1, p2;
+    void clear() {
+      p1.reset();
+      p2.reset();
+      m = k = 0;
+    }
+  } arith;
   bool capturing = false;
   // serialises the slot calls, which several threads may make on one context
   std::recursive_mutex mu;
@@ -1566,21 +1579,24 @@ int cwpir_selection(cwpir_ctx *c, int32_t db_id, uint32_t cfac, const uint64_t *
   return check_err_flag(c);
 }
 
-// Selection entries (coefficient form, [rows][2][L][N] at out) of the rows
-// of a database description d over the coefficient-form leaves `coef`
-// ([d.m][2][L][N]); the plan and its scratch are temporary.
-static int product_rows(cwpir_ctx *c, Db &d, const u64 *coef, u64 *out) {
+// The plan of the selection entries (coefficient form, [rows][2][L][N] at
+// out) of every row of a database description d, kept by the caller: its
+// jobs point into its own buffers and at out.
+static int rows_plan(cwpir_ctx *c, Db &d, u64 *out, std::unique_ptr<Plan> &P) {
   std::vector<u64> rv(d.n);
   for (u64 i = 0; i < d.n; ++i) rv[i] = i;
-  std::unique_ptr<Plan> P;
-  int rc = build_plan(c, 0, &d, rv, 1, 0, cw::ROOT_SEL, out, false, P);
+  return build_plan(c, 0, &d, rv, 1, 0, cw::ROOT_SEL, out, false, P);
+}
+
+// Enqueues the plan's products over the coefficient-form leaves `coef`
+// ([d.m][2][L][N]).
+static int run_rows_plan(cwpir_ctx *c, Db &d, Plan *P, const u64 *coef) {
+  int rc = prep_leaves(c, coef, d.m, P->leaves.p, c->stream);
   if (rc) return rc;
-  if ((rc = prep_leaves(c, coef, d.m, P->leaves.p, c->stream))) return rc;
   for (const auto &batch : P->batches)
     for (const Chunk &ch : batch)
-      if ((rc = run_chunk(c, *c->slots[0], P.get(), ch, nullptr, c->stream))) return rc;
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return check_err_flag(c);
+      if ((rc = run_chunk(c, *c->slots[0], P, ch, nullptr, c->stream))) return rc;
+  return CWPIR_OK;
 }
 
 int cwpir_arith_cw_eq(cwpir_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
@@ -1591,46 +1607,56 @@ int cwpir_arith_cw_eq(cwpir_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
   if (!x || !y || !out) return fail(c, CWPIR_EINVAL, "null buffer");
   if (k < 1 || k > 16 || k > m || m > 8192)
     return fail(c, CWPIR_EINVAL, "need 1 <= k <= 16, k <= m <= 8192");
-  if (!valid_residues(x, c->L, c->N, c->q, 2ull * m) ||
-      !valid_residues(y, c->L, c->N, c->q, 2ull * m))
-    return fail(c, CWPIR_EINVAL, "residue out of range");
   int rc = ensure_scratch(c);
   if (rc) return rc;
   const u64 ctw = c->ct();
   // leaves x_0 .. x_{m-1}, y_0 .. y_{m-1}; then m products, their sum, the
   // k factors and their product
-  DevBuf leaves, prods, fac;
-  CUDA_TRY(c, leaves.ensure(2ull * m * ctw, &c->acct));
-  CUDA_TRY(c, prods.ensure((u64)m * ctw, &c->acct));
-  CUDA_TRY(c, fac.ensure((u64)(k + 2) * ctw, &c->acct));
-  CUDA_TRY(c, cudaMemcpyAsync(leaves.p, x, (u64)m * ctw * sizeof(u64), cudaMemcpyHostToDevice,
-                              c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(leaves.p + (u64)m * ctw, y, (u64)m * ctw * sizeof(u64),
-                              cudaMemcpyHostToDevice, c->stream));
-  // k' = sum_i x_i y_i: rows i with codewords {i, m + i}
-  Db d1;
-  d1.n = m;
-  d1.k = 2;
-  d1.m = 2 * m;
-  d1.cw.resize(2ull * m);
-  for (u32 i = 0; i < m; ++i) {
-    d1.cw[2 * i] = (uint16_t)i;
-    d1.cw[2 * i + 1] = (uint16_t)(m + i);
+  auto &A = c->arith;
+  if (A.m != m || A.k != k) {
+    A.clear();
+    CUDA_TRY(c, A.leaves.ensure(2ull * m * ctw, &c->acct));
+    CUDA_TRY(c, A.prods.ensure((u64)m * ctw, &c->acct));
+    CUDA_TRY(c, A.fac.ensure((u64)(k + 2) * ctw, &c->acct));
+    CUDA_TRY(c, A.flag.ensure(1, &c->acct));
+    // k' = sum_i x_i y_i: rows i with codewords {i, m + i}
+    A.d1.n = m;
+    A.d1.k = 2;
+    A.d1.m = 2 * m;
+    A.d1.cw.resize(2ull * m);
+    for (u32 i = 0; i < m; ++i) {
+      A.d1.cw[2 * i] = (uint16_t)i;
+      A.d1.cw[2 * i + 1] = (uint16_t)(m + i);
+    }
+    if ((rc = rows_plan(c, A.d1, A.prods.p, A.p1))) return rc;
+    if (k > 1) {  // the product of the k factors by the balanced tree
+      A.d2.n = 1;
+      A.d2.k = k;
+      A.d2.m = k;
+      A.d2.cw.resize(k);
+      for (u32 i = 0; i < k; ++i) A.d2.cw[i] = (uint16_t)i;
+      if ((rc = rows_plan(c, A.d2, A.fac.p + (u64)(k + 1) * ctw, A.p2))) return rc;
+    }
+    A.m = m;
+    A.k = k;
   }
-  if ((rc = product_rows(c, d1, leaves.p, prods.p))) return rc;
-  u64 *kp = fac.p + (u64)k * ctw, *res = fac.p + (u64)(k + 1) * ctw;
-  CUDA_TRY(c, cw::launch_ct_sum(c->d_tab, c->h, prods.p, m, c->ct(), kp, c->stream));
-  // factors k' - i, i < k, and their product by the balanced tree
-  CUDA_TRY(c, cw::launch_minus_consts(c->d_tab, c->h, kp, k, fac.p, c->stream));
-  const u64 *prod = fac.p;
+  CUDA_TRY(c, cudaMemcpyAsync(A.leaves.p, x, (u64)m * ctw * sizeof(u64), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(A.leaves.p + (u64)m * ctw, y, (u64)m * ctw * sizeof(u64),
+                              cudaMemcpyHostToDevice, c->stream));
+  // the residue check runs on the device (the operands are large); its flag
+  // is read once the call has finished
+  int *flag = reinterpret_cast<int *>(A.flag.p);
+  CUDA_TRY(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  CUDA_TRY(c, cw::launch_check_residues(c->d_tab, c->h, A.leaves.p, 2ull * m, flag, c->stream));
+  if ((rc = run_rows_plan(c, A.d1, A.p1.get(), A.leaves.p))) return rc;
+  u64 *kp = A.fac.p + (u64)k * ctw, *res = A.fac.p + (u64)(k + 1) * ctw;
+  CUDA_TRY(c, cw::launch_ct_sum(c->d_tab, c->h, A.prods.p, m, c->ct(), kp, c->stream));
+  // factors k' - i, i < k, and their product
+  CUDA_TRY(c, cw::launch_minus_consts(c->d_tab, c->h, kp, k, A.fac.p, c->stream));
+  const u64 *prod = A.fac.p;
   if (k > 1) {
-    Db d2;
-    d2.n = 1;
-    d2.k = k;
-    d2.m = k;
-    d2.cw.resize(k);
-    for (u32 i = 0; i < k; ++i) d2.cw[i] = (uint16_t)i;
-    if ((rc = product_rows(c, d2, fac.p, res))) return rc;
+    if ((rc = run_rows_plan(c, A.d2, A.p2.get(), A.fac.p))) return rc;
     prod = res;
   }
   // times (k!)^-1 mod t
@@ -1639,8 +1665,11 @@ int cwpir_arith_cw_eq(cwpir_ctx *c, uint32_t m, uint32_t k, const uint64_t *x,
   const u64 s = hpow(kf, c->t - 2, c->t);
   CUDA_TRY(c, cw::launch_ct_scalar(c->d_tab, c->h, prod, s, kp, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(out, kp, ctw * sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  int bad = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return CWPIR_OK;
+  if (bad) return fail(c, CWPIR_EINVAL, "residue out of range");
+  return check_err_flag(c);
 }
 
 int cwpir_plain_mul(cwpir_ctx *c, int32_t db_id, uint64_t row, const uint64_t *ct, uint64_t *out) {
@@ -1766,6 +1795,7 @@ int cwpir_release_plans(cwpir_ctx *c, int32_t db_id) {
   cudaDeviceSynchronize();
   if (db_id < 0) {
     for (auto &kv : c->dbs) kv.second->plans.clear();
+    c->arith.clear();
     return CWPIR_OK;
   }
   Db *db = get_db(c, db_id);
@@ -1781,6 +1811,7 @@ static void drop_plans(cwpir_ctx *c) {
   cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
   for (auto &kv : c->dbs) kv.second->plans.clear();
+  c->arith.clear();
 }
 
 int cwpir_set_option(cwpir_ctx *c, int option, int64_t value) {

@@ -1481,6 +1481,24 @@ cudaError_t launch_ct_scalar(const DevTables *T, const DevTables &h, const u64 *
   return cudaGetLastError();
 }
 
+// *flag |= 1 if any residue of ct[count][2][L][N] is not below its prime
+// q_j.  grid (N/256, min(rows, 65535)) over the 2 L count limb rows.
+__global__ void k_check_residues(const DevTables *T, const u64 *ct, u64 rows, int *flag) {
+  const u32 N = T->N, L = T->L, c = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  for (u64 r = blockIdx.y; r < rows; r += gridDim.y) bad |= ct[r * N + c] >= T->prime[r % L].q;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_check_residues(const DevTables *T, const DevTables &h, const u64 *ct,
+                                  u64 count, int *flag, cudaStream_t st) {
+  const u64 rows = 2ull * h.L * count;
+  if (!rows) return cudaSuccess;
+  k_check_residues<<<dim3(h.N / 256, (u32)(rows < 65535 ? rows : 65535)), 256, 0, st>>>(
+      T, ct, rows, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_automorph(const DevTables *T, const DevTables &h, const SubJob *jobs,
                              u32 njobs, u32 g, u64 *tau, cudaStream_t st) {
   if (!njobs) return cudaSuccess;

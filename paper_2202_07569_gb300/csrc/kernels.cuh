@@ -192,6 +192,10 @@ cudaError_t launch_ct_reduce(const DevTables *T, const DevTables &h, const u64 *
                              u64 *out, cudaStream_t st);
 cudaError_t launch_minus_consts(const DevTables *T, const DevTables &h, const u64 *in,
                                 u32 count, u64 *out, cudaStream_t st);
+// *flag |= 1 if a residue of ct [count][2][L][N] is not below its q_j (the
+// flag is not cleared here).
+cudaError_t launch_check_residues(const DevTables *T, const DevTables &h, const u64 *ct,
+                                  u64 count, int *flag, cudaStream_t st);
 cudaError_t launch_ct_scalar(const DevTables *T, const DevTables &h, const u64 *in, u64 s,
                              u64 *out, cudaStream_t st);
 cudaError_t launch_key_prep(const DevTables *T, const DevTables &h, u64 *key, u64 *key_s,

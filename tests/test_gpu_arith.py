@@ -62,4 +62,17 @@ def test_arith_operator_bit_exact(N, L, m, k):
     with pytest.raises(B.CwpirError) as ei:
         ctx.arith_cw_eq(m, m + 1, x, y)
     assert ei.value.code == -1
+    # a second call with the same (m, k) reuses the kept buffers and plans;
+    # other operands, and the swapped operands
+    x2 = syn.uniform_ciphertexts(261 + k, cl.q, m, N)
+    assert np.array_equal(ctx.arith_cw_eq(m, k, x2, y), cl.O.arith_cw_eq(m, k, x2, y, cl.rlk))
+    assert np.array_equal(ctx.arith_cw_eq(m, k, y, x2), cl.O.arith_cw_eq(m, k, y, x2, cl.rlk))
+    # a residue at q_j (checked on the device) is rejected, and the next
+    # call is unaffected
+    bad = y.copy()
+    bad[m - 1, 1, L - 1, N - 1] = cl.q[L - 1]
+    with pytest.raises(B.CwpirError) as ei:
+        ctx.arith_cw_eq(m, k, x, bad)
+    assert ei.value.code == -1
+    assert np.array_equal(ctx.arith_cw_eq(m, k, x, y), cl.O.arith_cw_eq(m, k, x, y, cl.rlk))
     ctx.close()
