@@ -241,9 +241,10 @@ def run_gpu(args, rank: int, world: int, dist, keep: bool = False):
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
 
-    # end to end through the host-buffer call (H2D of the query, D2H of the
-    # response inside the timed region)
+    # end to end through the host-buffer call (H2D of the query from pinned
+    # host memory, D2H of the response inside the timed region)
     resp = np.zeros((2, WL["L"], WL["N"]), np.uint64)
+    query = torch.from_numpy(query).pin_memory().numpy()
     ctx.answer(db, query)
     e2e = []
     for _ in range(max(1, min(args.steps, 3))):
@@ -434,9 +435,10 @@ def run_large(args):
         kt = ctx.kernel_times()
         ctx.set_option(B.OPT_KERNEL_TIMING, 0)
         e2e = []
+        h_query = torch.from_numpy(query).pin_memory().numpy()  # pinned host memory
         for _ in range(max(1, min(args.steps, 3))):
             t = time.perf_counter()
-            resp = ctx.answer(db, query)
+            resp = ctx.answer(db, h_query)
             e2e.append(time.perf_counter() - t)
         mb = n * sp * N * 2 / 1e6
         kernels = {kk: {"ms": v[0] / args.steps, "launches": v[1] // max(1, args.steps)}

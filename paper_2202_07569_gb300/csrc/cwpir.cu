@@ -674,7 +674,7 @@ int run_chunk(cwpir_ctx *c, Scratch &S, Plan *P, const Chunk &ch, const u64 *dbp
     c->stats.db_bytes_read += (u64)ch.count * P->sp * c->L * c->N * sizeof(u64);
     return CWPIR_OK;
   }
-  CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor_intt(c->d_tab, c->h, jobs, ch.count, S.Tbuf.p, st); }));
+  CUDA_TRY(c, timed(c, CWPIR_K_TENSOR, st, [&] { return cw::launch_tensor(c->d_tab, c->h, jobs, ch.count, S.Tbuf.p, st); }));
   CUDA_TRY(c, timed(c, CWPIR_K_SCALE, st, [&] { return cw::launch_scale(c->d_tab, c->h, S.Tbuf.p, ch.count, S.E.p, S.d_err, st); }));
   const bool rows = ch.mode == cw::ROOT_PM && P->rows_db;
   if (ch.mode == cw::INTERNAL && c->ksr) {
@@ -2244,7 +2244,7 @@ extern "C" int cwpir_mul_noalloc(cwpir_ctx *c, const uint64_t *d_a, const uint64
   CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_a, (u64)c->L * N, qa, pw, 2, true, st));
   CUDA_TRY(c, cw::launch_lift(c->d_tab, c->h, d_b, (u64)c->L * N, qb, pw, 2, true, st));
   CUDA_TRY(c, cw::launch_ntt(c->d_tab, c->h, qa, 4, pw, 0, (u32)LK, false, nullptr, 0, st));
-  CUDA_TRY(c, cw::launch_tensor_intt(c->d_tab, c->h, job_dev, 1, tb, st));
+  CUDA_TRY(c, cw::launch_tensor(c->d_tab, c->h, job_dev, 1, tb, st));
   CUDA_TRY(c, cw::launch_scale(c->d_tab, c->h, tb, 1, eb, err, st));
   CUDA_TRY(c, cw::launch_relin(c->d_tab, c->h, eb, 1, 1, job_dev, cw::ROOT_SEL, c->rlk.p,
                                c->rlk_s.p, nullptr, 1, 1, dn, nullptr, ob, st));

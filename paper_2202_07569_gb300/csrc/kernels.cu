@@ -364,7 +364,8 @@ __global__ void __launch_bounds__(NttShape32<LOGN>::threads, LOGN <= 13 ? 2 : 1)
     const u32 c = ntt_pos32<LOGN>(t, r);
     const u32 x0 = a0[c], x1 = a1[c], z0 = b0[c], z1 = b1[c];
     y[r] = mulmod_ext_lazy(x0, z0, E.e);
-    y[R + r] = csub32(mulmod_ext_lazy(x0, z1, E.e) + mulmod_ext_lazy(x1, z0, E.e), p2);
+    // d1: both products summed exactly (below 2^61), one reduction
+    y[R + r] = csub32(reduce_ext62_lazy(wmul(x0, z1) + wmul(x1, z0), E.e), p2);
     y[2 * R + r] = mulmod_ext_lazy(x1, z1, E.e);
   }
   // the three inverse transforms in lock-step: N d in [0, 2p)
@@ -1182,7 +1183,7 @@ cudaError_t launch_ntt_jobs_p(const DevTables *T, const DevTables &h, const MulJ
   return cudaGetLastError();
 }
 
-cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const MulJob *jobs,
+cudaError_t launch_tensor(const DevTables *T, const DevTables &h, const MulJob *jobs,
                                u32 njobs, u64 *Tbuf, cudaStream_t st) {
   if (!njobs) return cudaSuccess;
   CW_DISPATCH_LOGN(h.logN, {

@@ -91,7 +91,7 @@ cudaError_t launch_lift_jobs(const DevTables *T, const DevTables &h, const u64 *
                              const MulJob *jobs, u32 njobs, cudaStream_t st);
 cudaError_t launch_ntt_jobs_p(const DevTables *T, const DevTables &h, const MulJob *jobs,
                               u32 njobs, cudaStream_t st);
-cudaError_t launch_tensor_intt(const DevTables *T, const DevTables &h, const MulJob *jobs,
+cudaError_t launch_tensor(const DevTables *T, const DevTables &h, const MulJob *jobs,
                                u32 njobs, u64 *Tbuf, cudaStream_t st);
 cudaError_t launch_scale(const DevTables *T, const DevTables &h, const u64 *Tbuf, u32 njobs,
                          u64 *E, int *err, cudaStream_t st);

@@ -203,7 +203,7 @@ int emu_bfv_mul(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t, const uin
         if (which == 0) v = mulmod_ext_lazy((u32)a0[c], (u32)b0[c], X);
         else if (which == 2) v = mulmod_ext_lazy((u32)a1[c], (u32)b1[c], X);
         else {
-          v = mulmod_ext_lazy((u32)a0[c], (u32)b1[c], X) + mulmod_ext_lazy((u32)a1[c], (u32)b0[c], X);
+          v = reduce_ext62_lazy(wmul((u32)a0[c], (u32)b1[c]) + wmul((u32)a1[c], (u32)b0[c]), X);
           v = v >= p2 ? v - p2 : v;
         }
         o[c] = v >= X.p ? v - X.p : v;
