@@ -165,8 +165,8 @@ def imad_per_job(kind: str, m54: float, m30: float) -> float:
 # jobs of a launch, so a full launch's traffic is this figure times its
 # jobs.
 DRAM_BYTES_PER_JOB = {
-    "tensor": (79718400 + 132160000) / 128,  # k_tensor_ext, K = 15
-    "scale": (188808448 + 69972992) / 128,
+    "tensor": (79719936 + 132475392) / 128,  # k_tensor_ext, K = 15
+    "scale": (188826624 + 70107136) / 128,
     "row_ntt": (108978176 + 100567296) / 128,
     # the row sums (k_rows_mac); the once-per-row-group conversions are
     # left out
