@@ -1006,9 +1006,11 @@ def main():
         res = run_sharded(args, rank, world, dist)
         if rank == 0:
             line = dict(base, scaling="strong")
+            exch = ("one SUM all-reduce of the partial responses' residues, then modulo q_j"
+                    if args.exchange == "allreduce" else
+                    "partial responses all-gathered and summed modulo q_j")
             line["config"] = dict(base["config"], parallelism=(
-                f"database rows sharded over {world} GPU(s); partial responses all-gathered "
-                "and summed modulo q_j"))
+                f"database rows sharded over {world} GPU(s); {exch}"))
             if args.rows:
                 line["config"]["rows"] = args.rows
             line.update(res)
