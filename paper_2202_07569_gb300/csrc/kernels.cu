@@ -118,18 +118,6 @@ __device__ __forceinline__ void ntt_inv(NttRegs<LOGN> &x, u64 *s, const NttPrime
 template <int LOGN>
 using NttRegs32 = u32[NttShape32<LOGN>::R];
 
-// Shared-memory slot of coefficient i in an exchange of 32-bit words
-// between the layouts of windows wa and wb: one pad word per 16 (a warp's
-// indices are strided when a window is below 5) or, when both windows are
-// at least 5 (a warp then touches 32 consecutive indices, which one pad
-// per 16 puts two to a bank), one per 32.  Used by the extension tensor
-// (tensor 82.3 -> 81.4 ms per metric answer); in the single-transform
-// kernels its addressing cost registers (the row transforms 63.3 -> 67.1 ms).
-template <int RB>
-__device__ __forceinline__ u32 xslot(u32 i, u32 wa, u32 wb) {
-  return (wa >= 5 && wb >= 5) ? i + (i >> 5) : sidx<RB>(i);
-}
-
 template <int LOGN>
 __device__ __forceinline__ void ntt_fwd32(NttRegs32<LOGN> &x, u32 *s, const ExtNtt &P) {
   constexpr int RB = NttShape32<LOGN>::RB, R = NttShape32<LOGN>::R;

@@ -20,6 +20,18 @@ namespace cw {
 // shared-memory slot of coefficient i (one pad word per 2^RB)
 template <int RB>
 CW_HD u32 sidx(u32 i) { return i + (i >> RB); }
+// Shared-memory slot of coefficient i in an exchange of 32-bit words
+// between the layouts of windows wa and wb: one pad word per 16 (a warp's
+// indices are strided when a window is below 5) or, when both windows are
+// at least 5 (a warp then touches 32 consecutive indices, which one pad
+// per 16 puts two to a bank), one per 32.  Used by the extension tensor
+// (tensor 82.3 -> 81.4 ms per metric answer); in the single-transform
+// kernels its addressing cost registers (the row transforms 63.3 -> 67.1 ms).
+template <int RB>
+CW_HD u32 xslot(u32 i, u32 wa, u32 wb) {
+  return (wa >= 5 && wb >= 5) ? i + (i >> 5) : sidx<RB>(i);
+}
+
 // words of shared memory for an N-point transform
 template <int RB>
 CW_HD u32 smem_words(u32 N) { return N + (N >> RB); }

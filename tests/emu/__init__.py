@@ -26,7 +26,7 @@ def lib():
     l = C.CDLL(SO)
     u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
     U32, U64 = C.c_uint32, C.c_uint64
-    l.emu_tensor_intt_compare.argtypes = [U32, u64p, U64, u64p]
+    l.emu_tensor_intt_compare.argtypes = [U32, U32, u64p, U64, u64p]
     l.emu_tensor_intt_compare.restype = U64
     l.emu_bfv_mul.argtypes = [U32, U32, u64p, U64, u64p, u64p, u64p, u64p, C.c_int]
     l.emu_scale_p.argtypes = [U32, U32, u64p, U64, U64,

@@ -365,29 +365,42 @@ void pass_ntt32(u32 *a, const u32 *tw, u32 p, bool inverse) {
   for (u32 i = 0; i < N; ++i) a[i] = s[sidx<RB>(i)];
 }
 
-// Three 32-bit inverse transforms of one prime in lock-step (inv_pass32m).
+// Three 32-bit inverse transforms of one prime in lock-step (inv_pass32m),
+// thread by thread as the extension tensor runs them: registers per
+// thread, exchanges through one shared array per transform with the
+// tensor's slot mapping (xslot) between the windows of consecutive passes;
+// a slot collision or an out-of-range slot would corrupt the result.
 template <int LOGN, int RB>
 void pass_ntt32_x3(u32 *a, const u32 *tw, u32 p) {
   constexpr u32 R = 1u << RB;
-  const u32 N = 1u << LOGN, T = N / R;
-  std::vector<u32> s(3 * smem_words<RB>(N));
-  const u32 SW = smem_words<RB>(N);
-  for (int i = 0; i < 3; ++i)
-    for (u32 j = 0; j < N; ++j) s[i * SW + sidx<RB>(j)] = a[i * N + j];
+  const u32 N = 1u << LOGN, T = N / R, SW = smem_words<RB>(N);
+  std::vector<u32> reg(3ull * T * R), s(3ull * SW, 0xFFFFFFFFu);
+  u32 lo, c, w, wprev = 0;
+  Passes<LOGN, RB>::inv(0, lo, c, w);
+  for (u32 t = 0; t < T; ++t)
+    for (int i = 0; i < 3; ++i)
+      for (u32 r = 0; r < R; ++r) reg[(t * 3 + i) * R + r] = a[i * N + pass_idx<RB>(t, r, w)];
   for (int pp = 0; pp < Passes<LOGN, RB>::count; ++pp) {
-    u32 lo, c, w;
     Passes<LOGN, RB>::inv(pp, lo, c, w);
-    for (u32 t = 0; t < T; ++t) {
-      u32 x[3 * R];
-      for (int i = 0; i < 3; ++i)
-        for (u32 r = 0; r < R; ++r) x[i * R + r] = s[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))];
-      inv_pass32m<LOGN, RB, 3>(x, t, lo, c, w, tw + 2 * N, p);
-      for (int i = 0; i < 3; ++i)
-        for (u32 r = 0; r < R; ++r) s[i * SW + sidx<RB>(pass_idx<RB>(t, r, w))] = x[i * R + r];
+    if (pp > 0) {
+      for (u32 t = 0; t < T; ++t)
+        for (int i = 0; i < 3; ++i)
+          for (u32 r = 0; r < R; ++r) {
+            const u32 slot = xslot<RB>(pass_idx<RB>(t, r, wprev), wprev, w);
+            if (slot >= SW) return;  // leaves a unchanged: the caller's comparison fails
+            s[i * SW + slot] = reg[(t * 3 + i) * R + r];
+          }
+      for (u32 t = 0; t < T; ++t)
+        for (int i = 0; i < 3; ++i)
+          for (u32 r = 0; r < R; ++r)
+            reg[(t * 3 + i) * R + r] = s[i * SW + xslot<RB>(pass_idx<RB>(t, r, w), wprev, w)];
     }
+    for (u32 t = 0; t < T; ++t) inv_pass32m<LOGN, RB, 3>(&reg[t * 3 * R], t, lo, c, w, tw + 2 * N, p);
+    wprev = w;
   }
-  for (int i = 0; i < 3; ++i)
-    for (u32 j = 0; j < N; ++j) a[i * N + j] = s[i * SW + sidx<RB>(j)];
+  for (u32 t = 0; t < T; ++t)
+    for (int i = 0; i < 3; ++i)
+      for (u32 r = 0; r < R; ++r) a[i * N + pass_idx<RB>(t, r, wprev)] = reg[(t * 3 + i) * R + r];
 }
 
 template <int RB>
@@ -463,23 +476,27 @@ uint64_t emu_ntt_compare(uint32_t N, uint32_t L, const uint64_t *q, uint64_t t,
 }
 
 extern "C" {
-// The tensor kernel's inverse transforms (N = 8192, 16 coefficients a
-// thread): the three-transform 32-bit schedule on every extension prime
-// must leave each of three inputs (below 2p) as the single schedule does.
-// Returns the number of mismatches.
-uint64_t emu_tensor_intt_compare(uint32_t L, const uint64_t *q, uint64_t t, const uint64_t *data) {
-  const u32 N = 8192;
+// The tensor kernel's inverse transforms (N = 2^logN, logN 13 or 14, 16
+// coefficients a thread): the three-transform 32-bit schedule with the
+// kernel's exchanges on every extension prime must leave each of three
+// inputs (below 2p) as the single schedule does.  Returns the number of
+// mismatches.
+uint64_t emu_tensor_intt_compare(uint32_t logN, uint32_t L, const uint64_t *q, uint64_t t,
+                                 const uint64_t *data) {
+  const u32 N = 1u << logN;
   Emu E(N, L, q, t);
   uint64_t bad = 0;
   for (u32 k = 0; k < E.K; ++k) {
     const u64 pr = E.p[k];
     std::vector<u32> x3(3 * N), x1(N);
-    for (u32 i = 0; i < 3 * N; ++i) x3[i] = (u32)(data[(7 * i + 3) % N] % (2 * pr));  // below 2p
+    for (u32 i = 0; i < 3 * N; ++i) x3[i] = (u32)(data[(7 * i + 3) % 8192] % (2 * pr));  // below 2p
+    std::vector<u32> y(x3);
+    if (logN == 13) pass_ntt32_x3<13, 4>(y.data(), E.tw32[k].data(), (u32)pr);
+    else pass_ntt32_x3<14, 4>(y.data(), E.tw32[k].data(), (u32)pr);
     for (int j = 0; j < 3; ++j) {
       for (u32 i = 0; i < N; ++i) x1[i] = x3[j * N + i];
-      pass_ntt32<13, 4>(x1.data(), E.tw32[k].data(), (u32)pr, true);
-      std::vector<u32> y(x3);
-      pass_ntt32_x3<13, 4>(y.data(), E.tw32[k].data(), (u32)pr);
+      if (logN == 13) pass_ntt32<13, 4>(x1.data(), E.tw32[k].data(), (u32)pr, true);
+      else pass_ntt32<14, 4>(x1.data(), E.tw32[k].data(), (u32)pr, true);
       for (u32 i = 0; i < N; ++i) bad += y[j * N + i] != x1[i];
     }
   }

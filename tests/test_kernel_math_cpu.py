@@ -240,13 +240,15 @@ def test_row_basis_crt(orc, N, L, nr):
         assert [int(v) for v in out] == [x % qq for qq in q], x
 
 
-def test_tensor_inverse_schedules(orc):
-    """The tensor kernel's inverse transforms at N = 8192: the 32-bit
-    schedule that runs the three outputs in lock-step equals three single
+@pytest.mark.parametrize("logn,L", [(13, 4), (14, 7)])
+def test_tensor_inverse_schedules(orc, logn, L):
+    """The tensor kernel's inverse transforms at N = 8192 and 16384: the
+    32-bit schedule that runs the three outputs in lock-step, with the
+    kernel's shared-memory slots in each exchange, equals three single
     transforms for every extension prime."""
-    q = orc.primes(8192, 4)
+    q = orc.primes(1 << logn, L)
     data = syn.Stream(13).words(8192)
-    assert emu.lib().emu_tensor_intt_compare(4, np.array(q, np.uint64), T, data) == 0
+    assert emu.lib().emu_tensor_intt_compare(logn, L, np.array(q, np.uint64), T, data) == 0
 
 
 @pytest.mark.parametrize("N,L", [(1024, 2), (8192, 4), (16384, 7), (16384, 8)])
