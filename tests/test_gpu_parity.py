@@ -47,7 +47,7 @@ def test_mul_matches_oracle(N, L):
         assert np.array_equal(got, cl.O.bfv_mul(a, b, cl.rlk)), trial
 
 
-@pytest.mark.parametrize("N,L", [(1024, 1), (8192, 4), (16384, 7)])
+@pytest.mark.parametrize("N,L", [(1024, 1), (8192, 4), (16384, 7), (4096, 8)])
 def test_scale_down_exact_path_matches_oracle(N, L):
     """The scale-down's exact path, forced for every coefficient
     (CWPIR_OPT_SCALE_EXACT = 1): products and a selection entry equal the
