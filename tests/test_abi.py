@@ -99,3 +99,24 @@ def test_setup_rejects_bad_parameters(cudalib):
         with pytest.raises(B.CwpirError) as ei:
             B.Context(N, np.array(q, np.uint64), t, relin)
         assert ei.value.code == -1 and msg in str(ei.value), (N, len(q), t, str(ei.value))
+
+
+def test_kernel_classes_match_the_header(cudalib):
+    """The timing classes: the binding's count is the header's
+    CWPIR_K_CLASSES, and each class name the library reports is the one the
+    header documents beside its enumerator."""
+    from paper_2202_07569_gb300 import binding as B
+
+    src = open(os.path.join(ROOT, "include", "cwpir.h")).read()
+    assert int(re.search(r"CWPIR_K_CLASSES\s*=\s*(\d+)", src).group(1)) == B.K_CLASSES
+    documented = {}
+    for m in re.finditer(r"CWPIR_K_[A-Z]+\s*=\s*(\d+),\s*/\*(.*?)\*/", src, flags=re.S):
+        name = re.search(r'\("([a-z_]+)"', m.group(2))
+        if name:
+            documented[int(m.group(1))] = name.group(1)
+    assert sorted(documented) == list(range(B.K_CLASSES))
+    lib = ctypes.CDLL(cudalib)
+    lib.cwpir_kernel_class_name.restype = ctypes.c_char_p
+    lib.cwpir_kernel_class_name.argtypes = [ctypes.c_int]
+    for i in range(B.K_CLASSES):
+        assert lib.cwpir_kernel_class_name(i).decode() == documented[i], i
