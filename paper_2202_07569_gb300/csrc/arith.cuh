@@ -416,8 +416,9 @@ struct ScaleTabP {
 };
 
 // Sum of x_k times 27-bit halves h[k][j] of residues modulo q_j, plus
-// `extra` (below 2^61 - (K + 1) 2^57) and v times the halves g: the words
-// stay below 2^62 and their combination below 2^90; reduced modulo q_j.
+// `extra` and v times the halves g: with extra below 2^62 - (K + 1) 2^57
+// (at least 2^57 for K <= 30) the words stay below 2^62 and their
+// combination below 2^90; reduced modulo q_j.
 template <int K>
 CW_HD u64 sum_to_q(const u32 *x, const u32 (*h)[kMaxL][2], int j, u64 v, const u32 *g,
                    u64 extra, u64 q, u64 mu) {
